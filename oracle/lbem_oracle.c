@@ -1,0 +1,521 @@
+/*
+ * lbem_oracle.c -- plain FP64 CPU oracle of the lattice-Boltzmann scheme for
+ * electromagnetic waves of Hanasoge, Succi & Orszag, "Lattice Boltzmann Method
+ * for Electromagnetic Wave Propagation" (EPL; arXiv:1108.2651).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * statement of what the GPU library computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the product path
+ * never does.  It shares no code, header, table or helper with the CUDA
+ * library.
+ *
+ * What is stored: the FULL D x D tensor g_{i,alpha,beta} for every lattice
+ * direction i (paper, Sec. "Lattice BGK formulation": the distribution is a
+ * tensor with built-in antisymmetry g_{ab} = -g_{ba}).  Nothing here exploits
+ * that antisymmetry, so a test can check it bit for bit.
+ *
+ * Layout: site s = x + nx*(y + ny*z); g[((s*Q + i)*D + a)*D + b].
+ * Lattice (Sec. "Lattice BGK formulation", the 4+1 and 6+1 speed lattices):
+ *   c_0 = 0; c_1..c_D = +e_1..+e_D; c_{D+1}..c_{2D} = -e_1..-e_D.
+ *   In 2D this is the paper's counter-clockwise order (1,0),(0,1),(-1,0),(0,-1).
+ *   The 3D order is not given by the paper; any order gives the same fields.
+ *
+ * Readings of the paper taken here (each is also listed in the design notes):
+ *  R1  c_L^2 = sum_i w_i c_ix^2 = (1-w0)/D, the per-axis second moment of the
+ *      weights (the paper's "sum_i w_i c_i^2" read per axis, which is what
+ *      makes Eqs. 9-11 hold and gives its (1-w0)/3 for the 6+1 lattice).
+ *  R2  B_beta is read from the first moment R_{a b k} = sum_i c_ik g_iab as
+ *      B_beta = sum_{alpha != beta} R_{alpha beta alpha} (Eq. 10 with
+ *      gamma = alpha, summed over the D-1 tensor components that carry it),
+ *      and the equilibrium of Eq. 8 is built with B/(D-1).  In 2D this is
+ *      literally Eq. 8; in 3D it is the reading that is stable.  The wave
+ *      speed is then c_eff^2 = c_L^2/(D-1).
+ *  R3  The source of Eq. 3 uses the physical wave speed c_eff^2 and
+ *      1/eps0 = mu0 c_eff^2; the frequency-dispersive (convolution) part of
+ *      Eq. 3 is not modelled (the paper defers it).
+ *  R4  Order within a step: moments from the pre-collision g; fields are
+ *      reported from those moments; T is added once, post-collision, with the
+ *      source at time t (Eq. 17); then streaming (Eq. 18).
+ *  R5  grad(ln mu) by second-order central differences, periodic.
+ *  R6  Periodic boundaries in every direction.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXQ 7
+#define MAXD 3
+
+typedef struct {
+    int D, Q, nx, ny, nz;
+    long nsite;
+    int c[MAXQ][3]; /* lattice velocities, unused axes 0 */
+} lattice_t;
+
+/* Lattice of Sec. "Lattice BGK formulation": 2D rest particles plus +/- unit
+ * speeds along each axis. */
+static void make_lattice(lattice_t *L, int D, int nx, int ny, int nz) {
+    L->D = D;
+    L->Q = 2 * D + 1;
+    L->nx = nx;
+    L->ny = ny;
+    L->nz = (D == 3) ? nz : 1;
+    L->nsite = (long)L->nx * L->ny * L->nz;
+    memset(L->c, 0, sizeof(L->c));
+    for (int a = 0; a < D; a++) {
+        L->c[1 + a][a] = +1;
+        L->c[1 + D + a][a] = -1;
+    }
+}
+
+/* Levi-Civita symbol epsilon_{abc}, indices 0..2. */
+static double levi(int a, int b, int c) {
+    if (a == b || b == c || a == c) return 0.0;
+    /* even permutations of (0,1,2) */
+    if ((a == 0 && b == 1 && c == 2) || (a == 1 && b == 2 && c == 0) || (a == 2 && b == 0 && c == 1))
+        return 1.0;
+    return -1.0;
+}
+
+/* Site index of (x + dx, y + dy, z + dz) with periodic wrap. */
+static long shifted(const lattice_t *L, long s, int dx, int dy, int dz) {
+    long x = s % L->nx;
+    long y = (s / L->nx) % L->ny;
+    long z = s / ((long)L->nx * L->ny);
+    x = ((x + dx) % L->nx + L->nx) % L->nx;
+    y = ((y + dy) % L->ny + L->ny) % L->ny;
+    z = ((z + dz) % L->nz + L->nz) % L->nz;
+    return x + L->nx * (y + L->ny * z);
+}
+
+static inline double *G(const lattice_t *L, double *g, long s, int i) {
+    return g + ((s * L->Q + i) * L->D) * L->D;
+}
+
+/* Lattice weights (Sec. "Lattice BGK formulation"): moving particles all get
+ * w_i = (1 - w0)/(2D); the rest particle gets w0. */
+static double weight(const lattice_t *L, int i, double w0) {
+    return (i == 0) ? w0 : (1.0 - w0) / (2.0 * L->D);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Medium: Eq. 3's heterogeneity and c = 1/sqrt(mu0 eps0).                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * From relative permittivity eps_r and permeability mu_r per site:
+ *   c_eff^2 = c_ref^2 / (eps_r mu_r)             (c = 1/sqrt(mu0 eps0))
+ *   c_L^2   = (D-1) c_eff^2                       (reading R2)
+ *   w0      = 1 - D c_L^2                         (reading R1)
+ *   dlnmu_k = (ln mu(x+e_k) - ln mu(x-e_k)) / 2   (reading R5)
+ * mu_r may be NULL (mu = 1).  Returns the number of sites whose w0 falls
+ * outside [0, 1) or whose inputs are not finite and positive.
+ */
+long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r, const double *mu_r,
+               double *ceff2, double *cL2, double *w0, double *mu, double *dlnmu) {
+    lattice_t L;
+    make_lattice(&L, D, nx, ny, nz);
+    long bad = 0;
+    for (long s = 0; s < L.nsite; s++) {
+        double e = eps_r[s];
+        double m = mu_r ? mu_r[s] : 1.0;
+        if (!(e > 0.0) || !(m > 0.0) || !isfinite(e) || !isfinite(m)) {
+            bad++;
+            e = 1.0;
+            m = 1.0;
+        }
+        ceff2[s] = c_ref2 / (e * m);
+        cL2[s] = (D - 1) * ceff2[s];
+        w0[s] = 1.0 - D * cL2[s];
+        mu[s] = m;
+        if (!(w0[s] >= 0.0 && w0[s] < 1.0)) bad++;
+    }
+    for (long s = 0; s < L.nsite; s++) {
+        for (int k = 0; k < 3; k++) dlnmu[3 * s + k] = 0.0;
+        for (int k = 0; k < D; k++) {
+            int dp[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
+            dp[k] = 1;
+            dm[k] = -1;
+            long sp = shifted(&L, s, dp[0], dp[1], dp[2]);
+            long sm = shifted(&L, s, dm[0], dm[1], dm[2]);
+            dlnmu[3 * s + k] = 0.5 * (log(mu[sp]) - log(mu[sm]));
+        }
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Moments (Eqs. 9, 10 and the field recovery after Eq. 6).                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Moments of the pre-collision tensor distribution at one site:
+ *   Lambda_ab = c_L^2 sum_i g_iab                        (Eq. 9)
+ *   E_g       = -1/2 eps_{g a b} Lambda_ab               (recovery of E from Lambda)
+ *   R_abk     = sum_i c_ik g_iab                         (Eq. 10)
+ *   B_b       = sum_{a != b} R_{a b a}                    (reading R2)
+ * E and B are 3-vectors; in 2D only E_z, B_x, B_y can be non-zero.
+ */
+static void site_moments(const lattice_t *L, const double *gs, double cL2, double Lam[MAXD][MAXD], double E[3],
+                         double B[3]) {
+    const int D = L->D, Q = L->Q;
+    double R[MAXD][MAXD][MAXD];
+    for (int a = 0; a < D; a++)
+        for (int b = 0; b < D; b++) {
+            double sum = 0.0;
+            for (int i = 0; i < Q; i++) sum += gs[(i * D + a) * D + b];
+            Lam[a][b] = cL2 * sum;
+            for (int k = 0; k < D; k++) {
+                double r = 0.0;
+                for (int i = 0; i < Q; i++) r += L->c[i][k] * gs[(i * D + a) * D + b];
+                R[a][b][k] = r;
+            }
+        }
+    for (int g = 0; g < 3; g++) {
+        double e = 0.0;
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) e += levi(g, a, b) * Lam[a][b];
+        E[g] = -0.5 * e;
+    }
+    for (int b = 0; b < 3; b++) {
+        double v = 0.0;
+        if (b < D)
+            for (int a = 0; a < D; a++)
+                if (a != b) v += R[a][b][a];
+        B[b] = v;
+    }
+}
+
+/* Local equilibrium, Eq. 8:
+ *   g^(0)_iab = (w_i / c_L^2) [ Lambda_ab + c_ia Bq_b - c_ib Bq_a ]
+ * with Bq = B/(D-1) (reading R2). */
+static void equilibrium(const lattice_t *L, double cL2, double w0, double Lam[MAXD][MAXD], const double B[3],
+                        double *geq) {
+    const int D = L->D, Q = L->Q;
+    double Bq[3];
+    for (int k = 0; k < 3; k++) Bq[k] = B[k] / (D - 1);
+    for (int i = 0; i < Q; i++) {
+        double wc = weight(L, i, w0) / cL2;
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++)
+                geq[(i * D + a) * D + b] = wc * (Lam[a][b] + L->c[i][a] * Bq[b] - L->c[i][b] * Bq[a]);
+    }
+}
+
+/* Initial state g = g^(0)(E, B): Lambda_ab = -eps_{g a b} E_g (Sec. "The
+ * Maxwell Equations", conservative form) and B as given.  E, B are
+ * [nsite][3]; either may be NULL (zero). */
+void or_init(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *E, const double *B,
+             double *g) {
+    lattice_t L;
+    make_lattice(&L, D, nx, ny, nz);
+    for (long s = 0; s < L.nsite; s++) {
+        double Lam[MAXD][MAXD], Bs[3] = {0, 0, 0};
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) {
+                double v = 0.0;
+                if (E)
+                    for (int k = 0; k < 3; k++) v -= levi(k, a, b) * E[3 * s + k];
+                Lam[a][b] = v;
+            }
+        if (B)
+            for (int k = 0; k < 3; k++) Bs[k] = B[3 * s + k];
+        equilibrium(&L, cL2[s], w0[s], Lam, Bs, G(&L, g, s, 0));
+    }
+}
+
+/* E and B ([nsite][3]) of a pre-collision state. */
+void or_fields(int D, int nx, int ny, int nz, const double *cL2, const double *g, double *E, double *B) {
+    lattice_t L;
+    make_lattice(&L, D, nx, ny, nz);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < L.nsite; s++) {
+        double Lam[MAXD][MAXD];
+        site_moments(&L, g + s * L.Q * D * D, cL2[s], Lam, E + 3 * s, B + 3 * s);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Collision (Eq. 17) with the tensor source T of Sec. "Lattice BGK          */
+/* formulation" and the source S of Eq. 3.                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One site's post-collision state, Eq. 17 with Delta t = 1, tau = 1/2 (the
+ * non-dissipative choice of Sec. "Lattice BGK formulation"):
+ *   g'_iab = (1 - dt/tau) g_iab + (dt/tau) g^(0)_iab + T_iab dt
+ *   T_iab  = -(w_i/c_L^2) eps_{g a b} S_g
+ *   S_g    = c_eff^2 eps_{g b k} B_b d_k ln(mu) - mu c_eff^2 j_g     (Eq. 3, R3)
+ * j is the current density at this site and time (3-vector).
+ */
+static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2, double mus, const double dlnmu[3],
+                         const double j[3], const double *gin, double *gout, double E[3], double B[3]) {
+    const int D = L->D, Q = L->Q;
+    const double dt = 1.0, tau = 0.5;
+    double Lam[MAXD][MAXD], S[3], geq[MAXQ * MAXD * MAXD];
+    site_moments(L, gin, cL2, Lam, E, B);
+    for (int g = 0; g < 3; g++) {
+        double curl = 0.0;
+        for (int b = 0; b < 3; b++)
+            for (int k = 0; k < 3; k++) curl += levi(g, b, k) * B[b] * dlnmu[k];
+        S[g] = ceff2 * curl - mus * ceff2 * j[g];
+    }
+    equilibrium(L, cL2, w0, Lam, B, geq);
+    for (int i = 0; i < Q; i++) {
+        double wc = weight(L, i, w0) / cL2;
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) {
+                double T = 0.0;
+                for (int g = 0; g < 3; g++) T -= wc * levi(g, a, b) * S[g];
+                int n = (i * D + a) * D + b;
+                gout[n] = (1.0 - dt / tau) * gin[n] + (dt / tau) * geq[n] + T * dt;
+            }
+    }
+}
+
+/* Field sample of a receiver: comp 0..2 = E_x..E_z, 3..5 = B_x..B_z. */
+static double pick(const double E[3], const double B[3], int comp) { return comp < 3 ? E[comp] : B[comp - 3]; }
+
+typedef struct {
+    int nsrc;
+    const long *site;
+    const int *comp;    /* 0..2: component of j */
+    const double *amp;  /* [nsrc][nt]: j(t) */
+    int nt;
+} sources_t;
+
+/* j at a site and time, summed over the point sources there. */
+static void current_at(const sources_t *src, long s, int t, double j[3]) {
+    j[0] = j[1] = j[2] = 0.0;
+    if (!src) return;
+    for (int k = 0; k < src->nsrc; k++)
+        if (src->site[k] == s && t >= 0 && t < src->nt) j[src->comp[k]] += src->amp[(long)k * src->nt + t];
+}
+
+/*
+ * Advance nsteps time steps, Eqs. 17 then 18.  g holds the pre-collision
+ * state at time t0 on entry and at t0 + nsteps on exit.  j(t) is taken from
+ * amp[k][t] for t in [0, nt).  Receivers record (before each collision) the
+ * field at time t0 + n into traces[r][n], n = 0..nsteps-1.  Returns 0.
+ */
+int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2, const double *mu,
+           const double *dlnmu, double *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
+           const double *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, double *traces) {
+    lattice_t L;
+    make_lattice(&L, D, nx, ny, nz);
+    const long per = (long)L.Q * D * D;
+    double *gpost = malloc(sizeof(double) * per * L.nsite);
+    double *E = malloc(sizeof(double) * 3 * L.nsite);
+    double *B = malloc(sizeof(double) * 3 * L.nsite);
+    sources_t src = {nsrc, src_site, src_comp, src_amp, nt};
+    for (int n = 0; n < nsteps; n++) {
+        int t = t0 + n;
+        /* collision at every site (Eq. 17) */
+#pragma omp parallel for schedule(static)
+        for (long s = 0; s < L.nsite; s++) {
+            double j[3];
+            current_at(&src, s, t, j);
+            collide_site(&L, cL2[s], w0[s], ceff2[s], mu[s], dlnmu + 3 * s, j, g + s * per, gpost + s * per, E + 3 * s,
+                         B + 3 * s);
+        }
+        for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = pick(E + 3 * rec_site[r], B + 3 * rec_site[r], rec_comp[r]);
+        /* streaming (Eq. 18): g_i(x + c_i, t+1) = g'_i(x, t) */
+#pragma omp parallel for schedule(static)
+        for (long s = 0; s < L.nsite; s++)
+            for (int i = 0; i < L.Q; i++) {
+                long d = shifted(&L, s, L.c[i][0], L.c[i][1], L.c[i][2]);
+                memcpy(G(&L, g, d, i), G(&L, gpost, s, i), sizeof(double) * D * D);
+            }
+    }
+    free(gpost);
+    free(E);
+    free(B);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics (Sec. "Heterogeneous media"; Eq. 19's concern with div B).    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * out[0] = field energy  sum_x sum_a (B_a^2 + E_a^2 / c_eff^2)   (Sec. "Heterogeneous media")
+ * out[1] = sum_x sum_i sum_ab g_iab^2 / w_i  (terms with w_i = 0 skipped)
+ * out[2] = sqrt( sum_x (div B)^2 ), div B by periodic central differences
+ * Sums run over sites in order, serially.
+ */
+void or_diagnostics(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2,
+                    const double *g, double *out) {
+    lattice_t L;
+    make_lattice(&L, D, nx, ny, nz);
+    double *E = malloc(sizeof(double) * 3 * L.nsite), *B = malloc(sizeof(double) * 3 * L.nsite);
+    or_fields(D, nx, ny, nz, cL2, g, E, B);
+    double en = 0.0, inv = 0.0, dv = 0.0;
+    for (long s = 0; s < L.nsite; s++) {
+        for (int a = 0; a < 3; a++) en += B[3 * s + a] * B[3 * s + a] + E[3 * s + a] * E[3 * s + a] / ceff2[s];
+        for (int i = 0; i < L.Q; i++) {
+            double w = weight(&L, i, w0[s]);
+            if (w == 0.0) continue;
+            const double *gi = g + (s * L.Q + i) * D * D;
+            for (int n = 0; n < D * D; n++) inv += gi[n] * gi[n] / w;
+        }
+        double div = 0.0;
+        for (int k = 0; k < D; k++) {
+            int dp[3] = {0, 0, 0};
+            dp[k] = 1;
+            long sp = shifted(&L, s, dp[0], dp[1], dp[2]);
+            long sm = shifted(&L, s, -dp[0], -dp[1], -dp[2]);
+            div += 0.5 * (B[3 * sp + k] - B[3 * sm + k]);
+        }
+        dv += div * div;
+    }
+    out[0] = en;
+    out[1] = inv;
+    out[2] = sqrt(dv);
+    free(E);
+    free(B);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the time stepping (not in the paper: gradient of a receiver    */
+/* misfit with respect to the permittivity).                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Post-collision state of one site as a function of c_L^2 alone, with
+ * w0 = 1 - D c_L^2 and c_eff^2 = c_L^2/(D-1) (readings R1, R2).  Written out,
+ * every term of Eq. 17 is affine in c_L^2 for fixed g, mu and j:
+ *   moving i: (w_i/c_L^2) = 1/(2D) * D = 1/2 and Lambda = c_L^2 sum g,
+ *   rest i  : w0 = 1 - D c_L^2,
+ *   S       : proportional to c_eff^2, multiplied by w_i/c_L^2 in T.
+ * The adjoint below uses that: d g'/d c_L^2 = (g'(2c) - g'(c)) / c exactly.
+ */
+static void collide_c(const lattice_t *L, double c, double mus, const double dlnmu[3], const double j[3],
+                      const double *gin, double *gout) {
+    double E[3], B[3];
+    collide_site(L, c, 1.0 - L->D * c, c / (L->D - 1), mus, dlnmu, j, gin, gout, E, B);
+}
+
+/*
+ * Gradient of the misfit
+ *   Lmis = 1/2 sum_{n<nsteps} sum_r ( F_r(t0+n) - obs[r][n] )^2,
+ * F_r the receiver fields recorded by or_run, with respect to eps_r at every
+ * site, for a run that starts from g0 (pre-collision state at t0, held fixed).
+ * Backward recursion over stored states: with  g^{n+1} = S (M_n g^n + T_n),
+ *   lam^{N} = 0,  lam^n = M_n^T S^T lam^{n+1} + dl_n/dg^n,
+ *   dL/dc_L^2(x) += (S^T lam^{n+1})(x) . d(M_n g^n + T_n)(x)/dc_L^2 + dl_n/dc_L^2(x)
+ * and  dL/deps_r = dL/dc_L^2 * dc_L^2/deps_r = -dL/dc_L^2 * c_L^2 / eps_r.
+ * M_n^T is applied as the transpose of the explicit local matrix of
+ * collide_c (built column by column from unit vectors).
+ * Returns the misfit; grad_eps is [nsite].
+ */
+double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const double *cL2, const double *mu,
+                  const double *dlnmu, const double *g0, int t0, int nsteps, int nsrc, const long *src_site,
+                  const int *src_comp, const double *src_amp, int nt, int nrec, const long *rec_site,
+                  const int *rec_comp, const double *obs, double *grad_eps) {
+    lattice_t L;
+    make_lattice(&L, D, nx, ny, nz);
+    const long per = (long)L.Q * D * D;
+    const long ns = L.nsite;
+    double *w0 = malloc(sizeof(double) * ns), *ceff2 = malloc(sizeof(double) * ns);
+    for (long s = 0; s < ns; s++) {
+        w0[s] = 1.0 - D * cL2[s];
+        ceff2[s] = cL2[s] / (D - 1);
+    }
+    /* forward pass, keeping every pre-collision state */
+    double *states = malloc(sizeof(double) * per * ns * (nsteps + 1));
+    double *traces = malloc(sizeof(double) * (nrec > 0 ? nrec : 1) * (nsteps > 0 ? nsteps : 1));
+    memcpy(states, g0, sizeof(double) * per * ns);
+    for (int n = 0; n < nsteps; n++) {
+        memcpy(states + (long)(n + 1) * per * ns, states + (long)n * per * ns, sizeof(double) * per * ns);
+        double *tr_n = malloc(sizeof(double) * (nrec > 0 ? nrec : 1));
+        or_run(D, nx, ny, nz, cL2, w0, ceff2, mu, dlnmu, states + (long)(n + 1) * per * ns, t0 + n, 1, nsrc, src_site,
+               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n);
+        for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = tr_n[r];
+        free(tr_n);
+    }
+    double misfit = 0.0;
+    for (int r = 0; r < nrec; r++)
+        for (int n = 0; n < nsteps; n++) {
+            double d = traces[(long)r * nsteps + n] - obs[(long)r * nsteps + n];
+            misfit += 0.5 * d * d;
+        }
+    /* backward pass */
+    double *lam = calloc(per * ns, sizeof(double));   /* lam^{n+1} */
+    double *lpost = malloc(sizeof(double) * per * ns); /* S^T lam^{n+1} */
+    double *gcl = calloc(ns, sizeof(double));          /* dL/dc_L^2 */
+    for (int n = nsteps - 1; n >= 0; n--) {
+        const double *gn = states + (long)n * per * ns;
+        /* S^T: streaming moved g'_i(x) to x + c_i, so its transpose pulls back */
+        for (long s = 0; s < ns; s++)
+            for (int i = 0; i < L.Q; i++) {
+                long d = shifted(&L, s, L.c[i][0], L.c[i][1], L.c[i][2]);
+                memcpy(G(&L, lpost, s, i), G(&L, lam, d, i), sizeof(double) * D * D);
+            }
+#pragma omp parallel for schedule(static)
+        for (long s = 0; s < ns; s++) {
+            double j[3], zero[3] = {0, 0, 0};
+            sources_t src = {nsrc, src_site, src_comp, src_amp, nt};
+            current_at(&src, s, t0 + n, j);
+            const double *gs = gn + s * per;
+            const double *ls = lpost + s * per;
+            double *out = lam + s * per;
+            /* lam^n(x) = M^T lpost(x): column m of M is collide_c(unit e_m) with j = 0 */
+            double unit[MAXQ * MAXD * MAXD], col[MAXQ * MAXD * MAXD];
+            for (long m = 0; m < per; m++) {
+                memset(unit, 0, sizeof(unit));
+                unit[m] = 1.0;
+                collide_c(&L, cL2[s], mu[s], dlnmu + 3 * s, zero, unit, col);
+                double v = 0.0;
+                for (long q = 0; q < per; q++) v += col[q] * ls[q];
+                out[m] = v;
+            }
+            /* dL/dc_L^2 through the collision and source (affine in c_L^2) */
+            double ga[MAXQ * MAXD * MAXD], gb[MAXQ * MAXD * MAXD];
+            collide_c(&L, 2.0 * cL2[s], mu[s], dlnmu + 3 * s, j, gs, ga);
+            collide_c(&L, cL2[s], mu[s], dlnmu + 3 * s, j, gs, gb);
+            double v = 0.0;
+            for (long q = 0; q < per; q++) v += ls[q] * (ga[q] - gb[q]) / cL2[s];
+            gcl[s] += v;
+        }
+        /* receivers: dl_n/dg^n and dl_n/dc_L^2 (E = -1/2 eps Lambda, Lambda = c_L^2 sum g) */
+        for (int r = 0; r < nrec; r++) {
+            long s = rec_site[r];
+            int comp = rec_comp[r];
+            double d = traces[(long)r * nsteps + n] - obs[(long)r * nsteps + n];
+            const double *gs = gn + s * per;
+            double *out = lam + s * per;
+            for (int i = 0; i < L.Q; i++)
+                for (int a = 0; a < D; a++)
+                    for (int b = 0; b < D; b++) {
+                        int m = (i * D + a) * D + b;
+                        if (comp < 3) {
+                            double e = -0.5 * levi(comp, a, b);
+                            out[m] += d * e * cL2[s];
+                            gcl[s] += d * e * gs[m];
+                        } else {
+                            int bc = comp - 3; /* B_bc = sum_{a != bc} sum_i c_ia g_{i a bc} */
+                            if (b == bc && a != bc) out[m] += d * L.c[i][a];
+                        }
+                    }
+        }
+    }
+    for (long s = 0; s < ns; s++) grad_eps[s] = -gcl[s] * cL2[s] / eps_r[s];
+    free(lam);
+    free(lpost);
+    free(gcl);
+    free(states);
+    free(traces);
+    free(w0);
+    free(ceff2);
+    return misfit;
+}
+
+/* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+int or_threads(void) {
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

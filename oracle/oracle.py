@@ -1,0 +1,187 @@
+"""ctypes wrapper of the FP64 C oracle (lbem_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Grids are numpy arrays indexed [y, x] in 2D and
+[z, y, x] in 3D, so that the flat C-order index is s = x + nx*(y + ny*z), the
+oracle's site index.  The state g has shape grid + (Q, D, D): the full tensor
+g_{i,alpha,beta} of the paper's Sec. "Lattice BGK formulation".
+"""
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build_oracle import build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        I, D_ = C.c_int, C.c_double
+        lib.or_medium.restype = C.c_long
+        lib.or_medium.argtypes = [I, I, I, I, D_, dp, C.c_void_p, dp, dp, dp, dp, dp]
+        lib.or_init.restype = None
+        lib.or_init.argtypes = [I, I, I, I, dp, dp, C.c_void_p, C.c_void_p, dp]
+        lib.or_fields.restype = None
+        lib.or_fields.argtypes = [I, I, I, I, dp, dp, dp, dp]
+        lib.or_run.restype = I
+        lib.or_run.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp]
+        lib.or_diagnostics.restype = None
+        lib.or_diagnostics.argtypes = [I, I, I, I, dp, dp, dp, dp, dp]
+        lib.or_adjoint.restype = D_
+        lib.or_adjoint.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, dp]
+        lib.or_threads.restype = I
+        lib.or_threads.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return _load().or_threads()
+
+
+@dataclass
+class Oracle:
+    """A medium on a periodic grid, as the oracle sees it (all FP64)."""
+
+    D: int
+    shape: tuple  # (ny, nx) or (nz, ny, nx)
+    eps_r: np.ndarray
+    ceff2: np.ndarray
+    cL2: np.ndarray
+    w0: np.ndarray
+    mu: np.ndarray
+    dlnmu: np.ndarray  # grid + (3,)
+    bad: int
+
+    @property
+    def dims(self):
+        if self.D == 2:
+            ny, nx = self.shape
+            return nx, ny, 1
+        nz, ny, nx = self.shape
+        return nx, ny, nz
+
+    @property
+    def Q(self):
+        return 2 * self.D + 1
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def medium(D, eps_r, mu_r=None, c_ref2=None) -> Oracle:
+    """Medium upload: eps_r, mu_r -> c_eff^2, c_L^2, w0, grad ln mu (Eq. 3)."""
+    lib = _load()
+    eps_r = _f64(eps_r)
+    shape = eps_r.shape
+    assert len(shape) == D
+    if c_ref2 is None:
+        c_ref2 = 0.5 if D == 2 else 1.0 / 6.0
+    n = eps_r.size
+    out = [np.empty(n) for _ in range(4)]
+    dl = np.empty(3 * n)
+    if mu_r is None:
+        mu_ptr = None
+    else:
+        mu_r = _f64(mu_r)
+        assert mu_r.shape == shape
+        mu_ptr = mu_r.ctypes.data_as(C.c_void_p)
+    nx, ny, nz = (shape[-1], shape[-2], shape[0] if D == 3 else 1)
+    bad = lib.or_medium(D, nx, ny, nz, float(c_ref2), eps_r.ravel(), mu_ptr, *out, dl)
+    ceff2, cL2, w0, mu = (o.reshape(shape) for o in out)
+    return Oracle(D, shape, eps_r, ceff2, cL2, w0, mu, dl.reshape(shape + (3,)), int(bad))
+
+
+def init_state(m: Oracle, E=None, B=None) -> np.ndarray:
+    """g = g^(0)(E, B) at every site (Eq. 8); E, B have shape grid + (3,)."""
+    lib = _load()
+    g = np.zeros(m.shape + (m.Q, m.D, m.D))
+    Ep = None if E is None else _f64(E, m.shape + (3,))
+    Bp = None if B is None else _f64(B, m.shape + (3,))
+    lib.or_init(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(),
+                None if Ep is None else Ep.ctypes.data_as(C.c_void_p),
+                None if Bp is None else Bp.ctypes.data_as(C.c_void_p), g.reshape(-1))
+    return g
+
+
+def _sources(sources, nsite):
+    if sources is None:
+        return 0, np.zeros(1, np.int64), np.zeros(1, np.int32), np.zeros(1), 1
+    site = np.ascontiguousarray(sources["site"], dtype=np.int64).ravel()
+    comp = np.ascontiguousarray(sources["comp"], dtype=np.int32).ravel()
+    amp = _f64(sources["amp"])
+    if amp.ndim == 1:
+        amp = amp[None, :]
+    assert amp.shape[0] == site.size == comp.size
+    assert np.all((site >= 0) & (site < nsite)) and np.all((comp >= 0) & (comp < 3))
+    return site.size, site, comp, np.ascontiguousarray(amp).ravel(), amp.shape[1]
+
+
+def _receivers(receivers, nsite):
+    if receivers is None:
+        return 0, np.zeros(1, np.int64), np.zeros(1, np.int32)
+    site = np.ascontiguousarray(receivers["site"], dtype=np.int64).ravel()
+    comp = np.ascontiguousarray(receivers["comp"], dtype=np.int32).ravel()
+    assert np.all((site >= 0) & (site < nsite)) and np.all((comp >= 0) & (comp < 6))
+    return site.size, site, comp
+
+
+def run(m: Oracle, g: np.ndarray, nsteps: int, t0: int = 0, sources=None, receivers=None) -> np.ndarray:
+    """Advance g (in place) by nsteps steps of Eqs. 17-18; returns receiver traces [nrec, nsteps].
+
+    sources: dict(site=flat indices, comp=0..2, amp=[nsrc, nt] current density j(t)).
+    receivers: dict(site=flat indices, comp=0..5 for E_x..E_z, B_x..B_z).
+    """
+    lib = _load()
+    assert g.dtype == np.float64 and g.flags.c_contiguous and g.shape == m.shape + (m.Q, m.D, m.D)
+    n = m.cL2.size
+    ns, ss, sc, sa, nt = _sources(sources, n)
+    nr, rs, rc = _receivers(receivers, n)
+    traces = np.zeros(max(nr, 1) * max(nsteps, 1))
+    lib.or_run(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(), m.mu.ravel(), m.dlnmu.reshape(-1),
+               g.reshape(-1), int(t0), int(nsteps), ns, ss, sc, sa, nt, nr, rs, rc, traces)
+    return traces[: nr * nsteps].reshape(nr, nsteps)
+
+
+def fields(m: Oracle, g: np.ndarray):
+    """E, B (each grid + (3,)) from the moments of a pre-collision state."""
+    lib = _load()
+    n = m.cL2.size
+    E = np.empty(3 * n)
+    B = np.empty(3 * n)
+    lib.or_fields(m.D, *m.dims, m.cL2.ravel(), np.ascontiguousarray(g).reshape(-1), E, B)
+    return E.reshape(m.shape + (3,)), B.reshape(m.shape + (3,))
+
+
+def diagnostics(m: Oracle, g: np.ndarray):
+    """(field energy, sum g^2/w invariant, ||div B||_2) of a pre-collision state."""
+    lib = _load()
+    out = np.zeros(3)
+    lib.or_diagnostics(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(),
+                       np.ascontiguousarray(g).reshape(-1), out)
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def adjoint(m: Oracle, g0: np.ndarray, nsteps: int, sources, receivers, obs, t0: int = 0):
+    """Misfit 1/2 sum (trace - obs)^2 and its gradient with respect to eps_r (grid shape)."""
+    lib = _load()
+    n = m.cL2.size
+    ns, ss, sc, sa, nt = _sources(sources, n)
+    nr, rs, rc = _receivers(receivers, n)
+    obs = _f64(obs).reshape(nr, nsteps)
+    grad = np.zeros(n)
+    mis = lib.or_adjoint(m.D, *m.dims, m.eps_r.ravel(), m.cL2.ravel(), m.mu.ravel(), m.dlnmu.reshape(-1),
+                         np.ascontiguousarray(g0).reshape(-1), int(t0), int(nsteps), ns, ss, sc, sa, nt, nr, rs, rc,
+                         np.ascontiguousarray(obs).ravel(), grad)
+    return float(mis), grad.reshape(m.shape)

@@ -1,0 +1,575 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+printed lattice and constants (tests/golden), exact identities of the
+equilibrium (Eqs. 9-11), exact conservation laws, the closed-form dispersion
+relation of the scheme's exact finite-difference form, time reversibility, an
+independent finite-difference program, and pseudo-spectral Maxwell solvers.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import crosscheck as X
+import oracle as O
+from paper_1108_2651_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden_lattice():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "d2q5_lattice.txt")) if l.strip() and not l.startswith("#")]
+    return {int(r[0]): (int(r[1]), int(r[2])) for r in rows}
+
+
+def golden_constants():
+    out = {}
+    for l in open(os.path.join(GOLDEN, "paper_constants.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()[:2]
+            out[k] = float(v)
+    return out
+
+
+def lattice3():
+    """6+1 lattice: rest plus the six unit vectors (order as the oracle's: +x,+y,+z,-x,-y,-z)."""
+    c = [(0, 0, 0)]
+    for s in (1, -1):
+        for a in range(3):
+            v = [0, 0, 0]
+            v[a] = s
+            c.append(tuple(v))
+    return np.array(c)
+
+
+def lattice2():
+    L = golden_lattice()
+    return np.array([L[i] for i in range(5)])
+
+
+def levi3():
+    e = np.zeros((3, 3, 3))
+    e[0, 1, 2] = e[1, 2, 0] = e[2, 0, 1] = 1
+    e[0, 2, 1] = e[2, 1, 0] = e[1, 0, 2] = -1
+    return e
+
+
+def antisym_err(g):
+    return np.abs(g + np.swapaxes(g, -1, -2)).max()
+
+
+def pull_back(g, D):
+    """Inverse of the streaming of Eq. 18 (a permutation): g_i(x) <- g_i(x + c_i)."""
+    C = lattice2() if D == 2 else lattice3()
+    out = np.empty_like(g)
+    for i, c in enumerate(C):
+        # grid axes are [y, x] or [z, y, x]; c is (cx, cy[, cz])
+        shift = tuple(-int(v) for v in c[::-1])
+        out[..., i, :, :] = np.roll(g[..., i, :, :], shift, axis=tuple(range(D)))
+    return out
+
+
+def collide_only(m, g):
+    """The collision M g alone (Eq. 17, no source) = S^{-1}(one oracle step)."""
+    h = g.copy()
+    O.run(m, h, 1)
+    return pull_back(h, m.D)
+
+
+def reflect(g, D):
+    """Swap each population with its opposite direction (c_i -> -c_i)."""
+    out = g.copy()
+    for a in range(D):
+        out[..., 1 + a, :, :] = g[..., 1 + D + a, :, :]
+        out[..., 1 + D + a, :, :] = g[..., 1 + a, :, :]
+    return out
+
+
+# --------------------------------------------------------------------------- paper's table and constants
+
+
+def test_lattice_matches_paper_table():
+    """A pure-equilibrium state at one site streams population i to x + c_i with the paper's c_i."""
+    N = 7
+    eps = np.full((N, N), 2.0)  # w0 = 0.5, so the rest population is non-zero too
+    m = O.medium(2, eps)
+    E = np.zeros((N, N, 3))
+    E[3, 3, 2] = 1.0
+    g = O.init_state(m, E=E)
+    g1 = g.copy()
+    O.run(m, g1, 1)
+    for i, (cx, cy) in golden_lattice().items():
+        mask = np.abs(g1[:, :, i]).max(axis=(-1, -2)) > 0
+        ys, xs = np.nonzero(mask)
+        assert list(zip(xs, ys)) == [((3 + cx) % N, (3 + cy) % N)], i
+        np.testing.assert_array_equal(g1[(3 + cy) % N, (3 + cx) % N, i], g[3, 3, i])
+
+
+def test_lattice_3d_unit_speeds():
+    N = 5
+    m = O.medium(3, np.full((N, N, N), 2.0))
+    E = np.zeros((N, N, N, 3))
+    E[2, 2, 2] = (0.3, -0.7, 1.0)
+    g = O.init_state(m, E=E)
+    O.run(m, g, 1)
+    seen = set()
+    for i in range(7):
+        z, y, x = np.nonzero(np.abs(g[:, :, :, i]).max(axis=(-1, -2)) > 0)
+        assert len(x) == 1
+        seen.add((int(x[0]) - 2, int(y[0]) - 2, int(z[0]) - 2))
+    assert seen == set(map(tuple, lattice3()))
+
+
+def test_tau_half_makes_collision_an_involution():
+    """tau = dt/2 (paper's non-dissipative choice): (1 - dt/tau) = -1, so collision twice is the identity
+    (source-free, uniform mu: the B x grad(ln mu) source would add a B-dependent term)."""
+    k = golden_constants()
+    assert 1 - k["dt"] / k["tau"] == -1.0
+    for D, shape in ((2, (6, 7)), (3, (4, 5, 3))):
+        eps, _ = W.random_medium(shape, 11)
+        m = O.medium(D, eps)
+        E, B = W.random_fields(shape, 12)
+        g = O.init_state(m, E, B)
+        rng = np.random.default_rng(0)
+        a = rng.standard_normal(g.shape)
+        g = g + (a - np.swapaxes(a, -1, -2))  # add non-equilibrium, antisymmetric parts
+        np.testing.assert_allclose(collide_only(m, collide_only(m, g)), g, atol=1e-13, rtol=0)
+
+
+def test_weights_and_lattice_speed_constants():
+    """w_i = (1-w0)/(2D) and the 6+1 lattice's c^2 = (1-w0)/3 (paper), read off the oracle's equilibrium."""
+    k = golden_constants()
+    # D = 2, w0 = 0.2  <=>  c_L^2 = 0.4 = c_eff^2 = c_ref^2/eps with c_ref^2 = 1/2
+    m = O.medium(2, np.full((3, 3), 0.5 / 0.4))
+    assert abs(m.w0[0, 0] - 0.2) < 1e-15
+    E = np.zeros((3, 3, 3))
+    E[1, 1, 2] = 1.0
+    g = O.init_state(m, E=E)
+    lam = -1.0  # Lambda_xy = -E_z
+    # g^(0)_i = (w_i/c^2) Lambda  =>  w_i = g_i c^2 / Lambda
+    w_moving = g[1, 1, 1, 0, 1] * m.cL2[1, 1] / lam
+    assert abs(w_moving - k["w_moving_D2_w0_0.2"]) < 1e-15
+    # D = 3, w0 = 0.4: the equilibrium's c^2 = (1-w0)/3 = 0.2
+    m3 = O.medium(3, np.full((2, 2, 2), (1 / 6) / (0.2 / 2)))
+    assert abs(m3.w0[0, 0, 0] - 0.4) < 1e-14
+    assert abs(m3.cL2[0, 0, 0] - k["c2_D3_w0_0.4"]) < 1e-15
+
+
+def test_medium_upload_relations():
+    for D, shape in ((2, (5, 6)), (3, (3, 4, 5))):
+        eps, mu = W.random_medium(shape, 3, mu=True)
+        m = O.medium(D, eps, mu)
+        assert m.bad == 0
+        c_ref2 = W.C_REF2[D]
+        np.testing.assert_allclose(m.ceff2 * eps * mu, c_ref2, rtol=1e-15)
+        np.testing.assert_allclose(m.w0 + D * m.cL2, 1.0, rtol=1e-15)
+        # vacuum gives zero rest weight at the default reference speed
+        mv = O.medium(D, np.ones(shape))
+        assert np.all(mv.w0 == 0.0)
+        # central-difference gradient of ln mu (periodic), x component
+        lm = np.log(mu)
+        ax = D - 1
+        np.testing.assert_allclose(m.dlnmu[..., 0], 0.5 * (np.roll(lm, -1, ax) - np.roll(lm, 1, ax)), atol=1e-15)
+    # invalid media are flagged: w0 < 0 (faster than the reference speed), non-positive eps
+    bad = np.ones((4, 4))
+    bad[0, 0] = 0.5
+    bad[1, 1] = -1.0
+    assert O.medium(2, bad).bad == 2
+
+
+# --------------------------------------------------------------------------- equilibrium identities (Eqs. 9-11)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_equilibrium_moments(D):
+    shape = (4, 5) if D == 2 else (3, 4, 2)
+    eps, _ = W.random_medium(shape, 21)
+    m = O.medium(D, eps)
+    E, B = W.random_fields(shape, 22)
+    if D == 2:
+        E[..., :2] = 0.0
+        B[..., 2] = 0.0
+    g = O.init_state(m, E, B)
+    C = lattice2() if D == 2 else lattice3()
+    eps3 = levi3()[:, :D, :D]
+    Lam = -np.einsum("gab,...g->...ab", eps3, E)  # Lambda_ab = -eps_{g a b} E_g
+    Bq = B[..., :D] / (D - 1)
+    c2 = m.cL2[..., None, None]
+    # Eq. 9: sum_i g^(0) = Lambda / c^2
+    np.testing.assert_allclose(g.sum(axis=-3), Lam / c2, atol=1e-12)
+    # Eq. 10: sum_i c_ig g^(0)_iab = delta_ga B_b - delta_gb B_a (with B/(D-1), see reading R2)
+    G3 = np.einsum("ig,...iab->...abg", C, g)
+    I = np.eye(D)
+    expect = np.einsum("ga,...b->...abg", I, Bq) - np.einsum("gb,...a->...abg", I, Bq)
+    np.testing.assert_allclose(G3, expect, atol=1e-12)
+    # Eq. 11: sum_i c_ig c_ik g^(0)_iab = delta_gk Lambda_ab
+    G4 = np.einsum("ig,ik,...iab->...abgk", C, C, g)
+    np.testing.assert_allclose(G4, np.einsum("gk,...ab->...abgk", I, Lam), atol=1e-12)
+    # recovery of the fields from the moments (Sec. "The Maxwell Equations"): E_g = -1/2 eps_gab Lambda_ab
+    Ef, Bf = O.fields(m, g)
+    np.testing.assert_allclose(Ef, E, atol=1e-13)
+    np.testing.assert_allclose(Bf, B, atol=1e-13)
+
+
+# --------------------------------------------------------------------------- exact structure of the update
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_antisymmetry_bitwise_every_step(D):
+    shape = (9, 8) if D == 2 else (5, 4, 6)
+    eps, mu = W.random_medium(shape, 31, mu=True)
+    m = O.medium(D, eps, mu)
+    E, B = W.random_fields(shape, 32)
+    g = O.init_state(m, E, B)
+    n = int(np.prod(shape))
+    rng = np.random.default_rng(33)
+    src = dict(site=np.arange(n), comp=rng.integers(0, 3, n), amp=rng.standard_normal((n, 20)))
+    for t in range(20):
+        assert antisym_err(g) == 0.0
+        assert np.all(np.diagonal(g, axis1=-2, axis2=-1) == 0.0)
+        O.run(m, g, 1, t0=t, sources=src)
+    assert antisym_err(g) == 0.0
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_global_conservation_and_source_injection(D):
+    """Eq. 12 per site + permutation streaming: sum_x sum_i g_iab changes only by sum_x sum_i T_iab,
+    and sum_i T_iab = -eps_gab S_g / c^2 = eps_gab j_g / (D-1) for mu = 1; sum_x B is conserved."""
+    shape = (10, 9) if D == 2 else (5, 6, 4)
+    eps, _ = W.random_medium(shape, 41)
+    m = O.medium(D, eps)
+    E, B = W.random_fields(shape, 42)
+    g = O.init_state(m, E, B)
+    n = int(np.prod(shape))
+    rng = np.random.default_rng(43)
+    k = 6
+    site = rng.choice(n, k, replace=False)
+    comp = rng.integers(0, 3, k) if D == 3 else np.full(k, 2)
+    amp = rng.standard_normal((k, 15))
+    src = dict(site=site, comp=comp, amp=amp)
+    e3 = levi3()[:, :D, :D]
+    for t in range(15):
+        tot0 = g.sum(axis=tuple(range(D)) + (D,))
+        _, B0 = O.fields(m, g)
+        O.run(m, g, 1, t0=t, sources=src)
+        tot1 = g.sum(axis=tuple(range(D)) + (D,))
+        _, B1 = O.fields(m, g)
+        jt = np.zeros(3)
+        for s, c, a in zip(site, comp, amp[:, t]):
+            jt[c] += a
+        inj = np.einsum("gab,g->ab", e3, jt) / (D - 1)
+        np.testing.assert_allclose(tot1 - tot0, inj, atol=1e-11)
+        np.testing.assert_allclose(B1.sum(axis=tuple(range(D))), B0.sum(axis=tuple(range(D))), atol=1e-11)
+
+
+def test_fd_form_equivalence_2d():
+    """The oracle's E_z, B_x, B_y equal the exact FD (leapfrog) form to round-off: heterogeneous medium,
+    random initial fields, random sources everywhere."""
+    N = 20
+    eps, _ = W.random_medium((N, N), 51)
+    m = O.medium(2, eps)
+    E0, B0 = W.random_fields((N, N), 52)
+    E0[..., :2] = 0
+    B0[..., 2] = 0
+    g = O.init_state(m, E0, B0)
+    T = 40
+    rng = np.random.default_rng(53)
+    amp = 0.1 * rng.standard_normal((N * N, T))
+    src = dict(site=np.arange(N * N), comp=np.full(N * N, 2), amp=amp)
+    Es, Bxs, Bys = [], [], []
+    for t in range(T):
+        E, B = O.fields(m, g)
+        Es.append(E[..., 2])
+        Bxs.append(B[..., 0])
+        Bys.append(B[..., 1])
+        O.run(m, g, 1, t0=t, sources=src)
+    S = [-m.ceff2 * amp[:, t].reshape(N, N) for t in range(T)]  # S_z = -mu c^2 j_z, mu = 1
+    Ef, Bxf, Byf = X.leapfrog_2d(m.cL2, Es[0], Es[1], Bxs[0], Bxs[1], Bys[0], Bys[1], S, T)
+    scale = np.abs(Es).max()
+    assert np.abs(Ef - np.array(Es)).max() < 1e-12 * scale
+    assert np.abs(Bxf - np.array(Bxs)).max() < 1e-12 * scale
+    assert np.abs(Byf - np.array(Bys)).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("w_eps", [1.0, 1.6, 4.0])
+@pytest.mark.parametrize("mode", [(3, 0), (2, 5), (7, 7), (1, 11)])
+def test_dispersion_matches_closed_form(w_eps, mode):
+    """Plane wave E_z = cos(k.x) in a homogeneous medium: its Fourier amplitude follows
+    cos(omega t), sin(omega t) with sin^2(omega/2) = c^2 (sin^2(kx/2) + sin^2(ky/2)) exactly."""
+    N = 24
+    m = O.medium(2, np.full((N, N), w_eps))
+    kx, ky = 2 * np.pi * mode[0] / N, 2 * np.pi * mode[1] / N
+    y, x = np.mgrid[0:N, 0:N]
+    E = np.zeros((N, N, 3))
+    E[..., 2] = np.cos(kx * x + ky * y)
+    g = O.init_state(m, E=E)
+    T = 60
+    amp = []
+    basis = np.exp(-1j * (kx * x + ky * y))
+    for t in range(T):
+        Ef, _ = O.fields(m, g)
+        amp.append(np.real((Ef[..., 2] * basis).sum()) / (N * N / 2))
+        O.run(m, g, 1)
+    amp = np.array(amp)
+    om = X.omega_2d(0.5 / w_eps, kx, ky)
+    t = np.arange(T)
+    b = (amp[1] - amp[0] * np.cos(om)) / np.sin(om)
+    pred = amp[0] * np.cos(om * t) + b * np.sin(om * t)
+    assert np.abs(amp - pred).max() < 1e-11
+
+
+def test_phase_speed_converges_to_c_over_n():
+    """Measured plane-wave phase speed -> c/n as k -> 0, error falling ~4x per halving of k (2nd order)."""
+    n_idx = 1.5
+    c = np.sqrt(0.5) / n_idx
+    errs = []
+    for N in (16, 32, 64):
+        m = O.medium(2, np.full((4, N), n_idx ** 2))
+        k = 2 * np.pi / N
+        x = np.arange(N)[None, :].repeat(4, 0)
+        E = np.zeros((4, N, 3))
+        E[..., 2] = np.cos(k * x)
+        g = O.init_state(m, E=E)
+        series = []
+        for t in range(3):
+            Ef, _ = O.fields(m, g)
+            series.append((Ef[..., 2] * np.cos(k * x)).sum())
+            O.run(m, g, 1)
+        # E^{t+1} + E^{t-1} = 2 cos(omega) E^t for the Fourier amplitude
+        om = np.arccos((series[2] + series[0]) / (2 * series[1]))
+        errs.append(abs(om / k / c - 1))
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+    assert errs[2] < 2e-3
+
+
+def _symbol_3d(m, N, kx):
+    """21x21 Fourier symbol of one oracle step on a (1, 1, N) grid restricted to antisymmetric tensors."""
+    e3 = levi3()
+    basis = []
+    for i in range(7):
+        for gam in range(3):
+            b = np.zeros((7, 3, 3))
+            b[i] = e3[gam]
+            basis.append(b)
+    A = np.zeros((21, 21), complex)
+    for col, b in enumerate(basis):
+        g = np.zeros((1, 1, N, 7, 3, 3))
+        g[0, 0, 0] = b
+        O.run(m, g, 1)
+        gk = np.einsum("xiab,x->iab", g[0, 0], np.exp(-1j * kx * np.arange(N)))
+        for row, bb in enumerate(basis):
+            A[row, col] = (gk * bb).sum() / 2.0  # <e_gamma, e_gamma'> = 2 delta
+    return A
+
+
+def test_3d_neutral_stability_and_wave_speed():
+    """3D (reading R2): every eigenvalue of the one-step symbol has |lambda| = 1 (tau = dt/2 removes
+    dissipation), and the transverse wave speed -> c_eff = c_L/sqrt(2) as k -> 0 at second order."""
+    errs = []
+    for N in (16, 32, 64):
+        m = O.medium(3, np.full((1, 1, N), 1.5))
+        c_eff = np.sqrt(m.ceff2[0, 0, 0])
+        k = 2 * np.pi / N
+        lam = np.linalg.eigvals(_symbol_3d(m, N, k))
+        assert np.abs(np.abs(lam) - 1).max() < 1e-12
+        om = np.abs(np.angle(lam))
+        phys = om[(om > 1e-9) & (om < 0.5)]
+        assert phys.size >= 2
+        errs.append(np.abs(phys / k / c_eff - 1).min())
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+
+
+@pytest.mark.parametrize("D,eps_val", [(2, 1.0), (2, 2.0), (3, 1.0), (3, 1.7)])
+def test_invariant_conserved_homogeneous(D, eps_val):
+    """sum_x sum_i |g_i|^2 / w_i is exactly conserved (homogeneous, source-free, periodic): the collision
+    2P - I is a reflection in the 1/w metric and streaming is a permutation."""
+    shape = (12, 10) if D == 2 else (6, 5, 4)
+    m = O.medium(D, np.full(shape, eps_val))
+    E, B = W.random_fields(shape, 61)
+    g = O.init_state(m, E, B)
+    rng = np.random.default_rng(62)
+    a = rng.standard_normal(g.shape)
+    if eps_val == 1.0:
+        a[..., 0, :, :] = 0  # w0 = 0: rest population stays zero
+    g += 0.3 * (a - np.swapaxes(a, -1, -2))
+    w = np.array([m.w0.flat[0]] + [(1 - m.w0.flat[0]) / (2 * D)] * (2 * D))
+
+    def inv(h):
+        terms = (h ** 2).sum(axis=(-1, -2))
+        return sum(terms[..., i].sum() / w[i] for i in range(2 * D + 1) if w[i] > 0)
+
+    i0 = inv(g)
+    assert abs(O.diagnostics(m, g)[1] - i0) < 1e-13 * i0
+    O.run(m, g, 150)
+    assert abs(inv(g) - i0) < 1e-12 * i0
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_time_reversibility(D):
+    """F^-N = M R F^N R M (M the collision, R the direction reversal): N steps back recover g0."""
+    shape = (11, 9) if D == 2 else (5, 6, 4)
+    eps, _ = W.random_medium(shape, 71)
+    m = O.medium(D, eps)
+    E, B = W.random_fields(shape, 72)
+    g0 = O.init_state(m, E, B)
+    g = g0.copy()
+    N = 60
+    O.run(m, g, N)
+    h = reflect(collide_only(m, g), D)
+    O.run(m, h, N)
+    h = collide_only(m, reflect(h, D))
+    assert np.abs(h - g0).max() < 1e-12 * np.abs(g0).max()
+
+
+def test_central_difference_div_b_is_two_step_invariant():
+    """2D: the central-difference divergence of B obeys div^{t+1} = div^{t-1} exactly (the two D_x D_y
+    terms of the FD form cancel), even with sources and a heterogeneous medium."""
+    N = 16
+    eps, _ = W.random_medium((N, N), 81)
+    m = O.medium(2, eps)
+    E, B = W.random_fields((N, N), 82)
+    g = O.init_state(m, E, B)
+    rng = np.random.default_rng(83)
+    src = dict(site=np.arange(N * N), comp=np.full(N * N, 2), amp=rng.standard_normal((N * N, 12)))
+    divs, norms = [], []
+    for t in range(12):
+        _, Bf = O.fields(m, g)
+        dv = 0.5 * (np.roll(Bf[..., 0], -1, 1) - np.roll(Bf[..., 0], 1, 1)) + 0.5 * (
+            np.roll(Bf[..., 1], -1, 0) - np.roll(Bf[..., 1], 1, 0))
+        divs.append(dv)
+        norms.append(O.diagnostics(m, g)[2])
+        O.run(m, g, 1, t0=t, sources=src)
+    for t in range(2, 12):
+        np.testing.assert_allclose(divs[t], divs[t - 2], atol=1e-12)
+        assert abs(norms[t] - np.sqrt((divs[t] ** 2).sum())) < 1e-12 * max(1, norms[t])
+
+
+def test_energy_nearly_conserved_homogeneous_pulse():
+    """The field energy of Sec. "Heterogeneous media" is conserved to O(k^2) for a smooth pulse."""
+    p = W.homogeneous_pulse(64, 6.0, 200)
+    m = O.medium(2, p.eps_r)
+    g = O.init_state(m, p.E0)
+    e0 = O.diagnostics(m, g)[0]
+    es = []
+    for _ in range(10):
+        O.run(m, g, 20)
+        es.append(O.diagnostics(m, g)[0])
+    assert np.abs(np.array(es) / e0 - 1).max() < 5e-3
+
+
+# --------------------------------------------------------------------------- against pseudo-spectral Maxwell
+
+
+def _paper_e2_fields(N):
+    k = golden_constants()
+    x = (np.arange(N) + 0.0) / N
+    X_, Y_ = np.meshgrid(x, x, indexing="xy")  # [y, x]
+    f = k["e2_A"] * np.exp(-((X_ - k["e2_xc"]) ** 2 + (Y_ - k["e2_yc"]) ** 2) / (2 * k["e2_s"] ** 2))
+    return (Y_ - k["e2_yc"]) * f, -(X_ - k["e2_xc"]) * f
+
+
+def test_lb_converges_to_pseudo_spectral_2d():
+    """The paper's heterogeneous test (Sec. "Heterogeneous media"): its divergence-free initial B, a
+    smooth heterogeneous c^2, compared with a pseudo-spectral RK4 solver at the same physical time; the
+    LB - PS difference falls about 4x per grid doubling (second order).  Step counts are even: starting
+    from equilibrium puts a constant O(dx^2) offset on B at odd steps (the non-dissipative period-2 mode
+    of tau = dt/2), so odd and even steps are compared only among themselves."""
+    errs = []
+    t_end = 0.25
+    for N in (64, 128, 256):
+        x = np.arange(N) / N
+        X_, Y_ = np.meshgrid(x, x, indexing="xy")
+        n_idx = 1.0 + 0.5 * (1 + np.sin(2 * np.pi * X_) * np.cos(2 * np.pi * Y_))
+        m = O.medium(2, n_idx ** 2)
+        Bx, By = _paper_e2_fields(N)
+        B = np.zeros((N, N, 3))
+        B[..., 0], B[..., 1] = Bx, By
+        g = O.init_state(m, B=B)
+        steps = int(round(t_end * N))
+        O.run(m, g, steps)
+        Ef, Bf = O.fields(m, g)
+        # lattice units: dx = dt = 1/N, so the physical speed equals the lattice speed
+        e, bx, by = X.maxwell_ps_2d(m.ceff2, np.zeros((N, N)), Bx, By, steps / N, 0.25 / N)
+        num = np.sqrt(((Ef[..., 2] - e) ** 2).sum() + ((Bf[..., 0] - bx) ** 2).sum() + ((Bf[..., 1] - by) ** 2).sum())
+        den = np.sqrt((e ** 2).sum() + (bx ** 2).sum() + (by ** 2).sum())
+        errs.append(num / den)
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+    assert errs[2] < 0.01, errs
+
+
+def test_lb_converges_to_pseudo_spectral_3d():
+    """3D with reading R2: the scheme solves Maxwell at c_eff^2 = c_L^2/2; LB - PS falls ~4x per doubling."""
+    errs = []
+    t_end = 0.25
+    for N in (16, 32):
+        z, y, x = np.meshgrid(*(np.arange(N) / N,) * 3, indexing="ij")
+        n_idx = 1.0 + 0.3 * (1 + np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.cos(2 * np.pi * z))
+        m = O.medium(3, n_idx ** 2)
+        # divergence-free smooth B: curl of a vector potential A = (0, 0, psi)
+        psi = np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2) / (2 * 0.12 ** 2))
+        kz, ky, kx = np.meshgrid(*(2 * np.pi * np.fft.fftfreq(N, 1 / N),) * 3, indexing="ij")
+        dpsi = lambda k: np.real(np.fft.ifftn(1j * k * np.fft.fftn(psi)))
+        Bv = np.array([dpsi(ky), -dpsi(kx), np.zeros_like(psi)])
+        g = O.init_state(m, B=np.moveaxis(Bv, 0, -1))
+        steps = int(round(t_end * N))
+        O.run(m, g, steps)
+        Ef, Bf = O.fields(m, g)
+        e, b = X.maxwell_ps_3d(m.ceff2, np.zeros_like(Bv), Bv, steps / N, 0.25 / N)
+        num = np.sqrt(((np.moveaxis(Ef, -1, 0) - e) ** 2).sum() + ((np.moveaxis(Bf, -1, 0) - b) ** 2).sum())
+        den = np.sqrt((e ** 2).sum() + (b ** 2).sum())
+        errs.append(num / den)
+    assert errs[0] / errs[1] > 3.0, errs
+
+
+def test_homogeneous_current_div_b_error_decreases_with_resolution():
+    """Sec. "Homogeneous media": forcing j_z (Gaussian at (0.3, 0.4), width 0.03), fields zero at t = 0,
+    c^2 = 1 in units of its uniform value; the L2 div-B error of Eq. 19 falls with grid spacing."""
+    k = golden_constants()
+    out = []
+    t_end = 0.2
+    for N in (32, 64, 128):
+        x = np.arange(N) / N
+        X_, Y_ = np.meshgrid(x, x, indexing="xy")
+        j = np.exp(-((X_ - k["e1_x0"]) ** 2 + (Y_ - k["e1_y0"]) ** 2) / (2 * k["e1_s"] ** 2))
+        m = O.medium(2, np.ones((N, N)))
+        g = O.init_state(m)
+        steps = int(round(t_end * N))
+        src = dict(site=np.arange(N * N), comp=np.full(N * N, 2), amp=np.repeat(j.reshape(-1, 1) / N, steps, 1))
+        O.run(m, g, steps, sources=src)
+        _, Bf = O.fields(m, g)
+        out.append(X.spectral_divb_error(Bf[..., 0], Bf[..., 1]))
+    assert out[0] > out[1] > out[2], out
+    assert out[0] / out[2] > 4.0, out
+
+
+# --------------------------------------------------------------------------- oracle adjoint
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_oracle_adjoint_matches_finite_differences(D):
+    shape = (10, 9) if D == 2 else (5, 6, 4)
+    eps, _ = W.random_medium(shape, 91)
+    m = O.medium(D, eps)
+    n = int(np.prod(shape))
+    nsteps = 14
+    rng = np.random.default_rng(92)
+    src = dict(site=np.array([n // 2]), comp=np.array([2]), amp=W.ricker(nsteps, 0.15)[None, :])
+    rec = dict(site=rng.choice(n, 4, replace=False), comp=np.array([2, 2, 3, 5 if D == 3 else 4]))
+    obs = 0.01 * rng.standard_normal((4, nsteps))
+    g0 = np.zeros(shape + (2 * D + 1, D, D))
+    mis, grad = O.adjoint(m, g0, nsteps, src, rec, obs)
+
+    def misfit(e):
+        mm = O.medium(D, e)
+        g = np.zeros_like(g0)
+        tr = O.run(mm, g, nsteps, sources=src, receivers=rec)
+        return 0.5 * ((tr - obs) ** 2).sum()
+
+    assert abs(misfit(eps) - mis) < 1e-14 * max(1, mis)
+    for seed in range(3):
+        d = W.smooth_perturbation(shape, 100 + seed, 1.5, amp=1.0)
+        h = 1e-5
+        fd = (misfit(eps + h * d) - misfit(eps - h * d)) / (2 * h)
+        an = (grad * d).sum()
+        assert abs(fd - an) < 1e-6 * abs(an) + 1e-14, (fd, an)
