@@ -68,24 +68,29 @@ static void make_lattice(lattice_t *L, int D, int nx, int ny, int nz) {
     }
 }
 
-/* Levi-Civita symbol epsilon_{abc}, indices 0..2. */
-static double levi(int a, int b, int c) {
-    if (a == b || b == c || a == c) return 0.0;
-    /* even permutations of (0,1,2) */
-    if ((a == 0 && b == 1 && c == 2) || (a == 1 && b == 2 && c == 0) || (a == 2 && b == 0 && c == 1))
-        return 1.0;
-    return -1.0;
+/* Levi-Civita symbol epsilon_{abc}, indices 0..2: +1 on even permutations of
+ * (0,1,2), -1 on odd ones, 0 when an index repeats. */
+static const double LEVI[3][3][3] = {
+    {{0, 0, 0}, {0, 0, 1}, {0, -1, 0}},
+    {{0, 0, -1}, {0, 0, 0}, {1, 0, 0}},
+    {{0, 1, 0}, {-1, 0, 0}, {0, 0, 0}},
+};
+static inline double levi(int a, int b, int c) { return LEVI[a][b][c]; }
+
+/* Periodic wrap of coordinate v + d into [0, n), for |d| <= n. */
+static inline long wrap(long v, int d, long n) {
+    v += d;
+    if (v >= n) v -= n;
+    if (v < 0) v += n;
+    return v;
 }
 
-/* Site index of (x + dx, y + dy, z + dz) with periodic wrap. */
+/* Site index of (x + dx, y + dy, z + dz) with periodic wrap, |d| <= 1. */
 static long shifted(const lattice_t *L, long s, int dx, int dy, int dz) {
     long x = s % L->nx;
     long y = (s / L->nx) % L->ny;
     long z = s / ((long)L->nx * L->ny);
-    x = ((x + dx) % L->nx + L->nx) % L->nx;
-    y = ((y + dy) % L->ny + L->ny) % L->ny;
-    z = ((z + dz) % L->nz + L->nz) % L->nz;
-    return x + L->nx * (y + L->ny * z);
+    return wrap(x, dx, L->nx) + L->nx * (wrap(y, dy, L->ny) + L->ny * wrap(z, dz, L->nz));
 }
 
 static inline double *G(const lattice_t *L, double *g, long s, int i) {
@@ -321,11 +326,13 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
         for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = pick(E + 3 * rec_site[r], B + 3 * rec_site[r], rec_comp[r]);
         /* streaming (Eq. 18): g_i(x + c_i, t+1) = g'_i(x, t) */
 #pragma omp parallel for schedule(static)
-        for (long s = 0; s < L.nsite; s++)
+        for (long s = 0; s < L.nsite; s++) {
+            const long x = s % L.nx, y = (s / L.nx) % L.ny, z = s / ((long)L.nx * L.ny);
             for (int i = 0; i < L.Q; i++) {
-                long d = shifted(&L, s, L.c[i][0], L.c[i][1], L.c[i][2]);
+                long d = wrap(x, L.c[i][0], L.nx) + L.nx * (wrap(y, L.c[i][1], L.ny) + L.ny * wrap(z, L.c[i][2], L.nz));
                 memcpy(G(&L, g, d, i), G(&L, gpost, s, i), sizeof(double) * D * D);
             }
+        }
     }
     free(gpost);
     free(E);
