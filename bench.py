@@ -1,0 +1,323 @@
+"""Throughput benchmark of the lattice-Boltzmann Maxwell hot path on one GB300.
+
+Workload (default): 4096 x 4096 periodic 2D heterogeneous medium (n = 1 + 2 s,
+s seeded smoothed random field, sigma = 20 cells, seed 2), Ricker point
+current at the centre (~20 cells per local wavelength), 64 receivers, 5000
+time steps, FP32 storage.  One benchmark step is one full pass of the hot
+path over that input: medium upload, initial state, 5000 fused
+stream-collide steps with the source and receivers, field extraction,
+receiver traces and the FP64 diagnostics.  The distributions (2 x 336 MB)
+are larger than L2, so no flush is needed between steps.
+
+Metric: Mlups (10^6 lattice-site updates per second) = sites x 5000 / time.
+The stream-collide kernel's roofline is HBM bandwidth: 44 algorithmic bytes
+per site per step (5 populations read + 5 written in FP32, plus c_L^2).
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload.  With torchrun (N > 1) every rank runs
+its own independent replica (no data-path collective: replicas only).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1108_2651_gb300 import workloads as W  # noqa: E402
+
+BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def measured_peak_gbs():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                vals = [v.strip() for v in out.stdout.strip().split(",")]
+                if len(vals) == 6:
+                    self.samples.append(vals)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[2 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def workload(name):
+    if name == "het2d_4096":
+        return W.heterogeneous_2d(4096, seed=2, nsteps=5000)
+    if name == "het2d_1024":
+        return W.heterogeneous_2d(1024, seed=1, nsteps=5000)
+    raise ValueError(name)
+
+
+def cpu_baseline(p, budget_s=12.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample: a 1024^2 crop of the medium centred on the
+    source, as many steps as fit in about budget_s seconds of CPU work."""
+    import oracle as O
+
+    n = min(1024, p.shape[0])
+    c0 = (p.shape[0] - n) // 2
+    eps = np.asarray(p.eps_r[c0:c0 + n, c0:c0 + n], np.float32).astype(np.float64)
+    m = O.medium(2, eps)
+    g = O.init_state(m)
+    src = dict(site=np.array([W.flat_index((n, n), (n // 2, n // 2))]), comp=np.array([2]),
+               amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
+    t0 = time.perf_counter()
+    O.run(m, g, 10, sources=src)
+    dt10 = time.perf_counter() - t0
+    steps = int(max(10, min(p.nsteps - 10, budget_s / max(dt10 / 10, 1e-6))))
+    t0 = time.perf_counter()
+    O.run(m, g, steps, t0=10, sources=src)
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps / dt / 1e6, "unit": "Mlups", "cores": O.threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, {n}x{n} crop of the workload's medium, point source, {steps} steps "
+                      f"({dt:.1f} s)"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    cores = None
+    times = []
+    steps_per = max(5, int(args.ref_steps))
+    import oracle as O
+
+    n = min(1024, p.shape[0])
+    c0 = (p.shape[0] - n) // 2
+    eps = np.asarray(p.eps_r[c0:c0 + n, c0:c0 + n], np.float32).astype(np.float64)
+    m = O.medium(2, eps)
+    src = dict(site=np.array([W.flat_index((n, n), (n // 2, n // 2))]), comp=np.array([2]),
+               amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
+    for k in range(args.warmup + args.steps):
+        g = O.init_state(m)
+        t0 = time.perf_counter()
+        O.run(m, g, steps_per, sources=src)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    cores = O.threads()
+    value = n * n * steps_per / (sum(times) / len(times)) / 1e6
+    line = {"impl": "reference", "metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p.name, "grid": list(p.shape), "lb_steps": p.nsteps, "storage": "f64-oracle"},
+            "cpu_baseline": {"value": value, "unit": "Mlups", "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle, {n}x{n} crop of the workload's medium, {steps_per} steps "
+                                       f"per benchmark step"},
+            "e2e": {"value": value, "unit": "Mlups", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
+    ap.add_argument("--workload", default="het2d_4096")
+    ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
+    ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
+    ap.add_argument("--ref-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_1108_2651_gb300 import lbem
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    lbem.load()
+    p = workload(args.workload)
+    if args.lb_steps:
+        p.nsteps = args.lb_steps
+        p.src_amp = p.src_amp[:, : p.nsteps]
+    nsteps = p.nsteps
+    stream = torch.cuda.Stream()
+    eps_d = torch.as_tensor(np.ascontiguousarray(p.eps_r, np.float32).ravel(), device="cuda")
+    with torch.cuda.stream(stream):
+        s = lbem.Solver(p.shape, storage=args.storage, stream=stream.cuda_stream)
+    h = s.h
+    lbem.lbem_set_medium(h, eps_d)
+    lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
+    lbem.lbem_set_receivers(h, p.rec_site, p.rec_comp, nsteps)
+    variant = 0
+    if args.autotune:
+        lbem.lbem_set_fields(h)
+        variant = lbem.lbem_autotune(h, 50)
+    nsite = s.nsite
+    E_d = torch.empty(3 * nsite, dtype=torch.float32, device="cuda")
+    B_d = torch.empty_like(E_d)
+    tr_d = torch.empty(p.rec_site.size * nsteps, dtype=torch.float32, device="cuda")
+
+    def one_pass(ev=None):
+        lbem.lbem_set_medium(h, eps_d)
+        lbem.lbem_set_fields(h)
+        if ev is not None:
+            ev[0].record(stream)
+        lbem.lbem_step(h, nsteps)
+        if ev is not None:
+            ev[1].record(stream)
+        lbem.lbem_fields(h, E_d, B_d)
+        lbem.lbem_traces(h, tr_d)
+        return lbem.lbem_diagnostics(h)
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            diag = one_pass(evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = start.elapsed_time(stop)
+    total_ms = dist_max(total_ms, world)
+    kern_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_per_launch = float(np.mean(kern_ms)) / nsteps
+    ms_per_step = total_ms / args.steps
+    value = world * nsite * nsteps / (ms_per_step * 1e-3) / 1e6
+
+    peak, peak_kind = measured_peak_gbs()
+    bps = BYTES_PER_SITE[args.storage]
+    achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"step2d<{args.storage}> (variant {variant})",
+                "algorithmic_bytes_per_site": bps, "ms_per_launch": ms_per_launch, "peak_kind": peak_kind}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        eps_h = np.ascontiguousarray(p.eps_r, np.float32).ravel()
+        E_h = np.empty(3 * nsite, np.float32)
+        B_h = np.empty(3 * nsite, np.float32)
+        tr_h = np.empty(p.rec_site.size * nsteps, np.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 2))
+        for _ in range(reps):
+            lbem.lbem_set_medium(h, eps_h)
+            lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
+            lbem.lbem_set_fields(h)
+            lbem.lbem_step(h, nsteps)
+            lbem.lbem_fields(h, E_h, B_h)
+            lbem.lbem_traces(h, tr_h)
+            lbem.lbem_diagnostics(h)
+        dt = (time.perf_counter() - t0) / reps
+        dt = dist_max(dt, world)
+        e2e = {"value": world * nsite * nsteps / dt / 1e6, "unit": "Mlups",
+               "h2d_bytes_per_step": int(eps_h.nbytes + p.src_amp.size * 4 + p.src_site.size * 12),
+               "d2h_bytes_per_step": int(E_h.nbytes + B_h.nbytes + tr_h.nbytes + 24)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p)
+    s.close()
+    if rank == 0:
+        launches = args.steps * (nsteps + 6 + (1 if args.storage == "f16" else 0))
+        line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32-math/{args.storage}-storage",
+                "data": "synthetic",
+                "config": {"workload": p.name, "grid": list(p.shape), "lb_steps": nsteps, "storage": args.storage,
+                           "sources": int(p.src_site.size), "receivers": int(p.rec_site.size),
+                           "l2": "inputs larger than L2 (2 x 336 MB distributions), no flush",
+                           "parallelism": f"replicas{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(), "diagnostics_last": list(diag)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * lbem.h -- C ABI of the GB300 (sm_103a) lattice-Boltzmann Maxwell solver.
+ *
+ * The method is that of Hanasoge, Succi & Orszag, "Lattice Boltzmann Method
+ * for Electromagnetic Wave Propagation" (EPL; arXiv:1108.2651): an
+ * antisymmetric tensor ("pseudo-vector") distribution g_{i,alpha,beta} on the
+ * D2Q5 ("4+1") or D3Q7 ("6+1") lattice, BGK collision at tau = dt/2 with the
+ * local equilibrium of Eq. 8 and the tensor source T_i built from Eq. 3's
+ * heterogeneity source S, followed by streaming (Eqs. 17-18); E and B are
+ * recovered from the zeroth and first moments (Eqs. 9-10).
+ *
+ * Conventions (every entry point):
+ *  - Every call returns an lbem_status; on failure a thread-local message is
+ *    available from lbem_last_error().  A handle stays usable after any
+ *    LBEM_ERR_ARG / LBEM_ERR_MEDIUM / LBEM_ERR_STATE failure.
+ *  - Grids are dense, C order: site s = x + nx*(y + ny*z) (nz = 1 in 2D).
+ *    Vector fields are component-major: F[c*nsite + s], c = 0,1,2 for x,y,z.
+ *  - Pointer arguments to grid-sized arrays may be host or device memory
+ *    (unified addressing); inputs are copied before the call returns or are
+ *    read by work enqueued on the handle's stream, outputs are written by
+ *    work enqueued on the stream.  Caller-owned memory is never freed or
+ *    retained past the call.  Host output buffers are complete when the call
+ *    returns; device outputs are complete when the stream reaches the call.
+ *  - Work runs asynchronously on the handle's stream (lbem_desc.stream);
+ *    errors raised by device work surface at the next synchronising call
+ *    (lbem_diagnostics, lbem_traces to host, lbem_sync) as LBEM_ERR_CUDA.
+ *  - Handles are not thread-safe: one thread drives one handle at a time.
+ *  - The state is 32-bit float arithmetic; the storage of the distribution is
+ *    FP32, or one of three 16-bit formats (lbem_storage).
+ */
+#ifndef LBEM_H
+#define LBEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbem lbem_t;
+typedef struct lbem_batch lbem_batch_t;
+
+typedef enum {
+    LBEM_OK = 0,
+    LBEM_ERR_ARG = 1,      /* invalid argument (null handle, bad size, index out of range) */
+    LBEM_ERR_CUDA = 2,     /* a CUDA runtime call or a kernel failed */
+    LBEM_ERR_MEDIUM = 3,   /* medium rejected: eps, mu not finite and > 0, or rest weight w0 outside [0, 1) */
+    LBEM_ERR_UNSTABLE = 4, /* non-finite values found in the state */
+    LBEM_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    LBEM_ERR_STATE = 6,    /* call not valid in the handle's current state (e.g. no medium yet) */
+    LBEM_ERR_NOMEM = 7     /* device allocation failed */
+} lbem_status;
+
+/* Storage format of the distribution (arithmetic is always FP32). */
+typedef enum {
+    LBEM_F32 = 0,  /* 4 bytes per value */
+    LBEM_F16 = 1,  /* IEEE binary16 of s*g, s a power of two chosen from the inputs (2 bytes) */
+    LBEM_BF16 = 2, /* bfloat16 of g (2 bytes) */
+    LBEM_I16B = 3  /* int16 mantissas sharing one exponent byte per 4 consecutive sites along x (2.25 bytes) */
+} lbem_storage;
+
+typedef struct {
+    int dim;        /* 2 (D2Q5, fields E_z, B_x, B_y) or 3 (D3Q7, all six components) */
+    int nx, ny, nz; /* grid size, periodic in every direction; nz ignored in 2D; each >= 1 */
+    int storage;    /* lbem_storage; LBEM_F32 in 3D */
+    double c_ref2;  /* wave speed squared (lattice units) at eps = mu = 1; <= 0 selects the largest the
+                       lattice carries with a non-negative rest weight: 1/2 in 2D, 1/6 in 3D */
+    void *stream;   /* cudaStream_t the handle enqueues on; NULL = legacy default stream */
+} lbem_desc;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a solver on the current CUDA device: allocates the two population
+ * buffers (ping-pong), the medium arrays and small scratch.  The state starts
+ * at t = 0 with all fields zero.  *out receives the handle (owned by the
+ * caller, released with lbem_destroy).  LBEM_ERR_ARG for invalid sizes,
+ * LBEM_ERR_NOMEM if the device memory does not fit. */
+lbem_status lbem_create(const lbem_desc *desc, lbem_t **out);
+
+/* Release every device allocation of the handle (synchronises its stream). */
+void lbem_destroy(lbem_t *h);
+
+/* Replace the stream the handle enqueues on (cudaStream_t as void*). */
+lbem_status lbem_set_stream(lbem_t *h, void *stream);
+
+/* Wait for all work enqueued on the handle's stream; reports deferred device errors. */
+lbem_status lbem_sync(lbem_t *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lbem_last_error(void);
+
+/* Grid geometry: number of sites and the bytes of one saved state (lbem_save_state). */
+lbem_status lbem_info(const lbem_t *h, long long *nsite, size_t *state_bytes);
+
+/* ---------------------------------------------------------------- problem set-up */
+
+/* Medium upload (paper, Eq. 3 and Sec. "Lattice BGK formulation").  eps_r and
+ * mu_r are relative permittivity and permeability per site ([nsite] floats,
+ * host or device); mu_r may be NULL (mu = 1 everywhere).  Per site:
+ *   c_eff^2 = c_ref2 / (eps_r mu_r)      (c = 1/sqrt(mu0 eps0))
+ *   c_L^2   = (D-1) c_eff^2              (equilibrium's lattice speed parameter)
+ *   w0      = 1 - D c_L^2                (rest weight; moving weights (1-w0)/(2D))
+ *   grad ln mu by periodic central differences (only kept when mu_r is given)
+ * Validated in FP64 on the device: LBEM_ERR_MEDIUM (handle's previous medium
+ * kept) if any site has eps_r or mu_r not finite and > 0, or w0 outside
+ * [0, 1).  Synchronises the stream (to read the validation count). */
+lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r);
+
+/* Initial fields (Eq. 8): sets g = g^(0)(E, B) at every site and t = 0, and
+ * clears recorded traces.  E and B are [3][nsite] floats (host or device), or
+ * NULL for zero.  In 2D only E_z, B_x and B_y are representable; the other
+ * components are ignored.  Requires a medium (LBEM_ERR_STATE otherwise). */
+lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B);
+
+/* Point current sources (Eq. 3's -j/eps0 term): source k injects the current
+ * density j_{comp[k]}(site[k], t) = amp[k*nt + t] for 0 <= t < nt (0 after).
+ * site: [n] flat indices, comp: [n] in 0..2 (in 2D only comp 2, j_z, couples
+ * to the TM fields; others are ignored), amp: [n*nt] floats.  All three are
+ * HOST arrays, copied.  n = 0 removes all sources.  At most 65536 sources. */
+lbem_status lbem_set_sources(lbem_t *h, int n, const long long *site, const int *comp, const float *amp, int nt);
+
+/* Receivers: each step, before the collision, receiver r records field
+ * comp[r] (0..2 = E_x..E_z, 3..5 = B_x..B_z) at site[r] into a handle-owned
+ * trace buffer of `capacity` samples per receiver (steps beyond capacity are
+ * not recorded).  site, comp: HOST arrays [n], copied.  n = 0 removes all
+ * receivers.  Recording restarts at the next lbem_set_fields. */
+lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const int *comp, int capacity);
+
+/* ---------------------------------------------------------------- time stepping */
+
+/* Advance nsteps steps: per site and step, pull-stream (Eq. 18), moments (Eqs.
+ * 9-10), source (Eq. 3), equilibrium (Eq. 8), collision at tau = dt/2 (Eq. 17);
+ * receivers sample the pre-collision fields.  One fused kernel launch per step,
+ * enqueued on the stream (or replayed from a cached CUDA graph when enabled by
+ * lbem_set_graphs).  Requires a medium.  nsteps >= 0. */
+lbem_status lbem_step(lbem_t *h, int nsteps);
+
+/* Use (on != 0) or not CUDA-graph replay of runs of steps in lbem_step. */
+lbem_status lbem_set_graphs(lbem_t *h, int on);
+
+/* Steps taken since the last lbem_set_fields / lbem_load_state. */
+lbem_status lbem_time(const lbem_t *h, long long *t);
+
+/* ---------------------------------------------------------------- outputs */
+
+/* Field extraction (Eqs. 9-10 and E_g = -1/2 eps_gab Lambda_ab): E, B of the
+ * current (pre-collision) state, [3][nsite] floats each, host or device; either
+ * may be NULL.  Components not representable in 2D are written as 0. */
+lbem_status lbem_fields(lbem_t *h, float *E, float *B);
+
+/* Receiver traces: out[r*nrec_steps + n] for n < nrec_steps = min(t, capacity),
+ * host or device; *nrecorded (host, may be NULL) receives nrec_steps.  out may be
+ * NULL to query the count only. */
+lbem_status lbem_traces(lbem_t *h, float *out, int *nrecorded);
+
+/* FP64 diagnostics of the current state (synchronising; result on the host):
+ *   out[0] = sum_x sum_a (B_a^2 + E_a^2 / c_eff^2)       (field energy, Sec. "Heterogeneous media")
+ *   out[1] = sum_x sum_i sum_ab g_iab^2 / w_i             (terms with w_i = 0 skipped)
+ *   out[2] = sqrt(sum_x (div B)^2), periodic central differences
+ * Deterministic: block partial sums in a handle-owned scratch array, reduced in
+ * fixed order.  LBEM_ERR_UNSTABLE if any of the three is not finite. */
+lbem_status lbem_diagnostics(lbem_t *h, double out[3]);
+
+/* ---------------------------------------------------------------- checkpoint / resume */
+
+/* Copy the distribution state (state_bytes from lbem_info) to dst / from src
+ * (host or device).  lbem_load_state also sets t (for source and receiver time
+ * indexing) to t_at_save. */
+lbem_status lbem_save_state(lbem_t *h, void *dst);
+lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save);
+
+/* ---------------------------------------------------------------- adjoint (not in the paper) */
+
+/* Forward run that records what the adjoint needs: advances nsteps steps from
+ * the current state (receivers record as in lbem_step) and keeps a copy of the
+ * state every `checkpoint_every` steps in handle-owned device memory.  FP32
+ * storage, uniform mu (LBEM_ERR_STATE otherwise). */
+lbem_status lbem_forward_record(lbem_t *h, int nsteps, int checkpoint_every);
+
+/* Reverse-time adjoint of the last lbem_forward_record: given the cotangent of
+ * the receiver traces dL/dtrace ([nrec][nsteps] floats, host or device), writes
+ * dL/d eps_r ([nsite] floats, host or device).  Recomputes each checkpoint
+ * segment forward, then runs the hand-written adjoint stream-collide kernel
+ * backwards through it; the gradient accumulates over time steps in FP64.
+ * If grad_cL2 is not NULL it also receives dL/dc_L^2 ([nsite] doubles). */
+lbem_status lbem_adjoint(lbem_t *h, const float *trace_cot, float *grad_eps, double *grad_cL2);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Time each launch shape of the stream-collide kernel on this handle for
+ * trial_steps steps (the state is saved and restored) and keep the fastest.
+ * *best (may be NULL) receives the chosen variant id. */
+lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best);
+lbem_status lbem_set_variant(lbem_t *h, int variant);
+lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);
+
+/* ---------------------------------------------------------------- batches of independent media */
+
+/* A batch steps n independent 2D FP32 handles (members, of any sizes) with one
+ * kernel launch per step over a flattened tile table; runs of steps are
+ * captured once into a CUDA graph and replayed.  Members keep their own
+ * medium, fields, sources, receivers and outputs (use the calls above on them);
+ * all members must be at the same time t when stepped.  The batch does not own
+ * the members. */
+lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out);
+lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps);
+lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best);
+void lbem_batch_destroy(lbem_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,572 @@
+// C ABI of the lbem library: handle lifecycle, problem set-up, time stepping,
+// outputs, diagnostics, checkpoint/resume and launch-shape autotuning.
+// Every entry point is declared and documented in include/lbem.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lbem_internal.cuh"
+
+namespace lbk {
+
+static thread_local std::string g_err;
+
+lbem_status fail(lbem_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+lbem_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return LBEM_ERR_CUDA;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device staging area of at least `floats` floats (grown on demand, owned by the handle).
+lbem_status ensure_stage(lbem_t *h, size_t floats) {
+    const size_t bytes = floats * sizeof(float);
+    if (h->stage_bytes >= bytes) return LBEM_OK;
+    if (h->d_stage) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->d_stage);
+        h->d_stage = nullptr;
+        h->stage_bytes = 0;
+    }
+    if (cudaMalloc(&h->d_stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBEM_ERR_NOMEM, "staging buffer allocation failed");
+    }
+    h->stage_bytes = bytes;
+    return LBEM_OK;
+}
+
+// A device view of caller input `p` (count floats): p itself if it is device
+// memory, else a copy in the staging area at float offset `off`.
+lbem_status device_input(lbem_t *h, const float *p, size_t count, size_t off, const float **out) {
+    if (!p) {
+        *out = nullptr;
+        return LBEM_OK;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return LBEM_OK;
+    }
+    lbem_status st = ensure_stage(h, off + count);
+    if (st != LBEM_OK) return st;
+    LBEM_CUDA(cudaMemcpyAsync(h->d_stage + off, p, count * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    *out = h->d_stage + off;
+    return LBEM_OK;
+}
+
+StepArgs step_args(const lbem_t *h, int cur_in) {
+    StepArgs a;
+    a.g = h->grid;
+    a.in = h->buf[cur_in];
+    a.out = h->buf[cur_in ^ 1];
+    a.med.cL2 = h->cL2;
+    a.med.mu = h->has_mu ? h->mu : nullptr;
+    a.med.dlnmu = h->has_mu ? h->dlnmu : nullptr;
+    a.evt.rowptr = h->nev ? h->d_rowptr : nullptr;
+    a.evt.ev = h->d_ev;
+    a.evt.amp = h->d_amp;
+    a.evt.nt = h->nsrc ? h->nt : 0;
+    a.evt.traces = h->d_traces;
+    a.evt.cap = h->nrec ? h->cap : 0;
+    a.t = h->t;
+    return a;
+}
+
+static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) {
+    if (h->dim == 2) return launch_step_2d(a, h->storage, h->has_mu, variant, h->stream);
+    return launch_step_3d(a, h->has_mu, variant, h->stream);
+}
+
+static void drop_graph(lbem_t *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_t0 = -1;
+}
+
+static size_t elem_bytes(int storage) { return storage == LBEM_F32 ? 4 : 2; }
+
+static lbem_status rebuild_events(lbem_t *h) {
+    std::vector<Event> ev;
+    std::vector<long long> rows;
+    const int nx = h->grid.nx;
+    for (int k = 0; k < h->nsrc; k++) {
+        ev.push_back(Event{(int)(h->src_site[k] % nx), 0, k, h->src_comp[k]});
+        rows.push_back(h->src_site[k] / nx);
+    }
+    for (int r = 0; r < h->nrec; r++) {
+        ev.push_back(Event{(int)(h->rec_site[r] % nx), 1, r, h->rec_comp[r]});
+        rows.push_back(h->rec_site[r] / nx);
+    }
+    std::vector<int> order(ev.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a] < rows[b]; });
+    std::vector<Event> sorted(ev.size());
+    std::vector<int> rowptr(h->grid.nrows + 1, 0);
+    for (size_t i = 0; i < order.size(); i++) {
+        sorted[i] = ev[order[i]];
+        rowptr[rows[order[i]] + 1]++;
+    }
+    for (int r = 0; r < h->grid.nrows; r++) rowptr[r + 1] += rowptr[r];
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_ev);
+    h->d_ev = nullptr;
+    h->nev = (int)sorted.size();
+    if (!h->d_rowptr) LBEM_CUDA(cudaMalloc(&h->d_rowptr, sizeof(int) * (h->grid.nrows + 1)));
+    LBEM_CUDA(cudaMemcpy(h->d_rowptr, rowptr.data(), sizeof(int) * rowptr.size(), cudaMemcpyHostToDevice));
+    if (h->nev) {
+        LBEM_CUDA(cudaMalloc(&h->d_ev, sizeof(Event) * sorted.size()));
+        LBEM_CUDA(cudaMemcpy(h->d_ev, sorted.data(), sizeof(Event) * sorted.size(), cudaMemcpyHostToDevice));
+    }
+    drop_graph(h);
+    return LBEM_OK;
+}
+
+}  // namespace lbk
+
+using namespace lbk;
+
+extern "C" {
+
+const char *lbem_last_error(void) { return g_err.c_str(); }
+
+lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
+    if (!d || !out) return fail(LBEM_ERR_ARG, "lbem_create: null argument");
+    *out = nullptr;
+    if (d->dim != 2 && d->dim != 3) return fail(LBEM_ERR_ARG, "lbem_create: dim must be 2 or 3");
+    const int nz = d->dim == 3 ? d->nz : 1;
+    if (d->nx < 1 || d->ny < 1 || nz < 1) return fail(LBEM_ERR_ARG, "lbem_create: grid sizes must be >= 1");
+    if (d->storage < LBEM_F32 || d->storage > LBEM_I16B) return fail(LBEM_ERR_ARG, "lbem_create: unknown storage");
+    if (d->dim == 3 && d->storage != LBEM_F32) return fail(LBEM_ERR_ARG, "lbem_create: 3D supports LBEM_F32 storage only");
+    if (d->nx > (1 << 28) || (long long)d->ny * nz > (1LL << 30))
+        return fail(LBEM_ERR_ARG, "lbem_create: grid too large");
+    lbem_t *h = new lbem_t();
+    h->dim = d->dim;
+    h->storage = d->storage;
+    h->npop = d->dim == 2 ? 5 : 21;
+    h->c_ref2 = d->c_ref2 > 0 ? d->c_ref2 : (d->dim == 2 ? 0.5 : 1.0 / 6.0);
+    h->stream = (cudaStream_t)d->stream;
+    Grid &G = h->grid;
+    G.nx = d->nx;
+    G.ny = d->ny;
+    G.nz = nz;
+    G.nrows = d->ny * nz;
+    G.nchunk = (d->nx + 3) / 4;
+    G.nchunk_pad = round_up(G.nchunk, 32);
+    G.pitch = 4 * G.nchunk_pad;
+    G.plane = (long long)G.pitch * G.nrows;
+    h->nsite = (long long)d->nx * d->ny * nz;
+    const size_t eb = elem_bytes(h->storage);
+    const size_t data_bytes = (size_t)h->npop * G.plane * eb;
+    const size_t ex_bytes = h->storage == LBEM_I16B ? (size_t)h->npop * G.nchunk_pad * G.nrows : 0;
+    const size_t per = ((data_bytes + 255) / 256 * 256) + ((ex_bytes + 255) / 256 * 256);
+    h->pool_bytes = 2 * per;
+    cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->cL2, sizeof(float) * G.plane);
+    if (e == cudaSuccess) {
+        h->n_partials = diag_blocks(h->nsite);
+        e = cudaMalloc((void **)&h->d_partials, sizeof(double) * 3 * h->n_partials);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_diag, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_counter, sizeof(unsigned) * 4);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lbem_destroy(h);
+        return fail(LBEM_ERR_NOMEM, "lbem_create: device allocation failed");
+    }
+    for (int b = 0; b < 2; b++) {
+        PopBuf &p = h->buf[b];
+        char *base = (char *)h->pool + b * per;
+        p.data = base;
+        p.ex = ex_bytes ? (int8_t *)(base + (data_bytes + 255) / 256 * 256) : nullptr;
+        p.plane = G.plane;
+        p.pitch = G.pitch;
+        p.expitch = G.nchunk_pad;
+        p.explane = (long long)G.nchunk_pad * G.nrows;
+        p.scale = p.inv_scale = 1.f;
+    }
+    cudaMemsetAsync(h->pool, 0, h->pool_bytes, h->stream);
+    cudaMemsetAsync(h->cL2, 0, sizeof(float) * G.plane, h->stream);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+        lbem_destroy(h);
+        return cuda_fail(e, "lbem_create");
+    }
+    *out = h;
+    return LBEM_OK;
+}
+
+void lbem_destroy(lbem_t *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    adjoint_free(h);
+    cudaFree(h->pool);
+    cudaFree(h->cL2);
+    cudaFree(h->mu);
+    cudaFree(h->dlnmu);
+    cudaFree(h->d_rowptr);
+    cudaFree(h->d_ev);
+    cudaFree(h->d_amp);
+    cudaFree(h->d_traces);
+    cudaFree(h->d_partials);
+    cudaFree(h->d_diag);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_stage);
+    delete h;
+}
+
+lbem_status lbem_set_stream(lbem_t *h, void *stream) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    cudaStreamSynchronize(h->stream);
+    h->stream = (cudaStream_t)stream;
+    drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_sync(lbem_t *h) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    LBEM_CUDA(cudaGetLastError());
+    return LBEM_OK;
+}
+
+lbem_status lbem_info(const lbem_t *h, long long *nsite, size_t *state_bytes) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (nsite) *nsite = h->nsite;
+    if (state_bytes) {
+        size_t b = (size_t)h->npop * h->grid.plane * elem_bytes(h->storage);
+        if (h->storage == LBEM_I16B) b += (size_t)h->npop * h->buf[0].explane;
+        *state_bytes = b;
+    }
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
+    if (!h || !eps_r) return fail(LBEM_ERR_ARG, "lbem_set_medium: null argument");
+    const float *de, *dm;
+    lbem_status st = device_input(h, eps_r, h->nsite, 0, &de);
+    if (st != LBEM_OK) return st;
+    if ((st = device_input(h, mu_r, h->nsite, h->nsite, &dm)) != LBEM_OK) return st;
+    LBEM_CUDA(launch_medium(h, de, dm, h->d_counter, h->stream));
+    unsigned bad = 0;
+    LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    if (bad)
+        return fail(LBEM_ERR_MEDIUM, "lbem_set_medium: " + std::to_string(bad) +
+                                         " sites with eps_r or mu_r not finite and > 0, or rest weight w0 outside "
+                                         "[0,1) (medium faster than c_ref)");
+    if (dm && !h->mu) {
+        LBEM_CUDA(cudaMalloc((void **)&h->mu, sizeof(float) * h->grid.plane));
+        LBEM_CUDA(cudaMalloc((void **)&h->dlnmu, sizeof(float) * h->grid.plane * h->dim));
+        LBEM_CUDA(cudaMemsetAsync(h->mu, 0, sizeof(float) * h->grid.plane, h->stream));
+        LBEM_CUDA(cudaMemsetAsync(h->dlnmu, 0, sizeof(float) * h->grid.plane * h->dim, h->stream));
+    }
+    LBEM_CUDA(launch_medium_write(h, de, dm, h->stream));
+    h->has_mu = dm != nullptr;
+    h->has_medium = true;
+    drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_set_fields: set a medium first");
+    const size_t n3 = 3 * (size_t)h->nsite;
+    const float *dE, *dB;
+    lbem_status st = device_input(h, E, n3, 0, &dE);
+    if (st != LBEM_OK) return st;
+    if ((st = device_input(h, B, n3, n3, &dB)) != LBEM_OK) return st;
+    if (h->storage == LBEM_F16) {
+        // power-of-two scale mapping the largest input magnitude to ~2^7 (headroom ~2^9 below the
+        // binary16 maximum for the populations, which can exceed the fields by the factor w0/c_L^2)
+        LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
+        if (dE) LBEM_CUDA(launch_maxabs(dE, n3, h->d_counter, h->stream));
+        if (dB) LBEM_CUDA(launch_maxabs(dB, n3, h->d_counter, h->stream));
+        unsigned bits = 0;
+        LBEM_CUDA(cudaMemcpyAsync(&bits, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        LBEM_CUDA(cudaStreamSynchronize(h->stream));
+        float m;
+        memcpy(&m, &bits, sizeof(m));
+        for (float a : h->src_amp) m = fmaxf(m, fabsf(a));
+        int k = 0;
+        if (m > 0 && isfinite(m)) k = 7 - (int)ceil(log2((double)m));
+        k = std::max(-40, std::min(40, k));
+        const float s = ldexpf(1.f, k);
+        for (int b = 0; b < 2; b++) {
+            h->buf[b].scale = s;
+            h->buf[b].inv_scale = 1.f / s;
+        }
+    }
+    cudaError_t e = h->dim == 2 ? launch_init_2d(h, dE, dB, h->stream) : launch_init_3d(h, dE, dB, h->stream);
+    LBEM_CUDA(e);
+    h->t = 0;
+    if (h->d_traces) LBEM_CUDA(cudaMemsetAsync(h->d_traces, 0, sizeof(float) * (size_t)h->nrec * h->cap, h->stream));
+    drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_sources(lbem_t *h, int n, const long long *site, const int *comp, const float *amp, int nt) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (n < 0 || n > 65536) return fail(LBEM_ERR_ARG, "lbem_set_sources: 0 <= n <= 65536");
+    if (n > 0 && (!site || !comp || !amp || nt < 1)) return fail(LBEM_ERR_ARG, "lbem_set_sources: null array or nt < 1");
+    for (int k = 0; k < n; k++) {
+        if (site[k] < 0 || site[k] >= h->nsite) return fail(LBEM_ERR_ARG, "lbem_set_sources: site out of range");
+        if (comp[k] < 0 || comp[k] > 2) return fail(LBEM_ERR_ARG, "lbem_set_sources: comp must be 0..2");
+    }
+    h->src_site.assign(site, site + n);
+    h->src_comp.assign(comp, comp + n);
+    h->src_amp.assign(amp, amp + (size_t)n * (n ? nt : 0));
+    h->nsrc = n;
+    h->nt = n ? nt : 0;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_amp);
+    h->d_amp = nullptr;
+    if (n) {
+        LBEM_CUDA(cudaMalloc((void **)&h->d_amp, sizeof(float) * (size_t)n * nt));
+        LBEM_CUDA(cudaMemcpy(h->d_amp, amp, sizeof(float) * (size_t)n * nt, cudaMemcpyHostToDevice));
+    }
+    return rebuild_events(h);
+}
+
+lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const int *comp, int capacity) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (n < 0 || n > 65536 || capacity < 0) return fail(LBEM_ERR_ARG, "lbem_set_receivers: 0 <= n <= 65536, capacity >= 0");
+    if (n > 0 && (!site || !comp)) return fail(LBEM_ERR_ARG, "lbem_set_receivers: null array");
+    for (int r = 0; r < n; r++) {
+        if (site[r] < 0 || site[r] >= h->nsite) return fail(LBEM_ERR_ARG, "lbem_set_receivers: site out of range");
+        if (comp[r] < 0 || comp[r] > 5) return fail(LBEM_ERR_ARG, "lbem_set_receivers: comp must be 0..5");
+    }
+    h->rec_site.assign(site, site + n);
+    h->rec_comp.assign(comp, comp + n);
+    h->nrec = n;
+    h->cap = capacity;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_traces);
+    h->d_traces = nullptr;
+    if (n && capacity) {
+        LBEM_CUDA(cudaMalloc((void **)&h->d_traces, sizeof(float) * (size_t)n * capacity));
+        LBEM_CUDA(cudaMemset(h->d_traces, 0, sizeof(float) * (size_t)n * capacity));
+    } else {
+        h->cap = 0;
+    }
+    return rebuild_events(h);
+}
+
+lbem_status lbem_set_graphs(lbem_t *h, int on) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    h->use_graphs = on != 0;
+    if (!on) drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_step(lbem_t *h, int nsteps) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (nsteps < 0) return fail(LBEM_ERR_ARG, "lbem_step: nsteps < 0");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_step: set a medium first");
+    if (nsteps == 0) return LBEM_OK;
+    if (h->use_graphs && h->stream == nullptr)
+        return fail(LBEM_ERR_STATE, "lbem_step: CUDA graphs need a non-default stream (lbem_set_stream)");
+    if (h->use_graphs) {
+        if (!(h->graph && h->graph_t0 == h->t && h->graph_steps == nsteps && h->graph_cur == h->cur &&
+              h->graph_variant == h->variant)) {
+            drop_graph(h);
+            LBEM_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            int cur = h->cur;
+            for (int n = 0; n < nsteps; n++) {
+                StepArgs a = step_args(h, cur);
+                a.t = h->t + n;
+                cudaError_t e = launch_step(h, a, h->variant);
+                if (e != cudaSuccess) {
+                    cudaGraph_t g;
+                    cudaStreamEndCapture(h->stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(e, "lbem_step (capture)");
+                }
+                cur ^= 1;
+            }
+            cudaGraph_t g = nullptr;
+            LBEM_CUDA(cudaStreamEndCapture(h->stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+            cudaGraphDestroy(g);
+            LBEM_CUDA(e);
+            h->graph_t0 = h->t;
+            h->graph_steps = nsteps;
+            h->graph_cur = h->cur;
+            h->graph_variant = h->variant;
+        }
+        LBEM_CUDA(cudaGraphLaunch(h->graph, h->stream));
+        h->cur ^= (nsteps & 1);
+        h->t += nsteps;
+        return LBEM_OK;
+    }
+    for (int n = 0; n < nsteps; n++) {
+        StepArgs a = step_args(h, h->cur);
+        LBEM_CUDA(launch_step(h, a, h->variant));
+        h->cur ^= 1;
+        h->t++;
+    }
+    return LBEM_OK;
+}
+
+lbem_status lbem_time(const lbem_t *h, long long *t) {
+    if (!h || !t) return fail(LBEM_ERR_ARG, "null argument");
+    *t = h->t;
+    return LBEM_OK;
+}
+
+lbem_status lbem_fields(lbem_t *h, float *E, float *B) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_fields: set a medium first");
+    if (!E && !B) return LBEM_OK;
+    const size_t n3 = 3 * (size_t)h->nsite;
+    const bool eh = E && !is_device_ptr(E), bh = B && !is_device_ptr(B);
+    if (eh || bh) {
+        lbem_status st = ensure_stage(h, 2 * n3);
+        if (st != LBEM_OK) return st;
+    }
+    float *dE = eh ? h->d_stage : E;
+    float *dB = bh ? h->d_stage + n3 : B;
+    cudaError_t e = h->dim == 2 ? launch_fields_2d(h, dE, dB, h->stream) : launch_fields_3d(h, dE, dB, h->stream);
+    LBEM_CUDA(e);
+    if (eh) LBEM_CUDA(cudaMemcpyAsync(E, dE, n3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (bh) LBEM_CUDA(cudaMemcpyAsync(B, dB, n3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (eh || bh) LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+lbem_status lbem_traces(lbem_t *h, float *out, int *nrecorded) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    const int n = (int)std::min<long long>(h->t, h->cap);
+    if (nrecorded) *nrecorded = n;
+    if (!out || n == 0 || h->nrec == 0) return LBEM_OK;
+    LBEM_CUDA(cudaMemcpy2DAsync(out, (size_t)n * sizeof(float), h->d_traces, (size_t)h->cap * sizeof(float),
+                                (size_t)n * sizeof(float), h->nrec, cudaMemcpyDefault, h->stream));
+    if (!is_device_ptr(out)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+lbem_status lbem_diagnostics(lbem_t *h, double out[3]) {
+    if (!h || !out) return fail(LBEM_ERR_ARG, "null argument");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_diagnostics: set a medium first");
+    cudaError_t e = h->dim == 2 ? launch_diag_2d(h, h->d_partials, h->n_partials, h->stream)
+                                : launch_diag_3d(h, h->d_partials, h->n_partials, h->stream);
+    LBEM_CUDA(e);
+    LBEM_CUDA(launch_reduce_partials(h->d_partials, h->n_partials, h->d_diag, h->stream));
+    LBEM_CUDA(cudaMemcpyAsync(out, h->d_diag, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; k++)
+        if (!isfinite(out[k])) return fail(LBEM_ERR_UNSTABLE, "lbem_diagnostics: non-finite state");
+    return LBEM_OK;
+}
+
+lbem_status lbem_save_state(lbem_t *h, void *dst) {
+    if (!h || !dst) return fail(LBEM_ERR_ARG, "null argument");
+    const PopBuf &p = h->buf[h->cur];
+    const size_t db = (size_t)h->npop * p.plane * elem_bytes(h->storage);
+    LBEM_CUDA(cudaMemcpyAsync(dst, p.data, db, cudaMemcpyDefault, h->stream));
+    if (p.ex) LBEM_CUDA(cudaMemcpyAsync((char *)dst + db, p.ex, (size_t)h->npop * p.explane, cudaMemcpyDefault, h->stream));
+    if (!is_device_ptr(dst)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
+    if (!h || !src || t_at_save < 0) return fail(LBEM_ERR_ARG, "lbem_load_state: bad argument");
+    const PopBuf &p = h->buf[h->cur];
+    const size_t db = (size_t)h->npop * p.plane * elem_bytes(h->storage);
+    LBEM_CUDA(cudaMemcpyAsync(p.data, src, db, cudaMemcpyDefault, h->stream));
+    if (p.ex)
+        LBEM_CUDA(cudaMemcpyAsync(p.ex, (const char *)src + db, (size_t)h->npop * p.explane, cudaMemcpyDefault, h->stream));
+    if (!is_device_ptr(src)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    h->t = t_at_save;
+    drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_variant(lbem_t *h, int variant) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    const int nv = h->dim == 2 ? nvariants_2d() : nvariants_3d();
+    if (variant < 0 || variant >= nv) return fail(LBEM_ERR_ARG, "lbem_set_variant: out of range");
+    h->variant = variant;
+    drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (variant) *variant = h->variant;
+    if (nvariants) *nvariants = h->dim == 2 ? nvariants_2d() : nvariants_3d();
+    return LBEM_OK;
+}
+
+lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_autotune: set a medium first");
+    if (trial_steps < 1) return fail(LBEM_ERR_ARG, "lbem_autotune: trial_steps >= 1");
+    const int nv = h->dim == 2 ? nvariants_2d() : nvariants_3d();
+    size_t bytes = 0;
+    lbem_info(h, nullptr, &bytes);
+    void *save = nullptr;
+    if (cudaMalloc(&save, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBEM_ERR_NOMEM, "lbem_autotune: no room to save the state");
+    }
+    const int cur0 = h->cur;
+    const long long t0 = h->t;
+    lbem_status st = lbem_save_state(h, save);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best_v = h->variant;
+    for (int v = 0; v < nv && st == LBEM_OK; v++) {
+        int cur = cur0;
+        for (int rep = 0; rep < 2 && st == LBEM_OK; rep++) {  // first pass warms up
+            cudaEventRecord(e0, h->stream);
+            for (int n = 0; n < trial_steps; n++) {
+                StepArgs a = step_args(h, cur);
+                a.evt.rowptr = nullptr;  // no trace writes while timing
+                cudaError_t e = launch_step(h, a, v);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "lbem_autotune");
+                    break;
+                }
+                cur ^= 1;
+            }
+            cudaEventRecord(e1, h->stream);
+        }
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cur = cur0;
+    if (st == LBEM_OK) st = lbem_load_state(h, save, t0);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(save);
+    if (st != LBEM_OK) return st;
+    h->variant = best_v;
+    drop_graph(h);
+    if (best) *best = best_v;
+    return LBEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+// Internal declarations of the lbem CUDA library (not part of the C ABI).
+//
+// Data layout in device memory (structure of arrays):
+//   * The distribution is stored as one plane per independent component:
+//     2D: 5 planes g_i = g_{i,xy} (i = 0..4, the D2Q5 order of the paper's
+//     Sec. "Lattice BGK formulation"); 3D: 21 planes h_{i,gamma} =
+//     (g_{i,yz}, g_{i,zx}, g_{i,xy}), plane index i*3 + gamma, i = 0..6 with
+//     c_1..c_3 = +x,+y,+z and c_4..c_6 = -x,-y,-z.
+//   * A plane is nrows = ny*nz rows of `pitch` elements; pitch = 4*nchunk_pad,
+//     nchunk_pad = 32*ceil(ceil(nx/4)/32), so every row is 128-element aligned
+//     and one warp covers 128 consecutive sites of one row (4 per lane).
+//   * Ping-pong: buffer `cur` holds the post-collision values g'_i(x, t-1)
+//     stored at the WRITING site x; the pre-collision state at time t is
+//     g_i(x, t) = buf[i](x - c_i) (pull streaming, Eq. 18).
+//   * Medium: c_L^2 per site in a pitched plane (FP32); mu and grad ln mu
+//     planes only when a non-uniform mu was given.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbem.h"
+
+namespace lbk {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int BLOCK = 256;  // threads per block of the stencil kernels
+
+// ------------------------------------------------------------------ storage
+struct PopBuf {
+    void *data = nullptr;    // npop planes of elements (float / half / bf16 / int16)
+    int8_t *ex = nullptr;    // LBEM_I16B: npop planes of per-chunk exponents
+    long long plane = 0;     // elements per plane
+    long long explane = 0;   // exponent bytes per plane
+    int pitch = 0;           // elements per row
+    int expitch = 0;         // exponents per row (= pitch / 4)
+    float scale = 1.f;       // LBEM_F16: stored = scale * value
+    float inv_scale = 1.f;
+};
+
+template <int ST>
+struct Codec;
+
+template <>
+struct Codec<LBEM_F32> {
+    static constexpr int bytes = 4;
+    __device__ static __forceinline__ float4 load4(const PopBuf &b, int p, int row, int c) {
+        const float4 *q = reinterpret_cast<const float4 *>(static_cast<const float *>(b.data) + p * b.plane +
+                                                           (long long)row * b.pitch);
+        return __ldg(q + c);
+    }
+    __device__ static __forceinline__ float load1(const PopBuf &b, int p, int row, int x) {
+        return __ldg(static_cast<const float *>(b.data) + p * b.plane + (long long)row * b.pitch + x);
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+        float4 *q = reinterpret_cast<float4 *>(static_cast<float *>(b.data) + p * b.plane + (long long)row * b.pitch);
+        __stcs(q + c, v);
+    }
+};
+
+__device__ __forceinline__ float4 h4_to_f4(uint2 r) {
+    __half2 a = *reinterpret_cast<__half2 *>(&r.x), c = *reinterpret_cast<__half2 *>(&r.y);
+    float2 fa = __half22float2(a), fc = __half22float2(c);
+    return make_float4(fa.x, fa.y, fc.x, fc.y);
+}
+
+template <>
+struct Codec<LBEM_F16> {
+    static constexpr int bytes = 2;
+    __device__ static __forceinline__ float4 load4(const PopBuf &b, int p, int row, int c) {
+        const uint2 *q = reinterpret_cast<const uint2 *>(static_cast<const __half *>(b.data) + p * b.plane +
+                                                         (long long)row * b.pitch);
+        float4 v = h4_to_f4(__ldg(q + c));
+        return make_float4(v.x * b.inv_scale, v.y * b.inv_scale, v.z * b.inv_scale, v.w * b.inv_scale);
+    }
+    __device__ static __forceinline__ float load1(const PopBuf &b, int p, int row, int x) {
+        const __half *q = static_cast<const __half *>(b.data) + p * b.plane + (long long)row * b.pitch + x;
+        return __half2float(__ldg(q)) * b.inv_scale;
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+        __half2 a = __floats2half2_rn(v.x * b.scale, v.y * b.scale);
+        __half2 d = __floats2half2_rn(v.z * b.scale, v.w * b.scale);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned *>(&a);
+        r.y = *reinterpret_cast<unsigned *>(&d);
+        uint2 *q = reinterpret_cast<uint2 *>(static_cast<__half *>(b.data) + p * b.plane + (long long)row * b.pitch);
+        __stcs(q + c, r);
+    }
+};
+
+template <>
+struct Codec<LBEM_BF16> {
+    static constexpr int bytes = 2;
+    __device__ static __forceinline__ float4 load4(const PopBuf &b, int p, int row, int c) {
+        const uint2 *q = reinterpret_cast<const uint2 *>(static_cast<const __nv_bfloat16 *>(b.data) + p * b.plane +
+                                                         (long long)row * b.pitch);
+        uint2 r = __ldg(q + c);
+        // bf16 -> f32 is a 16-bit left shift of the bit pattern
+        return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u),
+                           __uint_as_float(r.y << 16), __uint_as_float(r.y & 0xffff0000u));
+    }
+    __device__ static __forceinline__ float load1(const PopBuf &b, int p, int row, int x) {
+        const unsigned short *q = reinterpret_cast<const unsigned short *>(
+            static_cast<const __nv_bfloat16 *>(b.data) + p * b.plane + (long long)row * b.pitch + x);
+        return __uint_as_float(((unsigned)__ldg(q)) << 16);
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+        __nv_bfloat162 d = __floats2bfloat162_rn(v.z, v.w);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned *>(&a);
+        r.y = *reinterpret_cast<unsigned *>(&d);
+        uint2 *q = reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(b.data) + p * b.plane +
+                                             (long long)row * b.pitch);
+        __stcs(q + c, r);
+    }
+};
+
+// Block floating point: 4 consecutive sites of one plane row share exponent e
+// (int8); value = q * 2^(e - 15), q an int16 with |q| <= 32767.  Encoding picks
+// e = floor(log2(max|v|)) + 1, so max|v| < 2^e and q = rint(v * 2^(15 - e)):
+// the quantisation step is 2^-15 of the power of two above the block maximum.
+// Blocks whose maximum is below 2^-100 are stored as zero (e = -128).
+constexpr int I16B_ZERO = -128;
+
+__device__ __forceinline__ float pow2f(int k) {  // 2^k for -126 <= k <= 127
+    return __int_as_float((k + 127) << 23);
+}
+
+template <>
+struct Codec<LBEM_I16B> {
+    static constexpr int bytes = 2;
+    __device__ static __forceinline__ float4 load4(const PopBuf &b, int p, int row, int c) {
+        const uint2 *q = reinterpret_cast<const uint2 *>(static_cast<const int16_t *>(b.data) + p * b.plane +
+                                                         (long long)row * b.pitch);
+        uint2 r = __ldg(q + c);
+        int e = __ldg(b.ex + p * b.explane + (long long)row * b.expitch + c);
+        float f = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
+        return make_float4((float)(short)(r.x & 0xffffu) * f, (float)(short)(r.x >> 16) * f,
+                           (float)(short)(r.y & 0xffffu) * f, (float)(short)(r.y >> 16) * f);
+    }
+    __device__ static __forceinline__ float load1(const PopBuf &b, int p, int row, int x) {
+        short v = __ldg(static_cast<const short *>(b.data) + p * b.plane + (long long)row * b.pitch + x);
+        int e = __ldg(b.ex + p * b.explane + (long long)row * b.expitch + (x >> 2));
+        return (e == I16B_ZERO) ? 0.f : (float)v * pow2f(e - 15);
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+        float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+        int e;
+        uint2 r;
+        if (!(m < 0x1p+100f)) {  // huge or NaN: saturate, so the state stays visibly wrong
+            e = 127;
+            r.x = r.y = 0x7fff7fffu;
+        } else if (m < 0x1p-100f) {  // negligible block -> exact zero
+            e = I16B_ZERO;
+            r.x = r.y = 0u;
+        } else {
+            e = ((__float_as_int(m) >> 23) & 0xff) - 127 + 1;
+            float s = pow2f(15 - e);
+            int q0 = max(-32767, min(32767, __float2int_rn(v.x * s)));
+            int q1 = max(-32767, min(32767, __float2int_rn(v.y * s)));
+            int q2 = max(-32767, min(32767, __float2int_rn(v.z * s)));
+            int q3 = max(-32767, min(32767, __float2int_rn(v.w * s)));
+            r.x = (unsigned)(q0 & 0xffff) | ((unsigned)(q1 & 0xffff) << 16);
+            r.y = (unsigned)(q2 & 0xffff) | ((unsigned)(q3 & 0xffff) << 16);
+        }
+        uint2 *q = reinterpret_cast<uint2 *>(static_cast<int16_t *>(b.data) + p * b.plane + (long long)row * b.pitch);
+        __stcs(q + c, r);
+        b.ex[p * b.explane + (long long)row * b.expitch + c] = (int8_t)e;
+    }
+};
+
+__device__ __forceinline__ float get(const float4 &v, int j) {
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set(float4 &v, int j, float a) {
+    if (j == 0) v.x = a;
+    else if (j == 1) v.y = a;
+    else if (j == 2) v.z = a;
+    else v.w = a;
+}
+
+// ------------------------------------------------------------------ site events
+// Sources and receivers, sorted by row, with a CSR row pointer.  Event:
+//   x     : column
+//   kind  : 0 = point source (index = source k), 1 = receiver (index = receiver r)
+//   comp  : source current component 0..2 / receiver field 0..5
+struct Event {
+    int x, kind, index, comp;
+};
+
+struct Events {
+    const int *rowptr = nullptr;  // [nrows + 1] or null if no events
+    const Event *ev = nullptr;
+    const float *amp = nullptr;   // [nsrc][nt]
+    int nt = 0;
+    float *traces = nullptr;      // [nrec][cap]
+    int cap = 0;
+};
+
+// ------------------------------------------------------------------ launch parameters
+struct Grid {
+    int nx, ny, nz, nrows;   // nrows = ny*nz
+    int nchunk, nchunk_pad;  // chunks of 4 sites per row (active / padded to 32)
+    int pitch;               // elements per plane row
+    long long plane;         // elements per plane
+};
+
+struct Medium {
+    const float *cL2 = nullptr;    // [plane]
+    const float *mu = nullptr;     // [plane] or null
+    const float *dlnmu = nullptr;  // [D][plane] or null
+};
+
+struct StepArgs {
+    Grid g;
+    PopBuf in, out;
+    Medium med;
+    Events evt;
+    long long t;  // time of the pre-collision state being collided
+};
+
+// ------------------------------------------------------------------ handle
+struct Tuning {
+    int variant = 0;
+};
+
+struct AdjointState;  // defined in adjoint.cu
+
+}  // namespace lbk
+
+struct lbem {
+    int dim = 2, storage = LBEM_F32, npop = 5;
+    double c_ref2 = 0.5;
+    cudaStream_t stream = nullptr;
+    lbk::Grid grid{};
+    long long nsite = 0;
+    lbk::PopBuf buf[2];
+    int cur = 0;
+    void *pool = nullptr;  // population buffers
+    size_t pool_bytes = 0;
+    float *cL2 = nullptr, *mu = nullptr, *dlnmu = nullptr;
+    bool has_medium = false, has_mu = false;
+    long long t = 0;
+    // events
+    int *d_rowptr = nullptr;
+    lbk::Event *d_ev = nullptr;
+    float *d_amp = nullptr;
+    float *d_traces = nullptr;
+    int nsrc = 0, nrec = 0, nt = 0, cap = 0, nev = 0;
+    std::vector<long long> src_site;
+    std::vector<int> src_comp;
+    std::vector<float> src_amp;
+    std::vector<long long> rec_site;
+    std::vector<int> rec_comp;
+    // scratch
+    double *d_partials = nullptr;
+    int n_partials = 0;
+    double *d_diag = nullptr;     // [3]
+    unsigned *d_counter = nullptr; // validation / max-abs scratch
+    float *d_stage = nullptr;      // staging for host <-> device copies of grid fields
+    size_t stage_bytes = 0;
+    // graphs
+    bool use_graphs = false;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_t0 = -1;
+    int graph_steps = 0, graph_cur = -1, graph_variant = -1;
+    // tuning
+    int variant = 0;
+    // adjoint
+    lbk::AdjointState *adj = nullptr;
+};
+
+namespace lbk {
+
+// errors (lbem_api.cu)
+lbem_status fail(lbem_status s, const std::string &msg);
+lbem_status cuda_fail(cudaError_t e, const char *what);
+#define LBEM_CUDA(call)                                          \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return ::lbk::cuda_fail(_e, #call); \
+    } while (0)
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+StepArgs step_args(const lbem_t *h, int cur_in);
+
+// 2D (kernels2d.cu)
+int nvariants_2d();
+cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int variant, cudaStream_t s);
+cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
+cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);
+cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);
+// 3D (kernels3d.cu)
+int nvariants_3d();
+cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s);
+cudaError_t launch_init_3d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
+cudaError_t launch_fields_3d(const lbem_t *h, float *E, float *B, cudaStream_t s);
+cudaError_t launch_diag_3d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);
+// shared small kernels (medium.cu)
+cudaError_t launch_medium(lbem_t *h, const float *eps, const float *mu, unsigned *bad, cudaStream_t s);
+cudaError_t launch_maxabs(const float *a, long long n, unsigned *out, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double *partials, int n, double *out, cudaStream_t s);
+int diag_blocks(long long nsite);
+cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, cudaStream_t s);
+// adjoint.cu
+void adjoint_free(lbem_t *h);
+
+}  // namespace lbk

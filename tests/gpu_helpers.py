@@ -1,0 +1,52 @@
+"""Shared helpers of the GPU parity tests: run one problem on the GPU library and on the oracle."""
+import numpy as np
+
+import oracle as O
+from paper_1108_2651_gb300 import lbem
+
+
+def gpu_run(p, storage="f32", nsteps=None, variant=None, graphs=False):
+    """Run workloads.Problem p on the GPU; returns (E, B, traces) as float64 numpy, E/B grid + (3,)."""
+    import torch
+
+    nsteps = p.nsteps if nsteps is None else nsteps
+    stream = torch.cuda.Stream() if graphs else None  # graph capture needs a non-default stream
+    s = lbem.Solver(p.shape, storage=storage, stream=stream.cuda_stream if stream else None)
+    try:
+        s.set_problem(p)
+        if variant is not None:
+            lbem.lbem_set_variant(s.h, variant)
+        if graphs:
+            lbem.lbem_set_graphs(s.h, True)
+        s.step(nsteps)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        E = np.moveaxis(E.cpu().double().numpy(), 0, -1)
+        B = np.moveaxis(B.cpu().double().numpy(), 0, -1)
+        return E, B, tr.cpu().double().numpy()
+    finally:
+        s.close()
+
+
+def f32(a):
+    """The float32 value the GPU receives, as float64 (both sides get identical inputs)."""
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+def oracle_run(p, nsteps=None):
+    """The same problem on the FP64 oracle; returns (E, B, traces, medium, state)."""
+    nsteps = p.nsteps if nsteps is None else nsteps
+    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r))
+    g = O.init_state(m, f32(p.E0), f32(p.B0))
+    src = p.sources()
+    if src is not None:
+        src = dict(src, amp=f32(src["amp"]))
+    tr = O.run(m, g, nsteps, sources=src, receivers=p.receivers())
+    E, B = O.fields(m, g)
+    return E, B, tr, m, g
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)

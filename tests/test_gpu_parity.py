@@ -1,0 +1,259 @@
+"""GPU library vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 of E and B, and of receiver traces): FP32 storage
+<= 1e-5 at the 128^2 / 500-step homogeneous case and on small grids, <= 1e-4
+after 5000 steps.  Full-size grids are compared element by element over a
+bounded number of steps and, after the full number of steps, through the
+exact finite-difference identities that every FP32 state must satisfy.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import gpu_run, oracle_run, rel, f32
+from paper_1108_2651_gb300 import lbem, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem_small(D, shape, seed, nsteps, mu=True, nsrc=5, nrec=12):
+    eps, mu_r = W.random_medium(shape, seed, mu=mu)
+    p = W.Problem(f"small{D}", D, shape, eps, mu_r, nsteps)
+    E, B = W.random_fields(shape, seed + 1, 0.3)
+    p.E0, p.B0 = E, B
+    rng = np.random.default_rng(seed + 2)
+    n = int(np.prod(shape))
+    p.src_site = rng.choice(n, nsrc, replace=n < nsrc).astype(np.int64)
+    p.src_site[0] = 0
+    p.src_site[-1] = n - 1
+    p.src_comp = (rng.integers(0, 3, nsrc) if D == 3 else np.full(nsrc, 2)).astype(np.int32)
+    p.src_amp = rng.standard_normal((nsrc, nsteps))
+    p.rec_site = rng.choice(n, nrec, replace=True).astype(np.int64)
+    p.rec_comp = rng.integers(0, 6, nrec).astype(np.int32)
+    return p
+
+
+def _check(p, storage="f32", tol=1e-5, nsteps=None, **kw):
+    E, B, tr = gpu_run(p, storage, nsteps=nsteps, **kw)
+    oE, oB, otr, _, _ = oracle_run(p, nsteps=nsteps)
+    assert rel(E, oE) < tol, rel(E, oE)
+    assert rel(B, oB) < tol, rel(B, oB)
+    if otr.size:
+        assert rel(tr, otr) < tol, rel(tr, otr)
+    return rel(E, oE), rel(B, oB)
+
+
+def test_homogeneous_pulse_128_500_steps(lbem):
+    p = W.homogeneous_pulse(128, 6.0, 500)
+    eE, eB = _check(p, tol=1e-5)
+    print(f"128^2 x 500 FP32: rel-L2 E {eE:.2e} B {eB:.2e}")
+
+
+@pytest.mark.parametrize("shape", [(23, 37), (7, 130), (3, 5), (1, 1), (4, 1), (1, 9), (33, 129)])
+def test_small_ragged_2d(lbem, shape):
+    _check(_problem_small(2, shape, 11, 40), tol=1e-5)
+
+
+@pytest.mark.parametrize("shape", [(7, 9, 13), (3, 5, 130), (1, 1, 1), (2, 3, 1), (5, 1, 6)])
+def test_small_ragged_3d(lbem, shape):
+    _check(_problem_small(3, shape, 21, 25), tol=1e-5)
+
+
+@pytest.mark.parametrize("D,shape", [(2, (17, 45)), (3, (6, 7, 9))])
+def test_fields_round_trip(lbem, D, shape):
+    p = _problem_small(D, shape, 31, 1)
+    if D == 2:
+        p.E0[..., :2] = 0
+        p.B0[..., 2] = 0
+    E, B, _ = gpu_run(p, nsteps=0)
+    np.testing.assert_allclose(E, f32(p.E0), rtol=2e-6, atol=2e-6)
+    np.testing.assert_allclose(B, f32(p.B0), rtol=2e-6, atol=2e-6)
+
+
+@pytest.mark.parametrize("D,shape", [(2, (40, 52)), (3, (10, 11, 12))])
+def test_diagnostics_match_oracle(lbem, D, shape):
+    p = _problem_small(D, shape, 41, 30, mu=False)
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    s.step(30)
+    d = s.diagnostics()
+    s.close()
+    _, _, _, m, g = oracle_run(p)
+    od = O.diagnostics(m, g)
+    for a, b in zip(d, od):
+        assert abs(a - b) <= 1e-5 * abs(b) + 1e-9, (d, od)
+
+
+def test_5000_steps_fp32_heterogeneous_256(lbem):
+    """1024^2 recipe (n = 1 + 2 s, smoothing 20 cells, Ricker at ~20 cells per wavelength) at 256^2."""
+    p = W.heterogeneous_2d(256, seed=1, nsteps=5000)
+    eE, eB = _check(p, tol=1e-4)
+    print(f"256^2 x 5000 FP32: rel-L2 E {eE:.2e} B {eB:.2e}")
+
+
+def test_1024_full_size_elementwise_200_steps(lbem):
+    p = W.heterogeneous_2d(1024, seed=1, nsteps=200)
+    _check(p, tol=1e-5)
+
+
+def _leapfrog_residual(E3, cL2, S3):
+    """max |E^{t+1} - 2E^t + E^{t-1} - (c2 Lap5 E^t + S^t + c2/2 Lap5 S^t - S^{t-1})| over the grid."""
+    import crosscheck as X
+
+    Em, E0, Ep = E3
+    Sm, S0 = S3
+    r = Ep - 2 * E0 + Em - (cL2 * X.lap5(E0) + S0 + 0.5 * cL2 * X.lap5(S0) - Sm)
+    return np.abs(r).max()
+
+
+@pytest.mark.parametrize("n,seed", [(1024, 1), (4096, 2)])
+def test_full_size_5000_steps_satisfy_exact_fd_form(lbem, n, seed):
+    """After the full 5000 steps, the FP32 state obeys the scheme's exact FD form (a property the FP64
+    oracle is pinned to) at every site, to FP32 rounding of one step."""
+    import torch
+
+    p = W.heterogeneous_2d(n, seed=seed, nsteps=5000)
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    s.step(4998)
+    Es = []
+    for _ in range(3):
+        E, _ = s.fields()
+        Es.append(E[2].double().cpu().numpy())
+        s.step(1)
+    torch.cuda.synchronize()
+    m = O.medium(2, f32(p.eps_r))
+    amp = f32(p.src_amp[0])
+    S = []
+    for t in (4998, 4999):
+        st = np.zeros(p.shape)
+        st.flat[p.src_site[0]] = -m.ceff2.flat[p.src_site[0]] * amp[t]
+        S.append(st)
+    r = _leapfrog_residual(Es, m.cL2, S)
+    scale = max(np.abs(e).max() for e in Es)
+    s.close()
+    assert r < 2e-6 * scale, (r, scale)
+
+
+def test_4096_full_size_elementwise_20_steps(lbem):
+    p = W.heterogeneous_2d(4096, seed=2, nsteps=20)
+    _check(p, tol=1e-5)
+
+
+def test_192_cubed_full_size_elementwise_3_steps(lbem):
+    p = W.heterogeneous_3d(192, nsteps=3)
+    B = np.zeros(p.shape + (3,))
+    p.E0, B0 = W.random_fields(p.shape, 5, 0.1)
+    p.B0 = B0
+    _check(p, tol=1e-5)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16", "i16b"])
+def test_reduced_storage_short_run_tracks_oracle(lbem, storage):
+    """Half-precision storage on the homogeneous 128^2 pulse: error within the format's rounding bound
+    2 u sqrt(N/3) (u = unit roundoff; 2^-11 FP16, 2^-8 BF16, 2 * 2^-16 block int16)."""
+    p = W.homogeneous_pulse(128, 6.0, 500)
+    E, B, _ = gpu_run(p, storage)
+    oE, oB, _, _, _ = oracle_run(p)
+    u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8, "i16b": 2.0 ** -15}[storage]
+    bound = 2 * u * np.sqrt(500 / 3)
+    eE, eB = rel(E, oE), rel(B, oB)
+    print(f"{storage} 128^2 x 500: rel-L2 E {eE:.2e} B {eB:.2e} (bound {bound:.1e})")
+    assert eE < bound and eB < bound
+
+
+def test_variants_and_graphs_are_bitwise_identical(lbem):
+    p = _problem_small(2, (64, 300), 51, 30)
+    ref = gpu_run(p, variant=0)
+    n = lbem.lbem_get_variant(lbem.Solver((4, 4)).h)[1]
+    for v in range(n):
+        for graphs in (False, True):
+            out = gpu_run(p, variant=v, graphs=graphs)
+            for a, b in zip(out, ref):
+                np.testing.assert_array_equal(a, b)
+
+
+def test_host_and_device_pointers_agree(lbem):
+    import torch
+
+    p = _problem_small(2, (20, 30), 61, 15, mu=True)
+    ref = gpu_run(p)
+    s = lbem.Solver(p.shape)
+    lbem.lbem_set_medium(s.h, np.ascontiguousarray(p.eps_r, np.float32).ravel(),
+                         np.ascontiguousarray(p.mu_r, np.float32).ravel())
+    lbem.lbem_set_sources(s.h, p.src_site, p.src_comp, p.src_amp)
+    lbem.lbem_set_receivers(s.h, p.rec_site, p.rec_comp, p.nsteps)
+    lbem.lbem_set_fields(s.h, np.ascontiguousarray(np.moveaxis(p.E0, -1, 0), np.float32).ravel(),
+                         np.ascontiguousarray(np.moveaxis(p.B0, -1, 0), np.float32).ravel())
+    s.step(15)
+    E = np.zeros(3 * s.nsite, np.float32)
+    B = np.zeros(3 * s.nsite, np.float32)
+    lbem.lbem_fields(s.h, E, B)
+    tr = np.zeros(p.rec_site.size * 15, np.float32)
+    lbem.lbem_traces(s.h, tr)
+    s.close()
+    np.testing.assert_array_equal(np.moveaxis(E.reshape((3,) + p.shape), 0, -1), ref[0])
+    np.testing.assert_array_equal(np.moveaxis(B.reshape((3,) + p.shape), 0, -1), ref[1])
+    np.testing.assert_array_equal(tr.reshape(-1, 15), ref[2])
+
+
+def test_save_and_load_state_resume_bitwise(lbem):
+    import torch
+
+    p = _problem_small(2, (31, 70), 71, 60)
+    ref = gpu_run(p, nsteps=60)
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    s.step(25)
+    n, nbytes = lbem.lbem_info(s.h)
+    snap = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lbem.lbem_save_state(s.h, snap)
+    s.step(10)  # diverge, then resume from the snapshot
+    lbem.lbem_load_state(s.h, snap, 25)
+    s.step(35)
+    E, B = s.fields()
+    torch.cuda.synchronize()
+    s.close()
+    np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
+
+
+def test_errors_are_reported_and_handle_survives(lbem):
+    import torch
+
+    s = lbem.Solver((8, 8))
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_step(s.h, 1)
+    assert e.value.status == 6  # no medium yet
+    bad = torch.ones(64, device="cuda")
+    bad[5] = 0.25  # faster than the reference speed: w0 < 0
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_set_medium(s.h, bad)
+    assert e.value.status == 3
+    bad[5] = float("nan")
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_set_medium(s.h, bad)
+    assert e.value.status == 3
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_set_receivers(s.h, [64], [2], 10)
+    assert e.value.status == 1
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_set_sources(s.h, [3], [7], np.zeros((1, 4), np.float32))
+    assert e.value.status == 1
+    lbem.lbem_set_medium(s.h, torch.ones(64, device="cuda"))
+    lbem.lbem_set_fields(s.h)
+    lbem.lbem_step(s.h, 3)
+    assert lbem.lbem_time(s.h) == 3
+    s.close()
+
+
+def test_homogeneous_invariant_conserved_full_size(lbem):
+    """sum g^2/w is exactly conserved by the scheme (homogeneous, source-free); FP32 drift stays small."""
+    p = W.homogeneous_pulse(4096, 40.0, 1000)
+    p.eps_r = np.full(p.shape, 2.0)  # w0 = 1/2
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    d0 = s.diagnostics()
+    s.step(1000)
+    d1 = s.diagnostics()
+    s.close()
+    assert abs(d1[1] - d0[1]) < 1e-5 * d0[1], (d0, d1)
