@@ -468,6 +468,7 @@ lbem_status lbem_diagnostics(lbem_t *h, double out[3]) {
     LBEM_CUDA(launch_reduce_partials(h->d_partials, h->n_partials, h->d_diag, h->stream));
     LBEM_CUDA(cudaMemcpyAsync(out, h->d_diag, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    out[2] = sqrt(out[2]);  // the kernels sum (div B)^2
     for (int k = 0; k < 3; k++)
         if (!isfinite(out[k])) return fail(LBEM_ERR_UNSTABLE, "lbem_diagnostics: non-finite state");
     return LBEM_OK;
