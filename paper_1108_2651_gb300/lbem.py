@@ -52,6 +52,7 @@ _SIGS = {
     "lbem_fields": [_VP, _VP, _VP],
     "lbem_traces": [_VP, _VP, C.POINTER(_I)],
     "lbem_diagnostics": [_VP, C.POINTER(_D)],
+    "lbem_diagnostics_static": [_I, _I, _I, _I, _VP, _VP, _VP, _D, _VP, _VP],
     "lbem_save_state": [_VP, _VP],
     "lbem_load_state": [_VP, _VP, _LL],
     "lbem_forward_record": [_VP, _I, _I],
@@ -216,6 +217,11 @@ def lbem_diagnostics(h):
     out = (_D * 3)()
     _check(load().lbem_diagnostics(h, out))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def lbem_diagnostics_static(dim, nx, ny, nz, state, eps_r, mu_r, c_ref2, out, stream=None):
+    _check(load().lbem_diagnostics_static(int(dim), int(nx), int(ny), int(nz), _ptr(state, np.uint8), _ptr(eps_r),
+                                          _ptr(mu_r), float(c_ref2), _ptr(out, np.float64, 3, writable=True), stream))
 
 
 def lbem_save_state(h, dst):
