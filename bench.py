@@ -96,6 +96,76 @@ def workload(name):
     raise ValueError(name)
 
 
+def _time_run(lbem, torch, s, p, nsteps, stream, passes=1):
+    """Device time (ms) of `passes` full runs of nsteps steps on solver s (launch shape autotuned), after one
+    untimed run; returns (ms, variant)."""
+    s.set_problem(p)
+    v = lbem.lbem_autotune(s.h, 50)
+    lbem.lbem_step(s.h, nsteps)
+    ev = []
+    for _ in range(passes):
+        lbem.lbem_set_fields(s.h)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lbem.lbem_step(s.h, nsteps)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev])), v
+
+
+def other_forms(lbem, torch, p, peak, stream):
+    """Mlups and HBM roofline of the other forms on this GPU: 16-bit storage of the same workload, the
+    256-media batch (2000 steps, one graph-captured launch per step) and the 192^3 3D forward (1000 steps)."""
+    out = {}
+    n = int(np.prod(p.shape))
+    for st in ("f16", "bf16", "i16b"):
+        s = lbem.Solver(p.shape, storage=st, stream=stream.cuda_stream)
+        ms, v = _time_run(lbem, torch, s, p, p.nsteps, stream)
+        s.close()
+        per = ms / p.nsteps
+        gbs = BYTES_PER_SITE[st] * n / (per * 1e-3) / 1e9
+        out[st] = {"mlups": n * p.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                   "frac": gbs / peak, "bytes_per_site": BYTES_PER_SITE[st], "variant": v}
+    probs = W.batch_2d(256, nsteps=2000)
+    ss = []
+    for q in probs:
+        s = lbem.Solver(q.shape, stream=stream.cuda_stream)
+        s.set_problem(q)
+        ss.append(s)
+    b = lbem.lbem_batch_create([s.h for s in ss], stream.cuda_stream)
+    v = lbem.lbem_batch_autotune(b, 20)
+    lbem.lbem_batch_step(b, 2000)
+    for s in ss:
+        lbem.lbem_set_fields(s.h)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    lbem.lbem_batch_step(b, 2000)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e)
+    sites = sum(int(np.prod(q.shape)) for q in probs)
+    lbem.lbem_batch_destroy(b)
+    for s in ss:
+        s.close()
+    per = ms / 2000
+    gbs = 44 * sites / (per * 1e-3) / 1e9
+    out["batch256"] = {"mlups": sites * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                       "frac": gbs / peak, "sites": sites, "media": len(probs), "lb_steps": 2000, "variant": v,
+                       "graph": True}
+    q = W.heterogeneous_3d(192, nsteps=1000)
+    s = lbem.Solver(q.shape, stream=stream.cuda_stream)
+    ms, v = _time_run(lbem, torch, s, q, 1000, stream)
+    s.close()
+    n3 = 192 ** 3
+    per = ms / 1000
+    gbs = 172 * n3 / (per * 1e-3) / 1e9
+    out["het3d_192"] = {"mlups": n3 * 1000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                        "frac": gbs / peak, "bytes_per_site": 172, "variant": v}
+    return out
+
+
 def cpu_baseline(p, budget_s=12.0):
     """Time the FP64 oracle (as it stands) on a bounded sample: a 1024^2 crop of the medium centred on the
     source, as many steps as fit in about budget_s seconds of CPU work."""
@@ -197,6 +267,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the 16-bit, batched and 3D forms")
     args = ap.parse_args()
     rank, world = dist_setup(args)
     if args.impl == "reference":
@@ -296,6 +367,9 @@ def main():
                "h2d_bytes_per_step": int(eps_h.nbytes + p.src_amp.size * 4 + p.src_site.size * 12),
                "d2h_bytes_per_step": int(E_h.nbytes + B_h.nbytes + tr_h.nbytes + 24)}
 
+    forms = None
+    if not args.no_forms and args.lb_steps is None:
+        forms = other_forms(lbem, torch, p, peak, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
@@ -311,7 +385,7 @@ def main():
                            "l2": "inputs larger than L2 (2 x 336 MB distributions), no flush",
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "diagnostics_last": list(diag)}
+                "clocks": clk.summary(), "diagnostics_last": list(diag), "forms": forms}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -1,16 +1,334 @@
-// Batched stepping of independent media (placeholder until the batched kernel lands).
+// Batched stepping of many independent 2D FP32 media of uneven sizes: one
+// kernel launch per step covers every member through a flattened table of
+// warps (each warp = 128 sites of one row of one member, R rows per warp for
+// the variant R), and runs of steps are captured once into a CUDA graph.
+//
+// Per call, a small table of member descriptors (buffers, medium, events,
+// grid) is uploaded, and the start time t0 is written to device memory; the
+// captured launches read t0 and carry only their step offset and the
+// ping-pong parity, so one graph serves every call with the same number of
+// steps and the same members.
+#include <algorithm>
+#include <vector>
+
 #include "lbem_internal.cuh"
 
+namespace lbk {
+
+struct Member {
+    Grid g;
+    PopBuf a, b;  // a = buffer holding the state at the call's start
+    Medium med;
+    Events evt;
+};
+
+int nvariants_2d();
+
+// Same site update as step2d<F32, mu = false, R> (kernels2d.cu), with the grid,
+// buffers and events taken from the member this warp belongs to.
+__device__ __forceinline__ void pull_f32(const PopBuf &in, const Grid &G, int row, int c, int lane, float4 g[5]) {
+    using C = Codec<LBEM_F32>;
+    const int x0 = 4 * c;
+    const bool active = c < G.nchunk;
+    const int ym = row == 0 ? G.ny - 1 : row - 1;
+    const int yp = row == G.ny - 1 ? 0 : row + 1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    g[0] = active ? C::load4(in, 0, row, c) : z4;
+    float4 a1 = active ? C::load4(in, 1, row, c) : z4;
+    g[2] = active ? C::load4(in, 2, ym, c) : z4;
+    float4 a3 = active ? C::load4(in, 3, row, c) : z4;
+    g[4] = active ? C::load4(in, 4, yp, c) : z4;
+    float prev = __shfl_up_sync(FULL, a1.w, 1);
+    float next = __shfl_down_sync(FULL, a3.x, 1);
+    if (lane == 0 && active) prev = C::load1(in, 1, row, c == 0 ? G.nx - 1 : x0 - 1);
+    if (lane == 31 && x0 + 4 < G.nx) next = C::load1(in, 3, row, x0 + 4);
+    g[1] = make_float4(prev, a1.x, a1.y, a1.z);
+    g[3] = make_float4(a3.y, a3.z, a3.w, next);
+    if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, C::load1(in, 3, row, 0));
+}
+
+template <int R>
+__global__ void __launch_bounds__(BLOCK) step2d_batch(const Member *__restrict__ M, const long long *__restrict__ wstart,
+                                                      int n, const long long *__restrict__ t0p, int offset) {
+    using C = Codec<LBEM_F32>;
+    const int lane = threadIdx.x & 31;
+    const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    if (wg >= wstart[n]) return;
+    int lo = 0, hi = n - 1;  // member b with wstart[b] <= wg < wstart[b+1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(wstart + mid) <= wg) lo = mid;
+        else hi = mid - 1;
+    }
+    const Member &m = M[lo];
+    const Grid &G = m.g;
+    const long long lw = wg - wstart[lo];
+    const int wpr = G.nchunk_pad >> 5;
+    const int rg = (int)(lw / wpr);
+    const int c = (int)(lw - (long long)rg * wpr) * 32 + lane;
+    const int row0 = rg * R;
+    if (row0 >= G.ny) return;
+    const bool active = c < G.nchunk;
+    const PopBuf &in = (offset & 1) ? m.b : m.a;
+    const PopBuf &out = (offset & 1) ? m.a : m.b;
+    const long long t = *t0p + offset;
+    float4 g[R][5], cl[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int row = min(row0 + r, G.ny - 1);
+        pull_f32(in, G, row, c, lane, g[r]);
+        cl[r] = active ? __ldg(reinterpret_cast<const float4 *>(m.med.cL2 + (long long)row * G.pitch) + c)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int row = row0 + r;
+        if (row >= G.ny) break;
+        float4 shat = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m.evt.rowptr) {
+            const int e0 = __ldg(m.evt.rowptr + row), e1 = __ldg(m.evt.rowptr + row + 1);
+            for (int e = e0; e < e1; e++) {
+                const Event ev = m.evt.ev[e];
+                if ((ev.x >> 2) != c || !active) continue;
+                const int j = ev.x & 3;
+                if (ev.kind == 0) {
+                    if (ev.comp == 2 && t < m.evt.nt)
+                        set(shat, j, get(shat, j) - __ldg(m.evt.amp + (long long)ev.index * m.evt.nt + t));
+                } else if (t < m.evt.cap) {
+                    const float s = ((get(g[r][0], j) + get(g[r][1], j)) + (get(g[r][2], j) + get(g[r][3], j))) +
+                                    get(g[r][4], j);
+                    const float bx = get(g[r][4], j) - get(g[r][2], j), by = get(g[r][1], j) - get(g[r][3], j);
+                    float v = 0.f;
+                    if (ev.comp == 2) v = -get(cl[r], j) * s;
+                    else if (ev.comp == 3) v = bx;
+                    else if (ev.comp == 4) v = by;
+                    m.evt.traces[(long long)ev.index * m.evt.cap + t] = v;
+                }
+            }
+        }
+        float4 o[5];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float g0 = get(g[r][0], j), g1 = get(g[r][1], j), g2 = get(g[r][2], j), g3 = get(g[r][3], j),
+                        g4 = get(g[r][4], j), q = get(cl[r], j), sh = get(shat, j);
+            const float s = ((g0 + g1) + (g2 + g3)) + g4;
+            const float L = q * s, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
+            set(o[1], j, (L - g3) + Tm);
+            set(o[3], j, (L - g1) + Tm);
+            set(o[2], j, (L - g4) + Tm);
+            set(o[4], j, (L - g2) + Tm);
+            set(o[0], j, (2.f * w0 * s - g0) + T0);
+        }
+        if (active)
+            for (int i = 0; i < 5; i++) C::store4(out, i, row, c, o[i]);
+    }
+}
+
+}  // namespace lbk
+
+struct lbem_batch {
+    int n = 0;
+    std::vector<lbem_t *> members;
+    cudaStream_t stream = nullptr;
+    lbk::Member *d_members = nullptr;
+    long long *d_wstart = nullptr;  // [n + 1], per variant rebuilt
+    long long *d_t0 = nullptr;
+    long long total_warps = 0;
+    int variant = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0, graph_variant = -1;
+};
+
 using namespace lbk;
+
+static const int kRowsB[] = {1, 2, 4};
+
+static lbem_status upload_tables(lbem_batch_t *b, int variant) {
+    const int R = kRowsB[variant];
+    std::vector<Member> hm(b->n);
+    std::vector<long long> ws(b->n + 1, 0);
+    for (int k = 0; k < b->n; k++) {
+        lbem_t *h = b->members[k];
+        StepArgs a = step_args(h, h->cur);
+        hm[k].g = a.g;
+        hm[k].a = a.in;
+        hm[k].b = a.out;
+        hm[k].med = a.med;
+        hm[k].evt = a.evt;
+        ws[k + 1] = ws[k] + (long long)((h->grid.ny + R - 1) / R) * (h->grid.nchunk_pad / 32);
+    }
+    b->total_warps = ws[b->n];
+    LBEM_CUDA(cudaMemcpyAsync(b->d_members, hm.data(), sizeof(Member) * b->n, cudaMemcpyHostToDevice, b->stream));
+    LBEM_CUDA(cudaMemcpyAsync(b->d_wstart, ws.data(), sizeof(long long) * (b->n + 1), cudaMemcpyHostToDevice, b->stream));
+    LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vectors go out of scope
+    return LBEM_OK;
+}
+
+static cudaError_t launch_batch(lbem_batch_t *b, int variant, int offset) {
+    const unsigned blocks = (unsigned)((b->total_warps * 32 + BLOCK - 1) / BLOCK);
+    switch (kRowsB[variant]) {
+        case 1: step2d_batch<1><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->n, b->d_t0, offset); break;
+        case 2: step2d_batch<2><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->n, b->d_t0, offset); break;
+        default: step2d_batch<4><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->n, b->d_t0, offset); break;
+    }
+    return cudaGetLastError();
+}
+
+static void drop_batch_graph(lbem_batch_t *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = 0;
+    b->graph_variant = -1;
+}
+
+static lbem_status check_members(lbem_batch_t *b) {
+    const long long t = b->members[0]->t;
+    for (lbem_t *h : b->members) {
+        if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_batch_step: every member needs a medium");
+        if (h->t != t) return fail(LBEM_ERR_STATE, "lbem_batch_step: members are at different times");
+        if (h->stream != b->stream) {
+            // members may have work queued on their own streams: order it before the batch
+            LBEM_CUDA(cudaStreamSynchronize(h->stream));
+        }
+    }
+    return LBEM_OK;
+}
+
 extern "C" {
+
 lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out) {
-    (void)n; (void)members; (void)stream; (void)out;
-    return fail(LBEM_ERR_STATE, "lbem_batch_create: not available in this build");
+    if (!out || !members || n < 1) return fail(LBEM_ERR_ARG, "lbem_batch_create: need n >= 1 members");
+    *out = nullptr;
+    for (int k = 0; k < n; k++) {
+        const lbem_t *h = members[k];
+        if (!h) return fail(LBEM_ERR_ARG, "lbem_batch_create: null member");
+        if (h->dim != 2 || h->storage != LBEM_F32 || h->has_mu)
+            return fail(LBEM_ERR_ARG, "lbem_batch_create: members must be 2D, LBEM_F32 storage, uniform mu");
+        for (int j = 0; j < k; j++)
+            if (members[j] == h) return fail(LBEM_ERR_ARG, "lbem_batch_create: a member appears twice");
+    }
+    lbem_batch_t *b = new lbem_batch_t();
+    b->n = n;
+    b->members.assign(members, members + n);
+    b->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc((void **)&b->d_members, sizeof(Member) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_wstart, sizeof(long long) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_t0, sizeof(long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lbem_batch_destroy(b);
+        return fail(LBEM_ERR_NOMEM, "lbem_batch_create: device allocation failed");
+    }
+    *out = b;
+    return LBEM_OK;
 }
-lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps) { (void)b; (void)nsteps; return fail(LBEM_ERR_STATE, "not available"); }
+
+lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps) {
+    if (!b) return fail(LBEM_ERR_ARG, "null batch");
+    if (nsteps < 0) return fail(LBEM_ERR_ARG, "lbem_batch_step: nsteps < 0");
+    if (nsteps == 0) return LBEM_OK;
+    lbem_status st = check_members(b);
+    if (st != LBEM_OK) return st;
+    st = upload_tables(b, b->variant);
+    if (st != LBEM_OK) return st;
+    const long long t0 = b->members[0]->t;
+    LBEM_CUDA(cudaMemcpyAsync(b->d_t0, &t0, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    LBEM_CUDA(cudaStreamSynchronize(b->stream));
+    if (b->stream != nullptr) {
+        if (!(b->graph && b->graph_steps == nsteps && b->graph_variant == b->variant)) {
+            drop_batch_graph(b);
+            LBEM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < nsteps; k++) {
+                cudaError_t e = launch_batch(b, b->variant, k);
+                if (e != cudaSuccess) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(b->stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(e, "lbem_batch_step (capture)");
+                }
+            }
+            cudaGraph_t g = nullptr;
+            LBEM_CUDA(cudaStreamEndCapture(b->stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            LBEM_CUDA(e);
+            b->graph_steps = nsteps;
+            b->graph_variant = b->variant;
+        }
+        LBEM_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+        for (int k = 0; k < nsteps; k++) LBEM_CUDA(launch_batch(b, b->variant, k));
+    }
+    for (lbem_t *h : b->members) {
+        h->cur ^= (nsteps & 1);
+        h->t += nsteps;
+    }
+    // members' own streams must see the batch's work before their next call
+    if (b->stream != b->members[0]->stream) LBEM_CUDA(cudaStreamSynchronize(b->stream));
+    return LBEM_OK;
+}
+
 lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best) {
-    (void)b; (void)trial_steps; (void)best;
-    return fail(LBEM_ERR_STATE, "not available");
+    if (!b) return fail(LBEM_ERR_ARG, "null batch");
+    if (trial_steps < 1) return fail(LBEM_ERR_ARG, "lbem_batch_autotune: trial_steps >= 1");
+    lbem_status st = check_members(b);
+    if (st != LBEM_OK) return st;
+    // the trials step every member in place; the states are saved and restored
+    std::vector<void *> saves(b->n, nullptr);
+    for (int k = 0; k < b->n; k++) {
+        size_t bytes = 0;
+        lbem_info(b->members[k], nullptr, &bytes);
+        if (cudaMalloc(&saves[k], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            for (void *p : saves) cudaFree(p);
+            return fail(LBEM_ERR_NOMEM, "lbem_batch_autotune: no room to save member states");
+        }
+        if ((st = lbem_save_state(b->members[k], saves[k])) != LBEM_OK) break;
+    }
+    const long long t0 = b->members[0]->t;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best_v = b->variant;
+    const int nv = nvariants_2d();
+    for (int v = 0; v < nv && st == LBEM_OK; v++) {
+        if ((st = upload_tables(b, v)) != LBEM_OK) break;
+        LBEM_CUDA(cudaMemcpyAsync(b->d_t0, &t0, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+        for (int rep = 0; rep < 2; rep++) {
+            cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < trial_steps; k++) LBEM_CUDA(launch_batch(b, v, k));
+            cudaEventRecord(e1, b->stream);
+        }
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int k = 0; k < b->n && st == LBEM_OK; k++) st = lbem_load_state(b->members[k], saves[k], t0);
+    cudaStreamSynchronize(b->stream);
+    for (lbem_t *h : b->members) cudaStreamSynchronize(h->stream);
+    for (void *p : saves) cudaFree(p);
+    if (st != LBEM_OK) return st;
+    b->variant = best_v;
+    drop_batch_graph(b);
+    if (best) *best = best_v;
+    return LBEM_OK;
 }
-void lbem_batch_destroy(lbem_batch_t *b) { (void)b; }
+
+void lbem_batch_destroy(lbem_batch_t *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_batch_graph(b);
+    cudaFree(b->d_members);
+    cudaFree(b->d_wstart);
+    cudaFree(b->d_t0);
+    delete b;
 }
+
+}  // extern "C"

@@ -31,21 +31,23 @@ struct Pull2D {
 
 // Pre-collision populations of the 4 sites (row, 4c..4c+3): g_i(x) = buf_i(x - c_i).
 // Must be called by all 32 lanes of a warp (shuffles); lanes with c >= nchunk
-// read padding and their results are discarded by the caller.
+// load nothing and their results are discarded by the caller.
 template <int ST>
 __device__ __forceinline__ void pull2d(const PopBuf &in, const Grid &G, int row, int c, int lane, float4 g[5]) {
     using C = Codec<ST>;
     const int x0 = 4 * c;
+    const bool active = c < G.nchunk;  // lanes past the row end load nothing
     const int ym = row == 0 ? G.ny - 1 : row - 1;
     const int yp = row == G.ny - 1 ? 0 : row + 1;
-    g[0] = C::load4(in, 0, row, c);
-    float4 a1 = C::load4(in, 1, row, c);
-    g[2] = C::load4(in, 2, ym, c);
-    float4 a3 = C::load4(in, 3, row, c);
-    g[4] = C::load4(in, 4, yp, c);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    g[0] = active ? C::load4(in, 0, row, c) : z4;
+    float4 a1 = active ? C::load4(in, 1, row, c) : z4;
+    g[2] = active ? C::load4(in, 2, ym, c) : z4;
+    float4 a3 = active ? C::load4(in, 3, row, c) : z4;
+    g[4] = active ? C::load4(in, 4, yp, c) : z4;
     float prev = __shfl_up_sync(FULL, a1.w, 1);
     float next = __shfl_down_sync(FULL, a3.x, 1);
-    if (lane == 0) prev = C::load1(in, 1, row, c == 0 ? G.nx - 1 : x0 - 1);
+    if (lane == 0 && active) prev = C::load1(in, 1, row, c == 0 ? G.nx - 1 : x0 - 1);
     if (lane == 31 && x0 + 4 < G.nx) next = C::load1(in, 3, row, x0 + 4);
     g[1] = make_float4(prev, a1.x, a1.y, a1.z);
     g[3] = make_float4(a3.y, a3.z, a3.w, next);
@@ -99,14 +101,15 @@ __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {
     for (int r = 0; r < R; r++) {
         const int row = min(row0 + r, G.ny - 1);
         pull2d<ST>(a.in, G, row, c, lane, g[r]);
-        cl[r] = __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + c);
+        cl[r] = active ? __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + c)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int row = row0 + r;
         if (row >= G.ny) break;  // warp-uniform
         float4 shat = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (MU) {
+        if (MU && active) {
             const float4 dx = __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + (long long)row * G.pitch) + c);
             const float4 dy =
                 __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + (long long)row * G.pitch) + c);

@@ -41,18 +41,20 @@ __device__ __forceinline__ void pull3d(const PopBuf &in, const Grid &G, int row,
     using C = Codec<LBEM_F32>;
     const Rows3 R = rows3(G, row);
     const int x0 = 4 * c;
+    const bool active = c < G.nchunk;  // lanes past the row end load nothing
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int gm = 0; gm < 3; gm++) {
-        v[0 + gm] = C::load4(in, 0 + gm, R.r0, c);
-        float4 a1 = C::load4(in, 3 + gm, R.r0, c);
-        v[6 + gm] = C::load4(in, 6 + gm, R.ym, c);
-        v[9 + gm] = C::load4(in, 9 + gm, R.zm, c);
-        float4 a4 = C::load4(in, 12 + gm, R.r0, c);
-        v[15 + gm] = C::load4(in, 15 + gm, R.yp, c);
-        v[18 + gm] = C::load4(in, 18 + gm, R.zp, c);
+        v[0 + gm] = active ? C::load4(in, 0 + gm, R.r0, c) : z4;
+        float4 a1 = active ? C::load4(in, 3 + gm, R.r0, c) : z4;
+        v[6 + gm] = active ? C::load4(in, 6 + gm, R.ym, c) : z4;
+        v[9 + gm] = active ? C::load4(in, 9 + gm, R.zm, c) : z4;
+        float4 a4 = active ? C::load4(in, 12 + gm, R.r0, c) : z4;
+        v[15 + gm] = active ? C::load4(in, 15 + gm, R.yp, c) : z4;
+        v[18 + gm] = active ? C::load4(in, 18 + gm, R.zp, c) : z4;
         float prev = __shfl_up_sync(FULL, a1.w, 1);
         float next = __shfl_down_sync(FULL, a4.x, 1);
-        if (lane == 0) prev = C::load1(in, 3 + gm, R.r0, c == 0 ? G.nx - 1 : x0 - 1);
+        if (lane == 0 && active) prev = C::load1(in, 3 + gm, R.r0, c == 0 ? G.nx - 1 : x0 - 1);
         if (lane == 31 && x0 + 4 < G.nx) next = C::load1(in, 12 + gm, R.r0, x0 + 4);
         v[3 + gm] = make_float4(prev, a1.x, a1.y, a1.z);
         v[12 + gm] = make_float4(a4.y, a4.z, a4.w, next);
@@ -137,9 +139,10 @@ __global__ void __launch_bounds__(BLOCK) step3d(StepArgs a) {
     const bool active = c < G.nchunk;
     float4 v[21];
     pull3d(a.in, G, row, c, lane, v);
-    const float4 cl = __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + c);
+    const float4 cl = active ? __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + c)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 shx = make_float4(0.f, 0.f, 0.f, 0.f), shy = shx, shz = shx;
-    if (MU) {
+    if (MU && active) {
         const float4 dx = __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + (long long)row * G.pitch) + c);
         const float4 dy = __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + (long long)row * G.pitch) + c);
         const float4 dz =
@@ -192,10 +195,77 @@ __global__ void __launch_bounds__(BLOCK) step3d(StepArgs a) {
     }
 }
 
-int nvariants_3d() { return 1; }
+// One site per thread: a warp covers 32 consecutive sites of a row; the +-x
+// pulls are plain (unaligned, coalesced) loads whose overlap L1/L2 absorbs.
+// Far fewer registers than the 4-sites-per-lane kernel, so more warps per SM.
+template <bool MU>
+__global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a) {
+    const Grid &G = a.g;
+    const int tpr = G.pitch;  // threads per row (pitch is a multiple of 32)
+    const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
+    const int row = (int)(tid / tpr);
+    const int x = (int)(tid - (long long)row * tpr);
+    if (row >= G.nrows || x >= G.nx) return;
+    const Rows3 R = rows3(G, row);
+    const int xm = x == 0 ? G.nx - 1 : x - 1, xp = x == G.nx - 1 ? 0 : x + 1;
+    const float *in = static_cast<const float *>(a.in.data);
+    auto ld = [&](int p, int r, int xx) { return __ldg(in + p * G.plane + (long long)r * G.pitch + xx); };
+    float h[21];
+#pragma unroll
+    for (int gm = 0; gm < 3; gm++) {
+        h[0 + gm] = ld(0 + gm, R.r0, x);
+        h[3 + gm] = ld(3 + gm, R.r0, xm);
+        h[6 + gm] = ld(6 + gm, R.ym, x);
+        h[9 + gm] = ld(9 + gm, R.zm, x);
+        h[12 + gm] = ld(12 + gm, R.r0, xp);
+        h[15 + gm] = ld(15 + gm, R.yp, x);
+        h[18 + gm] = ld(18 + gm, R.zp, x);
+    }
+    const long long o = (long long)row * G.pitch + x;
+    const float cl = __ldg(a.med.cL2 + o);
+    float shx = 0.f, shy = 0.f, shz = 0.f;
+    if (MU) {
+        const float dx = __ldg(a.med.dlnmu + o), dy = __ldg(a.med.dlnmu + G.plane + o),
+                    dz = __ldg(a.med.dlnmu + 2 * G.plane + o);
+        const Mom3 m = moments3(h);
+        shx = m.by * dz - m.bz * dy;
+        shy = m.bz * dx - m.bx * dz;
+        shz = m.bx * dy - m.by * dx;
+    }
+    if (a.evt.rowptr) {
+        const int e0 = __ldg(a.evt.rowptr + row), e1 = __ldg(a.evt.rowptr + row + 1);
+        for (int e = e0; e < e1; e++) {
+            const Event ev = a.evt.ev[e];
+            if (ev.x != x) continue;
+            if (ev.kind == 0) {
+                if (a.t < a.evt.nt) {
+                    float jj = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
+                    if (MU) jj *= __ldg(a.med.mu + o);
+                    if (ev.comp == 0) shx -= jj;
+                    else if (ev.comp == 1) shy -= jj;
+                    else shz -= jj;
+                }
+            } else if (a.t < a.evt.cap) {
+                a.evt.traces[(long long)ev.index * a.evt.cap + a.t] = field3d(ev.comp, cl, moments3(h));
+            }
+        }
+    }
+    collide3d(h, cl, shx, shy, shz);
+    float *out = static_cast<float *>(a.out.data);
+#pragma unroll
+    for (int p = 0; p < 21; p++) __stcs(out + p * G.plane + o, h[p]);
+}
+
+int nvariants_3d() { return 2; }
 
 cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s) {
-    (void)variant;
+    if (variant == 1) {
+        const long long threads = (long long)a.g.nrows * a.g.pitch;
+        const unsigned blocks = (unsigned)((threads + BLOCK - 1) / BLOCK);
+        if (has_mu) step3d_site<true><<<blocks, BLOCK, 0, s>>>(a);
+        else step3d_site<false><<<blocks, BLOCK, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const long long warps = (long long)a.g.nrows * (a.g.nchunk_pad / 32);
     const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
     if (has_mu) step3d<true><<<blocks, BLOCK, 0, s>>>(a);

@@ -167,12 +167,12 @@ lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
     G.nrows = d->ny * nz;
     G.nchunk = (d->nx + 3) / 4;
     G.nchunk_pad = round_up(G.nchunk, 32);
-    G.pitch = 4 * G.nchunk_pad;
+    G.pitch = round_up(d->nx, 32);  // 128-byte aligned FP32 rows; >= 4 * nchunk
     G.plane = (long long)G.pitch * G.nrows;
     h->nsite = (long long)d->nx * d->ny * nz;
     const size_t eb = elem_bytes(h->storage);
     const size_t data_bytes = (size_t)h->npop * G.plane * eb;
-    const size_t ex_bytes = h->storage == LBEM_I16B ? (size_t)h->npop * G.nchunk_pad * G.nrows : 0;
+    const size_t ex_bytes = h->storage == LBEM_I16B ? (size_t)h->npop * (G.pitch / 4) * G.nrows : 0;
     const size_t per = ((data_bytes + 255) / 256 * 256) + ((ex_bytes + 255) / 256 * 256);
     h->pool_bytes = 2 * per;
     cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
@@ -195,8 +195,8 @@ lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
         p.ex = ex_bytes ? (int8_t *)(base + (data_bytes + 255) / 256 * 256) : nullptr;
         p.plane = G.plane;
         p.pitch = G.pitch;
-        p.expitch = G.nchunk_pad;
-        p.explane = (long long)G.nchunk_pad * G.nrows;
+        p.expitch = G.pitch / 4;
+        p.explane = (long long)(G.pitch / 4) * G.nrows;
         p.scale = p.inv_scale = 1.f;
     }
     cudaMemsetAsync(h->pool, 0, h->pool_bytes, h->stream);

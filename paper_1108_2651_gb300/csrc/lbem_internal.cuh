@@ -6,9 +6,11 @@
 //     Sec. "Lattice BGK formulation"); 3D: 21 planes h_{i,gamma} =
 //     (g_{i,yz}, g_{i,zx}, g_{i,xy}), plane index i*3 + gamma, i = 0..6 with
 //     c_1..c_3 = +x,+y,+z and c_4..c_6 = -x,-y,-z.
-//   * A plane is nrows = ny*nz rows of `pitch` elements; pitch = 4*nchunk_pad,
-//     nchunk_pad = 32*ceil(ceil(nx/4)/32), so every row is 128-element aligned
-//     and one warp covers 128 consecutive sites of one row (4 per lane).
+//   * A plane is nrows = ny*nz rows of `pitch` elements, pitch = nx rounded up
+//     to a multiple of 32 (128-byte aligned FP32 rows).  Threads: a row is cut
+//     into nchunk = ceil(nx/4) chunks of 4 sites, one per lane, padded to
+//     nchunk_pad = 32*ceil(nchunk/32) lanes, so one warp covers 128
+//     consecutive sites of one row; lanes past the row end load nothing.
 //   * Ping-pong: buffer `cur` holds the post-collision values g'_i(x, t-1)
 //     stored at the WRITING site x; the pre-collision state at time t is
 //     g_i(x, t) = buf[i](x - c_i) (pull streaming, Eq. 18).

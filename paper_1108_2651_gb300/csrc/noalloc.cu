@@ -198,7 +198,7 @@ extern "C" lbem_status lbem_diagnostics_static(int dim, int nx, int ny, int nz, 
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.pitch = 4 * round_up((nx + 3) / 4, 32);
+    g.pitch = round_up(nx, 32);  // the row pitch of lbem_create's layout
     g.plane = (long long)g.pitch * ny * nz;
     g.nsite = nsite;
     g.c_ref2 = c_ref2 > 0 ? c_ref2 : (dim == 2 ? 0.5 : 1.0 / 6.0);
