@@ -22,8 +22,6 @@ struct Member {
     Events evt;
 };
 
-int nvariants_2d();
-
 // Same site update as step2d<F32, mu = false, R> (kernels2d.cu), with the grid,
 // buffers and events taken from the member this warp belongs to.
 __device__ __forceinline__ void pull_f32(const PopBuf &in, const Grid &G, int row, int c, int lane, float4 g[5]) {
@@ -142,6 +140,7 @@ struct lbem_batch {
 using namespace lbk;
 
 static const int kRowsB[] = {1, 2, 4};
+static const int kBatchVariants = (int)(sizeof(kRowsB) / sizeof(kRowsB[0]));
 
 static lbem_status upload_tables(lbem_batch_t *b, int variant) {
     const int R = kRowsB[variant];
@@ -291,8 +290,7 @@ lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best) {
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     int best_v = b->variant;
-    const int nv = nvariants_2d();
-    for (int v = 0; v < nv && st == LBEM_OK; v++) {
+    for (int v = 0; v < kBatchVariants && st == LBEM_OK; v++) {
         if ((st = upload_tables(b, v)) != LBEM_OK) break;
         LBEM_CUDA(cudaMemcpyAsync(b->d_t0, &t0, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
         for (int rep = 0; rep < 2; rep++) {

@@ -161,12 +161,567 @@ __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ persistent, software-pipelined variant
+// Each warp walks units of 128 sites (one row segment) with a grid-sized
+// stride and issues the loads of its next unit before it shuffles, collides
+// and stores the current one, so the memory system always has a unit's loads
+// in flight per warp even while it computes.
+struct Raw2 {
+    float4 v0, a1, v2, a3, v4, cl;
+    float s1, s3, sw;
+};
+
+template <int ST>
+__device__ __forceinline__ void load_raw(const StepArgs &a, int row, int c, int lane, Raw2 &r) {
+    using C = Codec<ST>;
+    const Grid &G = a.g;
+    const bool active = c < G.nchunk;
+    const int x0 = 4 * c;
+    const int ym = row == 0 ? G.ny - 1 : row - 1, yp = row == G.ny - 1 ? 0 : row + 1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.v0 = active ? C::load4(a.in, 0, row, c) : z4;
+    r.a1 = active ? C::load4(a.in, 1, row, c) : z4;
+    r.v2 = active ? C::load4(a.in, 2, ym, c) : z4;
+    r.a3 = active ? C::load4(a.in, 3, row, c) : z4;
+    r.v4 = active ? C::load4(a.in, 4, yp, c) : z4;
+    r.cl = active ? __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + c) : z4;
+    r.s1 = (lane == 0 && active) ? C::load1(a.in, 1, row, c == 0 ? G.nx - 1 : x0 - 1) : 0.f;
+    r.s3 = (lane == 31 && x0 + 4 < G.nx) ? C::load1(a.in, 3, row, x0 + 4) : 0.f;
+    r.sw = (c == G.nchunk - 1) ? C::load1(a.in, 3, row, 0) : 0.f;
+}
+
+template <int ST, bool MU>
+__global__ void __launch_bounds__(BLOCK) step2d_pipe(StepArgs a) {
+    using C = Codec<ST>;
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31;
+    const int wpr = G.nchunk_pad >> 5;
+    const long long nunits = (long long)G.ny * wpr;
+    const long long nwarps = (long long)gridDim.x * (BLOCK / 32);
+    long long u = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    if (u >= nunits) return;  // warp-uniform
+    Raw2 cur;
+    int row = (int)(u / wpr), c = (int)(u - (long long)row * wpr) * 32 + lane;
+    load_raw<ST>(a, row, c, lane, cur);
+    while (true) {
+        const long long un = u + nwarps;
+        const bool more = un < nunits;  // warp-uniform
+        int nrow = 0, nc = 0;
+        Raw2 nxt;
+        if (more) {
+            nrow = (int)(un / wpr);
+            nc = (int)(un - (long long)nrow * wpr) * 32 + lane;
+            load_raw<ST>(a, nrow, nc, lane, nxt);
+        }
+        // finish the pull of the current unit
+        const int x0 = 4 * c;
+        const bool active = c < G.nchunk;
+        float prev = __shfl_up_sync(FULL, cur.a1.w, 1);
+        float next = __shfl_down_sync(FULL, cur.a3.x, 1);
+        if (lane == 0) prev = cur.s1;
+        if (lane == 31 && x0 + 4 < G.nx) next = cur.s3;
+        float4 g[5];
+        g[0] = cur.v0;
+        g[1] = make_float4(prev, cur.a1.x, cur.a1.y, cur.a1.z);
+        g[2] = cur.v2;
+        g[3] = make_float4(cur.a3.y, cur.a3.z, cur.a3.w, next);
+        g[4] = cur.v4;
+        if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, cur.sw);
+        float4 shat = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MU && active) {
+            const float4 dx = __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + (long long)row * G.pitch) + c);
+            const float4 dy =
+                __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + (long long)row * G.pitch) + c);
+            for (int j = 0; j < 4; j++) {
+                const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
+                set(shat, j, bx * get(dy, j) - by * get(dx, j));
+            }
+        }
+        if (a.evt.rowptr) {
+            const int e0 = __ldg(a.evt.rowptr + row), e1 = __ldg(a.evt.rowptr + row + 1);
+            for (int e = e0; e < e1; e++) {
+                const Event ev = a.evt.ev[e];
+                if ((ev.x >> 2) != c || !active) continue;
+                const int j = ev.x & 3;
+                if (ev.kind == 0) {
+                    if (ev.comp == 2 && a.t < a.evt.nt) {
+                        float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
+                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
+                        set(shat, j, get(shat, j) - jz);
+                    }
+                } else if (a.t < a.evt.cap) {
+                    const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
+                    a.evt.traces[(long long)ev.index * a.evt.cap + a.t] =
+                        field2d(ev.comp, get(cur.cl, j), s, get(g[4], j) - get(g[2], j), get(g[1], j) - get(g[3], j));
+                }
+            }
+        }
+        float4 o0, o1, o2, o3, o4;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            Out5 o = collide2d(get(g[0], j), get(g[1], j), get(g[2], j), get(g[3], j), get(g[4], j),
+                               get(cur.cl, j), get(shat, j));
+            set(o0, j, o.o0);
+            set(o1, j, o.o1);
+            set(o2, j, o.o2);
+            set(o3, j, o.o3);
+            set(o4, j, o.o4);
+        }
+        if (active) {
+            C::store4(a.out, 0, row, c, o0);
+            C::store4(a.out, 1, row, c, o1);
+            C::store4(a.out, 2, row, c, o2);
+            C::store4(a.out, 3, row, c, o3);
+            C::store4(a.out, 4, row, c, o4);
+        }
+        if (!more) break;
+        u = un;
+        row = nrow;
+        c = nc;
+        cur = nxt;
+    }
+}
+
+template <int ST, bool MU>
+static cudaError_t launch_pipe(const StepArgs &a, cudaStream_t s) {
+    static int per_sm = 0, nsm = 0;  // resident blocks per SM of this instantiation, SM count
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_pipe<ST, MU>, BLOCK, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long units = (long long)a.g.ny * (a.g.nchunk_pad / 32);
+    long long blocks = (units * 32 + BLOCK - 1) / BLOCK;
+    blocks = blocks < (long long)per_sm * nsm ? blocks : (long long)per_sm * nsm;
+    step2d_pipe<ST, MU><<<(unsigned)blocks, BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ persistent variant with cp.async staging
+// Each lane copies its own unit data (the five population vectors, c_L^2, the
+// halo words of the +-x pulls and, for LBEM_I16B, the exponent words)
+// asynchronously into a private slot of a KS-stage shared-memory ring, KS-1
+// units ahead of the unit it computes.  Only the lane that issued a copy reads
+// it, so a cp.async.wait_group is the only wait (no barrier, no spin).
+constexpr int KS = 3;          // pipeline stages
+constexpr int SLOT = 112;      // bytes per lane and stage
+
+__device__ __forceinline__ void cpa4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cpa8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cpa16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// slot layout: [0,80) five population vectors (16 B each; 8 B used for 16-bit storage),
+// [80,96) c_L^2 float4, [96,100) word holding x0-1 of plane 1, [100,104) word holding x0+4 of plane 3,
+// [104,108) word holding x = 0 of plane 3; LBEM_I16B exponent words in [80,100) reuse is avoided by
+// placing them after: own exponents at [108,112) would not fit five, so I16B keeps its exponent bytes
+// in a second slot array (see ExSlot).
+struct ExSlot {
+    unsigned own[5];      // words holding the chunk exponent of each plane
+    unsigned s1, s3, sw;  // exponent words of the three halo elements
+};
+
+template <int ST>
+__device__ __forceinline__ const char *plane_row(const PopBuf &b, int p, int row) {
+    return static_cast<const char *>(b.data) + (p * b.plane + (long long)row * b.pitch) * Codec<ST>::bytes;
+}
+
+template <int ST>
+__device__ __forceinline__ void issue_unit(const StepArgs &a, int row, int c, int lane, char *slot, ExSlot *ex) {
+    const Grid &G = a.g;
+    if (c >= G.nchunk) return;
+    const int x0 = 4 * c;
+    const int ym = row == 0 ? G.ny - 1 : row - 1, yp = row == G.ny - 1 ? 0 : row + 1;
+    const int rows[5] = {row, row, ym, row, yp};
+    constexpr int VB = 4 * Codec<ST>::bytes;  // bytes of one 4-site vector
+#pragma unroll
+    for (int p = 0; p < 5; p++) {
+        const char *src = plane_row<ST>(a.in, p, rows[p]) + (long long)c * VB;
+        if (VB == 16) cpa16(slot + 16 * p, src);
+        else cpa8(slot + 16 * p, src);
+    }
+    cpa16(slot + 80, a.med.cL2 + (long long)row * G.pitch + x0);
+    constexpr int EB = Codec<ST>::bytes;
+    auto word = [&](int p, int x) {  // the aligned 4-byte word holding element x of plane p, row `row`
+        const int e = (EB == 4) ? x : (x & ~1);
+        return plane_row<ST>(a.in, p, row) + (long long)e * EB;
+    };
+    const int x1 = c == 0 ? G.nx - 1 : x0 - 1;
+    if (lane == 0) cpa4(slot + 96, word(1, x1));
+    if (lane == 31 && x0 + 4 < G.nx) cpa4(slot + 100, word(3, x0 + 4));
+    if (c == G.nchunk - 1) cpa4(slot + 104, word(3, 0));
+    if (ST == LBEM_I16B) {
+        auto exw = [&](int p, int r, int ch) {
+            return reinterpret_cast<const char *>(a.in.ex + p * a.in.explane + (long long)r * a.in.expitch + (ch & ~3));
+        };
+#pragma unroll
+        for (int p = 0; p < 5; p++) cpa4(&ex->own[p], exw(p, rows[p], c));
+        if (lane == 0) cpa4(&ex->s1, exw(1, row, x1 >> 2));
+        if (lane == 31 && x0 + 4 < G.nx) cpa4(&ex->s3, exw(3, row, (x0 + 4) >> 2));
+        if (c == G.nchunk - 1) cpa4(&ex->sw, exw(3, row, 0));
+    }
+}
+
+// decode a 4-site vector / one element staged in shared memory
+template <int ST>
+__device__ __forceinline__ float4 dec4(const PopBuf &b, const char *v, unsigned exword, int c) {
+    if (ST == LBEM_F32) return *reinterpret_cast<const float4 *>(v);
+    const uint2 r = *reinterpret_cast<const uint2 *>(v);
+    if (ST == LBEM_F16) {
+        const float4 f = h4_to_f4(r);
+        return make_float4(f.x * b.inv_scale, f.y * b.inv_scale, f.z * b.inv_scale, f.w * b.inv_scale);
+    }
+    if (ST == LBEM_BF16)
+        return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u), __uint_as_float(r.y << 16),
+                           __uint_as_float(r.y & 0xffff0000u));
+    const int e = (int)(signed char)((exword >> (8 * (c & 3))) & 0xffu);
+    const float f = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
+    return make_float4(i16_to_f((short)(r.x & 0xffffu)) * f, i16_to_f((short)(r.x >> 16)) * f,
+                       i16_to_f((short)(r.y & 0xffffu)) * f, i16_to_f((short)(r.y >> 16)) * f);
+}
+
+template <int ST>
+__device__ __forceinline__ float dec1(const PopBuf &b, unsigned w, int x, unsigned exword) {
+    if (ST == LBEM_F32) return __uint_as_float(w);
+    const unsigned short hbits = (unsigned short)((x & 1) ? (w >> 16) : (w & 0xffffu));
+    if (ST == LBEM_F16) return __half2float(__ushort_as_half(hbits)) * b.inv_scale;
+    if (ST == LBEM_BF16) return __uint_as_float(((unsigned)hbits) << 16);
+    const int e = (int)(signed char)((exword >> (8 * ((x >> 2) & 3))) & 0xffu);
+    return (e == I16B_ZERO) ? 0.f : i16_to_f((short)hbits) * pow2f(e - 15);
+}
+
+template <int ST, bool MU>
+__global__ void __launch_bounds__(BLOCK) step2d_async(StepArgs a) {
+    using C = Codec<ST>;
+    extern __shared__ __align__(16) char smem[];
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int wpr = G.nchunk_pad >> 5;
+    const long long nunits = (long long)G.ny * wpr;
+    const long long nwarps = (long long)gridDim.x * (BLOCK / 32);
+    const long long u0 = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    if (u0 >= nunits) return;  // warp-uniform
+    char *slots = smem + ((size_t)wib * KS * 32 + lane) * SLOT;  // stage k at slots + k * 32 * SLOT
+    ExSlot *exs = reinterpret_cast<ExSlot *>(smem + (size_t)(BLOCK / 32) * KS * 32 * SLOT) + (wib * KS * 32 + lane);
+    auto unit_rc = [&](long long u, int &row, int &c) {
+        row = (int)(u / wpr);
+        c = (int)(u - (long long)row * wpr) * 32 + lane;
+    };
+    // prologue: KS-1 units in flight
+#pragma unroll
+    for (int k = 0; k < KS - 1; k++) {
+        const long long u = u0 + k * nwarps;
+        if (u < nunits) {
+            int row, c;
+            unit_rc(u, row, c);
+            issue_unit<ST>(a, row, c, lane, slots + (size_t)k * 32 * SLOT, exs + k * 32);
+        }
+        cpa_commit();
+    }
+    for (long long k = 0;; k++) {
+        const long long u = u0 + k * nwarps;
+        if (u >= nunits) break;  // warp-uniform
+        {
+            const long long un = u + (KS - 1) * nwarps;
+            const int sn = (int)((k + KS - 1) % KS);
+            if (un < nunits) {
+                int row, c;
+                unit_rc(un, row, c);
+                issue_unit<ST>(a, row, c, lane, slots + (size_t)sn * 32 * SLOT, exs + sn * 32);
+            }
+            cpa_commit();
+        }
+        cpa_wait<KS - 1>();  // this lane's copies of unit k are complete
+        const int sk = (int)(k % KS);
+        const char *sl = slots + (size_t)sk * 32 * SLOT;
+        const ExSlot &ex = exs[sk * 32];
+        int row, c;
+        unit_rc(u, row, c);
+        const bool active = c < G.nchunk;
+        const int x0 = 4 * c;
+        float4 g[5];
+        float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a3 = a1, cl = a1;
+        if (active) {
+            g[0] = dec4<ST>(a.in, sl + 0, ST == LBEM_I16B ? ex.own[0] : 0u, c);
+            a1 = dec4<ST>(a.in, sl + 16, ST == LBEM_I16B ? ex.own[1] : 0u, c);
+            g[2] = dec4<ST>(a.in, sl + 32, ST == LBEM_I16B ? ex.own[2] : 0u, c);
+            a3 = dec4<ST>(a.in, sl + 48, ST == LBEM_I16B ? ex.own[3] : 0u, c);
+            g[4] = dec4<ST>(a.in, sl + 64, ST == LBEM_I16B ? ex.own[4] : 0u, c);
+            cl = *reinterpret_cast<const float4 *>(sl + 80);
+        } else {
+            g[0] = g[2] = g[4] = a1;
+        }
+        float prev = __shfl_up_sync(FULL, a1.w, 1);
+        float next = __shfl_down_sync(FULL, a3.x, 1);
+        if (lane == 0 && active)
+            prev = dec1<ST>(a.in, *reinterpret_cast<const unsigned *>(sl + 96), c == 0 ? G.nx - 1 : x0 - 1, ex.s1);
+        if (lane == 31 && x0 + 4 < G.nx) next = dec1<ST>(a.in, *reinterpret_cast<const unsigned *>(sl + 100), x0 + 4, ex.s3);
+        g[1] = make_float4(prev, a1.x, a1.y, a1.z);
+        g[3] = make_float4(a3.y, a3.z, a3.w, next);
+        if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, dec1<ST>(a.in, *reinterpret_cast<const unsigned *>(sl + 104), 0, ex.sw));
+        float4 shat = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MU && active) {
+            const float4 dx = __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + (long long)row * G.pitch) + c);
+            const float4 dy =
+                __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + (long long)row * G.pitch) + c);
+            for (int j = 0; j < 4; j++) {
+                const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
+                set(shat, j, bx * get(dy, j) - by * get(dx, j));
+            }
+        }
+        if (a.evt.rowptr) {
+            const int e0 = __ldg(a.evt.rowptr + row), e1 = __ldg(a.evt.rowptr + row + 1);
+            for (int e = e0; e < e1; e++) {
+                const Event ev = a.evt.ev[e];
+                if ((ev.x >> 2) != c || !active) continue;
+                const int j = ev.x & 3;
+                if (ev.kind == 0) {
+                    if (ev.comp == 2 && a.t < a.evt.nt) {
+                        float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
+                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
+                        set(shat, j, get(shat, j) - jz);
+                    }
+                } else if (a.t < a.evt.cap) {
+                    const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
+                    a.evt.traces[(long long)ev.index * a.evt.cap + a.t] =
+                        field2d(ev.comp, get(cl, j), s, get(g[4], j) - get(g[2], j), get(g[1], j) - get(g[3], j));
+                }
+            }
+        }
+        float4 o0, o1, o2, o3, o4;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            Out5 o = collide2d(get(g[0], j), get(g[1], j), get(g[2], j), get(g[3], j), get(g[4], j), get(cl, j),
+                               get(shat, j));
+            set(o0, j, o.o0);
+            set(o1, j, o.o1);
+            set(o2, j, o.o2);
+            set(o3, j, o.o3);
+            set(o4, j, o.o4);
+        }
+        if (active) {
+            C::store4(a.out, 0, row, c, o0);
+            C::store4(a.out, 1, row, c, o1);
+            C::store4(a.out, 2, row, c, o2);
+            C::store4(a.out, 3, row, c, o3);
+            C::store4(a.out, 4, row, c, o4);
+        }
+    }
+    cpa_wait<0>();  // nothing may stay in flight into a slot when the block exits
+}
+
+template <int ST, bool MU>
+static cudaError_t launch_async(const StepArgs &a, cudaStream_t s) {
+    static int per_sm = 0, nsm = 0;
+    const size_t smem = (size_t)(BLOCK / 32) * KS * 32 * (SLOT + sizeof(ExSlot));
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaFuncSetAttribute(step2d_async<ST, MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_async<ST, MU>, BLOCK, smem);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long units = (long long)a.g.ny * (a.g.nchunk_pad / 32);
+    long long blocks = (units * 32 + BLOCK - 1) / BLOCK;
+    blocks = blocks < (long long)per_sm * nsm ? blocks : (long long)per_sm * nsm;
+    step2d_async<ST, MU><<<(unsigned)blocks, BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ 16-bit storage, 8 sites per lane
+// One 16-byte load per population and lane (eight 16-bit values), so a warp
+// request is 512 bytes as in the FP32 kernel; a warp covers 256 sites.
+struct F8 {
+    float v[8];
+};
+
+template <int ST>
+__device__ __forceinline__ F8 load8(const PopBuf &b, int p, int row, int c8) {
+    F8 f;
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(static_cast<const char *>(b.data) +
+                                                         (p * b.plane + (long long)row * b.pitch) * 2) + c8);
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+    if (ST == LBEM_F16) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+            f.v[2 * k] = t.x * b.inv_scale;
+            f.v[2 * k + 1] = t.y * b.inv_scale;
+        }
+    } else if (ST == LBEM_BF16) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            f.v[2 * k] = __uint_as_float(w[k] << 16);
+            f.v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    } else {
+        const unsigned short e2 = __ldg(reinterpret_cast<const unsigned short *>(b.ex + p * b.explane +
+                                                                                 (long long)row * b.expitch) + c8);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int e = (int)(signed char)((e2 >> (8 * (k >> 1))) & 0xffu);
+            const float sc = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
+            f.v[2 * k] = i16_to_f((short)(w[k] & 0xffffu)) * sc;
+            f.v[2 * k + 1] = i16_to_f((short)(w[k] >> 16)) * sc;
+        }
+    }
+    return f;
+}
+
+template <int ST>
+__device__ __forceinline__ void store8(const PopBuf &b, int p, int row, int c8, const F8 &f) {
+    using C = Codec<ST>;
+    // each 4-site half is encoded exactly as the 4-site codec encodes it; one 16-byte store per lane
+    const float4 lo = make_float4(f.v[0], f.v[1], f.v[2], f.v[3]), hi = make_float4(f.v[4], f.v[5], f.v[6], f.v[7]);
+    uint2 r0, r1;
+    unsigned short e2 = 0;
+    if (ST == LBEM_I16B) {
+        const int e0 = Codec<LBEM_I16B>::enc4e(lo, r0), e1 = Codec<LBEM_I16B>::enc4e(hi, r1);
+        e2 = (unsigned short)((unsigned)(e0 & 0xff) | ((unsigned)(e1 & 0xff) << 8));
+    } else if (ST == LBEM_F16) {
+        r0 = Codec<LBEM_F16>::enc4(b, lo);
+        r1 = Codec<LBEM_F16>::enc4(b, hi);
+    } else {
+        r0 = Codec<LBEM_BF16>::enc4(b, lo);
+        r1 = Codec<LBEM_BF16>::enc4(b, hi);
+    }
+    uint4 *q = reinterpret_cast<uint4 *>(static_cast<char *>(b.data) + (p * b.plane + (long long)row * b.pitch) * 2);
+    __stcs(q + c8, make_uint4(r0.x, r0.y, r1.x, r1.y));
+    if (ST == LBEM_I16B)
+        reinterpret_cast<unsigned short *>(b.ex + p * b.explane + (long long)row * b.expitch)[c8] = e2;
+    (void)sizeof(C);
+}
+
+template <int ST, bool MU>
+__global__ void __launch_bounds__(BLOCK) step2d_w8(StepArgs a) {
+    using C = Codec<ST>;
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31;
+    const int n8 = (G.nx + 7) / 8, n8p = (n8 + 31) / 32 * 32;
+    const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    const int wpr = n8p >> 5;
+    const int row = (int)(wg / wpr);
+    const int c8 = (int)(wg - (long long)row * wpr) * 32 + lane;
+    if (row >= G.ny) return;
+    const bool active = c8 < n8 && 8 * c8 < G.nx;
+    const int x0 = 8 * c8;
+    const int ym = row == 0 ? G.ny - 1 : row - 1, yp = row == G.ny - 1 ? 0 : row + 1;
+    F8 g0{}, a1{}, g2{}, a3{}, g4{};
+    if (active) {
+        g0 = load8<ST>(a.in, 0, row, c8);
+        a1 = load8<ST>(a.in, 1, row, c8);
+        g2 = load8<ST>(a.in, 2, ym, c8);
+        a3 = load8<ST>(a.in, 3, row, c8);
+        g4 = load8<ST>(a.in, 4, yp, c8);
+    }
+    float prev = __shfl_up_sync(FULL, a1.v[7], 1);
+    float next = __shfl_down_sync(FULL, a3.v[0], 1);
+    if (lane == 0 && active) prev = C::load1(a.in, 1, row, c8 == 0 ? G.nx - 1 : x0 - 1);
+    if (lane == 31 && x0 + 8 < G.nx) next = C::load1(a.in, 3, row, x0 + 8);
+    if (!active) return;
+    F8 g1, g3;
+    g1.v[0] = prev;
+#pragma unroll
+    for (int k = 1; k < 8; k++) g1.v[k] = a1.v[k - 1];
+#pragma unroll
+    for (int k = 0; k < 7; k++) g3.v[k] = a3.v[k + 1];
+    g3.v[7] = next;
+    if (x0 + 8 >= G.nx) {  // periodic wrap at x = nx-1 inside this lane's 8 sites
+        const float w = C::load1(a.in, 3, row, 0);
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (x0 + k == G.nx - 1) g3.v[k] = w;
+    }
+    const float4 cA = __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + 2 * c8);
+    const float4 cB = __ldg(reinterpret_cast<const float4 *>(a.med.cL2 + (long long)row * G.pitch) + 2 * c8 + 1);
+    const float cl[8] = {cA.x, cA.y, cA.z, cA.w, cB.x, cB.y, cB.z, cB.w};
+    float shat[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) shat[k] = 0.f;
+    if (MU) {
+        const float *dxr = a.med.dlnmu + (long long)row * G.pitch, *dyr = a.med.dlnmu + G.plane + (long long)row * G.pitch;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const float bx = g4.v[k] - g2.v[k], by = g1.v[k] - g3.v[k];
+            shat[k] = bx * __ldg(dyr + x0 + k) - by * __ldg(dxr + x0 + k);
+        }
+    }
+    if (a.evt.rowptr) {
+        const int e0 = __ldg(a.evt.rowptr + row), e1 = __ldg(a.evt.rowptr + row + 1);
+        for (int e = e0; e < e1; e++) {
+            const Event ev = a.evt.ev[e];
+            if ((ev.x >> 3) != c8) continue;
+            const int j = ev.x & 7;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (k != j) continue;
+                if (ev.kind == 0) {
+                    if (ev.comp == 2 && a.t < a.evt.nt) {
+                        float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
+                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
+                        shat[k] -= jz;
+                    }
+                } else if (a.t < a.evt.cap) {
+                    const float sg = ((g0.v[k] + g1.v[k]) + (g2.v[k] + g3.v[k])) + g4.v[k];
+                    a.evt.traces[(long long)ev.index * a.evt.cap + a.t] =
+                        field2d(ev.comp, cl[k], sg, g4.v[k] - g2.v[k], g1.v[k] - g3.v[k]);
+                }
+            }
+        }
+    }
+    F8 o0, o1, o2, o3, o4;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const Out5 o = collide2d(g0.v[k], g1.v[k], g2.v[k], g3.v[k], g4.v[k], cl[k], shat[k]);
+        o0.v[k] = o.o0;
+        o1.v[k] = o.o1;
+        o2.v[k] = o.o2;
+        o3.v[k] = o.o3;
+        o4.v[k] = o.o4;
+    }
+    store8<ST>(a.out, 0, row, c8, o0);
+    store8<ST>(a.out, 1, row, c8, o1);
+    store8<ST>(a.out, 2, row, c8, o2);
+    store8<ST>(a.out, 3, row, c8, o3);
+    store8<ST>(a.out, 4, row, c8, o4);
+}
+
+template <int ST, bool MU>
+static cudaError_t launch_w8(const StepArgs &a, cudaStream_t s) {
+    const int n8 = (a.g.nx + 7) / 8, n8p = (n8 + 31) / 32 * 32;
+    const long long warps = (long long)a.g.ny * (n8p / 32);
+    step2d_w8<ST, MU><<<(unsigned)((warps * 32 + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 static const int kRows2d[] = {1, 2, 4};
-int nvariants_2d() { return 3; }
+// rows per warp 1, 2, 4; 3 = persistent pipelined; 4 = cp.async staged; 5 = 8 sites per lane (16-bit storage)
+int nvariants_2d() { return 6; }
 
 template <int ST, bool MU>
 static cudaError_t launch_st(const StepArgs &a, int variant, cudaStream_t s) {
+    if (variant == 3) return launch_pipe<ST, MU>(a, s);
+    if (variant == 4) return launch_async<ST, MU>(a, s);
+    if (variant == 5) {
+        if (ST == LBEM_F32) variant = 0;  // FP32 already issues 16-byte loads with 4 sites per lane
+        else return launch_w8<ST, MU>(a, s);
+    }
     const int R = kRows2d[variant];
     const long long warps = (long long)((a.g.ny + R - 1) / R) * (a.g.nchunk_pad / 32);
     const long long blocks = (warps * 32 + BLOCK - 1) / BLOCK;

@@ -83,14 +83,17 @@ struct Codec<LBEM_F16> {
         const __half *q = static_cast<const __half *>(b.data) + p * b.plane + (long long)row * b.pitch + x;
         return __half2float(__ldg(q)) * b.inv_scale;
     }
-    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+    __device__ static __forceinline__ uint2 enc4(const PopBuf &b, float4 v) {
         __half2 a = __floats2half2_rn(v.x * b.scale, v.y * b.scale);
         __half2 d = __floats2half2_rn(v.z * b.scale, v.w * b.scale);
         uint2 r;
         r.x = *reinterpret_cast<unsigned *>(&a);
         r.y = *reinterpret_cast<unsigned *>(&d);
+        return r;
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
         uint2 *q = reinterpret_cast<uint2 *>(static_cast<__half *>(b.data) + p * b.plane + (long long)row * b.pitch);
-        __stcs(q + c, r);
+        __stcs(q + c, enc4(b, v));
     }
 };
 
@@ -110,15 +113,19 @@ struct Codec<LBEM_BF16> {
             static_cast<const __nv_bfloat16 *>(b.data) + p * b.plane + (long long)row * b.pitch + x);
         return __uint_as_float(((unsigned)__ldg(q)) << 16);
     }
-    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+    __device__ static __forceinline__ uint2 enc4(const PopBuf &b, float4 v) {
+        (void)b;
         __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
         __nv_bfloat162 d = __floats2bfloat162_rn(v.z, v.w);
         uint2 r;
         r.x = *reinterpret_cast<unsigned *>(&a);
         r.y = *reinterpret_cast<unsigned *>(&d);
+        return r;
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
         uint2 *q = reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(b.data) + p * b.plane +
                                              (long long)row * b.pitch);
-        __stcs(q + c, r);
+        __stcs(q + c, enc4(b, v));
     }
 };
 
@@ -133,6 +140,15 @@ __device__ __forceinline__ float pow2f(int k) {  // 2^k for -126 <= k <= 127
     return __int_as_float((k + 127) << 23);
 }
 
+// Exact int16 <-> float conversions on the FP32 adder instead of the reduced-rate
+// conversion unit: for |q| < 2^22 the float 1.5*2^23 + q has q in its low mantissa
+// bits, and adding 1.5*2^23 to a float of magnitude < 2^22 rounds it to the nearest
+// integer (ties to even), exactly as __float2int_rn does.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+__device__ __forceinline__ float i16_to_f(int q) { return __int_as_float(kMagicBits + q) - kMagic; }
+__device__ __forceinline__ int f_to_int_rn(float v) { return __float_as_int(v + kMagic) - kMagicBits; }
+
 template <>
 struct Codec<LBEM_I16B> {
     static constexpr int bytes = 2;
@@ -142,18 +158,18 @@ struct Codec<LBEM_I16B> {
         uint2 r = __ldg(q + c);
         int e = __ldg(b.ex + p * b.explane + (long long)row * b.expitch + c);
         float f = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
-        return make_float4((float)(short)(r.x & 0xffffu) * f, (float)(short)(r.x >> 16) * f,
-                           (float)(short)(r.y & 0xffffu) * f, (float)(short)(r.y >> 16) * f);
+        return make_float4(i16_to_f((short)(r.x & 0xffffu)) * f, i16_to_f((short)(r.x >> 16)) * f,
+                           i16_to_f((short)(r.y & 0xffffu)) * f, i16_to_f((short)(r.y >> 16)) * f);
     }
     __device__ static __forceinline__ float load1(const PopBuf &b, int p, int row, int x) {
         short v = __ldg(static_cast<const short *>(b.data) + p * b.plane + (long long)row * b.pitch + x);
         int e = __ldg(b.ex + p * b.explane + (long long)row * b.expitch + (x >> 2));
-        return (e == I16B_ZERO) ? 0.f : (float)v * pow2f(e - 15);
+        return (e == I16B_ZERO) ? 0.f : i16_to_f(v) * pow2f(e - 15);
     }
-    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+    // encoded 4-site block: mantissas in r, exponent returned
+    __device__ static __forceinline__ int enc4e(float4 v, uint2 &r) {
         float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
         int e;
-        uint2 r;
         if (!(m < 0x1p+100f)) {  // huge or NaN: saturate, so the state stays visibly wrong
             e = 127;
             r.x = r.y = 0x7fff7fffu;
@@ -163,13 +179,19 @@ struct Codec<LBEM_I16B> {
         } else {
             e = ((__float_as_int(m) >> 23) & 0xff) - 127 + 1;
             float s = pow2f(15 - e);
-            int q0 = max(-32767, min(32767, __float2int_rn(v.x * s)));
-            int q1 = max(-32767, min(32767, __float2int_rn(v.y * s)));
-            int q2 = max(-32767, min(32767, __float2int_rn(v.z * s)));
-            int q3 = max(-32767, min(32767, __float2int_rn(v.w * s)));
+            // |v * s| < 2^15 here, so the adder-based rounding is exact
+            int q0 = max(-32767, min(32767, f_to_int_rn(v.x * s)));
+            int q1 = max(-32767, min(32767, f_to_int_rn(v.y * s)));
+            int q2 = max(-32767, min(32767, f_to_int_rn(v.z * s)));
+            int q3 = max(-32767, min(32767, f_to_int_rn(v.w * s)));
             r.x = (unsigned)(q0 & 0xffff) | ((unsigned)(q1 & 0xffff) << 16);
             r.y = (unsigned)(q2 & 0xffff) | ((unsigned)(q3 & 0xffff) << 16);
         }
+        return e;
+    }
+    __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
+        uint2 r;
+        const int e = enc4e(v, r);
         uint2 *q = reinterpret_cast<uint2 *>(static_cast<int16_t *>(b.data) + p * b.plane + (long long)row * b.pitch);
         __stcs(q + c, r);
         b.ex[p * b.explane + (long long)row * b.expitch + c] = (int8_t)e;
