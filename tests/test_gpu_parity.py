@@ -257,3 +257,26 @@ def test_homogeneous_invariant_conserved_full_size(lbem):
     d1 = s.diagnostics()
     s.close()
     assert abs(d1[1] - d0[1]) < 1e-5 * d0[1], (d0, d1)
+
+
+def test_storage_forms_5000_steps_on_512_crop_of_4096_medium(lbem):
+    """The 4096^2 (seed 2) medium's central 512^2 crop run in FP64 (oracle) and on the GPU in every storage
+    form for 5000 steps, Ricker source at the crop centre.  FP32 must meet 1e-4; each 16-bit form must stay
+    within its rounding-walk bound 2 u sqrt(N/3); block-int16 must meet the reduced-precision bar 1e-3."""
+    big = W.heterogeneous_2d(4096, seed=2, nsteps=5000)
+    c0 = 2048 - 256
+    eps = big.eps_r[c0:c0 + 512, c0:c0 + 512].copy()
+    n_idx = np.sqrt(eps)
+    recs = W.circle_receivers((256, 256), 128, 64)
+    p = W.point_source_problem(2, (512, 512), n_idx, 5000, (256, 256), 64, recs, name="crop512")
+    oE, oB, otr, _, _ = oracle_run(p)
+    u = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8, "i16b": 2.0 ** -15}
+    report = {}
+    for st in ("f32", "f16", "bf16", "i16b"):
+        E, B, tr = gpu_run(p, st)
+        report[st] = (rel(E, oE), rel(B, oB), rel(tr, otr))
+    print("512^2 crop x 5000 rel-L2 (E, B, traces):", {k: tuple(f"{x:.2e}" for x in v) for k, v in report.items()})
+    assert max(report["f32"]) < 1e-4, report["f32"]
+    for st in ("f16", "bf16"):
+        assert max(report[st]) < 2 * u[st] * np.sqrt(5000 / 3), (st, report[st])
+    assert max(report["i16b"][:2]) < 1e-3, report["i16b"]
