@@ -93,7 +93,57 @@ def workload(name):
         return W.heterogeneous_2d(4096, seed=2, nsteps=5000)
     if name == "het2d_1024":
         return W.heterogeneous_2d(1024, seed=1, nsteps=5000)
+    if name == "het3d_192":
+        return W.heterogeneous_3d(192, seed=4, nsteps=1000)
     raise ValueError(name)
+
+
+def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
+    """The 256-media batch as the timed workload (used to profile the batched kernel on its own)."""
+    probs = W.batch_2d(256, nsteps=args.lb_steps or 2000)
+    nsteps = probs[0].nsteps
+    ss = []
+    for q in probs:
+        s = lbem.Solver(q.shape, stream=stream.cuda_stream)
+        s.set_problem(q)
+        ss.append(s)
+    b = lbem.lbem_batch_create([s.h for s in ss], stream.cuda_stream)
+    v = lbem.lbem_batch_autotune(b, 20) if args.autotune else lbem.lbem_batch_get_variant(b)[0]
+    if args.variant is not None:
+        lbem.lbem_batch_set_variant(b, args.variant)
+        v = args.variant
+    for _ in range(args.warmup):
+        for s in ss:
+            lbem.lbem_set_fields(s.h)
+        lbem.lbem_batch_step(b, nsteps)
+    torch.cuda.synchronize()
+    evs = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            for s in ss:
+                lbem.lbem_set_fields(s.h)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lbem.lbem_batch_step(b, nsteps)
+            e.record(stream)
+            evs.append((a, e))
+        torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(e) for a, e in evs]))
+    sites = sum(int(np.prod(q.shape)) for q in probs)
+    lbem.lbem_batch_destroy(b)
+    for s in ss:
+        s.close()
+    per = ms / nsteps
+    gbs = 44 * sites / (per * 1e-3) / 1e9
+    value = sites * nsteps / (ms * 1e-3) / 1e6
+    print(json.dumps({"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batch256", "media": len(probs), "sites": sites, "lb_steps": nsteps},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "traffic": None, "kernel": f"step2d_batch (variant {v})",
+                                   "ms_per_launch": per, "peak_kind": peak_kind},
+                      "gpu_launches": args.steps * nsteps, "clocks": clk.summary()}), flush=True)
 
 
 def _time_run(lbem, torch, s, p, nsteps, stream, passes=1):
@@ -171,12 +221,14 @@ def cpu_baseline(p, budget_s=12.0):
     source, as many steps as fit in about budget_s seconds of CPU work."""
     import oracle as O
 
-    n = min(1024, p.shape[0])
+    n = min(1024 if p.D == 2 else 64, p.shape[0])
     c0 = (p.shape[0] - n) // 2
-    eps = np.asarray(p.eps_r[c0:c0 + n, c0:c0 + n], np.float32).astype(np.float64)
-    m = O.medium(2, eps)
+    crop = tuple(slice(c0, c0 + n) for _ in range(p.D))
+    eps = np.asarray(p.eps_r[crop], np.float32).astype(np.float64)
+    m = O.medium(p.D, eps)
     g = O.init_state(m)
-    src = dict(site=np.array([W.flat_index((n, n), (n // 2, n // 2))]), comp=np.array([2]),
+    shape = (n,) * p.D
+    src = dict(site=np.array([W.flat_index(shape, (n // 2,) * p.D)]), comp=np.array([2]),
                amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
     t0 = time.perf_counter()
     O.run(m, g, 10, sources=src)
@@ -185,8 +237,8 @@ def cpu_baseline(p, budget_s=12.0):
     t0 = time.perf_counter()
     O.run(m, g, steps, t0=10, sources=src)
     dt = time.perf_counter() - t0
-    return {"value": n * n * steps / dt / 1e6, "unit": "Mlups", "cores": O.threads(), "kind": "oracle",
-            "sample": f"FP64 oracle, {n}x{n} crop of the workload's medium, point source, {steps} steps "
+    return {"value": n ** p.D * steps / dt / 1e6, "unit": "Mlups", "cores": O.threads(), "kind": "oracle",
+            "sample": f"FP64 oracle, {n}^{p.D} crop of the workload's medium, point source, {steps} steps "
                       f"({dt:.1f} s)"}
 
 
@@ -260,13 +312,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
-    ap.add_argument("--workload", default="het2d_4096")
+    ap.add_argument("--workload", default="het2d_4096", choices=["het2d_4096", "het2d_1024", "het3d_192", "batch256"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
     ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
     ap.add_argument("--ref-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="force a launch shape of the stream-collide kernel")
     ap.add_argument("--no-forms", action="store_true", help="skip the 16-bit, batched and 3D forms")
     args = ap.parse_args()
     rank, world = dist_setup(args)
@@ -281,7 +334,14 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     lbem.load()
+    if args.workload == "batch256":
+        peak, peak_kind = measured_peak_gbs()
+        run_batch_main(args, lbem, torch, torch.cuda.Stream(), peak, peak_kind)
+        return
     p = workload(args.workload)
+    if p.D == 3:
+        args.storage = "f32"
+        args.no_forms = True
     if args.lb_steps:
         p.nsteps = args.lb_steps
         p.src_amp = p.src_amp[:, : p.nsteps]
@@ -291,13 +351,17 @@ def main():
     with torch.cuda.stream(stream):
         s = lbem.Solver(p.shape, storage=args.storage, stream=stream.cuda_stream)
     h = s.h
+    state_mb = lbem.lbem_info(h)[1] / 1e6
     lbem.lbem_set_medium(h, eps_d)
     lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
     lbem.lbem_set_receivers(h, p.rec_site, p.rec_comp, nsteps)
-    variant = 0
+    variant = lbem.lbem_get_variant(h)[0]
     if args.autotune:
         lbem.lbem_set_fields(h)
         variant = lbem.lbem_autotune(h, 50)
+    if args.variant is not None:
+        lbem.lbem_set_variant(h, args.variant)
+        variant = args.variant
     nsite = s.nsite
     E_d = torch.empty(3 * nsite, dtype=torch.float32, device="cuda")
     B_d = torch.empty_like(E_d)
@@ -337,10 +401,11 @@ def main():
     value = world * nsite * nsteps / (ms_per_step * 1e-3) / 1e6
 
     peak, peak_kind = measured_peak_gbs()
-    bps = BYTES_PER_SITE[args.storage]
+    bps = BYTES_PER_SITE[args.storage] if p.D == 2 else 172
     achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
+    kname = f"step2d<{args.storage}>" if p.D == 2 else "step3d"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"step2d<{args.storage}> (variant {variant})",
+                "traffic": None, "kernel": f"{kname} (variant {variant})",
                 "algorithmic_bytes_per_site": bps, "ms_per_launch": ms_per_launch, "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -382,7 +447,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": p.name, "grid": list(p.shape), "lb_steps": nsteps, "storage": args.storage,
                            "sources": int(p.src_site.size), "receivers": int(p.rec_site.size),
-                           "l2": "inputs larger than L2 (2 x 336 MB distributions), no flush",
+                           "l2": f"inputs larger than L2 (2 x {state_mb:.0f} MB distributions), no flush",
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "diagnostics_last": list(diag), "forms": forms}

@@ -224,6 +224,9 @@ lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);
 lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out);
 lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps);
 lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best);
+/* Choose the batched kernel's launch shape directly (0 <= variant < *nvariants of lbem_batch_get_variant). */
+lbem_status lbem_batch_set_variant(lbem_batch_t *b, int variant);
+lbem_status lbem_batch_get_variant(const lbem_batch_t *b, int *variant, int *nvariants);
 void lbem_batch_destroy(lbem_batch_t *b);
 
 #ifdef __cplusplus

@@ -45,19 +45,15 @@ __device__ __forceinline__ void pull_f32(const PopBuf &in, const Grid &G, int ro
     if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, C::load1(in, 3, row, 0));
 }
 
-template <int R>
-__global__ void __launch_bounds__(BLOCK) step2d_batch(const Member *__restrict__ M, const long long *__restrict__ wstart,
-                                                      int n, const long long *__restrict__ t0p, int offset) {
+template <int R, int MINB = 1>
+__global__ void __launch_bounds__(BLOCK, MINB) step2d_batch(const Member *__restrict__ M, const long long *__restrict__ wstart,
+                                                      const int *__restrict__ wmember, long long nwarps,
+                                                      const long long *__restrict__ t0p, int offset) {
     using C = Codec<LBEM_F32>;
     const int lane = threadIdx.x & 31;
     const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
-    if (wg >= wstart[n]) return;
-    int lo = 0, hi = n - 1;  // member b with wstart[b] <= wg < wstart[b+1]
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(wstart + mid) <= wg) lo = mid;
-        else hi = mid - 1;
-    }
+    if (wg >= nwarps) return;
+    const int lo = __ldg(wmember + wg);  // member of this warp
     const Member &m = M[lo];
     const Grid &G = m.g;
     const long long lw = wg - wstart[lo];
@@ -122,6 +118,189 @@ __global__ void __launch_bounds__(BLOCK) step2d_batch(const Member *__restrict__
     }
 }
 
+// Flattened mapping: one site per thread, sites of a member numbered x + nx*y
+// and cut into blocks of BLOCK consecutive sites (a block never spans two
+// members), so no lane idles except in a member's last block.
+__global__ void __launch_bounds__(BLOCK) step2d_batch_site(const Member *__restrict__ M, const int *__restrict__ bmember,
+                                                           const long long *__restrict__ bstart,
+                                                           const long long *__restrict__ t0p, int offset) {
+    const int mi = __ldg(bmember + blockIdx.x);
+    const Member &m = M[mi];
+    const Grid &G = m.g;
+    const long long s = (long long)(blockIdx.x - bstart[mi]) * BLOCK + threadIdx.x;
+    if (s >= (long long)G.nx * G.ny) return;
+    const int row = (int)(s / G.nx), x = (int)(s - (long long)row * G.nx);
+    const int xm = x == 0 ? G.nx - 1 : x - 1, xp = x == G.nx - 1 ? 0 : x + 1;
+    const int ym = row == 0 ? G.ny - 1 : row - 1, yp = row == G.ny - 1 ? 0 : row + 1;
+    const PopBuf &in = (offset & 1) ? m.b : m.a;
+    const PopBuf &out = (offset & 1) ? m.a : m.b;
+    const float *ip = static_cast<const float *>(in.data);
+    const long long P = G.plane, W = G.pitch;
+    const float g0 = __ldg(ip + (long long)row * W + x);
+    const float g1 = __ldg(ip + P + (long long)row * W + xm);
+    const float g2 = __ldg(ip + 2 * P + (long long)ym * W + x);
+    const float g3 = __ldg(ip + 3 * P + (long long)row * W + xp);
+    const float g4 = __ldg(ip + 4 * P + (long long)yp * W + x);
+    const float q = __ldg(m.med.cL2 + (long long)row * W + x);
+    const long long t = *t0p + offset;
+    float sh = 0.f;
+    if (m.evt.rowptr) {
+        const int e0 = __ldg(m.evt.rowptr + row), e1 = __ldg(m.evt.rowptr + row + 1);
+        for (int e = e0; e < e1; e++) {
+            const Event ev = m.evt.ev[e];
+            if (ev.x != x) continue;
+            if (ev.kind == 0) {
+                if (ev.comp == 2 && t < m.evt.nt) sh -= __ldg(m.evt.amp + (long long)ev.index * m.evt.nt + t);
+            } else if (t < m.evt.cap) {
+                const float sg = ((g0 + g1) + (g2 + g3)) + g4;
+                float v = 0.f;
+                if (ev.comp == 2) v = -q * sg;
+                else if (ev.comp == 3) v = g4 - g2;
+                else if (ev.comp == 4) v = g1 - g3;
+                m.evt.traces[(long long)ev.index * m.evt.cap + t] = v;
+            }
+        }
+    }
+    const float sg = ((g0 + g1) + (g2 + g3)) + g4;
+    const float L = q * sg, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
+    float *op = static_cast<float *>(out.data) + (long long)row * W + x;
+    __stcs(op, (2.f * w0 * sg - g0) + T0);
+    __stcs(op + P, (L - g3) + Tm);
+    __stcs(op + 2 * P, (L - g4) + Tm);
+    __stcs(op + 3 * P, (L - g1) + Tm);
+    __stcs(op + 4 * P, (L - g2) + Tm);
+}
+
+// Persistent row mapping: warp w walks the contiguous units [w*k, (w+1)*k) of the
+// flattened table (nearly always one member), keeps that member's descriptor in
+// registers, and issues the loads of its next unit before it computes the current one.
+struct RawB {
+    float4 v0, a1, v2, a3, v4, cl;
+    float s1, s3, sw;
+};
+
+__device__ __forceinline__ void batch_raw(const Member &m, const PopBuf &in, int row, int c, int lane, RawB &r) {
+    using C = Codec<LBEM_F32>;
+    const Grid &G = m.g;
+    const bool active = c < G.nchunk;
+    const int x0 = 4 * c;
+    const int ym = row == 0 ? G.ny - 1 : row - 1, yp = row == G.ny - 1 ? 0 : row + 1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.v0 = active ? C::load4(in, 0, row, c) : z4;
+    r.a1 = active ? C::load4(in, 1, row, c) : z4;
+    r.v2 = active ? C::load4(in, 2, ym, c) : z4;
+    r.a3 = active ? C::load4(in, 3, row, c) : z4;
+    r.v4 = active ? C::load4(in, 4, yp, c) : z4;
+    r.cl = active ? __ldg(reinterpret_cast<const float4 *>(m.med.cL2 + (long long)row * G.pitch) + c) : z4;
+    r.s1 = (lane == 0 && active) ? C::load1(in, 1, row, c == 0 ? G.nx - 1 : x0 - 1) : 0.f;
+    r.s3 = (lane == 31 && x0 + 4 < G.nx) ? C::load1(in, 3, row, x0 + 4) : 0.f;
+    r.sw = (c == G.nchunk - 1) ? C::load1(in, 3, row, 0) : 0.f;
+}
+
+__global__ void __launch_bounds__(BLOCK) step2d_batch_pipe(const Member *__restrict__ M, const long long *__restrict__ wstart,
+                                                           const int *__restrict__ wmember, long long nunits,
+                                                           long long per_warp, const long long *__restrict__ t0p,
+                                                           int offset) {
+    using C = Codec<LBEM_F32>;
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    long long u = w * per_warp;
+    const long long uend = min(nunits, u + per_warp);
+    if (u >= uend) return;  // warp-uniform
+    const long long t = *t0p + offset;
+    int mi = __ldg(wmember + u);
+    const Member *mp = M + mi;
+    long long ubase = __ldg(wstart + mi);
+    auto rc = [&](const Member &mm, long long uu, long long base, int &row, int &c) {
+        const int wpr = mm.g.nchunk_pad >> 5;
+        const long long lu = uu - base;
+        row = (int)(lu / wpr);
+        c = (int)(lu - (long long)row * wpr) * 32 + lane;
+    };
+    int row, c;
+    rc(*mp, u, ubase, row, c);
+    RawB cur;
+    batch_raw(*mp, (offset & 1) ? mp->b : mp->a, row, c, lane, cur);
+    while (true) {
+        const long long un = u + 1;
+        const bool more = un < uend;
+        int nmi = mi, nrow = 0, nc = 0;
+        const Member *nmp = mp;
+        long long nbase = ubase;
+        RawB nxt;
+        if (more) {
+            nmi = __ldg(wmember + un);
+            if (nmi != mi) {  // warp-uniform: the next unit starts a new member
+                nmp = M + nmi;
+                nbase = __ldg(wstart + nmi);
+            }
+            rc(*nmp, un, nbase, nrow, nc);
+            batch_raw(*nmp, (offset & 1) ? nmp->b : nmp->a, nrow, nc, lane, nxt);
+        }
+        const Member &m = *mp;
+        const Grid &G = m.g;
+        const bool active = c < G.nchunk;
+        const int x0 = 4 * c;
+        float prev = __shfl_up_sync(FULL, cur.a1.w, 1);
+        float next = __shfl_down_sync(FULL, cur.a3.x, 1);
+        if (lane == 0) prev = cur.s1;
+        if (lane == 31 && x0 + 4 < G.nx) next = cur.s3;
+        float4 g[5];
+        g[0] = cur.v0;
+        g[1] = make_float4(prev, cur.a1.x, cur.a1.y, cur.a1.z);
+        g[2] = cur.v2;
+        g[3] = make_float4(cur.a3.y, cur.a3.z, cur.a3.w, next);
+        g[4] = cur.v4;
+        if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, cur.sw);
+        float4 shat = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m.evt.rowptr) {
+            const int e0 = __ldg(m.evt.rowptr + row), e1 = __ldg(m.evt.rowptr + row + 1);
+            for (int e = e0; e < e1; e++) {
+                const Event ev = m.evt.ev[e];
+                if ((ev.x >> 2) != c || !active) continue;
+                const int j = ev.x & 3;
+                if (ev.kind == 0) {
+                    if (ev.comp == 2 && t < m.evt.nt)
+                        set(shat, j, get(shat, j) - __ldg(m.evt.amp + (long long)ev.index * m.evt.nt + t));
+                } else if (t < m.evt.cap) {
+                    const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
+                    const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
+                    float v = 0.f;
+                    if (ev.comp == 2) v = -get(cur.cl, j) * s;
+                    else if (ev.comp == 3) v = bx;
+                    else if (ev.comp == 4) v = by;
+                    m.evt.traces[(long long)ev.index * m.evt.cap + t] = v;
+                }
+            }
+        }
+        float4 o[5];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float g0 = get(g[0], j), g1 = get(g[1], j), g2 = get(g[2], j), g3 = get(g[3], j), g4 = get(g[4], j),
+                        q = get(cur.cl, j), sh = get(shat, j);
+            const float s = ((g0 + g1) + (g2 + g3)) + g4;
+            const float L = q * s, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
+            set(o[1], j, (L - g3) + Tm);
+            set(o[3], j, (L - g1) + Tm);
+            set(o[2], j, (L - g4) + Tm);
+            set(o[4], j, (L - g2) + Tm);
+            set(o[0], j, (2.f * w0 * s - g0) + T0);
+        }
+        if (active) {
+            const PopBuf &out = (offset & 1) ? m.a : m.b;
+            for (int i = 0; i < 5; i++) C::store4(out, i, row, c, o[i]);
+        }
+        if (!more) break;
+        u = un;
+        mp = nmp;
+        mi = nmi;
+        ubase = nbase;
+        row = nrow;
+        c = nc;
+        cur = nxt;
+    }
+}
+
 }  // namespace lbk
 
 struct lbem_batch {
@@ -129,9 +308,11 @@ struct lbem_batch {
     std::vector<lbem_t *> members;
     cudaStream_t stream = nullptr;
     lbk::Member *d_members = nullptr;
-    long long *d_wstart = nullptr;  // [n + 1], per variant rebuilt
+    long long *d_wstart = nullptr;  // [n + 1] first warp (row variants) or block (site variant) of each member
+    int *d_map = nullptr;           // warp -> member (row variants) or block -> member (site variant)
+    size_t map_cap = 0;
     long long *d_t0 = nullptr;
-    long long total_warps = 0;
+    long long total_warps = 0, total_blocks = 0;
     int variant = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0, graph_variant = -1;
@@ -139,11 +320,14 @@ struct lbem_batch {
 
 using namespace lbk;
 
-static const int kRowsB[] = {1, 2, 4};
+// variants 0..2: row mapping with R = 1, 2, 4 rows per warp; variant 3: flattened one-site-per-thread mapping;
+// variant 4: persistent row mapping (R = 1 table) with contiguous unit ranges and prefetch;
+// variants 5, 6: R = 1 with registers capped for 5 / 6 resident blocks per SM
+static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6};
 static const int kBatchVariants = (int)(sizeof(kRowsB) / sizeof(kRowsB[0]));
 
 static lbem_status upload_tables(lbem_batch_t *b, int variant) {
-    const int R = kRowsB[variant];
+    const int R = kRowsB[variant] < 0 ? 1 : kRowsB[variant];  // persistent and capped variants use the R = 1 table
     std::vector<Member> hm(b->n);
     std::vector<long long> ws(b->n + 1, 0);
     for (int k = 0; k < b->n; k++) {
@@ -154,21 +338,64 @@ static lbem_status upload_tables(lbem_batch_t *b, int variant) {
         hm[k].b = a.out;
         hm[k].med = a.med;
         hm[k].evt = a.evt;
-        ws[k + 1] = ws[k] + (long long)((h->grid.ny + R - 1) / R) * (h->grid.nchunk_pad / 32);
+        const long long units = R ? (long long)((h->grid.ny + R - 1) / R) * (h->grid.nchunk_pad / 32)
+                                  : ((long long)h->grid.nx * h->grid.ny + BLOCK - 1) / BLOCK;
+        ws[k + 1] = ws[k] + units;
     }
-    b->total_warps = ws[b->n];
+    const long long total = ws[b->n];
+    if (R) {
+        b->total_warps = total;
+        b->total_blocks = (total * 32 + BLOCK - 1) / BLOCK;
+    } else {
+        b->total_warps = total * (BLOCK / 32);
+        b->total_blocks = total;
+    }
+    std::vector<int> map((size_t)total);
+    for (int k = 0; k < b->n; k++)
+        for (long long u = ws[k]; u < ws[k + 1]; u++) map[(size_t)u] = k;
+    if (b->map_cap < map.size()) {
+        cudaFree(b->d_map);
+        b->d_map = nullptr;
+        b->map_cap = 0;
+        if (cudaMalloc((void **)&b->d_map, sizeof(int) * map.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBEM_ERR_NOMEM, "lbem_batch: no room for the work table");
+        }
+        b->map_cap = map.size();
+    }
     LBEM_CUDA(cudaMemcpyAsync(b->d_members, hm.data(), sizeof(Member) * b->n, cudaMemcpyHostToDevice, b->stream));
     LBEM_CUDA(cudaMemcpyAsync(b->d_wstart, ws.data(), sizeof(long long) * (b->n + 1), cudaMemcpyHostToDevice, b->stream));
+    LBEM_CUDA(cudaMemcpyAsync(b->d_map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, b->stream));
     LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vectors go out of scope
     return LBEM_OK;
 }
 
 static cudaError_t launch_batch(lbem_batch_t *b, int variant, int offset) {
-    const unsigned blocks = (unsigned)((b->total_warps * 32 + BLOCK - 1) / BLOCK);
+    const unsigned blocks = (unsigned)b->total_blocks;
+    const long long nw = b->total_warps;
     switch (kRowsB[variant]) {
-        case 1: step2d_batch<1><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->n, b->d_t0, offset); break;
-        case 2: step2d_batch<2><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->n, b->d_t0, offset); break;
-        default: step2d_batch<4><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->n, b->d_t0, offset); break;
+        case 1: step2d_batch<1><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        case 2: step2d_batch<2><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        case 4: step2d_batch<4><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        case 0: step2d_batch_site<<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_map, b->d_wstart, b->d_t0, offset); break;
+        case -5: step2d_batch<1, 5><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        case -6: step2d_batch<1, 6><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        default: {
+            static int per_sm = 0, nsm = 0;
+            if (!per_sm) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_batch_pipe, BLOCK, 0);
+                if (per_sm < 1) per_sm = 1;
+            }
+            const long long warps = (long long)per_sm * nsm * (BLOCK / 32);
+            const long long per_warp = (nw + warps - 1) / warps;
+            const long long used = (nw + per_warp - 1) / per_warp;
+            const unsigned pb = (unsigned)((used * 32 + BLOCK - 1) / BLOCK);
+            step2d_batch_pipe<<<pb, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, per_warp, b->d_t0, offset);
+            break;
+        }
     }
     return cudaGetLastError();
 }
@@ -319,12 +546,28 @@ lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best) {
     return LBEM_OK;
 }
 
+lbem_status lbem_batch_set_variant(lbem_batch_t *b, int variant) {
+    if (!b) return fail(LBEM_ERR_ARG, "null batch");
+    if (variant < 0 || variant >= kBatchVariants) return fail(LBEM_ERR_ARG, "lbem_batch_set_variant: out of range");
+    b->variant = variant;
+    drop_batch_graph(b);
+    return LBEM_OK;
+}
+
+lbem_status lbem_batch_get_variant(const lbem_batch_t *b, int *variant, int *nvariants) {
+    if (!b) return fail(LBEM_ERR_ARG, "null batch");
+    if (variant) *variant = b->variant;
+    if (nvariants) *nvariants = kBatchVariants;
+    return LBEM_OK;
+}
+
 void lbem_batch_destroy(lbem_batch_t *b) {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     drop_batch_graph(b);
     cudaFree(b->d_members);
     cudaFree(b->d_wstart);
+    cudaFree(b->d_map);
     cudaFree(b->d_t0);
     delete b;
 }

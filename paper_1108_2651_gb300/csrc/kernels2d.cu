@@ -607,8 +607,8 @@ __device__ __forceinline__ void store8(const PopBuf &b, int p, int row, int c8, 
     (void)sizeof(C);
 }
 
-template <int ST, bool MU>
-__global__ void __launch_bounds__(BLOCK) step2d_w8(StepArgs a) {
+template <int ST, bool MU, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) step2d_w8(StepArgs a) {
     using C = Codec<ST>;
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
@@ -702,25 +702,30 @@ __global__ void __launch_bounds__(BLOCK) step2d_w8(StepArgs a) {
 }
 
 template <int ST, bool MU>
-static cudaError_t launch_w8(const StepArgs &a, cudaStream_t s) {
+static cudaError_t launch_w8(const StepArgs &a, cudaStream_t s, int minb) {
     const int n8 = (a.g.nx + 7) / 8, n8p = (n8 + 31) / 32 * 32;
     const long long warps = (long long)a.g.ny * (n8p / 32);
-    step2d_w8<ST, MU><<<(unsigned)((warps * 32 + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(a);
+    const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
+    // minb: registers capped so that minb blocks of 256 threads are resident per SM
+    if (minb == 5) step2d_w8<ST, MU, 5><<<blocks, BLOCK, 0, s>>>(a);
+    else if (minb == 4) step2d_w8<ST, MU, 4><<<blocks, BLOCK, 0, s>>>(a);
+    else step2d_w8<ST, MU, 1><<<blocks, BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers
 static const int kRows2d[] = {1, 2, 4};
-// rows per warp 1, 2, 4; 3 = persistent pipelined; 4 = cp.async staged; 5 = 8 sites per lane (16-bit storage)
-int nvariants_2d() { return 6; }
+// rows per warp 1, 2, 4; 3 = persistent pipelined; 4 = cp.async staged; 5 = 8 sites per lane (16-bit storage);
+// 6, 7 = variant 5 with registers capped for 4 / 5 resident blocks per SM
+int nvariants_2d() { return 8; }
 
 template <int ST, bool MU>
 static cudaError_t launch_st(const StepArgs &a, int variant, cudaStream_t s) {
     if (variant == 3) return launch_pipe<ST, MU>(a, s);
     if (variant == 4) return launch_async<ST, MU>(a, s);
-    if (variant == 5) {
+    if (variant >= 5 && variant <= 7) {
         if (ST == LBEM_F32) variant = 0;  // FP32 already issues 16-byte loads with 4 sites per lane
-        else return launch_w8<ST, MU>(a, s);
+        else return launch_w8<ST, MU>(a, s, variant == 5 ? 1 : variant - 2);
     }
     const int R = kRows2d[variant];
     const long long warps = (long long)((a.g.ny + R - 1) / R) * (a.g.nchunk_pad / 32);

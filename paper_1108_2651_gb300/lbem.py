@@ -64,6 +64,8 @@ _SIGS = {
     "lbem_batch_step": [_VP, _I],
     "lbem_batch_autotune": [_VP, _I, C.POINTER(_I)],
     "lbem_batch_destroy": [_VP],
+    "lbem_batch_set_variant": [_VP, _I],
+    "lbem_batch_get_variant": [_VP, C.POINTER(_I), C.POINTER(_I)],
 }
 
 
@@ -272,6 +274,16 @@ def lbem_batch_autotune(b, trial_steps):
     k = _I()
     _check(load().lbem_batch_autotune(b, int(trial_steps), C.byref(k)))
     return k.value
+
+
+def lbem_batch_set_variant(b, v):
+    _check(load().lbem_batch_set_variant(b, int(v)))
+
+
+def lbem_batch_get_variant(b):
+    v, n = _I(), _I()
+    _check(load().lbem_batch_get_variant(b, C.byref(v), C.byref(n)))
+    return v.value, n.value
 
 
 def lbem_batch_destroy(b):

@@ -36,6 +36,7 @@ def test_batch_of_256_equals_members_stepped_alone(lbem):
     batch_s = _solvers(probs, st.cuda_stream)
     b = lbem.lbem_batch_create([s.h for s in batch_s], st.cuda_stream)
     v = lbem.lbem_batch_autotune(b, 20)
+    assert 0 <= v < lbem.lbem_batch_get_variant(b)[1]
     lbem.lbem_batch_step(b, 1500)
     lbem.lbem_batch_step(b, 500)  # a second call reuses nothing but the members' state
     for s, p in zip(batch_s, probs):
@@ -97,4 +98,34 @@ def test_batch_rejects_mismatched_members(lbem):
     assert e.value.status == 6  # members at different times
     lbem.lbem_batch_destroy(b)
     for s in (a, c, d):
+        s.close()
+
+
+def test_every_batch_variant_is_bitwise_identical(lbem):
+    import torch
+
+    sizes = [64, 70, 97, 130, 200, 257, 333, 512]
+    probs = [W.heterogeneous_2d(N, seed=2000 + k, nsteps=120, sigma=min(20.0, N / 8.0), nrec=8,
+                                rec_radius=max(1, N // 4)) for k, N in enumerate(sizes)]
+    st = torch.cuda.Stream()
+    ref = []
+    for p in probs:
+        s = lbem.Solver(p.shape, stream=st.cuda_stream)
+        s.set_problem(p)
+        s.step(120)
+        ref.append(_read(s, p))
+        s.close()
+    ss = _solvers(probs, st.cuda_stream)
+    b = lbem.lbem_batch_create([s.h for s in ss], st.cuda_stream)
+    nv = lbem.lbem_batch_get_variant(b)[1]
+    for v in range(nv):
+        for s, p in zip(ss, probs):
+            s.set_problem(p)
+        lbem.lbem_batch_set_variant(b, v)
+        lbem.lbem_batch_step(b, 120)
+        for s, p, r in zip(ss, probs, ref):
+            for a, q in zip(_read(s, p), r):
+                np.testing.assert_array_equal(a, q, err_msg=f"variant {v}, {p.shape}")
+    lbem.lbem_batch_destroy(b)
+    for s in ss:
         s.close()
