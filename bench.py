@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 from paper_1108_2651_gb300 import workloads as W  # noqa: E402
 
 BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it is now built, keyed by
+# (workload, storage, variant); the capture and its command are summarised in profiles/.  Only reported for
+# the kernel that was captured.
+NCU_TRAFFIC = {("het2d_4096", "f32", 0): 402.705920e6 + 281.868288e6}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -404,8 +408,9 @@ def main():
     bps = BYTES_PER_SITE[args.storage] if p.D == 2 else 172
     achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
     kname = f"step2d<{args.storage}>" if p.D == 2 else "step3d"
+    traffic = NCU_TRAFFIC.get((args.workload, args.storage, variant)) if args.lb_steps is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"{kname} (variant {variant})",
+                "traffic": traffic, "kernel": f"{kname} (variant {variant})",
                 "algorithmic_bytes_per_site": bps, "ms_per_launch": ms_per_launch, "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)

@@ -280,3 +280,19 @@ def test_storage_forms_5000_steps_on_512_crop_of_4096_medium(lbem):
     for st in ("f16", "bf16"):
         assert max(report[st]) < 2 * u[st] * np.sqrt(5000 / 3), (st, report[st])
     assert max(report["i16b"][:2]) < 1e-3, report["i16b"]
+
+
+@pytest.mark.slow
+def test_1024_heterogeneous_5000_steps_64_receivers_elementwise(lbem):
+    """1024^2 heterogeneous medium (seed 1), Ricker point source, 64 receivers, 5000 steps, FP32: every field
+    value and every trace sample against the FP64 oracle (about a minute of oracle time on 16 cores)."""
+    p = W.heterogeneous_2d(1024, seed=1, nsteps=5000)
+    eE, eB = _check(p, tol=1e-4)
+    print(f"1024^2 x 5000 FP32: rel-L2 E {eE:.2e} B {eB:.2e}")
+
+
+def test_3d_48_cubed_1000_steps_forward(lbem):
+    """3D heterogeneous medium (48^3, n in [1, 3]), Ricker j_z, 1000 steps, FP32 vs the FP64 oracle."""
+    p = W.heterogeneous_3d(48, seed=4, nsteps=1000, sigma=4.0, plane_dz=12, rec_grid=(4, 4))
+    eE, eB = _check(p, tol=1e-4)
+    print(f"48^3 x 1000 FP32: rel-L2 E {eE:.2e} B {eB:.2e}")
