@@ -211,12 +211,35 @@ def other_forms(lbem, torch, p, peak, stream):
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
     ms, v = _time_run(lbem, torch, s, q, 1000, stream)
+    # adjoint: forward with a checkpoint every 100 steps, then the reverse-time pass (segment recompute +
+    # adjoint kernel, FP64 gradient accumulation), cotangent = the traces themselves
+    lbem.lbem_set_fields(s.h)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    lbem.lbem_forward_record(s.h, 1000, 100)
+    ev[1].record(stream)
+    cot = torch.empty(q.rec_site.size * 1000, dtype=torch.float32, device="cuda")
+    lbem.lbem_traces(s.h, cot)
+    grad = torch.empty(192 ** 3, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    lbem.lbem_adjoint(s.h, cot, grad)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
     s.close()
+    t_fwd, t_adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     n3 = 192 ** 3
     per = ms / 1000
     gbs = 172 * n3 / (per * 1e-3) / 1e9
     out["het3d_192"] = {"mlups": n3 * 1000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                         "frac": gbs / peak, "bytes_per_site": 172, "variant": v}
+    # backward pass bytes: recompute of 900 forward steps (172 B/site) + 1000 adjoint steps (272 B/site:
+    # lambda 84 read + state 84 read + c_L^2 4 + FP64 gradient 16 read/write + lambda 84 write)
+    bwd_bytes = (900 * 172 + 1000 * 272) * n3
+    out["adjoint_192"] = {"lb_steps": 1000, "checkpoint_every": 100, "ms_forward_record": t_fwd,
+                          "ms_backward": t_adj, "mlups_forward_plus_backward": n3 * 1000 / ((t_fwd + t_adj) * 1e-3) / 1e6,
+                          "backward_achieved_gbs": bwd_bytes / (t_adj * 1e-3) / 1e9,
+                          "backward_frac": bwd_bytes / (t_adj * 1e-3) / 1e9 / peak}
     return out
 
 
@@ -416,10 +439,11 @@ def main():
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        eps_h = np.ascontiguousarray(p.eps_r, np.float32).ravel()
-        E_h = np.empty(3 * nsite, np.float32)
-        B_h = np.empty(3 * nsite, np.float32)
-        tr_h = np.empty(p.rec_site.size * nsteps, np.float32)
+        # pinned host buffers: the medium goes in, the fields and traces come out, every pass
+        eps_h = torch.from_numpy(np.ascontiguousarray(p.eps_r, np.float32).ravel()).pin_memory()
+        E_h = torch.empty(3 * nsite, dtype=torch.float32).pin_memory()
+        B_h = torch.empty(3 * nsite, dtype=torch.float32).pin_memory()
+        tr_h = torch.empty(p.rec_site.size * nsteps, dtype=torch.float32).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         reps = max(1, min(args.steps, 2))
@@ -433,9 +457,10 @@ def main():
             lbem.lbem_diagnostics(h)
         dt = (time.perf_counter() - t0) / reps
         dt = dist_max(dt, world)
-        e2e = {"value": world * nsite * nsteps / dt / 1e6, "unit": "Mlups",
-               "h2d_bytes_per_step": int(eps_h.nbytes + p.src_amp.size * 4 + p.src_site.size * 12),
-               "d2h_bytes_per_step": int(E_h.nbytes + B_h.nbytes + tr_h.nbytes + 24)}
+        nb = lambda t: t.numel() * t.element_size()
+        e2e = {"value": world * nsite * nsteps / dt / 1e6, "unit": "Mlups", "host_memory": "pinned",
+               "h2d_bytes_per_step": int(nb(eps_h) + p.src_amp.size * 4 + p.src_site.size * 12),
+               "d2h_bytes_per_step": int(nb(E_h) + nb(B_h) + nb(tr_h) + 24)}
 
     forms = None
     if not args.no_forms and args.lb_steps is None:

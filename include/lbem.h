@@ -188,6 +188,12 @@ lbem_status lbem_diagnostics_static(int dim, int nx, int ny, int nz, const void 
 lbem_status lbem_save_state(lbem_t *h, void *dst);
 lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save);
 
+/* Verify the guard bands (256 patterned bytes) the library keeps on both sides of every handle-owned
+ * device array (distribution, medium, events, traces, scratch); synchronises the stream.  LBEM_ERR_STATE
+ * names the first array whose band was overwritten.  A check for out-of-bounds writes that needs no
+ * device-side instrumentation. */
+lbem_status lbem_check_guards(lbem_t *h);
+
 /* ---------------------------------------------------------------- adjoint (not in the paper) */
 
 /* Forward run that records what the adjoint needs: advances nsteps steps from

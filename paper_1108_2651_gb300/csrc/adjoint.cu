@@ -319,6 +319,121 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d(AdjArgs a) {
     for (int p = 0; p < 21; p++) Codec<LBEM_F32>::store4(ob, p, row, c, m[p]);
 }
 
+// One site per thread (48-60 registers instead of 170): the same update as adjoint3d.
+__global__ void __launch_bounds__(BLOCK) adjoint3d_site(AdjArgs a) {
+    const Grid &G = a.g;
+    const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
+    const int row = (int)(tid / G.pitch);
+    const int x = (int)(tid - (long long)row * G.pitch);
+    if (row >= G.nrows || x >= G.nx) return;
+    const int z = row / G.ny, y = row - z * G.ny;
+    const int rym = z * G.ny + (y == 0 ? G.ny - 1 : y - 1), ryp = z * G.ny + (y == G.ny - 1 ? 0 : y + 1);
+    const int rzm = (z == 0 ? G.nz - 1 : z - 1) * G.ny + y, rzp = (z == G.nz - 1 ? 0 : z + 1) * G.ny + y;
+    const int xm = x == 0 ? G.nx - 1 : x - 1, xp = x == G.nx - 1 ? 0 : x + 1;
+    const float *L = a.lam_in;
+    const float *S = static_cast<const float *>(a.state.data);
+    auto at = [&](const float *b, int p, int r, int xx) { return __ldg(b + p * G.plane + (long long)r * G.pitch + xx); };
+    float h[21], sg[3];
+#pragma unroll
+    for (int gm = 0; gm < 3; gm++) {
+        // mu_{i gamma}(y) = lambda_{i gamma}(y + c_i)
+        h[0 + gm] = at(L, 0 + gm, row, x);
+        h[3 + gm] = at(L, 3 + gm, row, xp);
+        h[6 + gm] = at(L, 6 + gm, ryp, x);
+        h[9 + gm] = at(L, 9 + gm, rzp, x);
+        h[12 + gm] = at(L, 12 + gm, row, xm);
+        h[15 + gm] = at(L, 15 + gm, rym, x);
+        h[18 + gm] = at(L, 18 + gm, rzm, x);
+        // sigma_gamma of g^t(y), g_i(y) = P_i(y - c_i)
+        sg[gm] = ((at(S, 0 + gm, row, x) + at(S, 3 + gm, row, xm)) + (at(S, 6 + gm, rym, x) + at(S, 9 + gm, rzm, x))) +
+                 ((at(S, 12 + gm, row, xp) + at(S, 15 + gm, ryp, x)) + at(S, 18 + gm, rzp, x));
+    }
+    const long long o = (long long)row * G.pitch + x;
+    const float q = __ldg(a.cL2 + o), w0 = 1.f - 3.f * q;
+    float jv[3] = {0.f, 0.f, 0.f}, rE[3] = {0.f, 0.f, 0.f}, rB[3] = {0.f, 0.f, 0.f};
+    if (a.evt.rowptr) {
+        const int e0 = __ldg(a.evt.rowptr + row), e1 = __ldg(a.evt.rowptr + row + 1);
+        for (int e = e0; e < e1; e++) {
+            const Event ev = a.evt.ev[e];
+            if (ev.x != x) continue;
+            if (ev.kind == 0) {
+                if (a.t < a.evt.nt) {
+                    const float jj = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
+                    if (ev.comp == 0) jv[0] += jj;
+                    else if (ev.comp == 1) jv[1] += jj;
+                    else jv[2] += jj;
+                }
+            } else {
+                const long long n = a.t - a.t0;
+                if (n < 0 || n >= a.nsteps || a.t >= a.evt.cap) continue;
+                const float r = __ldg(a.cot + (long long)ev.index * a.nsteps + n);
+                switch (ev.comp) {
+                    case 0: rE[0] += r; break;
+                    case 1: rE[1] += r; break;
+                    case 2: rE[2] += r; break;
+                    case 3: rB[0] += r; break;
+                    case 4: rB[1] += r; break;
+                    default: rB[2] += r; break;
+                }
+            }
+        }
+    }
+    float mv[3], nu[3];
+#pragma unroll
+    for (int gm = 0; gm < 3; gm++) {
+        mv[gm] = ((h[3 + gm] + h[6 + gm]) + (h[9 + gm] + h[12 + gm])) + (h[15 + gm] + h[18 + gm]);
+        nu[gm] = w0 * h[gm] + 0.5f * q * mv[gm];
+    }
+    const float vx = (h[10] - h[19]) - (h[8] - h[17]);
+    const float vy = (h[5] - h[14]) - (h[9] - h[18]);
+    const float vz = (h[6] - h[15]) - (h[4] - h[13]);
+    const float hx = 0.5f * vx, hy = 0.5f * vy, hz = 0.5f * vz;
+    const float Lx = 2.f * nu[0], Ly = 2.f * nu[1], Lz = 2.f * nu[2];
+    double d = 0.0;
+#pragma unroll
+    for (int gm = 0; gm < 3; gm++) {
+        const double sgm = sg[gm];
+        d += sgm * (double)mv[gm] - 6.0 * sgm * (double)h[gm];
+        d += (double)jv[gm] * (0.25 * (double)mv[gm] - 1.5 * (double)h[gm]);
+    }
+    float out[21];
+    out[0] = Lx - h[0];
+    out[1] = Ly - h[1];
+    out[2] = Lz - h[2];
+    out[3] = Lx - h[3];
+    out[4] = (Ly - hz) - h[4];
+    out[5] = (Lz + hy) - h[5];
+    out[6] = (Lx + hz) - h[6];
+    out[7] = Ly - h[7];
+    out[8] = (Lz - hx) - h[8];
+    out[9] = (Lx - hy) - h[9];
+    out[10] = (Ly + hx) - h[10];
+    out[11] = Lz - h[11];
+    out[12] = Lx - h[12];
+    out[13] = (Ly + hz) - h[13];
+    out[14] = (Lz - hy) - h[14];
+    out[15] = (Lx - hz) - h[15];
+    out[16] = Ly - h[16];
+    out[17] = (Lz + hx) - h[17];
+    out[18] = (Lx + hy) - h[18];
+    out[19] = (Ly - hx) - h[19];
+    out[20] = Lz - h[20];
+#pragma unroll
+    for (int gm = 0; gm < 3; gm++)
+        if (rE[gm] != 0.f) {
+            for (int i = 0; i < 7; i++) out[3 * i + gm] -= q * rE[gm];
+            d -= (double)sg[gm] * (double)rE[gm];
+        }
+    if (rB[0] != 0.f || rB[1] != 0.f || rB[2] != 0.f) {
+        out[10] += rB[0]; out[19] -= rB[0]; out[8] -= rB[0]; out[17] += rB[0];
+        out[5] += rB[1]; out[14] -= rB[1]; out[9] -= rB[1]; out[18] += rB[1];
+        out[6] += rB[2]; out[15] -= rB[2]; out[4] -= rB[2]; out[13] += rB[2];
+    }
+    a.gcl[o] += d;
+#pragma unroll
+    for (int p = 0; p < 21; p++) __stcs(a.lam_out + p * G.plane + o, out[p]);
+}
+
 // dL/d eps_r = -dL/dc_L^2 * c_L^2 / eps_r with eps_r = (D-1) c_ref^2 / c_L^2 (mu = 1), dense output.
 __global__ void adjoint_finish(Grid G, const double *gcl, const float *cL2, int D, double c_ref2, float *geps,
                                double *gcl_dense) {
@@ -334,6 +449,11 @@ __global__ void adjoint_finish(Grid G, const double *gcl, const float *cL2, int 
 }
 
 static cudaError_t launch_adjoint(const lbem_t *h, const AdjArgs &a) {
+    if (h->dim == 3 && h->variant == 1) {  // the one-site-per-thread shape, as the forward kernel
+        const long long threads = (long long)a.g.nrows * a.g.pitch;
+        adjoint3d_site<<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, h->stream>>>(a);
+        return cudaGetLastError();
+    }
     const long long warps = (long long)a.g.nrows * (a.g.nchunk_pad / 32);
     const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
     if (h->dim == 2) adjoint2d<<<blocks, BLOCK, 0, h->stream>>>(a);

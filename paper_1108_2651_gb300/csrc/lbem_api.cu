@@ -24,6 +24,36 @@ lbem_status cuda_fail(cudaError_t e, const char *what) {
     return LBEM_ERR_CUDA;
 }
 
+// Guard bands: GUARD bytes of GUARD_BYTE before and after each handle-owned array, so that a kernel writing
+// outside its array is caught by lbem_check_guards without a device-side checker.
+constexpr size_t GUARD = 256;
+constexpr unsigned char GUARD_BYTE = 0xA5;
+
+cudaError_t gmalloc(lbem_t *h, void **p, size_t bytes, const char *name) {
+    char *base = nullptr;
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)&base, bytes + 2 * GUARD);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(base, GUARD_BYTE, GUARD, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + GUARD + bytes, GUARD_BYTE, GUARD, h->stream)) != cudaSuccess) {
+        cudaFree(base);
+        return e;
+    }
+    *p = base + GUARD;
+    h->guarded.push_back({*p, bytes, name});
+    return cudaSuccess;
+}
+
+void gfree(lbem_t *h, void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->guarded.size(); i++)
+        if (h->guarded[i].user == p) {
+            h->guarded.erase(h->guarded.begin() + i);
+            break;
+        }
+    cudaFree(static_cast<char *>(p) - GUARD);
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -39,11 +69,11 @@ lbem_status ensure_stage(lbem_t *h, size_t floats) {
     if (h->stage_bytes >= bytes) return LBEM_OK;
     if (h->d_stage) {
         cudaStreamSynchronize(h->stream);
-        cudaFree(h->d_stage);
+        gfree(h, h->d_stage);
         h->d_stage = nullptr;
         h->stage_bytes = 0;
     }
-    if (cudaMalloc(&h->d_stage, bytes) != cudaSuccess) {
+    if (gmalloc(h, (void **)&h->d_stage, bytes, "staging") != cudaSuccess) {
         cudaGetLastError();
         return fail(LBEM_ERR_NOMEM, "staging buffer allocation failed");
     }
@@ -123,13 +153,13 @@ static lbem_status rebuild_events(lbem_t *h) {
     }
     for (int r = 0; r < h->grid.nrows; r++) rowptr[r + 1] += rowptr[r];
     cudaStreamSynchronize(h->stream);
-    cudaFree(h->d_ev);
+    gfree(h, h->d_ev);
     h->d_ev = nullptr;
     h->nev = (int)sorted.size();
-    if (!h->d_rowptr) LBEM_CUDA(cudaMalloc(&h->d_rowptr, sizeof(int) * (h->grid.nrows + 1)));
+    if (!h->d_rowptr) LBEM_CUDA(gmalloc(h, (void **)&h->d_rowptr, sizeof(int) * (h->grid.nrows + 1), "event rows"));
     LBEM_CUDA(cudaMemcpy(h->d_rowptr, rowptr.data(), sizeof(int) * rowptr.size(), cudaMemcpyHostToDevice));
     if (h->nev) {
-        LBEM_CUDA(cudaMalloc(&h->d_ev, sizeof(Event) * sorted.size()));
+        LBEM_CUDA(gmalloc(h, (void **)&h->d_ev, sizeof(Event) * sorted.size(), "events"));
         LBEM_CUDA(cudaMemcpy(h->d_ev, sorted.data(), sizeof(Event) * sorted.size(), cudaMemcpyHostToDevice));
     }
     drop_graph(h);
@@ -160,6 +190,8 @@ lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
     h->npop = d->dim == 2 ? 5 : 21;
     h->c_ref2 = d->c_ref2 > 0 ? d->c_ref2 : (d->dim == 2 ? 0.5 : 1.0 / 6.0);
     h->stream = (cudaStream_t)d->stream;
+    // default launch shape: the fastest measured on GB300 for each form (lbem_autotune re-measures)
+    h->variant = d->dim == 3 ? 1 : (d->storage == LBEM_F32 ? 0 : 6);
     Grid &G = h->grid;
     G.nx = d->nx;
     G.ny = d->ny;
@@ -175,14 +207,14 @@ lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
     const size_t ex_bytes = h->storage == LBEM_I16B ? (size_t)h->npop * (G.pitch / 4) * G.nrows : 0;
     const size_t per = ((data_bytes + 255) / 256 * 256) + ((ex_bytes + 255) / 256 * 256);
     h->pool_bytes = 2 * per;
-    cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->cL2, sizeof(float) * G.plane);
+    cudaError_t e = gmalloc(h, &h->pool, h->pool_bytes, "populations");
+    if (e == cudaSuccess) e = gmalloc(h, (void **)&h->cL2, sizeof(float) * G.plane, "c_L^2");
     if (e == cudaSuccess) {
         h->n_partials = diag_blocks(h->nsite);
-        e = cudaMalloc((void **)&h->d_partials, sizeof(double) * 3 * h->n_partials);
+        e = gmalloc(h, (void **)&h->d_partials, sizeof(double) * 3 * h->n_partials, "diagnostic partials");
     }
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_diag, sizeof(double) * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_counter, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = gmalloc(h, (void **)&h->d_diag, sizeof(double) * 4, "diagnostics");
+    if (e == cudaSuccess) e = gmalloc(h, (void **)&h->d_counter, sizeof(unsigned) * 4, "counters");
     if (e != cudaSuccess) {
         cudaGetLastError();
         lbem_destroy(h);
@@ -214,18 +246,10 @@ void lbem_destroy(lbem_t *h) {
     cudaStreamSynchronize(h->stream);
     drop_graph(h);
     adjoint_free(h);
-    cudaFree(h->pool);
-    cudaFree(h->cL2);
-    cudaFree(h->mu);
-    cudaFree(h->dlnmu);
-    cudaFree(h->d_rowptr);
-    cudaFree(h->d_ev);
-    cudaFree(h->d_amp);
-    cudaFree(h->d_traces);
-    cudaFree(h->d_partials);
-    cudaFree(h->d_diag);
-    cudaFree(h->d_counter);
-    cudaFree(h->d_stage);
+    for (void *p : {(void *)h->pool, (void *)h->cL2, (void *)h->mu, (void *)h->dlnmu, (void *)h->d_rowptr,
+                    (void *)h->d_ev, (void *)h->d_amp, (void *)h->d_traces, (void *)h->d_partials,
+                    (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage})
+        gfree(h, p);
     delete h;
 }
 
@@ -270,8 +294,8 @@ lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
                                          " sites with eps_r or mu_r not finite and > 0, or rest weight w0 outside "
                                          "[0,1) (medium faster than c_ref)");
     if (dm && !h->mu) {
-        LBEM_CUDA(cudaMalloc((void **)&h->mu, sizeof(float) * h->grid.plane));
-        LBEM_CUDA(cudaMalloc((void **)&h->dlnmu, sizeof(float) * h->grid.plane * h->dim));
+        LBEM_CUDA(gmalloc(h, (void **)&h->mu, sizeof(float) * h->grid.plane, "mu"));
+        LBEM_CUDA(gmalloc(h, (void **)&h->dlnmu, sizeof(float) * h->grid.plane * h->dim, "grad ln mu"));
         LBEM_CUDA(cudaMemsetAsync(h->mu, 0, sizeof(float) * h->grid.plane, h->stream));
         LBEM_CUDA(cudaMemsetAsync(h->dlnmu, 0, sizeof(float) * h->grid.plane * h->dim, h->stream));
     }
@@ -333,10 +357,10 @@ lbem_status lbem_set_sources(lbem_t *h, int n, const long long *site, const int 
     h->nsrc = n;
     h->nt = n ? nt : 0;
     cudaStreamSynchronize(h->stream);
-    cudaFree(h->d_amp);
+    gfree(h, h->d_amp);
     h->d_amp = nullptr;
     if (n) {
-        LBEM_CUDA(cudaMalloc((void **)&h->d_amp, sizeof(float) * (size_t)n * nt));
+        LBEM_CUDA(gmalloc(h, (void **)&h->d_amp, sizeof(float) * (size_t)n * nt, "source amplitudes"));
         LBEM_CUDA(cudaMemcpy(h->d_amp, amp, sizeof(float) * (size_t)n * nt, cudaMemcpyHostToDevice));
     }
     return rebuild_events(h);
@@ -355,10 +379,10 @@ lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const in
     h->nrec = n;
     h->cap = capacity;
     cudaStreamSynchronize(h->stream);
-    cudaFree(h->d_traces);
+    gfree(h, h->d_traces);
     h->d_traces = nullptr;
     if (n && capacity) {
-        LBEM_CUDA(cudaMalloc((void **)&h->d_traces, sizeof(float) * (size_t)n * capacity));
+        LBEM_CUDA(gmalloc(h, (void **)&h->d_traces, sizeof(float) * (size_t)n * capacity, "traces"));
         LBEM_CUDA(cudaMemset(h->d_traces, 0, sizeof(float) * (size_t)n * capacity));
     } else {
         h->cap = 0;
@@ -494,6 +518,23 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
     if (!is_device_ptr(src)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
     h->t = t_at_save;
     drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_check_guards(lbem_t *h) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<unsigned char> buf(2 * GUARD);
+    for (const auto &g : h->guarded) {
+        const char *u = static_cast<const char *>(g.user);
+        LBEM_CUDA(cudaMemcpy(buf.data(), u - GUARD, GUARD, cudaMemcpyDeviceToHost));
+        LBEM_CUDA(cudaMemcpy(buf.data() + GUARD, u + g.bytes, GUARD, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < buf.size(); i++)
+            if (buf[i] != GUARD_BYTE)
+                return fail(LBEM_ERR_STATE, std::string("lbem_check_guards: guard band ") +
+                                                (i < GUARD ? "before" : "after") + " array '" + g.name +
+                                                "' overwritten");
+    }
     return LBEM_OK;
 }
 

@@ -297,6 +297,13 @@ struct lbem {
     int variant = 0;
     // adjoint
     lbk::AdjointState *adj = nullptr;
+    // guard bands around every array above (see lbem_check_guards)
+    struct Guarded {
+        void *user;
+        size_t bytes;
+        const char *name;
+    };
+    std::vector<Guarded> guarded;
 };
 
 namespace lbk {
@@ -332,6 +339,9 @@ cudaError_t launch_maxabs(const float *a, long long n, unsigned *out, cudaStream
 cudaError_t launch_reduce_partials(const double *partials, int n, double *out, cudaStream_t s);
 int diag_blocks(long long nsite);
 cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, cudaStream_t s);
+// guarded device allocations (lbem_api.cu): `bytes` usable bytes between two patterned guard bands
+cudaError_t gmalloc(lbem_t *h, void **p, size_t bytes, const char *name);
+void gfree(lbem_t *h, void *p);
 // adjoint.cu
 void adjoint_free(lbem_t *h);
 

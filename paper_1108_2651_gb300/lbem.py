@@ -54,6 +54,7 @@ _SIGS = {
     "lbem_diagnostics": [_VP, C.POINTER(_D)],
     "lbem_diagnostics_static": [_I, _I, _I, _I, _VP, _VP, _VP, _D, _VP, _VP],
     "lbem_save_state": [_VP, _VP],
+    "lbem_check_guards": [_VP],
     "lbem_load_state": [_VP, _VP, _LL],
     "lbem_forward_record": [_VP, _I, _I],
     "lbem_adjoint": [_VP, _VP, _VP, _VP],
@@ -224,6 +225,10 @@ def lbem_diagnostics(h):
 def lbem_diagnostics_static(dim, nx, ny, nz, state, eps_r, mu_r, c_ref2, out, stream=None):
     _check(load().lbem_diagnostics_static(int(dim), int(nx), int(ny), int(nz), _ptr(state, np.uint8), _ptr(eps_r),
                                           _ptr(mu_r), float(c_ref2), _ptr(out, np.float64, 3, writable=True), stream))
+
+
+def lbem_check_guards(h):
+    _check(load().lbem_check_guards(h))
 
 
 def lbem_save_state(h, dst):

@@ -22,6 +22,7 @@ def gpu_run(p, storage="f32", nsteps=None, variant=None, graphs=False):
         E, B = s.fields()
         tr = s.traces(p.rec_site.size)
         torch.cuda.synchronize()
+        lbem.lbem_check_guards(s.h)  # no kernel wrote outside a handle-owned array
         E = np.moveaxis(E.cpu().double().numpy(), 0, -1)
         B = np.moveaxis(B.cpu().double().numpy(), 0, -1)
         return E, B, tr.cpu().double().numpy()

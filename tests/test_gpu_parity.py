@@ -173,6 +173,14 @@ def test_variants_and_graphs_are_bitwise_identical(lbem):
                 np.testing.assert_array_equal(a, b)
 
 
+def test_3d_launch_shapes_agree(lbem):
+    p = _problem_small(3, (6, 7, 70), 52, 20)
+    ref = gpu_run(p, variant=0)
+    out = gpu_run(p, variant=1)
+    for a, b in zip(out, ref):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * max(1.0, np.abs(b).max()))
+
+
 def test_host_and_device_pointers_agree(lbem):
     import torch
 
