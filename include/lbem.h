@@ -135,6 +135,13 @@ lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const in
  * lbem_set_graphs).  Requires a medium.  nsteps >= 0. */
 lbem_status lbem_step(lbem_t *h, int nsteps);
 
+/* Watchdog (off by default): with every > 0, lbem_step computes the FP64 field energy (as
+ * lbem_diagnostics, synchronising) whenever t reaches a multiple of `every`, and stops with
+ * LBEM_ERR_UNSTABLE (t left at the check) if the state is not finite or the energy grew by more than
+ * max_growth (> 1) since the previous check.  every = 0 switches it off.  The scheme is neutral (no
+ * growth without sources), so a jump means an over-driven source or a corrupted state. */
+lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
+
 /* Use (on != 0) or not CUDA-graph replay of runs of steps in lbem_step. */
 lbem_status lbem_set_graphs(lbem_t *h, int on);
 

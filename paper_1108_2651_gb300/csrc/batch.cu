@@ -171,6 +171,88 @@ __global__ void __launch_bounds__(BLOCK) step2d_batch_site(const Member *__restr
     __stcs(op + 4 * P, (L - g2) + Tm);
 }
 
+// Linear mapping over the padded plane: lane L of a member covers 4 sites at
+// row = L / (pitch/4), chunk c = L % (pitch/4); warps may span row ends, so only
+// the pitch padding idles lanes.  A lane at a row start or end takes its +-x
+// neighbour from the periodic wrap, a lane at a warp edge by a scalar load, any
+// other lane by shuffle from its neighbour (which is then in the same row).
+template <int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) step2d_batch_lin(const Member *__restrict__ M,
+                                                                const long long *__restrict__ wstart,
+                                                                const int *__restrict__ wmember, long long nwarps,
+                                                                const long long *__restrict__ t0p, int offset) {
+    using C = Codec<LBEM_F32>;
+    const int lane = threadIdx.x & 31;
+    const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    if (wg >= nwarps) return;
+    const int mi = __ldg(wmember + wg);
+    const Member &m = M[mi];
+    const Grid &G = m.g;
+    const int cpr = G.pitch >> 2;  // chunks per padded row
+    const long long L = (wg - wstart[mi]) * 32 + lane;
+    const int row = (int)(L / cpr);
+    const int c = (int)(L - (long long)row * cpr);
+    const bool inrow = row < G.ny;
+    const bool active = inrow && c < G.nchunk;
+    const int rr = inrow ? row : G.ny - 1;
+    const PopBuf &in = (offset & 1) ? m.b : m.a;
+    const PopBuf &out = (offset & 1) ? m.a : m.b;
+    const long long t = *t0p + offset;
+    const int x0 = 4 * c;
+    const int ym = rr == 0 ? G.ny - 1 : rr - 1, yp = rr == G.ny - 1 ? 0 : rr + 1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 g[5];
+    g[0] = active ? C::load4(in, 0, rr, c) : z4;
+    float4 a1 = active ? C::load4(in, 1, rr, c) : z4;
+    g[2] = active ? C::load4(in, 2, ym, c) : z4;
+    float4 a3 = active ? C::load4(in, 3, rr, c) : z4;
+    g[4] = active ? C::load4(in, 4, yp, c) : z4;
+    const float4 cl = active ? __ldg(reinterpret_cast<const float4 *>(m.med.cL2 + (long long)rr * G.pitch) + c) : z4;
+    float prev = __shfl_up_sync(FULL, a1.w, 1);
+    float next = __shfl_down_sync(FULL, a3.x, 1);
+    if (active && (lane == 0 || c == 0)) prev = C::load1(in, 1, rr, c == 0 ? G.nx - 1 : x0 - 1);
+    if (active && lane == 31 && x0 + 4 < G.nx) next = C::load1(in, 3, rr, x0 + 4);
+    if (!active) return;
+    g[1] = make_float4(prev, a1.x, a1.y, a1.z);
+    g[3] = make_float4(a3.y, a3.z, a3.w, next);
+    if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, C::load1(in, 3, rr, 0));
+    float4 shat = z4;
+    if (m.evt.rowptr) {
+        const int e0 = __ldg(m.evt.rowptr + rr), e1 = __ldg(m.evt.rowptr + rr + 1);
+        for (int e = e0; e < e1; e++) {
+            const Event ev = m.evt.ev[e];
+            if ((ev.x >> 2) != c) continue;
+            const int j = ev.x & 3;
+            if (ev.kind == 0) {
+                if (ev.comp == 2 && t < m.evt.nt)
+                    set(shat, j, get(shat, j) - __ldg(m.evt.amp + (long long)ev.index * m.evt.nt + t));
+            } else if (t < m.evt.cap) {
+                const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
+                const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
+                float v = 0.f;
+                if (ev.comp == 2) v = -get(cl, j) * s;
+                else if (ev.comp == 3) v = bx;
+                else if (ev.comp == 4) v = by;
+                m.evt.traces[(long long)ev.index * m.evt.cap + t] = v;
+            }
+        }
+    }
+    float4 o[5];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float g0 = get(g[0], j), g1 = get(g[1], j), g2 = get(g[2], j), g3 = get(g[3], j), g4 = get(g[4], j),
+                    q = get(cl, j), sh = get(shat, j);
+        const float s = ((g0 + g1) + (g2 + g3)) + g4;
+        const float Lq = q * s, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
+        set(o[1], j, (Lq - g3) + Tm);
+        set(o[3], j, (Lq - g1) + Tm);
+        set(o[2], j, (Lq - g4) + Tm);
+        set(o[4], j, (Lq - g2) + Tm);
+        set(o[0], j, (2.f * w0 * s - g0) + T0);
+    }
+    for (int i = 0; i < 5; i++) C::store4(out, i, rr, c, o[i]);
+}
+
 // Persistent row mapping: warp w walks the contiguous units [w*k, (w+1)*k) of the
 // flattened table (nearly always one member), keeps that member's descriptor in
 // registers, and issues the loads of its next unit before it computes the current one.
@@ -322,8 +404,9 @@ using namespace lbk;
 
 // variants 0..2: row mapping with R = 1, 2, 4 rows per warp; variant 3: flattened one-site-per-thread mapping;
 // variant 4: persistent row mapping (R = 1 table) with contiguous unit ranges and prefetch;
-// variants 5, 6: R = 1 with registers capped for 5 / 6 resident blocks per SM
-static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6};
+// variants 5, 6: R = 1 with registers capped for 5 / 6 resident blocks per SM;
+// variants 7, 8: linear mapping over the padded plane (uncapped / capped for 5 blocks per SM)
+static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8};
 static const int kBatchVariants = (int)(sizeof(kRowsB) / sizeof(kRowsB[0]));
 
 static lbem_status upload_tables(lbem_batch_t *b, int variant) {
@@ -338,8 +421,10 @@ static lbem_status upload_tables(lbem_batch_t *b, int variant) {
         hm[k].b = a.out;
         hm[k].med = a.med;
         hm[k].evt = a.evt;
-        const long long units = R ? (long long)((h->grid.ny + R - 1) / R) * (h->grid.nchunk_pad / 32)
-                                  : ((long long)h->grid.nx * h->grid.ny + BLOCK - 1) / BLOCK;
+        const bool lin = kRowsB[variant] == -7 || kRowsB[variant] == -8;
+        const long long units = lin ? ((long long)h->grid.ny * (h->grid.pitch / 4) + 31) / 32
+                                : R ? (long long)((h->grid.ny + R - 1) / R) * (h->grid.nchunk_pad / 32)
+                                    : ((long long)h->grid.nx * h->grid.ny + BLOCK - 1) / BLOCK;
         ws[k + 1] = ws[k] + units;
     }
     const long long total = ws[b->n];
@@ -380,6 +465,8 @@ static cudaError_t launch_batch(lbem_batch_t *b, int variant, int offset) {
         case 0: step2d_batch_site<<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_map, b->d_wstart, b->d_t0, offset); break;
         case -5: step2d_batch<1, 5><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
         case -6: step2d_batch<1, 6><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        case -7: step2d_batch_lin<1><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
+        case -8: step2d_batch_lin<5><<<blocks, BLOCK, 0, b->stream>>>(b->d_members, b->d_wstart, b->d_map, nw, b->d_t0, offset); break;
         default: {
             static int per_sm = 0, nsm = 0;
             if (!per_sm) {

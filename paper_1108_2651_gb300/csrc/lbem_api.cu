@@ -338,6 +338,7 @@ lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B) {
     cudaError_t e = h->dim == 2 ? launch_init_2d(h, dE, dB, h->stream) : launch_init_3d(h, dE, dB, h->stream);
     LBEM_CUDA(e);
     h->t = 0;
+    h->wd_last = -1.0;
     if (h->d_traces) LBEM_CUDA(cudaMemsetAsync(h->d_traces, 0, sizeof(float) * (size_t)h->nrec * h->cap, h->stream));
     drop_graph(h);
     return LBEM_OK;
@@ -397,7 +398,46 @@ lbem_status lbem_set_graphs(lbem_t *h, int on) {
     return LBEM_OK;
 }
 
+static lbem_status step_run(lbem_t *h, int nsteps);
+
+lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (every < 0 || (every > 0 && !(max_growth > 1.0)))
+        return fail(LBEM_ERR_ARG, "lbem_set_watchdog: every >= 0 and max_growth > 1");
+    h->wd_every = every;
+    h->wd_growth = max_growth;
+    h->wd_last = -1.0;
+    return LBEM_OK;
+}
+
 lbem_status lbem_step(lbem_t *h, int nsteps) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (h->wd_every <= 0 || nsteps <= 0) return step_run(h, nsteps);
+    // watchdog: FP64 field energy after every `wd_every` steps; non-finite or a jump by more than
+    // wd_growth since the previous check stops the run
+    int left = nsteps;
+    while (left > 0) {
+        const long long into = h->t % h->wd_every;
+        const int chunk = (int)std::min<long long>(left, h->wd_every - into);
+        lbem_status st = step_run(h, chunk);
+        if (st != LBEM_OK) return st;
+        left -= chunk;
+        if ((h->t % h->wd_every) == 0) {
+            double d[3];
+            st = lbem_diagnostics(h, d);
+            if (st == LBEM_ERR_UNSTABLE)
+                return fail(LBEM_ERR_UNSTABLE, "lbem_step: watchdog found a non-finite state at t = " + std::to_string(h->t));
+            if (st != LBEM_OK) return st;
+            if (h->wd_last > 0.0 && d[0] > h->wd_growth * h->wd_last)
+                return fail(LBEM_ERR_UNSTABLE, "lbem_step: watchdog: field energy grew by more than the allowed factor "
+                                               "between checks at t = " + std::to_string(h->t));
+            h->wd_last = d[0];
+        }
+    }
+    return LBEM_OK;
+}
+
+static lbem_status step_run(lbem_t *h, int nsteps) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (nsteps < 0) return fail(LBEM_ERR_ARG, "lbem_step: nsteps < 0");
     if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_step: set a medium first");

@@ -295,6 +295,9 @@ struct lbem {
     int graph_steps = 0, graph_cur = -1, graph_variant = -1;
     // tuning
     int variant = 0;
+    // watchdog (lbem_set_watchdog)
+    int wd_every = 0;
+    double wd_growth = 0.0, wd_last = -1.0;
     // adjoint
     lbk::AdjointState *adj = nullptr;
     // guard bands around every array above (see lbem_check_guards)

@@ -48,6 +48,7 @@ _SIGS = {
     "lbem_set_receivers": [_VP, _I, _VP, _VP, _I],
     "lbem_step": [_VP, _I],
     "lbem_set_graphs": [_VP, _I],
+    "lbem_set_watchdog": [_VP, _I, _D],
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
     "lbem_traces": [_VP, _VP, C.POINTER(_I)],
@@ -193,6 +194,10 @@ def lbem_set_receivers(h, site, comp, capacity):
 
 def lbem_step(h, nsteps):
     _check(load().lbem_step(h, int(nsteps)))
+
+
+def lbem_set_watchdog(h, every, max_growth=1e6):
+    _check(load().lbem_set_watchdog(h, int(every), float(max_growth)))
 
 
 def lbem_set_graphs(h, on):

@@ -304,3 +304,21 @@ def test_3d_48_cubed_1000_steps_forward(lbem):
     p = W.heterogeneous_3d(48, seed=4, nsteps=1000, sigma=4.0, plane_dz=12, rec_grid=(4, 4))
     eE, eB = _check(p, tol=1e-4)
     print(f"48^3 x 1000 FP32: rel-L2 E {eE:.2e} B {eB:.2e}")
+
+
+def test_watchdog_passes_stable_runs_and_stops_overflow(lbem):
+    p = W.heterogeneous_2d(128, seed=3, nsteps=300, sigma=6.0, nrec=4, rec_radius=30)
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    lbem.lbem_set_watchdog(s.h, 50, 1e6)
+    s.step(300)  # a stable run is not stopped
+    assert lbem.lbem_time(s.h) == 300
+    # an over-driven source overflows the FP32 state (inf, then nan): the watchdog stops the run
+    p.src_amp = np.full_like(p.src_amp, 3e38)
+    lbem.lbem_set_sources(s.h, p.src_site, p.src_comp, p.src_amp)
+    lbem.lbem_set_fields(s.h)
+    with pytest.raises(lbem.LbemError) as e:
+        s.step(300)
+    assert e.value.status == 4
+    assert lbem.lbem_time(s.h) % 50 == 0 and lbem.lbem_time(s.h) < 300
+    s.close()
