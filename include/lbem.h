@@ -155,6 +155,12 @@ lbem_status lbem_time(const lbem_t *h, long long *t);
  * may be NULL.  Components not representable in 2D are written as 0. */
 lbem_status lbem_fields(lbem_t *h, float *E, float *B);
 
+/* Energy density and Poynting vector of the current state (paper, Sec. "Heterogeneous media"):
+ *   u[s]      = sum_a (B_a^2 + E_a^2 / c_eff^2)      ([nsite] floats; its sum is out[0] of lbem_diagnostics)
+ *   P[a*n+s]  = eps_abc E_b B_c                       ([3][nsite] floats)
+ * either may be NULL; host or device memory.  Uses the handle's staging area (allocated on first use). */
+lbem_status lbem_energy_flux(lbem_t *h, float *u, float *P);
+
 /* Receiver traces: out[r*nrec_steps + n] for n < nrec_steps = min(t, capacity),
  * host or device; *nrecorded (host, may be NULL) receives nrec_steps.  out may be
  * NULL to query the count only. */

@@ -512,6 +512,27 @@ lbem_status lbem_fields(lbem_t *h, float *E, float *B) {
     return LBEM_OK;
 }
 
+lbem_status lbem_energy_flux(lbem_t *h, float *u, float *P) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_energy_flux: set a medium first");
+    if (!u && !P) return LBEM_OK;
+    const size_t n = (size_t)h->nsite, n3 = 3 * n;
+    const bool uh = u && !is_device_ptr(u), ph = P && !is_device_ptr(P);
+    // staging: E, B (6n floats), then host-output copies of u (n) and P (3n)
+    lbem_status st = ensure_stage(h, 2 * n3 + (uh ? n : 0) + (ph ? n3 : 0));
+    if (st != LBEM_OK) return st;
+    float *E = h->d_stage, *B = h->d_stage + n3;
+    float *du = uh ? h->d_stage + 2 * n3 : u;
+    float *dP = ph ? h->d_stage + 2 * n3 + (uh ? n : 0) : P;
+    cudaError_t e = h->dim == 2 ? launch_fields_2d(h, E, B, h->stream) : launch_fields_3d(h, E, B, h->stream);
+    LBEM_CUDA(e);
+    LBEM_CUDA(launch_energy_flux(h, E, B, du, dP, h->stream));
+    if (uh) LBEM_CUDA(cudaMemcpyAsync(u, du, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (ph) LBEM_CUDA(cudaMemcpyAsync(P, dP, n3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (uh || ph) LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
 lbem_status lbem_traces(lbem_t *h, float *out, int *nrecorded) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     const int n = (int)std::min<long long>(h->t, h->cap);

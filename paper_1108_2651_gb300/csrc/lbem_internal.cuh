@@ -342,6 +342,7 @@ cudaError_t launch_maxabs(const float *a, long long n, unsigned *out, cudaStream
 cudaError_t launch_reduce_partials(const double *partials, int n, double *out, cudaStream_t s);
 int diag_blocks(long long nsite);
 cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, cudaStream_t s);
+cudaError_t launch_energy_flux(const lbem_t *h, const float *E, const float *B, float *u, float *P, cudaStream_t s);
 // guarded device allocations (lbem_api.cu): `bytes` usable bytes between two patterned guard bands
 cudaError_t gmalloc(lbem_t *h, void **p, size_t bytes, const char *name);
 void gfree(lbem_t *h, void *p);

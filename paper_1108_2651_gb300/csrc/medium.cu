@@ -115,6 +115,30 @@ cudaError_t launch_reduce_partials(const double *partials, int n, double *out, c
     return cudaGetLastError();
 }
 
+// Energy density and Poynting vector per site from dense E, B (paper, Sec. "Heterogeneous media"):
+//   u = sum_a (B_a^2 + E_a^2 / c_eff^2),   P_a = eps_abc E_b B_c,   c_eff^2 = c_L^2 / (D - 1)
+__global__ void energy_flux_kernel(Grid G, int D, const float *E, const float *B, const float *cL2, float *u, float *P) {
+    const long long n = (long long)G.nx * G.nrows;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const long long row = s / G.nx;
+        const int x = (int)(s - row * G.nx);
+        const float ce2 = cL2[row * G.pitch + x] / (float)(D - 1);
+        const float ex = E[s], ey = E[n + s], ez = E[2 * n + s];
+        const float bx = B[s], by = B[n + s], bz = B[2 * n + s];
+        if (u) u[s] = (bx * bx + by * by + bz * bz) + (ex * ex + ey * ey + ez * ez) / ce2;
+        if (P) {
+            P[s] = ey * bz - ez * by;
+            P[n + s] = ez * bx - ex * bz;
+            P[2 * n + s] = ex * by - ey * bx;
+        }
+    }
+}
+
+cudaError_t launch_energy_flux(const lbem_t *h, const float *E, const float *B, float *u, float *P, cudaStream_t s) {
+    energy_flux_kernel<<<grid_for(h->nsite), 256, 0, s>>>(h->grid, h->dim, E, B, h->cL2, u, P);
+    return cudaGetLastError();
+}
+
 int diag_blocks(long long nsite) {
     long long b = (nsite + BLOCK - 1) / BLOCK;
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);  // 152 SMs x 8

@@ -52,6 +52,7 @@ _SIGS = {
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
     "lbem_traces": [_VP, _VP, C.POINTER(_I)],
+    "lbem_energy_flux": [_VP, _VP, _VP],
     "lbem_diagnostics": [_VP, C.POINTER(_D)],
     "lbem_diagnostics_static": [_I, _I, _I, _I, _VP, _VP, _VP, _D, _VP, _VP],
     "lbem_save_state": [_VP, _VP],
@@ -213,6 +214,11 @@ def lbem_time(h):
 def lbem_fields(h, E=None, B=None):
     n = lbem_info(h)[0]
     _check(load().lbem_fields(h, _ptr(E, count=3 * n, writable=True), _ptr(B, count=3 * n, writable=True)))
+
+
+def lbem_energy_flux(h, u=None, P=None):
+    n = lbem_info(h)[0]
+    _check(load().lbem_energy_flux(h, _ptr(u, count=n, writable=True), _ptr(P, count=3 * n, writable=True)))
 
 
 def lbem_traces(h, out=None):

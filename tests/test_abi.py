@@ -63,3 +63,32 @@ def test_product_path_refuses_to_run_without_the_library(tmp_path):
             lbem.load(str(tmp_path / "missing.so"))
     finally:
         lbem._lib = saved
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dim=4, nx=8, ny=8), "dim"),
+    (dict(dim=2, nx=0, ny=8), "sizes"),
+    (dict(dim=2, nx=8, ny=-1), "sizes"),
+    (dict(dim=3, nx=8, ny=8, nz=0), "sizes"),
+    (dict(dim=2, nx=8, ny=8, storage=9), "storage"),
+    (dict(dim=3, nx=8, ny=8, nz=8, storage=1), "3D"),
+    (dict(dim=2, nx=1 << 29, ny=1), "too large"),
+])
+def test_create_rejects_invalid_descriptors_before_touching_the_device(lib, kw, msg):
+    """Descriptor validation happens on the host, before any CUDA call, so it is testable without a GPU."""
+    from paper_1108_2651_gb300 import lbem
+
+    args = dict(dim=2, nx=8, ny=8, nz=1, storage=0)
+    args.update(kw)
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_create(args["dim"], args["nx"], args["ny"], args.get("nz", 1), args["storage"])
+    assert e.value.status == 1 and msg in str(e.value)
+
+
+def test_null_handles_are_rejected(lib):
+    from paper_1108_2651_gb300 import lbem
+
+    for f, extra in (("lbem_step", [1]), ("lbem_sync", []), ("lbem_set_graphs", [1]), ("lbem_set_variant", [0]),
+                     ("lbem_check_guards", []), ("lbem_batch_step", [1])):
+        assert getattr(lib, f)(None, *extra) == 1, f
+    assert "null" in lbem.lbem_last_error()

@@ -322,3 +322,42 @@ def test_watchdog_passes_stable_runs_and_stops_overflow(lbem):
     assert e.value.status == 4
     assert lbem.lbem_time(s.h) % 50 == 0 and lbem.lbem_time(s.h) < 300
     s.close()
+
+
+@pytest.mark.parametrize("D,shape", [(2, (37, 50)), (3, (7, 9, 11))])
+def test_energy_density_and_poynting_vector(lbem, D, shape):
+    """u = |B|^2 + |E|^2/c^2 and P = E x B (paper, Sec. "Heterogeneous media") against the oracle's fields;
+    u summed over the grid equals the FP64 energy diagnostic."""
+    import torch
+
+    p = _problem_small(D, shape, 81, 25, mu=False)
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    s.step(25)
+    n = s.nsite
+    u = torch.empty(n, device="cuda")
+    P = torch.empty(3 * n, device="cuda")
+    lbem.lbem_energy_flux(s.h, u, P)
+    d = s.diagnostics()
+    torch.cuda.synchronize()
+    s.close()
+    oE, oB, _, m, _ = oracle_run(p)
+    ou = (oB ** 2).sum(-1) + (oE ** 2).sum(-1) / m.ceff2
+    oP = np.cross(oE, oB)
+    gu = u.cpu().double().numpy().reshape(shape)
+    gP = np.moveaxis(P.cpu().double().numpy().reshape((3,) + shape), 0, -1)
+    assert rel(gu, ou) < 1e-5 and rel(gP, oP) < 1e-5
+    assert abs(gu.sum() - d[0]) < 1e-5 * d[0]
+
+
+def test_extreme_index_contrast(lbem):
+    """Degenerate weights: refractive index from 1 (rest weight 0) to 100 (rest weight 1 - 1e-4)."""
+    shape = (40, 44)
+    rng = np.random.default_rng(90)
+    n_idx = np.exp(rng.uniform(0.0, np.log(100.0), shape))
+    n_idx[0, 0] = 1.0
+    p = W.Problem("contrast", 2, shape, n_idx ** 2, None, 60)
+    p.E0, p.B0 = W.random_fields(shape, 91, 0.3)
+    p.E0[..., :2] = 0
+    p.B0[..., 2] = 0
+    _check(p, tol=1e-5)
