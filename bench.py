@@ -212,7 +212,22 @@ def other_forms(lbem, torch, p, peak, stream):
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
     ms, v = _time_run(lbem, torch, s, q, 1000, stream)
     # adjoint: forward with a checkpoint every 100 steps, then the reverse-time pass (segment recompute +
-    # adjoint kernel, FP64 gradient accumulation), cotangent = the traces themselves
+    # adjoint kernel, FP64 gradient accumulation), cotangent = the traces themselves; the faster of the
+    # two one-site-per-thread adjoint shapes (3D variants 1 and 2) on a short trial
+    trial = {}
+    for v3 in (1, 2):
+        lbem.lbem_set_variant(s.h, v3)
+        lbem.lbem_set_fields(s.h)
+        lbem.lbem_forward_record(s.h, 50, 25)
+        c0 = torch.zeros(q.rec_site.size * 50, dtype=torch.float32, device="cuda")
+        g0 = torch.empty(192 ** 3, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbem.lbem_adjoint(s.h, c0, g0)
+        torch.cuda.synchronize()
+        trial[v3] = time.perf_counter() - t0
+    v_adj = min(trial, key=trial.get)
+    lbem.lbem_set_variant(s.h, v_adj)
     lbem.lbem_set_fields(s.h)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record(stream)
@@ -236,7 +251,7 @@ def other_forms(lbem, torch, p, peak, stream):
     # backward pass bytes: recompute of 900 forward steps (172 B/site) + 1000 adjoint steps (272 B/site:
     # lambda 84 read + state 84 read + c_L^2 4 + FP64 gradient 16 read/write + lambda 84 write)
     bwd_bytes = (900 * 172 + 1000 * 272) * n3
-    out["adjoint_192"] = {"lb_steps": 1000, "checkpoint_every": 100, "ms_forward_record": t_fwd,
+    out["adjoint_192"] = {"lb_steps": 1000, "checkpoint_every": 100, "variant": v_adj, "ms_forward_record": t_fwd,
                           "ms_backward": t_adj, "mlups_forward_plus_backward": n3 * 1000 / ((t_fwd + t_adj) * 1e-3) / 1e6,
                           "backward_achieved_gbs": bwd_bytes / (t_adj * 1e-3) / 1e9,
                           "backward_frac": bwd_bytes / (t_adj * 1e-3) / 1e9 / peak}

@@ -319,8 +319,10 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d(AdjArgs a) {
     for (int p = 0; p < 21; p++) Codec<LBEM_F32>::store4(ob, p, row, c, m[p]);
 }
 
-// One site per thread (48-60 registers instead of 170): the same update as adjoint3d.
-__global__ void __launch_bounds__(BLOCK) adjoint3d_site(AdjArgs a) {
+// One site per thread (48-64 registers instead of 170): the same update as adjoint3d.  The FP64
+// gradient accumulator is loaded with the other operands, at the top, so its latency overlaps theirs.
+template <int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) adjoint3d_site(AdjArgs a) {
     const Grid &G = a.g;
     const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
     const int row = (int)(tid / G.pitch);
@@ -333,6 +335,8 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d_site(AdjArgs a) {
     const float *L = a.lam_in;
     const float *S = static_cast<const float *>(a.state.data);
     auto at = [&](const float *b, int p, int r, int xx) { return __ldg(b + p * G.plane + (long long)r * G.pitch + xx); };
+    const long long o = (long long)row * G.pitch + x;
+    const double gacc = a.gcl[o];
     float h[21], sg[3];
 #pragma unroll
     for (int gm = 0; gm < 3; gm++) {
@@ -348,7 +352,6 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d_site(AdjArgs a) {
         sg[gm] = ((at(S, 0 + gm, row, x) + at(S, 3 + gm, row, xm)) + (at(S, 6 + gm, rym, x) + at(S, 9 + gm, rzm, x))) +
                  ((at(S, 12 + gm, row, xp) + at(S, 15 + gm, ryp, x)) + at(S, 18 + gm, rzp, x));
     }
-    const long long o = (long long)row * G.pitch + x;
     const float q = __ldg(a.cL2 + o), w0 = 1.f - 3.f * q;
     float jv[3] = {0.f, 0.f, 0.f}, rE[3] = {0.f, 0.f, 0.f}, rB[3] = {0.f, 0.f, 0.f};
     if (a.evt.rowptr) {
@@ -429,7 +432,7 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d_site(AdjArgs a) {
         out[5] += rB[1]; out[14] -= rB[1]; out[9] -= rB[1]; out[18] += rB[1];
         out[6] += rB[2]; out[15] -= rB[2]; out[4] -= rB[2]; out[13] += rB[2];
     }
-    a.gcl[o] += d;
+    a.gcl[o] = gacc + d;
 #pragma unroll
     for (int p = 0; p < 21; p++) __stcs(a.lam_out + p * G.plane + o, out[p]);
 }
@@ -449,9 +452,11 @@ __global__ void adjoint_finish(Grid G, const double *gcl, const float *cL2, int 
 }
 
 static cudaError_t launch_adjoint(const lbem_t *h, const AdjArgs &a) {
-    if (h->dim == 3 && h->variant == 1) {  // the one-site-per-thread shape, as the forward kernel
+    if (h->dim == 3 && h->variant >= 1) {  // the one-site-per-thread shapes, as the forward kernel
         const long long threads = (long long)a.g.nrows * a.g.pitch;
-        adjoint3d_site<<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, h->stream>>>(a);
+        const unsigned blocks = (unsigned)((threads + BLOCK - 1) / BLOCK);
+        if (h->variant == 2) adjoint3d_site<5><<<blocks, BLOCK, 0, h->stream>>>(a);  // registers capped
+        else adjoint3d_site<1><<<blocks, BLOCK, 0, h->stream>>>(a);
         return cudaGetLastError();
     }
     const long long warps = (long long)a.g.nrows * (a.g.nchunk_pad / 32);

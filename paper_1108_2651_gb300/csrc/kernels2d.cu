@@ -24,11 +24,6 @@
 
 namespace lbk {
 
-template <int ST>
-struct Pull2D {
-    float4 g[5];
-};
-
 // Pre-collision populations of the 4 sites (row, 4c..4c+3): g_i(x) = buf_i(x - c_i).
 // Must be called by all 32 lanes of a warp (shuffles); lanes with c >= nchunk
 // load nothing and their results are discarded by the caller.

@@ -22,7 +22,7 @@
 namespace lbk {
 
 struct Rows3 {
-    int r0, xm, ym, zm, yp, zp;  // own row and the rows pulled from
+    int r0, ym, zm, yp, zp;  // own row and the rows pulled from (y-1, z-1, y+1, z+1)
 };
 
 __device__ __forceinline__ Rows3 rows3(const Grid &G, int row) {
@@ -256,10 +256,12 @@ __global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a) {
     for (int p = 0; p < 21; p++) __stcs(out + p * G.plane + o, h[p]);
 }
 
-int nvariants_3d() { return 2; }
+// 0 = four sites per lane; 1 = one site per thread; 2 = as 1 (forward), with the adjoint kernel's
+// registers capped for 5 resident blocks per SM
+int nvariants_3d() { return 3; }
 
 cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s) {
-    if (variant == 1) {
+    if (variant >= 1) {
         const long long threads = (long long)a.g.nrows * a.g.pitch;
         const unsigned blocks = (unsigned)((threads + BLOCK - 1) / BLOCK);
         if (has_mu) step3d_site<true><<<blocks, BLOCK, 0, s>>>(a);

@@ -249,10 +249,6 @@ struct StepArgs {
 };
 
 // ------------------------------------------------------------------ handle
-struct Tuning {
-    int variant = 0;
-};
-
 struct AdjointState;  // defined in adjoint.cu
 
 }  // namespace lbk

@@ -25,7 +25,8 @@ def _small(D, shape, seed, nsteps):
 
 
 @pytest.mark.parametrize("D,shape,every,variant", [(2, (20, 27), 7, 0), (2, (9, 130), 40, 0), (3, (7, 8, 9), 5, 0),
-                                                   (3, (7, 8, 9), 5, 1), (3, (5, 6, 70), 11, 1)])
+                                                   (3, (7, 8, 9), 5, 1), (3, (5, 6, 70), 11, 1),
+                                                   (3, (5, 6, 70), 11, 2)])
 def test_adjoint_matches_oracle_adjoint(lbem, D, shape, every, variant):
     import torch
 
@@ -34,7 +35,7 @@ def test_adjoint_matches_oracle_adjoint(lbem, D, shape, every, variant):
     p = _small(D, shape, 3, 30)
     obs = 0.05 * np.random.default_rng(4).standard_normal((p.rec_site.size, p.nsteps))
     s = lbem.Solver(shape)
-    lbem.lbem_set_variant(s.h, variant)  # 3D: 0 = four sites per lane, 1 = one site per thread
+    lbem.lbem_set_variant(s.h, variant)  # 3D: 0 = four sites per lane, 1 = one site per thread, 2 = capped
     eps = torch.tensor(np.asarray(p.eps_r, np.float32), device="cuda", requires_grad=True)
     tr = receiver_traces(eps, s, p, checkpoint_every=every)
     L = misfit(tr, torch.tensor(obs, device="cuda"))
