@@ -5,13 +5,15 @@ s seeded smoothed random field, sigma = 20 cells, seed 2), Ricker point
 current at the centre (~20 cells per local wavelength), 64 receivers, 5000
 time steps, FP32 storage.  One benchmark step is one full pass of the hot
 path over that input: medium upload, initial state, 5000 fused
-stream-collide steps with the source and receivers, field extraction,
+stream-collide steps with the source and receivers (2500 launches of the
+two-step kernel, the library's default for this case), field extraction,
 receiver traces and the FP64 diagnostics.  The distributions (2 x 336 MB)
 are larger than L2, so no flush is needed between steps.
 
 Metric: Mlups (10^6 lattice-site updates per second) = sites x 5000 / time.
-The stream-collide kernel's roofline is HBM bandwidth: 44 algorithmic bytes
-per site per step (5 populations read + 5 written in FP32, plus c_L^2).
+The stream-collide kernels are bound by HBM bandwidth: 44 algorithmic bytes
+per site per launch (5 populations read + 5 written in FP32, plus c_L^2),
+whether a launch advances one step or two.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a
 bounded sample of the same workload.  With torchrun (N > 1) every rank runs
@@ -36,7 +38,7 @@ BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it is now built, keyed by
 # (workload, storage, variant); the capture and its command are summarised in profiles/.  Only reported for
 # the kernel that was captured.
-NCU_TRAFFIC = {("het2d_4096", "f32", 0): 402.705920e6 + 281.868288e6}
+NCU_TRAFFIC = {}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -169,8 +171,9 @@ def _time_run(lbem, torch, s, p, nsteps, stream, passes=1):
 
 
 def other_forms(lbem, torch, p, peak, stream):
-    """Mlups and HBM roofline of the other forms on this GPU: 16-bit storage of the same workload, the
-    256-media batch (2000 steps, one graph-captured launch per step) and the 192^3 3D forward (1000 steps)."""
+    """Mlups and HBM roofline of the other forms on this GPU: 16-bit storage and single-step launches of the
+    same workload, the 256-media batch (2000 steps, one graph-captured launch per step), the 192^3 3D forward
+    (1000 steps) and the 3D adjoint."""
     out = {}
     n = int(np.prod(p.shape))
     for st in ("f16", "bf16", "i16b"):
@@ -181,6 +184,15 @@ def other_forms(lbem, torch, p, peak, stream):
         gbs = BYTES_PER_SITE[st] * n / (per * 1e-3) / 1e9
         out[st] = {"mlups": n * p.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                    "frac": gbs / peak, "bytes_per_site": BYTES_PER_SITE[st], "variant": v}
+    # single-step launches (same workload, FP32): the fastest single-step kernel, 44 B/site per step
+    s = lbem.Solver(p.shape, stream=stream.cuda_stream)
+    lbem.lbem_set_temporal_blocking(s.h, 1, -1)
+    ms, v = _time_run(lbem, torch, s, p, p.nsteps, stream)
+    s.close()
+    per = ms / p.nsteps
+    gbs = 44 * n / (per * 1e-3) / 1e9
+    out["f32_single_step"] = {"mlups": n * p.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                              "frac": gbs / peak, "bytes_per_site": 44, "variant": v}
     probs = W.batch_2d(256, nsteps=2000)
     ss = []
     for q in probs:
@@ -361,7 +373,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--variant", type=int, default=None, help="force a launch shape of the stream-collide kernel")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force a launch shape of the single-step stream-collide kernel (every step single)")
+    ap.add_argument("--steps-per-pass", type=int, default=None, choices=[1, 2],
+                    help="1: single-step launches; 2: two steps per launch (the library default where it applies)")
+    ap.add_argument("--tile-shape", type=int, default=None, help="tile shape of the two-step kernel")
     ap.add_argument("--no-forms", action="store_true", help="skip the 16-bit, batched and 3D forms")
     args = ap.parse_args()
     rank, world = dist_setup(args)
@@ -398,12 +414,17 @@ def main():
     lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
     lbem.lbem_set_receivers(h, p.rec_site, p.rec_comp, nsteps)
     variant = lbem.lbem_get_variant(h)[0]
+    if args.variant is not None:  # a single-step launch shape: every step runs it
+        lbem.lbem_set_temporal_blocking(h, 1, -1)
+    if args.steps_per_pass is not None or args.tile_shape is not None:
+        lbem.lbem_set_temporal_blocking(h, args.steps_per_pass or 2, -1 if args.tile_shape is None else args.tile_shape)
     if args.autotune:
         lbem.lbem_set_fields(h)
         variant = lbem.lbem_autotune(h, 50)
     if args.variant is not None:
         lbem.lbem_set_variant(h, args.variant)
         variant = args.variant
+    spp, tile_shape, _ = lbem.lbem_get_temporal_blocking(h)
     nsite = s.nsite
     E_d = torch.empty(3 * nsite, dtype=torch.float32, device="cuda")
     B_d = torch.empty_like(E_d)
@@ -438,18 +459,25 @@ def main():
     total_ms = start.elapsed_time(stop)
     total_ms = dist_max(total_ms, world)
     kern_ms = [a.elapsed_time(b) for a, b in evs]
-    ms_per_launch = float(np.mean(kern_ms)) / nsteps
+    # stream-collide launches per run: pairs of steps (plus an odd last step) or single steps
+    step_launches = nsteps // 2 + nsteps % 2 if spp == 2 else nsteps
+    ms_per_launch = float(np.mean(kern_ms)) / step_launches
     ms_per_step = total_ms / args.steps
     value = world * nsite * nsteps / (ms_per_step * 1e-3) / 1e6
 
     peak, peak_kind = measured_peak_gbs()
     bps = BYTES_PER_SITE[args.storage] if p.D == 2 else 172
     achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
-    kname = f"step2d<{args.storage}>" if p.D == 2 else "step3d"
-    traffic = NCU_TRAFFIC.get((args.workload, args.storage, variant)) if args.lb_steps is None else None
+    if spp == 2:
+        kname, kid = f"step2d_tb2 (tile shape {tile_shape}, two steps per launch)", f"tb2-{tile_shape}"
+    else:
+        kname = (f"step2d<{args.storage}>" if p.D == 2 else "step3d") + f" (variant {variant})"
+        kid = variant
+    traffic = NCU_TRAFFIC.get((args.workload, args.storage, kid)) if args.lb_steps is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": f"{kname} (variant {variant})",
-                "algorithmic_bytes_per_site": bps, "ms_per_launch": ms_per_launch, "peak_kind": peak_kind}
+                "traffic": traffic, "kernel": kname, "steps_per_launch": spp,
+                "algorithmic_bytes_per_site_per_launch": bps, "ms_per_launch": ms_per_launch,
+                "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -485,7 +513,7 @@ def main():
         cpu = cpu_baseline(p)
     s.close()
     if rank == 0:
-        launches = args.steps * (nsteps + 6 + (1 if args.storage == "f16" else 0))
+        launches = args.steps * (step_launches + 6 + (1 if args.storage == "f16" else 0))
         line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32-math/{args.storage}-storage",

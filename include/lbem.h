@@ -83,7 +83,8 @@ void lbem_destroy(lbem_t *h);
 /* Replace the stream the handle enqueues on (cudaStream_t as void*). */
 lbem_status lbem_set_stream(lbem_t *h, void *stream);
 
-/* Wait for all work enqueued on the handle's stream; reports deferred device errors. */
+/* Wait for all work enqueued on the handle's stream; reports deferred device errors, and LBEM_ERR_TIMEOUT
+ * if a shared-memory tile load of the two-step kernel (lbem_set_temporal_blocking) gave up waiting. */
 lbem_status lbem_sync(lbem_t *h);
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -141,6 +142,20 @@ lbem_status lbem_step(lbem_t *h, int nsteps);
  * max_growth (> 1) since the previous check.  every = 0 switches it off.  The scheme is neutral (no
  * growth without sources), so a jump means an over-driven source or a corrupted state. */
 lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
+
+/* Temporal blocking (2D, LBEM_F32 storage, uniform mu; otherwise ignored).  With steps_per_pass = 2 (the
+ * default) lbem_step advances pairs of steps with one kernel that stages a tile plus a two-site halo in
+ * shared memory and performs both steps there, so the state crosses HBM once per two steps (44 instead of
+ * 88 bytes per site and step pair); an odd last step is a single step.  Results are bit-identical to single
+ * steps.  1 makes every step a single-step launch (the kernel lbem_set_variant selects).  tile_shape
+ * selects the tile (128 sites wide) height, threads per CTA and CTAs per SM: 0 = 6 rows, 256 threads, 5
+ * per SM (the default, also -1); 1 = 8 rows, 320, 3; 2 = 8 rows, 352, 3; 3 = 10 rows, 384, 3; 4 = 5 rows,
+ * 224, 5; 5 = 4 rows, 192, 6; 6 = 14 rows, 512, 2.  LBEM_ERR_ARG for other values. */
+lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
+
+/* Steps per launch in effect (2 only where the two-step kernel is enabled and applies), the tile shape (as
+ * set or autotuned) and the number of tile shapes; any pointer may be NULL. */
+lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int *tile_shape, int *nshapes);
 
 /* Use (on != 0) or not CUDA-graph replay of runs of steps in lbem_step. */
 lbem_status lbem_set_graphs(lbem_t *h, int on);
@@ -227,7 +242,10 @@ lbem_status lbem_adjoint(lbem_t *h, const float *trace_cot, float *grad_eps, dou
 
 /* Time each launch shape of the stream-collide kernel on this handle for
  * trial_steps steps (the state is saved and restored) and keep the fastest.
- * *best (may be NULL) receives the chosen variant id. */
+ * *best (may be NULL) receives the chosen variant id.  Where two steps per
+ * launch apply and are enabled (lbem_set_temporal_blocking), every tile shape
+ * of that kernel is timed too; the fastest is kept, and two-step launches stay
+ * on only if they beat the best single-step kernel. */
 lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best);
 lbem_status lbem_set_variant(lbem_t *h, int variant);
 lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);

@@ -49,33 +49,7 @@ __device__ __forceinline__ void pull2d(const PopBuf &in, const Grid &G, int row,
     if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, C::load1(in, 3, row, 0));  // periodic wrap at x = nx-1
 }
 
-// Collision of one site (closed form above).  shat = S^ (zero without sources).
-struct Out5 {
-    float o0, o1, o2, o3, o4;
-};
-__device__ __forceinline__ Out5 collide2d(float g0, float g1, float g2, float g3, float g4, float cl, float shat) {
-    const float s = ((g0 + g1) + (g2 + g3)) + g4;
-    const float L = cl * s;
-    const float w0 = 1.f - 2.f * cl;
-    const float Tm = -0.5f * cl * shat;
-    const float T0 = -w0 * shat;
-    Out5 o;
-    o.o1 = (L - g3) + Tm;
-    o.o3 = (L - g1) + Tm;
-    o.o2 = (L - g4) + Tm;
-    o.o4 = (L - g2) + Tm;
-    o.o0 = (2.f * w0 * s - g0) + T0;
-    return o;
-}
-
-__device__ __forceinline__ float field2d(int comp, float cl, float s, float bx, float by) {
-    switch (comp) {
-        case 2: return -cl * s;  // E_z = -Lambda_xy
-        case 3: return bx;
-        case 4: return by;
-        default: return 0.f;  // E_x, E_y, B_z are not representable in 2D
-    }
-}
+// collide2d and field2d (the per-site update and the receiver readout) are in lbem_internal.cuh.
 
 template <int ST, bool MU, int R>
 __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {

@@ -122,6 +122,37 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
     return launch_step_3d(a, h->has_mu, variant, h->stream);
 }
 
+// what a captured graph depends on besides t, nsteps and the buffer: kernel variant and two-step shape
+static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16 + h->tb_shape + 1; }
+
+static bool two_step_ok(const lbem_t *h) {
+    return h->tblock == 2 && h->dim == 2 && h->storage == LBEM_F32 && !h->has_mu;
+}
+
+// Enqueue nsteps steps starting from buffer `cur` at time t0: pairs of steps with the two-step kernel
+// when enabled, single steps otherwise; returns the buffer holding the final state in *cur_out.
+static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {
+    int n = 0;
+    if (two_step_ok(h)) {
+        for (; n + 2 <= nsteps; n += 2) {
+            StepArgs a = step_args(h, cur);
+            a.t = t0 + n;
+            cudaError_t e = launch_step_2d_tb2(a, h->tb_shape, h->stream);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    }
+    for (; n < nsteps; n++) {
+        StepArgs a = step_args(h, cur);
+        a.t = t0 + n;
+        cudaError_t e = launch_step(h, a, h->variant);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    *cur_out = cur;
+    return cudaSuccess;
+}
+
 static void drop_graph(lbem_t *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -265,6 +296,8 @@ lbem_status lbem_sync(lbem_t *h) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     LBEM_CUDA(cudaGetLastError());
+    if (tb2_take_timeouts())
+        return fail(LBEM_ERR_TIMEOUT, "lbem_sync: a tile load of the two-step kernel did not complete in 2 s");
     return LBEM_OK;
 }
 
@@ -446,43 +479,49 @@ static lbem_status step_run(lbem_t *h, int nsteps) {
         return fail(LBEM_ERR_STATE, "lbem_step: CUDA graphs need a non-default stream (lbem_set_stream)");
     if (h->use_graphs) {
         if (!(h->graph && h->graph_t0 == h->t && h->graph_steps == nsteps && h->graph_cur == h->cur &&
-              h->graph_variant == h->variant)) {
+              h->graph_variant == graph_key(h))) {
             drop_graph(h);
             LBEM_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            int cur = h->cur;
-            for (int n = 0; n < nsteps; n++) {
-                StepArgs a = step_args(h, cur);
-                a.t = h->t + n;
-                cudaError_t e = launch_step(h, a, h->variant);
-                if (e != cudaSuccess) {
-                    cudaGraph_t g;
-                    cudaStreamEndCapture(h->stream, &g);
-                    if (g) cudaGraphDestroy(g);
-                    return cuda_fail(e, "lbem_step (capture)");
-                }
-                cur ^= 1;
+            int cur_end = h->cur;
+            cudaError_t e = enqueue_steps(h, h->cur, h->t, nsteps, &cur_end);
+            if (e != cudaSuccess) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(h->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(e, "lbem_step (capture)");
             }
+            h->graph_cur_end = cur_end;
             cudaGraph_t g = nullptr;
             LBEM_CUDA(cudaStreamEndCapture(h->stream, &g));
-            cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+            e = cudaGraphInstantiate(&h->graph, g, 0);
             cudaGraphDestroy(g);
             LBEM_CUDA(e);
             h->graph_t0 = h->t;
             h->graph_steps = nsteps;
             h->graph_cur = h->cur;
-            h->graph_variant = h->variant;
+            h->graph_variant = graph_key(h);
         }
         LBEM_CUDA(cudaGraphLaunch(h->graph, h->stream));
-        h->cur ^= (nsteps & 1);
+        h->cur = h->graph_cur_end;
         h->t += nsteps;
         return LBEM_OK;
     }
-    for (int n = 0; n < nsteps; n++) {
-        StepArgs a = step_args(h, h->cur);
-        LBEM_CUDA(launch_step(h, a, h->variant));
-        h->cur ^= 1;
-        h->t++;
-    }
+    int cur_end = h->cur;
+    LBEM_CUDA(enqueue_steps(h, h->cur, h->t, nsteps, &cur_end));
+    h->cur = cur_end;
+    h->t += nsteps;
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (steps_per_pass != 1 && steps_per_pass != 2)
+        return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: steps_per_pass must be 1 or 2");
+    if (tile_shape < -1 || tile_shape >= tb2_nshapes())
+        return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: tile_shape out of range");
+    h->tblock = steps_per_pass;
+    h->tb_shape = tile_shape < 0 ? 0 : tile_shape;
+    drop_graph(h);
     return LBEM_OK;
 }
 
@@ -585,6 +624,8 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
 lbem_status lbem_check_guards(lbem_t *h) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    if (tb2_take_timeouts())
+        return fail(LBEM_ERR_TIMEOUT, "lbem_check_guards: a tile load of the two-step kernel did not complete");
     std::vector<unsigned char> buf(2 * GUARD);
     for (const auto &g : h->guarded) {
         const char *u = static_cast<const char *>(g.user);
@@ -659,6 +700,38 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
             best_v = v;
         }
     }
+    // two steps per launch: time every tile shape; keep it only if it beats the best single-step kernel
+    const float single_ms_per_step = best_ms / trial_steps;
+    int best_shape = h->tb_shape, best_tblock = h->tblock;
+    if (h->tblock == 2 && two_step_ok(h)) {
+        const int npair = trial_steps / 2 > 0 ? trial_steps / 2 : 1;
+        float best_pair = 1e30f;
+        for (int shape = 0; shape < tb2_nshapes() && st == LBEM_OK; shape++) {
+            int cur = cur0;
+            for (int rep = 0; rep < 2 && st == LBEM_OK; rep++) {
+                cudaEventRecord(e0, h->stream);
+                for (int n = 0; n < npair; n++) {
+                    StepArgs a = step_args(h, cur);
+                    a.evt.rowptr = nullptr;
+                    cudaError_t e = launch_step_2d_tb2(a, shape, h->stream);
+                    if (e != cudaSuccess) {
+                        st = cuda_fail(e, "lbem_autotune");
+                        break;
+                    }
+                    cur ^= 1;
+                }
+                cudaEventRecord(e1, h->stream);
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_pair) {
+                best_pair = ms;
+                best_shape = shape;
+            }
+        }
+        best_tblock = best_pair / (2 * npair) < single_ms_per_step ? 2 : 1;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->cur = cur0;
@@ -667,8 +740,18 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
     cudaFree(save);
     if (st != LBEM_OK) return st;
     h->variant = best_v;
+    h->tb_shape = best_shape;
+    h->tblock = best_tblock;
     drop_graph(h);
     if (best) *best = best_v;
+    return LBEM_OK;
+}
+
+lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int *tile_shape, int *nshapes) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (steps_per_pass) *steps_per_pass = two_step_ok(h) ? 2 : 1;
+    if (tile_shape) *tile_shape = h->tb_shape;
+    if (nshapes) *nshapes = tb2_nshapes();
     return LBEM_OK;
 }
 

@@ -208,6 +208,36 @@ __device__ __forceinline__ void set(float4 &v, int j, float a) {
     else v.w = a;
 }
 
+// ------------------------------------------------------------------ 2D site update
+// Collision of one D2Q5 site at tau = dt/2 (Eqs. 8 and 17 in closed form, derived in kernels2d.cu), used by
+// every 2D kernel so that all launch shapes compute bit-identical results.  shat = S^ (zero without sources).
+struct Out5 {
+    float o0, o1, o2, o3, o4;
+};
+__device__ __forceinline__ Out5 collide2d(float g0, float g1, float g2, float g3, float g4, float cl, float shat) {
+    const float s = ((g0 + g1) + (g2 + g3)) + g4;
+    const float L = cl * s;
+    const float w0 = 1.f - 2.f * cl;
+    const float Tm = -0.5f * cl * shat;
+    const float T0 = -w0 * shat;
+    Out5 o;
+    o.o1 = (L - g3) + Tm;
+    o.o3 = (L - g1) + Tm;
+    o.o2 = (L - g4) + Tm;
+    o.o4 = (L - g2) + Tm;
+    o.o0 = (2.f * w0 * s - g0) + T0;
+    return o;
+}
+
+__device__ __forceinline__ float field2d(int comp, float cl, float s, float bx, float by) {
+    switch (comp) {
+        case 2: return -cl * s;  // E_z = -Lambda_xy
+        case 3: return bx;
+        case 4: return by;
+        default: return 0.f;  // E_x, E_y, B_z are not representable in 2D
+    }
+}
+
 // ------------------------------------------------------------------ site events
 // Sources and receivers, sorted by row, with a CSR row pointer.  Event:
 //   x     : column
@@ -288,9 +318,11 @@ struct lbem {
     bool use_graphs = false;
     cudaGraphExec_t graph = nullptr;
     long long graph_t0 = -1;
-    int graph_steps = 0, graph_cur = -1, graph_variant = -1;
+    int graph_steps = 0, graph_cur = -1, graph_variant = -1, graph_cur_end = 0;
     // tuning
     int variant = 0;
+    int tblock = 2;  // steps per pass (lbem_set_temporal_blocking)
+    int tb_shape = 0;  // tile shape of the two-step kernel
     // watchdog (lbem_set_watchdog)
     int wd_every = 0;
     double wd_growth = 0.0, wd_last = -1.0;
@@ -323,6 +355,10 @@ StepArgs step_args(const lbem_t *h, int cur_in);
 // 2D (kernels2d.cu)
 int nvariants_2d();
 cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int variant, cudaStream_t s);
+// two steps per launch (tblock.cu): FP32 storage, uniform mu
+int tb2_nshapes();
+bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag
+cudaError_t launch_step_2d_tb2(const StepArgs &a, int shape, cudaStream_t s);
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);

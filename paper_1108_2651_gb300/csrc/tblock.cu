@@ -1,0 +1,487 @@
+// Two time steps per pass (temporal blocking), 2D, FP32 storage, uniform mu.
+//
+// A persistent CTA takes tiles of 128 x TBY sites in turn.  For each it loads
+// the post-collision state at t of the tile plus a halo of 2 sites (one per
+// step of the pull stencil) and c_L^2 into shared memory, computes step t on
+// the tile plus a ring of 1 site (Eqs. 17-18, the same site update as the
+// single-step kernels), then step t+1 on the tile from those values, and writes
+// only the final post-collision state.  The loads of the next tile (TMA boxes,
+// or 16-byte asynchronous copies where the window wraps periodically) run
+// while step t+1 of the current one is computed, and several CTAs share an SM.
+//
+// Each population plane is staged shifted by its pull offset in y, so that
+// row r of every staged plane holds exactly what the update of tile row r
+// pulls (the moving populations g2 from the row above and g4 from the row
+// below), and a plane keeps only the rows that are read: TBY + 2 rows of each
+// plane at t, TBY rows of each at t + 1.  A lane updates 4 consecutive sites
+// of a row with 16-byte shared-memory accesses; one warp covers a tile row.
+//
+// HBM traffic per two site updates is 24 bytes read (5 populations and c_L^2)
+// and 20 written, against 88 for two single steps.  The arithmetic of each
+// site update is that of collide2d, so the results are bit-identical to two
+// single steps.  Sources act at both steps on every site computed; receivers
+// record at the owned sites only.
+#include <cuda.h>
+#include <string.h>
+
+#include "lbem_internal.cuh"
+
+namespace lbk {
+
+constexpr int TBX = 128;     // tile width: one warp of 4-site lanes
+constexpr int TW = TBX + 8;  // staged columns x0-4 .. x0+TBX+3 (16-byte aligned); column j <-> x0-4+j
+
+// Row shift of the staged planes: plane p row r of the t stage holds global row y0 - 1 + r + in_shift(p), and
+// plane p row j of the t+1 stage holds global row y0 + j + in_shift(p).
+__device__ __host__ constexpr int in_shift(int p) { return p == 2 ? -1 : p == 4 ? 1 : 0; }
+
+// Periodic index, cheap when v is already in range (the common case).
+__device__ __forceinline__ int wrapi(int v, int n) {
+    if ((unsigned)v < (unsigned)n) return v;
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Source current at global site (x, y) and time t, and the receiver write of the pre-collision
+// fields (only when `owned`).  Returns S^ (zero where there is no source).
+__device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
+                                             float g1, float g2, float g3, float g4, float cl) {
+    float shat = 0.f;
+    if (!a.evt.rowptr) return shat;
+    const int e0 = __ldg(a.evt.rowptr + y), e1 = __ldg(a.evt.rowptr + y + 1);
+    for (int e = e0; e < e1; e++) {
+        const Event ev = a.evt.ev[e];
+        if (ev.x != x) continue;
+        if (ev.kind == 0) {
+            if (ev.comp == 2 && t < a.evt.nt) shat -= __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
+        } else if (owned && t < a.evt.cap) {
+            const float s = ((g0 + g1) + (g2 + g3)) + g4;
+            a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+        }
+    }
+    return shat;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tb_cpa4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void tb_cpa16(float *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// Shared-memory layout of a CTA (floats; regions start on 128-byte boundaries), then one mbarrier.
+template <int TBY>
+struct TbGeom {
+    static constexpr int R = TBY + 2;  // staged rows per plane at t (tile rows y0-1 .. y0+TBY), and of c_L^2
+    static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
+    // plane strides (each staged plane at t is a TMA destination: 128-byte aligned)
+    static constexpr int IN_PL = up32(R * TW), P_PL = TBY * TW;
+    static constexpr int IN_SZ = up32(5 * IN_PL), CL_SZ = up32(R * TW), P_SZ = up32(5 * P_PL);
+    static constexpr int SZ = IN_SZ + CL_SZ + P_SZ;
+    static constexpr size_t BYTES = sizeof(float) * SZ + sizeof(unsigned long long);
+    static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * R * TW;
+};
+
+// Asynchronous copies of one tile's window with periodic wrap (16 bytes per copy when every group of 4
+// columns stays contiguous after the wrap, else 4).
+template <int TBY>
+__device__ __forceinline__ void tb_issue(const StepArgs &a, int x0, int y0, float *IN, float *CL, int nt) {
+    constexpr int R = TbGeom<TBY>::R, PL = TbGeom<TBY>::IN_PL, Q = TW / 4;
+    const Grid &G = a.g;
+    const float *in = static_cast<const float *>(a.in.data);
+    const int tid = threadIdx.x;
+    if (((x0 - 4 >= 0) && (x0 + TBX + 4 <= G.nx)) || (G.nx & 3) == 0) {
+        for (int k = tid; k < 6 * R * Q; k += nt) {
+            const int pr = k / Q, q = k - pr * Q;  // pr = plane * R + row; plane 5 is c_L^2
+            const int pl = pr / R, r = pr - pl * R;
+            const int gx = wrapi(x0 - 4 + 4 * q, G.nx);
+            if (pl < 5) {
+                const int gy = wrapi(y0 - 1 + r + in_shift(pl), G.ny);
+                tb_cpa16(IN + pl * PL + r * TW + 4 * q, in + pl * G.plane + (long long)gy * G.pitch + gx);
+            } else {
+                const int gy = wrapi(y0 - 1 + r, G.ny);
+                tb_cpa16(CL + r * TW + 4 * q, a.med.cL2 + (long long)gy * G.pitch + gx);
+            }
+        }
+    } else {  // columns wrap inside a group: element copies
+        for (int k = tid; k < 6 * R * TW; k += nt) {
+            const int pr = k / TW, c = k - pr * TW;
+            const int pl = pr / R, r = pr - pl * R;
+            const int gx = wrapi(x0 - 4 + c, G.nx);
+            if (pl < 5) {
+                const int gy = wrapi(y0 - 1 + r + in_shift(pl), G.ny);
+                tb_cpa4(IN + pl * PL + r * TW + c, in + pl * G.plane + (long long)gy * G.pitch + gx);
+            } else {
+                const int gy = wrapi(y0 - 1 + r, G.ny);
+                tb_cpa4(CL + r * TW + c, a.med.cL2 + (long long)gy * G.pitch + gx);
+            }
+        }
+    }
+}
+
+// ---- tensor-memory-accelerator (TMA) window loads for tiles whose window needs no periodic wrap
+
+__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *m, int x, int y, int z, unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(m), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(float *dst, const CUtensorMap *m, int x, int y, unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(smem_u32(dst)), "l"(m), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ int g_tb_timeouts = 0;  // set when a bounded wait of the two-step kernel gave up
+
+// Wait for phase `parity` of the mbarrier, giving up after about 2 s of device time.
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (unsigned it = 0;; it++) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63) {
+            unsigned long long t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+            if (t1 - t0 > 2000000000ull) return false;
+        }
+    }
+}
+
+template <int TBY>
+__device__ __forceinline__ bool tb_interior(int x0, int y0, const Grid &G) {
+    return x0 - 4 >= 0 && x0 + TBX + 4 <= G.nx && y0 - 2 >= 0 && y0 + TBY + 2 <= G.ny;
+}
+
+// Start the loads of one tile's window: one thread issues six TMA copies (each population plane as a
+// (TBY+2) x (TBX+8) box at its row shift, and c_L^2) for interior tiles; every thread issues its share of the
+// asynchronous copies otherwise.
+template <int TBY>
+__device__ __forceinline__ void tb_load(const StepArgs &a, int x0, int y0, float *IN, float *CL, unsigned mbar,
+                                        bool tma, const CUtensorMap *tmIn, const CUtensorMap *tmCL, int nt) {
+    if (tma) {
+        if (threadIdx.x == 0) {
+            // earlier generic-proxy accesses of the window (ordered by the preceding barrier) before the
+            // asynchronous-proxy writes
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
+                         "r"(TbGeom<TBY>::TMA_BYTES)
+                         : "memory");
+#pragma unroll
+            for (int p = 0; p < 5; p++)
+                tma_load_3d(IN + p * TbGeom<TBY>::IN_PL, tmIn, x0 - 4, y0 - 1 + in_shift(p), p, mbar);
+            tma_load_2d(CL, tmCL, x0 - 4, y0 - 1, mbar);
+        }
+    } else {
+        tb_issue<TBY>(a, x0, y0, IN, CL, nt);
+    }
+}
+
+// Whether tile rows y0-1 .. y0+TBY may hold a source or receiver (if not, the usual case, no per-site lookups).
+template <int TBY>
+__device__ __forceinline__ bool tb_events(const StepArgs &a, int y0) {
+    const Grid &G = a.g;
+    return a.evt.rowptr && !(y0 >= 1 && y0 + TBY + 1 <= G.ny &&
+                             __ldg(a.evt.rowptr + y0 - 1) == __ldg(a.evt.rowptr + y0 + TBY + 1));
+}
+
+// Populations pulled by four consecutive sites at shared row `row`, column c (a multiple of 4) of a shifted
+// stage S with plane stride PL: g0, g2, g4 from columns c.., g1 from c-1.., g3 from c+1.. (Eq. 17).
+struct Pull4 {
+    float4 g0, g1, g2, g3, g4;
+    __device__ __forceinline__ Pull4(const float *S, int PL, int row, int c) {
+        const float *r = S + row * TW + c;
+        g0 = lds4(r);
+        const float4 l1 = lds4(r + PL - 4), m1 = lds4(r + PL);
+        g1 = make_float4(l1.w, m1.x, m1.y, m1.z);
+        g2 = lds4(r + 2 * PL);
+        const float4 m3 = lds4(r + 3 * PL), h3 = lds4(r + 3 * PL + 4);
+        g3 = make_float4(m3.y, m3.z, m3.w, h3.x);
+        g4 = lds4(r + 4 * PL);
+    }
+};
+
+#define TB_COMP(v, k) (k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w)
+#define TB_SET(v, k, val) (k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w) = (val)
+
+// Four site updates (collide2d each) at global row gy, columns x0+4*lane.., time t.
+template <bool EV>
+__device__ __forceinline__ void tb_update4(const StepArgs &a, const Pull4 &g, float4 cl, int x0, int gy, long long t,
+                                           bool owned_row, float4 &o0, float4 &o1, float4 &o2, float4 &o3,
+                                           float4 &o4) {
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float q0 = TB_COMP(g.g0, k), q1 = TB_COMP(g.g1, k), q2 = TB_COMP(g.g2, k), q3 = TB_COMP(g.g3, k),
+                    q4 = TB_COMP(g.g4, k), ck = TB_COMP(cl, k);
+        float shat = 0.f;
+        if (EV) {
+            const int gx = x0 + 4 * lane + k;
+            shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, owned_row && gx < G.nx && gy < G.ny, q0, q1,
+                               q2, q3, q4, ck);
+        }
+        const Out5 o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        TB_SET(o0, k, o.o0);
+        TB_SET(o1, k, o.o1);
+        TB_SET(o2, k, o.o2);
+        TB_SET(o3, k, o.o3);
+        TB_SET(o4, k, o.o4);
+    }
+}
+
+// Step t on tile rows y0-1 .. y0+TBY (stage row py <-> global row y0-1+py), one warp per row, storing each
+// plane's result only where step t+1 reads it (planes 0, 1, 3 at stage row py-1, plane 2 at py, plane 4 at
+// py-2); then the ring sites x0-1 (plane 1 only) and x0+TBX (plane 3 only) of rows y0 .. y0+TBY-1.  Also
+// reads into clb the c_L^2 of the warp's step-(t+1) row, as the c_L^2 stage is reloaded before step t+1.
+template <int TBY, int NT, bool EV>
+__device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, const float *CL, float *P, int x0,
+                                          int y0, long long t, float4 &clb) {
+    using Gm = TbGeom<TBY>;
+    constexpr int R = Gm::R, NW = NT / 32, PL = Gm::P_PL;
+    const Grid &G = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = 4 + 4 * lane;
+    if (warp < TBY) clb = lds4(CL + (warp + 1) * TW + c);
+    for (int py = warp; py < R; py += NW) {
+        const Pull4 g(IN, Gm::IN_PL, py, c);
+        const float4 cl = lds4(CL + py * TW + c);
+        float4 o0, o1, o2, o3, o4;
+        tb_update4<EV>(a, g, cl, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2, o3, o4);
+        float *Pr = P + c;
+        if (py >= 1 && py <= TBY) {
+            sts4(Pr + 0 * PL + (py - 1) * TW, o0);
+            sts4(Pr + 1 * PL + (py - 1) * TW, o1);
+            sts4(Pr + 3 * PL + (py - 1) * TW, o3);
+        }
+        if (py < TBY) sts4(Pr + 2 * PL + py * TW, o2);
+        if (py >= 2) sts4(Pr + 4 * PL + (py - 2) * TW, o4);
+    }
+    // ring sites go to the warps with one row fewer (from warp R % NW on)
+    int k0 = tid - 32 * (R % NW);
+    if (k0 < 0) k0 += NT;
+    for (int k = k0; k < 2 * TBY; k += NT) {
+        const int py = (k >> 1) + 1, cc = (k & 1) ? TBX + 4 : 3;
+        const float *r = IN + py * TW + cc;
+        const float q0 = r[0], q1 = r[Gm::IN_PL - 1], q2 = r[2 * Gm::IN_PL], q3 = r[3 * Gm::IN_PL + 1],
+                    q4 = r[4 * Gm::IN_PL];
+        const float ck = CL[py * TW + cc];
+        float shat = 0.f;
+        if (EV)
+            shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3, q4,
+                               ck);
+        const Out5 o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        if (k & 1)
+            P[3 * PL + (py - 1) * TW + cc] = o.o3;
+        else
+            P[1 * PL + (py - 1) * TW + cc] = o.o1;
+    }
+}
+
+// Step t+1 on tile row y0 + warp from the t+1 stage, written as 16-byte streaming stores.
+template <int TBY, bool EV>
+__device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, float4 clb, int x0, int y0,
+                                          long long t) {
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31, oy = threadIdx.x >> 5;
+    const int gy = y0 + oy;
+    if (oy >= TBY || gy >= G.ny) return;
+    const int c = 4 + 4 * lane;
+    const Pull4 g(P, TbGeom<TBY>::P_PL, oy, c);
+    float4 o0, o1, o2, o3, o4;
+    tb_update4<EV>(a, g, clb, x0, gy, t + 1, true, o0, o1, o2, o3, o4);
+    if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
+        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)gy * G.pitch + x0 +
+                                               4 * lane);
+        const long long pl4 = G.plane / 4;
+        __stcs(o, o0);
+        __stcs(o + pl4, o1);
+        __stcs(o + 2 * pl4, o2);
+        __stcs(o + 3 * pl4, o3);
+        __stcs(o + 4 * pl4, o4);
+    }
+}
+#undef TB_SET
+#undef TB_COMP
+
+// One persistent CTA per SM slot; CTA b takes tiles b, b + gridDim.x, ... (row-major over the tile grid).
+// The window of the next tile is loaded while step t+1 of the current one is computed.
+template <int TBY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    step2d_tb2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
+               int use_tma, int ntx, int nty, int dq, int dr) {
+    static_assert(NT / 32 >= TBY, "one warp per row of step t+1");
+    using Gm = TbGeom<TBY>;
+    extern __shared__ __align__(1024) float sm[];
+    float *IN = sm;              // [5][TBY+2][TW], shifted planes at t
+    float *CL = sm + Gm::IN_SZ;  // [TBY+2][TW]
+    float *P = CL + Gm::CL_SZ;   // [5][TBY][TW], shifted planes at t+1
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(sm + Gm::SZ);
+    const Grid &G = a.g;
+    const int tid = threadIdx.x;
+    if (smem_u32(sm) & 127) use_tma = 0;  // TMA destinations here are 128-byte aligned; else element copies
+    int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    if (ty >= nty) return;
+    const unsigned mbar = smem_u32(mb);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;  // next phase of the mbarrier to wait for
+    tb_load<TBY>(a, tx * TBX, ty * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
+                 &tmCL, NT);
+    asm volatile("cp.async.commit_group;\n" ::);
+    bool events = tb_events<TBY>(a, ty * TBY);
+    const long long t = a.t;
+    while (ty < nty) {
+        int ntx_ = tx + dr, nty_ = ty + dq;  // next tile of this CTA
+        if (ntx_ >= ntx) {
+            ntx_ -= ntx;
+            nty_++;
+        }
+        const bool has_next = nty_ < nty;
+        const bool events_next = has_next && tb_events<TBY>(a, nty_ * TBY);  // latency hidden behind this tile
+        const int x0 = tx * TBX, y0 = ty * TBY;
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        bool ok = true;
+        if (use_tma && tb_interior<TBY>(x0, y0, G)) {
+            ok = mbar_wait(mbar, parity);
+            parity ^= 1u;
+        }
+        // every thread's copies have landed, and step t+1 of the previous tile is done with P
+        if (__syncthreads_or(!ok)) {  // a TMA load never completed: flag it, let it drain (bounded), stop
+            if (tid == 0) atomicExch(&g_tb_timeouts, 1);
+            mbar_wait(mbar, parity ^ 1u);
+            return;
+        }
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (events)
+            tb_step_a<TBY, NT, true>(a, IN, CL, P, x0, y0, t, clb);
+        else
+            tb_step_a<TBY, NT, false>(a, IN, CL, P, x0, y0, t, clb);
+        __syncthreads();
+        if (has_next)  // the t stage and c_L^2 are free: start the loads of the next tile
+            tb_load<TBY>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G),
+                         &tmIn, &tmCL, NT);
+        asm volatile("cp.async.commit_group;\n" ::);
+        if (events)
+            tb_step_b<TBY, true>(a, P, clb, x0, y0, t);
+        else
+            tb_step_b<TBY, false>(a, P, clb, x0, y0, t);
+        tx = ntx_;
+        ty = nty_;
+        events = events_next;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps of the populations ([5][ny][pitch] floats, box: one plane of TBY+2 rows) and c_L^2
+// ([ny][pitch], box: TBY+2 rows); false if unavailable.
+template <int TBY>
+static bool make_maps(const StepArgs &a, CUtensorMap *mIn, CUtensorMap *mCL) {
+    constexpr int R = TbGeom<TBY>::R;
+    EncodeTiled fn = encode_fn();
+    if (!fn || a.g.nx < TW || a.g.ny < TBY + 4) return false;
+    const cuuint64_t dims3[3] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny, 5};
+    const cuuint64_t str3[2] = {(cuuint64_t)a.g.pitch * 4, (cuuint64_t)a.g.plane * 4};
+    const cuuint32_t box3[3] = {(cuuint32_t)TW, (cuuint32_t)R, 1};
+    const cuuint32_t one[3] = {1, 1, 1};
+    if (fn(mIn, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.in.data), dims3, str3, box3, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t dims2[2] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny};
+    const cuuint64_t str2[1] = {(cuuint64_t)a.g.pitch * 4};
+    const cuuint32_t box2[2] = {(cuuint32_t)TW, (cuuint32_t)R};
+    return fn(mCL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(a.med.cL2), dims2, str2, box2, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TBY, int NT, int MINB>
+static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
+    using Gm = TbGeom<TBY>;
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB>, NT, Gm::BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    CUtensorMap mIn, mCL;
+    memset(&mIn, 0, sizeof mIn);
+    memset(&mCL, 0, sizeof mCL);
+    const int use_tma = make_maps<TBY>(a, &mIn, &mCL) ? 1 : 0;
+    const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
+    const int ntiles = ntx * nty;
+    const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
+    step2d_tb2<TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, use_tma, ntx, nty, blocks / ntx,
+                                                            blocks % ntx);
+    return cudaGetLastError();
+}
+
+// Tile shapes (rows, threads, CTAs per SM).  Measured on 4096^2 (heterogeneous medium, FP32): 6 rows at five
+// CTAs per SM is the fastest; the others remain selectable for other sizes and for the bit-identity tests.
+int tb2_nshapes() { return 7; }
+
+cudaError_t launch_step_2d_tb2(const StepArgs &a, int shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_tb<8, 320, 3>(a, s);
+        case 2: return launch_tb<8, 352, 3>(a, s);   // ring sites on the 11th warp
+        case 3: return launch_tb<10, 384, 3>(a, s);
+        case 4: return launch_tb<5, 224, 5>(a, s);
+        case 5: return launch_tb<4, 192, 6>(a, s);
+        case 6: return launch_tb<14, 512, 2>(a, s);
+        default: return launch_tb<6, 256, 5>(a, s);  // 42 KB of shared memory
+    }
+}
+
+bool tb2_take_timeouts() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tb_timeouts, sizeof v) != cudaSuccess) return false;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tb_timeouts, &z, sizeof z);
+    }
+    return v != 0;
+}
+
+}  // namespace lbk

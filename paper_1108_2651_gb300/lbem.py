@@ -48,6 +48,8 @@ _SIGS = {
     "lbem_set_receivers": [_VP, _I, _VP, _VP, _I],
     "lbem_step": [_VP, _I],
     "lbem_set_graphs": [_VP, _I],
+    "lbem_set_temporal_blocking": [_VP, _I, _I],
+    "lbem_get_temporal_blocking": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)],
     "lbem_set_watchdog": [_VP, _I, _D],
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
@@ -199,6 +201,17 @@ def lbem_step(h, nsteps):
 
 def lbem_set_watchdog(h, every, max_growth=1e6):
     _check(load().lbem_set_watchdog(h, int(every), float(max_growth)))
+
+
+def lbem_set_temporal_blocking(h, steps_per_pass, tile_shape=-1):
+    _check(load().lbem_set_temporal_blocking(h, int(steps_per_pass), int(tile_shape)))
+
+
+def lbem_get_temporal_blocking(h):
+    """(steps_per_pass, tile_shape, number of tile shapes)."""
+    a, b, c = _I(), _I(), _I()
+    _check(load().lbem_get_temporal_blocking(h, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def lbem_set_graphs(h, on):

@@ -5,8 +5,10 @@ import oracle as O
 from paper_1108_2651_gb300 import lbem
 
 
-def gpu_run(p, storage="f32", nsteps=None, variant=None, graphs=False):
-    """Run workloads.Problem p on the GPU; returns (E, B, traces) as float64 numpy, E/B grid + (3,)."""
+def gpu_run(p, storage="f32", nsteps=None, variant=None, graphs=False, steps_per_pass=None):
+    """Run workloads.Problem p on the GPU; returns (E, B, traces) as float64 numpy, E/B grid + (3,).
+    A given single-step variant runs every step (steps_per_pass 1); steps_per_pass None keeps the library
+    default (two steps per launch where that applies)."""
     import torch
 
     nsteps = p.nsteps if nsteps is None else nsteps
@@ -16,6 +18,9 @@ def gpu_run(p, storage="f32", nsteps=None, variant=None, graphs=False):
         s.set_problem(p)
         if variant is not None:
             lbem.lbem_set_variant(s.h, variant)
+            steps_per_pass = 1 if steps_per_pass is None else steps_per_pass
+        if steps_per_pass is not None:
+            lbem.lbem_set_temporal_blocking(s.h, steps_per_pass, -1)
         if graphs:
             lbem.lbem_set_graphs(s.h, True)
         s.step(nsteps)

@@ -25,6 +25,7 @@ def test_guards_intact_2d(lbem, shape, storage):
     p.rec_comp = np.array([2, 3, 4], np.int32)
     s = lbem.Solver(shape, storage=storage)
     s.set_problem(p)
+    lbem.lbem_set_temporal_blocking(s.h, 1, -1)
     for v in range(lbem.lbem_get_variant(s.h)[1]):
         lbem.lbem_set_variant(s.h, v)
         s.step(3)
@@ -35,6 +36,31 @@ def test_guards_intact_2d(lbem, shape, storage):
     lbem.lbem_save_state(s.h, snap)
     lbem.lbem_load_state(s.h, snap, 3)
     torch.cuda.synchronize()
+    lbem.lbem_check_guards(s.h)
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (17, 45), (9, 130), (33, 257), (40, 300), (130, 644)])
+def test_guards_intact_two_step(lbem, shape):
+    """The two-step kernel in every tile shape, on ragged grids, with sources and receivers at the corners."""
+    import torch
+
+    eps, _ = W.random_medium(shape, 6)
+    p = W.Problem("g2", 2, shape, eps, None, 13)
+    p.E0, p.B0 = W.random_fields(shape, 7, 0.2)
+    n = int(np.prod(shape))
+    p.src_site = np.array([0, n - 1], np.int64)
+    p.src_comp = np.array([2, 2], np.int32)
+    p.src_amp = np.ones((2, 13))
+    p.rec_site = np.array([0, n // 2, n - 1], np.int64)
+    p.rec_comp = np.array([2, 3, 4], np.int32)
+    s = lbem.Solver(shape)
+    s.set_problem(p)
+    for k in range(lbem.lbem_get_temporal_blocking(s.h)[2]):
+        lbem.lbem_set_temporal_blocking(s.h, 2, k)
+        s.step(3)
+    torch.cuda.synchronize()
+    lbem.lbem_sync(s.h)
     lbem.lbem_check_guards(s.h)
     s.close()
 
