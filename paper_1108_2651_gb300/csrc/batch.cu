@@ -105,13 +105,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) step2d_batch(const Member *__rest
         for (int j = 0; j < 4; j++) {
             const float g0 = get(g[r][0], j), g1 = get(g[r][1], j), g2 = get(g[r][2], j), g3 = get(g[r][3], j),
                         g4 = get(g[r][4], j), q = get(cl[r], j), sh = get(shat, j);
-            const float s = ((g0 + g1) + (g2 + g3)) + g4;
-            const float L = q * s, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
-            set(o[1], j, (L - g3) + Tm);
-            set(o[3], j, (L - g1) + Tm);
-            set(o[2], j, (L - g4) + Tm);
-            set(o[4], j, (L - g2) + Tm);
-            set(o[0], j, (2.f * w0 * s - g0) + T0);
+            const Out5 u = collide2d(g0, g1, g2, g3, g4, q, sh);
+            set(o[0], j, u.o0);
+            set(o[1], j, u.o1);
+            set(o[2], j, u.o2);
+            set(o[3], j, u.o3);
+            set(o[4], j, u.o4);
         }
         if (active)
             for (int i = 0; i < 5; i++) C::store4(out, i, row, c, o[i]);
@@ -161,14 +160,13 @@ __global__ void __launch_bounds__(BLOCK) step2d_batch_site(const Member *__restr
             }
         }
     }
-    const float sg = ((g0 + g1) + (g2 + g3)) + g4;
-    const float L = q * sg, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
+    const Out5 u = collide2d(g0, g1, g2, g3, g4, q, sh);
     float *op = static_cast<float *>(out.data) + (long long)row * W + x;
-    __stcs(op, (2.f * w0 * sg - g0) + T0);
-    __stcs(op + P, (L - g3) + Tm);
-    __stcs(op + 2 * P, (L - g4) + Tm);
-    __stcs(op + 3 * P, (L - g1) + Tm);
-    __stcs(op + 4 * P, (L - g2) + Tm);
+    __stcs(op, u.o0);
+    __stcs(op + P, u.o1);
+    __stcs(op + 2 * P, u.o2);
+    __stcs(op + 3 * P, u.o3);
+    __stcs(op + 4 * P, u.o4);
 }
 
 // Linear mapping over the padded plane: lane L of a member covers 4 sites at
@@ -242,13 +240,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) step2d_batch_lin(const Member *__
     for (int j = 0; j < 4; j++) {
         const float g0 = get(g[0], j), g1 = get(g[1], j), g2 = get(g[2], j), g3 = get(g[3], j), g4 = get(g[4], j),
                     q = get(cl, j), sh = get(shat, j);
-        const float s = ((g0 + g1) + (g2 + g3)) + g4;
-        const float Lq = q * s, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
-        set(o[1], j, (Lq - g3) + Tm);
-        set(o[3], j, (Lq - g1) + Tm);
-        set(o[2], j, (Lq - g4) + Tm);
-        set(o[4], j, (Lq - g2) + Tm);
-        set(o[0], j, (2.f * w0 * s - g0) + T0);
+        const Out5 u = collide2d(g0, g1, g2, g3, g4, q, sh);
+        set(o[0], j, u.o0);
+        set(o[1], j, u.o1);
+        set(o[2], j, u.o2);
+        set(o[3], j, u.o3);
+        set(o[4], j, u.o4);
     }
     for (int i = 0; i < 5; i++) C::store4(out, i, rr, c, o[i]);
 }
@@ -360,13 +357,12 @@ __global__ void __launch_bounds__(BLOCK) step2d_batch_pipe(const Member *__restr
         for (int j = 0; j < 4; j++) {
             const float g0 = get(g[0], j), g1 = get(g[1], j), g2 = get(g[2], j), g3 = get(g[3], j), g4 = get(g[4], j),
                         q = get(cur.cl, j), sh = get(shat, j);
-            const float s = ((g0 + g1) + (g2 + g3)) + g4;
-            const float L = q * s, w0 = 1.f - 2.f * q, Tm = -0.5f * q * sh, T0 = -w0 * sh;
-            set(o[1], j, (L - g3) + Tm);
-            set(o[3], j, (L - g1) + Tm);
-            set(o[2], j, (L - g4) + Tm);
-            set(o[4], j, (L - g2) + Tm);
-            set(o[0], j, (2.f * w0 * s - g0) + T0);
+            const Out5 u = collide2d(g0, g1, g2, g3, g4, q, sh);
+            set(o[0], j, u.o0);
+            set(o[1], j, u.o1);
+            set(o[2], j, u.o2);
+            set(o[3], j, u.o3);
+            set(o[4], j, u.o4);
         }
         if (active) {
             const PopBuf &out = (offset & 1) ? m.a : m.b;

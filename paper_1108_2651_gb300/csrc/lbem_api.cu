@@ -126,7 +126,7 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
 static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16 + h->tb_shape + 1; }
 
 static bool two_step_ok(const lbem_t *h) {
-    return h->tblock == 2 && h->dim == 2 && h->storage == LBEM_F32 && !h->has_mu;
+    return h->tblock == 2 && h->dim == 2 && !h->has_mu && (h->storage == LBEM_F32 || h->grid.nx % 4 == 0);
 }
 
 // Enqueue nsteps steps starting from buffer `cur` at time t0: pairs of steps with the two-step kernel
@@ -137,7 +137,7 @@ static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nst
         for (; n + 2 <= nsteps; n += 2) {
             StepArgs a = step_args(h, cur);
             a.t = t0 + n;
-            cudaError_t e = launch_step_2d_tb2(a, h->tb_shape, h->stream);
+            cudaError_t e = launch_step_2d_tb2(a, h->storage, h->tb_shape, h->stream);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -713,7 +713,7 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
                 for (int n = 0; n < npair; n++) {
                     StepArgs a = step_args(h, cur);
                     a.evt.rowptr = nullptr;
-                    cudaError_t e = launch_step_2d_tb2(a, shape, h->stream);
+                    cudaError_t e = launch_step_2d_tb2(a, h->storage, shape, h->stream);
                     if (e != cudaSuccess) {
                         st = cuda_fail(e, "lbem_autotune");
                         break;

@@ -214,18 +214,20 @@ __device__ __forceinline__ void set(float4 &v, int j, float a) {
 struct Out5 {
     float o0, o1, o2, o3, o4;
 };
+// Written with explicitly rounded operations (never contracted into FMAs), so that every kernel that calls it
+// performs the same sequence of roundings whatever the compiler schedules around it.
 __device__ __forceinline__ Out5 collide2d(float g0, float g1, float g2, float g3, float g4, float cl, float shat) {
-    const float s = ((g0 + g1) + (g2 + g3)) + g4;
-    const float L = cl * s;
-    const float w0 = 1.f - 2.f * cl;
-    const float Tm = -0.5f * cl * shat;
-    const float T0 = -w0 * shat;
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, g3)), g4);
+    const float L = __fmul_rn(cl, s);
+    const float w0 = __fsub_rn(1.f, 2.f * cl);          // 2 cl is exact
+    const float Tm = __fmul_rn(-0.5f * cl, shat);        // -cl/2 is exact
+    const float T0 = __fmul_rn(-w0, shat);
     Out5 o;
-    o.o1 = (L - g3) + Tm;
-    o.o3 = (L - g1) + Tm;
-    o.o2 = (L - g4) + Tm;
-    o.o4 = (L - g2) + Tm;
-    o.o0 = (2.f * w0 * s - g0) + T0;
+    o.o1 = __fadd_rn(__fsub_rn(L, g3), Tm);
+    o.o3 = __fadd_rn(__fsub_rn(L, g1), Tm);
+    o.o2 = __fadd_rn(__fsub_rn(L, g4), Tm);
+    o.o4 = __fadd_rn(__fsub_rn(L, g2), Tm);
+    o.o0 = __fadd_rn(__fsub_rn(__fmul_rn(2.f * w0, s), g0), T0);  // 2 w0 is exact
     return o;
 }
 
@@ -355,10 +357,10 @@ StepArgs step_args(const lbem_t *h, int cur_in);
 // 2D (kernels2d.cu)
 int nvariants_2d();
 cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int variant, cudaStream_t s);
-// two steps per launch (tblock.cu): FP32 storage, uniform mu
+// two steps per launch (tblock.cu): uniform mu; 16-bit storage needs nx % 4 == 0
 int tb2_nshapes();
 bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag
-cudaError_t launch_step_2d_tb2(const StepArgs &a, int shape, cudaStream_t s);
+cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s);
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);

@@ -124,14 +124,14 @@ __device__ __forceinline__ void tb_issue(const StepArgs &a, int x0, int y0, floa
 
 // ---- tensor-memory-accelerator (TMA) window loads for tiles whose window needs no periodic wrap
 
-__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *m, int x, int y, int z, unsigned mbar) {
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *m, int x, int y, int z, unsigned mbar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
         "[%5];\n" ::"r"(smem_u32(dst)),
         "l"(m), "r"(x), "r"(y), "r"(z), "r"(mbar)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_2d(float *dst, const CUtensorMap *m, int x, int y, unsigned mbar) {
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int x, int y, unsigned mbar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
         ::"r"(smem_u32(dst)), "l"(m), "r"(x), "r"(y), "r"(mbar)
@@ -217,8 +217,8 @@ struct Pull4 {
 #define TB_SET(v, k, val) (k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w) = (val)
 
 // Four site updates (collide2d each) at global row gy, columns x0+4*lane.., time t.
-template <bool EV>
-__device__ __forceinline__ void tb_update4(const StepArgs &a, const Pull4 &g, float4 cl, int x0, int gy, long long t,
+template <bool EV, class PULL>
+__device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, float4 cl, int x0, int gy, long long t,
                                            bool owned_row, float4 &o0, float4 &o1, float4 &o2, float4 &o3,
                                            float4 &o4) {
     const Grid &G = a.g;
@@ -458,11 +458,367 @@ static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// =====================================================================================================
+// 16-bit storage (LBEM_F16, LBEM_BF16, LBEM_I16B).  Same tiles and steps; the t stage holds the stored 16-bit
+// values (half the shared memory), each value is decoded once as step t pulls it, the t+1 stage is FP32, and
+// step t+1 encodes what it writes.  So a launch rounds the state to the storage format once per two steps
+// (the single-step kernels round at every step); the arithmetic is FP32 as everywhere.  Needs nx % 4 == 0,
+// so that every group of 4 columns (one block-int16 exponent) stays contiguous across the periodic wrap.
+
+constexpr int THW = TBX + 16;  // staged 16-bit columns x0-8 .. x0+TBX+7 (16-bit TMA boxes start at x = 8k)
+constexpr int TEX = 64;        // staged exponent groups per row: group x0/4-16+k at column k (byte boxes: x = 16k)
+
+template <int ST, int TBY>
+struct TbGeomH {
+    static constexpr int R = TBY + 2;
+    static constexpr int up(int n, int m) { return (n + m - 1) / m * m; }
+    static constexpr int INH_PL = up(R * THW * 2, 128);                    // bytes per staged 16-bit plane
+    static constexpr int EX_PL = ST == LBEM_I16B ? up(R * TEX, 128) : 0;  // bytes per staged exponent plane
+    static constexpr int P_PL = TBY * TW;                                 // floats per t+1 plane
+    static constexpr int OFF_EX = 5 * INH_PL, OFF_CL = OFF_EX + 5 * EX_PL, OFF_P = OFF_CL + up(R * TW * 4, 128);
+    static constexpr int OFF_MB = OFF_P + up(5 * P_PL * 4, 128);
+    static constexpr size_t BYTES = OFF_MB + sizeof(unsigned long long);
+    static constexpr unsigned TMA_BYTES = 5 * R * THW * 2 + R * TW * 4 + (ST == LBEM_I16B ? 5 * R * TEX : 0);
+};
+
+// One stored 16-bit value to FP32 (as Codec<ST>::load4 does): f is inv_scale (F16) or the block's 2^(e-15)
+// (I16B, 0 for a zero block).
+template <int ST>
+__device__ __forceinline__ float dec16(unsigned h, float f) {
+    if (ST == LBEM_F16) return __fmul_rn(__half2float(__ushort_as_half((unsigned short)h)), f);
+    if (ST == LBEM_BF16) return __uint_as_float(h << 16);
+    return __fmul_rn(i16_to_f((short)h), f);
+}
+__device__ __forceinline__ float ex_factor(int e) { return (e == I16B_ZERO) ? 0.f : pow2f(e - 15); }
+
+__device__ __forceinline__ void tb_cpa8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+// Pulled populations of four sites at stage row `row`, lane L (16-bit stage column j = 8 + 4L <-> x0+4L).
+template <int ST, int TBY>
+struct Pull4h {
+    float4 g0, g1, g2, g3, g4;
+    __device__ __forceinline__ Pull4h(const char *INh, const signed char *EX, int row, int L, float inv_scale) {
+        using Gm = TbGeomH<ST, TBY>;
+        const int j = 8 + 4 * L;
+        const char *r = INh + (row * THW + j) * 2;
+        const uint2 r0 = *reinterpret_cast<const uint2 *>(r);
+        const uint2 a1 = *reinterpret_cast<const uint2 *>(r + Gm::INH_PL - 8);
+        const uint2 b1 = *reinterpret_cast<const uint2 *>(r + Gm::INH_PL);
+        const uint2 r2 = *reinterpret_cast<const uint2 *>(r + 2 * Gm::INH_PL);
+        const uint2 r3 = *reinterpret_cast<const uint2 *>(r + 3 * Gm::INH_PL);
+        const uint2 c3 = *reinterpret_cast<const uint2 *>(r + 3 * Gm::INH_PL + 8);
+        const uint2 r4 = *reinterpret_cast<const uint2 *>(r + 4 * Gm::INH_PL);
+        float f0 = inv_scale, f1a = inv_scale, f1b = inv_scale, f2 = inv_scale, f3a = inv_scale, f3b = inv_scale,
+              f4 = inv_scale;
+        if (ST == LBEM_I16B) {  // exponent column of stage column j: 14 + j/4
+            const signed char *e = EX + row * TEX + 16 + L;
+            f0 = ex_factor(e[0]);
+            f1a = ex_factor(e[Gm::EX_PL - 1]);
+            f1b = ex_factor(e[Gm::EX_PL]);
+            f2 = ex_factor(e[2 * Gm::EX_PL]);
+            f3a = ex_factor(e[3 * Gm::EX_PL]);
+            f3b = ex_factor(e[3 * Gm::EX_PL + 1]);
+            f4 = ex_factor(e[4 * Gm::EX_PL]);
+        }
+        g0 = make_float4(dec16<ST>(r0.x & 0xffffu, f0), dec16<ST>(r0.x >> 16, f0), dec16<ST>(r0.y & 0xffffu, f0),
+                         dec16<ST>(r0.y >> 16, f0));
+        g1 = make_float4(dec16<ST>(a1.y >> 16, f1a), dec16<ST>(b1.x & 0xffffu, f1b), dec16<ST>(b1.x >> 16, f1b),
+                         dec16<ST>(b1.y & 0xffffu, f1b));
+        g2 = make_float4(dec16<ST>(r2.x & 0xffffu, f2), dec16<ST>(r2.x >> 16, f2), dec16<ST>(r2.y & 0xffffu, f2),
+                         dec16<ST>(r2.y >> 16, f2));
+        g3 = make_float4(dec16<ST>(r3.x >> 16, f3a), dec16<ST>(r3.y & 0xffffu, f3a), dec16<ST>(r3.y >> 16, f3a),
+                         dec16<ST>(c3.x & 0xffffu, f3b));
+        g4 = make_float4(dec16<ST>(r4.x & 0xffffu, f4), dec16<ST>(r4.x >> 16, f4), dec16<ST>(r4.y & 0xffffu, f4),
+                         dec16<ST>(r4.y >> 16, f4));
+    }
+};
+
+// One decoded value of the 16-bit stage (plane p, row, stage column j).
+template <int ST, int TBY>
+__device__ __forceinline__ float stage16(const char *INh, const signed char *EX, int p, int row, int j, float inv_scale) {
+    using Gm = TbGeomH<ST, TBY>;
+    const unsigned h = *reinterpret_cast<const unsigned short *>(INh + p * Gm::INH_PL + (row * THW + j) * 2);
+    const float f = ST == LBEM_I16B ? ex_factor(EX[p * Gm::EX_PL + row * TEX + 14 + j / 4]) : inv_scale;
+    return dec16<ST>(h, f);
+}
+
+template <int TBY>
+__device__ __forceinline__ bool tb_interior16(int x0, int y0, const Grid &G) {
+    return x0 - 8 >= 0 && x0 + TBX + 8 <= G.nx && y0 - 2 >= 0 && y0 + TBY + 2 <= G.ny;
+}
+
+// Loads of one tile's window: TMA boxes for interior tiles (one thread), asynchronous copies of 4-column
+// groups with periodic wrap otherwise (nx % 4 == 0), exponent bytes by plain loads.
+template <int ST, int TBY>
+__device__ __forceinline__ void tb_load16(const StepArgs &a, int x0, int y0, char *sm, unsigned mbar, bool tma,
+                                          const CUtensorMap *tmIn, const CUtensorMap *tmCL, const CUtensorMap *tmEx,
+                                          int nt) {
+    using Gm = TbGeomH<ST, TBY>;
+    constexpr int R = Gm::R;
+    char *INh = sm;
+    signed char *EX = reinterpret_cast<signed char *>(sm + Gm::OFF_EX);
+    float *CL = reinterpret_cast<float *>(sm + Gm::OFF_CL);
+    if (tma) {
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(Gm::TMA_BYTES)
+                         : "memory");
+#pragma unroll
+            for (int p = 0; p < 5; p++) tma_load_3d(INh + p * Gm::INH_PL, tmIn, x0 - 8, y0 - 1 + in_shift(p), p, mbar);
+            tma_load_2d(CL, tmCL, x0 - 4, y0 - 1, mbar);
+            if (ST == LBEM_I16B) {
+#pragma unroll
+                for (int p = 0; p < 5; p++)
+                    tma_load_3d(EX + p * Gm::EX_PL, tmEx, x0 / 4 - 16, y0 - 1 + in_shift(p), p, mbar);
+            }
+        }
+        return;
+    }
+    const Grid &G = a.g;
+    const unsigned short *in = static_cast<const unsigned short *>(a.in.data);
+    constexpr int QH = THW / 4, QC = TW / 4;
+    for (int k = threadIdx.x; k < 5 * R * QH; k += nt) {
+        const int pr = k / QH, q = k - pr * QH;
+        const int pl = pr / R, r = pr - pl * R;
+        const int gy = wrapi(y0 - 1 + r + in_shift(pl), G.ny), gx = wrapi(x0 - 8 + 4 * q, G.nx);
+        tb_cpa8(INh + pl * Gm::INH_PL + (r * THW + 4 * q) * 2, in + pl * G.plane + (long long)gy * G.pitch + gx);
+        if (ST == LBEM_I16B)
+            EX[pl * Gm::EX_PL + r * TEX + 14 + q] = __ldg(a.in.ex + pl * a.in.explane + (long long)gy * a.in.expitch + gx / 4);
+    }
+    for (int k = threadIdx.x; k < R * QC; k += nt) {
+        const int r = k / QC, q = k - r * QC;
+        const int gy = wrapi(y0 - 1 + r, G.ny), gx = wrapi(x0 - 4 + 4 * q, G.nx);
+        tb_cpa16(CL + r * TW + 4 * q, a.med.cL2 + (long long)gy * G.pitch + gx);
+    }
+}
+
+// Step t from the 16-bit stage into the FP32 t+1 stage (as tb_step_a).
+template <int ST, int TBY, int NT, bool EV>
+__device__ __forceinline__ void tb_step_a16(const StepArgs &a, const char *INh, const signed char *EX, const float *CL,
+                                            float *P, int x0, int y0, long long t, float4 &clb) {
+    using Gm = TbGeomH<ST, TBY>;
+    constexpr int R = Gm::R, NW = NT / 32, PL = Gm::P_PL;
+    const Grid &G = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = 4 + 4 * lane;
+    const float is = a.in.inv_scale;
+    if (warp < TBY) clb = lds4(CL + (warp + 1) * TW + c);
+    for (int py = warp; py < R; py += NW) {
+        const Pull4h<ST, TBY> g(INh, EX, py, lane, is);
+        const float4 cl = lds4(CL + py * TW + c);
+        float4 o0, o1, o2, o3, o4;
+        tb_update4<EV>(a, g, cl, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2, o3, o4);
+        float *Pr = P + c;
+        if (py >= 1 && py <= TBY) {
+            sts4(Pr + 0 * PL + (py - 1) * TW, o0);
+            sts4(Pr + 1 * PL + (py - 1) * TW, o1);
+            sts4(Pr + 3 * PL + (py - 1) * TW, o3);
+        }
+        if (py < TBY) sts4(Pr + 2 * PL + py * TW, o2);
+        if (py >= 2) sts4(Pr + 4 * PL + (py - 2) * TW, o4);
+    }
+    int k0 = tid - 32 * (R % NW);
+    if (k0 < 0) k0 += NT;
+    for (int k = k0; k < 2 * TBY; k += NT) {
+        const int py = (k >> 1) + 1, j = (k & 1) ? TBX + 8 : 7;  // 16-bit stage column of x0-1 / x0+TBX
+        const int cc = j - 4;                                    // FP32 column of the same site
+        const float q0 = stage16<ST, TBY>(INh, EX, 0, py, j, is), q1 = stage16<ST, TBY>(INh, EX, 1, py, j - 1, is),
+                    q2 = stage16<ST, TBY>(INh, EX, 2, py, j, is), q3 = stage16<ST, TBY>(INh, EX, 3, py, j + 1, is),
+                    q4 = stage16<ST, TBY>(INh, EX, 4, py, j, is);
+        const float ck = CL[py * TW + cc];
+        float shat = 0.f;
+        if (EV)
+            shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3, q4,
+                               ck);
+        const Out5 o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        if (k & 1)
+            P[3 * PL + (py - 1) * TW + cc] = o.o3;
+        else
+            P[1 * PL + (py - 1) * TW + cc] = o.o1;
+    }
+}
+
+// Step t+1 on tile row y0 + warp, encoded to the storage format as it is written.
+template <int ST, int TBY, bool EV>
+__device__ __forceinline__ void tb_step_b16(const StepArgs &a, const float *P, float4 clb, int x0, int y0, long long t) {
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31, oy = threadIdx.x >> 5;
+    const int gy = y0 + oy;
+    if (oy >= TBY || gy >= G.ny) return;
+    const int c = 4 + 4 * lane;
+    const Pull4 g(P, TbGeomH<ST, TBY>::P_PL, oy, c);
+    float4 o[5];
+    tb_update4<EV>(a, g, clb, x0, gy, t + 1, true, o[0], o[1], o[2], o[3], o[4]);
+    if (x0 + 4 * lane < G.pitch) {
+        unsigned short *out = static_cast<unsigned short *>(a.out.data) + (long long)gy * G.pitch + x0 + 4 * lane;
+#pragma unroll
+        for (int p = 0; p < 5; p++) {
+            uint2 r;
+            if constexpr (ST == LBEM_I16B) {
+                const int e = Codec<LBEM_I16B>::enc4e(o[p], r);
+                a.out.ex[p * a.out.explane + (long long)gy * a.out.expitch + x0 / 4 + lane] = (int8_t)e;
+            } else {
+                r = Codec<ST>::enc4(a.out, o[p]);
+            }
+            __stcs(reinterpret_cast<uint2 *>(out + p * G.plane), r);
+        }
+    }
+}
+
+template <int ST, int TBY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    step2d_tb2h(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
+                const __grid_constant__ CUtensorMap tmEx, int use_tma, int ntx, int nty, int dq, int dr) {
+    static_assert(NT / 32 >= TBY, "one warp per row of step t+1");
+    using Gm = TbGeomH<ST, TBY>;
+    extern __shared__ __align__(1024) char smb[];
+    const char *INh = smb;
+    const signed char *EX = reinterpret_cast<const signed char *>(smb + Gm::OFF_EX);
+    const float *CL = reinterpret_cast<const float *>(smb + Gm::OFF_CL);
+    float *P = reinterpret_cast<float *>(smb + Gm::OFF_P);
+    const unsigned mbar = smem_u32(smb + Gm::OFF_MB);
+    const Grid &G = a.g;
+    const int tid = threadIdx.x;
+    if (smem_u32(smb) & 127) use_tma = 0;
+    int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    if (ty >= nty) return;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    tb_load16<ST, TBY>(a, tx * TBX, ty * TBY, smb, mbar, use_tma && tb_interior16<TBY>(tx * TBX, ty * TBY, G), &tmIn,
+                       &tmCL, &tmEx, NT);
+    asm volatile("cp.async.commit_group;\n" ::);
+    bool events = tb_events<TBY>(a, ty * TBY);
+    const long long t = a.t;
+    while (ty < nty) {
+        int ntx_ = tx + dr, nty_ = ty + dq;
+        if (ntx_ >= ntx) {
+            ntx_ -= ntx;
+            nty_++;
+        }
+        const bool has_next = nty_ < nty;
+        const bool events_next = has_next && tb_events<TBY>(a, nty_ * TBY);
+        const int x0 = tx * TBX, y0 = ty * TBY;
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        bool ok = true;
+        if (use_tma && tb_interior16<TBY>(x0, y0, G)) {
+            ok = mbar_wait(mbar, parity);
+            parity ^= 1u;
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(&g_tb_timeouts, 1);
+            mbar_wait(mbar, parity ^ 1u);
+            return;
+        }
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (events)
+            tb_step_a16<ST, TBY, NT, true>(a, INh, EX, CL, P, x0, y0, t, clb);
+        else
+            tb_step_a16<ST, TBY, NT, false>(a, INh, EX, CL, P, x0, y0, t, clb);
+        __syncthreads();
+        if (has_next)
+            tb_load16<ST, TBY>(a, ntx_ * TBX, nty_ * TBY, smb, mbar,
+                               use_tma && tb_interior16<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, &tmEx, NT);
+        asm volatile("cp.async.commit_group;\n" ::);
+        if (events)
+            tb_step_b16<ST, TBY, true>(a, P, clb, x0, y0, t);
+        else
+            tb_step_b16<ST, TBY, false>(a, P, clb, x0, y0, t);
+        tx = ntx_;
+        ty = nty_;
+        events = events_next;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// Tensor maps of the 16-bit populations (box: one plane of TBY+2 rows of THW values), c_L^2 and, for block-int16,
+// the exponent planes (box: TEX bytes of TBY+2 rows); false if unavailable or the strides do not allow it.
+template <int ST, int TBY>
+static bool make_maps16(const StepArgs &a, CUtensorMap *mIn, CUtensorMap *mCL, CUtensorMap *mEx) {
+    constexpr int R = TbGeomH<ST, TBY>::R;
+    EncodeTiled fn = encode_fn();
+    if (!fn || a.g.nx < THW || a.g.ny < TBY + 4) return false;
+    const cuuint32_t one[3] = {1, 1, 1};
+    const cuuint64_t dims3[3] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny, 5};
+    const cuuint64_t str3[2] = {(cuuint64_t)a.g.pitch * 2, (cuuint64_t)a.g.plane * 2};
+    const cuuint32_t box3[3] = {(cuuint32_t)THW, (cuuint32_t)R, 1};
+    if (fn(mIn, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void *>(a.in.data), dims3, str3, box3, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t dims2[2] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny};
+    const cuuint64_t str2[1] = {(cuuint64_t)a.g.pitch * 4};
+    const cuuint32_t box2[2] = {(cuuint32_t)TW, (cuuint32_t)R};
+    if (fn(mCL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(a.med.cL2), dims2, str2, box2, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (ST != LBEM_I16B) return true;
+    if (a.in.expitch % 16 || a.in.explane % 16) return false;
+    const cuuint64_t dimsE[3] = {(cuuint64_t)a.in.expitch, (cuuint64_t)a.g.ny, 5};
+    const cuuint64_t strE[2] = {(cuuint64_t)a.in.expitch, (cuuint64_t)a.in.explane};
+    const cuuint32_t boxE[3] = {(cuuint32_t)TEX, (cuuint32_t)R, 1};
+    return fn(mEx, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, a.in.ex, dimsE, strE, boxE, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <int ST, int TBY, int NT, int MINB>
+static cudaError_t launch_tb16(const StepArgs &a, cudaStream_t s) {
+    using Gm = TbGeomH<ST, TBY>;
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(step2d_tb2h<ST, TBY, NT, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2h<ST, TBY, NT, MINB>, NT, Gm::BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    CUtensorMap mIn, mCL, mEx;
+    memset(&mIn, 0, sizeof mIn);
+    memset(&mCL, 0, sizeof mCL);
+    memset(&mEx, 0, sizeof mEx);
+    const int use_tma = make_maps16<ST, TBY>(a, &mIn, &mCL, &mEx) ? 1 : 0;
+    const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
+    const int ntiles = ntx * nty;
+    const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
+    step2d_tb2h<ST, TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mEx, use_tma, ntx, nty, blocks / ntx,
+                                                                 blocks % ntx);
+    return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_16(const StepArgs &a, int shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_tb16<ST, 6, 256, 4>(a, s);
+        case 2: return launch_tb16<ST, 8, 320, 4>(a, s);
+        case 3: return launch_tb16<ST, 8, 320, 3>(a, s);
+        case 4: return launch_tb16<ST, 4, 192, 6>(a, s);
+        case 5: return launch_tb16<ST, 10, 384, 3>(a, s);
+        case 6: return launch_tb16<ST, 14, 512, 2>(a, s);
+        default: return launch_tb16<ST, 6, 256, 5>(a, s);
+    }
+}
+
 // Tile shapes (rows, threads, CTAs per SM).  Measured on 4096^2 (heterogeneous medium, FP32): 6 rows at five
 // CTAs per SM is the fastest; the others remain selectable for other sizes and for the bit-identity tests.
 int tb2_nshapes() { return 7; }
 
-cudaError_t launch_step_2d_tb2(const StepArgs &a, int shape, cudaStream_t s) {
+cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s) {
+    switch (storage) {
+        case LBEM_F16: return launch_16<LBEM_F16>(a, shape, s);
+        case LBEM_BF16: return launch_16<LBEM_BF16>(a, shape, s);
+        case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
+        default: break;
+    }
     switch (shape) {
         case 1: return launch_tb<8, 320, 3>(a, s);
         case 2: return launch_tb<8, 352, 3>(a, s);   // ring sites on the 11th warp

@@ -148,17 +148,20 @@ def test_192_cubed_full_size_elementwise_3_steps(lbem):
     _check(p, tol=1e-5)
 
 
+@pytest.mark.parametrize("steps_per_pass", [1, 2])
 @pytest.mark.parametrize("storage", ["f16", "bf16", "i16b"])
-def test_reduced_storage_short_run_tracks_oracle(lbem, storage):
+def test_reduced_storage_short_run_tracks_oracle(lbem, storage, steps_per_pass):
     """Half-precision storage on the homogeneous 128^2 pulse: error within the format's rounding bound
-    2 u sqrt(N/3) (u = unit roundoff; 2^-11 FP16, 2^-8 BF16, 2 * 2^-16 block int16)."""
+    2 u sqrt(N/3) (u = unit roundoff; 2^-11 FP16, 2^-8 BF16, 2 * 2^-16 block int16), with single steps and
+    with two steps per launch (one rounding per two steps)."""
     p = W.homogeneous_pulse(128, 6.0, 500)
-    E, B, _ = gpu_run(p, storage)
+    E, B, _ = gpu_run(p, storage, steps_per_pass=steps_per_pass)
     oE, oB, _, _, _ = oracle_run(p)
     u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8, "i16b": 2.0 ** -15}[storage]
     bound = 2 * u * np.sqrt(500 / 3)
     eE, eB = rel(E, oE), rel(B, oB)
-    print(f"{storage} 128^2 x 500: rel-L2 E {eE:.2e} B {eB:.2e} (bound {bound:.1e})")
+    print(f"{storage} 128^2 x 500, {steps_per_pass} step(s)/launch: rel-L2 E {eE:.2e} B {eB:.2e} "
+          f"(bound {bound:.1e})")
     assert eE < bound and eB < bound
 
 
@@ -281,13 +284,16 @@ def test_storage_forms_5000_steps_on_512_crop_of_4096_medium(lbem):
     u = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8, "i16b": 2.0 ** -15}
     report = {}
     for st in ("f32", "f16", "bf16", "i16b"):
-        E, B, tr = gpu_run(p, st)
-        report[st] = (rel(E, oE), rel(B, oB), rel(tr, otr))
-    print("512^2 crop x 5000 rel-L2 (E, B, traces):", {k: tuple(f"{x:.2e}" for x in v) for k, v in report.items()})
-    assert max(report["f32"]) < 1e-4, report["f32"]
-    for st in ("f16", "bf16"):
-        assert max(report[st]) < 2 * u[st] * np.sqrt(5000 / 3), (st, report[st])
-    assert max(report["i16b"][:2]) < 1e-3, report["i16b"]
+        for spp in (1, 2):
+            E, B, tr = gpu_run(p, st, steps_per_pass=spp)
+            report[(st, spp)] = (rel(E, oE), rel(B, oB), rel(tr, otr))
+    print("512^2 crop x 5000 rel-L2 (E, B, traces) by (storage, steps per launch):",
+          {f"{k[0]}/{k[1]}": tuple(f"{x:.2e}" for x in v) for k, v in report.items()})
+    for spp in (1, 2):
+        assert max(report[("f32", spp)]) < 1e-4, report[("f32", spp)]
+        for st in ("f16", "bf16"):
+            assert max(report[(st, spp)]) < 2 * u[st] * np.sqrt(5000 / 3), (st, spp, report[(st, spp)])
+        assert max(report[("i16b", spp)][:2]) < 1e-3, report[("i16b", spp)]
 
 
 @pytest.mark.slow
