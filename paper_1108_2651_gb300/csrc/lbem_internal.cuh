@@ -149,6 +149,17 @@ constexpr int kMagicBits = 0x4B400000;
 __device__ __forceinline__ float i16_to_f(int q) { return __int_as_float(kMagicBits + q) - kMagic; }
 __device__ __forceinline__ int f_to_int_rn(float v) { return __float_as_int(v + kMagic) - kMagicBits; }
 
+// Block-int16 decoding of the two values packed in w (low half first), f = 2^(e-15) (0 for a zero block):
+// h ^ 0x8000 = q + 2^15 placed under the exponent of 1.5 * 2^23 gives the float 1.5 * 2^23 + 2^15 + q exactly,
+// and one rounding of (that float) * f - (1.5 * 2^23 + 2^15) * f is q * f, the same value as float(q) * f.
+constexpr float kMagic16 = 12615680.0f;  // 1.5 * 2^23 + 2^15
+__device__ __forceinline__ float2 i16x2_to_f2(unsigned w, float f) {
+    const unsigned u = w ^ 0x80008000u;
+    const float nf = -kMagic16 * f;  // exact: f is a power of two or zero
+    return make_float2(__fmaf_rn(__uint_as_float(__byte_perm(u, 0x4B40u, 0x5410)), f, nf),
+                       __fmaf_rn(__uint_as_float(__byte_perm(u, 0x4B40u, 0x5432)), f, nf));
+}
+
 template <>
 struct Codec<LBEM_I16B> {
     static constexpr int bytes = 2;
@@ -158,8 +169,8 @@ struct Codec<LBEM_I16B> {
         uint2 r = __ldg(q + c);
         int e = __ldg(b.ex + p * b.explane + (long long)row * b.expitch + c);
         float f = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
-        return make_float4(i16_to_f((short)(r.x & 0xffffu)) * f, i16_to_f((short)(r.x >> 16)) * f,
-                           i16_to_f((short)(r.y & 0xffffu)) * f, i16_to_f((short)(r.y >> 16)) * f);
+        const float2 lo = i16x2_to_f2(r.x, f), hi = i16x2_to_f2(r.y, f);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
     }
     __device__ static __forceinline__ float load1(const PopBuf &b, int p, int row, int x) {
         short v = __ldg(static_cast<const short *>(b.data) + p * b.plane + (long long)row * b.pitch + x);
@@ -178,14 +189,15 @@ struct Codec<LBEM_I16B> {
             r.x = r.y = 0u;
         } else {
             e = ((__float_as_int(m) >> 23) & 0xff) - 127 + 1;
-            float s = pow2f(15 - e);
-            // |v * s| < 2^15 here, so the adder-based rounding is exact
-            int q0 = max(-32767, min(32767, f_to_int_rn(v.x * s)));
-            int q1 = max(-32767, min(32767, f_to_int_rn(v.y * s)));
-            int q2 = max(-32767, min(32767, f_to_int_rn(v.z * s)));
-            int q3 = max(-32767, min(32767, f_to_int_rn(v.w * s)));
-            r.x = (unsigned)(q0 & 0xffff) | ((unsigned)(q1 & 0xffff) << 16);
-            r.y = (unsigned)(q2 & 0xffff) | ((unsigned)(q3 & 0xffff) << 16);
+            const float s = pow2f(15 - e);
+            // |v * s| <= 2^15 here; clamping to the integers +-32767 before the rounding equals clamping after it.
+            // The adder-based rounding leaves q in the low 16 bits of the sum's bit pattern (two's complement).
+            const unsigned b0 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.x, s), -32767.f), 32767.f) + kMagic);
+            const unsigned b1 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.y, s), -32767.f), 32767.f) + kMagic);
+            const unsigned b2 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.z, s), -32767.f), 32767.f) + kMagic);
+            const unsigned b3 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.w, s), -32767.f), 32767.f) + kMagic);
+            r.x = __byte_perm(b0, b1, 0x5410);
+            r.y = __byte_perm(b2, b3, 0x5410);
         }
         return e;
     }
@@ -228,6 +240,21 @@ __device__ __forceinline__ Out5 collide2d(float g0, float g1, float g2, float g3
     o.o2 = __fadd_rn(__fsub_rn(L, g4), Tm);
     o.o4 = __fadd_rn(__fsub_rn(L, g2), Tm);
     o.o0 = __fadd_rn(__fsub_rn(__fmul_rn(2.f * w0, s), g0), T0);  // 2 w0 is exact
+    return o;
+}
+
+// collide2d at a site without a source (S^ = +0): there T_m and T_0 are -0 (c_L^2 > 0, w0 >= 0), and adding
+// -0 leaves every value unchanged, so dropping them gives the same bits as collide2d(..., 0.f).
+__device__ __forceinline__ Out5 collide2d_free(float g0, float g1, float g2, float g3, float g4, float cl) {
+    const float s = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, g3)), g4);
+    const float L = __fmul_rn(cl, s);
+    const float w0 = __fsub_rn(1.f, 2.f * cl);
+    Out5 o;
+    o.o1 = __fsub_rn(L, g3);
+    o.o3 = __fsub_rn(L, g1);
+    o.o2 = __fsub_rn(L, g4);
+    o.o4 = __fsub_rn(L, g2);
+    o.o0 = __fsub_rn(__fmul_rn(2.f * w0, s), g0);
     return o;
 }
 

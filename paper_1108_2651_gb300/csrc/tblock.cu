@@ -227,13 +227,15 @@ __device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, flo
     for (int k = 0; k < 4; k++) {
         const float q0 = TB_COMP(g.g0, k), q1 = TB_COMP(g.g1, k), q2 = TB_COMP(g.g2, k), q3 = TB_COMP(g.g3, k),
                     q4 = TB_COMP(g.g4, k), ck = TB_COMP(cl, k);
-        float shat = 0.f;
+        Out5 o;
         if (EV) {
             const int gx = x0 + 4 * lane + k;
-            shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, owned_row && gx < G.nx && gy < G.ny, q0, q1,
-                               q2, q3, q4, ck);
+            const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
+                                           owned_row && gx < G.nx && gy < G.ny, q0, q1, q2, q3, q4, ck);
+            o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        } else {
+            o = collide2d_free(q0, q1, q2, q3, q4, ck);
         }
-        const Out5 o = collide2d(q0, q1, q2, q3, q4, ck, shat);
         TB_SET(o0, k, o.o0);
         TB_SET(o1, k, o.o1);
         TB_SET(o2, k, o.o2);
@@ -491,6 +493,19 @@ __device__ __forceinline__ float dec16(unsigned h, float f) {
 }
 __device__ __forceinline__ float ex_factor(int e) { return (e == I16B_ZERO) ? 0.f : pow2f(e - 15); }
 
+// The two stored values packed in w (low half first), decoded as dec16 does.
+template <int ST>
+__device__ __forceinline__ float2 dec16x2(unsigned w, float f) {
+    if constexpr (ST == LBEM_I16B) {
+        return i16x2_to_f2(w, f);
+    } else if constexpr (ST == LBEM_F16) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        return make_float2(__fmul_rn(v.x, f), __fmul_rn(v.y, f));
+    } else {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+}
+
 __device__ __forceinline__ void tb_cpa8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
 }
@@ -522,16 +537,16 @@ struct Pull4h {
             f3b = ex_factor(e[3 * Gm::EX_PL + 1]);
             f4 = ex_factor(e[4 * Gm::EX_PL]);
         }
-        g0 = make_float4(dec16<ST>(r0.x & 0xffffu, f0), dec16<ST>(r0.x >> 16, f0), dec16<ST>(r0.y & 0xffffu, f0),
-                         dec16<ST>(r0.y >> 16, f0));
-        g1 = make_float4(dec16<ST>(a1.y >> 16, f1a), dec16<ST>(b1.x & 0xffffu, f1b), dec16<ST>(b1.x >> 16, f1b),
-                         dec16<ST>(b1.y & 0xffffu, f1b));
-        g2 = make_float4(dec16<ST>(r2.x & 0xffffu, f2), dec16<ST>(r2.x >> 16, f2), dec16<ST>(r2.y & 0xffffu, f2),
-                         dec16<ST>(r2.y >> 16, f2));
-        g3 = make_float4(dec16<ST>(r3.x >> 16, f3a), dec16<ST>(r3.y & 0xffffu, f3a), dec16<ST>(r3.y >> 16, f3a),
-                         dec16<ST>(c3.x & 0xffffu, f3b));
-        g4 = make_float4(dec16<ST>(r4.x & 0xffffu, f4), dec16<ST>(r4.x >> 16, f4), dec16<ST>(r4.y & 0xffffu, f4),
-                         dec16<ST>(r4.y >> 16, f4));
+        const float2 p0a = dec16x2<ST>(r0.x, f0), p0b = dec16x2<ST>(r0.y, f0);
+        const float2 p1a = dec16x2<ST>(a1.y, f1a), p1b = dec16x2<ST>(b1.x, f1b), p1c = dec16x2<ST>(b1.y, f1b);
+        const float2 p2a = dec16x2<ST>(r2.x, f2), p2b = dec16x2<ST>(r2.y, f2);
+        const float2 p3a = dec16x2<ST>(r3.x, f3a), p3b = dec16x2<ST>(r3.y, f3a), p3c = dec16x2<ST>(c3.x, f3b);
+        const float2 p4a = dec16x2<ST>(r4.x, f4), p4b = dec16x2<ST>(r4.y, f4);
+        g0 = make_float4(p0a.x, p0a.y, p0b.x, p0b.y);
+        g1 = make_float4(p1a.y, p1b.x, p1b.y, p1c.x);
+        g2 = make_float4(p2a.x, p2a.y, p2b.x, p2b.y);
+        g3 = make_float4(p3a.y, p3b.x, p3b.y, p3c.x);
+        g4 = make_float4(p4a.x, p4a.y, p4b.x, p4b.y);
     }
 };
 
