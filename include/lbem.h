@@ -143,18 +143,23 @@ lbem_status lbem_step(lbem_t *h, int nsteps);
  * growth without sources), so a jump means an over-driven source or a corrupted state. */
 lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
 
-/* Temporal blocking (2D, LBEM_F32 storage, uniform mu; otherwise ignored).  With steps_per_pass = 2 (the
- * default) lbem_step advances pairs of steps with one kernel that stages a tile plus a two-site halo in
- * shared memory and performs both steps there, so the state crosses HBM once per two steps (44 instead of
- * 88 bytes per site and step pair); an odd last step is a single step.  Results are bit-identical to single
- * steps.  1 makes every step a single-step launch (the kernel lbem_set_variant selects).  tile_shape
+/* Temporal blocking (2D, uniform mu; 16-bit storage needs nx % 4 == 0; otherwise ignored).  With
+ * steps_per_pass = 2 (the default) lbem_step advances pairs of steps with one kernel that stages a tile plus
+ * a two-site halo in shared memory and performs both steps there, so the state crosses HBM once per two steps
+ * (44 instead of 88 bytes per site and step pair for FP32); an odd last step is a single step.  For FP32
+ * storage results are bit-identical to single steps; 16-bit storage is rounded once per launch (decode, two
+ * FP32 steps, encode).  steps_per_pass = 3 (FP32 storage only; otherwise as 2) advances triples of steps
+ * through a three-site halo (44 bytes per site per three steps), a remaining pair with the two-step kernel;
+ * again bit-identical to single steps.  1 makes every step a single-step launch (the kernel lbem_set_variant
+ * selects).  With steps_per_pass = 3, tile_shape selects 0 = 6 rows, 384 threads, 3 CTAs per SM (also -1);
+ * 1 = 4 rows, 288, 4; 2 = 8 rows, 448, 2.  With steps_per_pass = 2, tile_shape
  * selects the tile (128 sites wide) height, threads per CTA and CTAs per SM: 0 = 6 rows, 256 threads, 5
  * per SM (the default, also -1); 1 = 8 rows, 320, 3; 2 = 8 rows, 352, 3; 3 = 10 rows, 384, 3; 4 = 5 rows,
  * 224, 5; 5 = 4 rows, 192, 6; 6 = 14 rows, 512, 2.  LBEM_ERR_ARG for other values. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 
-/* Steps per launch in effect (2 only where the two-step kernel is enabled and applies), the tile shape (as
- * set or autotuned) and the number of tile shapes; any pointer may be NULL. */
+/* Steps per launch in effect (2 or 3 only where that kernel is enabled and applies), the tile shape (as set
+ * or autotuned) and the number of tile shapes of the selected steps per pass; any pointer may be NULL. */
 lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int *tile_shape, int *nshapes);
 
 /* Use (on != 0) or not CUDA-graph replay of runs of steps in lbem_step. */

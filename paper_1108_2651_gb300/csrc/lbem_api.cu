@@ -125,19 +125,34 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
 // what a captured graph depends on besides t, nsteps and the buffer: kernel variant and two-step shape
 static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16 + h->tb_shape + 1; }
 
-static bool two_step_ok(const lbem_t *h) {
-    return h->tblock == 2 && h->dim == 2 && !h->has_mu && (h->storage == LBEM_F32 || h->grid.nx % 4 == 0);
+// Whether launches of two (three) steps apply: 2D, uniform mu; 16-bit storage needs nx % 4 == 0; three steps
+// per launch exist for FP32 storage.
+static bool multi_step_base(const lbem_t *h) {
+    return h->dim == 2 && !h->has_mu && (h->storage == LBEM_F32 || h->grid.nx % 4 == 0);
 }
+static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
+static bool three_step_ok(const lbem_t *h) { return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32; }
+static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two_step_ok(h) ? 2 : 1; }
 
-// Enqueue nsteps steps starting from buffer `cur` at time t0: pairs of steps with the two-step kernel
-// when enabled, single steps otherwise; returns the buffer holding the final state in *cur_out.
+// Enqueue nsteps steps starting from buffer `cur` at time t0: triples (pairs) of steps with the three-step
+// (two-step) kernel when enabled, a remaining pair with the two-step kernel's default tile, single steps
+// otherwise; returns the buffer holding the final state in *cur_out.
 static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {
     int n = 0;
+    if (three_step_ok(h)) {
+        for (; n + 3 <= nsteps; n += 3) {
+            StepArgs a = step_args(h, cur);
+            a.t = t0 + n;
+            cudaError_t e = launch_step_2d_tb3(a, h->tb_shape, h->stream);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    }
     if (two_step_ok(h)) {
         for (; n + 2 <= nsteps; n += 2) {
             StepArgs a = step_args(h, cur);
             a.t = t0 + n;
-            cudaError_t e = launch_step_2d_tb2(a, h->storage, h->tb_shape, h->stream);
+            cudaError_t e = launch_step_2d_tb2(a, h->storage, h->tblock == 2 ? h->tb_shape : 0, h->stream);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -515,9 +530,9 @@ static lbem_status step_run(lbem_t *h, int nsteps) {
 
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
-    if (steps_per_pass != 1 && steps_per_pass != 2)
-        return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: steps_per_pass must be 1 or 2");
-    if (tile_shape < -1 || tile_shape >= tb2_nshapes())
+    if (steps_per_pass < 1 || steps_per_pass > 3)
+        return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: steps_per_pass must be 1, 2 or 3");
+    if (tile_shape < -1 || tile_shape >= (steps_per_pass == 3 ? tb3_nshapes() : tb2_nshapes()))
         return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: tile_shape out of range");
     h->tblock = steps_per_pass;
     h->tb_shape = tile_shape < 0 ? 0 : tile_shape;
@@ -700,20 +715,24 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
             best_v = v;
         }
     }
-    // two steps per launch: time every tile shape; keep it only if it beats the best single-step kernel
-    const float single_ms_per_step = best_ms / trial_steps;
-    int best_shape = h->tb_shape, best_tblock = h->tblock;
-    if (h->tblock == 2 && two_step_ok(h)) {
-        const int npair = trial_steps / 2 > 0 ? trial_steps / 2 : 1;
-        float best_pair = 1e30f;
-        for (int shape = 0; shape < tb2_nshapes() && st == LBEM_OK; shape++) {
+    // two and three steps per launch (where enabled and applicable): time every tile shape; keep the fastest
+    // per step, single steps included
+    float best_per_step = best_ms / trial_steps;
+    int best_shape = h->tb_shape, best_tblock = 1;
+    const int max_k = h->tblock;
+    for (int k = 2; k <= max_k && st == LBEM_OK; k++) {
+        if (!multi_step_base(h) || (k == 3 && h->storage != LBEM_F32)) continue;
+        const int nl = trial_steps / k > 0 ? trial_steps / k : 1;
+        const int nsh = k == 3 ? tb3_nshapes() : tb2_nshapes();
+        for (int shape = 0; shape < nsh && st == LBEM_OK; shape++) {
             int cur = cur0;
             for (int rep = 0; rep < 2 && st == LBEM_OK; rep++) {
                 cudaEventRecord(e0, h->stream);
-                for (int n = 0; n < npair; n++) {
+                for (int n = 0; n < nl; n++) {
                     StepArgs a = step_args(h, cur);
                     a.evt.rowptr = nullptr;
-                    cudaError_t e = launch_step_2d_tb2(a, h->storage, shape, h->stream);
+                    cudaError_t e = k == 3 ? launch_step_2d_tb3(a, shape, h->stream)
+                                           : launch_step_2d_tb2(a, h->storage, shape, h->stream);
                     if (e != cudaSuccess) {
                         st = cuda_fail(e, "lbem_autotune");
                         break;
@@ -725,13 +744,14 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_pair) {
-                best_pair = ms;
+            if (ms / (k * nl) < best_per_step) {
+                best_per_step = ms / (k * nl);
                 best_shape = shape;
+                best_tblock = k;
             }
         }
-        best_tblock = best_pair / (2 * npair) < single_ms_per_step ? 2 : 1;
     }
+    if (best_tblock == 1) best_shape = 0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->cur = cur0;
@@ -749,9 +769,9 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
 
 lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int *tile_shape, int *nshapes) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
-    if (steps_per_pass) *steps_per_pass = two_step_ok(h) ? 2 : 1;
+    if (steps_per_pass) *steps_per_pass = steps_per_launch(h);
     if (tile_shape) *tile_shape = h->tb_shape;
-    if (nshapes) *nshapes = tb2_nshapes();
+    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : tb2_nshapes();
     return LBEM_OK;
 }
 

@@ -387,6 +387,9 @@ cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int vari
 // two steps per launch (tblock.cu): uniform mu; 16-bit storage needs nx % 4 == 0
 int tb2_nshapes();
 bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag
+// three steps per launch (tblock.cu): FP32 storage, uniform mu
+int tb3_nshapes();
+cudaError_t launch_step_2d_tb3(const StepArgs &a, int shape, cudaStream_t s);
 cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s);
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);

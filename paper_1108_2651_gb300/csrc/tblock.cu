@@ -390,6 +390,284 @@ __global__ void __launch_bounds__(NT, MINB)
     asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
+// =====================================================================================================
+// Three steps per launch, FP32 storage.  Stage S0 (state at t, staged from HBM) -> step A -> S1 (t+1) -> step B
+// -> S2 (t+2) -> step C -> HBM (t+3).  Output rows y0 .. y0+TBY-1; step B computes rows y0-1 .. y0+TBY and
+// columns x0-1 .. x0+TBX (one ring column), step A rows y0-2 .. y0+TBY+1 and columns x0-2 .. x0+TBX+1 (two).
+// Every stage is staged shifted by the pull offsets, so a stage stores plane p of its row r at row
+// r - 1 - in_shift(p) of the next stage (when that row exists), exactly as in the two-step kernel; all columns
+// are indexed as in the two-step kernel (shared column j <-> x0-4+j).  HBM traffic: 44 bytes per site per three
+// steps.
+template <int TBY>
+struct TbGeom3 {
+    static constexpr int R0 = TBY + 4, R1 = TBY + 2, R2 = TBY;  // rows per plane of S0, S1, S2
+    static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
+    static constexpr int S0_PL = up32(R0 * TW), S1_PL = R1 * TW, S2_PL = R2 * TW;
+    static constexpr int S0_SZ = up32(5 * S0_PL), CL_SZ = up32(R0 * TW), S1_SZ = up32(5 * S1_PL);
+    static constexpr int S2_SZ = up32(5 * S2_PL);
+    static constexpr int SZ = S0_SZ + CL_SZ + S1_SZ + S2_SZ;
+    static constexpr size_t BYTES = sizeof(float) * SZ + sizeof(unsigned long long);
+    static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * R0 * TW;
+};
+
+template <int TBY>
+__device__ __forceinline__ bool tb3_interior(int x0, int y0, const Grid &G) {
+    return x0 - 4 >= 0 && x0 + TBX + 4 <= G.nx && y0 - 3 >= 0 && y0 + TBY + 3 <= G.ny;
+}
+
+// Window of a tile: S0 plane p rows 0 .. TBY+3 <-> global rows y0-2+r+in_shift(p); c_L^2 rows y0-2 .. y0+TBY+1.
+template <int TBY>
+__device__ __forceinline__ void tb3_load(const StepArgs &a, int x0, int y0, float *S0, float *CL, unsigned mbar,
+                                         bool tma, const CUtensorMap *tmIn, const CUtensorMap *tmCL, int nt) {
+    using Gm = TbGeom3<TBY>;
+    constexpr int R = Gm::R0, Q = TW / 4;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(Gm::TMA_BYTES)
+                         : "memory");
+#pragma unroll
+            for (int p = 0; p < 5; p++) tma_load_3d(S0 + p * Gm::S0_PL, tmIn, x0 - 4, y0 - 2 + in_shift(p), p, mbar);
+            tma_load_2d(CL, tmCL, x0 - 4, y0 - 2, mbar);
+        }
+        return;
+    }
+    const Grid &G = a.g;
+    const float *in = static_cast<const float *>(a.in.data);
+    const int tid = threadIdx.x;
+    if (((x0 - 4 >= 0) && (x0 + TBX + 4 <= G.nx)) || (G.nx & 3) == 0) {
+        for (int k = tid; k < 6 * R * Q; k += nt) {
+            const int pr = k / Q, q = k - pr * Q;
+            const int pl = pr / R, r = pr - pl * R;
+            const int gx = wrapi(x0 - 4 + 4 * q, G.nx);
+            if (pl < 5) {
+                const int gy = wrapi(y0 - 2 + r + in_shift(pl), G.ny);
+                tb_cpa16(S0 + pl * Gm::S0_PL + r * TW + 4 * q, in + pl * G.plane + (long long)gy * G.pitch + gx);
+            } else {
+                const int gy = wrapi(y0 - 2 + r, G.ny);
+                tb_cpa16(CL + r * TW + 4 * q, a.med.cL2 + (long long)gy * G.pitch + gx);
+            }
+        }
+    } else {
+        for (int k = tid; k < 6 * R * TW; k += nt) {
+            const int pr = k / TW, c = k - pr * TW;
+            const int pl = pr / R, r = pr - pl * R;
+            const int gx = wrapi(x0 - 4 + c, G.nx);
+            if (pl < 5) {
+                const int gy = wrapi(y0 - 2 + r + in_shift(pl), G.ny);
+                tb_cpa4(S0 + pl * Gm::S0_PL + r * TW + c, in + pl * G.plane + (long long)gy * G.pitch + gx);
+            } else {
+                const int gy = wrapi(y0 - 2 + r, G.ny);
+                tb_cpa4(CL + r * TW + c, a.med.cL2 + (long long)gy * G.pitch + gx);
+            }
+        }
+    }
+}
+
+// Store the five outputs of stage row r at column(s) c of the next stage D (rows RD, plane stride DPL):
+// plane p goes to row r - 1 - in_shift(p) when 0 <= that < RD.
+template <int RD, int DPL>
+__device__ __forceinline__ void tb3_store4(float *D, int r, int c, float4 o0, float4 o1, float4 o2, float4 o3,
+                                           float4 o4) {
+    float *d = D + c;
+    if (r >= 1 && r <= RD) {
+        sts4(d + 0 * DPL + (r - 1) * TW, o0);
+        sts4(d + 1 * DPL + (r - 1) * TW, o1);
+        sts4(d + 3 * DPL + (r - 1) * TW, o3);
+    }
+    if (r < RD) sts4(d + 2 * DPL + r * TW, o2);
+    if (r >= 2 && r <= RD + 1) sts4(d + 4 * DPL + (r - 2) * TW, o4);
+}
+template <int RD, int DPL>
+__device__ __forceinline__ void tb3_store1(float *D, int r, int c, const Out5 &o) {
+    if (r >= 1 && r <= RD) {
+        D[0 * DPL + (r - 1) * TW + c] = o.o0;
+        D[1 * DPL + (r - 1) * TW + c] = o.o1;
+        D[3 * DPL + (r - 1) * TW + c] = o.o3;
+    }
+    if (r < RD) D[2 * DPL + r * TW + c] = o.o2;
+    if (r >= 2 && r <= RD + 1) D[4 * DPL + (r - 2) * TW + c] = o.o4;
+}
+
+// One site of a ring column cc of stage S (plane stride SPL) at stage row r, c_L^2 ck, global (gx, gy), time t.
+template <bool EV>
+__device__ __forceinline__ Out5 tb3_site(const StepArgs &a, const float *S, int SPL, int r, int cc, float ck, int gx,
+                                         int gy, long long t, bool owned) {
+    const float *q = S + r * TW + cc;
+    const float q0 = q[0], q1 = q[SPL - 1], q2 = q[2 * SPL], q3 = q[3 * SPL + 1], q4 = q[4 * SPL];
+    if (EV) {
+        const Grid &G = a.g;
+        const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, owned, q0, q1, q2, q3, q4, ck);
+        return collide2d(q0, q1, q2, q3, q4, ck, shat);
+    }
+    return collide2d_free(q0, q1, q2, q3, q4, ck);
+}
+
+// Steps A and B of a tile (the staged window in S0/CL must be complete).  Reads into clb / clc the c_L^2 of the
+// warp's step-B and step-C rows and into clr the ring sites' c_L^2 of step B, as c_L^2 is reloaded after A.
+template <int TBY, int NT, bool EV>
+__device__ __forceinline__ void tb3_step_a(const StepArgs &a, const float *S0, const float *CL, float *S1, int x0,
+                                           int y0, long long t, float4 &clb, float4 &clc, float &clr) {
+    using Gm = TbGeom3<TBY>;
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = 4 + 4 * lane;
+    // c_L^2 row of global row g is g - (y0 - 2)
+    if (warp < Gm::R1) clb = lds4(CL + (warp + 1) * TW + c);
+    if (warp < Gm::R2) clc = lds4(CL + (warp + 2) * TW + c);
+    {
+        const int k = tid - 32 * Gm::R0;  // step-B ring sites (rows 0 .. TBY+1, columns 3 and TBX+4) on spare warps
+        if (k >= 0 && k < 2 * Gm::R1) clr = CL[((k >> 1) + 1) * TW + ((k & 1) ? TBX + 4 : 3)];
+    }
+    for (int r = warp; r < Gm::R0; r += NW) {
+        const Pull4 g(S0, Gm::S0_PL, r, c);
+        const float4 cl = lds4(CL + r * TW + c);
+        float4 o0, o1, o2, o3, o4;
+        tb_update4<EV>(a, g, cl, x0, y0 - 2 + r, t, r >= 2 && r < TBY + 2, o0, o1, o2, o3, o4);
+        tb3_store4<Gm::R1, Gm::S1_PL>(S1, r, c, o0, o1, o2, o3, o4);
+    }
+    // ring columns x0-2, x0-1, x0+TBX, x0+TBX+1 (shared columns 2, 3, TBX+4, TBX+5), on the warps after the rows
+    for (int k = tid - 32 * Gm::R0; k >= 0 && k < 4 * Gm::R0; k += NT) {
+        const int r = k >> 2, cc = (k & 3) < 2 ? 2 + (k & 3) : TBX + 2 + (k & 3);
+        const Out5 o = tb3_site<EV>(a, S0, Gm::S0_PL, r, cc, CL[r * TW + cc], x0 - 4 + cc, y0 - 2 + r, t, false);
+        tb3_store1<Gm::R1, Gm::S1_PL>(S1, r, cc, o);
+    }
+}
+
+template <int TBY, int NT, bool EV>
+__device__ __forceinline__ void tb3_step_b(const StepArgs &a, const float *S1, float *S2, int x0, int y0, long long t,
+                                           float4 clb, float clr) {
+    using Gm = TbGeom3<TBY>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = 4 + 4 * lane;
+    if (warp < Gm::R1) {
+        const int r = warp;
+        const Pull4 g(S1, Gm::S1_PL, r, c);
+        float4 o0, o1, o2, o3, o4;
+        tb_update4<EV>(a, g, clb, x0, y0 - 1 + r, t + 1, r >= 1 && r <= TBY, o0, o1, o2, o3, o4);
+        tb3_store4<Gm::R2, Gm::S2_PL>(S2, r, c, o0, o1, o2, o3, o4);
+    }
+    const int k = tid - 32 * Gm::R0;
+    if (k >= 0 && k < 2 * Gm::R1) {  // ring columns x0-1 (plane 1 needed) and x0+TBX (plane 3)
+        const int r = k >> 1, cc = (k & 1) ? TBX + 4 : 3;
+        const Out5 o = tb3_site<EV>(a, S1, Gm::S1_PL, r, cc, clr, x0 - 4 + cc, y0 - 1 + r, t + 1, false);
+        if (r >= 1 && r <= TBY) {
+            if (k & 1)
+                S2[3 * Gm::S2_PL + (r - 1) * TW + cc] = o.o3;
+            else
+                S2[1 * Gm::S2_PL + (r - 1) * TW + cc] = o.o1;
+        }
+    }
+}
+
+template <int TBY, bool EV>
+__device__ __forceinline__ void tb3_step_c(const StepArgs &a, const float *S2, int x0, int y0, long long t,
+                                           float4 clc) {
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31, oy = threadIdx.x >> 5;
+    const int gy = y0 + oy;
+    if (oy >= TBY || gy >= G.ny) return;
+    const int c = 4 + 4 * lane;
+    const Pull4 g(S2, TbGeom3<TBY>::S2_PL, oy, c);
+    float4 o0, o1, o2, o3, o4;
+    tb_update4<EV>(a, g, clc, x0, gy, t + 2, true, o0, o1, o2, o3, o4);
+    if (x0 + 4 * lane < G.pitch) {
+        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)gy * G.pitch + x0 +
+                                               4 * lane);
+        const long long pl4 = G.plane / 4;
+        __stcs(o, o0);
+        __stcs(o + pl4, o1);
+        __stcs(o + 2 * pl4, o2);
+        __stcs(o + 3 * pl4, o3);
+        __stcs(o + 4 * pl4, o4);
+    }
+}
+
+template <int TBY>
+__device__ __forceinline__ bool tb3_events(const StepArgs &a, int y0) {
+    const Grid &G = a.g;
+    return a.evt.rowptr && !(y0 >= 2 && y0 + TBY + 2 <= G.ny &&
+                             __ldg(a.evt.rowptr + y0 - 2) == __ldg(a.evt.rowptr + y0 + TBY + 2));
+}
+
+// Persistent like step2d_tb2; the window of the next tile loads during steps B and C of the current one.
+template <int TBY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    step2d_tb3(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
+               int use_tma, int ntx, int nty, int dq, int dr) {
+    using Gm = TbGeom3<TBY>;
+    static_assert(NT / 32 >= Gm::R0 + 1, "one warp per step-A row, spare threads for the ring columns");
+    static_assert(NT - 32 * Gm::R0 >= 4 * Gm::R0, "one thread per step-A ring site");
+    extern __shared__ __align__(1024) float sm[];
+    float *S0 = sm;
+    float *CL = sm + Gm::S0_SZ;
+    float *S1 = CL + Gm::CL_SZ;
+    float *S2 = S1 + Gm::S1_SZ;
+    const unsigned mbar = smem_u32(S2 + Gm::S2_SZ);
+    const Grid &G = a.g;
+    const int tid = threadIdx.x;
+    if (smem_u32(sm) & 127) use_tma = 0;
+    int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+    if (ty >= nty) return;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    tb3_load<TBY>(a, tx * TBX, ty * TBY, S0, CL, mbar, use_tma && tb3_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
+                  &tmCL, NT);
+    asm volatile("cp.async.commit_group;\n" ::);
+    bool events = tb3_events<TBY>(a, ty * TBY);
+    const long long t = a.t;
+    while (ty < nty) {
+        int ntx_ = tx + dr, nty_ = ty + dq;
+        if (ntx_ >= ntx) {
+            ntx_ -= ntx;
+            nty_++;
+        }
+        const bool has_next = nty_ < nty;
+        const bool events_next = has_next && tb3_events<TBY>(a, nty_ * TBY);
+        const int x0 = tx * TBX, y0 = ty * TBY;
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        bool ok = true;
+        if (use_tma && tb3_interior<TBY>(x0, y0, G)) {
+            ok = mbar_wait(mbar, parity);
+            parity ^= 1u;
+        }
+        // every thread's copies have landed, and step C of the previous tile is done with S2
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(&g_tb_timeouts, 1);
+            mbar_wait(mbar, parity ^ 1u);
+            return;
+        }
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), clc = clb;
+        float clr = 0.f;
+        if (events)
+            tb3_step_a<TBY, NT, true>(a, S0, CL, S1, x0, y0, t, clb, clc, clr);
+        else
+            tb3_step_a<TBY, NT, false>(a, S0, CL, S1, x0, y0, t, clb, clc, clr);
+        __syncthreads();
+        if (has_next)  // S0 and c_L^2 are free: start the loads of the next tile
+            tb3_load<TBY>(a, ntx_ * TBX, nty_ * TBY, S0, CL, mbar,
+                          use_tma && tb3_interior<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, NT);
+        asm volatile("cp.async.commit_group;\n" ::);
+        if (events)
+            tb3_step_b<TBY, NT, true>(a, S1, S2, x0, y0, t, clb, clr);
+        else
+            tb3_step_b<TBY, NT, false>(a, S1, S2, x0, y0, t, clb, clr);
+        __syncthreads();
+        if (events)
+            tb3_step_c<TBY, true>(a, S2, x0, y0, t, clc);
+        else
+            tb3_step_c<TBY, false>(a, S2, x0, y0, t, clc);
+        tx = ntx_;
+        ty = nty_;
+        events = events_next;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -749,6 +1027,43 @@ __global__ void __launch_bounds__(NT, MINB)
         events = events_next;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+template <int TBY, int NT, int MINB>
+static cudaError_t launch_tb3(const StepArgs &a, cudaStream_t s) {
+    using Gm = TbGeom3<TBY>;
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(step2d_tb3<TBY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb3<TBY, NT, MINB>, NT, Gm::BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    CUtensorMap mIn, mCL;
+    memset(&mIn, 0, sizeof mIn);
+    memset(&mCL, 0, sizeof mCL);
+    // boxes of TBY+4 rows: the two-step map builder with the row count of a (TBY+2)-row tile
+    const int use_tma = (a.g.ny >= TBY + 6 && make_maps<TBY + 2>(a, &mIn, &mCL)) ? 1 : 0;
+    const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
+    const int ntiles = ntx * nty;
+    const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
+    step2d_tb3<TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, use_tma, ntx, nty, blocks / ntx,
+                                                            blocks % ntx);
+    return cudaGetLastError();
+}
+
+int tb3_nshapes() { return 3; }
+
+cudaError_t launch_step_2d_tb3(const StepArgs &a, int shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_tb3<4, 288, 4>(a, s);
+        case 2: return launch_tb3<8, 448, 2>(a, s);
+        default: return launch_tb3<6, 384, 3>(a, s);
+    }
 }
 
 // Tensor maps of the 16-bit populations (box: one plane of TBY+2 rows of THW values), c_L^2 and, for block-int16,

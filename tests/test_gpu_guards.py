@@ -42,7 +42,8 @@ def test_guards_intact_2d(lbem, shape, storage):
 
 @pytest.mark.parametrize("shape", [(1, 1), (3, 5), (17, 45), (9, 130), (33, 257), (40, 300), (130, 644)])
 def test_guards_intact_two_step(lbem, shape):
-    """The two-step kernel in every tile shape, on ragged grids, with sources and receivers at the corners."""
+    """The two- and three-step kernels in every tile shape, on ragged grids, with sources and receivers at the
+    corners."""
     import torch
 
     eps, _ = W.random_medium(shape, 6)
@@ -56,9 +57,11 @@ def test_guards_intact_two_step(lbem, shape):
     p.rec_comp = np.array([2, 3, 4], np.int32)
     s = lbem.Solver(shape)
     s.set_problem(p)
-    for k in range(lbem.lbem_get_temporal_blocking(s.h)[2]):
-        lbem.lbem_set_temporal_blocking(s.h, 2, k)
-        s.step(3)
+    for spp in (2, 3):
+        lbem.lbem_set_temporal_blocking(s.h, spp, 0)
+        for k in range(lbem.lbem_get_temporal_blocking(s.h)[2]):
+            lbem.lbem_set_temporal_blocking(s.h, spp, k)
+            s.step(4)
     torch.cuda.synchronize()
     lbem.lbem_sync(s.h)
     lbem.lbem_check_guards(s.h)

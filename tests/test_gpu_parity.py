@@ -398,9 +398,70 @@ def test_two_step_blocking_is_bitwise_identical(lbem, shape):
         np.testing.assert_array_equal(tr.cpu().double().numpy(), ref[2])
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (17, 45), (16, 128), (33, 257), (70, 300), (130, 131),
+                                   (9, 1), (200, 7), (301, 777), (40, 4), (50, 264)])
+def test_three_step_blocking_is_bitwise_identical(lbem, shape):
+    """Three steps per launch (FP32): the same bits as single steps, for every tile shape, with sources and
+    receivers anywhere, step counts that leave a pair or a single step over, and graphs."""
+    p = _problem_small(2, shape, 96, 41, mu=False, nsrc=7, nrec=15)
+    ref = gpu_run(p, steps_per_pass=1)
+    import torch
+
+    nsh = None
+    for tile_shape, graphs in [(k, g) for k in range(3) for g in (False, True)]:
+        stream = torch.cuda.Stream() if graphs else None
+        s = lbem.Solver(p.shape, stream=stream.cuda_stream if stream else None)
+        s.set_problem(p)
+        lbem.lbem_set_temporal_blocking(s.h, 3, tile_shape)
+        spp, _, nsh = lbem.lbem_get_temporal_blocking(s.h)
+        assert spp == 3
+        if graphs:
+            lbem.lbem_set_graphs(s.h, True)
+        s.step(20)
+        s.step(19)
+        s.step(2)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        lbem.lbem_sync(s.h)
+        lbem.lbem_check_guards(s.h)
+        s.close()
+        np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
+        np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1])
+        np.testing.assert_array_equal(tr.cpu().double().numpy(), ref[2])
+    assert nsh == 3
+
+
+def test_three_step_blocking_full_size_matches_oracle(lbem):
+    """4096^2 heterogeneous medium, 21 steps: every three-step tile shape gives the bits of single steps'
+    two-step equivalent, and the result matches the oracle."""
+    p = W.heterogeneous_2d(4096, seed=2, nsteps=21)
+    import torch
+
+    res = []
+    for spp, tile_shape in ((2, 0), (3, 0), (3, 1), (3, 2)):
+        s = lbem.Solver(p.shape)
+        s.set_problem(p)
+        lbem.lbem_set_temporal_blocking(s.h, spp, tile_shape)
+        s.step(21)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        s.close()
+        res.append((E.cpu(), B.cpu(), tr.cpu()))
+    for r in res[1:]:
+        for a, b in zip(r, res[0]):
+            assert torch.equal(a, b)
+    E, B, tr = res[1]
+    oE, oB, otr, _, _ = oracle_run(p)
+    assert rel(np.moveaxis(E.cpu().double().numpy(), 0, -1), oE) < 1e-5
+    assert rel(np.moveaxis(B.cpu().double().numpy(), 0, -1), oB) < 1e-5
+    assert rel(tr.cpu().double().numpy(), otr) < 1e-5
+
+
 def test_two_step_blocking_rejects_bad_arguments(lbem):
     s = lbem.Solver((16, 16))
-    for steps, shape in ((0, 0), (3, 0), (2, 7), (2, -2)):
+    for steps, shape in ((0, 0), (4, 0), (2, 7), (3, 3), (2, -2)):
         with pytest.raises(lbem.LbemError) as e:
             lbem.lbem_set_temporal_blocking(s.h, steps, shape)
         assert e.value.status == 1
