@@ -155,7 +155,9 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * 1 = 4 rows, 288, 4; 2 = 8 rows, 448, 2.  With steps_per_pass = 2, tile_shape
  * selects the tile (128 sites wide) height, threads per CTA and CTAs per SM: 0 = 6 rows, 256 threads, 5
  * per SM (the default, also -1); 1 = 8 rows, 320, 3; 2 = 8 rows, 352, 3; 3 = 10 rows, 384, 3; 4 = 5 rows,
- * 224, 5; 5 = 4 rows, 192, 6; 6 = 14 rows, 512, 2.  LBEM_ERR_ARG for other values. */
+ * 224, 5; 5 = 4 rows, 192, 6; 6 = 14 rows, 512, 2; FP32 only: 7, 8 = no tiles: each warp streams a
+ * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM).
+ * LBEM_ERR_ARG for other values. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 
 /* Steps per launch in effect (2 or 3 only where that kernel is enabled and applies), the tile shape (as set

@@ -532,7 +532,7 @@ lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_s
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass < 1 || steps_per_pass > 3)
         return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: steps_per_pass must be 1, 2 or 3");
-    if (tile_shape < -1 || tile_shape >= (steps_per_pass == 3 ? tb3_nshapes() : tb2_nshapes()))
+    if (tile_shape < -1 || tile_shape >= (steps_per_pass == 3 ? tb3_nshapes() : tb2_nshapes(h->storage)))
         return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: tile_shape out of range");
     h->tblock = steps_per_pass;
     h->tb_shape = tile_shape < 0 ? 0 : tile_shape;
@@ -723,7 +723,7 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
     for (int k = 2; k <= max_k && st == LBEM_OK; k++) {
         if (!multi_step_base(h) || (k == 3 && h->storage != LBEM_F32)) continue;
         const int nl = trial_steps / k > 0 ? trial_steps / k : 1;
-        const int nsh = k == 3 ? tb3_nshapes() : tb2_nshapes();
+        const int nsh = k == 3 ? tb3_nshapes() : tb2_nshapes(h->storage);
         for (int shape = 0; shape < nsh && st == LBEM_OK; shape++) {
             int cur = cur0;
             for (int rep = 0; rep < 2 && st == LBEM_OK; rep++) {
@@ -771,7 +771,7 @@ lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass) *steps_per_pass = steps_per_launch(h);
     if (tile_shape) *tile_shape = h->tb_shape;
-    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : tb2_nshapes();
+    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : tb2_nshapes(h->storage);
     return LBEM_OK;
 }
 

@@ -307,6 +307,33 @@ struct StepArgs {
     long long t;  // time of the pre-collision state being collided
 };
 
+// Periodic index, cheap when v is already in range (the common case).
+__device__ __forceinline__ int wrapi(int v, int n) {
+    if ((unsigned)v < (unsigned)n) return v;
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Source current at global site (x, y) and time t, and the receiver write of the pre-collision fields (only
+// when `owned`), for the multi-step kernels.  Returns S^ (zero where there is no source).
+__device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
+                                             float g1, float g2, float g3, float g4, float cl) {
+    float shat = 0.f;
+    if (!a.evt.rowptr) return shat;
+    const int e0 = __ldg(a.evt.rowptr + y), e1 = __ldg(a.evt.rowptr + y + 1);
+    for (int e = e0; e < e1; e++) {
+        const Event ev = a.evt.ev[e];
+        if (ev.x != x) continue;
+        if (ev.kind == 0) {
+            if (ev.comp == 2 && t < a.evt.nt) shat -= __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
+        } else if (owned && t < a.evt.cap) {
+            const float s = ((g0 + g1) + (g2 + g3)) + g4;
+            a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+        }
+    }
+    return shat;
+}
+
 // ------------------------------------------------------------------ handle
 struct AdjointState;  // defined in adjoint.cu
 
@@ -385,7 +412,10 @@ StepArgs step_args(const lbem_t *h, int cur_in);
 int nvariants_2d();
 cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int variant, cudaStream_t s);
 // two steps per launch (tblock.cu): uniform mu; 16-bit storage needs nx % 4 == 0
-int tb2_nshapes();
+int tb2_nshapes(int storage);
+// two steps per launch by register streaming (rstream.cu): FP32 storage, uniform mu
+int rs2_nshapes();
+cudaError_t launch_step_2d_rs2(const StepArgs &a, int shape, cudaStream_t s);
 bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag
 // three steps per launch (tblock.cu): FP32 storage, uniform mu
 int tb3_nshapes();

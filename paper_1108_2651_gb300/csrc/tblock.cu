@@ -35,32 +35,6 @@ constexpr int TW = TBX + 8;  // staged columns x0-4 .. x0+TBX+3 (16-byte aligned
 // plane p row j of the t+1 stage holds global row y0 + j + in_shift(p).
 __device__ __host__ constexpr int in_shift(int p) { return p == 2 ? -1 : p == 4 ? 1 : 0; }
 
-// Periodic index, cheap when v is already in range (the common case).
-__device__ __forceinline__ int wrapi(int v, int n) {
-    if ((unsigned)v < (unsigned)n) return v;
-    v %= n;
-    return v < 0 ? v + n : v;
-}
-
-// Source current at global site (x, y) and time t, and the receiver write of the pre-collision
-// fields (only when `owned`).  Returns S^ (zero where there is no source).
-__device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
-                                             float g1, float g2, float g3, float g4, float cl) {
-    float shat = 0.f;
-    if (!a.evt.rowptr) return shat;
-    const int e0 = __ldg(a.evt.rowptr + y), e1 = __ldg(a.evt.rowptr + y + 1);
-    for (int e = e0; e < e1; e++) {
-        const Event ev = a.evt.ev[e];
-        if (ev.x != x) continue;
-        if (ev.kind == 0) {
-            if (ev.comp == 2 && t < a.evt.nt) shat -= __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
-        } else if (owned && t < a.evt.cap) {
-            const float s = ((g0 + g1) + (g2 + g3)) + g4;
-            a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
-        }
-    }
-    return shat;
-}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void tb_cpa4(float *dst, const float *src) {
@@ -1140,7 +1114,7 @@ static cudaError_t launch_16(const StepArgs &a, int shape, cudaStream_t s) {
 
 // Tile shapes (rows, threads, CTAs per SM).  Measured on 4096^2 (heterogeneous medium, FP32): 6 rows at five
 // CTAs per SM is the fastest; the others remain selectable for other sizes and for the bit-identity tests.
-int tb2_nshapes() { return 7; }
+int tb2_nshapes(int storage) { return storage == LBEM_F32 ? 7 + rs2_nshapes() : 7; }
 
 cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s) {
     switch (storage) {
@@ -1149,6 +1123,7 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
         default: break;
     }
+    if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)
     switch (shape) {
         case 1: return launch_tb<8, 320, 3>(a, s);
         case 2: return launch_tb<8, 352, 3>(a, s);   // ring sites on the 11th warp

@@ -379,7 +379,11 @@ def test_two_step_blocking_is_bitwise_identical(lbem, shape):
     ref = gpu_run(p, steps_per_pass=1)
     import torch
 
-    for tile_shape, graphs in [(k, g) for k in range(7) for g in (False, True)]:
+    probe = lbem.Solver((4, 4))
+    nsh = lbem.lbem_get_temporal_blocking(probe.h)[2]  # FP32: tile shapes, then the register-streaming kernel
+    probe.close()
+    assert nsh == 9
+    for tile_shape, graphs in [(k, g) for k in range(nsh) for g in (False, True)]:
         stream = torch.cuda.Stream() if graphs else None
         s = lbem.Solver(p.shape, stream=stream.cuda_stream if stream else None)
         s.set_problem(p)
@@ -461,7 +465,7 @@ def test_three_step_blocking_full_size_matches_oracle(lbem):
 
 def test_two_step_blocking_rejects_bad_arguments(lbem):
     s = lbem.Solver((16, 16))
-    for steps, shape in ((0, 0), (4, 0), (2, 7), (3, 3), (2, -2)):
+    for steps, shape in ((0, 0), (4, 0), (2, 9), (3, 3), (2, -2)):
         with pytest.raises(lbem.LbemError) as e:
             lbem.lbem_set_temporal_blocking(s.h, steps, shape)
         assert e.value.status == 1
@@ -475,7 +479,7 @@ def test_two_step_blocking_full_size_matches_oracle(lbem):
     import torch
 
     res = []
-    for tile_shape in range(7):
+    for tile_shape in range(9):
         s = lbem.Solver(p.shape)
         s.set_problem(p)
         lbem.lbem_set_temporal_blocking(s.h, 2, tile_shape)
