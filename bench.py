@@ -38,7 +38,9 @@ BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it is now built, keyed by
 # (workload, storage, variant); the capture and its command are summarised in profiles/.  Only reported for
 # the kernel that was captured.
-NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 431.313408e6 + 290.863616e6}
+NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 431.689216e6 + 290.764544e6,
+               ("het2d_4096", "f16", "tb2-0"): 238.224640e6 + 128.392192e6,
+               ("het2d_4096", "i16b", "tb2-0"): 267.625984e6 + 152.067840e6}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -154,9 +156,10 @@ def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
 
 def _time_run(lbem, torch, s, p, nsteps, stream, passes=1):
     """Device time (ms) of `passes` full runs of nsteps steps on solver s (launch shape autotuned), after one
-    untimed run; returns (ms, variant)."""
+    untimed run; returns (ms, variant, steps per launch)."""
     s.set_problem(p)
     v = lbem.lbem_autotune(s.h, 50)
+    spp = lbem.lbem_get_temporal_blocking(s.h)[0]
     lbem.lbem_step(s.h, nsteps)
     ev = []
     for _ in range(passes):
@@ -167,7 +170,7 @@ def _time_run(lbem, torch, s, p, nsteps, stream, passes=1):
         b.record(stream)
         ev.append((a, b))
     torch.cuda.synchronize()
-    return float(np.mean([a.elapsed_time(b) for a, b in ev])), v
+    return float(np.mean([a.elapsed_time(b) for a, b in ev])), v, spp
 
 
 def other_forms(lbem, torch, p, peak, stream):
@@ -178,16 +181,17 @@ def other_forms(lbem, torch, p, peak, stream):
     n = int(np.prod(p.shape))
     for st in ("f16", "bf16", "i16b"):
         s = lbem.Solver(p.shape, storage=st, stream=stream.cuda_stream)
-        ms, v = _time_run(lbem, torch, s, p, p.nsteps, stream)
+        ms, v, spp = _time_run(lbem, torch, s, p, p.nsteps, stream)
         s.close()
-        per = ms / p.nsteps
+        per = ms / (p.nsteps // spp + p.nsteps % spp)  # per launch of `spp` steps
         gbs = BYTES_PER_SITE[st] * n / (per * 1e-3) / 1e9
         out[st] = {"mlups": n * p.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
-                   "frac": gbs / peak, "bytes_per_site": BYTES_PER_SITE[st], "variant": v}
+                   "frac": gbs / peak, "bytes_per_site_per_launch": BYTES_PER_SITE[st], "steps_per_launch": spp,
+                   "variant": v}
     # single-step launches (same workload, FP32): the fastest single-step kernel, 44 B/site per step
     s = lbem.Solver(p.shape, stream=stream.cuda_stream)
     lbem.lbem_set_temporal_blocking(s.h, 1, -1)
-    ms, v = _time_run(lbem, torch, s, p, p.nsteps, stream)
+    ms, v, _ = _time_run(lbem, torch, s, p, p.nsteps, stream)
     s.close()
     per = ms / p.nsteps
     gbs = 44 * n / (per * 1e-3) / 1e9
@@ -222,7 +226,7 @@ def other_forms(lbem, torch, p, peak, stream):
                        "graph": True}
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
-    ms, v = _time_run(lbem, torch, s, q, 1000, stream)
+    ms, v, _ = _time_run(lbem, torch, s, q, 1000, stream)
     # adjoint: forward with a checkpoint every 100 steps, then the reverse-time pass (segment recompute +
     # adjoint kernel, FP64 gradient accumulation), cotangent = the traces themselves; the faster of the
     # two one-site-per-thread adjoint shapes (3D variants 1 and 2) on a short trial
@@ -468,8 +472,9 @@ def main():
     peak, peak_kind = measured_peak_gbs()
     bps = BYTES_PER_SITE[args.storage] if p.D == 2 else 172
     achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
-    if spp == 2:
-        kname, kid = f"step2d_tb2 (tile shape {tile_shape}, two steps per launch)", f"tb2-{tile_shape}"
+    if spp >= 2:
+        kern = {2: "step2d_tb2", 3: "step2d_tb3"}[spp] + ("" if args.storage == "f32" else f"h<{args.storage}>")
+        kname, kid = f"{kern} (tile shape {tile_shape}, {spp} steps per launch)", f"tb{spp}-{tile_shape}"
     else:
         kname = (f"step2d<{args.storage}>" if p.D == 2 else "step3d") + f" (variant {variant})"
         kid = variant
