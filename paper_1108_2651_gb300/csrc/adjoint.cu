@@ -25,7 +25,10 @@
 // Checkpointing: lbem_forward_record keeps the state every K steps; the
 // backward pass recomputes one segment of at most K states at a time (kept
 // in device memory) and runs the adjoint kernel backwards through it.  The
-// gradient is accumulated over time steps in FP64.
+// gradient is accumulated over time steps in FP64; each step's contribution at
+// a site is formed in FP32, like the rest of the arithmetic (GB300's FP64 rate
+// is a small fraction of its FP32 rate, and the per-site FP64 products had made
+// the adjoint step compute-bound).
 #include <math.h>
 
 #include <algorithm>
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(BLOCK) adjoint2d(AdjArgs a) {
     const float4 cl = f4(a.cL2, 0, 0, row, G.pitch, c);
     float4 jz = z4;
     float4 o[5];
-    double dg[4] = {0.0, 0.0, 0.0, 0.0};
+    float dg[4] = {0.f, 0.f, 0.f, 0.f};  // this step's contribution, FP32; accumulated over steps in FP64
     for (int j = 0; j < 4; j++) {
         const float q = get(cl, j), w0 = 1.f - 2.f * q;
         const float mm = ((get(m[1], j) + get(m[2], j)) + get(m[3], j)) + get(m[4], j);
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(BLOCK) adjoint2d(AdjArgs a) {
         set(o[2], j, 2.f * nu - get(m[4], j));
         set(o[4], j, 2.f * nu - get(m[2], j));
         const float s = get(sg, j);
-        dg[j] = (double)s * (double)mm - 4.0 * (double)s * (double)get(m[0], j);
+        dg[j] = s * mm - 4.f * (s * get(m[0], j));
     }
     if (a.evt.rowptr) {
         const int e0 = __ldg(a.evt.rowptr + row), e1 = __ldg(a.evt.rowptr + row + 1);
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(BLOCK) adjoint2d(AdjArgs a) {
                 if (ev.comp == 2) {  // E_z = -c_L^2 sigma
                     const float d = -get(cl, j) * r;
                     for (int i = 0; i < 5; i++) set(o[i], j, get(o[i], j) + d);
-                    dg[j] -= (double)get(sg, j) * (double)r;
+                    dg[j] -= get(sg, j) * r;
                 } else if (ev.comp == 3) {  // B_x = g_4 - g_2
                     set(o[4], j, get(o[4], j) + r);
                     set(o[2], j, get(o[2], j) - r);
@@ -177,9 +180,9 @@ __global__ void __launch_bounds__(BLOCK) adjoint2d(AdjArgs a) {
     }
     for (int j = 0; j < 4; j++) {
         const float mm = ((get(m[1], j) + get(m[2], j)) + get(m[3], j)) + get(m[4], j);
-        dg[j] += (double)get(jz, j) * (0.5 * (double)mm - 2.0 * (double)get(m[0], j));
+        dg[j] += get(jz, j) * (0.5f * mm - 2.f * get(m[0], j));
         const int x = 4 * c + j;
-        if (x < G.nx) a.gcl[(long long)row * G.pitch + x] += dg[j];
+        if (x < G.nx) a.gcl[(long long)row * G.pitch + x] += (double)dg[j];
     }
     for (int i = 0; i < 5; i++) Codec<LBEM_F32>::store4(PopBuf{a.lam_out, nullptr, G.plane, 0, G.pitch, 0}, i, row, c, o[i]);
 }
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d(AdjArgs a) {
     if (!active) return;
     const float4 cl = f4(a.cL2, 0, 0, row, G.pitch, c);
     float4 jv[3] = {z4, z4, z4};
-    double dg[4] = {0.0, 0.0, 0.0, 0.0};
+    float dg[4] = {0.f, 0.f, 0.f, 0.f};  // this step's contribution, FP32; accumulated over steps in FP64
     // receivers add to lambda after M^T; collect them first per site
     float4 recE[3] = {z4, z4, z4}, recB[3] = {z4, z4, z4};
     if (a.evt.rowptr) {
@@ -286,16 +289,16 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d(AdjArgs a) {
         o[18] = (Lx + hy) - h[18];    // -z
         o[19] = (Ly - hx) - h[19];
         o[20] = Lz - h[20];
-        double d = 0.0;
+        float d = 0.f;
         for (int gm = 0; gm < 3; gm++) {
-            const double s = get(sg[gm], j);
-            d += s * (double)mv[gm] - 6.0 * s * (double)h[gm];
-            d += (double)get(jv[gm], j) * (0.25 * (double)mv[gm] - 1.5 * (double)h[gm]);
+            const float s = get(sg[gm], j);
+            d += s * mv[gm] - 6.f * (s * h[gm]);
+            d += get(jv[gm], j) * (0.25f * mv[gm] - 1.5f * h[gm]);
             // E_gamma = -c_L^2 sigma_gamma receivers
             const float rE = get(recE[gm], j);
             if (rE != 0.f) {
                 for (int i = 0; i < 7; i++) o[3 * i + gm] -= q * rE;
-                d -= s * (double)rE;
+                d -= s * rE;
             }
         }
         // B receivers: B_nu = sum_i (g_i x c_i)_nu = eps_{gamma kappa nu} c_{i kappa} g_{i gamma}
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(BLOCK) adjoint3d(AdjArgs a) {
     }
     for (int j = 0; j < 4; j++) {
         const int x = 4 * c + j;
-        if (x < G.nx) a.gcl[(long long)row * G.pitch + x] += dg[j];
+        if (x < G.nx) a.gcl[(long long)row * G.pitch + x] += (double)dg[j];
     }
     PopBuf ob{a.lam_out, nullptr, G.plane, 0, G.pitch, 0};
 #pragma unroll
@@ -392,12 +395,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) adjoint3d_site(AdjArgs a) {
     const float vz = (h[6] - h[15]) - (h[4] - h[13]);
     const float hx = 0.5f * vx, hy = 0.5f * vy, hz = 0.5f * vz;
     const float Lx = 2.f * nu[0], Ly = 2.f * nu[1], Lz = 2.f * nu[2];
-    double d = 0.0;
+    float d = 0.f;  // this step's contribution, FP32; accumulated over steps in FP64
 #pragma unroll
     for (int gm = 0; gm < 3; gm++) {
-        const double sgm = sg[gm];
-        d += sgm * (double)mv[gm] - 6.0 * sgm * (double)h[gm];
-        d += (double)jv[gm] * (0.25 * (double)mv[gm] - 1.5 * (double)h[gm]);
+        d += sg[gm] * mv[gm] - 6.f * (sg[gm] * h[gm]);
+        d += jv[gm] * (0.25f * mv[gm] - 1.5f * h[gm]);
     }
     float out[21];
     out[0] = Lx - h[0];
@@ -425,14 +427,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) adjoint3d_site(AdjArgs a) {
     for (int gm = 0; gm < 3; gm++)
         if (rE[gm] != 0.f) {
             for (int i = 0; i < 7; i++) out[3 * i + gm] -= q * rE[gm];
-            d -= (double)sg[gm] * (double)rE[gm];
+            d -= sg[gm] * rE[gm];
         }
     if (rB[0] != 0.f || rB[1] != 0.f || rB[2] != 0.f) {
         out[10] += rB[0]; out[19] -= rB[0]; out[8] -= rB[0]; out[17] += rB[0];
         out[5] += rB[1]; out[14] -= rB[1]; out[9] -= rB[1]; out[18] += rB[1];
         out[6] += rB[2]; out[15] -= rB[2]; out[4] -= rB[2]; out[13] += rB[2];
     }
-    a.gcl[o] = gacc + d;
+    a.gcl[o] = gacc + (double)d;
 #pragma unroll
     for (int p = 0; p < 21; p++) __stcs(a.lam_out + p * G.plane + o, out[p]);
 }
