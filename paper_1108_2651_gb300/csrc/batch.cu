@@ -236,16 +236,29 @@ __global__ void __launch_bounds__(BLOCK, MINB) step2d_batch_lin(const Member *__
         }
     }
     float4 o[5];
+    // rows without a source have S^ = +0 everywhere: collide2d_free gives the same bits
+    if (m.evt.rowptr && __ldg(m.evt.rowptr + rr) != __ldg(m.evt.rowptr + rr + 1)) {
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const float g0 = get(g[0], j), g1 = get(g[1], j), g2 = get(g[2], j), g3 = get(g[3], j), g4 = get(g[4], j),
-                    q = get(cl, j), sh = get(shat, j);
-        const Out5 u = collide2d(g0, g1, g2, g3, g4, q, sh);
-        set(o[0], j, u.o0);
-        set(o[1], j, u.o1);
-        set(o[2], j, u.o2);
-        set(o[3], j, u.o3);
-        set(o[4], j, u.o4);
+        for (int j = 0; j < 4; j++) {
+            const Out5 u = collide2d(get(g[0], j), get(g[1], j), get(g[2], j), get(g[3], j), get(g[4], j),
+                                     get(cl, j), get(shat, j));
+            set(o[0], j, u.o0);
+            set(o[1], j, u.o1);
+            set(o[2], j, u.o2);
+            set(o[3], j, u.o3);
+            set(o[4], j, u.o4);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const Out5 u = collide2d_free(get(g[0], j), get(g[1], j), get(g[2], j), get(g[3], j), get(g[4], j),
+                                          get(cl, j));
+            set(o[0], j, u.o0);
+            set(o[1], j, u.o1);
+            set(o[2], j, u.o2);
+            set(o[3], j, u.o3);
+            set(o[4], j, u.o4);
+        }
     }
     for (int i = 0; i < 5; i++) C::store4(out, i, rr, c, o[i]);
 }

@@ -110,15 +110,30 @@ __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {
             }
         }
         float4 o0, o1, o2, o3, o4;
+        // rows without a source (and mu uniform) have S^ = +0 everywhere: collide2d_free gives the same bits
+        const bool src = MU || (a.evt.rowptr && __ldg(a.evt.rowptr + row) != __ldg(a.evt.rowptr + row + 1));
+        if (src) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            Out5 o = collide2d(get(g[r][0], j), get(g[r][1], j), get(g[r][2], j), get(g[r][3], j), get(g[r][4], j),
-                               get(cl[r], j), get(shat, j));
-            set(o0, j, o.o0);
-            set(o1, j, o.o1);
-            set(o2, j, o.o2);
-            set(o3, j, o.o3);
-            set(o4, j, o.o4);
+            for (int j = 0; j < 4; j++) {
+                Out5 o = collide2d(get(g[r][0], j), get(g[r][1], j), get(g[r][2], j), get(g[r][3], j),
+                                   get(g[r][4], j), get(cl[r], j), get(shat, j));
+                set(o0, j, o.o0);
+                set(o1, j, o.o1);
+                set(o2, j, o.o2);
+                set(o3, j, o.o3);
+                set(o4, j, o.o4);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                Out5 o = collide2d_free(get(g[r][0], j), get(g[r][1], j), get(g[r][2], j), get(g[r][3], j),
+                                        get(g[r][4], j), get(cl[r], j));
+                set(o0, j, o.o0);
+                set(o1, j, o.o1);
+                set(o2, j, o.o2);
+                set(o3, j, o.o3);
+                set(o4, j, o.o4);
+            }
         }
         if (active) {
             C::store4(a.out, 0, row, c, o0);
@@ -654,14 +669,28 @@ __global__ void __launch_bounds__(BLOCK, MINB) step2d_w8(StepArgs a) {
         }
     }
     F8 o0, o1, o2, o3, o4;
+    // rows without a source (and mu uniform) have S^ = +0 everywhere: collide2d_free gives the same bits
+    const bool src = MU || (a.evt.rowptr && __ldg(a.evt.rowptr + row) != __ldg(a.evt.rowptr + row + 1));
+    if (src) {
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const Out5 o = collide2d(g0.v[k], g1.v[k], g2.v[k], g3.v[k], g4.v[k], cl[k], shat[k]);
-        o0.v[k] = o.o0;
-        o1.v[k] = o.o1;
-        o2.v[k] = o.o2;
-        o3.v[k] = o.o3;
-        o4.v[k] = o.o4;
+        for (int k = 0; k < 8; k++) {
+            const Out5 o = collide2d(g0.v[k], g1.v[k], g2.v[k], g3.v[k], g4.v[k], cl[k], shat[k]);
+            o0.v[k] = o.o0;
+            o1.v[k] = o.o1;
+            o2.v[k] = o.o2;
+            o3.v[k] = o.o3;
+            o4.v[k] = o.o4;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const Out5 o = collide2d_free(g0.v[k], g1.v[k], g2.v[k], g3.v[k], g4.v[k], cl[k]);
+            o0.v[k] = o.o0;
+            o1.v[k] = o.o1;
+            o2.v[k] = o.o2;
+            o3.v[k] = o.o3;
+            o4.v[k] = o.o4;
+        }
     }
     store8<ST>(a.out, 0, row, c8, o0);
     store8<ST>(a.out, 1, row, c8, o1);
