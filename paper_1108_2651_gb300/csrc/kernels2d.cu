@@ -372,9 +372,9 @@ __device__ __forceinline__ float4 dec4(const PopBuf &b, const char *v, unsigned 
         return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u), __uint_as_float(r.y << 16),
                            __uint_as_float(r.y & 0xffff0000u));
     const int e = (int)(signed char)((exword >> (8 * (c & 3))) & 0xffu);
-    const float f = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
-    return make_float4(i16_to_f((short)(r.x & 0xffffu)) * f, i16_to_f((short)(r.x >> 16)) * f,
-                       i16_to_f((short)(r.y & 0xffffu)) * f, i16_to_f((short)(r.y >> 16)) * f);
+    const float f = i16b_factor(e);
+    const float2 lo = i16x2_to_f2(r.x, f), hi = i16x2_to_f2(r.y, f);
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 template <int ST>
@@ -384,7 +384,7 @@ __device__ __forceinline__ float dec1(const PopBuf &b, unsigned w, int x, unsign
     if (ST == LBEM_F16) return __half2float(__ushort_as_half(hbits)) * b.inv_scale;
     if (ST == LBEM_BF16) return __uint_as_float(((unsigned)hbits) << 16);
     const int e = (int)(signed char)((exword >> (8 * ((x >> 2) & 3))) & 0xffu);
-    return (e == I16B_ZERO) ? 0.f : i16_to_f((short)hbits) * pow2f(e - 15);
+    return i16_to_f((short)hbits) * i16b_factor(e);
 }
 
 template <int ST, bool MU>
@@ -559,9 +559,9 @@ __device__ __forceinline__ F8 load8(const PopBuf &b, int p, int row, int c8) {
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int e = (int)(signed char)((e2 >> (8 * (k >> 1))) & 0xffu);
-            const float sc = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
-            f.v[2 * k] = i16_to_f((short)(w[k] & 0xffffu)) * sc;
-            f.v[2 * k + 1] = i16_to_f((short)(w[k] >> 16)) * sc;
+            const float2 d = i16x2_to_f2(w[k], i16b_factor(e));
+            f.v[2 * k] = d.x;
+            f.v[2 * k + 1] = d.y;
         }
     }
     return f;

@@ -149,6 +149,10 @@ constexpr int kMagicBits = 0x4B400000;
 __device__ __forceinline__ float i16_to_f(int q) { return __int_as_float(kMagicBits + q) - kMagic; }
 __device__ __forceinline__ int f_to_int_rn(float v) { return __float_as_int(v + kMagic) - kMagicBits; }
 
+// The factor 2^(e-15) of a block-int16 block with exponent e, 0 for a zero block (e = -128): the encoder writes
+// e in [-99, 100] or 127, so e + 112 is a positive biased exponent, and max(e + 112, 0) maps e = -128 to +0.
+__device__ __forceinline__ float i16b_factor(int e) { return __int_as_float(max(e + 112, 0) << 23); }
+
 // Block-int16 decoding of the two values packed in w (low half first), f = 2^(e-15) (0 for a zero block):
 // h ^ 0x8000 = q + 2^15 placed under the exponent of 1.5 * 2^23 gives the float 1.5 * 2^23 + 2^15 + q exactly,
 // and one rounding of (that float) * f - (1.5 * 2^23 + 2^15) * f is q * f, the same value as float(q) * f.
@@ -167,8 +171,7 @@ struct Codec<LBEM_I16B> {
         const uint2 *q = reinterpret_cast<const uint2 *>(static_cast<const int16_t *>(b.data) + p * b.plane +
                                                          (long long)row * b.pitch);
         uint2 r = __ldg(q + c);
-        int e = __ldg(b.ex + p * b.explane + (long long)row * b.expitch + c);
-        float f = (e == I16B_ZERO) ? 0.f : pow2f(e - 15);
+        const float f = i16b_factor(__ldg(b.ex + p * b.explane + (long long)row * b.expitch + c));
         const float2 lo = i16x2_to_f2(r.x, f), hi = i16x2_to_f2(r.y, f);
         return make_float4(lo.x, lo.y, hi.x, hi.y);
     }
@@ -179,27 +182,22 @@ struct Codec<LBEM_I16B> {
     }
     // encoded 4-site block: mantissas in r, exponent returned
     __device__ static __forceinline__ int enc4e(float4 v, uint2 &r) {
-        float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-        int e;
-        if (!(m < 0x1p+100f)) {  // huge or NaN: saturate, so the state stays visibly wrong
-            e = 127;
-            r.x = r.y = 0x7fff7fffu;
-        } else if (m < 0x1p-100f) {  // negligible block -> exact zero
-            e = I16B_ZERO;
-            r.x = r.y = 0u;
-        } else {
-            e = ((__float_as_int(m) >> 23) & 0xff) - 127 + 1;
-            const float s = pow2f(15 - e);
-            // |v * s| <= 2^15 here; clamping to the integers +-32767 before the rounding equals clamping after it.
-            // The adder-based rounding leaves q in the low 16 bits of the sum's bit pattern (two's complement).
-            const unsigned b0 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.x, s), -32767.f), 32767.f) + kMagic);
-            const unsigned b1 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.y, s), -32767.f), 32767.f) + kMagic);
-            const unsigned b2 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.z, s), -32767.f), 32767.f) + kMagic);
-            const unsigned b3 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.w, s), -32767.f), 32767.f) + kMagic);
-            r.x = __byte_perm(b0, b1, 0x5410);
-            r.y = __byte_perm(b2, b3, 0x5410);
-        }
-        return e;
+        const float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+        // the ordinary block, computed for every block (no divergent branches); the two special cases below
+        // replace its result.  For 2^-100 <= m < 2^100 the exponent e lies in [-99, 100], so the clamp is idle.
+        const int e = ((__float_as_int(m) >> 23) & 0xff) - 127 + 1;
+        const float s = pow2f(15 - min(max(e, -99), 100));
+        // |v * s| <= 2^15 here; clamping to the integers +-32767 before the rounding equals clamping after it.
+        // The adder-based rounding leaves q in the low 16 bits of the sum's bit pattern (two's complement).
+        const unsigned b0 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.x, s), -32767.f), 32767.f) + kMagic);
+        const unsigned b1 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.y, s), -32767.f), 32767.f) + kMagic);
+        const unsigned b2 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.z, s), -32767.f), 32767.f) + kMagic);
+        const unsigned b3 = __float_as_uint(fminf(fmaxf(__fmul_rn(v.w, s), -32767.f), 32767.f) + kMagic);
+        const bool huge = !(m < 0x1p+100f);  // huge or NaN: saturate, so the state stays visibly wrong
+        const bool tiny = m < 0x1p-100f;     // negligible block -> exact zero
+        r.x = huge ? 0x7fff7fffu : tiny ? 0u : __byte_perm(b0, b1, 0x5410);
+        r.y = huge ? 0x7fff7fffu : tiny ? 0u : __byte_perm(b2, b3, 0x5410);
+        return huge ? 127 : tiny ? I16B_ZERO : e;
     }
     __device__ static __forceinline__ void store4(const PopBuf &b, int p, int row, int c, float4 v) {
         uint2 r;

@@ -743,7 +743,7 @@ __device__ __forceinline__ float dec16(unsigned h, float f) {
     if (ST == LBEM_BF16) return __uint_as_float(h << 16);
     return __fmul_rn(i16_to_f((short)h), f);
 }
-__device__ __forceinline__ float ex_factor(int e) { return (e == I16B_ZERO) ? 0.f : pow2f(e - 15); }
+__device__ __forceinline__ float ex_factor(int e) { return i16b_factor(e); }
 
 // The two stored values packed in w (low half first), decoded as dec16 does.
 template <int ST>
