@@ -463,6 +463,31 @@ def test_three_step_blocking_full_size_matches_oracle(lbem):
     assert rel(tr.cpu().double().numpy(), otr) < 1e-5
 
 
+@pytest.mark.parametrize("spp", [2, 3])
+def test_autotuned_stepping_is_bitwise_identical(lbem, spp):
+    """lbem_autotune picks among single steps and every two- (three-) step tile shape; whatever it keeps, the
+    results are those of single steps, and the state it timed on is restored."""
+    p = _problem_small(2, (150, 390), 97, 33, mu=False, nsrc=5, nrec=9)
+    ref = gpu_run(p, steps_per_pass=1)
+    import torch
+
+    s = lbem.Solver(p.shape)
+    s.set_problem(p)
+    lbem.lbem_set_temporal_blocking(s.h, spp, -1)
+    lbem.lbem_autotune(s.h, 6)
+    got_spp, shape, nsh = lbem.lbem_get_temporal_blocking(s.h)
+    assert 1 <= got_spp <= spp and 0 <= shape < max(nsh, 1)
+    assert lbem.lbem_time(s.h) == 0
+    s.step(33)
+    E, B = s.fields()
+    tr = s.traces(p.rec_site.size)
+    torch.cuda.synchronize()
+    s.close()
+    np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
+    np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1])
+    np.testing.assert_array_equal(tr.cpu().double().numpy(), ref[2])
+
+
 def test_two_step_blocking_rejects_bad_arguments(lbem):
     s = lbem.Solver((16, 16))
     for steps, shape in ((0, 0), (4, 0), (2, 9), (3, 3), (2, -2)):
