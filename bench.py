@@ -154,6 +154,57 @@ def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
                       "gpu_launches": args.steps * nsteps, "clocks": clk.summary()}), flush=True)
 
 
+def run_adjoint_main(args, lbem, torch, stream, peak, peak_kind):
+    """The 3D adjoint on a 96^3 heterogeneous medium as the timed workload (small enough to profile): one
+    benchmark step = forward record (lb_steps steps, checkpoint every 10) + the backward pass."""
+    nsteps = args.lb_steps or 40
+    q = W.heterogeneous_3d(96, seed=4, nsteps=nsteps)
+    s = lbem.Solver(q.shape, stream=stream.cuda_stream)
+    s.set_problem(q)
+    lbem.lbem_set_variant(s.h, 1)
+    n3 = 96 ** 3
+    cot = torch.empty(q.rec_site.size * nsteps, dtype=torch.float32, device="cuda")
+    grad = torch.empty(n3, dtype=torch.float32, device="cuda")
+
+    def one(ev=None):
+        lbem.lbem_set_fields(s.h)
+        lbem.lbem_forward_record(s.h, nsteps, 10)
+        lbem.lbem_traces(s.h, cot)
+        if ev is not None:
+            ev[0].record(stream)
+        lbem.lbem_adjoint(s.h, cot, grad)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            one(evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(stop) / args.steps
+    bwd = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    s.close()
+    # backward bytes: recompute of nsteps - every forward steps (172 B/site) + nsteps adjoint steps (272 B/site)
+    bb = ((nsteps - 10) * 172 + nsteps * 272) * n3
+    gbs = bb / (bwd * 1e-3) / 1e9
+    print(json.dumps({"metric": "Mlups", "value": n3 * nsteps / (ms * 1e-3) / 1e6, "unit": "Mlups", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "adjoint3d_96", "grid": [96, 96, 96], "lb_steps": nsteps,
+                                 "checkpoint_every": 10, "note": "value counts forward site-steps per second of "
+                                 "forward record + backward pass"},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "traffic": None, "kernel": "backward pass (recompute + adjoint3d_site)",
+                                   "ms_backward": bwd, "peak_kind": peak_kind},
+                      "gpu_launches": None, "clocks": clk.summary()}), flush=True)
+
+
 def _time_run(lbem, torch, s, p, nsteps, stream, passes=1):
     """Device time (ms) of `passes` full runs of nsteps steps on solver s (launch shape autotuned), after one
     untimed run; returns (ms, variant, steps per launch)."""
@@ -370,7 +421,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
-    ap.add_argument("--workload", default="het2d_4096", choices=["het2d_4096", "het2d_1024", "het3d_192", "batch256"])
+    ap.add_argument("--workload", default="het2d_4096",
+                    choices=["het2d_4096", "het2d_1024", "het3d_192", "batch256", "adjoint3d_96"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
     ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
     ap.add_argument("--ref-steps", type=int, default=40)
@@ -399,6 +451,10 @@ def main():
     if args.workload == "batch256":
         peak, peak_kind = measured_peak_gbs()
         run_batch_main(args, lbem, torch, torch.cuda.Stream(), peak, peak_kind)
+        return
+    if args.workload == "adjoint3d_96":
+        peak, peak_kind = measured_peak_gbs()
+        run_adjoint_main(args, lbem, torch, torch.cuda.Stream(), peak, peak_kind)
         return
     p = workload(args.workload)
     if p.D == 3:
