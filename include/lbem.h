@@ -132,8 +132,10 @@ lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const in
 /* Advance nsteps steps: per site and step, pull-stream (Eq. 18), moments (Eqs.
  * 9-10), source (Eq. 3), equilibrium (Eq. 8), collision at tau = dt/2 (Eq. 17);
  * receivers sample the pre-collision fields.  One fused kernel launch per step,
- * enqueued on the stream (or replayed from a cached CUDA graph when enabled by
- * lbem_set_graphs).  Requires a medium.  nsteps >= 0. */
+ * or per two (three) steps where lbem_set_temporal_blocking enables it (two is
+ * the default for 2D with uniform mu), enqueued on the stream (or replayed from
+ * a cached CUDA graph when enabled by lbem_set_graphs).  Requires a medium.
+ * nsteps >= 0. */
 lbem_status lbem_step(lbem_t *h, int nsteps);
 
 /* Watchdog (off by default): with every > 0, lbem_step computes the FP64 field energy (as
