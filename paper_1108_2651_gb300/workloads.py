@@ -141,6 +141,25 @@ def heterogeneous_2d(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec_radiu
     return point_source_problem(2, shape, nidx, nsteps, c, nrec, recs, name=name or f"het2d_{n}")
 
 
+def heterogeneous_2d_mu(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec_radius=None, mu_contrast=1.0,
+                        mu_seed=None, name=None):
+    """heterogeneous_2d with the same refractive index n = 1 + 2 s but a heterogeneous permeability:
+    mu_r = 1 + mu_contrast * s2 (s2 a second smoothed unit field, seed mu_seed, default seed + 7919) and
+    eps_r = n^2 / mu_r, so the wave speed c/n is unchanged while the impedance varies and the B x grad ln mu
+    source term (Eq. 3) acts everywhere."""
+    p = heterogeneous_2d(n, seed, nsteps, sigma, nrec, rec_radius, name=name or f"het2d_mu_{n}")
+    n2 = p.eps_r
+    mu = np.float32(1.0 + mu_contrast * smoothed_unit_field(p.shape, sigma, seed + 7919 if mu_seed is None else mu_seed))
+    eps = np.float32(n2 / mu.astype(np.float64))
+    # the media are given to the solver in FP32: where rounding made eps_r mu_r < n^2 (which at n = 1 would put the
+    # medium above the reference speed), step eps_r up by one unit in the last place
+    low = eps.astype(np.float64) * mu.astype(np.float64) < n2
+    eps[low] = np.nextafter(eps[low], np.float32(np.inf))
+    p.eps_r = eps.astype(np.float64)
+    p.mu_r = mu.astype(np.float64)
+    return p
+
+
 def batch_sizes(count=256, seed=3, lo=64, hi=512):
     """Square grid sizes N_b = round(exp(U(ln lo, ln hi))) from PCG64(seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -296,6 +296,14 @@ def test_storage_forms_5000_steps_on_512_crop_of_4096_medium(lbem):
         assert max(report[("i16b", spp)][:2]) < 1e-3, report[("i16b", spp)]
 
 
+def test_mu_heterogeneous_256_1000_steps(lbem):
+    """Heterogeneous permeability (the B x grad ln mu source of Eq. 3 acts at every site): 256^2 medium with the
+    headline recipe's refractive index and mu_r = 1 + s2, 1000 steps, FP32 against the oracle."""
+    p = W.heterogeneous_2d_mu(256, seed=1, nsteps=1000, sigma=12.0)
+    eE, eB = _check(p, tol=1e-4)
+    print(f"mu-heterogeneous 256^2 x 1000 FP32: rel-L2 E {eE:.2e} B {eB:.2e}")
+
+
 @pytest.mark.slow
 def test_1024_heterogeneous_5000_steps_64_receivers_elementwise(lbem):
     """1024^2 heterogeneous medium (seed 1), Ricker point source, 64 receivers, 5000 steps, FP32: every field

@@ -573,3 +573,4 @@ def test_oracle_adjoint_matches_finite_differences(D):
         fd = (misfit(eps + h * d) - misfit(eps - h * d)) / (2 * h)
         an = (grad * d).sum()
         assert abs(fd - an) < 1e-6 * abs(an) + 1e-14, (fd, an)
+
