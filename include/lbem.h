@@ -133,7 +133,7 @@ lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const in
  * 9-10), source (Eq. 3), equilibrium (Eq. 8), collision at tau = dt/2 (Eq. 17);
  * receivers sample the pre-collision fields.  One fused kernel launch per step,
  * or per two (three) steps where lbem_set_temporal_blocking enables it (two is
- * the default for 2D with uniform mu), enqueued on the stream (or replayed from
+ * the default for 2D), enqueued on the stream (or replayed from
  * a cached CUDA graph when enabled by lbem_set_graphs).  Requires a medium.
  * nsteps >= 0. */
 lbem_status lbem_step(lbem_t *h, int nsteps);
@@ -145,12 +145,12 @@ lbem_status lbem_step(lbem_t *h, int nsteps);
  * growth without sources), so a jump means an over-driven source or a corrupted state. */
 lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
 
-/* Temporal blocking (2D, uniform mu; 16-bit storage needs nx % 4 == 0; otherwise ignored).  With
+/* Temporal blocking (2D; 16-bit storage needs uniform mu and nx % 4 == 0; otherwise ignored).  With
  * steps_per_pass = 2 (the default) lbem_step advances pairs of steps with one kernel that stages a tile plus
  * a two-site halo in shared memory and performs both steps there, so the state crosses HBM once per two steps
  * (44 instead of 88 bytes per site and step pair for FP32); an odd last step is a single step.  For FP32
  * storage results are bit-identical to single steps; 16-bit storage is rounded once per launch (decode, two
- * FP32 steps, encode).  steps_per_pass = 3 (FP32 storage only; otherwise as 2) advances triples of steps
+ * FP32 steps, encode).  steps_per_pass = 3 (FP32 storage, uniform mu; otherwise as 2) advances triples of steps
  * through a three-site halo (44 bytes per site per three steps), a remaining pair with the two-step kernel;
  * again bit-identical to single steps.  1 makes every step a single-step launch (the kernel lbem_set_variant
  * selects).  With steps_per_pass = 3, tile_shape selects 0 = 6 rows, 384 threads, 3 CTAs per SM (also -1);
@@ -158,8 +158,10 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * selects the tile (128 sites wide) height, threads per CTA and CTAs per SM: 0 = 6 rows, 256 threads, 5
  * per SM (the default, also -1); 1 = 8 rows, 320, 3; 2 = 8 rows, 352, 3; 3 = 10 rows, 384, 3; 4 = 5 rows,
  * 224, 5; 5 = 4 rows, 192, 6; 6 = 14 rows, 512, 2; FP32 only: 7, 8 = no tiles: each warp streams a
- * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM).
- * LBEM_ERR_ARG for other values. */
+ * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM).  With
+ * a heterogeneous mu (FP32; the two grad ln mu planes are staged beside c_L^2, 52 instead of 104 bytes per
+ * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, and 1 = 14 rows, 512, 2 exist; a larger
+ * shape set before the medium falls back to 0.  LBEM_ERR_ARG for values outside the current handle's set. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 
 /* Steps per launch in effect (2 or 3 only where that kernel is enabled and applies), the tile shape (as set

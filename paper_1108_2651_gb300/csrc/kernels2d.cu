@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const float bx = get(g[r][4], j) - get(g[r][2], j), by = get(g[r][1], j) - get(g[r][3], j);
-                set(shat, j, bx * get(dy, j) - by * get(dx, j));
+                set(shat, j, mu_source(bx, by, get(dx, j), get(dy, j)));
             }
         }
         if (a.evt.rowptr) {
@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {
                 if (ev.kind == 0) {
                     if (ev.comp == 2 && a.t < a.evt.nt) {
                         float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
-                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
-                        set(shat, j, get(shat, j) - jz);
+                        if (MU) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)row * G.pitch + ev.x));
+                        set(shat, j, __fsub_rn(get(shat, j), jz));
                     }
                 } else if (a.t < a.evt.cap) {
                     const float gj[5] = {get(g[r][0], j), get(g[r][1], j), get(g[r][2], j), get(g[r][3], j),
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(BLOCK) step2d_pipe(StepArgs a) {
                 __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + (long long)row * G.pitch) + c);
             for (int j = 0; j < 4; j++) {
                 const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
-                set(shat, j, bx * get(dy, j) - by * get(dx, j));
+                set(shat, j, mu_source(bx, by, get(dx, j), get(dy, j)));
             }
         }
         if (a.evt.rowptr) {
@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(BLOCK) step2d_pipe(StepArgs a) {
                 if (ev.kind == 0) {
                     if (ev.comp == 2 && a.t < a.evt.nt) {
                         float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
-                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
-                        set(shat, j, get(shat, j) - jz);
+                        if (MU) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)row * G.pitch + ev.x));
+                        set(shat, j, __fsub_rn(get(shat, j), jz));
                     }
                 } else if (a.t < a.evt.cap) {
                     const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(BLOCK) step2d_async(StepArgs a) {
                 __ldg(reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + (long long)row * G.pitch) + c);
             for (int j = 0; j < 4; j++) {
                 const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
-                set(shat, j, bx * get(dy, j) - by * get(dx, j));
+                set(shat, j, mu_source(bx, by, get(dx, j), get(dy, j)));
             }
         }
         if (a.evt.rowptr) {
@@ -475,8 +475,8 @@ __global__ void __launch_bounds__(BLOCK) step2d_async(StepArgs a) {
                 if (ev.kind == 0) {
                     if (ev.comp == 2 && a.t < a.evt.nt) {
                         float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
-                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
-                        set(shat, j, get(shat, j) - jz);
+                        if (MU) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)row * G.pitch + ev.x));
+                        set(shat, j, __fsub_rn(get(shat, j), jz));
                     }
                 } else if (a.t < a.evt.cap) {
                     const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step2d_w8(StepArgs a) {
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             const float bx = g4.v[k] - g2.v[k], by = g1.v[k] - g3.v[k];
-            shat[k] = bx * __ldg(dyr + x0 + k) - by * __ldg(dxr + x0 + k);
+            shat[k] = mu_source(bx, by, __ldg(dxr + x0 + k), __ldg(dyr + x0 + k));
         }
     }
     if (a.evt.rowptr) {
@@ -657,8 +657,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) step2d_w8(StepArgs a) {
                 if (ev.kind == 0) {
                     if (ev.comp == 2 && a.t < a.evt.nt) {
                         float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + a.t);
-                        if (MU) jz *= __ldg(a.med.mu + (long long)row * G.pitch + ev.x);
-                        shat[k] -= jz;
+                        if (MU) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)row * G.pitch + ev.x));
+                        shat[k] = __fsub_rn(shat[k], jz);
                     }
                 } else if (a.t < a.evt.cap) {
                     const float sg = ((g0.v[k] + g1.v[k]) + (g2.v[k] + g3.v[k])) + g4.v[k];

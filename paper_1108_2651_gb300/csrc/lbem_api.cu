@@ -125,13 +125,19 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
 // what a captured graph depends on besides t, nsteps and the buffer: kernel variant and two-step shape
 static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16 + h->tb_shape + 1; }
 
-// Whether launches of two (three) steps apply: 2D, uniform mu; 16-bit storage needs nx % 4 == 0; three steps
-// per launch exist for FP32 storage.
+// Whether launches of two (three) steps apply: 2D; FP32 storage with any medium, 16-bit storage with uniform mu
+// and nx % 4 == 0; three steps per launch exist for FP32 storage with uniform mu.
 static bool multi_step_base(const lbem_t *h) {
-    return h->dim == 2 && !h->has_mu && (h->storage == LBEM_F32 || h->grid.nx % 4 == 0);
+    return h->dim == 2 && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
 }
 static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
-static bool three_step_ok(const lbem_t *h) { return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32; }
+static bool three_step_ok(const lbem_t *h) {
+    return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32 && !h->has_mu;
+}
+// the two-step tile shape to launch: the one set (or autotuned) when it exists for this medium, else 0
+static int two_step_shape(const lbem_t *h) {
+    return h->tblock == 2 && h->tb_shape < tb2_nshapes(h->storage, h->has_mu) ? h->tb_shape : 0;
+}
 static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two_step_ok(h) ? 2 : 1; }
 
 // Enqueue nsteps steps starting from buffer `cur` at time t0: triples (pairs) of steps with the three-step
@@ -152,7 +158,7 @@ static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nst
         for (; n + 2 <= nsteps; n += 2) {
             StepArgs a = step_args(h, cur);
             a.t = t0 + n;
-            cudaError_t e = launch_step_2d_tb2(a, h->storage, h->tblock == 2 ? h->tb_shape : 0, h->stream);
+            cudaError_t e = launch_step_2d_tb2(a, h->storage, two_step_shape(h), h->stream);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -532,7 +538,7 @@ lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_s
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass < 1 || steps_per_pass > 3)
         return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: steps_per_pass must be 1, 2 or 3");
-    if (tile_shape < -1 || tile_shape >= (steps_per_pass == 3 ? tb3_nshapes() : tb2_nshapes(h->storage)))
+    if (tile_shape < -1 || tile_shape >= (steps_per_pass == 3 ? tb3_nshapes() : tb2_nshapes(h->storage, h->has_mu)))
         return fail(LBEM_ERR_ARG, "lbem_set_temporal_blocking: tile_shape out of range");
     h->tblock = steps_per_pass;
     h->tb_shape = tile_shape < 0 ? 0 : tile_shape;
@@ -721,9 +727,9 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
     int best_shape = h->tb_shape, best_tblock = 1;
     const int max_k = h->tblock;
     for (int k = 2; k <= max_k && st == LBEM_OK; k++) {
-        if (!multi_step_base(h) || (k == 3 && h->storage != LBEM_F32)) continue;
+        if (!multi_step_base(h) || (k == 3 && (h->storage != LBEM_F32 || h->has_mu))) continue;
         const int nl = trial_steps / k > 0 ? trial_steps / k : 1;
-        const int nsh = k == 3 ? tb3_nshapes() : tb2_nshapes(h->storage);
+        const int nsh = k == 3 ? tb3_nshapes() : tb2_nshapes(h->storage, h->has_mu);
         for (int shape = 0; shape < nsh && st == LBEM_OK; shape++) {
             int cur = cur0;
             for (int rep = 0; rep < 2 && st == LBEM_OK; rep++) {
@@ -771,7 +777,7 @@ lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass) *steps_per_pass = steps_per_launch(h);
     if (tile_shape) *tile_shape = h->tb_shape;
-    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : tb2_nshapes(h->storage);
+    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : tb2_nshapes(h->storage, h->has_mu);
     return LBEM_OK;
 }
 

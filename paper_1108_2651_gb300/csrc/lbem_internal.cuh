@@ -312,18 +312,29 @@ __device__ __forceinline__ int wrapi(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
+// S^ of Eq. 3 from a heterogeneous permeability, B_x d_y ln mu - B_y d_x ln mu, explicitly rounded so that every
+// kernel forms it with the same roundings.
+__device__ __forceinline__ float mu_source(float bx, float by, float dlx, float dly) {
+    return __fsub_rn(__fmul_rn(bx, dly), __fmul_rn(by, dlx));
+}
+
 // Source current at global site (x, y) and time t, and the receiver write of the pre-collision fields (only
-// when `owned`), for the multi-step kernels.  Returns S^ (zero where there is no source).
+// when `owned`), for the multi-step kernels.  Returns S^: shat0 (the permeability term, 0 for uniform mu)
+// minus mu j_z of the sources at the site.
 __device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
-                                             float g1, float g2, float g3, float g4, float cl) {
-    float shat = 0.f;
+                                             float g1, float g2, float g3, float g4, float cl, float shat0 = 0.f) {
+    float shat = shat0;
     if (!a.evt.rowptr) return shat;
     const int e0 = __ldg(a.evt.rowptr + y), e1 = __ldg(a.evt.rowptr + y + 1);
     for (int e = e0; e < e1; e++) {
         const Event ev = a.evt.ev[e];
         if (ev.x != x) continue;
         if (ev.kind == 0) {
-            if (ev.comp == 2 && t < a.evt.nt) shat -= __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
+            if (ev.comp == 2 && t < a.evt.nt) {
+                float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
+                if (a.med.mu) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)y * a.g.pitch + x));
+                shat = __fsub_rn(shat, jz);
+            }
         } else if (owned && t < a.evt.cap) {
             const float s = ((g0 + g1) + (g2 + g3)) + g4;
             a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
@@ -409,8 +420,8 @@ StepArgs step_args(const lbem_t *h, int cur_in);
 // 2D (kernels2d.cu)
 int nvariants_2d();
 cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int variant, cudaStream_t s);
-// two steps per launch (tblock.cu): uniform mu; 16-bit storage needs nx % 4 == 0
-int tb2_nshapes(int storage);
+// two steps per launch (tblock.cu): FP32 (uniform or heterogeneous mu), 16-bit storage (uniform mu, nx % 4 == 0)
+int tb2_nshapes(int storage, bool has_mu);
 // two steps per launch by register streaming (rstream.cu): FP32 storage, uniform mu
 int rs2_nshapes();
 cudaError_t launch_step_2d_rs2(const StepArgs &a, int shape, cudaStream_t s);

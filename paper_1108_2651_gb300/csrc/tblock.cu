@@ -46,30 +46,39 @@ __device__ __forceinline__ void tb_cpa16(float *dst, const float *src) {
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-// Shared-memory layout of a CTA (floats; regions start on 128-byte boundaries), then one mbarrier.
-template <int TBY>
+// Shared-memory layout of a CTA (floats; regions start on 128-byte boundaries), then one mbarrier.  The
+// medium stage holds c_L^2 and, with a heterogeneous permeability (MU), d_x ln mu and d_y ln mu after it, each
+// R rows of TW (the two gradient planes are one TMA box, so R * TW floats must be a multiple of 128 bytes).
+template <int TBY, bool MU = false>
 struct TbGeom {
     static constexpr int R = TBY + 2;  // staged rows per plane at t (tile rows y0-1 .. y0+TBY), and of c_L^2
+    static constexpr int NCL = MU ? 3 : 1;  // medium planes
     static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
     // plane strides (each staged plane at t is a TMA destination: 128-byte aligned)
     static constexpr int IN_PL = up32(R * TW), P_PL = TBY * TW;
-    static constexpr int IN_SZ = up32(5 * IN_PL), CL_SZ = up32(R * TW), P_SZ = up32(5 * P_PL);
+    static constexpr int IN_SZ = up32(5 * IN_PL), CL_SZ = up32(NCL * R * TW), P_SZ = up32(5 * P_PL);
     static constexpr int SZ = IN_SZ + CL_SZ + P_SZ;
     static constexpr size_t BYTES = sizeof(float) * SZ + sizeof(unsigned long long);
-    static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * R * TW;
+    static constexpr unsigned TMA_BYTES = sizeof(float) * (5 + NCL) * R * TW;
+    static_assert(!MU || (R * TW) % 32 == 0, "gradient planes 128-byte aligned");
 };
+
+// Source plane k of the medium stage: c_L^2, then d_x ln mu and d_y ln mu.
+__device__ __forceinline__ const float *medium_plane(const StepArgs &a, int k) {
+    return k == 0 ? a.med.cL2 : a.med.dlnmu + (k - 1) * a.g.plane;
+}
 
 // Asynchronous copies of one tile's window with periodic wrap (16 bytes per copy when every group of 4
 // columns stays contiguous after the wrap, else 4).
-template <int TBY>
+template <int TBY, bool MU = false>
 __device__ __forceinline__ void tb_issue(const StepArgs &a, int x0, int y0, float *IN, float *CL, int nt) {
-    constexpr int R = TbGeom<TBY>::R, PL = TbGeom<TBY>::IN_PL, Q = TW / 4;
+    constexpr int R = TbGeom<TBY>::R, PL = TbGeom<TBY>::IN_PL, Q = TW / 4, NP = 5 + TbGeom<TBY, MU>::NCL;
     const Grid &G = a.g;
     const float *in = static_cast<const float *>(a.in.data);
     const int tid = threadIdx.x;
     if (((x0 - 4 >= 0) && (x0 + TBX + 4 <= G.nx)) || (G.nx & 3) == 0) {
-        for (int k = tid; k < 6 * R * Q; k += nt) {
-            const int pr = k / Q, q = k - pr * Q;  // pr = plane * R + row; plane 5 is c_L^2
+        for (int k = tid; k < NP * R * Q; k += nt) {
+            const int pr = k / Q, q = k - pr * Q;  // pr = plane * R + row; planes 5.. are the medium stage
             const int pl = pr / R, r = pr - pl * R;
             const int gx = wrapi(x0 - 4 + 4 * q, G.nx);
             if (pl < 5) {
@@ -77,11 +86,12 @@ __device__ __forceinline__ void tb_issue(const StepArgs &a, int x0, int y0, floa
                 tb_cpa16(IN + pl * PL + r * TW + 4 * q, in + pl * G.plane + (long long)gy * G.pitch + gx);
             } else {
                 const int gy = wrapi(y0 - 1 + r, G.ny);
-                tb_cpa16(CL + r * TW + 4 * q, a.med.cL2 + (long long)gy * G.pitch + gx);
+                tb_cpa16(CL + (pl - 5) * R * TW + r * TW + 4 * q,
+                         medium_plane(a, pl - 5) + (long long)gy * G.pitch + gx);
             }
         }
     } else {  // columns wrap inside a group: element copies
-        for (int k = tid; k < 6 * R * TW; k += nt) {
+        for (int k = tid; k < NP * R * TW; k += nt) {
             const int pr = k / TW, c = k - pr * TW;
             const int pl = pr / R, r = pr - pl * R;
             const int gx = wrapi(x0 - 4 + c, G.nx);
@@ -90,7 +100,8 @@ __device__ __forceinline__ void tb_issue(const StepArgs &a, int x0, int y0, floa
                 tb_cpa4(IN + pl * PL + r * TW + c, in + pl * G.plane + (long long)gy * G.pitch + gx);
             } else {
                 const int gy = wrapi(y0 - 1 + r, G.ny);
-                tb_cpa4(CL + r * TW + c, a.med.cL2 + (long long)gy * G.pitch + gx);
+                tb_cpa4(CL + (pl - 5) * R * TW + r * TW + c,
+                        medium_plane(a, pl - 5) + (long long)gy * G.pitch + gx);
             }
         }
     }
@@ -142,24 +153,26 @@ __device__ __forceinline__ bool tb_interior(int x0, int y0, const Grid &G) {
 // Start the loads of one tile's window: one thread issues six TMA copies (each population plane as a
 // (TBY+2) x (TBX+8) box at its row shift, and c_L^2) for interior tiles; every thread issues its share of the
 // asynchronous copies otherwise.
-template <int TBY>
+template <int TBY, bool MU = false>
 __device__ __forceinline__ void tb_load(const StepArgs &a, int x0, int y0, float *IN, float *CL, unsigned mbar,
-                                        bool tma, const CUtensorMap *tmIn, const CUtensorMap *tmCL, int nt) {
+                                        bool tma, const CUtensorMap *tmIn, const CUtensorMap *tmCL, int nt,
+                                        const CUtensorMap *tmDL = nullptr) {
     if (tma) {
         if (threadIdx.x == 0) {
             // earlier generic-proxy accesses of the window (ordered by the preceding barrier) before the
             // asynchronous-proxy writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
-                         "r"(TbGeom<TBY>::TMA_BYTES)
+                         "r"(TbGeom<TBY, MU>::TMA_BYTES)
                          : "memory");
 #pragma unroll
             for (int p = 0; p < 5; p++)
                 tma_load_3d(IN + p * TbGeom<TBY>::IN_PL, tmIn, x0 - 4, y0 - 1 + in_shift(p), p, mbar);
             tma_load_2d(CL, tmCL, x0 - 4, y0 - 1, mbar);
+            if (MU) tma_load_3d(CL + TbGeom<TBY>::R * TW, tmDL, x0 - 4, y0 - 1, 0, mbar);
         }
     } else {
-        tb_issue<TBY>(a, x0, y0, IN, CL, nt);
+        tb_issue<TBY, MU>(a, x0, y0, IN, CL, nt);
     }
 }
 
@@ -191,10 +204,12 @@ struct Pull4 {
 #define TB_SET(v, k, val) (k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w) = (val)
 
 // Four site updates (collide2d each) at global row gy, columns x0+4*lane.., time t.
-template <bool EV, class PULL>
-__device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, float4 cl, int x0, int gy, long long t,
-                                           bool owned_row, float4 &o0, float4 &o1, float4 &o2, float4 &o3,
-                                           float4 &o4) {
+// With a heterogeneous permeability (MU) the source carries B_x d_y ln mu - B_y d_x ln mu (dlx, dly: the
+// gradient of ln mu at the four sites) at every site, as in the single-step kernels.
+template <bool EV, bool MU, class PULL>
+__device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, float4 cl, float4 dlx, float4 dly,
+                                            int x0, int gy, long long t, bool owned_row, float4 &o0, float4 &o1,
+                                            float4 &o2, float4 &o3, float4 &o4) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -202,11 +217,14 @@ __device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, flo
         const float q0 = TB_COMP(g.g0, k), q1 = TB_COMP(g.g1, k), q2 = TB_COMP(g.g2, k), q3 = TB_COMP(g.g3, k),
                     q4 = TB_COMP(g.g4, k), ck = TB_COMP(cl, k);
         Out5 o;
+        const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, TB_COMP(dlx, k), TB_COMP(dly, k)) : 0.f;
         if (EV) {
             const int gx = x0 + 4 * lane + k;
             const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
-                                           owned_row && gx < G.nx && gy < G.ny, q0, q1, q2, q3, q4, ck);
+                                           owned_row && gx < G.nx && gy < G.ny, q0, q1, q2, q3, q4, ck, shat0);
             o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        } else if (MU) {
+            o = collide2d(q0, q1, q2, q3, q4, ck, shat0);
         } else {
             o = collide2d_free(q0, q1, q2, q3, q4, ck);
         }
@@ -218,24 +236,39 @@ __device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, flo
     }
 }
 
+template <bool EV, class PULL>
+__device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, float4 cl, int x0, int gy, long long t,
+                                           bool owned_row, float4 &o0, float4 &o1, float4 &o2, float4 &o3,
+                                           float4 &o4) {
+    tb_update4m<EV, false>(a, g, cl, cl, cl, x0, gy, t, owned_row, o0, o1, o2, o3, o4);
+}
+
 // Step t on tile rows y0-1 .. y0+TBY (stage row py <-> global row y0-1+py), one warp per row, storing each
 // plane's result only where step t+1 reads it (planes 0, 1, 3 at stage row py-1, plane 2 at py, plane 4 at
 // py-2); then the ring sites x0-1 (plane 1 only) and x0+TBX (plane 3 only) of rows y0 .. y0+TBY-1.  Also
-// reads into clb the c_L^2 of the warp's step-(t+1) row, as the c_L^2 stage is reloaded before step t+1.
-template <int TBY, int NT, bool EV>
+// reads into clb the c_L^2 of the warp's step-(t+1) row (and with MU into dbx, dby its gradient of ln mu), as
+// the medium stage is reloaded before step t+1.
+template <int TBY, int NT, bool EV, bool MU = false>
 __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, const float *CL, float *P, int x0,
-                                          int y0, long long t, float4 &clb) {
+                                          int y0, long long t, float4 &clb, float4 &dbx, float4 &dby) {
     using Gm = TbGeom<TBY>;
-    constexpr int R = Gm::R, NW = NT / 32, PL = Gm::P_PL;
+    constexpr int R = Gm::R, NW = NT / 32, PL = Gm::P_PL, DX = R * TW, DY = 2 * R * TW;
     const Grid &G = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c = 4 + 4 * lane;
-    if (warp < TBY) clb = lds4(CL + (warp + 1) * TW + c);
+    if (warp < TBY) {
+        clb = lds4(CL + (warp + 1) * TW + c);
+        if (MU) {
+            dbx = lds4(CL + DX + (warp + 1) * TW + c);
+            dby = lds4(CL + DY + (warp + 1) * TW + c);
+        }
+    }
     for (int py = warp; py < R; py += NW) {
         const Pull4 g(IN, Gm::IN_PL, py, c);
         const float4 cl = lds4(CL + py * TW + c);
+        const float4 dlx = MU ? lds4(CL + DX + py * TW + c) : cl, dly = MU ? lds4(CL + DY + py * TW + c) : cl;
         float4 o0, o1, o2, o3, o4;
-        tb_update4<EV>(a, g, cl, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2, o3, o4);
+        tb_update4m<EV, MU>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2, o3, o4);
         float *Pr = P + c;
         if (py >= 1 && py <= TBY) {
             sts4(Pr + 0 * PL + (py - 1) * TW, o0);
@@ -254,10 +287,10 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
         const float q0 = r[0], q1 = r[Gm::IN_PL - 1], q2 = r[2 * Gm::IN_PL], q3 = r[3 * Gm::IN_PL + 1],
                     q4 = r[4 * Gm::IN_PL];
         const float ck = CL[py * TW + cc];
-        float shat = 0.f;
+        float shat = MU ? mu_source(q4 - q2, q1 - q3, CL[DX + py * TW + cc], CL[DY + py * TW + cc]) : 0.f;
         if (EV)
             shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3, q4,
-                               ck);
+                               ck, shat);
         const Out5 o = collide2d(q0, q1, q2, q3, q4, ck, shat);
         if (k & 1)
             P[3 * PL + (py - 1) * TW + cc] = o.o3;
@@ -267,9 +300,9 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
 }
 
 // Step t+1 on tile row y0 + warp from the t+1 stage, written as 16-byte streaming stores.
-template <int TBY, bool EV>
-__device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, float4 clb, int x0, int y0,
-                                          long long t) {
+template <int TBY, bool EV, bool MU = false>
+__device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, float4 clb, float4 dbx, float4 dby,
+                                          int x0, int y0, long long t) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31, oy = threadIdx.x >> 5;
     const int gy = y0 + oy;
@@ -277,7 +310,7 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
     const int c = 4 + 4 * lane;
     const Pull4 g(P, TbGeom<TBY>::P_PL, oy, c);
     float4 o0, o1, o2, o3, o4;
-    tb_update4<EV>(a, g, clb, x0, gy, t + 1, true, o0, o1, o2, o3, o4);
+    tb_update4m<EV, MU>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
         float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)gy * G.pitch + x0 +
                                                4 * lane);
@@ -294,15 +327,15 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
 
 // One persistent CTA per SM slot; CTA b takes tiles b, b + gridDim.x, ... (row-major over the tile grid).
 // The window of the next tile is loaded while step t+1 of the current one is computed.
-template <int TBY, int NT, int MINB>
+template <int TBY, int NT, int MINB, bool MU = false>
 __global__ void __launch_bounds__(NT, MINB)
     step2d_tb2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
-               int use_tma, int ntx, int nty, int dq, int dr) {
+               const __grid_constant__ CUtensorMap tmDL, int use_tma, int ntx, int nty, int dq, int dr) {
     static_assert(NT / 32 >= TBY, "one warp per row of step t+1");
-    using Gm = TbGeom<TBY>;
+    using Gm = TbGeom<TBY, MU>;
     extern __shared__ __align__(1024) float sm[];
     float *IN = sm;              // [5][TBY+2][TW], shifted planes at t
-    float *CL = sm + Gm::IN_SZ;  // [TBY+2][TW]
+    float *CL = sm + Gm::IN_SZ;  // [1 or 3][TBY+2][TW]: c_L^2 (and d_x ln mu, d_y ln mu)
     float *P = CL + Gm::CL_SZ;   // [5][TBY][TW], shifted planes at t+1
     unsigned long long *mb = reinterpret_cast<unsigned long long *>(sm + Gm::SZ);
     const Grid &G = a.g;
@@ -317,8 +350,8 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     unsigned parity = 0;  // next phase of the mbarrier to wait for
-    tb_load<TBY>(a, tx * TBX, ty * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
-                 &tmCL, NT);
+    tb_load<TBY, MU>(a, tx * TBX, ty * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
+                     &tmCL, NT, &tmDL);
     asm volatile("cp.async.commit_group;\n" ::);
     bool events = tb_events<TBY>(a, ty * TBY);
     const long long t = a.t;
@@ -343,20 +376,20 @@ __global__ void __launch_bounds__(NT, MINB)
             mbar_wait(mbar, parity ^ 1u);
             return;
         }
-        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb;
         if (events)
-            tb_step_a<TBY, NT, true>(a, IN, CL, P, x0, y0, t, clb);
+            tb_step_a<TBY, NT, true, MU>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
         else
-            tb_step_a<TBY, NT, false>(a, IN, CL, P, x0, y0, t, clb);
+            tb_step_a<TBY, NT, false, MU>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
         __syncthreads();
-        if (has_next)  // the t stage and c_L^2 are free: start the loads of the next tile
-            tb_load<TBY>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G),
-                         &tmIn, &tmCL, NT);
+        if (has_next)  // the t stage and the medium stage are free: start the loads of the next tile
+            tb_load<TBY, MU>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar,
+                             use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, NT, &tmDL);
         asm volatile("cp.async.commit_group;\n" ::);
         if (events)
-            tb_step_b<TBY, true>(a, P, clb, x0, y0, t);
+            tb_step_b<TBY, true, MU>(a, P, clb, dbx, dby, x0, y0, t);
         else
-            tb_step_b<TBY, false>(a, P, clb, x0, y0, t);
+            tb_step_b<TBY, false, MU>(a, P, clb, dbx, dby, x0, y0, t);
         tx = ntx_;
         ty = nty_;
         events = events_next;
@@ -686,29 +719,44 @@ static bool make_maps(const StepArgs &a, CUtensorMap *mIn, CUtensorMap *mCL) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TBY, int NT, int MINB>
+// Tensor map of the gradient of ln mu ([2][ny][pitch] floats: d_x, d_y), box: both planes of TBY+2 rows.
+template <int TBY>
+static bool make_dl_map(const StepArgs &a, CUtensorMap *mDL) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || !a.med.dlnmu) return false;
+    const cuuint64_t dims3[3] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny, 2};
+    const cuuint64_t str3[2] = {(cuuint64_t)a.g.pitch * 4, (cuuint64_t)a.g.plane * 4};
+    const cuuint32_t box3[3] = {(cuuint32_t)TW, (cuuint32_t)TbGeom<TBY>::R, 2};
+    const cuuint32_t one[3] = {1, 1, 1};
+    return fn(mDL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(a.med.dlnmu), dims3, str3, box3, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TBY, int NT, int MINB, bool MU = false>
 static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
-    using Gm = TbGeom<TBY>;
+    using Gm = TbGeom<TBY, MU>;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Gm::BYTES);
+        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB, MU>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB>, NT, Gm::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB, MU>, NT, Gm::BYTES);
         if (per_sm < 1) per_sm = 1;
     }
-    CUtensorMap mIn, mCL;
+    CUtensorMap mIn, mCL, mDL;
     memset(&mIn, 0, sizeof mIn);
     memset(&mCL, 0, sizeof mCL);
-    const int use_tma = make_maps<TBY>(a, &mIn, &mCL) ? 1 : 0;
+    memset(&mDL, 0, sizeof mDL);
+    const int use_tma = (make_maps<TBY>(a, &mIn, &mCL) && (!MU || make_dl_map<TBY>(a, &mDL))) ? 1 : 0;
     const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
     const int ntiles = ntx * nty;
     const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
-    step2d_tb2<TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, use_tma, ntx, nty, blocks / ntx,
-                                                            blocks % ntx);
+    step2d_tb2<TBY, NT, MINB, MU><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, use_tma, ntx, nty, blocks / ntx,
+                                                                blocks % ntx);
     return cudaGetLastError();
 }
 
@@ -1114,7 +1162,11 @@ static cudaError_t launch_16(const StepArgs &a, int shape, cudaStream_t s) {
 
 // Tile shapes (rows, threads, CTAs per SM).  Measured on 4096^2 (heterogeneous medium, FP32): 6 rows at five
 // CTAs per SM is the fastest; the others remain selectable for other sizes and for the bit-identity tests.
-int tb2_nshapes(int storage) { return storage == LBEM_F32 ? 7 + rs2_nshapes() : 7; }
+// With a heterogeneous permeability (FP32 only): 6 rows at four CTAs per SM (51 KB), or 14 rows at two.
+int tb2_nshapes(int storage, bool has_mu) {
+    if (has_mu) return storage == LBEM_F32 ? 2 : 0;
+    return storage == LBEM_F32 ? 7 + rs2_nshapes() : 7;
+}
 
 cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s) {
     switch (storage) {
@@ -1123,6 +1175,7 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
         default: break;
     }
+    if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)
     switch (shape) {
         case 1: return launch_tb<8, 320, 3>(a, s);

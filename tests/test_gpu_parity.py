@@ -496,6 +496,46 @@ def test_autotuned_stepping_is_bitwise_identical(lbem, spp):
     np.testing.assert_array_equal(tr.cpu().double().numpy(), ref[2])
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (17, 45), (16, 128), (33, 257), (70, 300), (130, 131),
+                                   (9, 1), (200, 7), (301, 777), (40, 4), (50, 264)])
+def test_two_step_blocking_heterogeneous_mu_is_bitwise_identical(lbem, shape):
+    """Two steps per launch with a heterogeneous permeability (the grad ln mu planes staged beside c_L^2): the
+    same bits as single steps for both tile shapes, with sources and receivers anywhere, odd step counts and
+    graphs; a third tile shape does not exist for such a medium, and three steps per launch fall back to two
+    (uniform mu only), as does a shape set before the medium."""
+    p = _problem_small(2, shape, 98, 41, mu=True, nsrc=7, nrec=15)
+    ref = gpu_run(p, steps_per_pass=1)
+    import torch
+
+    for spp_set, tile_shape, graphs in [(2, k, g) for k in range(2) for g in (False, True)] + [(3, 0, False),
+                                                                                              (2, 8, False)]:
+        stream = torch.cuda.Stream() if graphs else None
+        s = lbem.Solver(p.shape, stream=stream.cuda_stream if stream else None)
+        if tile_shape < 2:
+            s.set_problem(p)
+            lbem.lbem_set_temporal_blocking(s.h, spp_set, tile_shape)
+        else:
+            lbem.lbem_set_temporal_blocking(s.h, spp_set, tile_shape)
+            s.set_problem(p)
+        spp, _, nsh = lbem.lbem_get_temporal_blocking(s.h)
+        assert spp == 2 and nsh == (3 if spp_set == 3 else 2)
+        with pytest.raises(lbem.LbemError):
+            lbem.lbem_set_temporal_blocking(s.h, 2, 2)
+        if graphs:
+            lbem.lbem_set_graphs(s.h, True)
+        s.step(20)
+        s.step(21)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        lbem.lbem_sync(s.h)
+        lbem.lbem_check_guards(s.h)
+        s.close()
+        np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
+        np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1])
+        np.testing.assert_array_equal(tr.cpu().double().numpy(), ref[2])
+
+
 def test_two_step_blocking_rejects_bad_arguments(lbem):
     s = lbem.Solver((16, 16))
     for steps, shape in ((0, 0), (4, 0), (2, 9), (3, 3), (2, -2)):
