@@ -37,7 +37,25 @@
  *      reported from those moments; T is added once, post-collision, with the
  *      source at time t (Eq. 17); then streaming (Eq. 18).
  *  R5  grad(ln mu) by second-order central differences, periodic.
- *  R6  Periodic boundaries in every direction.
+ *  R6  Periodic boundaries in every direction, unless walls are asked for.
+ *  R7  Walls (the paper treats periodic domains only and leaves reflecting
+ *      and absorbing boundaries open): a wall sits half a site beyond the
+ *      first and last site of an axis.  A particle that streams across it
+ *      comes back to the site it left, in the opposite direction, times
+ *      s = +1 (halfway bounce-back) or s = -1 (anti-bounce-back).  In 2D the
+ *      state then evolves exactly as the periodic state on a domain twice as
+ *      long with the mirror image of the medium, fields and currents
+ *      (populations i <-> opposite(i) times s): s = -1 makes E_z and B_normal
+ *      odd about the wall (a perfect electric conductor, PEC); s = +1 makes
+ *      the tangential B odd (a perfect magnetic conductor, PMC).  grad ln mu
+ *      at the first / last site uses the mirror image of mu (the one-sided
+ *      difference halved), as the doubled domain would.  Walls are 2D only.
+ *  R8  Absorbing layer of L sites inside each wall: after the collision the
+ *      populations of a site at distance i = 0 .. L-1 from the wall-adjacent
+ *      site are multiplied by 1 - gamma_i, gamma_i = gamma_max ((L - i)/L)^2,
+ *      the factors of two axes multiplied at corners.  Scaling E and B by the
+ *      same factor damps them equally (matched electric and magnetic
+ *      conductivity), so the layer keeps the wave impedance of the medium.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -93,6 +111,24 @@ static long shifted(const lattice_t *L, long s, int dx, int dy, int dz) {
     return wrap(x, dx, L->nx) + L->nx * (wrap(y, dy, L->ny) + L->ny * wrap(z, dz, L->nz));
 }
 
+/* Coordinate v + d along an axis of length n with boundary kind `bc` (0 = periodic, else walls): the periodic
+ * wrap, or the mirror image inside the wall (-1 -> 0, n -> n-1), for |d| <= 1. */
+static inline long mirror_or_wrap(long v, int d, long n, int bc) {
+    if (!bc) return wrap(v, d, n);
+    v += d;
+    if (v < 0) return -1 - v;
+    if (v >= n) return 2 * n - 1 - v;
+    return v;
+}
+
+/* Damping factor 1 - gamma of reading R8 at coordinate v of an axis of length n (1 outside the layer). */
+static double layer_factor(long v, long n, int layer, double gamma_max) {
+    long i = v < n - 1 - v ? v : n - 1 - v; /* distance from the nearer wall-adjacent site */
+    if (layer <= 0 || i >= layer) return 1.0;
+    double r = (double)(layer - i) / layer;
+    return 1.0 - gamma_max * r * r;
+}
+
 static inline double *G(const lattice_t *L, double *g, long s, int i) {
     return g + ((s * L->Q + i) * L->D) * L->D;
 }
@@ -116,7 +152,7 @@ static double weight(const lattice_t *L, int i, double w0) {
  * mu_r may be NULL (mu = 1).  Returns the number of sites whose w0 falls
  * outside [0, 1) or whose inputs are not finite and positive.
  */
-long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r, const double *mu_r,
+long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r, const double *mu_r, const int *bc,
                double *ceff2, double *cL2, double *w0, double *mu, double *dlnmu) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
@@ -136,13 +172,15 @@ long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r
         if (!(w0[s] >= 0.0 && w0[s] < 1.0)) bad++;
     }
     for (long s = 0; s < L.nsite; s++) {
+        const long xyz[3] = {s % L.nx, (s / L.nx) % L.ny, s / ((long)L.nx * L.ny)};
+        const long n[3] = {L.nx, L.ny, L.nz};
         for (int k = 0; k < 3; k++) dlnmu[3 * s + k] = 0.0;
         for (int k = 0; k < D; k++) {
-            int dp[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
-            dp[k] = 1;
-            dm[k] = -1;
-            long sp = shifted(&L, s, dp[0], dp[1], dp[2]);
-            long sm = shifted(&L, s, dm[0], dm[1], dm[2]);
+            long p[3] = {xyz[0], xyz[1], xyz[2]}, m[3] = {xyz[0], xyz[1], xyz[2]};
+            p[k] = mirror_or_wrap(xyz[k], +1, n[k], bc ? bc[k] : 0);
+            m[k] = mirror_or_wrap(xyz[k], -1, n[k], bc ? bc[k] : 0);
+            long sp = p[0] + L.nx * (p[1] + L.ny * p[2]);
+            long sm = m[0] + L.nx * (m[1] + L.ny * m[2]);
             dlnmu[3 * s + k] = 0.5 * (log(mu[sp]) - log(mu[sm]));
         }
     }
@@ -301,13 +339,21 @@ static void current_at(const sources_t *src, long s, int t, double j[3]) {
  * Advance nsteps time steps, Eqs. 17 then 18.  g holds the pre-collision
  * state at time t0 on entry and at t0 + nsteps on exit.  j(t) is taken from
  * amp[k][t] for t in [0, nt).  Receivers record (before each collision) the
- * field at time t0 + n into traces[r][n], n = 0..nsteps-1.  Returns 0.
+ * field at time t0 + n into traces[r][n], n = 0..nsteps-1.  bc[a] (NULL = all
+ * periodic) is the boundary of axis a: 0 periodic, 1 PEC wall, 2 PMC wall
+ * (readings R6-R7); `layer` > 0 adds the absorbing layer of reading R8 inside
+ * every wall.  Returns 0, or -1 for walls in 3D.
  */
 int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2, const double *mu,
            const double *dlnmu, double *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
-           const double *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, double *traces) {
+           const double *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, double *traces,
+           const int *bc, int layer, double gamma_max) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
+    int kind[3] = {0, 0, 0};
+    for (int a = 0; bc && a < 3; a++) kind[a] = a < D ? bc[a] : 0;
+    if (D == 3 && (kind[0] || kind[1] || kind[2])) return -1;
+    const long len[3] = {L.nx, L.ny, L.nz};
     const long per = (long)L.Q * D * D;
     double *gpost = malloc(sizeof(double) * per * L.nsite);
     double *E = malloc(sizeof(double) * 3 * L.nsite);
@@ -322,6 +368,13 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
             current_at(&src, s, t, j);
             collide_site(&L, cL2[s], w0[s], ceff2[s], mu[s], dlnmu + 3 * s, j, g + s * per, gpost + s * per, E + 3 * s,
                          B + 3 * s);
+            /* absorbing layer (reading R8): scale the post-collision populations */
+            const long xyz[3] = {s % L.nx, (s / L.nx) % L.ny, s / ((long)L.nx * L.ny)};
+            double f = 1.0;
+            for (int a = 0; a < D; a++)
+                if (kind[a]) f *= layer_factor(xyz[a], len[a], layer, gamma_max);
+            if (f != 1.0)
+                for (long k = 0; k < per; k++) gpost[s * per + k] *= f;
         }
         for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = pick(E + 3 * rec_site[r], B + 3 * rec_site[r], rec_comp[r]);
         /* streaming (Eq. 18): g_i(x + c_i, t+1) = g'_i(x, t) */
@@ -329,6 +382,20 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
         for (long s = 0; s < L.nsite; s++) {
             const long x = s % L.nx, y = (s / L.nx) % L.ny, z = s / ((long)L.nx * L.ny);
             for (int i = 0; i < L.Q; i++) {
+                /* a particle that would cross a wall (reading R7) returns to s in the opposite direction, times
+                 * -1 at a PEC wall and +1 at a PMC wall */
+                const long xyz[3] = {x + L.c[i][0], y + L.c[i][1], z + L.c[i][2]};
+                int crossed = -1;
+                for (int a = 0; a < D; a++)
+                    if (kind[a] && (xyz[a] < 0 || xyz[a] >= len[a])) crossed = a;
+                if (crossed >= 0) {
+                    const int io = i == 0 ? 0 : (i <= D ? i + D : i - D); /* opposite direction */
+                    const double sgn = kind[crossed] == 1 ? -1.0 : 1.0;
+                    const double *src = G(&L, gpost, s, i);
+                    double *dst = G(&L, g, s, io);
+                    for (int k = 0; k < D * D; k++) dst[k] = sgn * src[k];
+                    continue;
+                }
                 long d = wrap(x, L.c[i][0], L.nx) + L.nx * (wrap(y, L.c[i][1], L.ny) + L.ny * wrap(z, L.c[i][2], L.nz));
                 memcpy(G(&L, g, d, i), G(&L, gpost, s, i), sizeof(double) * D * D);
             }
@@ -436,7 +503,7 @@ double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const doub
         memcpy(states + (long)(n + 1) * per * ns, states + (long)n * per * ns, sizeof(double) * per * ns);
         double *tr_n = malloc(sizeof(double) * (nrec > 0 ? nrec : 1));
         or_run(D, nx, ny, nz, cL2, w0, ceff2, mu, dlnmu, states + (long)(n + 1) * per * ns, t0 + n, 1, nsrc, src_site,
-               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n);
+               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n, NULL, 0, 0.0);
         for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = tr_n[r];
         free(tr_n);
     }

@@ -24,13 +24,13 @@ def _load():
         ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
         I, D_ = C.c_int, C.c_double
         lib.or_medium.restype = C.c_long
-        lib.or_medium.argtypes = [I, I, I, I, D_, dp, C.c_void_p, dp, dp, dp, dp, dp]
+        lib.or_medium.argtypes = [I, I, I, I, D_, dp, C.c_void_p, ip, dp, dp, dp, dp, dp]
         lib.or_init.restype = None
         lib.or_init.argtypes = [I, I, I, I, dp, dp, C.c_void_p, C.c_void_p, dp]
         lib.or_fields.restype = None
         lib.or_fields.argtypes = [I, I, I, I, dp, dp, dp, dp]
         lib.or_run.restype = I
-        lib.or_run.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp]
+        lib.or_run.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, ip, I, D_]
         lib.or_diagnostics.restype = None
         lib.or_diagnostics.argtypes = [I, I, I, I, dp, dp, dp, dp, dp]
         lib.or_adjoint.restype = D_
@@ -59,6 +59,9 @@ class Oracle:
     mu: np.ndarray
     dlnmu: np.ndarray  # grid + (3,)
     bad: int
+    bc: tuple = (0, 0, 0)  # per axis x, y, z: 0 periodic, 1 PEC wall, 2 PMC wall
+    layer: int = 0  # absorbing layer width inside the walls (sites)
+    gamma_max: float = 0.0  # damping of the wall-adjacent site
 
     @property
     def dims(self):
@@ -80,9 +83,18 @@ def _f64(a, shape=None):
     return a
 
 
-def medium(D, eps_r, mu_r=None, c_ref2=None) -> Oracle:
-    """Medium upload: eps_r, mu_r -> c_eff^2, c_L^2, w0, grad ln mu (Eq. 3)."""
+PERIODIC, PEC, PMC = 0, 1, 2
+
+
+def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.0) -> Oracle:
+    """Medium upload: eps_r, mu_r -> c_eff^2, c_L^2, w0, grad ln mu (Eq. 3).
+
+    bc (x, y, z): 0 periodic, 1 PEC wall, 2 PMC wall on both ends of that axis (2D only); layer > 0 adds an
+    absorbing layer of that many sites inside every wall, damping 1 - gamma_max ((L - i)/L)^2 at distance i."""
     lib = _load()
+    bc = tuple(int(b) for b in bc) + (0,) * (3 - len(bc))
+    assert all(b in (PERIODIC, PEC, PMC) for b in bc) and (D == 2 or not any(bc))
+    assert layer >= 0 and 0.0 <= gamma_max < 1.0
     eps_r = _f64(eps_r)
     shape = eps_r.shape
     assert len(shape) == D
@@ -98,9 +110,10 @@ def medium(D, eps_r, mu_r=None, c_ref2=None) -> Oracle:
         assert mu_r.shape == shape
         mu_ptr = mu_r.ctypes.data_as(C.c_void_p)
     nx, ny, nz = (shape[-1], shape[-2], shape[0] if D == 3 else 1)
-    bad = lib.or_medium(D, nx, ny, nz, float(c_ref2), eps_r.ravel(), mu_ptr, *out, dl)
+    bad = lib.or_medium(D, nx, ny, nz, float(c_ref2), eps_r.ravel(), mu_ptr, np.array(bc, np.int32), *out, dl)
     ceff2, cL2, w0, mu = (o.reshape(shape) for o in out)
-    return Oracle(D, shape, eps_r, ceff2, cL2, w0, mu, dl.reshape(shape + (3,)), int(bad))
+    return Oracle(D, shape, eps_r, ceff2, cL2, w0, mu, dl.reshape(shape + (3,)), int(bad), bc, int(layer),
+                  float(gamma_max))
 
 
 def init_state(m: Oracle, E=None, B=None) -> np.ndarray:
@@ -149,8 +162,10 @@ def run(m: Oracle, g: np.ndarray, nsteps: int, t0: int = 0, sources=None, receiv
     ns, ss, sc, sa, nt = _sources(sources, n)
     nr, rs, rc = _receivers(receivers, n)
     traces = np.zeros(max(nr, 1) * max(nsteps, 1))
-    lib.or_run(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(), m.mu.ravel(), m.dlnmu.reshape(-1),
-               g.reshape(-1), int(t0), int(nsteps), ns, ss, sc, sa, nt, nr, rs, rc, traces)
+    rc_ = lib.or_run(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(), m.mu.ravel(), m.dlnmu.reshape(-1),
+                     g.reshape(-1), int(t0), int(nsteps), ns, ss, sc, sa, nt, nr, rs, rc, traces,
+                     np.array(m.bc, np.int32), m.layer, m.gamma_max)
+    assert rc_ == 0
     return traces[: nr * nsteps].reshape(nr, nsteps)
 
 
@@ -174,8 +189,9 @@ def diagnostics(m: Oracle, g: np.ndarray):
 
 
 def adjoint(m: Oracle, g0: np.ndarray, nsteps: int, sources, receivers, obs, t0: int = 0):
-    """Misfit 1/2 sum (trace - obs)^2 and its gradient with respect to eps_r (grid shape)."""
+    """Misfit 1/2 sum (trace - obs)^2 and its gradient with respect to eps_r (grid shape); periodic only."""
     lib = _load()
+    assert not any(m.bc)
     n = m.cL2.size
     ns, ss, sc, sa, nt = _sources(sources, n)
     nr, rs, rc = _receivers(receivers, n)
