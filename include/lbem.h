@@ -59,9 +59,17 @@ typedef enum {
     LBEM_I16B = 3  /* int16 mantissas sharing one exponent byte per 4 consecutive sites along x (2.25 bytes) */
 } lbem_storage;
 
+/* Boundary of one axis (lbem_set_boundaries). */
+typedef enum {
+    LBEM_BC_PERIODIC = 0, /* the default */
+    LBEM_BC_PEC = 1,      /* perfect electric conductor: tangential E and normal B vanish on the wall */
+    LBEM_BC_PMC = 2       /* perfect magnetic conductor: tangential B vanishes on the wall */
+} lbem_bc;
+
 typedef struct {
     int dim;        /* 2 (D2Q5, fields E_z, B_x, B_y) or 3 (D3Q7, all six components) */
-    int nx, ny, nz; /* grid size, periodic in every direction; nz ignored in 2D; each >= 1 */
+    int nx, ny, nz; /* grid size, periodic in every direction unless lbem_set_boundaries puts walls;
+                       nz ignored in 2D; each >= 1 */
     int storage;    /* lbem_storage; LBEM_F32 in 3D */
     double c_ref2;  /* wave speed squared (lattice units) at eps = mu = 1; <= 0 selects the largest the
                        lattice carries with a non-negative rest weight: 1/2 in 2D, 1/6 in 3D */
@@ -137,6 +145,28 @@ lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const in
  * a cached CUDA graph when enabled by lbem_set_graphs).  Requires a medium.
  * nsteps >= 0. */
 lbem_status lbem_step(lbem_t *h, int nsteps);
+
+/* Walls and absorbing layers (2D, LBEM_F32 storage; the paper treats periodic
+ * domains only and leaves other boundaries open).  kind[a] (a = x, y, z; z must
+ * be LBEM_BC_PERIODIC) puts a wall half a site beyond the first and the last
+ * site of axis a: a population that would cross it returns to the site it
+ * left in the opposite direction, times -1 (LBEM_BC_PEC) or +1 (LBEM_BC_PMC)
+ * (halfway bounce-back; the state then evolves as the periodic state on a
+ * domain twice as long holding the mirror image).  grad ln mu at the edge sites
+ * uses the mirror image of mu.  layer > 0 (at most half the walled axis) adds
+ * an absorbing layer inside every wall: after each collision the populations of
+ * a site at distance i = 0 .. layer-1 from the wall-adjacent site are scaled by
+ * 1 - gamma_max ((layer - i)/layer)^2 (both axes' factors at corners), which
+ * damps E and B alike and keeps the medium's wave impedance; 0 <= gamma_max < 1.
+ * Every stepping mode applies (single, two and three steps per launch, graphs):
+ * after each launch a small kernel recomputes that launch's steps on the sites
+ * within max(layer, 1) + steps - 1 of a wall, so results stay bit-identical
+ * across modes.  All-periodic kind[] removes the walls.  LBEM_ERR_ARG for other
+ * values, 3D, or 16-bit storage; LBEM_ERR_STATE after lbem_forward_record (the
+ * adjoint is periodic only).  Batches (lbem_batch_create) take periodic members
+ * only.  Synchronises the stream. */
+lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double gamma_max);
+lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double *gamma_max);
 
 /* Watchdog (off by default): with every > 0, lbem_step computes the FP64 field energy (as
  * lbem_diagnostics, synchronising) whenever t reaches a multiple of `every`, and stops with

@@ -750,10 +750,17 @@ cudaError_t launch_step_2d(const StepArgs &a, int storage, bool has_mu, int vari
 #undef LBEM_CASE
 }
 
+// ------------------------------------------------------------------ walls in the state's readout
+// The stored state is post-collision: site x pulls g_i(x) = buf_i(x - c_i).  Across a wall (walls.cu) the pull is
+// the site's own opposite population times the wall sign: g_i(x) = s buf_opp(i)(x).
+__device__ __forceinline__ int opp2d(int i) { return i == 0 ? 0 : (i <= 2 ? i + 2 : i - 2); }
+__device__ __forceinline__ float wall_sign(int kind) { return kind == 1 ? -1.f : 1.f; }
+
 // ------------------------------------------------------------------ initial state: buf_i(x) = g^(0)_i(x + c_i)
+// (with walls, where x + c_i lies beyond a wall, buf_i(x) is what site x pulls back: s g^(0)_opp(i)(x))
 template <int ST>
 __global__ void __launch_bounds__(BLOCK) init2d(Grid G, PopBuf out, const float *cL2, const float *E, const float *B,
-                                                long long nsite) {
+                                                long long nsite, Walls w) {
     using C = Codec<ST>;
     const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
     const int row = (int)(tid / G.nchunk_pad);
@@ -765,17 +772,36 @@ __global__ void __launch_bounds__(BLOCK) init2d(Grid G, PopBuf out, const float 
         for (int j = 0; j < 4; j++) {
             const int x = 4 * c + j;
             if (x >= G.nx) break;
-            const int xs = (x + cx[i] + G.nx) % G.nx, ys = (row + cy[i] + G.ny) % G.ny;
+            int xs = x + cx[i], ys = row + cy[i], ie = i;
+            float sg = 1.f;
+            if (w.kind[0] && (xs < 0 || xs >= G.nx)) {
+                xs = x;
+                ie = opp2d(i);
+                sg = wall_sign(w.kind[0]);
+            } else if (w.kind[1] && (ys < 0 || ys >= G.ny)) {
+                ys = row;
+                ie = opp2d(i);
+                sg = wall_sign(w.kind[1]);
+            }
+            xs = (xs + G.nx) % G.nx;
+            ys = (ys + G.ny) % G.ny;
             const long long sd = (long long)ys * G.nx + xs;
             const float cl = cL2[(long long)ys * G.pitch + xs];
             const float Lam = E ? -E[2 * nsite + sd] : 0.f;
             const float bx = B ? B[sd] : 0.f, by = B ? B[nsite + sd] : 0.f;
             // Eq. 8: g^(0)_i = (w_i / c_L^2) [Lambda + c_ix B_y - c_iy B_x]
-            const float wc = (i == 0) ? (1.f - 2.f * cl) / cl : 0.5f;
-            set(v, j, wc * (Lam + cx[i] * by - cy[i] * bx));
+            const float wc = (ie == 0) ? (1.f - 2.f * cl) / cl : 0.5f;
+            set(v, j, sg * (wc * (Lam + cx[ie] * by - cy[ie] * bx)));
         }
         C::store4(out, i, row, c, v);
     }
+}
+
+static Walls handle_walls(const lbem_t *h) {
+    Walls w;
+    w.kind[0] = h->bc[0];
+    w.kind[1] = h->bc[1];
+    return w;
 }
 
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s) {
@@ -783,11 +809,12 @@ cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cuda
     const long long n = (long long)G.ny * G.nchunk_pad;
     const unsigned blocks = (unsigned)((n + BLOCK - 1) / BLOCK);
     const PopBuf &o = h->buf[h->cur];
+    const Walls w = handle_walls(h);
     switch (h->storage) {
-        case LBEM_F32: init2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite); break;
-        case LBEM_F16: init2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite); break;
-        case LBEM_BF16: init2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite); break;
-        default: init2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite); break;
+        case LBEM_F32: init2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
+        case LBEM_F16: init2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
+        case LBEM_BF16: init2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
+        default: init2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
     }
     return cudaGetLastError();
 }
@@ -795,7 +822,8 @@ cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cuda
 // ------------------------------------------------------------------ field extraction (dense [3][nsite] outputs)
 template <int ST>
 __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float *cL2, float *E, float *B,
-                                                  long long nsite) {
+                                                  long long nsite, Walls w) {
+    using C = Codec<ST>;
     const int lane = threadIdx.x & 31;
     const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const int wpr = G.nchunk_pad >> 5;
@@ -809,6 +837,11 @@ __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float
     for (int j = 0; j < 4; j++) {
         const int x = 4 * c + j;
         if (x >= G.nx) break;
+        // pulls across a wall
+        if (w.kind[0] && x == 0) set(g[1], j, wall_sign(w.kind[0]) * C::load1(in, 3, row, x));
+        if (w.kind[0] && x == G.nx - 1) set(g[3], j, wall_sign(w.kind[0]) * C::load1(in, 1, row, x));
+        if (w.kind[1] && row == 0) set(g[2], j, wall_sign(w.kind[1]) * C::load1(in, 4, row, x));
+        if (w.kind[1] && row == G.ny - 1) set(g[4], j, wall_sign(w.kind[1]) * C::load1(in, 2, row, x));
         const long long sd = (long long)row * G.nx + x;
         const float s = ((get(g[0], j) + get(g[1], j)) + (get(g[2], j) + get(g[3], j))) + get(g[4], j);
         if (E) {
@@ -829,28 +862,35 @@ cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s
     const long long warps = (long long)G.ny * (G.nchunk_pad / 32);
     const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
     const PopBuf &in = h->buf[h->cur];
+    const Walls w = handle_walls(h);
     switch (h->storage) {
-        case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite); break;
-        case LBEM_F16: fields2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite); break;
-        case LBEM_BF16: fields2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite); break;
-        default: fields2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite); break;
+        case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
+        case LBEM_F16: fields2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
+        case LBEM_BF16: fields2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
+        default: fields2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
     }
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ FP64 diagnostics
 template <int ST>
-__device__ __forceinline__ double pop2d(const PopBuf &in, const Grid &G, int i, int x, int y) {
-    // pre-collision g_i at (x, y): buf_i(x - c_i)
+__device__ __forceinline__ double pop2d(const PopBuf &in, const Grid &G, const Walls &w, int i, int x, int y) {
+    // pre-collision g_i at (x, y): buf_i(x - c_i), or s buf_opp(i)(x, y) across a wall
     const int cx[5] = {0, 1, 0, -1, 0}, cy[5] = {0, 0, 1, 0, -1};
-    const int xs = (x - cx[i] + G.nx) % G.nx, ys = (y - cy[i] + G.ny) % G.ny;
+    const int xu = x - cx[i], yu = y - cy[i];
+    if (w.kind[0] && (xu < 0 || xu >= G.nx))
+        return (double)wall_sign(w.kind[0]) * (double)Codec<ST>::load1(in, opp2d(i), y, x);
+    if (w.kind[1] && (yu < 0 || yu >= G.ny))
+        return (double)wall_sign(w.kind[1]) * (double)Codec<ST>::load1(in, opp2d(i), y, x);
+    const int xs = (xu + G.nx) % G.nx, ys = (yu + G.ny) % G.ny;
     return (double)Codec<ST>::load1(in, i, ys, xs);
 }
 
 template <int ST>
-__device__ __forceinline__ void bfield2d(const PopBuf &in, const Grid &G, int x, int y, double &bx, double &by) {
-    bx = pop2d<ST>(in, G, 4, x, y) - pop2d<ST>(in, G, 2, x, y);
-    by = pop2d<ST>(in, G, 1, x, y) - pop2d<ST>(in, G, 3, x, y);
+__device__ __forceinline__ void bfield2d(const PopBuf &in, const Grid &G, const Walls &w, int x, int y, double &bx,
+                                         double &by) {
+    bx = pop2d<ST>(in, G, w, 4, x, y) - pop2d<ST>(in, G, w, 2, x, y);
+    by = pop2d<ST>(in, G, w, 1, x, y) - pop2d<ST>(in, G, w, 3, x, y);
 }
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
@@ -866,7 +906,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 template <int ST>
-__global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *cL2, double *partials) {
+__global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *cL2, double *partials, Walls w) {
     __shared__ double sh[BLOCK / 32];
     double en = 0.0, inv = 0.0, dv = 0.0;
     const long long nsite = (long long)G.nx * G.ny;
@@ -874,7 +914,7 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
         const int y = (int)(s / G.nx), x = (int)(s - (long long)y * G.nx);
         double g[5], sum = 0.0;
         for (int i = 0; i < 5; i++) {
-            g[i] = pop2d<ST>(in, G, i, x, y);
+            g[i] = pop2d<ST>(in, G, w, i, x, y);
             sum += g[i];
         }
         const double cl = (double)cL2[(long long)y * G.pitch + x];
@@ -885,10 +925,11 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
         if (w0 != 0.0) q += g[0] * g[0] / w0;
         inv += 2.0 * q;  // g_xy and g_yx = -g_xy both count
         double bxp, byp, bxm, bym, t1, t2;
-        bfield2d<ST>(in, G, (x + 1) % G.nx, y, bxp, t1);
-        bfield2d<ST>(in, G, (x - 1 + G.nx) % G.nx, y, bxm, t2);
-        bfield2d<ST>(in, G, x, (y + 1) % G.ny, t1, byp);
-        bfield2d<ST>(in, G, x, (y - 1 + G.ny) % G.ny, t2, bym);
+        // (periodic central differences, also next to walls)
+        bfield2d<ST>(in, G, w, (x + 1) % G.nx, y, bxp, t1);
+        bfield2d<ST>(in, G, w, (x - 1 + G.nx) % G.nx, y, bxm, t2);
+        bfield2d<ST>(in, G, w, x, (y + 1) % G.ny, t1, byp);
+        bfield2d<ST>(in, G, w, x, (y - 1 + G.ny) % G.ny, t2, bym);
         const double div = 0.5 * (bxp - bxm) + 0.5 * (byp - bym);
         dv += div * div;
     }
@@ -902,11 +943,12 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
 
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s) {
     const PopBuf &in = h->buf[h->cur];
+    const Walls w = handle_walls(h);
     switch (h->storage) {
-        case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials); break;
-        case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials); break;
-        case LBEM_BF16: diag2d<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials); break;
-        default: diag2d<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials); break;
+        case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
+        case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
+        case LBEM_BF16: diag2d<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
+        default: diag2d<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
     }
     return cudaGetLastError();
 }

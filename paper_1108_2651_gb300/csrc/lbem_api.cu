@@ -143,6 +143,17 @@ static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two
 // Enqueue nsteps steps starting from buffer `cur` at time t0: triples (pairs) of steps with the three-step
 // (two-step) kernel when enabled, a remaining pair with the two-step kernel's default tile, single steps
 // otherwise; returns the buffer holding the final state in *cur_out.
+// With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu).
+static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
+    if (!h->walls()) return cudaSuccess;
+    Walls w;
+    w.kind[0] = h->bc[0];
+    w.kind[1] = h->bc[1];
+    w.fx = h->bc[0] ? h->d_fx : nullptr;
+    w.fy = h->bc[1] ? h->d_fy : nullptr;
+    return launch_edge_2d(a, w, h->d_tiles[k], h->ntiles[k], h->tile_smem[k], k, h->stream);
+}
+
 static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {
     int n = 0;
     if (three_step_ok(h)) {
@@ -150,6 +161,7 @@ static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nst
             StepArgs a = step_args(h, cur);
             a.t = t0 + n;
             cudaError_t e = launch_step_2d_tb3(a, h->tb_shape, h->stream);
+            if (e == cudaSuccess) e = edge_fixup(h, a, 3);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -159,6 +171,7 @@ static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nst
             StepArgs a = step_args(h, cur);
             a.t = t0 + n;
             cudaError_t e = launch_step_2d_tb2(a, h->storage, two_step_shape(h), h->stream);
+            if (e == cudaSuccess) e = edge_fixup(h, a, 2);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -167,6 +180,7 @@ static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nst
         StepArgs a = step_args(h, cur);
         a.t = t0 + n;
         cudaError_t e = launch_step(h, a, h->variant);
+        if (e == cudaSuccess) e = edge_fixup(h, a, 1);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
@@ -300,8 +314,9 @@ void lbem_destroy(lbem_t *h) {
     adjoint_free(h);
     for (void *p : {(void *)h->pool, (void *)h->cL2, (void *)h->mu, (void *)h->dlnmu, (void *)h->d_rowptr,
                     (void *)h->d_ev, (void *)h->d_amp, (void *)h->d_traces, (void *)h->d_partials,
-                    (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage})
+                    (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage, (void *)h->d_fx, (void *)h->d_fy})
         gfree(h, p);
+    for (int k = 1; k <= 3; k++) gfree(h, h->d_tiles[k]);
     delete h;
 }
 
@@ -354,6 +369,7 @@ lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
         LBEM_CUDA(cudaMemsetAsync(h->dlnmu, 0, sizeof(float) * h->grid.plane * h->dim, h->stream));
     }
     LBEM_CUDA(launch_medium_write(h, de, dm, h->stream));
+    if (dm && h->walls()) LBEM_CUDA(launch_medium_grad_walls(h, h->stream));
     h->has_mu = dm != nullptr;
     h->has_medium = true;
     drop_graph(h);
@@ -543,6 +559,70 @@ lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_s
     h->tblock = steps_per_pass;
     h->tb_shape = tile_shape < 0 ? 0 : tile_shape;
     drop_graph(h);
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double gamma_max) {
+    if (!h || !kind) return fail(LBEM_ERR_ARG, "null argument");
+    for (int a = 0; a < 3; a++)
+        if (kind[a] < LBEM_BC_PERIODIC || kind[a] > LBEM_BC_PMC)
+            return fail(LBEM_ERR_ARG, "lbem_set_boundaries: kind must be LBEM_BC_PERIODIC, _PEC or _PMC");
+    const bool any = kind[0] || kind[1] || kind[2];
+    if (any && (h->dim != 2 || kind[2]))
+        return fail(LBEM_ERR_ARG, "lbem_set_boundaries: walls exist for 2D grids (x and y)");
+    if (any && h->storage != LBEM_F32) return fail(LBEM_ERR_ARG, "lbem_set_boundaries: walls need LBEM_F32 storage");
+    if (layer < 0 || !(gamma_max >= 0.0 && gamma_max < 1.0))
+        return fail(LBEM_ERR_ARG, "lbem_set_boundaries: layer >= 0 and 0 <= gamma_max < 1");
+    if (layer > 0 && !any) return fail(LBEM_ERR_ARG, "lbem_set_boundaries: an absorbing layer needs a wall");
+    if ((kind[0] && 2 * layer > h->grid.nx) || (kind[1] && 2 * layer > h->grid.ny))
+        return fail(LBEM_ERR_ARG, "lbem_set_boundaries: layer wider than half the walled axis");
+    if (h->adj) return fail(LBEM_ERR_STATE, "lbem_set_boundaries: a recorded adjoint run exists (periodic only)");
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    gfree(h, h->d_fx);
+    gfree(h, h->d_fy);
+    h->d_fx = h->d_fy = nullptr;
+    for (int k = 1; k <= 3; k++) {
+        gfree(h, h->d_tiles[k]);
+        h->d_tiles[k] = nullptr;
+        h->ntiles[k] = 0;
+        h->tile_smem[k] = 0;
+    }
+    for (int a = 0; a < 3; a++) h->bc[a] = kind[a];
+    h->layer = any ? layer : 0;
+    h->gamma_max = any ? gamma_max : 0.0;
+    drop_graph(h);
+    if (h->has_mu && h->dim == 2) LBEM_CUDA(launch_medium_grad_walls(h, h->stream));  // grad ln mu at the walls
+    if (!any) return LBEM_OK;
+    // layer factors 1 - gamma_max ((L - i)/L)^2 at distance i from the wall-adjacent site, per column / row
+    const int len[2] = {h->grid.nx, h->grid.ny};
+    float **dst[2] = {&h->d_fx, &h->d_fy};
+    for (int a = 0; a < 2; a++) {
+        if (!kind[a] || layer == 0) continue;
+        std::vector<float> f(len[a]);
+        for (int v = 0; v < len[a]; v++) {
+            const int i = std::min(v, len[a] - 1 - v);
+            const double r = (double)(layer - i) / layer;
+            f[v] = i < layer ? (float)(1.0 - gamma_max * r * r) : 1.f;
+        }
+        LBEM_CUDA(gmalloc(h, (void **)dst[a], sizeof(float) * len[a], "layer factors"));
+        LBEM_CUDA(cudaMemcpy(*dst[a], f.data(), sizeof(float) * len[a], cudaMemcpyHostToDevice));
+    }
+    for (int k = 1; k <= 3; k++) {
+        const std::vector<EdgeTile> t = edge_tiles(h->grid, h->bc, h->layer, k);
+        h->ntiles[k] = (int)t.size();
+        h->tile_smem[k] = edge_smem_bytes(k, t, true);
+        LBEM_CUDA(gmalloc(h, (void **)&h->d_tiles[k], sizeof(EdgeTile) * std::max<size_t>(t.size(), 1), "edge tiles"));
+        LBEM_CUDA(cudaMemcpy(h->d_tiles[k], t.data(), sizeof(EdgeTile) * t.size(), cudaMemcpyHostToDevice));
+    }
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBEM_OK;
+}
+
+lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double *gamma_max) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    for (int a = 0; kind && a < 3; a++) kind[a] = h->bc[a];
+    if (layer) *layer = h->layer;
+    if (gamma_max) *gamma_max = h->gamma_max;
     return LBEM_OK;
 }
 

@@ -297,6 +297,17 @@ struct Medium {
     const float *dlnmu = nullptr;  // [D][plane] or null
 };
 
+// Walls and absorbing layers (walls.cu): per axis x, y 0 = periodic, 1 = PEC wall, 2 = PMC wall; layer
+// damping factors per column / row (null: no layer on that axis).
+struct Walls {
+    int kind[2] = {0, 0};
+    const float *fx = nullptr, *fy = nullptr;
+};
+// Output rectangle of one edge tile: columns x0 .. x0+w-1, rows y0 .. y0+h-1.
+struct EdgeTile {
+    int x0, y0, w, h;
+};
+
 struct StepArgs {
     Grid g;
     PopBuf in, out;
@@ -391,6 +402,15 @@ struct lbem {
     // watchdog (lbem_set_watchdog)
     int wd_every = 0;
     double wd_growth = 0.0, wd_last = -1.0;
+    // walls and absorbing layers (lbem_set_boundaries); edge tiles per steps-per-launch k = 1..3
+    int bc[3] = {0, 0, 0};
+    int layer = 0;
+    double gamma_max = 0.0;
+    float *d_fx = nullptr, *d_fy = nullptr;
+    lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
+    int ntiles[4] = {0, 0, 0, 0};
+    size_t tile_smem[4] = {0, 0, 0, 0};
+    bool walls() const { return bc[0] || bc[1] || bc[2]; }
     // adjoint
     lbk::AdjointState *adj = nullptr;
     // guard bands around every array above (see lbem_check_guards)
@@ -451,5 +471,11 @@ cudaError_t gmalloc(lbem_t *h, void **p, size_t bytes, const char *name);
 void gfree(lbem_t *h, void *p);
 // adjoint.cu
 void adjoint_free(lbem_t *h);
+// walls.cu: the k steps of a launch recomputed on the bands next to walls and in layers
+std::vector<EdgeTile> edge_tiles(const Grid &G, const int kind[2], int layer, int k);
+size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu);
+cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
+                           cudaStream_t s);
+cudaError_t launch_medium_grad_walls(const lbem_t *h, cudaStream_t s);
 
 }  // namespace lbk

@@ -51,6 +51,8 @@ _SIGS = {
     "lbem_set_temporal_blocking": [_VP, _I, _I],
     "lbem_get_temporal_blocking": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)],
     "lbem_set_watchdog": [_VP, _I, _D],
+    "lbem_set_boundaries": [_VP, C.POINTER(_I), _I, _D],
+    "lbem_get_boundaries": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)],
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
     "lbem_traces": [_VP, _VP, C.POINTER(_I)],
@@ -201,6 +203,22 @@ def lbem_step(h, nsteps):
 
 def lbem_set_watchdog(h, every, max_growth=1e6):
     _check(load().lbem_set_watchdog(h, int(every), float(max_growth)))
+
+
+BC_PERIODIC, BC_PEC, BC_PMC = 0, 1, 2
+
+
+def lbem_set_boundaries(h, kind, layer=0, gamma_max=0.0):
+    """kind: boundary per axis (x, y[, z]): BC_PERIODIC, BC_PEC or BC_PMC."""
+    k = (_I * 3)(*(list(kind) + [0] * (3 - len(kind))))
+    _check(load().lbem_set_boundaries(h, k, int(layer), float(gamma_max)))
+
+
+def lbem_get_boundaries(h):
+    """((kind_x, kind_y, kind_z), layer, gamma_max)."""
+    k, L, g = (_I * 3)(), _I(), _D()
+    _check(load().lbem_get_boundaries(h, k, C.byref(L), C.byref(g)))
+    return tuple(k), L.value, g.value
 
 
 def lbem_set_temporal_blocking(h, steps_per_pass, tile_shape=-1):
@@ -360,6 +378,9 @@ class Solver:
         eps = torch.as_tensor(np.ascontiguousarray(p.eps_r, np.float32).ravel(), device=device)
         mu = None if p.mu_r is None else torch.as_tensor(np.ascontiguousarray(p.mu_r, np.float32).ravel(), device=device)
         lbem_set_medium(self.h, eps, mu)
+        bc = tuple(getattr(p, "bc", (0, 0, 0)))
+        if any(bc) or any(lbem_get_boundaries(self.h)[0]):
+            lbem_set_boundaries(self.h, bc, getattr(p, "layer", 0), getattr(p, "gamma_max", 0.0))
         if p.src_site.size:
             lbem_set_sources(self.h, p.src_site, p.src_comp, p.src_amp)
         else:

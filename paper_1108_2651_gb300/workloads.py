@@ -79,6 +79,9 @@ class Problem:
     src_amp: np.ndarray = field(default_factory=lambda: np.zeros((0, 1)))
     rec_site: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     rec_comp: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    bc: tuple = (0, 0, 0)  # boundary per axis x, y, z: 0 periodic, 1 PEC wall, 2 PMC wall (2D)
+    layer: int = 0  # absorbing layer inside the walls (sites)
+    gamma_max: float = 0.0  # its damping at the wall-adjacent site
 
     @property
     def c_ref2(self):
@@ -157,6 +160,17 @@ def heterogeneous_2d_mu(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec_ra
     eps[low] = np.nextafter(eps[low], np.float32(np.inf))
     p.eps_r = eps.astype(np.float64)
     p.mu_r = mu.astype(np.float64)
+    return p
+
+
+def heterogeneous_2d_walls(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec_radius=None, bc=(1, 1, 0),
+                           layer=32, gamma_max=0.2, name=None):
+    """heterogeneous_2d in a box: walls on x and y (default PEC) with an absorbing layer of `layer` sites inside
+    them (damping gamma_max at the wall-adjacent site), so the waves leave the domain instead of wrapping."""
+    p = heterogeneous_2d(n, seed, nsteps, sigma, nrec, rec_radius, name=name or f"het2d_walls_{n}")
+    p.bc = tuple(bc) + (0,) * (3 - len(bc))
+    p.layer = int(layer)
+    p.gamma_max = float(gamma_max)
     return p
 
 

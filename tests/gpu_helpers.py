@@ -43,7 +43,7 @@ def f32(a):
 def oracle_run(p, nsteps=None):
     """The same problem on the FP64 oracle; returns (E, B, traces, medium, state)."""
     nsteps = p.nsteps if nsteps is None else nsteps
-    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r))
+    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r), bc=p.bc, layer=p.layer, gamma_max=p.gamma_max)
     g = O.init_state(m, f32(p.E0), f32(p.B0))
     src = p.sources()
     if src is not None:
