@@ -101,6 +101,8 @@ def workload(name):
         return W.heterogeneous_2d(4096, seed=2, nsteps=5000)
     if name == "het2d_1024":
         return W.heterogeneous_2d(1024, seed=1, nsteps=5000)
+    if name == "het2d_walls_4096":
+        return W.heterogeneous_2d_walls(4096, seed=2, nsteps=5000)
     if name == "het3d_192":
         return W.heterogeneous_3d(192, seed=4, nsteps=1000)
     raise ValueError(name)
@@ -289,6 +291,18 @@ def other_forms(lbem, torch, p, peak, stream):
         out[key] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                     "frac": gbs / peak, "bytes_per_site_per_launch": 52, "steps_per_launch": spp, "variant": v,
                     "lb_steps": 2000}
+    # the same medium in a PEC box with a 32-site absorbing layer, 2000 steps: the stream-collide launches plus
+    # the edge kernel after each (44 algorithmic B/site per launch; the edge recompute counts as overhead)
+    pw = W.heterogeneous_2d_walls(p.shape[0], seed=2, nsteps=2000)
+    s = lbem.Solver(pw.shape, stream=stream.cuda_stream)
+    ms, v, spp = _time_run(lbem, torch, s, pw, 2000, stream)
+    s.close()
+    per = ms / (2000 // spp)
+    gbs = 44 * n / (per * 1e-3) / 1e9
+    out["f32_walls_absorbing"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                                  "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp,
+                                  "variant": v, "lb_steps": 2000, "bc": list(pw.bc), "layer": pw.layer,
+                                  "gamma_max": pw.gamma_max}
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
     ms, v, _ = _time_run(lbem, torch, s, q, 1000, stream)
@@ -348,7 +362,7 @@ def cpu_baseline(p, budget_s=12.0):
     c0 = (p.shape[0] - n) // 2
     crop = tuple(slice(c0, c0 + n) for _ in range(p.D))
     eps = np.asarray(p.eps_r[crop], np.float32).astype(np.float64)
-    m = O.medium(p.D, eps)
+    m = O.medium(p.D, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max)
     g = O.init_state(m)
     shape = (n,) * p.D
     src = dict(site=np.array([W.flat_index(shape, (n // 2,) * p.D)]), comp=np.array([2]),
@@ -406,7 +420,7 @@ def run_reference(args, rank, world):
     n = min(1024, p.shape[0])
     c0 = (p.shape[0] - n) // 2
     eps = np.asarray(p.eps_r[c0:c0 + n, c0:c0 + n], np.float32).astype(np.float64)
-    m = O.medium(2, eps)
+    m = O.medium(2, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max)
     src = dict(site=np.array([W.flat_index((n, n), (n // 2, n // 2))]), comp=np.array([2]),
                amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
     for k in range(args.warmup + args.steps):
@@ -436,7 +450,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
     ap.add_argument("--workload", default="het2d_4096",
-                    choices=["het2d_4096", "het2d_1024", "het3d_192", "batch256", "adjoint3d_96"])
+                    choices=["het2d_4096", "het2d_1024", "het2d_walls_4096", "het3d_192", "batch256",
+                             "adjoint3d_96"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
     ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
     ap.add_argument("--ref-steps", type=int, default=40)
@@ -485,6 +500,9 @@ def main():
     h = s.h
     state_mb = lbem.lbem_info(h)[1] / 1e6
     lbem.lbem_set_medium(h, eps_d)
+    walls = any(p.bc)
+    if walls:
+        lbem.lbem_set_boundaries(h, p.bc, p.layer, p.gamma_max)
     lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
     lbem.lbem_set_receivers(h, p.rec_site, p.rec_comp, nsteps)
     variant = lbem.lbem_get_variant(h)[0]
@@ -548,6 +566,8 @@ def main():
     else:
         kname = (f"step2d<{args.storage}>" if p.D == 2 else "step3d") + f" (variant {variant})"
         kid = variant
+    if walls:
+        kname += " + edge2d (walls and layers)"
     traffic = NCU_TRAFFIC.get((args.workload, args.storage, kid)) if args.lb_steps is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "steps_per_launch": spp,
@@ -588,7 +608,7 @@ def main():
         cpu = cpu_baseline(p)
     s.close()
     if rank == 0:
-        launches = args.steps * (step_launches + 6 + (1 if args.storage == "f16" else 0))
+        launches = args.steps * (step_launches * (2 if walls else 1) + 6 + (1 if args.storage == "f16" else 0))
         line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32-math/{args.storage}-storage",

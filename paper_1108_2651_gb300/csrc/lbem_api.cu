@@ -151,7 +151,8 @@ static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
     w.kind[1] = h->bc[1];
     w.fx = h->bc[0] ? h->d_fx : nullptr;
     w.fy = h->bc[1] ? h->d_fy : nullptr;
-    return launch_edge_2d(a, w, h->d_tiles[k], h->ntiles[k], h->tile_smem[k], k, h->stream);
+    return launch_edge_2d(a, w, h->d_tiles[k], h->ntiles[k], h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k,
+                          h->stream);
 }
 
 static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {
@@ -585,7 +586,7 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
         gfree(h, h->d_tiles[k]);
         h->d_tiles[k] = nullptr;
         h->ntiles[k] = 0;
-        h->tile_smem[k] = 0;
+        h->tile_smem[k] = h->tile_smem_mu[k] = 0;
     }
     for (int a = 0; a < 3; a++) h->bc[a] = kind[a];
     h->layer = any ? layer : 0;
@@ -610,7 +611,8 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
     for (int k = 1; k <= 3; k++) {
         const std::vector<EdgeTile> t = edge_tiles(h->grid, h->bc, h->layer, k);
         h->ntiles[k] = (int)t.size();
-        h->tile_smem[k] = edge_smem_bytes(k, t, true);
+        h->tile_smem[k] = edge_smem_bytes(k, t, false);
+        h->tile_smem_mu[k] = edge_smem_bytes(k, t, true);
         LBEM_CUDA(gmalloc(h, (void **)&h->d_tiles[k], sizeof(EdgeTile) * std::max<size_t>(t.size(), 1), "edge tiles"));
         LBEM_CUDA(cudaMemcpy(h->d_tiles[k], t.data(), sizeof(EdgeTile) * t.size(), cudaMemcpyHostToDevice));
     }

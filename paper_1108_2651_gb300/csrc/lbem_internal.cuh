@@ -409,7 +409,7 @@ struct lbem {
     float *d_fx = nullptr, *d_fy = nullptr;
     lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     int ntiles[4] = {0, 0, 0, 0};
-    size_t tile_smem[4] = {0, 0, 0, 0};
+    size_t tile_smem[4] = {0, 0, 0, 0}, tile_smem_mu[4] = {0, 0, 0, 0};  // uniform / heterogeneous mu
     bool walls() const { return bc[0] || bc[1] || bc[2]; }
     // adjoint
     lbk::AdjointState *adj = nullptr;

@@ -27,14 +27,16 @@
 
 namespace lbk {
 
-constexpr int EDGE_THREADS = 256;
+constexpr int EDGE_THREADS = 512;
 constexpr int EDGE_MAX_WINDOW = 1536;  // staged sites per tile (output rectangle plus halo)
+constexpr int EDGE_PER_THREAD = EDGE_MAX_WINDOW / EDGE_THREADS;
 
 // Per staged site: current and next populations (10 floats), c_L^2, the layer factor; with mu, grad ln mu.
-static int edge_floats_per_site(bool mu) { return 12 + (mu ? 2 : 0); }
+// Then one int per window row: whether the row holds sources or receivers.
+__host__ __device__ constexpr int edge_floats_per_site(bool mu) { return 12 + (mu ? 2 : 0); }
 
 template <bool MU>
-__global__ void __launch_bounds__(EDGE_THREADS) edge2d(StepArgs a, Walls w, const EdgeTile *tiles, int k) {
+__global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, const EdgeTile *tiles, int k) {
     extern __shared__ __align__(16) float sm[];
     const Grid &G = a.g;
     const EdgeTile T = tiles[blockIdx.x];
@@ -42,35 +44,66 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge2d(StepArgs a, Walls w, cons
     const int wx0 = T.x0 - k, wy0 = T.y0 - k;  // unwrapped coordinates of window site (0, 0)
     float *cur = sm, *nxt = sm + 5 * NW, *cl = sm + 10 * NW, *fac = sm + 11 * NW;
     float *dxm = sm + 12 * NW, *dym = sm + 13 * NW;  // MU only
+    int *rowev = reinterpret_cast<int *>(sm + edge_floats_per_site(MU) * NW);
     const float *in = static_cast<const float *>(a.in.data);
     const float sx = w.kind[0] == 1 ? -1.f : 1.f, sy = w.kind[1] == 1 ? -1.f : 1.f;
 
     // global coordinate of an unwrapped one along an axis, or -1 beyond a wall
     auto gcoord = [](int v, int n, int kind) { return kind ? ((unsigned)v < (unsigned)n ? v : -1) : wrapi(v, n); };
 
-    for (int s = threadIdx.x; s < NW; s += EDGE_THREADS) {
-        const int j = s / WW, i = s - j * WW;
-        const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
-        if (gx < 0 || gy < 0) continue;
-        const long long o = (long long)gy * G.pitch + gx;
-        const long long oi = (long long)gy * a.in.pitch + gx;
+    for (int j = threadIdx.x; j < WH; j += EDGE_THREADS) {
+        const int gy = gcoord(wy0 + j, G.ny, w.kind[1]);
+        rowev[j] = (gy >= 0 && a.evt.rowptr) ? (__ldg(a.evt.rowptr + gy + 1) > __ldg(a.evt.rowptr + gy)) : 0;
+    }
+    // window load: a thread's sites are loaded together (the loads of all of them in flight at once)
+    {
+        float v[EDGE_PER_THREAD][5], c[EDGE_PER_THREAD], f[EDGE_PER_THREAD], dx[EDGE_PER_THREAD],
+            dy[EDGE_PER_THREAD];
 #pragma unroll
-        for (int p = 0; p < 5; p++) cur[p * NW + s] = in[p * a.in.plane + oi];
-        cl[s] = a.med.cL2[o];
-        fac[s] = __fmul_rn(w.fx ? w.fx[gx] : 1.f, w.fy ? w.fy[gy] : 1.f);
-        if (MU) {
-            dxm[s] = a.med.dlnmu[o];
-            dym[s] = a.med.dlnmu[G.plane + o];
+        for (int u = 0; u < EDGE_PER_THREAD; u++) {
+            const int s = threadIdx.x + u * EDGE_THREADS;
+            const int j = s / WW, i = s - j * WW;
+            const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
+            if (s < NW && gx >= 0 && gy >= 0) {
+                const long long o = (long long)gy * G.pitch + gx;
+                const long long oi = (long long)gy * a.in.pitch + gx;
+#pragma unroll
+                for (int p = 0; p < 5; p++) v[u][p] = __ldg(in + p * a.in.plane + oi);
+                c[u] = __ldg(a.med.cL2 + o);
+                f[u] = __fmul_rn(w.fx ? __ldg(w.fx + gx) : 1.f, w.fy ? __ldg(w.fy + gy) : 1.f);
+                if (MU) {
+                    dx[u] = __ldg(a.med.dlnmu + o);
+                    dy[u] = __ldg(a.med.dlnmu + G.plane + o);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < EDGE_PER_THREAD; u++) {
+            const int s = threadIdx.x + u * EDGE_THREADS;
+            const int j = s / WW, i = s - j * WW;
+            const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
+            if (s < NW && gx >= 0 && gy >= 0) {
+#pragma unroll
+                for (int p = 0; p < 5; p++) cur[p * NW + s] = v[u][p];
+                cl[s] = c[u];
+                fac[s] = f[u];
+                if (MU) {
+                    dxm[s] = dx[u];
+                    dym[s] = dy[u];
+                }
+            }
         }
     }
     __syncthreads();
 
     for (int step = 0; step < k; step++) {
         const long long t = a.t + step;
-        for (int s = threadIdx.x; s < NW; s += EDGE_THREADS) {
+#pragma unroll
+        for (int u = 0; u < EDGE_PER_THREAD; u++) {
+            const int s = threadIdx.x + u * EDGE_THREADS;
             const int j = s / WW, i = s - j * WW;
             const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
-            if (gx < 0 || gy < 0) continue;
+            if (s >= NW || gx < 0 || gy < 0) continue;
             // pulls g_i(x) = g'_i(x - c_i): across a wall the opposite population of this site times the wall
             // sign; beyond the window's open edges the value is never used by an output site (0 here)
             const float g0 = cur[s];
@@ -86,8 +119,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) edge2d(StepArgs a, Walls w, cons
             const float c = cl[s];
             float shat = 0.f;
             if (MU) shat = mu_source(g4 - g2, g1 - g3, dxm[s], dym[s]);
-            const bool owned = i >= k && i < k + T.w && j >= k && j < k + T.h;
-            shat = site_events(a, gx, gy, t, owned, g0, g1, g2, g3, g4, c, shat);
+            if (rowev[j]) {
+                const bool owned = i >= k && i < k + T.w && j >= k && j < k + T.h;
+                shat = site_events(a, gx, gy, t, owned, g0, g1, g2, g3, g4, c, shat);
+            }
             Out5 r = collide2d(g0, g1, g2, g3, g4, c, shat);
             const float f = fac[s];
             nxt[s] = __fmul_rn(r.o0, f);
@@ -161,9 +196,12 @@ std::vector<EdgeTile> edge_tiles(const Grid &G, const int kind[2], int layer, in
 }
 
 size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu) {
-    int nw = 0;
-    for (auto &e : tiles) nw = std::max(nw, (e.w + 2 * k) * (e.h + 2 * k));
-    return sizeof(float) * (size_t)edge_floats_per_site(mu) * nw;
+    int nw = 0, wh = 0;
+    for (auto &e : tiles) {
+        nw = std::max(nw, (e.w + 2 * k) * (e.h + 2 * k));
+        wh = std::max(wh, e.h + 2 * k);
+    }
+    return sizeof(float) * (size_t)edge_floats_per_site(mu) * nw + sizeof(int) * (size_t)wh;
 }
 
 cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
@@ -172,7 +210,7 @@ cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_
     static bool attr[2] = {false, false};
     const bool mu = a.med.dlnmu != nullptr;
     if (!attr[mu]) {
-        const int max_bytes = (int)(sizeof(float) * edge_floats_per_site(true) * EDGE_MAX_WINDOW);
+        const int max_bytes = (int)((sizeof(float) * edge_floats_per_site(true) + sizeof(int)) * EDGE_MAX_WINDOW);
         cudaError_t e = mu ? cudaFuncSetAttribute(edge2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes)
                            : cudaFuncSetAttribute(edge2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         if (e != cudaSuccess) return e;
