@@ -32,7 +32,8 @@ constexpr int EDGE_MAX_WINDOW = 1536;  // staged sites per tile (output rectangl
 constexpr int EDGE_PER_THREAD = EDGE_MAX_WINDOW / EDGE_THREADS;
 
 // Per staged site: current and next populations (10 floats), c_L^2, the layer factor; with mu, grad ln mu.
-// Then one int per window row: whether the row holds sources or receivers.
+// Then per window column its global x and per window row its global y (-1 beyond a wall) and whether the row
+// holds sources or receivers.
 __host__ __device__ constexpr int edge_floats_per_site(bool mu) { return 12 + (mu ? 2 : 0); }
 
 template <bool MU>
@@ -44,27 +45,38 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, c
     const int wx0 = T.x0 - k, wy0 = T.y0 - k;  // unwrapped coordinates of window site (0, 0)
     float *cur = sm, *nxt = sm + 5 * NW, *cl = sm + 10 * NW, *fac = sm + 11 * NW;
     float *dxm = sm + 12 * NW, *dym = sm + 13 * NW;  // MU only
-    int *rowev = reinterpret_cast<int *>(sm + edge_floats_per_site(MU) * NW);
+    int *colg = reinterpret_cast<int *>(sm + edge_floats_per_site(MU) * NW), *rowg = colg + WW, *rowev = rowg + WH;
     const float *in = static_cast<const float *>(a.in.data);
     const float sx = w.kind[0] == 1 ? -1.f : 1.f, sy = w.kind[1] == 1 ? -1.f : 1.f;
 
     // global coordinate of an unwrapped one along an axis, or -1 beyond a wall
     auto gcoord = [](int v, int n, int kind) { return kind ? ((unsigned)v < (unsigned)n ? v : -1) : wrapi(v, n); };
-
+    for (int i = threadIdx.x; i < WW; i += EDGE_THREADS) colg[i] = gcoord(wx0 + i, G.nx, w.kind[0]);
     for (int j = threadIdx.x; j < WH; j += EDGE_THREADS) {
         const int gy = gcoord(wy0 + j, G.ny, w.kind[1]);
+        rowg[j] = gy;
         rowev[j] = (gy >= 0 && a.evt.rowptr) ? (__ldg(a.evt.rowptr + gy + 1) > __ldg(a.evt.rowptr + gy)) : 0;
     }
+    // this thread's window sites s = threadIdx.x + u * EDGE_THREADS, as (column, row); row WH marks none
+    int ci[EDGE_PER_THREAD], rj[EDGE_PER_THREAD];
+#pragma unroll
+    for (int u = 0; u < EDGE_PER_THREAD; u++) {
+        const int s = threadIdx.x + u * EDGE_THREADS;
+        rj[u] = s < NW ? s / WW : WH;
+        ci[u] = s - rj[u] * WW;
+    }
+    __syncthreads();
+
     // window load: a thread's sites are loaded together (the loads of all of them in flight at once)
     {
         float v[EDGE_PER_THREAD][5], c[EDGE_PER_THREAD], f[EDGE_PER_THREAD], dx[EDGE_PER_THREAD],
             dy[EDGE_PER_THREAD];
+        bool ok[EDGE_PER_THREAD];
 #pragma unroll
         for (int u = 0; u < EDGE_PER_THREAD; u++) {
-            const int s = threadIdx.x + u * EDGE_THREADS;
-            const int j = s / WW, i = s - j * WW;
-            const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
-            if (s < NW && gx >= 0 && gy >= 0) {
+            const int gx = rj[u] < WH ? colg[ci[u]] : -1, gy = rj[u] < WH ? rowg[rj[u]] : -1;
+            ok[u] = gx >= 0 && gy >= 0;
+            if (ok[u]) {
                 const long long o = (long long)gy * G.pitch + gx;
                 const long long oi = (long long)gy * a.in.pitch + gx;
 #pragma unroll
@@ -80,9 +92,7 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, c
 #pragma unroll
         for (int u = 0; u < EDGE_PER_THREAD; u++) {
             const int s = threadIdx.x + u * EDGE_THREADS;
-            const int j = s / WW, i = s - j * WW;
-            const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
-            if (s < NW && gx >= 0 && gy >= 0) {
+            if (ok[u]) {
 #pragma unroll
                 for (int p = 0; p < 5; p++) cur[p * NW + s] = v[u][p];
                 cl[s] = c[u];
@@ -100,10 +110,11 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, c
         const long long t = a.t + step;
 #pragma unroll
         for (int u = 0; u < EDGE_PER_THREAD; u++) {
+            const int i = ci[u], j = rj[u];
+            if (j >= WH) continue;
+            const int gx = colg[i], gy = rowg[j];
+            if (gx < 0 || gy < 0) continue;
             const int s = threadIdx.x + u * EDGE_THREADS;
-            const int j = s / WW, i = s - j * WW;
-            const int gx = gcoord(wx0 + i, G.nx, w.kind[0]), gy = gcoord(wy0 + j, G.ny, w.kind[1]);
-            if (s >= NW || gx < 0 || gy < 0) continue;
             // pulls g_i(x) = g'_i(x - c_i): across a wall the opposite population of this site times the wall
             // sign; beyond the window's open edges the value is never used by an output site (0 here)
             const float g0 = cur[s];
@@ -137,14 +148,16 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, c
         nxt = tmp;
     }
 
+    // the output rectangle (window columns and rows k .. k + w - 1, k .. k + h - 1)
     float *out = static_cast<float *>(a.out.data);
-    for (int s = threadIdx.x; s < T.w * T.h; s += EDGE_THREADS) {
-        const int j = s / T.w, i = s - j * T.w;
-        const int gx = T.x0 + i, gy = T.y0 + j;
-        const int ws = (j + k) * WW + (i + k);
-        const long long o = (long long)gy * a.out.pitch + gx;
 #pragma unroll
-        for (int p = 0; p < 5; p++) out[p * a.out.plane + o] = cur[p * NW + ws];
+    for (int u = 0; u < EDGE_PER_THREAD; u++) {
+        const int i = ci[u], j = rj[u];
+        if (j < k || j >= k + T.h || i < k || i >= k + T.w) continue;
+        const int s = threadIdx.x + u * EDGE_THREADS;
+        const long long o = (long long)(T.y0 + j - k) * a.out.pitch + (T.x0 + i - k);
+#pragma unroll
+        for (int p = 0; p < 5; p++) out[p * a.out.plane + o] = cur[p * NW + s];
     }
 }
 
@@ -201,7 +214,9 @@ size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu) {
         nw = std::max(nw, (e.w + 2 * k) * (e.h + 2 * k));
         wh = std::max(wh, e.h + 2 * k);
     }
-    return sizeof(float) * (size_t)edge_floats_per_site(mu) * nw + sizeof(int) * (size_t)wh;
+    int ww = 0;
+    for (auto &e : tiles) ww = std::max(ww, e.w + 2 * k);
+    return sizeof(float) * (size_t)edge_floats_per_site(mu) * nw + sizeof(int) * (size_t)(ww + 2 * wh);
 }
 
 cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
@@ -210,7 +225,7 @@ cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_
     static bool attr[2] = {false, false};
     const bool mu = a.med.dlnmu != nullptr;
     if (!attr[mu]) {
-        const int max_bytes = (int)((sizeof(float) * edge_floats_per_site(true) + sizeof(int)) * EDGE_MAX_WINDOW);
+        const int max_bytes = (int)((sizeof(float) * edge_floats_per_site(true) + 3 * sizeof(int)) * EDGE_MAX_WINDOW);
         cudaError_t e = mu ? cudaFuncSetAttribute(edge2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes)
                            : cudaFuncSetAttribute(edge2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         if (e != cudaSuccess) return e;
