@@ -56,6 +56,25 @@
  *      the factors of two axes multiplied at corners.  Scaling E and B by the
  *      same factor damps them equally (matched electric and magnetic
  *      conductivity), so the layer keeps the wave impedance of the medium.
+ *  R9  Frequency-dispersive permittivity (the convolution term of Eq. 3,
+ *      which the paper defers to auxiliary differential equations): one
+ *      Drude-Lorentz pole per site, d_t J + gamma J + wr^2 P = wp^2 E with
+ *      J = d_t P (P in units of E: eps(omega) = eps_inf (1 + wp^2 / (wr^2 -
+ *      omega^2 - i gamma omega))).  Entering P as the source S = -d_t P of
+ *      Eq. 3 makes the scheme unstable (the source's (c^2/2) Lap S part acts
+ *      on the accumulated current); it enters instead as the displacement
+ *      form of the same equations: the lattice's zeroth moment carries
+ *      D/eps_inf (no source: d_t D = curl H), the field is E = D/eps_inf - P,
+ *      and the equilibrium keeps its zeroth and first moments while its
+ *      second moment Lambda_ab takes E (Lambda_ab += eps_gab P_g: +1/2 of
+ *      that on every moving population, -D times it on the rest one).  J
+ *      lives at half steps, P at whole ones; at time t, from the pre-collision
+ *      E(t) = D(t)/eps_inf - P(t):
+ *        J(t+1/2) = [(1 - gamma/2) J(t-1/2) + wp^2 E(t) - wr^2 P(t)] / (1 + gamma/2)
+ *        P(t+1)   = P(t) + J(t+1/2)
+ *      and the collision at t uses P(t).  A uniform medium then has the plane
+ *      waves 4 sin^2(omega/2) = 4 c^2 (sin^2(kx/2) + sin^2(ky/2)) + wp^2
+ *      (wr = gamma = 0), and stays stable where wp^2 + wr^2 <= 4 w0.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -292,11 +311,14 @@ void or_fields(int D, int nx, int ny, int nz, const double *cL2, const double *g
  * j is the current density at this site and time (3-vector).
  */
 static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2, double mus, const double dlnmu[3],
-                         const double j[3], const double *gin, double *gout, double E[3], double B[3]) {
+                         const double j[3], const double *ppol, const double *gin, double *gout, double E[3],
+                         double B[3]) {
     const int D = L->D, Q = L->Q;
     const double dt = 1.0, tau = 0.5;
     double Lam[MAXD][MAXD], S[3], geq[MAXQ * MAXD * MAXD];
     site_moments(L, gin, cL2, Lam, E, B);
+    if (ppol) /* reading R9: the field is D/eps_inf - P */
+        for (int g = 0; g < 3; g++) E[g] -= ppol[g];
     for (int g = 0; g < 3; g++) {
         double curl = 0.0;
         for (int b = 0; b < 3; b++)
@@ -304,6 +326,15 @@ static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2
         S[g] = ceff2 * curl - mus * ceff2 * j[g];
     }
     equilibrium(L, cL2, w0, Lam, B, geq);
+    if (ppol) {
+        /* reading R9: second moment Lambda_ab + eps_gab P_g, zeroth and first moments unchanged */
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) {
+                double dl = 0.0;
+                for (int g = 0; g < 3; g++) dl += levi(g, a, b) * ppol[g];
+                for (int i = 0; i < Q; i++) geq[(i * D + a) * D + b] += (i == 0 ? -(double)D : 0.5) * dl;
+            }
+    }
     for (int i = 0; i < Q; i++) {
         double wc = weight(L, i, w0) / cL2;
         for (int a = 0; a < D; a++)
@@ -347,7 +378,8 @@ static void current_at(const sources_t *src, long s, int t, double j[3]) {
 int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2, const double *mu,
            const double *dlnmu, double *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
            const double *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, double *traces,
-           const int *bc, int layer, double gamma_max) {
+           const int *bc, int layer, double gamma_max, const double *wp2, const double *wr2, const double *gam,
+           double *Jpol, double *Ppol) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     int kind[3] = {0, 0, 0};
@@ -366,8 +398,24 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
         for (long s = 0; s < L.nsite; s++) {
             double j[3];
             current_at(&src, s, t, j);
-            collide_site(&L, cL2[s], w0[s], ceff2[s], mu[s], dlnmu + 3 * s, j, g + s * per, gpost + s * per, E + 3 * s,
-                         B + 3 * s);
+            double pt[3];
+            const double *ppol = NULL;
+            if (wp2) {
+                /* the pole's update from the pre-collision E(t) = D/eps_inf - P(t) (reading R9) */
+                double Lam[MAXD][MAXD], Et[3], Bt[3];
+                site_moments(&L, g + s * per, cL2[s], Lam, Et, Bt);
+                const double gm = gam ? gam[s] : 0.0, om = wr2 ? wr2[s] : 0.0;
+                for (int a = 0; a < 3; a++) {
+                    pt[a] = Ppol[3 * s + a];
+                    const double ea = Et[a] - pt[a];
+                    const double jn = ((1.0 - 0.5 * gm) * Jpol[3 * s + a] + wp2[s] * ea - om * pt[a]) / (1.0 + 0.5 * gm);
+                    Jpol[3 * s + a] = jn;
+                    Ppol[3 * s + a] = pt[a] + jn;
+                }
+                ppol = pt; /* the collision at t uses P(t) */
+            }
+            collide_site(&L, cL2[s], w0[s], ceff2[s], mu[s], dlnmu + 3 * s, j, ppol, g + s * per, gpost + s * per,
+                         E + 3 * s, B + 3 * s);
             /* absorbing layer (reading R8): scale the post-collision populations */
             const long xyz[3] = {s % L.nx, (s / L.nx) % L.ny, s / ((long)L.nx * L.ny)};
             double f = 1.0;
@@ -466,7 +514,7 @@ void or_diagnostics(int D, int nx, int ny, int nz, const double *cL2, const doub
 static void collide_c(const lattice_t *L, double c, double mus, const double dlnmu[3], const double j[3],
                       const double *gin, double *gout) {
     double E[3], B[3];
-    collide_site(L, c, 1.0 - L->D * c, c / (L->D - 1), mus, dlnmu, j, gin, gout, E, B);
+    collide_site(L, c, 1.0 - L->D * c, c / (L->D - 1), mus, dlnmu, j, NULL, gin, gout, E, B);
 }
 
 /*
@@ -503,7 +551,7 @@ double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const doub
         memcpy(states + (long)(n + 1) * per * ns, states + (long)n * per * ns, sizeof(double) * per * ns);
         double *tr_n = malloc(sizeof(double) * (nrec > 0 ? nrec : 1));
         or_run(D, nx, ny, nz, cL2, w0, ceff2, mu, dlnmu, states + (long)(n + 1) * per * ns, t0 + n, 1, nsrc, src_site,
-               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n, NULL, 0, 0.0);
+               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n, NULL, 0, 0.0, NULL, NULL, NULL, NULL, NULL);
         for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = tr_n[r];
         free(tr_n);
     }

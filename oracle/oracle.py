@@ -30,7 +30,9 @@ def _load():
         lib.or_fields.restype = None
         lib.or_fields.argtypes = [I, I, I, I, dp, dp, dp, dp]
         lib.or_run.restype = I
-        lib.or_run.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, ip, I, D_]
+        vp = C.c_void_p
+        lib.or_run.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, ip, I, D_,
+                               vp, vp, vp, vp, vp]
         lib.or_diagnostics.restype = None
         lib.or_diagnostics.argtypes = [I, I, I, I, dp, dp, dp, dp, dp]
         lib.or_adjoint.restype = D_
@@ -62,6 +64,9 @@ class Oracle:
     bc: tuple = (0, 0, 0)  # per axis x, y, z: 0 periodic, 1 PEC wall, 2 PMC wall
     layer: int = 0  # absorbing layer width inside the walls (sites)
     gamma_max: float = 0.0  # damping of the wall-adjacent site
+    wp2: np.ndarray = None  # frequency-dispersive permittivity: one Drude-Lorentz pole per site (grid), or None
+    wr2: np.ndarray = None  # its resonance frequency squared (0: Drude)
+    gamma: np.ndarray = None  # its damping rate
 
     @property
     def dims(self):
@@ -86,11 +91,14 @@ def _f64(a, shape=None):
 PERIODIC, PEC, PMC = 0, 1, 2
 
 
-def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.0) -> Oracle:
+def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.0, dispersion=None) -> Oracle:
     """Medium upload: eps_r, mu_r -> c_eff^2, c_L^2, w0, grad ln mu (Eq. 3).
 
     bc (x, y, z): 0 periodic, 1 PEC wall, 2 PMC wall on both ends of that axis (2D only); layer > 0 adds an
-    absorbing layer of that many sites inside every wall, damping 1 - gamma_max ((L - i)/L)^2 at distance i."""
+    absorbing layer of that many sites inside every wall, damping 1 - gamma_max ((L - i)/L)^2 at distance i.
+    dispersion: dict(wp2=, wr2=, gamma=) (arrays of the grid's shape or scalars; wr2 and gamma default to 0): one
+    Drude-Lorentz pole per site, d_t J + gamma J + wr2 P = wp2 E, J = d_t P; the lattice then carries D/eps_inf
+    and the field is E = D/eps_inf - P (the oracle's reading R9)."""
     lib = _load()
     bc = tuple(int(b) for b in bc) + (0,) * (3 - len(bc))
     assert all(b in (PERIODIC, PEC, PMC) for b in bc) and (D == 2 or not any(bc))
@@ -112,8 +120,19 @@ def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.
     nx, ny, nz = (shape[-1], shape[-2], shape[0] if D == 3 else 1)
     bad = lib.or_medium(D, nx, ny, nz, float(c_ref2), eps_r.ravel(), mu_ptr, np.array(bc, np.int32), *out, dl)
     ceff2, cL2, w0, mu = (o.reshape(shape) for o in out)
-    return Oracle(D, shape, eps_r, ceff2, cL2, w0, mu, dl.reshape(shape + (3,)), int(bad), bc, int(layer),
-                  float(gamma_max))
+    m = Oracle(D, shape, eps_r, ceff2, cL2, w0, mu, dl.reshape(shape + (3,)), int(bad), bc, int(layer),
+               float(gamma_max))
+    if dispersion is not None:
+        full = lambda v: np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), shape))
+        m.wp2 = full(dispersion["wp2"])
+        m.wr2 = full(dispersion.get("wr2", 0.0))
+        m.gamma = full(dispersion.get("gamma", 0.0))
+    return m
+
+
+def pole_state(m: Oracle):
+    """Zero state of the dispersive pole: dict(J=, P=), each grid + (3,) (J at t - 1/2, P at t)."""
+    return dict(J=np.zeros(m.shape + (3,)), P=np.zeros(m.shape + (3,)))
 
 
 def init_state(m: Oracle, E=None, B=None) -> np.ndarray:
@@ -150,13 +169,18 @@ def _receivers(receivers, nsite):
     return site.size, site, comp
 
 
-def run(m: Oracle, g: np.ndarray, nsteps: int, t0: int = 0, sources=None, receivers=None) -> np.ndarray:
+def run(m: Oracle, g: np.ndarray, nsteps: int, t0: int = 0, sources=None, receivers=None, pole=None) -> np.ndarray:
     """Advance g (in place) by nsteps steps of Eqs. 17-18; returns receiver traces [nrec, nsteps].
 
     sources: dict(site=flat indices, comp=0..2, amp=[nsrc, nt] current density j(t)).
     receivers: dict(site=flat indices, comp=0..5 for E_x..E_z, B_x..B_z).
+    pole: the dispersive pole's state (pole_state), advanced in place; required with a dispersive medium.
     """
     lib = _load()
+    assert (m.wp2 is None) == (pole is None)
+    vp = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+    if pole is not None:
+        assert pole["J"].flags.c_contiguous and pole["P"].flags.c_contiguous
     assert g.dtype == np.float64 and g.flags.c_contiguous and g.shape == m.shape + (m.Q, m.D, m.D)
     n = m.cL2.size
     ns, ss, sc, sa, nt = _sources(sources, n)
@@ -164,19 +188,24 @@ def run(m: Oracle, g: np.ndarray, nsteps: int, t0: int = 0, sources=None, receiv
     traces = np.zeros(max(nr, 1) * max(nsteps, 1))
     rc_ = lib.or_run(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(), m.mu.ravel(), m.dlnmu.reshape(-1),
                      g.reshape(-1), int(t0), int(nsteps), ns, ss, sc, sa, nt, nr, rs, rc, traces,
-                     np.array(m.bc, np.int32), m.layer, m.gamma_max)
+                     np.array(m.bc, np.int32), m.layer, m.gamma_max, vp(m.wp2), vp(m.wr2), vp(m.gamma),
+                     vp(None if pole is None else pole["J"]), vp(None if pole is None else pole["P"]))
     assert rc_ == 0
     return traces[: nr * nsteps].reshape(nr, nsteps)
 
 
-def fields(m: Oracle, g: np.ndarray):
-    """E, B (each grid + (3,)) from the moments of a pre-collision state."""
+def fields(m: Oracle, g: np.ndarray, pole=None):
+    """E, B (each grid + (3,)) from the moments of a pre-collision state (with a dispersive pole's state, E is
+    the lattice's D/eps_inf minus P)."""
     lib = _load()
     n = m.cL2.size
     E = np.empty(3 * n)
     B = np.empty(3 * n)
     lib.or_fields(m.D, *m.dims, m.cL2.ravel(), np.ascontiguousarray(g).reshape(-1), E, B)
-    return E.reshape(m.shape + (3,)), B.reshape(m.shape + (3,))
+    E = E.reshape(m.shape + (3,))
+    if pole is not None:
+        E = E - pole["P"]
+    return E, B.reshape(m.shape + (3,))
 
 
 def diagnostics(m: Oracle, g: np.ndarray):
