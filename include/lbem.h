@@ -168,6 +168,28 @@ lbem_status lbem_step(lbem_t *h, int nsteps);
 lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double gamma_max);
 lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double *gamma_max);
 
+/* Frequency-dispersive permittivity (the convolution term of Eq. 3, which the
+ * paper leaves to auxiliary differential equations): one Drude-Lorentz pole per
+ * site, d_t J + gamma J + wr^2 P = wp^2 E with J = d_t P, i.e.
+ * eps(omega) = eps_r (1 + wp^2 / (wr^2 - omega^2 - i gamma omega)) with eps_r of
+ * lbem_set_medium as eps_infinity (lattice units: frequencies per step).  wp2,
+ * wr2, gamma: [nsite] floats, host or device, copied; wr2 and gamma may be NULL
+ * (zero); wp2 = NULL removes the pole.  The lattice's zeroth moment then
+ * carries D/eps_r, E = D/eps_r - P is what lbem_fields, receivers and
+ * lbem_diagnostics report, and P enters the equilibrium's second moment; J at
+ * half steps and P at whole ones are stepped time-centred before each
+ * collision (homogeneous lossless Drude medium: 4 sin^2(omega/2) =
+ * 4 c^2 (sin^2(kx/2) + sin^2(ky/2)) + wp^2).  2D, LBEM_F32 storage
+ * (LBEM_ERR_ARG otherwise), after lbem_set_medium (LBEM_ERR_STATE); validated in
+ * FP64: LBEM_ERR_MEDIUM (nothing changed) unless every parameter is finite and
+ * >= 0 and wp2 + wr2 <= 4 w0 (w0 = 1 - 2 c_L^2, the rest weight: the stability
+ * bound), which lbem_set_medium also checks against a new medium.  A dispersive
+ * handle steps one step per launch with its own kernel (walls and layers
+ * included); lbem_set_fields starts the pole at rest (D = E); lbem_save_state
+ * appends J and P (lbem_info's state_bytes counts them).  Batches and the
+ * adjoint take non-dispersive handles only.  Synchronises the stream. */
+lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, const float *gamma);
+
 /* Watchdog (off by default): with every > 0, lbem_step computes the FP64 field energy (as
  * lbem_diagnostics, synchronising) whenever t reaches a multiple of `every`, and stops with
  * LBEM_ERR_UNSTABLE (t left at the check) if the state is not finite or the energy grew by more than

@@ -822,7 +822,7 @@ cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cuda
 // ------------------------------------------------------------------ field extraction (dense [3][nsite] outputs)
 template <int ST>
 __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float *cL2, float *E, float *B,
-                                                  long long nsite, Walls w) {
+                                                  long long nsite, Walls w, const float *Pz) {
     using C = Codec<ST>;
     const int lane = threadIdx.x & 31;
     const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
@@ -847,7 +847,8 @@ __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float
         if (E) {
             E[sd] = 0.f;
             E[nsite + sd] = 0.f;
-            E[2 * nsite + sd] = -get(cl, j) * s;
+            const float ez = -get(cl, j) * s;
+            E[2 * nsite + sd] = Pz ? __fsub_rn(ez, Pz[sd]) : ez;  // with a dispersive pole E = D/eps_inf - P
         }
         if (B) {
             B[sd] = get(g[4], j) - get(g[2], j);
@@ -863,11 +864,12 @@ cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s
     const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
+    const float *Pz = h->disp ? h->d_P : nullptr;
     switch (h->storage) {
-        case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
-        case LBEM_F16: fields2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
-        case LBEM_BF16: fields2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
-        default: fields2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w); break;
+        case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
+        case LBEM_F16: fields2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
+        case LBEM_BF16: fields2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
+        default: fields2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
     }
     return cudaGetLastError();
 }
@@ -906,7 +908,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 }
 
 template <int ST>
-__global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *cL2, double *partials, Walls w) {
+__global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *cL2, double *partials, Walls w,
+                                                const float *Pz) {
     __shared__ double sh[BLOCK / 32];
     double en = 0.0, inv = 0.0, dv = 0.0;
     const long long nsite = (long long)G.nx * G.ny;
@@ -918,7 +921,7 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
             sum += g[i];
         }
         const double cl = (double)cL2[(long long)y * G.pitch + x];
-        const double Ez = -cl * sum, bx = g[4] - g[2], by = g[1] - g[3];
+        const double Ez = -cl * sum - (Pz ? (double)Pz[s] : 0.0), bx = g[4] - g[2], by = g[1] - g[3];
         en += bx * bx + by * by + Ez * Ez / cl;  // c_eff^2 = c_L^2 in 2D
         const double w0 = 1.0 - 2.0 * cl, wm = 0.5 * cl;
         double q = (g[1] * g[1] + g[2] * g[2] + g[3] * g[3] + g[4] * g[4]) / wm;
@@ -944,11 +947,12 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s) {
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
+    const float *Pz = h->disp ? h->d_P : nullptr;
     switch (h->storage) {
-        case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
-        case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
-        case LBEM_BF16: diag2d<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
-        default: diag2d<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w); break;
+        case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
+        case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
+        case LBEM_BF16: diag2d<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
+        default: diag2d<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
     }
     return cudaGetLastError();
 }

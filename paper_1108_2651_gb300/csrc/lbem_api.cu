@@ -117,7 +117,25 @@ StepArgs step_args(const lbem_t *h, int cur_in) {
     return a;
 }
 
+static Walls handle_walls(const lbem_t *h) {
+    Walls w;
+    w.kind[0] = h->bc[0];
+    w.kind[1] = h->bc[1];
+    w.fx = h->bc[0] ? h->d_fx : nullptr;
+    w.fy = h->bc[1] ? h->d_fy : nullptr;
+    return w;
+}
+
 static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) {
+    if (h->disp) {
+        Pole q;
+        q.wp2 = h->d_wp2;
+        q.wr2 = h->d_wr2;
+        q.gam = h->d_gam;
+        q.J = h->d_J;
+        q.P = h->d_P;
+        return launch_step_2d_disp(a, handle_walls(h), q, h->stream);
+    }
     if (h->dim == 2) return launch_step_2d(a, h->storage, h->has_mu, variant, h->stream);
     return launch_step_3d(a, h->has_mu, variant, h->stream);
 }
@@ -128,7 +146,7 @@ static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16
 // Whether launches of two (three) steps apply: 2D; FP32 storage with any medium, 16-bit storage with uniform mu
 // and nx % 4 == 0; three steps per launch exist for FP32 storage with uniform mu.
 static bool multi_step_base(const lbem_t *h) {
-    return h->dim == 2 && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
+    return h->dim == 2 && !h->disp && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
 }
 static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
 static bool three_step_ok(const lbem_t *h) {
@@ -143,16 +161,12 @@ static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two
 // Enqueue nsteps steps starting from buffer `cur` at time t0: triples (pairs) of steps with the three-step
 // (two-step) kernel when enabled, a remaining pair with the two-step kernel's default tile, single steps
 // otherwise; returns the buffer holding the final state in *cur_out.
-// With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu).
+// With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu); the
+// dispersive kernel applies walls and layers itself.
 static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
-    if (!h->walls()) return cudaSuccess;
-    Walls w;
-    w.kind[0] = h->bc[0];
-    w.kind[1] = h->bc[1];
-    w.fx = h->bc[0] ? h->d_fx : nullptr;
-    w.fy = h->bc[1] ? h->d_fy : nullptr;
-    return launch_edge_2d(a, w, h->d_tiles[k], h->ntiles[k], h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k,
-                          h->stream);
+    if (!h->walls() || h->disp) return cudaSuccess;
+    return launch_edge_2d(a, handle_walls(h), h->d_tiles[k], h->ntiles[k],
+                          h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->stream);
 }
 
 static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {
@@ -315,7 +329,8 @@ void lbem_destroy(lbem_t *h) {
     adjoint_free(h);
     for (void *p : {(void *)h->pool, (void *)h->cL2, (void *)h->mu, (void *)h->dlnmu, (void *)h->d_rowptr,
                     (void *)h->d_ev, (void *)h->d_amp, (void *)h->d_traces, (void *)h->d_partials,
-                    (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage, (void *)h->d_fx, (void *)h->d_fy})
+                    (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage, (void *)h->d_fx, (void *)h->d_fy,
+                    (void *)h->d_wp2, (void *)h->d_wr2, (void *)h->d_gam, (void *)h->d_J, (void *)h->d_P})
         gfree(h, p);
     for (int k = 1; k <= 3; k++) gfree(h, h->d_tiles[k]);
     delete h;
@@ -344,6 +359,7 @@ lbem_status lbem_info(const lbem_t *h, long long *nsite, size_t *state_bytes) {
     if (state_bytes) {
         size_t b = (size_t)h->npop * h->grid.plane * elem_bytes(h->storage);
         if (h->storage == LBEM_I16B) b += (size_t)h->npop * h->buf[0].explane;
+        if (h->disp) b += 2 * sizeof(float) * (size_t)h->nsite;  // the pole's J and P
         *state_bytes = b;
     }
     return LBEM_OK;
@@ -363,6 +379,15 @@ lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
         return fail(LBEM_ERR_MEDIUM, "lbem_set_medium: " + std::to_string(bad) +
                                          " sites with eps_r or mu_r not finite and > 0, or rest weight w0 outside "
                                          "[0,1) (medium faster than c_ref)");
+    if (h->disp) {  // the pole must stay within its stability bound in the new medium
+        LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
+        LBEM_CUDA(launch_disp_check(h, de, dm, h->d_wp2, h->d_wr2, h->d_gam, h->d_counter, h->stream));
+        LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        LBEM_CUDA(cudaStreamSynchronize(h->stream));
+        if (bad)
+            return fail(LBEM_ERR_MEDIUM, "lbem_set_medium: " + std::to_string(bad) +
+                                             " sites where the dispersive pole exceeds wp^2 + wr^2 <= 4 w0");
+    }
     if (dm && !h->mu) {
         LBEM_CUDA(gmalloc(h, (void **)&h->mu, sizeof(float) * h->grid.plane, "mu"));
         LBEM_CUDA(gmalloc(h, (void **)&h->dlnmu, sizeof(float) * h->grid.plane * h->dim, "grad ln mu"));
@@ -411,6 +436,10 @@ lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B) {
     h->t = 0;
     h->wd_last = -1.0;
     if (h->d_traces) LBEM_CUDA(cudaMemsetAsync(h->d_traces, 0, sizeof(float) * (size_t)h->nrec * h->cap, h->stream));
+    if (h->disp) {  // the pole starts at rest: D = E
+        LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * (size_t)h->nsite, h->stream));
+        LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * (size_t)h->nsite, h->stream));
+    }
     drop_graph(h);
     return LBEM_OK;
 }
@@ -620,6 +649,54 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
     return LBEM_OK;
 }
 
+lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, const float *gamma) {
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (!wp2) {  // back to a non-dispersive medium
+        LBEM_CUDA(cudaStreamSynchronize(h->stream));
+        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P}) {
+            gfree(h, *p);
+            *p = nullptr;
+        }
+        h->disp = false;
+        drop_graph(h);
+        return LBEM_OK;
+    }
+    if (h->dim != 2 || h->storage != LBEM_F32)
+        return fail(LBEM_ERR_ARG, "lbem_set_dispersion: 2D grids with LBEM_F32 storage only");
+    if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_set_dispersion: set a medium first");
+    if (h->adj) return fail(LBEM_ERR_STATE, "lbem_set_dispersion: a recorded adjoint run exists (non-dispersive only)");
+    const size_t n = (size_t)h->nsite;
+    const float *dp, *dr, *dg;
+    lbem_status st = device_input(h, wp2, n, 0, &dp);
+    if (st != LBEM_OK) return st;
+    if ((st = device_input(h, wr2, n, n, &dr)) != LBEM_OK) return st;
+    if ((st = device_input(h, gamma, n, 2 * n, &dg)) != LBEM_OK) return st;
+    LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
+    LBEM_CUDA(launch_disp_check(h, nullptr, nullptr, dp, dr, dg, h->d_counter, h->stream));
+    unsigned bad = 0;
+    LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    if (bad)
+        return fail(LBEM_ERR_MEDIUM, "lbem_set_dispersion: " + std::to_string(bad) +
+                                         " sites with a parameter not finite and >= 0, or wp^2 + wr^2 > 4 w0");
+    if (!h->d_wp2) {
+        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P})
+            LBEM_CUDA(gmalloc(h, (void **)p, sizeof(float) * n, "dispersive pole"));
+    }
+    const float *src[3] = {dp, dr, dg};
+    float *dst[3] = {h->d_wp2, h->d_wr2, h->d_gam};
+    for (int k = 0; k < 3; k++) {
+        if (src[k]) LBEM_CUDA(cudaMemcpyAsync(dst[k], src[k], sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream));
+        else LBEM_CUDA(cudaMemsetAsync(dst[k], 0, sizeof(float) * n, h->stream));
+    }
+    LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * n, h->stream));
+    LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * n, h->stream));
+    LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    h->disp = true;
+    drop_graph(h);
+    return LBEM_OK;
+}
+
 lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double *gamma_max) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     for (int a = 0; kind && a < 3; a++) kind[a] = h->bc[a];
@@ -707,6 +784,11 @@ lbem_status lbem_save_state(lbem_t *h, void *dst) {
     const size_t db = (size_t)h->npop * p.plane * elem_bytes(h->storage);
     LBEM_CUDA(cudaMemcpyAsync(dst, p.data, db, cudaMemcpyDefault, h->stream));
     if (p.ex) LBEM_CUDA(cudaMemcpyAsync((char *)dst + db, p.ex, (size_t)h->npop * p.explane, cudaMemcpyDefault, h->stream));
+    if (h->disp) {  // then the pole's J and P
+        const size_t pb = sizeof(float) * (size_t)h->nsite;
+        LBEM_CUDA(cudaMemcpyAsync((char *)dst + db, h->d_J, pb, cudaMemcpyDefault, h->stream));
+        LBEM_CUDA(cudaMemcpyAsync((char *)dst + db + pb, h->d_P, pb, cudaMemcpyDefault, h->stream));
+    }
     if (!is_device_ptr(dst)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
     return LBEM_OK;
 }
@@ -718,6 +800,11 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
     LBEM_CUDA(cudaMemcpyAsync(p.data, src, db, cudaMemcpyDefault, h->stream));
     if (p.ex)
         LBEM_CUDA(cudaMemcpyAsync(p.ex, (const char *)src + db, (size_t)h->npop * p.explane, cudaMemcpyDefault, h->stream));
+    if (h->disp) {
+        const size_t pb = sizeof(float) * (size_t)h->nsite;
+        LBEM_CUDA(cudaMemcpyAsync(h->d_J, (const char *)src + db, pb, cudaMemcpyDefault, h->stream));
+        LBEM_CUDA(cudaMemcpyAsync(h->d_P, (const char *)src + db + pb, pb, cudaMemcpyDefault, h->stream));
+    }
     if (!is_device_ptr(src)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
     h->t = t_at_save;
     drop_graph(h);
@@ -763,6 +850,10 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_autotune: set a medium first");
     if (trial_steps < 1) return fail(LBEM_ERR_ARG, "lbem_autotune: trial_steps >= 1");
+    if (h->disp) {  // a dispersive handle has one kernel
+        if (best) *best = h->variant;
+        return LBEM_OK;
+    }
     const int nv = h->dim == 2 ? nvariants_2d() : nvariants_3d();
     size_t bytes = 0;
     lbem_info(h, nullptr, &bytes);

@@ -303,6 +303,11 @@ struct Walls {
     int kind[2] = {0, 0};
     const float *fx = nullptr, *fy = nullptr;
 };
+// One Drude-Lorentz pole per site (disp.cu): parameters and state, dense [nsite] arrays (J at t - 1/2, P at t).
+struct Pole {
+    const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr;
+    float *J = nullptr, *P = nullptr;
+};
 // Output rectangle of one edge tile: columns x0 .. x0+w-1, rows y0 .. y0+h-1.
 struct EdgeTile {
     int x0, y0, w, h;
@@ -333,7 +338,8 @@ __device__ __forceinline__ float mu_source(float bx, float by, float dlx, float 
 // when `owned`), for the multi-step kernels.  Returns S^: shat0 (the permeability term, 0 for uniform mu)
 // minus mu j_z of the sources at the site.
 __device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
-                                             float g1, float g2, float g3, float g4, float cl, float shat0 = 0.f) {
+                                             float g1, float g2, float g3, float g4, float cl, float shat0 = 0.f,
+                                             float pz = 0.f) {
     float shat = shat0;
     if (!a.evt.rowptr) return shat;
     const int e0 = __ldg(a.evt.rowptr + y), e1 = __ldg(a.evt.rowptr + y + 1);
@@ -348,7 +354,9 @@ __device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, lo
             }
         } else if (owned && t < a.evt.cap) {
             const float s = ((g0 + g1) + (g2 + g3)) + g4;
-            a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+            float v = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+            if (ev.comp == 2) v = __fsub_rn(v, pz);  // with a dispersive pole E = D/eps_inf - P (else pz = +0)
+            a.evt.traces[(long long)ev.index * a.evt.cap + t] = v;
         }
     }
     return shat;
@@ -409,6 +417,9 @@ struct lbem {
     float *d_fx = nullptr, *d_fy = nullptr;
     lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     int ntiles[4] = {0, 0, 0, 0};
+    // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, dense [nsite]
+    float *d_wp2 = nullptr, *d_wr2 = nullptr, *d_gam = nullptr, *d_J = nullptr, *d_P = nullptr;
+    bool disp = false;
     size_t tile_smem[4] = {0, 0, 0, 0}, tile_smem_mu[4] = {0, 0, 0, 0};  // uniform / heterogeneous mu
     bool walls() const { return bc[0] || bc[1] || bc[2]; }
     // adjoint
@@ -477,5 +488,9 @@ size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu);
 cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
                            cudaStream_t s);
 cudaError_t launch_medium_grad_walls(const lbem_t *h, cudaStream_t s);
+// disp.cu: single steps with a dispersive pole (walls and layers applied in the kernel)
+cudaError_t launch_step_2d_disp(const StepArgs &a, const Walls &w, const Pole &q, cudaStream_t s);
+cudaError_t launch_disp_check(const lbem_t *h, const float *eps, const float *mu, const float *wp2, const float *wr2,
+                              const float *gam, unsigned *bad, cudaStream_t s);
 
 }  // namespace lbk

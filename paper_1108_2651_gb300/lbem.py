@@ -52,6 +52,7 @@ _SIGS = {
     "lbem_get_temporal_blocking": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)],
     "lbem_set_watchdog": [_VP, _I, _D],
     "lbem_set_boundaries": [_VP, C.POINTER(_I), _I, _D],
+    "lbem_set_dispersion": [_VP, _VP, _VP, _VP],
     "lbem_get_boundaries": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)],
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
@@ -212,6 +213,12 @@ def lbem_set_boundaries(h, kind, layer=0, gamma_max=0.0):
     """kind: boundary per axis (x, y[, z]): BC_PERIODIC, BC_PEC or BC_PMC."""
     k = (_I * 3)(*(list(kind) + [0] * (3 - len(kind))))
     _check(load().lbem_set_boundaries(h, k, int(layer), float(gamma_max)))
+
+
+def lbem_set_dispersion(h, wp2, wr2=None, gamma=None):
+    """One Drude-Lorentz pole per site ([nsite] arrays, host or device; wp2 None removes it)."""
+    n = lbem_info(h)[0]
+    _check(load().lbem_set_dispersion(h, _ptr(wp2, count=n), _ptr(wr2, count=n), _ptr(gamma, count=n)))
 
 
 def lbem_get_boundaries(h):
@@ -378,6 +385,10 @@ class Solver:
         eps = torch.as_tensor(np.ascontiguousarray(p.eps_r, np.float32).ravel(), device=device)
         mu = None if p.mu_r is None else torch.as_tensor(np.ascontiguousarray(p.mu_r, np.float32).ravel(), device=device)
         lbem_set_medium(self.h, eps, mu)
+        if getattr(p, "wp2", None) is not None:
+            dev = lambda a: None if a is None else torch.as_tensor(
+                np.ascontiguousarray(np.broadcast_to(a, p.shape), np.float32).ravel(), device=device)
+            lbem_set_dispersion(self.h, dev(p.wp2), dev(p.wr2), dev(p.gamma))
         bc = tuple(getattr(p, "bc", (0, 0, 0)))
         if any(bc) or any(lbem_get_boundaries(self.h)[0]):
             lbem_set_boundaries(self.h, bc, getattr(p, "layer", 0), getattr(p, "gamma_max", 0.0))

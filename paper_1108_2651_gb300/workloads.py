@@ -82,6 +82,9 @@ class Problem:
     bc: tuple = (0, 0, 0)  # boundary per axis x, y, z: 0 periodic, 1 PEC wall, 2 PMC wall (2D)
     layer: int = 0  # absorbing layer inside the walls (sites)
     gamma_max: float = 0.0  # its damping at the wall-adjacent site
+    wp2: Optional[np.ndarray] = None  # dispersive pole per site (grid): plasma frequency squared, or None
+    wr2: Optional[np.ndarray] = None  # its resonance frequency squared
+    gamma: Optional[np.ndarray] = None  # its damping rate
 
     @property
     def c_ref2(self):
@@ -171,6 +174,22 @@ def heterogeneous_2d_walls(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec
     p.bc = tuple(bc) + (0,) * (3 - len(bc))
     p.layer = int(layer)
     p.gamma_max = float(gamma_max)
+    return p
+
+
+def heterogeneous_2d_drude(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec_radius=None, wp2=0.5, gamma=0.01,
+                           name=None):
+    """heterogeneous_2d with a lossy Drude cylinder (a plasmonic scatterer): inside the disk of radius n/8 centred
+    n/4 from the source along x, eps_r (eps_infinity) is raised to at least 2.25 and the pole has wp^2 = wp2,
+    damping gamma (wr = 0); zero elsewhere.  At eps_r >= 2.25 the rest weight is >= 0.55, so wp2 <= 2.2 keeps the
+    pole within its stability bound wp^2 <= 4 w0."""
+    p = heterogeneous_2d(n, seed, nsteps, sigma, nrec, rec_radius, name=name or f"het2d_drude_{n}")
+    y, x = np.mgrid[0:n, 0:n]
+    disk = (x - (n // 2 + n // 4)) ** 2 + (y - n // 2) ** 2 <= (n / 8) ** 2
+    p.eps_r = np.where(disk, np.maximum(p.eps_r, 2.25), p.eps_r)
+    p.wp2 = np.where(disk, wp2, 0.0)
+    p.wr2 = np.zeros(p.shape)
+    p.gamma = np.where(disk, gamma, 0.0)
     return p
 
 

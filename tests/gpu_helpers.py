@@ -43,13 +43,18 @@ def f32(a):
 def oracle_run(p, nsteps=None):
     """The same problem on the FP64 oracle; returns (E, B, traces, medium, state)."""
     nsteps = p.nsteps if nsteps is None else nsteps
-    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r), bc=p.bc, layer=p.layer, gamma_max=p.gamma_max)
+    disp = None
+    if p.wp2 is not None:
+        full = lambda a: f32(np.broadcast_to(0.0 if a is None else a, p.shape))
+        disp = dict(wp2=full(p.wp2), wr2=full(p.wr2), gamma=full(p.gamma))
+    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r), bc=p.bc, layer=p.layer, gamma_max=p.gamma_max, dispersion=disp)
     g = O.init_state(m, f32(p.E0), f32(p.B0))
+    pole = O.pole_state(m) if disp is not None else None
     src = p.sources()
     if src is not None:
         src = dict(src, amp=f32(src["amp"]))
-    tr = O.run(m, g, nsteps, sources=src, receivers=p.receivers())
-    E, B = O.fields(m, g)
+    tr = O.run(m, g, nsteps, sources=src, receivers=p.receivers(), pole=pole)
+    E, B = O.fields(m, g, pole)
     return E, B, tr, m, g
 
 
