@@ -40,7 +40,9 @@ BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
 # the kernel that was captured.
 NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 431.689216e6 + 290.764544e6,
                ("het2d_4096", "f16", "tb2-0"): 238.224640e6 + 128.392192e6,
-               ("het2d_4096", "i16b", "tb2-0"): 267.625984e6 + 152.067840e6}
+               ("het2d_4096", "i16b", "tb2-0"): 267.625984e6 + 152.067840e6,
+               # dram__bytes.sum.per_second x gpu__time_duration.sum (5.911738 TB/s x 197.696 us)
+               ("het2d_drude_4096", "f32", "disp"): 5.911738e12 * 197.696e-6}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -103,6 +105,8 @@ def workload(name):
         return W.heterogeneous_2d(1024, seed=1, nsteps=5000)
     if name == "het2d_walls_4096":
         return W.heterogeneous_2d_walls(4096, seed=2, nsteps=5000)
+    if name == "het2d_drude_4096":
+        return W.heterogeneous_2d_drude(4096, seed=2, nsteps=5000)
     if name == "het3d_192":
         return W.heterogeneous_3d(192, seed=4, nsteps=1000)
     raise ValueError(name)
@@ -303,6 +307,17 @@ def other_forms(lbem, torch, p, peak, stream):
                                   "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp,
                                   "variant": v, "lb_steps": 2000, "bc": list(pw.bc), "layer": pw.layer,
                                   "gamma_max": pw.gamma_max}
+    # the same medium with a lossy Drude cylinder (one dispersive pole per site), 2000 single-step launches:
+    # 44 B/site plus the pole's J and P read and written (16) and its three parameters read (12) = 72 B/site
+    pd = W.heterogeneous_2d_drude(p.shape[0], seed=2, nsteps=2000)
+    s = lbem.Solver(pd.shape, stream=stream.cuda_stream)
+    ms, v, spp = _time_run(lbem, torch, s, pd, 2000, stream)
+    s.close()
+    per = ms / 2000
+    gbs = 72 * n / (per * 1e-3) / 1e9
+    out["f32_drude_dispersive"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                                   "frac": gbs / peak, "bytes_per_site_per_launch": 72, "steps_per_launch": spp,
+                                   "lb_steps": 2000, "kernel": "step2d_disp"}
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
     ms, v, _ = _time_run(lbem, torch, s, q, 1000, stream)
@@ -353,6 +368,14 @@ def other_forms(lbem, torch, p, peak, stream):
     return out
 
 
+def _crop_pole(p, crop):
+    """The workload's dispersive pole on a crop of its grid (None without one)."""
+    if p.D != 2 or p.wp2 is None:
+        return None
+    f = lambda a: np.asarray(np.broadcast_to(0.0 if a is None else a, p.shape)[crop], np.float32).astype(np.float64)
+    return dict(wp2=f(p.wp2), wr2=f(p.wr2), gamma=f(p.gamma))
+
+
 def cpu_baseline(p, budget_s=12.0):
     """Time the FP64 oracle (as it stands) on a bounded sample: a 1024^2 crop of the medium centred on the
     source, as many steps as fit in about budget_s seconds of CPU work."""
@@ -362,17 +385,18 @@ def cpu_baseline(p, budget_s=12.0):
     c0 = (p.shape[0] - n) // 2
     crop = tuple(slice(c0, c0 + n) for _ in range(p.D))
     eps = np.asarray(p.eps_r[crop], np.float32).astype(np.float64)
-    m = O.medium(p.D, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max)
+    m = O.medium(p.D, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max, dispersion=_crop_pole(p, crop))
     g = O.init_state(m)
+    pole = O.pole_state(m) if m.wp2 is not None else None
     shape = (n,) * p.D
     src = dict(site=np.array([W.flat_index(shape, (n // 2,) * p.D)]), comp=np.array([2]),
                amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
     t0 = time.perf_counter()
-    O.run(m, g, 10, sources=src)
+    O.run(m, g, 10, sources=src, pole=pole)
     dt10 = time.perf_counter() - t0
     steps = int(max(10, min(p.nsteps - 10, budget_s / max(dt10 / 10, 1e-6))))
     t0 = time.perf_counter()
-    O.run(m, g, steps, t0=10, sources=src)
+    O.run(m, g, steps, t0=10, sources=src, pole=pole)
     dt = time.perf_counter() - t0
     return {"value": n ** p.D * steps / dt / 1e6, "unit": "Mlups", "cores": O.threads(), "kind": "oracle",
             "sample": f"FP64 oracle, {n}^{p.D} crop of the workload's medium, point source, {steps} steps "
@@ -420,13 +444,15 @@ def run_reference(args, rank, world):
     n = min(1024, p.shape[0])
     c0 = (p.shape[0] - n) // 2
     eps = np.asarray(p.eps_r[c0:c0 + n, c0:c0 + n], np.float32).astype(np.float64)
-    m = O.medium(2, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max)
+    crop = (slice(c0, c0 + n), slice(c0, c0 + n))
+    m = O.medium(2, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max, dispersion=_crop_pole(p, crop))
     src = dict(site=np.array([W.flat_index((n, n), (n // 2, n // 2))]), comp=np.array([2]),
                amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
     for k in range(args.warmup + args.steps):
         g = O.init_state(m)
+        pole = O.pole_state(m) if m.wp2 is not None else None
         t0 = time.perf_counter()
-        O.run(m, g, steps_per, sources=src)
+        O.run(m, g, steps_per, sources=src, pole=pole)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
@@ -450,8 +476,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
     ap.add_argument("--workload", default="het2d_4096",
-                    choices=["het2d_4096", "het2d_1024", "het2d_walls_4096", "het3d_192", "batch256",
-                             "adjoint3d_96"])
+                    choices=["het2d_4096", "het2d_1024", "het2d_walls_4096", "het2d_drude_4096", "het3d_192",
+                             "batch256", "adjoint3d_96"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
     ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
     ap.add_argument("--ref-steps", type=int, default=40)
@@ -503,6 +529,10 @@ def main():
     walls = any(p.bc)
     if walls:
         lbem.lbem_set_boundaries(h, p.bc, p.layer, p.gamma_max)
+    disp = p.D == 2 and p.wp2 is not None
+    if disp:
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32).ravel(), device="cuda")
+        lbem.lbem_set_dispersion(h, dev(p.wp2), dev(p.wr2), dev(p.gamma))
     lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
     lbem.lbem_set_receivers(h, p.rec_site, p.rec_comp, nsteps)
     variant = lbem.lbem_get_variant(h)[0]
@@ -558,7 +588,7 @@ def main():
     value = world * nsite * nsteps / (ms_per_step * 1e-3) / 1e6
 
     peak, peak_kind = measured_peak_gbs()
-    bps = BYTES_PER_SITE[args.storage] if p.D == 2 else 172
+    bps = (72 if disp else BYTES_PER_SITE[args.storage]) if p.D == 2 else 172
     achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
     if spp >= 2:
         kern = {2: "step2d_tb2", 3: "step2d_tb3"}[spp] + ("" if args.storage == "f32" else f"h<{args.storage}>")
@@ -566,7 +596,9 @@ def main():
     else:
         kname = (f"step2d<{args.storage}>" if p.D == 2 else "step3d") + f" (variant {variant})"
         kid = variant
-    if walls:
+    if disp:
+        kname, kid = "step2d_disp (one dispersive pole per site, single steps)", "disp"
+    elif walls:
         kname += " + edge2d (walls and layers)"
     traffic = NCU_TRAFFIC.get((args.workload, args.storage, kid)) if args.lb_steps is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -608,7 +640,8 @@ def main():
         cpu = cpu_baseline(p)
     s.close()
     if rank == 0:
-        launches = args.steps * (step_launches * (2 if walls else 1) + 6 + (1 if args.storage == "f16" else 0))
+        launches = args.steps * (step_launches * (2 if walls and not disp else 1) + 6 +
+                                 (1 if args.storage == "f16" else 0))
         line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32-math/{args.storage}-storage",
