@@ -75,6 +75,20 @@
  *      and the collision at t uses P(t).  A uniform medium then has the plane
  *      waves 4 sin^2(omega/2) = 4 c^2 (sin^2(kx/2) + sin^2(ky/2)) + wp^2
  *      (wr = gamma = 0), and stays stable where wp^2 + wr^2 <= 4 w0.
+ *  R10 Anisotropic media (the paper: different weights for particles moving
+ *      along different axes): a uniform in-plane relative permeability
+ *      tensor diag(mu_xx, mu_yy) in 2D, eps_r per site.  The lattice speed of
+ *      axis a is c_a^2 = f_a cbar^2 with cbar^2 = c_ref^2 / (eps_r sqrt(mu_xx
+ *      mu_yy)) (stored as c_L^2), f_x = r, f_y = 1/r, r = sqrt(mu_xx / mu_yy):
+ *      c_x^2 = c_ref^2 / (eps_r mu_yy) is the speed of a wave moving along x.
+ *      Moving particles of axis a carry w = c_a^2/2, so w0 = 1 - sum_a c_a^2;
+ *      Lambda = cbar^2 sum_i g_i gives E (E_z = -cbar^2 sigma); the first
+ *      moments carry H up to a uniform factor, so B_x = s_x (g_4 - g_2), B_y =
+ *      s_y (g_1 - g_3) with s_x = r, s_y = 1/r; the equilibrium has the same
+ *      moments as Eq. 8 with c^2 read per axis.  The source S of Eq. 3 uses
+ *      mu = sqrt(mu_xx mu_yy) (so 1/eps0 = c_ref^2/eps_r).  The update is then
+ *      exactly 2D TM Maxwell with that tensor and a heterogeneous eps_r, and
+ *      r = 1 is the isotropic scheme with mu_r = mu_xx.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -87,6 +101,8 @@ typedef struct {
     int D, Q, nx, ny, nz;
     long nsite;
     int c[MAXQ][3]; /* lattice velocities, unused axes 0 */
+    double fa[3];   /* per-axis lattice speeds c_a^2 = fa[a] c_L^2 (reading R10; 1 when isotropic) */
+    double bs[3];   /* B_b = bs[b] x its first moment (reading R10; 1 when isotropic) */
 } lattice_t;
 
 /* Lattice of Sec. "Lattice BGK formulation": 2D rest particles plus +/- unit
@@ -99,6 +115,7 @@ static void make_lattice(lattice_t *L, int D, int nx, int ny, int nz) {
     L->nz = (D == 3) ? nz : 1;
     L->nsite = (long)L->nx * L->ny * L->nz;
     memset(L->c, 0, sizeof(L->c));
+    for (int a = 0; a < 3; a++) L->fa[a] = L->bs[a] = 1.0;
     for (int a = 0; a < D; a++) {
         L->c[1 + a][a] = +1;
         L->c[1 + D + a][a] = -1;
@@ -152,10 +169,31 @@ static inline double *G(const lattice_t *L, double *g, long s, int i) {
     return g + ((s * L->Q + i) * L->D) * L->D;
 }
 
+/* Anisotropy ratio r = sqrt(mu_xx / mu_yy) of reading R10 (2D; r = 1: isotropic). */
+static void set_axes(lattice_t *L, double r) {
+    if (L->D != 2 || !(r > 0.0) || r == 1.0) return;
+    L->fa[0] = r;
+    L->fa[1] = 1.0 / r;
+    L->bs[0] = r;
+    L->bs[1] = 1.0 / r;
+}
+
+/* axis along which direction i moves (-1 for the rest particle) */
+static int axis_of(const lattice_t *L, int i) {
+    for (int a = 0; a < L->D; a++)
+        if (L->c[i][a]) return a;
+    return -1;
+}
+
 /* Lattice weights (Sec. "Lattice BGK formulation"): moving particles all get
- * w_i = (1 - w0)/(2D); the rest particle gets w0. */
+ * w_i = (1 - w0)/(2D); the rest particle gets w0.  With per-axis speeds
+ * (reading R10) a moving particle of axis a gets (1 - w0) fa[a] / (2 sum_b fa[b])
+ * = c_a^2 / 2. */
 static double weight(const lattice_t *L, int i, double w0) {
-    return (i == 0) ? w0 : (1.0 - w0) / (2.0 * L->D);
+    if (i == 0) return w0;
+    double sum = 0.0;
+    for (int b = 0; b < L->D; b++) sum += L->fa[b];
+    return (1.0 - w0) * L->fa[axis_of(L, i)] / (2.0 * sum);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -172,9 +210,12 @@ static double weight(const lattice_t *L, int i, double w0) {
  * outside [0, 1) or whose inputs are not finite and positive.
  */
 long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r, const double *mu_r, const int *bc,
-               double *ceff2, double *cL2, double *w0, double *mu, double *dlnmu) {
+               double aniso_r, double *ceff2, double *cL2, double *w0, double *mu, double *dlnmu) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
+    set_axes(&L, aniso_r);
+    double fsum = 0.0;
+    for (int a = 0; a < D; a++) fsum += L.fa[a];
     long bad = 0;
     for (long s = 0; s < L.nsite; s++) {
         double e = eps_r[s];
@@ -186,7 +227,7 @@ long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r
         }
         ceff2[s] = c_ref2 / (e * m);
         cL2[s] = (D - 1) * ceff2[s];
-        w0[s] = 1.0 - D * cL2[s];
+        w0[s] = 1.0 - fsum * cL2[s]; /* 1 - D c_L^2, or 1 - sum_a c_a^2 (reading R10) */
         mu[s] = m;
         if (!(w0[s] >= 0.0 && w0[s] < 1.0)) bad++;
     }
@@ -244,23 +285,26 @@ static void site_moments(const lattice_t *L, const double *gs, double cL2, doubl
         if (b < D)
             for (int a = 0; a < D; a++)
                 if (a != b) v += R[a][b][a];
-        B[b] = v;
+        B[b] = L->bs[b] * v;
     }
 }
 
 /* Local equilibrium, Eq. 8:
  *   g^(0)_iab = (w_i / c_L^2) [ Lambda_ab + c_ia Bq_b - c_ib Bq_a ]
- * with Bq = B/(D-1) (reading R2). */
+ * with Bq = B/(D-1) (reading R2).  With per-axis speeds (reading R10) the c^2
+ * of the B term is that of the particle's axis, c_a^2 = fa[a] c_L^2, and Bq is
+ * the first moment B/bs. */
 static void equilibrium(const lattice_t *L, double cL2, double w0, double Lam[MAXD][MAXD], const double B[3],
                         double *geq) {
     const int D = L->D, Q = L->Q;
     double Bq[3];
-    for (int k = 0; k < 3; k++) Bq[k] = B[k] / (D - 1);
+    for (int k = 0; k < 3; k++) Bq[k] = B[k] / (D - 1) / L->bs[k];
     for (int i = 0; i < Q; i++) {
-        double wc = weight(L, i, w0) / cL2;
+        const double w = weight(L, i, w0), ax = i == 0 ? 1.0 : L->fa[axis_of(L, i)];
         for (int a = 0; a < D; a++)
             for (int b = 0; b < D; b++)
-                geq[(i * D + a) * D + b] = wc * (Lam[a][b] + L->c[i][a] * Bq[b] - L->c[i][b] * Bq[a]);
+                geq[(i * D + a) * D + b] =
+                    (w / cL2) * Lam[a][b] + (w / (ax * cL2)) * (L->c[i][a] * Bq[b] - L->c[i][b] * Bq[a]);
     }
 }
 
@@ -268,9 +312,10 @@ static void equilibrium(const lattice_t *L, double cL2, double w0, double Lam[MA
  * Maxwell Equations", conservative form) and B as given.  E, B are
  * [nsite][3]; either may be NULL (zero). */
 void or_init(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *E, const double *B,
-             double *g) {
+             double *g, double aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
+    set_axes(&L, aniso_r);
     for (long s = 0; s < L.nsite; s++) {
         double Lam[MAXD][MAXD], Bs[3] = {0, 0, 0};
         for (int a = 0; a < D; a++)
@@ -287,9 +332,11 @@ void or_init(int D, int nx, int ny, int nz, const double *cL2, const double *w0,
 }
 
 /* E and B ([nsite][3]) of a pre-collision state. */
-void or_fields(int D, int nx, int ny, int nz, const double *cL2, const double *g, double *E, double *B) {
+void or_fields(int D, int nx, int ny, int nz, const double *cL2, const double *g, double *E, double *B,
+               double aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
+    set_axes(&L, aniso_r);
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < L.nsite; s++) {
         double Lam[MAXD][MAXD];
@@ -332,7 +379,10 @@ static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2
             for (int b = 0; b < D; b++) {
                 double dl = 0.0;
                 for (int g = 0; g < 3; g++) dl += levi(g, a, b) * ppol[g];
-                for (int i = 0; i < Q; i++) geq[(i * D + a) * D + b] += (i == 0 ? -(double)D : 0.5) * dl;
+                double fsum = 0.0; /* sum_a c_a^2 / c_L^2: D when isotropic */
+                for (int k = 0; k < D; k++) fsum += L->fa[k];
+                for (int i = 0; i < Q; i++)
+                    geq[(i * D + a) * D + b] += (i == 0 ? -fsum : 0.5 * L->fa[axis_of(L, i)]) * dl;
             }
     }
     for (int i = 0; i < Q; i++) {
@@ -379,9 +429,10 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
            const double *dlnmu, double *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
            const double *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, double *traces,
            const int *bc, int layer, double gamma_max, const double *wp2, const double *wr2, const double *gam,
-           double *Jpol, double *Ppol) {
+           double *Jpol, double *Ppol, double aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
+    set_axes(&L, aniso_r);
     int kind[3] = {0, 0, 0};
     for (int a = 0; bc && a < 3; a++) kind[a] = a < D ? bc[a] : 0;
     if (D == 3 && (kind[0] || kind[1] || kind[2])) return -1;
@@ -466,11 +517,12 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
  * Sums run over sites in order, serially.
  */
 void or_diagnostics(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2,
-                    const double *g, double *out) {
+                    const double *g, double *out, double aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
+    set_axes(&L, aniso_r);
     double *E = malloc(sizeof(double) * 3 * L.nsite), *B = malloc(sizeof(double) * 3 * L.nsite);
-    or_fields(D, nx, ny, nz, cL2, g, E, B);
+    or_fields(D, nx, ny, nz, cL2, g, E, B, aniso_r);
     double en = 0.0, inv = 0.0, dv = 0.0;
     for (long s = 0; s < L.nsite; s++) {
         for (int a = 0; a < 3; a++) en += B[3 * s + a] * B[3 * s + a] + E[3 * s + a] * E[3 * s + a] / ceff2[s];
@@ -551,7 +603,7 @@ double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const doub
         memcpy(states + (long)(n + 1) * per * ns, states + (long)n * per * ns, sizeof(double) * per * ns);
         double *tr_n = malloc(sizeof(double) * (nrec > 0 ? nrec : 1));
         or_run(D, nx, ny, nz, cL2, w0, ceff2, mu, dlnmu, states + (long)(n + 1) * per * ns, t0 + n, 1, nsrc, src_site,
-               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n, NULL, 0, 0.0, NULL, NULL, NULL, NULL, NULL);
+               src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n, NULL, 0, 0.0, NULL, NULL, NULL, NULL, NULL, 1.0);
         for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = tr_n[r];
         free(tr_n);
     }

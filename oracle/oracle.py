@@ -24,17 +24,17 @@ def _load():
         ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
         I, D_ = C.c_int, C.c_double
         lib.or_medium.restype = C.c_long
-        lib.or_medium.argtypes = [I, I, I, I, D_, dp, C.c_void_p, ip, dp, dp, dp, dp, dp]
+        lib.or_medium.argtypes = [I, I, I, I, D_, dp, C.c_void_p, ip, D_, dp, dp, dp, dp, dp]
         lib.or_init.restype = None
-        lib.or_init.argtypes = [I, I, I, I, dp, dp, C.c_void_p, C.c_void_p, dp]
+        lib.or_init.argtypes = [I, I, I, I, dp, dp, C.c_void_p, C.c_void_p, dp, D_]
         lib.or_fields.restype = None
-        lib.or_fields.argtypes = [I, I, I, I, dp, dp, dp, dp]
+        lib.or_fields.argtypes = [I, I, I, I, dp, dp, dp, dp, D_]
         lib.or_run.restype = I
         vp = C.c_void_p
         lib.or_run.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, ip, I, D_,
-                               vp, vp, vp, vp, vp]
+                               vp, vp, vp, vp, vp, D_]
         lib.or_diagnostics.restype = None
-        lib.or_diagnostics.argtypes = [I, I, I, I, dp, dp, dp, dp, dp]
+        lib.or_diagnostics.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, D_]
         lib.or_adjoint.restype = D_
         lib.or_adjoint.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, dp]
         lib.or_threads.restype = I
@@ -67,6 +67,7 @@ class Oracle:
     wp2: np.ndarray = None  # frequency-dispersive permittivity: one Drude-Lorentz pole per site (grid), or None
     wr2: np.ndarray = None  # its resonance frequency squared (0: Drude)
     gamma: np.ndarray = None  # its damping rate
+    aniso_r: float = 1.0  # sqrt(mu_xx / mu_yy) of a uniform in-plane permeability tensor (2D); 1: isotropic
 
     @property
     def dims(self):
@@ -91,14 +92,17 @@ def _f64(a, shape=None):
 PERIODIC, PEC, PMC = 0, 1, 2
 
 
-def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.0, dispersion=None) -> Oracle:
+def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.0, dispersion=None,
+           aniso=None) -> Oracle:
     """Medium upload: eps_r, mu_r -> c_eff^2, c_L^2, w0, grad ln mu (Eq. 3).
 
     bc (x, y, z): 0 periodic, 1 PEC wall, 2 PMC wall on both ends of that axis (2D only); layer > 0 adds an
     absorbing layer of that many sites inside every wall, damping 1 - gamma_max ((L - i)/L)^2 at distance i.
     dispersion: dict(wp2=, wr2=, gamma=) (arrays of the grid's shape or scalars; wr2 and gamma default to 0): one
     Drude-Lorentz pole per site, d_t J + gamma J + wr2 P = wp2 E, J = d_t P; the lattice then carries D/eps_inf
-    and the field is E = D/eps_inf - P (the oracle's reading R9)."""
+    and the field is E = D/eps_inf - P (the oracle's reading R9).
+    aniso: (mu_xx, mu_yy), a uniform in-plane relative permeability tensor (2D, mu_r must be None): per-axis
+    lattice speeds c_x^2 = c_ref^2/(eps_r mu_yy), c_y^2 = c_ref^2/(eps_r mu_xx) (the oracle's reading R10)."""
     lib = _load()
     bc = tuple(int(b) for b in bc) + (0,) * (3 - len(bc))
     assert all(b in (PERIODIC, PEC, PMC) for b in bc) and (D == 2 or not any(bc))
@@ -108,6 +112,12 @@ def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.
     assert len(shape) == D
     if c_ref2 is None:
         c_ref2 = 0.5 if D == 2 else 1.0 / 6.0
+    r = 1.0
+    if aniso is not None:
+        assert D == 2 and mu_r is None
+        mxx, myy = float(aniso[0]), float(aniso[1])
+        r = float(np.sqrt(mxx / myy))
+        mu_r = np.full(shape, np.sqrt(mxx * myy))
     n = eps_r.size
     out = [np.empty(n) for _ in range(4)]
     dl = np.empty(3 * n)
@@ -118,10 +128,14 @@ def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.
         assert mu_r.shape == shape
         mu_ptr = mu_r.ctypes.data_as(C.c_void_p)
     nx, ny, nz = (shape[-1], shape[-2], shape[0] if D == 3 else 1)
-    bad = lib.or_medium(D, nx, ny, nz, float(c_ref2), eps_r.ravel(), mu_ptr, np.array(bc, np.int32), *out, dl)
+    if aniso is not None:
+        mu_r = _f64(mu_r)
+        mu_ptr = mu_r.ctypes.data_as(C.c_void_p)
+    bad = lib.or_medium(D, nx, ny, nz, float(c_ref2), eps_r.ravel(), mu_ptr, np.array(bc, np.int32), r, *out, dl)
     ceff2, cL2, w0, mu = (o.reshape(shape) for o in out)
     m = Oracle(D, shape, eps_r, ceff2, cL2, w0, mu, dl.reshape(shape + (3,)), int(bad), bc, int(layer),
                float(gamma_max))
+    m.aniso_r = r
     if dispersion is not None:
         full = lambda v: np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), shape))
         m.wp2 = full(dispersion["wp2"])
@@ -143,7 +157,7 @@ def init_state(m: Oracle, E=None, B=None) -> np.ndarray:
     Bp = None if B is None else _f64(B, m.shape + (3,))
     lib.or_init(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(),
                 None if Ep is None else Ep.ctypes.data_as(C.c_void_p),
-                None if Bp is None else Bp.ctypes.data_as(C.c_void_p), g.reshape(-1))
+                None if Bp is None else Bp.ctypes.data_as(C.c_void_p), g.reshape(-1), m.aniso_r)
     return g
 
 
@@ -189,7 +203,7 @@ def run(m: Oracle, g: np.ndarray, nsteps: int, t0: int = 0, sources=None, receiv
     rc_ = lib.or_run(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(), m.mu.ravel(), m.dlnmu.reshape(-1),
                      g.reshape(-1), int(t0), int(nsteps), ns, ss, sc, sa, nt, nr, rs, rc, traces,
                      np.array(m.bc, np.int32), m.layer, m.gamma_max, vp(m.wp2), vp(m.wr2), vp(m.gamma),
-                     vp(None if pole is None else pole["J"]), vp(None if pole is None else pole["P"]))
+                     vp(None if pole is None else pole["J"]), vp(None if pole is None else pole["P"]), m.aniso_r)
     assert rc_ == 0
     return traces[: nr * nsteps].reshape(nr, nsteps)
 
@@ -201,7 +215,7 @@ def fields(m: Oracle, g: np.ndarray, pole=None):
     n = m.cL2.size
     E = np.empty(3 * n)
     B = np.empty(3 * n)
-    lib.or_fields(m.D, *m.dims, m.cL2.ravel(), np.ascontiguousarray(g).reshape(-1), E, B)
+    lib.or_fields(m.D, *m.dims, m.cL2.ravel(), np.ascontiguousarray(g).reshape(-1), E, B, m.aniso_r)
     E = E.reshape(m.shape + (3,))
     if pole is not None:
         E = E - pole["P"]
@@ -213,14 +227,14 @@ def diagnostics(m: Oracle, g: np.ndarray):
     lib = _load()
     out = np.zeros(3)
     lib.or_diagnostics(m.D, *m.dims, m.cL2.ravel(), m.w0.ravel(), m.ceff2.ravel(),
-                       np.ascontiguousarray(g).reshape(-1), out)
+                       np.ascontiguousarray(g).reshape(-1), out, m.aniso_r)
     return float(out[0]), float(out[1]), float(out[2])
 
 
 def adjoint(m: Oracle, g0: np.ndarray, nsteps: int, sources, receivers, obs, t0: int = 0):
     """Misfit 1/2 sum (trace - obs)^2 and its gradient with respect to eps_r (grid shape); periodic only."""
     lib = _load()
-    assert not any(m.bc)
+    assert not any(m.bc) and m.aniso_r == 1.0 and m.wp2 is None
     n = m.cL2.size
     ns, ss, sc, sa, nt = _sources(sources, n)
     nr, rs, rc = _receivers(receivers, n)
