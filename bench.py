@@ -107,6 +107,8 @@ def workload(name):
         return W.heterogeneous_2d_walls(4096, seed=2, nsteps=5000)
     if name == "het2d_drude_4096":
         return W.heterogeneous_2d_drude(4096, seed=2, nsteps=5000)
+    if name == "het2d_aniso_4096":
+        return W.heterogeneous_2d_aniso(4096, seed=2, nsteps=5000)
     if name == "het3d_192":
         return W.heterogeneous_3d(192, seed=4, nsteps=1000)
     raise ValueError(name)
@@ -317,7 +319,18 @@ def other_forms(lbem, torch, p, peak, stream):
     gbs = 72 * n / (per * 1e-3) / 1e9
     out["f32_drude_dispersive"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                                    "frac": gbs / peak, "bytes_per_site_per_launch": 72, "steps_per_launch": spp,
-                                   "lb_steps": 2000, "kernel": "step2d_disp"}
+                                   "lb_steps": 2000, "kernel": "step2d_gen"}
+    # the same medium made uniaxial, mu = diag(2, 1) (per-axis lattice weights), 2000 single-step launches of the
+    # general kernel: 44 B/site
+    pa = W.heterogeneous_2d_aniso(p.shape[0], seed=2, nsteps=2000)
+    s = lbem.Solver(pa.shape, stream=stream.cuda_stream)
+    ms, v, spp = _time_run(lbem, torch, s, pa, 2000, stream)
+    s.close()
+    per = ms / 2000
+    gbs = 44 * n / (per * 1e-3) / 1e9
+    out["f32_anisotropic"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                              "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp,
+                              "lb_steps": 2000, "kernel": "step2d_gen", "mu_tensor": list(pa.aniso)}
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
     ms, v, _ = _time_run(lbem, torch, s, q, 1000, stream)
@@ -385,7 +398,8 @@ def cpu_baseline(p, budget_s=12.0):
     c0 = (p.shape[0] - n) // 2
     crop = tuple(slice(c0, c0 + n) for _ in range(p.D))
     eps = np.asarray(p.eps_r[crop], np.float32).astype(np.float64)
-    m = O.medium(p.D, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max, dispersion=_crop_pole(p, crop))
+    m = O.medium(p.D, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max, dispersion=_crop_pole(p, crop),
+                 aniso=p.aniso)
     g = O.init_state(m)
     pole = O.pole_state(m) if m.wp2 is not None else None
     shape = (n,) * p.D
@@ -445,7 +459,8 @@ def run_reference(args, rank, world):
     c0 = (p.shape[0] - n) // 2
     eps = np.asarray(p.eps_r[c0:c0 + n, c0:c0 + n], np.float32).astype(np.float64)
     crop = (slice(c0, c0 + n), slice(c0, c0 + n))
-    m = O.medium(2, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max, dispersion=_crop_pole(p, crop))
+    m = O.medium(2, eps, bc=p.bc, layer=min(p.layer, n // 2), gamma_max=p.gamma_max, dispersion=_crop_pole(p, crop),
+                 aniso=p.aniso)
     src = dict(site=np.array([W.flat_index((n, n), (n // 2, n // 2))]), comp=np.array([2]),
                amp=np.asarray(p.src_amp, np.float32).astype(np.float64))
     for k in range(args.warmup + args.steps):
@@ -476,8 +491,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
     ap.add_argument("--workload", default="het2d_4096",
-                    choices=["het2d_4096", "het2d_1024", "het2d_walls_4096", "het2d_drude_4096", "het3d_192",
-                             "batch256", "adjoint3d_96"])
+                    choices=["het2d_4096", "het2d_1024", "het2d_walls_4096", "het2d_drude_4096",
+                             "het2d_aniso_4096", "het3d_192", "batch256", "adjoint3d_96"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
     ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
     ap.add_argument("--ref-steps", type=int, default=40)
@@ -525,7 +540,15 @@ def main():
         s = lbem.Solver(p.shape, storage=args.storage, stream=stream.cuda_stream)
     h = s.h
     state_mb = lbem.lbem_info(h)[1] / 1e6
-    lbem.lbem_set_medium(h, eps_d)
+    aniso = p.D == 2 and p.aniso is not None
+
+    def upload_medium(eps):
+        if aniso:
+            lbem.lbem_set_medium_aniso(h, eps, *p.aniso)
+        else:
+            lbem.lbem_set_medium(h, eps)
+
+    upload_medium(eps_d)
     walls = any(p.bc)
     if walls:
         lbem.lbem_set_boundaries(h, p.bc, p.layer, p.gamma_max)
@@ -553,7 +576,7 @@ def main():
     tr_d = torch.empty(p.rec_site.size * nsteps, dtype=torch.float32, device="cuda")
 
     def one_pass(ev=None):
-        lbem.lbem_set_medium(h, eps_d)
+        upload_medium(eps_d)
         lbem.lbem_set_fields(h)
         if ev is not None:
             ev[0].record(stream)
@@ -597,7 +620,9 @@ def main():
         kname = (f"step2d<{args.storage}>" if p.D == 2 else "step3d") + f" (variant {variant})"
         kid = variant
     if disp:
-        kname, kid = "step2d_disp (one dispersive pole per site, single steps)", "disp"
+        kname, kid = "step2d_gen (one dispersive pole per site, single steps)", "disp"
+    elif aniso:
+        kname, kid = "step2d_gen (anisotropic medium, single steps)", "gen"
     elif walls:
         kname += " + edge2d (walls and layers)"
     traffic = NCU_TRAFFIC.get((args.workload, args.storage, kid)) if args.lb_steps is None else None
@@ -618,7 +643,7 @@ def main():
         t0 = time.perf_counter()
         reps = max(1, min(args.steps, 2))
         for _ in range(reps):
-            lbem.lbem_set_medium(h, eps_h)
+            upload_medium(eps_h)
             lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
             lbem.lbem_set_fields(h)
             lbem.lbem_step(h, nsteps)

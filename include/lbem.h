@@ -115,6 +115,22 @@ lbem_status lbem_info(const lbem_t *h, long long *nsite, size_t *state_bytes);
  * [0, 1).  Synchronises the stream (to read the validation count). */
 lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r);
 
+/* Anisotropic medium (the paper: different weights for particles moving along
+ * different axes): eps_r per site ([nsite] floats, host or device) and a
+ * uniform in-plane relative permeability tensor diag(mu_xx, mu_yy), 2D TM.  The
+ * lattice speed of axis x is c_x^2 = c_ref2 / (eps_r mu_yy) (a wave moving
+ * along x), of axis y c_y^2 = c_ref2 / (eps_r mu_xx); moving particles of an
+ * axis weigh c_a^2 / 2, w0 = 1 - c_x^2 - c_y^2 must lie in [0, 1)
+ * (LBEM_ERR_MEDIUM otherwise, previous medium kept).  Fields: E_z =
+ * -cbar^2 sigma with cbar^2 = sqrt(c_x^2 c_y^2), B_x = r (g_4 - g_2), B_y =
+ * (g_1 - g_3) / r, r = sqrt(mu_xx / mu_yy); a current j_z enters with
+ * mu = sqrt(mu_xx mu_yy).  mu_xx = mu_yy = mu is the isotropic scheme with a
+ * uniform mu.  2D, LBEM_F32 storage (LBEM_ERR_ARG otherwise); the handle then
+ * steps one step per launch with the general kernel (walls, layers and a
+ * dispersive pole included); lbem_set_medium makes it isotropic again.  Batches
+ * and the adjoint take isotropic handles only.  Synchronises the stream. */
+lbem_status lbem_set_medium_aniso(lbem_t *h, const float *eps_r, double mu_xx, double mu_yy);
+
 /* Initial fields (Eq. 8): sets g = g^(0)(E, B) at every site and t = 0, and
  * clears recorded traces.  E and B are [3][nsite] floats (host or device), or
  * NULL for zero.  In 2D only E_z, B_x and B_y are representable; the other
@@ -182,10 +198,10 @@ lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double
  * 4 c^2 (sin^2(kx/2) + sin^2(ky/2)) + wp^2).  2D, LBEM_F32 storage
  * (LBEM_ERR_ARG otherwise), after lbem_set_medium (LBEM_ERR_STATE); validated in
  * FP64: LBEM_ERR_MEDIUM (nothing changed) unless every parameter is finite and
- * >= 0 and wp2 + wr2 <= 4 w0 (w0 = 1 - 2 c_L^2, the rest weight: the stability
+ * >= 0 and wp2 + wr2 <= 4 w0 (w0 the rest weight, 1 - 2 c_L^2 or 1 - c_x^2 - c_y^2: the stability
  * bound), which lbem_set_medium also checks against a new medium.  A dispersive
- * handle steps one step per launch with its own kernel (walls and layers
- * included); lbem_set_fields starts the pole at rest (D = E); lbem_save_state
+ * handle steps one step per launch with the general kernel (walls, layers and
+ * an anisotropic medium included); lbem_set_fields starts the pole at rest (D = E); lbem_save_state
  * appends J and P (lbem_info's state_bytes counts them).  Batches and the
  * adjoint take non-dispersive handles only.  Synchronises the stream. */
 lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, const float *gamma);

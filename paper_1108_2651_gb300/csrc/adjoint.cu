@@ -489,7 +489,8 @@ lbem_status lbem_forward_record(lbem_t *h, int nsteps, int every) {
     if (h->storage != LBEM_F32) return fail(LBEM_ERR_STATE, "lbem_forward_record: the adjoint needs LBEM_F32 storage");
     if (h->has_mu) return fail(LBEM_ERR_STATE, "lbem_forward_record: the adjoint supports uniform mu only (mu_r = NULL)");
     if (h->walls()) return fail(LBEM_ERR_STATE, "lbem_forward_record: the adjoint supports periodic boundaries only");
-    if (h->disp) return fail(LBEM_ERR_STATE, "lbem_forward_record: the adjoint supports non-dispersive media only");
+    if (h->disp || h->aniso)
+        return fail(LBEM_ERR_STATE, "lbem_forward_record: the adjoint supports non-dispersive isotropic media only");
     adjoint_free(h);
     AdjointState *A = new AdjointState();
     h->adj = A;

@@ -507,7 +507,7 @@ static lbem_status check_members(lbem_batch_t *b) {
     const long long t = b->members[0]->t;
     for (lbem_t *h : b->members) {
         if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_batch_step: every member needs a medium");
-        if (h->has_mu || h->walls() || h->disp)
+        if (h->has_mu || h->walls() || h->general())
             return fail(LBEM_ERR_STATE,
                         "lbem_batch_step: members need uniform mu, periodic boundaries and no dispersive pole");
         if (h->t != t) return fail(LBEM_ERR_STATE, "lbem_batch_step: members are at different times");
@@ -527,7 +527,7 @@ lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_
     for (int k = 0; k < n; k++) {
         const lbem_t *h = members[k];
         if (!h) return fail(LBEM_ERR_ARG, "lbem_batch_create: null member");
-        if (h->dim != 2 || h->storage != LBEM_F32 || h->has_mu || h->walls() || h->disp)
+        if (h->dim != 2 || h->storage != LBEM_F32 || h->has_mu || h->walls() || h->general())
             return fail(LBEM_ERR_ARG,
                         "lbem_batch_create: members must be 2D, LBEM_F32 storage, uniform mu, periodic boundaries");
         for (int j = 0; j < k; j++)

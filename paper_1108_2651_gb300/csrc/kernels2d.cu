@@ -758,9 +758,11 @@ __device__ __forceinline__ float wall_sign(int kind) { return kind == 1 ? -1.f :
 
 // ------------------------------------------------------------------ initial state: buf_i(x) = g^(0)_i(x + c_i)
 // (with walls, where x + c_i lies beyond a wall, buf_i(x) is what site x pulls back: s g^(0)_opp(i)(x))
+// (anisotropic medium, ratio r = c_x / c_y: moving particles of axis x get (r/2)(Lambda + c_x B_y), of axis y
+// (1/(2r))(Lambda - c_y B_x), the rest one (w0/c^2) Lambda with w0 = 1 - c^2 (r + 1/r))
 template <int ST>
 __global__ void __launch_bounds__(BLOCK) init2d(Grid G, PopBuf out, const float *cL2, const float *E, const float *B,
-                                                long long nsite, Walls w) {
+                                                long long nsite, Walls w, float r) {
     using C = Codec<ST>;
     const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
     const int row = (int)(tid / G.nchunk_pad);
@@ -790,7 +792,9 @@ __global__ void __launch_bounds__(BLOCK) init2d(Grid G, PopBuf out, const float 
             const float Lam = E ? -E[2 * nsite + sd] : 0.f;
             const float bx = B ? B[sd] : 0.f, by = B ? B[nsite + sd] : 0.f;
             // Eq. 8: g^(0)_i = (w_i / c_L^2) [Lambda + c_ix B_y - c_iy B_x]
-            const float wc = (ie == 0) ? (1.f - 2.f * cl) / cl : 0.5f;
+            float wc;
+            if (r == 1.f) wc = (ie == 0) ? (1.f - 2.f * cl) / cl : 0.5f;
+            else wc = (ie == 0) ? (1.f - (r + 1.f / r) * cl) / cl : (cx[ie] ? 0.5f * r : 0.5f / r);
             set(v, j, sg * (wc * (Lam + cx[ie] * by - cy[ie] * bx)));
         }
         C::store4(out, i, row, c, v);
@@ -810,11 +814,12 @@ cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cuda
     const unsigned blocks = (unsigned)((n + BLOCK - 1) / BLOCK);
     const PopBuf &o = h->buf[h->cur];
     const Walls w = handle_walls(h);
+    const float r = h->aniso_r;
     switch (h->storage) {
-        case LBEM_F32: init2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
-        case LBEM_F16: init2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
-        case LBEM_BF16: init2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
-        default: init2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w); break;
+        case LBEM_F32: init2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w, r); break;
+        case LBEM_F16: init2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w, r); break;
+        case LBEM_BF16: init2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w, r); break;
+        default: init2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, o, h->cL2, E, B, h->nsite, w, r); break;
     }
     return cudaGetLastError();
 }
@@ -822,7 +827,7 @@ cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cuda
 // ------------------------------------------------------------------ field extraction (dense [3][nsite] outputs)
 template <int ST>
 __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float *cL2, float *E, float *B,
-                                                  long long nsite, Walls w, const float *Pz) {
+                                                  long long nsite, Walls w, const float *Pz, float r) {
     using C = Codec<ST>;
     const int lane = threadIdx.x & 31;
     const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
@@ -850,9 +855,10 @@ __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float
             const float ez = -get(cl, j) * s;
             E[2 * nsite + sd] = Pz ? __fsub_rn(ez, Pz[sd]) : ez;  // with a dispersive pole E = D/eps_inf - P
         }
-        if (B) {
-            B[sd] = get(g[4], j) - get(g[2], j);
-            B[nsite + sd] = get(g[1], j) - get(g[3], j);
+        if (B) {  // anisotropic medium: B_x = r (g_4 - g_2), B_y = (g_1 - g_3) / r
+            const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
+            B[sd] = r == 1.f ? bx : __fmul_rn(r, bx);
+            B[nsite + sd] = r == 1.f ? by : __fmul_rn(__fdiv_rn(1.f, r), by);
             B[2 * nsite + sd] = 0.f;
         }
     }
@@ -865,11 +871,12 @@ cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
     const float *Pz = h->disp ? h->d_P : nullptr;
+    const float r = h->aniso_r;
     switch (h->storage) {
-        case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
-        case LBEM_F16: fields2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
-        case LBEM_BF16: fields2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
-        default: fields2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz); break;
+        case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz, r); break;
+        case LBEM_F16: fields2d<LBEM_F16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz, r); break;
+        case LBEM_BF16: fields2d<LBEM_BF16><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz, r); break;
+        default: fields2d<LBEM_I16B><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz, r); break;
     }
     return cudaGetLastError();
 }
@@ -909,7 +916,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 template <int ST>
 __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *cL2, double *partials, Walls w,
-                                                const float *Pz) {
+                                                const float *Pz, float r) {
     __shared__ double sh[BLOCK / 32];
     double en = 0.0, inv = 0.0, dv = 0.0;
     const long long nsite = (long long)G.nx * G.ny;
@@ -921,10 +928,12 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
             sum += g[i];
         }
         const double cl = (double)cL2[(long long)y * G.pitch + x];
-        const double Ez = -cl * sum - (Pz ? (double)Pz[s] : 0.0), bx = g[4] - g[2], by = g[1] - g[3];
+        const double rd = r, Ez = -cl * sum - (Pz ? (double)Pz[s] : 0.0), bx = rd * (g[4] - g[2]),
+                     by = (g[1] - g[3]) / rd;
         en += bx * bx + by * by + Ez * Ez / cl;  // c_eff^2 = c_L^2 in 2D
-        const double w0 = 1.0 - 2.0 * cl, wm = 0.5 * cl;
-        double q = (g[1] * g[1] + g[2] * g[2] + g[3] * g[3] + g[4] * g[4]) / wm;
+        // weights: c_x^2 / 2 = r c_L^2 / 2 for x-movers, c_L^2 / (2 r) for y-movers (r = 1: isotropic)
+        const double w0 = 1.0 - (rd + 1.0 / rd) * cl, wx = 0.5 * rd * cl, wy = 0.5 * cl / rd;
+        double q = (g[1] * g[1] + g[3] * g[3]) / wx + (g[2] * g[2] + g[4] * g[4]) / wy;
         if (w0 != 0.0) q += g[0] * g[0] / w0;
         inv += 2.0 * q;  // g_xy and g_yx = -g_xy both count
         double bxp, byp, bxm, bym, t1, t2;
@@ -948,11 +957,12 @@ cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaS
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
     const float *Pz = h->disp ? h->d_P : nullptr;
+    const float r = h->aniso_r;
     switch (h->storage) {
-        case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
-        case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
-        case LBEM_BF16: diag2d<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
-        default: diag2d<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz); break;
+        case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;
+        case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;
+        case LBEM_BF16: diag2d<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;
+        default: diag2d<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;
     }
     return cudaGetLastError();
 }

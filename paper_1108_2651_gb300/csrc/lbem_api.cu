@@ -127,14 +127,18 @@ static Walls handle_walls(const lbem_t *h) {
 }
 
 static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) {
-    if (h->disp) {
-        Pole q;
-        q.wp2 = h->d_wp2;
-        q.wr2 = h->d_wr2;
-        q.gam = h->d_gam;
-        q.J = h->d_J;
-        q.P = h->d_P;
-        return launch_step_2d_disp(a, handle_walls(h), q, h->stream);
+    if (h->general()) {
+        General q;
+        if (h->disp) {
+            q.wp2 = h->d_wp2;
+            q.wr2 = h->d_wr2;
+            q.gam = h->d_gam;
+            q.J = h->d_J;
+            q.P = h->d_P;
+        }
+        q.r = h->aniso_r;
+        q.mubar = h->aniso_mu;
+        return launch_step_2d_gen(a, handle_walls(h), q, h->stream);
     }
     if (h->dim == 2) return launch_step_2d(a, h->storage, h->has_mu, variant, h->stream);
     return launch_step_3d(a, h->has_mu, variant, h->stream);
@@ -146,7 +150,7 @@ static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16
 // Whether launches of two (three) steps apply: 2D; FP32 storage with any medium, 16-bit storage with uniform mu
 // and nx % 4 == 0; three steps per launch exist for FP32 storage with uniform mu.
 static bool multi_step_base(const lbem_t *h) {
-    return h->dim == 2 && !h->disp && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
+    return h->dim == 2 && !h->general() && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
 }
 static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
 static bool three_step_ok(const lbem_t *h) {
@@ -162,9 +166,9 @@ static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two
 // (two-step) kernel when enabled, a remaining pair with the two-step kernel's default tile, single steps
 // otherwise; returns the buffer holding the final state in *cur_out.
 // With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu); the
-// dispersive kernel applies walls and layers itself.
+// general kernel applies walls and layers itself.
 static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
-    if (!h->walls() || h->disp) return cudaSuccess;
+    if (!h->walls() || h->general()) return cudaSuccess;
     return launch_edge_2d(a, handle_walls(h), h->d_tiles[k], h->ntiles[k],
                           h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->stream);
 }
@@ -365,27 +369,32 @@ lbem_status lbem_info(const lbem_t *h, long long *nsite, size_t *state_bytes) {
     return LBEM_OK;
 }
 
-lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
-    if (!h || !eps_r) return fail(LBEM_ERR_ARG, "lbem_set_medium: null argument");
+// Medium upload shared by lbem_set_medium (isotropic, mu_r per site or NULL) and lbem_set_medium_aniso (a
+// uniform in-plane tensor diag(mu_xx, mu_yy), mu_r NULL): validate everything first, then write.
+static lbem_status set_medium(lbem_t *h, const float *eps_r, const float *mu_r, bool aniso, double mu_xx,
+                              double mu_yy, const char *who) {
+    const std::string name(who);
     const float *de, *dm;
     lbem_status st = device_input(h, eps_r, h->nsite, 0, &de);
     if (st != LBEM_OK) return st;
     if ((st = device_input(h, mu_r, h->nsite, h->nsite, &dm)) != LBEM_OK) return st;
-    LBEM_CUDA(launch_medium(h, de, dm, h->d_counter, h->stream));
+    const double r = aniso ? sqrt(mu_xx / mu_yy) : 1.0, mubar = aniso ? sqrt(mu_xx * mu_yy) : 1.0;
+    const double fsum = aniso ? (double)((float)r + 1.f / (float)r) : (double)h->dim;
+    LBEM_CUDA(launch_medium(h, de, dm, fsum, mubar, h->d_counter, h->stream));
     unsigned bad = 0;
     LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     if (bad)
-        return fail(LBEM_ERR_MEDIUM, "lbem_set_medium: " + std::to_string(bad) +
+        return fail(LBEM_ERR_MEDIUM, name + ": " + std::to_string(bad) +
                                          " sites with eps_r or mu_r not finite and > 0, or rest weight w0 outside "
                                          "[0,1) (medium faster than c_ref)");
     if (h->disp) {  // the pole must stay within its stability bound in the new medium
         LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
-        LBEM_CUDA(launch_disp_check(h, de, dm, h->d_wp2, h->d_wr2, h->d_gam, h->d_counter, h->stream));
+        LBEM_CUDA(launch_disp_check(h, de, dm, fsum, mubar, h->d_wp2, h->d_wr2, h->d_gam, h->d_counter, h->stream));
         LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
         LBEM_CUDA(cudaStreamSynchronize(h->stream));
         if (bad)
-            return fail(LBEM_ERR_MEDIUM, "lbem_set_medium: " + std::to_string(bad) +
+            return fail(LBEM_ERR_MEDIUM, name + ": " + std::to_string(bad) +
                                              " sites where the dispersive pole exceeds wp^2 + wr^2 <= 4 w0");
     }
     if (dm && !h->mu) {
@@ -394,12 +403,30 @@ lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
         LBEM_CUDA(cudaMemsetAsync(h->mu, 0, sizeof(float) * h->grid.plane, h->stream));
         LBEM_CUDA(cudaMemsetAsync(h->dlnmu, 0, sizeof(float) * h->grid.plane * h->dim, h->stream));
     }
-    LBEM_CUDA(launch_medium_write(h, de, dm, h->stream));
+    LBEM_CUDA(launch_medium_write(h, de, dm, mubar, h->stream));
     if (dm && h->walls()) LBEM_CUDA(launch_medium_grad_walls(h, h->stream));
     h->has_mu = dm != nullptr;
+    h->aniso = aniso;
+    h->aniso_r = (float)r;
+    h->aniso_mu = (float)mubar;
     h->has_medium = true;
     drop_graph(h);
     return LBEM_OK;
+}
+
+lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r) {
+    if (!h || !eps_r) return fail(LBEM_ERR_ARG, "lbem_set_medium: null argument");
+    return set_medium(h, eps_r, mu_r, false, 1.0, 1.0, "lbem_set_medium");
+}
+
+lbem_status lbem_set_medium_aniso(lbem_t *h, const float *eps_r, double mu_xx, double mu_yy) {
+    if (!h || !eps_r) return fail(LBEM_ERR_ARG, "lbem_set_medium_aniso: null argument");
+    if (h->dim != 2 || h->storage != LBEM_F32)
+        return fail(LBEM_ERR_ARG, "lbem_set_medium_aniso: 2D grids with LBEM_F32 storage only");
+    if (!(mu_xx > 0.0 && mu_yy > 0.0 && isfinite(mu_xx) && isfinite(mu_yy)))
+        return fail(LBEM_ERR_ARG, "lbem_set_medium_aniso: mu_xx and mu_yy must be finite and > 0");
+    if (h->adj) return fail(LBEM_ERR_STATE, "lbem_set_medium_aniso: a recorded adjoint run exists (isotropic only)");
+    return set_medium(h, eps_r, nullptr, true, mu_xx, mu_yy, "lbem_set_medium_aniso");
 }
 
 lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B) {
@@ -672,7 +699,7 @@ lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, c
     if ((st = device_input(h, wr2, n, n, &dr)) != LBEM_OK) return st;
     if ((st = device_input(h, gamma, n, 2 * n, &dg)) != LBEM_OK) return st;
     LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
-    LBEM_CUDA(launch_disp_check(h, nullptr, nullptr, dp, dr, dg, h->d_counter, h->stream));
+    LBEM_CUDA(launch_disp_check(h, nullptr, nullptr, h->aniso_fsum(), 1.0, dp, dr, dg, h->d_counter, h->stream));
     unsigned bad = 0;
     LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
@@ -850,7 +877,7 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (!h->has_medium) return fail(LBEM_ERR_STATE, "lbem_autotune: set a medium first");
     if (trial_steps < 1) return fail(LBEM_ERR_ARG, "lbem_autotune: trial_steps >= 1");
-    if (h->disp) {  // a dispersive handle has one kernel
+    if (h->general()) {  // a dispersive or anisotropic handle has one kernel
         if (best) *best = h->variant;
         return LBEM_OK;
     }

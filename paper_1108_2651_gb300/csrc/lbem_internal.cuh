@@ -303,10 +303,13 @@ struct Walls {
     int kind[2] = {0, 0};
     const float *fx = nullptr, *fy = nullptr;
 };
-// One Drude-Lorentz pole per site (disp.cu): parameters and state, dense [nsite] arrays (J at t - 1/2, P at t).
-struct Pole {
+// What the general single-step kernel (general.cu) adds to a step: one Drude-Lorentz pole per site (dense [nsite]
+// parameters and state, J at t - 1/2, P at t; wp2 null: no pole) and a uniform in-plane permeability tensor
+// (axis speeds c_x^2 = r cbar^2, c_y^2 = cbar^2 / r with cbar^2 the stored c_L^2; mubar = sqrt(mu_xx mu_yy)).
+struct General {
     const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr;
     float *J = nullptr, *P = nullptr;
+    float r = 1.f, mubar = 1.f;
 };
 // Output rectangle of one edge tile: columns x0 .. x0+w-1, rows y0 .. y0+h-1.
 struct EdgeTile {
@@ -337,9 +340,11 @@ __device__ __forceinline__ float mu_source(float bx, float by, float dlx, float 
 // Source current at global site (x, y) and time t, and the receiver write of the pre-collision fields (only
 // when `owned`), for the multi-step kernels.  Returns S^: shat0 (the permeability term, 0 for uniform mu)
 // minus mu j_z of the sources at the site.
+// shat0: the source already formed at the site; pz, sbx, sby, jmu: what the general kernel adds (E_z = -c^2 sigma
+// - pz, B_x and B_y scaled by sbx, sby, j_z by jmu; 0, 1, 1, 1 leave every value unchanged).
 __device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
                                              float g1, float g2, float g3, float g4, float cl, float shat0 = 0.f,
-                                             float pz = 0.f) {
+                                             float pz = 0.f, float sbx = 1.f, float sby = 1.f, float jmu = 1.f) {
     float shat = shat0;
     if (!a.evt.rowptr) return shat;
     const int e0 = __ldg(a.evt.rowptr + y), e1 = __ldg(a.evt.rowptr + y + 1);
@@ -350,12 +355,15 @@ __device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, lo
             if (ev.comp == 2 && t < a.evt.nt) {
                 float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
                 if (a.med.mu) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)y * a.g.pitch + x));
+                jz = __fmul_rn(jz, jmu);
                 shat = __fsub_rn(shat, jz);
             }
         } else if (owned && t < a.evt.cap) {
             const float s = ((g0 + g1) + (g2 + g3)) + g4;
             float v = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
             if (ev.comp == 2) v = __fsub_rn(v, pz);  // with a dispersive pole E = D/eps_inf - P (else pz = +0)
+            if (ev.comp == 3) v = __fmul_rn(v, sbx);
+            if (ev.comp == 4) v = __fmul_rn(v, sby);
             a.evt.traces[(long long)ev.index * a.evt.cap + t] = v;
         }
     }
@@ -420,6 +428,12 @@ struct lbem {
     // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, dense [nsite]
     float *d_wp2 = nullptr, *d_wr2 = nullptr, *d_gam = nullptr, *d_J = nullptr, *d_P = nullptr;
     bool disp = false;
+    // anisotropic medium (lbem_set_medium_aniso): r = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy)
+    bool aniso = false;
+    float aniso_r = 1.f, aniso_mu = 1.f;
+    // steps that only the general single-step kernel takes (general.cu)
+    bool general() const { return disp || aniso; }
+    float aniso_fsum() const { return aniso ? aniso_r + 1.f / aniso_r : 2.f; }  // (c_x^2 + c_y^2) / cbar^2
     size_t tile_smem[4] = {0, 0, 0, 0}, tile_smem_mu[4] = {0, 0, 0, 0};  // uniform / heterogeneous mu
     bool walls() const { return bc[0] || bc[1] || bc[2]; }
     // adjoint
@@ -471,11 +485,13 @@ cudaError_t launch_init_3d(const lbem_t *h, const float *E, const float *B, cuda
 cudaError_t launch_fields_3d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_3d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);
 // shared small kernels (medium.cu)
-cudaError_t launch_medium(lbem_t *h, const float *eps, const float *mu, unsigned *bad, cudaStream_t s);
+// fsum = sum of the axis speeds over c_L^2 (D, or r + 1/r anisotropic), mubar = sqrt(mu_xx mu_yy) (else 1)
+cudaError_t launch_medium(lbem_t *h, const float *eps, const float *mu, double fsum, double mubar, unsigned *bad,
+                          cudaStream_t s);
 cudaError_t launch_maxabs(const float *a, long long n, unsigned *out, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double *partials, int n, double *out, cudaStream_t s);
 int diag_blocks(long long nsite);
-cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, cudaStream_t s);
+cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, double mubar, cudaStream_t s);
 cudaError_t launch_energy_flux(const lbem_t *h, const float *E, const float *B, float *u, float *P, cudaStream_t s);
 // guarded device allocations (lbem_api.cu): `bytes` usable bytes between two patterned guard bands
 cudaError_t gmalloc(lbem_t *h, void **p, size_t bytes, const char *name);
@@ -488,9 +504,10 @@ size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu);
 cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
                            cudaStream_t s);
 cudaError_t launch_medium_grad_walls(const lbem_t *h, cudaStream_t s);
-// disp.cu: single steps with a dispersive pole (walls and layers applied in the kernel)
-cudaError_t launch_step_2d_disp(const StepArgs &a, const Walls &w, const Pole &q, cudaStream_t s);
-cudaError_t launch_disp_check(const lbem_t *h, const float *eps, const float *mu, const float *wp2, const float *wr2,
-                              const float *gam, unsigned *bad, cudaStream_t s);
+// general.cu: single steps with a dispersive pole and / or an anisotropic medium (walls and layers applied in the
+// kernel)
+cudaError_t launch_step_2d_gen(const StepArgs &a, const Walls &w, const General &q, cudaStream_t s);
+cudaError_t launch_disp_check(const lbem_t *h, const float *eps, const float *mu, double fsum, double mubar,
+                              const float *wp2, const float *wr2, const float *gam, unsigned *bad, cudaStream_t s);
 
 }  // namespace lbk

@@ -10,7 +10,8 @@
 
 namespace lbk {
 
-__global__ void medium_check(const float *eps, const float *mu, long long n, int D, double c_ref2, unsigned *bad) {
+__global__ void medium_check(const float *eps, const float *mu, long long n, int D, double c_ref2, double fsum,
+                             double mubar, unsigned *bad) {
     unsigned local = 0;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const double e = eps[s], m = mu ? (double)mu[s] : 1.0;
@@ -18,20 +19,21 @@ __global__ void medium_check(const float *eps, const float *mu, long long n, int
             local++;
             continue;
         }
-        const double cl = (D - 1) * c_ref2 / (e * m);
-        const double w0 = 1.0 - D * cl;
+        const double cl = (D - 1) * c_ref2 / (e * m * mubar);
+        const double w0 = 1.0 - fsum * cl;  // 1 - D c_L^2; anisotropic: 1 - (c_x^2 + c_y^2)
         if (!(w0 >= 0.0 && w0 < 1.0)) local++;
     }
     if (local) atomicAdd(bad, local);
 }
 
-__global__ void medium_write(Grid G, int D, double c_ref2, const float *eps, const float *mu, float *cL2, float *mu_out) {
+__global__ void medium_write(Grid G, int D, double c_ref2, double mubar, const float *eps, const float *mu, float *cL2,
+                             float *mu_out) {
     const long long n = (long long)G.nx * G.nrows;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const long long row = s / G.nx;
         const int x = (int)(s - row * G.nx);
         const double m = mu ? (double)mu[s] : 1.0;
-        const double cl = (D - 1) * c_ref2 / ((double)eps[s] * m);
+        const double cl = (D - 1) * c_ref2 / ((double)eps[s] * m * mubar);
         cL2[row * G.pitch + x] = (float)cl;
         if (mu_out) mu_out[row * G.pitch + x] = (float)m;
     }
@@ -62,16 +64,18 @@ static unsigned grid_for(long long n) {
     return (unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
 }
 
-cudaError_t launch_medium(lbem_t *h, const float *eps, const float *mu, unsigned *bad, cudaStream_t s) {
+cudaError_t launch_medium(lbem_t *h, const float *eps, const float *mu, double fsum, double mubar, unsigned *bad,
+                          cudaStream_t s) {
     // pass 1: validation only (caller reads *bad and decides)
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    medium_check<<<grid_for(h->nsite), 256, 0, s>>>(eps, mu, h->nsite, h->dim, h->c_ref2, bad);
+    medium_check<<<grid_for(h->nsite), 256, 0, s>>>(eps, mu, h->nsite, h->dim, h->c_ref2, fsum, mubar, bad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, cudaStream_t s) {
-    medium_write<<<grid_for(h->nsite), 256, 0, s>>>(h->grid, h->dim, h->c_ref2, eps, mu, h->cL2, mu ? h->mu : nullptr);
+cudaError_t launch_medium_write(lbem_t *h, const float *eps, const float *mu, double mubar, cudaStream_t s) {
+    medium_write<<<grid_for(h->nsite), 256, 0, s>>>(h->grid, h->dim, h->c_ref2, mubar, eps, mu, h->cL2,
+                                                     mu ? h->mu : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !mu) return e;
     medium_grad<<<grid_for(h->nsite), 256, 0, s>>>(h->grid, h->dim, h->mu, h->dlnmu);

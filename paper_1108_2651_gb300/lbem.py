@@ -53,6 +53,7 @@ _SIGS = {
     "lbem_set_watchdog": [_VP, _I, _D],
     "lbem_set_boundaries": [_VP, C.POINTER(_I), _I, _D],
     "lbem_set_dispersion": [_VP, _VP, _VP, _VP],
+    "lbem_set_medium_aniso": [_VP, _VP, _D, _D],
     "lbem_get_boundaries": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)],
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
@@ -213,6 +214,12 @@ def lbem_set_boundaries(h, kind, layer=0, gamma_max=0.0):
     """kind: boundary per axis (x, y[, z]): BC_PERIODIC, BC_PEC or BC_PMC."""
     k = (_I * 3)(*(list(kind) + [0] * (3 - len(kind))))
     _check(load().lbem_set_boundaries(h, k, int(layer), float(gamma_max)))
+
+
+def lbem_set_medium_aniso(h, eps_r, mu_xx, mu_yy):
+    """eps_r per site ([nsite], host or device) and a uniform permeability tensor diag(mu_xx, mu_yy) (2D)."""
+    n = lbem_info(h)[0]
+    _check(load().lbem_set_medium_aniso(h, _ptr(eps_r, count=n), float(mu_xx), float(mu_yy)))
 
 
 def lbem_set_dispersion(h, wp2, wr2=None, gamma=None):
@@ -384,7 +391,10 @@ class Solver:
 
         eps = torch.as_tensor(np.ascontiguousarray(p.eps_r, np.float32).ravel(), device=device)
         mu = None if p.mu_r is None else torch.as_tensor(np.ascontiguousarray(p.mu_r, np.float32).ravel(), device=device)
-        lbem_set_medium(self.h, eps, mu)
+        if getattr(p, "aniso", None) is not None:
+            lbem_set_medium_aniso(self.h, eps, *p.aniso)
+        else:
+            lbem_set_medium(self.h, eps, mu)
         if getattr(p, "wp2", None) is not None:
             dev = lambda a: None if a is None else torch.as_tensor(
                 np.ascontiguousarray(np.broadcast_to(a, p.shape), np.float32).ravel(), device=device)

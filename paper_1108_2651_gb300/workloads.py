@@ -85,6 +85,7 @@ class Problem:
     wp2: Optional[np.ndarray] = None  # dispersive pole per site (grid): plasma frequency squared, or None
     wr2: Optional[np.ndarray] = None  # its resonance frequency squared
     gamma: Optional[np.ndarray] = None  # its damping rate
+    aniso: Optional[tuple] = None  # (mu_xx, mu_yy): a uniform in-plane permeability tensor (2D; mu_r must be None)
 
     @property
     def c_ref2(self):
@@ -190,6 +191,18 @@ def heterogeneous_2d_drude(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec
     p.wp2 = np.where(disk, wp2, 0.0)
     p.wr2 = np.zeros(p.shape)
     p.gamma = np.where(disk, gamma, 0.0)
+    return p
+
+
+def heterogeneous_2d_aniso(n=1024, seed=1, nsteps=5000, sigma=20.0, nrec=64, rec_radius=None, mu_xx=2.0, mu_yy=1.0,
+                           name=None):
+    """heterogeneous_2d in a uniaxial medium: the same eps_r with a uniform permeability tensor diag(mu_xx, mu_yy),
+    so waves move sqrt(mu_xx / mu_yy) times faster along x than along y.  The lattice needs
+    c_ref^2 (1/mu_xx + 1/mu_yy) <= eps_r (rest weight >= 0): eps_r is raised to at least that."""
+    p = heterogeneous_2d(n, seed, nsteps, sigma, nrec, rec_radius, name=name or f"het2d_aniso_{n}")
+    need = C_REF2[2] * (1.0 / mu_xx + 1.0 / mu_yy)
+    p.eps_r = np.maximum(p.eps_r, need)
+    p.aniso = (float(mu_xx), float(mu_yy))
     return p
 
 

@@ -47,7 +47,8 @@ def oracle_run(p, nsteps=None):
     if p.wp2 is not None:
         full = lambda a: f32(np.broadcast_to(0.0 if a is None else a, p.shape))
         disp = dict(wp2=full(p.wp2), wr2=full(p.wr2), gamma=full(p.gamma))
-    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r), bc=p.bc, layer=p.layer, gamma_max=p.gamma_max, dispersion=disp)
+    m = O.medium(p.D, f32(p.eps_r), f32(p.mu_r), bc=p.bc, layer=p.layer, gamma_max=p.gamma_max, dispersion=disp,
+                 aniso=p.aniso)
     g = O.init_state(m, f32(p.E0), f32(p.B0))
     pole = O.pole_state(m) if disp is not None else None
     src = p.sources()
