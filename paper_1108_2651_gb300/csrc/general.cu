@@ -35,11 +35,13 @@
 // plain scheme.
 //
 // step2d_gen is the single-step kernel for the media the fast kernels do not
-// cover (a pole, an anisotropic tensor), one site per thread: pulls with
-// periodic wrap or across walls (the wall rule of walls.cu), the B x grad ln mu
-// source, sources and receivers, the pole, the collision, the absorbing layer's
-// factor.  J and P are read and written at the site only, so they are updated
-// in place.
+// cover (a pole, an anisotropic tensor).  Thread mapping as the plain
+// single-step kernel: one warp covers 128 consecutive sites of a row, 4 per
+// lane, with 16-byte loads and the +-x pulls by warp shuffle (pull2d); pulls
+// across a wall are then replaced by the wall rule of walls.cu.  Per site: the
+// B x grad ln mu source, sources and receivers, the pole, the collision, the
+// absorbing layer's factor.  The pole's arrays are planes like c_L^2; J and P
+// are read and written at the site only, so they are updated in place.
 #include <algorithm>
 
 #include "lbem_internal.cuh"
@@ -47,90 +49,121 @@
 namespace lbk {
 
 template <bool MU>
-__global__ void __launch_bounds__(256) step2d_gen(StepArgs a, Walls w, General q) {
+__global__ void __launch_bounds__(BLOCK, 4) step2d_gen(StepArgs a, Walls w, General q) {
+    using C = Codec<LBEM_F32>;
     const Grid &G = a.g;
-    const long long n = (long long)G.nx * G.ny;
-    const float *in = static_cast<const float *>(a.in.data);
-    float *out = static_cast<float *>(a.out.data);
-    const long long PL = a.in.plane, PO = a.out.plane;
+    const int lane = threadIdx.x & 31;
+    const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    const int wpr = G.nchunk_pad >> 5;
+    const int row = (int)(wg / wpr);
+    const int c = (int)(wg - (long long)row * wpr) * 32 + lane;
+    if (row >= G.ny) return;  // warp-uniform
+    const bool active = c < G.nchunk;
+    const int x0 = 4 * c;
+    float4 g[5];
+    pull2d<LBEM_F32>(a.in, G, row, c, lane, g);
+    if (!active) return;
+    // pulls across a wall: the site's own opposite population times the wall sign
     const float sx = w.kind[0] == 1 ? -1.f : 1.f, sy = w.kind[1] == 1 ? -1.f : 1.f;
-    const float r = q.r, ri = __fdiv_rn(1.f, q.r), fs = __fadd_rn(r, ri);  // fs = 2 when isotropic
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(s / G.nx), x = (int)(s - (long long)y * G.nx);
-        const long long rw = (long long)y * a.in.pitch;
-        const int ym = y == 0 ? G.ny - 1 : y - 1, yp = y == G.ny - 1 ? 0 : y + 1;
-        const int xm = x == 0 ? G.nx - 1 : x - 1, xp = x == G.nx - 1 ? 0 : x + 1;
-        // pulls g_i(x) = g'_i(x - c_i); across a wall the site's own opposite population times the wall sign
-        const float g0 = in[rw + x];
-        const float g1 = (w.kind[0] && x == 0) ? sx * in[3 * PL + rw + x] : in[PL + rw + xm];
-        const float g3 = (w.kind[0] && x == G.nx - 1) ? sx * in[PL + rw + x] : in[3 * PL + rw + xp];
-        const float g2 = (w.kind[1] && y == 0) ? sy * in[4 * PL + rw + x] : in[2 * PL + (long long)ym * a.in.pitch + x];
-        const float g4 = (w.kind[1] && y == G.ny - 1) ? sy * in[2 * PL + rw + x]
-                                                        : in[4 * PL + (long long)yp * a.in.pitch + x];
-        const long long o = (long long)y * G.pitch + x;
-        const float cl = a.med.cL2[o];
-        float shat = MU ? mu_source(g4 - g2, g1 - g3, a.med.dlnmu[o], a.med.dlnmu[G.plane + o]) : 0.f;
-        const float sig = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, g3)), g4);
-        float P = 0.f;
-        if (q.wp2) {
-            // the pole, from the pre-collision field E = D/eps_inf - P
-            P = q.P[s];
-            const float J = q.J[s], gm = q.gam[s];
-            const float E = __fsub_rn(__fmul_rn(-cl, sig), P);
-            const float num = __fadd_rn(__fsub_rn(__fmul_rn(__fsub_rn(1.f, 0.5f * gm), J), __fmul_rn(q.wr2[s], P)),
-                                        __fmul_rn(q.wp2[s], E));
-            const float Jn = __fdiv_rn(num, __fadd_rn(1.f, 0.5f * gm));
-            q.J[s] = Jn;
-            q.P[s] = __fadd_rn(P, Jn);
-        }
-        if (a.evt.rowptr && __ldg(a.evt.rowptr + y) != __ldg(a.evt.rowptr + y + 1))
-            shat = site_events(a, x, y, a.t, true, g0, g1, g2, g3, g4, cl, shat, P, r, ri, q.mubar);
-        // collision with the second moment Lambda + P read per axis
-        const float Lam = __fadd_rn(__fmul_rn(cl, sig), P);
-        const float Lx = __fmul_rn(r, Lam), Ly = __fmul_rn(ri, Lam);
-        const float w0 = __fsub_rn(1.f, __fmul_rn(fs, cl));
-        const float Tm = __fmul_rn(-0.5f * cl, shat), T0 = __fmul_rn(-w0, shat);
-        const float Tx = __fmul_rn(r, Tm), Ty = __fmul_rn(ri, Tm);
-        const float f = __fmul_rn(w.fx ? w.fx[x] : 1.f, w.fy ? w.fy[y] : 1.f);
-        const long long ro = (long long)y * a.out.pitch + x;
-        out[ro] = __fmul_rn(
-            __fadd_rn(__fsub_rn(__fsub_rn(__fmul_rn(2.f * w0, sig), g0), __fmul_rn(2.f * fs, P)), T0), f);
-        out[PO + ro] = __fmul_rn(__fadd_rn(__fsub_rn(Lx, g3), Tx), f);
-        out[2 * PO + ro] = __fmul_rn(__fadd_rn(__fsub_rn(Ly, g4), Ty), f);
-        out[3 * PO + ro] = __fmul_rn(__fadd_rn(__fsub_rn(Lx, g1), Tx), f);
-        out[4 * PO + ro] = __fmul_rn(__fadd_rn(__fsub_rn(Ly, g2), Ty), f);
+    if (w.kind[1] && row == 0) {
+        const float4 v = C::load4(a.in, 4, row, c);
+        g[2] = make_float4(sy * v.x, sy * v.y, sy * v.z, sy * v.w);
     }
+    if (w.kind[1] && row == G.ny - 1) {
+        const float4 v = C::load4(a.in, 2, row, c);
+        g[4] = make_float4(sy * v.x, sy * v.y, sy * v.z, sy * v.w);
+    }
+    if (w.kind[0] && x0 == 0) set(g[1], 0, sx * C::load1(a.in, 3, row, 0));
+    if (w.kind[0] && x0 + 4 >= G.nx) set(g[3], G.nx - 1 - x0, sx * C::load1(a.in, 1, row, G.nx - 1));
+    const long long o4 = (long long)row * G.pitch + x0;  // first of the lane's 4 sites in a medium plane
+    const float4 cl = *reinterpret_cast<const float4 *>(a.med.cL2 + o4);
+    float4 dlx = make_float4(0.f, 0.f, 0.f, 0.f), dly = dlx;
+    if (MU) {
+        dlx = *reinterpret_cast<const float4 *>(a.med.dlnmu + o4);
+        dly = *reinterpret_cast<const float4 *>(a.med.dlnmu + G.plane + o4);
+    }
+    float4 sig4;  // sigma = sum_i g_i per site (the order of collide2d)
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        set(sig4, j, __fadd_rn(__fadd_rn(__fadd_rn(get(g[0], j), get(g[1], j)), __fadd_rn(get(g[2], j), get(g[3], j))),
+                               get(g[4], j)));
+    float4 P4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.wp2) {
+        // the pole, from the pre-collision field E = D/eps_inf - P; the collision below uses P(t)
+        P4 = *reinterpret_cast<const float4 *>(q.P + o4);
+        const float4 J4 = *reinterpret_cast<const float4 *>(q.J + o4);
+        const float4 wp4 = *reinterpret_cast<const float4 *>(q.wp2 + o4);
+        const float4 wr4 = *reinterpret_cast<const float4 *>(q.wr2 + o4);
+        const float4 gm4 = *reinterpret_cast<const float4 *>(q.gam + o4);
+        float4 Jn4, Pn4;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float P = get(P4, j), gm = get(gm4, j);
+            const float E = __fsub_rn(__fmul_rn(-get(cl, j), get(sig4, j)), P);
+            const float num = __fadd_rn(
+                __fsub_rn(__fmul_rn(__fsub_rn(1.f, 0.5f * gm), get(J4, j)), __fmul_rn(get(wr4, j), P)),
+                __fmul_rn(get(wp4, j), E));
+            const float Jn = __fdiv_rn(num, __fadd_rn(1.f, 0.5f * gm));
+            set(Jn4, j, Jn);
+            set(Pn4, j, __fadd_rn(P, Jn));
+        }
+        *reinterpret_cast<float4 *>(q.J + o4) = Jn4;
+        *reinterpret_cast<float4 *>(q.P + o4) = Pn4;
+    }
+    const float4 one4 = make_float4(1.f, 1.f, 1.f, 1.f);
+    const float4 fx4 = w.fx ? *reinterpret_cast<const float4 *>(w.fx + x0) : one4;
+    const float fy = w.fy ? w.fy[row] : 1.f;
+    const bool ev = a.evt.rowptr && __ldg(a.evt.rowptr + row) != __ldg(a.evt.rowptr + row + 1);
+    const float r = q.r, ri = __fdiv_rn(1.f, q.r), fs = __fadd_rn(r, ri);  // fs = 2 when isotropic
+    float4 o[5];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float g0 = get(g[0], j), g1 = get(g[1], j), g2 = get(g[2], j), g3 = get(g[3], j), g4 = get(g[4], j);
+        const float ck = get(cl, j);
+        float shat = MU ? mu_source(g4 - g2, g1 - g3, get(dlx, j), get(dly, j)) : 0.f;
+        const float sig = get(sig4, j);
+        const float P = get(P4, j);
+        if (ev && x0 + j < G.nx)
+            shat = site_events(a, x0 + j, row, a.t, true, g0, g1, g2, g3, g4, ck, shat, P, r, ri, q.mubar);
+        // collision with the second moment Lambda + P read per axis
+        const float Lam = __fadd_rn(__fmul_rn(ck, sig), P);
+        const float Lx = __fmul_rn(r, Lam), Ly = __fmul_rn(ri, Lam);
+        const float w0 = __fsub_rn(1.f, __fmul_rn(fs, ck));
+        const float Tm = __fmul_rn(-0.5f * ck, shat), T0 = __fmul_rn(-w0, shat);
+        const float Tx = __fmul_rn(r, Tm), Ty = __fmul_rn(ri, Tm);
+        const float f = __fmul_rn(get(fx4, j), fy);
+        set(o[0], j, __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(__fmul_rn(2.f * w0, sig), g0), __fmul_rn(2.f * fs, P)), T0),
+                               f));
+        set(o[1], j, __fmul_rn(__fadd_rn(__fsub_rn(Lx, g3), Tx), f));
+        set(o[2], j, __fmul_rn(__fadd_rn(__fsub_rn(Ly, g4), Ty), f));
+        set(o[3], j, __fmul_rn(__fadd_rn(__fsub_rn(Lx, g1), Tx), f));
+        set(o[4], j, __fmul_rn(__fadd_rn(__fsub_rn(Ly, g2), Ty), f));
+    }
+#pragma unroll
+    for (int p = 0; p < 5; p++) C::store4(a.out, p, row, c, o[p]);
 }
 
 cudaError_t launch_step_2d_gen(const StepArgs &a, const Walls &w, const General &q, cudaStream_t s) {
-    static int per_sm[2] = {0, 0}, nsm = 0;
-    const bool mu = a.med.dlnmu != nullptr;
-    if (!per_sm[mu]) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (mu) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], step2d_gen<true>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], step2d_gen<false>, 256, 0);
-        if (per_sm[mu] < 1) per_sm[mu] = 1;
-    }
-    const long long n = (long long)a.g.nx * a.g.ny;
-    const long long blocks = std::min<long long>((n + 255) / 256, (long long)per_sm[mu] * nsm);
-    if (mu) step2d_gen<true><<<(unsigned)blocks, 256, 0, s>>>(a, w, q);
-    else step2d_gen<false><<<(unsigned)blocks, 256, 0, s>>>(a, w, q);
+    const long long warps = (long long)a.g.ny * (a.g.nchunk_pad / 32);
+    const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
+    if (a.med.dlnmu) step2d_gen<true><<<blocks, BLOCK, 0, s>>>(a, w, q);
+    else step2d_gen<false><<<blocks, BLOCK, 0, s>>>(a, w, q);
     return cudaGetLastError();
 }
 
-// Validation of a pole (dense [nsite] arrays; wr2, gam may be null) against a medium: finite, non-negative,
+// Validation of a pole (dense [nsite] arrays, or planes with the grid's pitch; wr2, gam may be null) against a medium: finite, non-negative,
 // wp^2 + wr^2 <= 4 w0 with w0 = 1 - fsum c_L^2 in FP64 (fsum = 2, or r + 1/r for an anisotropic medium).  The
 // medium is either the stored c_L^2 (pitched; eps null) or a new eps_r, mu_r (dense; mu may be null) with
 // c_L^2 = c_ref^2 / (eps_r mu_r mubar).
 __global__ void disp_check(Grid G, const float *cL2, const float *eps, const float *mu, double c_ref2, double fsum,
-                           double mubar, const float *wp2, const float *wr2, const float *gam, unsigned *bad) {
+                           double mubar, const float *wp2, const float *wr2, const float *gam, bool pitched,
+                           unsigned *bad) {
     unsigned local = 0;
     const long long n = (long long)G.nx * G.ny;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(s / G.nx), x = (int)(s - (long long)y * G.nx);
-        const double p = wp2[s], r = wr2 ? (double)wr2[s] : 0.0, g = gam ? (double)gam[s] : 0.0;
+        const long long k = pitched ? (long long)y * G.pitch + x : s;
+        const double p = wp2[k], r = wr2 ? (double)wr2[k] : 0.0, g = gam ? (double)gam[k] : 0.0;
         const double cl = eps ? c_ref2 / ((double)eps[s] * (mu ? (double)mu[s] : 1.0) * mubar)
                               : (double)cL2[(long long)y * G.pitch + x];
         const double w0 = 1.0 - fsum * cl;
@@ -140,10 +173,29 @@ __global__ void disp_check(Grid G, const float *cL2, const float *eps, const flo
     if (local) atomicAdd(bad, local);
 }
 
+static unsigned blocks_for(long long n) {
+    return (unsigned)std::min<long long>(4096, std::max<long long>(1, (n + 255) / 256));
+}
+
 cudaError_t launch_disp_check(const lbem_t *h, const float *eps, const float *mu, double fsum, double mubar,
-                              const float *wp2, const float *wr2, const float *gam, unsigned *bad, cudaStream_t s) {
-    const unsigned blocks = (unsigned)std::min<long long>(4096, std::max<long long>(1, (h->nsite + 255) / 256));
-    disp_check<<<blocks, 256, 0, s>>>(h->grid, h->cL2, eps, mu, h->c_ref2, fsum, mubar, wp2, wr2, gam, bad);
+                              const float *wp2, const float *wr2, const float *gam, bool pitched, unsigned *bad,
+                              cudaStream_t s) {
+    disp_check<<<blocks_for(h->nsite), 256, 0, s>>>(h->grid, h->cL2, eps, mu, h->c_ref2, fsum, mubar, wp2, wr2, gam,
+                                                     pitched, bad);
+    return cudaGetLastError();
+}
+
+// dense [nsite] (null: zeros) -> plane with the grid's pitch (padding columns zero)
+__global__ void to_plane(Grid G, const float *src, float *dst) {
+    const long long n = (long long)G.pitch * G.ny;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / G.pitch), x = (int)(k - (long long)y * G.pitch);
+        dst[k] = (src && x < G.nx) ? src[(long long)y * G.nx + x] : 0.f;
+    }
+}
+
+cudaError_t launch_to_plane(const lbem_t *h, const float *src, float *dst, cudaStream_t s) {
+    to_plane<<<blocks_for((long long)h->grid.pitch * h->grid.ny), 256, 0, s>>>(h->grid, src, dst);
     return cudaGetLastError();
 }
 

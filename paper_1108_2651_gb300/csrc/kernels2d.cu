@@ -24,32 +24,7 @@
 
 namespace lbk {
 
-// Pre-collision populations of the 4 sites (row, 4c..4c+3): g_i(x) = buf_i(x - c_i).
-// Must be called by all 32 lanes of a warp (shuffles); lanes with c >= nchunk
-// load nothing and their results are discarded by the caller.
-template <int ST>
-__device__ __forceinline__ void pull2d(const PopBuf &in, const Grid &G, int row, int c, int lane, float4 g[5]) {
-    using C = Codec<ST>;
-    const int x0 = 4 * c;
-    const bool active = c < G.nchunk;  // lanes past the row end load nothing
-    const int ym = row == 0 ? G.ny - 1 : row - 1;
-    const int yp = row == G.ny - 1 ? 0 : row + 1;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    g[0] = active ? C::load4(in, 0, row, c) : z4;
-    float4 a1 = active ? C::load4(in, 1, row, c) : z4;
-    g[2] = active ? C::load4(in, 2, ym, c) : z4;
-    float4 a3 = active ? C::load4(in, 3, row, c) : z4;
-    g[4] = active ? C::load4(in, 4, yp, c) : z4;
-    float prev = __shfl_up_sync(FULL, a1.w, 1);
-    float next = __shfl_down_sync(FULL, a3.x, 1);
-    if (lane == 0 && active) prev = C::load1(in, 1, row, c == 0 ? G.nx - 1 : x0 - 1);
-    if (lane == 31 && x0 + 4 < G.nx) next = C::load1(in, 3, row, x0 + 4);
-    g[1] = make_float4(prev, a1.x, a1.y, a1.z);
-    g[3] = make_float4(a3.y, a3.z, a3.w, next);
-    if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, C::load1(in, 3, row, 0));  // periodic wrap at x = nx-1
-}
-
-// collide2d and field2d (the per-site update and the receiver readout) are in lbem_internal.cuh.
+// pull2d (the pulls of 4 sites of a row by one lane), collide2d and field2d are in lbem_internal.cuh.
 
 template <int ST, bool MU, int R>
 __global__ void __launch_bounds__(BLOCK) step2d(StepArgs a) {
@@ -853,7 +828,7 @@ __global__ void __launch_bounds__(BLOCK) fields2d(Grid G, PopBuf in, const float
             E[sd] = 0.f;
             E[nsite + sd] = 0.f;
             const float ez = -get(cl, j) * s;
-            E[2 * nsite + sd] = Pz ? __fsub_rn(ez, Pz[sd]) : ez;  // with a dispersive pole E = D/eps_inf - P
+            E[2 * nsite + sd] = Pz ? __fsub_rn(ez, Pz[(long long)row * G.pitch + x]) : ez;  // E = D/eps_inf - P
         }
         if (B) {  // anisotropic medium: B_x = r (g_4 - g_2), B_y = (g_1 - g_3) / r
             const float bx = get(g[4], j) - get(g[2], j), by = get(g[1], j) - get(g[3], j);
@@ -928,7 +903,7 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
             sum += g[i];
         }
         const double cl = (double)cL2[(long long)y * G.pitch + x];
-        const double rd = r, Ez = -cl * sum - (Pz ? (double)Pz[s] : 0.0), bx = rd * (g[4] - g[2]),
+        const double rd = r, Ez = -cl * sum - (Pz ? (double)Pz[(long long)y * G.pitch + x] : 0.0), bx = rd * (g[4] - g[2]),
                      by = (g[1] - g[3]) / rd;
         en += bx * bx + by * by + Ez * Ez / cl;  // c_eff^2 = c_L^2 in 2D
         // weights: c_x^2 / 2 = r c_L^2 / 2 for x-movers, c_L^2 / (2 r) for y-movers (r = 1: isotropic)

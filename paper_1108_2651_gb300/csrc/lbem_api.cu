@@ -363,7 +363,7 @@ lbem_status lbem_info(const lbem_t *h, long long *nsite, size_t *state_bytes) {
     if (state_bytes) {
         size_t b = (size_t)h->npop * h->grid.plane * elem_bytes(h->storage);
         if (h->storage == LBEM_I16B) b += (size_t)h->npop * h->buf[0].explane;
-        if (h->disp) b += 2 * sizeof(float) * (size_t)h->nsite;  // the pole's J and P
+        if (h->disp) b += 2 * sizeof(float) * (size_t)h->grid.plane;  // the pole's J and P planes
         *state_bytes = b;
     }
     return LBEM_OK;
@@ -390,7 +390,8 @@ static lbem_status set_medium(lbem_t *h, const float *eps_r, const float *mu_r, 
                                          "[0,1) (medium faster than c_ref)");
     if (h->disp) {  // the pole must stay within its stability bound in the new medium
         LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
-        LBEM_CUDA(launch_disp_check(h, de, dm, fsum, mubar, h->d_wp2, h->d_wr2, h->d_gam, h->d_counter, h->stream));
+        LBEM_CUDA(launch_disp_check(h, de, dm, fsum, mubar, h->d_wp2, h->d_wr2, h->d_gam, true, h->d_counter,
+                                    h->stream));
         LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
         LBEM_CUDA(cudaStreamSynchronize(h->stream));
         if (bad)
@@ -464,8 +465,8 @@ lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B) {
     h->wd_last = -1.0;
     if (h->d_traces) LBEM_CUDA(cudaMemsetAsync(h->d_traces, 0, sizeof(float) * (size_t)h->nrec * h->cap, h->stream));
     if (h->disp) {  // the pole starts at rest: D = E
-        LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * (size_t)h->nsite, h->stream));
-        LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * (size_t)h->nsite, h->stream));
+        LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * (size_t)h->grid.plane, h->stream));
+        LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * (size_t)h->grid.plane, h->stream));
     }
     drop_graph(h);
     return LBEM_OK;
@@ -650,19 +651,20 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
     drop_graph(h);
     if (h->has_mu && h->dim == 2) LBEM_CUDA(launch_medium_grad_walls(h, h->stream));  // grad ln mu at the walls
     if (!any) return LBEM_OK;
-    // layer factors 1 - gamma_max ((L - i)/L)^2 at distance i from the wall-adjacent site, per column / row
-    const int len[2] = {h->grid.nx, h->grid.ny};
+    // layer factors 1 - gamma_max ((L - i)/L)^2 at distance i from the wall-adjacent site, per column / row (the
+    // column table padded with 1 to the row pitch, for 16-byte loads)
+    const int len[2] = {h->grid.nx, h->grid.ny}, alloc[2] = {h->grid.pitch, h->grid.ny};
     float **dst[2] = {&h->d_fx, &h->d_fy};
     for (int a = 0; a < 2; a++) {
         if (!kind[a] || layer == 0) continue;
-        std::vector<float> f(len[a]);
+        std::vector<float> f(alloc[a], 1.f);
         for (int v = 0; v < len[a]; v++) {
             const int i = std::min(v, len[a] - 1 - v);
             const double r = (double)(layer - i) / layer;
             f[v] = i < layer ? (float)(1.0 - gamma_max * r * r) : 1.f;
         }
-        LBEM_CUDA(gmalloc(h, (void **)dst[a], sizeof(float) * len[a], "layer factors"));
-        LBEM_CUDA(cudaMemcpy(*dst[a], f.data(), sizeof(float) * len[a], cudaMemcpyHostToDevice));
+        LBEM_CUDA(gmalloc(h, (void **)dst[a], sizeof(float) * alloc[a], "layer factors"));
+        LBEM_CUDA(cudaMemcpy(*dst[a], f.data(), sizeof(float) * alloc[a], cudaMemcpyHostToDevice));
     }
     for (int k = 1; k <= 3; k++) {
         const std::vector<EdgeTile> t = edge_tiles(h->grid, h->bc, h->layer, k);
@@ -699,25 +701,24 @@ lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, c
     if ((st = device_input(h, wr2, n, n, &dr)) != LBEM_OK) return st;
     if ((st = device_input(h, gamma, n, 2 * n, &dg)) != LBEM_OK) return st;
     LBEM_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned), h->stream));
-    LBEM_CUDA(launch_disp_check(h, nullptr, nullptr, h->aniso_fsum(), 1.0, dp, dr, dg, h->d_counter, h->stream));
+    LBEM_CUDA(launch_disp_check(h, nullptr, nullptr, h->aniso_fsum(), 1.0, dp, dr, dg, false, h->d_counter,
+                                h->stream));
     unsigned bad = 0;
     LBEM_CUDA(cudaMemcpyAsync(&bad, h->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     if (bad)
         return fail(LBEM_ERR_MEDIUM, "lbem_set_dispersion: " + std::to_string(bad) +
                                          " sites with a parameter not finite and >= 0, or wp^2 + wr^2 > 4 w0");
+    const size_t pl = (size_t)h->grid.plane;  // stored as planes with the grid's pitch (padding zero)
     if (!h->d_wp2) {
         for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P})
-            LBEM_CUDA(gmalloc(h, (void **)p, sizeof(float) * n, "dispersive pole"));
+            LBEM_CUDA(gmalloc(h, (void **)p, sizeof(float) * pl, "dispersive pole"));
     }
     const float *src[3] = {dp, dr, dg};
     float *dst[3] = {h->d_wp2, h->d_wr2, h->d_gam};
-    for (int k = 0; k < 3; k++) {
-        if (src[k]) LBEM_CUDA(cudaMemcpyAsync(dst[k], src[k], sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream));
-        else LBEM_CUDA(cudaMemsetAsync(dst[k], 0, sizeof(float) * n, h->stream));
-    }
-    LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * n, h->stream));
-    LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * n, h->stream));
+    for (int k = 0; k < 3; k++) LBEM_CUDA(launch_to_plane(h, src[k], dst[k], h->stream));
+    LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * pl, h->stream));
+    LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * pl, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     h->disp = true;
     drop_graph(h);
@@ -811,8 +812,8 @@ lbem_status lbem_save_state(lbem_t *h, void *dst) {
     const size_t db = (size_t)h->npop * p.plane * elem_bytes(h->storage);
     LBEM_CUDA(cudaMemcpyAsync(dst, p.data, db, cudaMemcpyDefault, h->stream));
     if (p.ex) LBEM_CUDA(cudaMemcpyAsync((char *)dst + db, p.ex, (size_t)h->npop * p.explane, cudaMemcpyDefault, h->stream));
-    if (h->disp) {  // then the pole's J and P
-        const size_t pb = sizeof(float) * (size_t)h->nsite;
+    if (h->disp) {  // then the pole's J and P planes
+        const size_t pb = sizeof(float) * (size_t)h->grid.plane;
         LBEM_CUDA(cudaMemcpyAsync((char *)dst + db, h->d_J, pb, cudaMemcpyDefault, h->stream));
         LBEM_CUDA(cudaMemcpyAsync((char *)dst + db + pb, h->d_P, pb, cudaMemcpyDefault, h->stream));
     }
@@ -828,7 +829,7 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
     if (p.ex)
         LBEM_CUDA(cudaMemcpyAsync(p.ex, (const char *)src + db, (size_t)h->npop * p.explane, cudaMemcpyDefault, h->stream));
     if (h->disp) {
-        const size_t pb = sizeof(float) * (size_t)h->nsite;
+        const size_t pb = sizeof(float) * (size_t)h->grid.plane;
         LBEM_CUDA(cudaMemcpyAsync(h->d_J, (const char *)src + db, pb, cudaMemcpyDefault, h->stream));
         LBEM_CUDA(cudaMemcpyAsync(h->d_P, (const char *)src + db + pb, pb, cudaMemcpyDefault, h->stream));
     }

@@ -303,8 +303,8 @@ struct Walls {
     int kind[2] = {0, 0};
     const float *fx = nullptr, *fy = nullptr;
 };
-// What the general single-step kernel (general.cu) adds to a step: one Drude-Lorentz pole per site (dense [nsite]
-// parameters and state, J at t - 1/2, P at t; wp2 null: no pole) and a uniform in-plane permeability tensor
+// What the general single-step kernel (general.cu) adds to a step: one Drude-Lorentz pole per site (parameters
+// and state as planes with the grid's pitch, J at t - 1/2, P at t; wp2 null: no pole) and a uniform in-plane permeability tensor
 // (axis speeds c_x^2 = r cbar^2, c_y^2 = cbar^2 / r with cbar^2 the stored c_L^2; mubar = sqrt(mu_xx mu_yy)).
 struct General {
     const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr;
@@ -340,6 +340,31 @@ __device__ __forceinline__ float mu_source(float bx, float by, float dlx, float 
 // Source current at global site (x, y) and time t, and the receiver write of the pre-collision fields (only
 // when `owned`), for the multi-step kernels.  Returns S^: shat0 (the permeability term, 0 for uniform mu)
 // minus mu j_z of the sources at the site.
+// Pre-collision populations of the 4 sites (row, 4c..4c+3): g_i(x) = buf_i(x - c_i).
+// Must be called by all 32 lanes of a warp (shuffles); lanes with c >= nchunk
+// load nothing and their results are discarded by the caller.
+template <int ST>
+__device__ __forceinline__ void pull2d(const PopBuf &in, const Grid &G, int row, int c, int lane, float4 g[5]) {
+    using C = Codec<ST>;
+    const int x0 = 4 * c;
+    const bool active = c < G.nchunk;  // lanes past the row end load nothing
+    const int ym = row == 0 ? G.ny - 1 : row - 1;
+    const int yp = row == G.ny - 1 ? 0 : row + 1;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    g[0] = active ? C::load4(in, 0, row, c) : z4;
+    float4 a1 = active ? C::load4(in, 1, row, c) : z4;
+    g[2] = active ? C::load4(in, 2, ym, c) : z4;
+    float4 a3 = active ? C::load4(in, 3, row, c) : z4;
+    g[4] = active ? C::load4(in, 4, yp, c) : z4;
+    float prev = __shfl_up_sync(FULL, a1.w, 1);
+    float next = __shfl_down_sync(FULL, a3.x, 1);
+    if (lane == 0 && active) prev = C::load1(in, 1, row, c == 0 ? G.nx - 1 : x0 - 1);
+    if (lane == 31 && x0 + 4 < G.nx) next = C::load1(in, 3, row, x0 + 4);
+    g[1] = make_float4(prev, a1.x, a1.y, a1.z);
+    g[3] = make_float4(a3.y, a3.z, a3.w, next);
+    if (c == G.nchunk - 1) set(g[3], G.nx - 1 - x0, C::load1(in, 3, row, 0));  // periodic wrap at x = nx-1
+}
+
 // shat0: the source already formed at the site; pz, sbx, sby, jmu: what the general kernel adds (E_z = -c^2 sigma
 // - pz, B_x and B_y scaled by sbx, sby, j_z by jmu; 0, 1, 1, 1 leave every value unchanged).
 __device__ __forceinline__ float site_events(const StepArgs &a, int x, int y, long long t, bool owned, float g0,
@@ -425,7 +450,7 @@ struct lbem {
     float *d_fx = nullptr, *d_fy = nullptr;
     lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     int ntiles[4] = {0, 0, 0, 0};
-    // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, dense [nsite]
+    // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, planes (pitch layout)
     float *d_wp2 = nullptr, *d_wr2 = nullptr, *d_gam = nullptr, *d_J = nullptr, *d_P = nullptr;
     bool disp = false;
     // anisotropic medium (lbem_set_medium_aniso): r = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy)
@@ -508,6 +533,8 @@ cudaError_t launch_medium_grad_walls(const lbem_t *h, cudaStream_t s);
 // kernel)
 cudaError_t launch_step_2d_gen(const StepArgs &a, const Walls &w, const General &q, cudaStream_t s);
 cudaError_t launch_disp_check(const lbem_t *h, const float *eps, const float *mu, double fsum, double mubar,
-                              const float *wp2, const float *wr2, const float *gam, unsigned *bad, cudaStream_t s);
+                              const float *wp2, const float *wr2, const float *gam, bool pitched, unsigned *bad,
+                              cudaStream_t s);
+cudaError_t launch_to_plane(const lbem_t *h, const float *src, float *dst, cudaStream_t s);
 
 }  // namespace lbk

@@ -99,7 +99,7 @@ def test_dispersive_graphs_splits_and_state_round_trip(lbem):
     lbem.lbem_set_graphs(s.h, True)
     s.step(10)
     nb = lbem.lbem_info(s.h)[1]
-    assert nb == 5 * 40 * 160 * 4 + 2 * 40 * 130 * 4  # populations (pitch 160) + the pole's J and P
+    assert nb == 5 * 40 * 160 * 4 + 2 * 40 * 160 * 4  # populations (pitch 160) + the pole's J and P planes
     saved = torch.empty(nb, dtype=torch.uint8, device="cuda")
     lbem.lbem_save_state(s.h, saved)
     s.step(11)
