@@ -187,3 +187,36 @@ def test_layer_absorbs_a_pulse_the_bare_wall_returns(kind):
         left.append(O.diagnostics(m, g)[0] / e0)
     assert abs(left[0] - 1) < 1e-2, left
     assert left[1] < 1e-5, left
+
+
+@pytest.mark.parametrize("kind", [PEC, PMC])
+def test_walls_with_a_dispersive_pole_and_anisotropy_equal_the_mirror_image(kind):
+    """The method of images with the other readings switched on: a Drude-Lorentz pole per site (its J and P
+    mirror with E, times the wall sign) and a uniform permeability tensor (the mirror keeps each axis)."""
+    ny, nx, nsteps = 8, 10, 40
+    rng = np.random.default_rng(31 + kind)
+    eps = 1.5 + rng.random((ny, nx))
+    aniso = (1.8, 1.1)
+    r = np.sqrt(aniso[0] / aniso[1])
+    w0 = 1 - (r + 1 / r) * 0.5 / (eps * np.sqrt(aniso[0] * aniso[1]))
+    wp2, wr2, gam = 2.0 * w0 * rng.random((ny, nx)), 1.0 * w0 * rng.random((ny, nx)), 0.1 * rng.random((ny, nx))
+    E = np.zeros((ny, nx, 3))
+    B = np.zeros_like(E)
+    E[..., 2] = rng.standard_normal((ny, nx))
+    B[..., :2] = rng.standard_normal((ny, nx, 2))
+    m = O.medium(2, eps, bc=(kind, 0), aniso=aniso, dispersion=dict(wp2=wp2, wr2=wr2, gamma=gam))
+    g = O.init_state(m, E, B)
+    pole = O.pole_state(m)
+    O.run(m, g, nsteps, pole=pole)
+    Ew, Bw = O.fields(m, g, pole)
+    s = -1.0 if kind == PEC else 1.0
+    mb = O.medium(2, _mirror(eps, 1), aniso=aniso,
+                  dispersion=dict(wp2=_mirror(wp2, 1), wr2=_mirror(wr2, 1), gamma=_mirror(gam, 1)))
+    gb = _mirror_g(O.init_state(m, E, B), 1, s)
+    pb = O.pole_state(mb)
+    O.run(mb, gb, nsteps, pole=pb)
+    Eb, Bb = O.fields(mb, gb, pb)
+    scale = max(np.abs(Ew).max(), np.abs(Bw).max())
+    np.testing.assert_allclose(Eb[:, :nx], Ew, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(Bb[:, :nx], Bw, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(pb["P"][:, :nx], pole["P"], rtol=0, atol=1e-12 * scale)
