@@ -49,7 +49,11 @@
  *      odd about the wall (a perfect electric conductor, PEC); s = +1 makes
  *      the tangential B odd (a perfect magnetic conductor, PMC).  grad ln mu
  *      at the first / last site uses the mirror image of mu (the one-sided
- *      difference halved), as the doubled domain would.  Walls are 2D only.
+ *      difference halved), as the doubled domain would.  In 3D (and
+ *      consistently in 2D) the factor is per tensor component: a wall across
+ *      axis a reflects g_bc with (b == a ? -1 : 1) (c == a ? -1 : 1), the
+ *      geometric mirror of the tensor, times +1 (PEC) or -1 (PMC); in 2D the
+ *      component xy then gets -1 (PEC) or +1 (PMC) at either wall, as above.
  *  R8  Absorbing layer of L sites inside each wall: after the collision the
  *      populations of a site at distance i = 0 .. L-1 from the wall-adjacent
  *      site are multiplied by 1 - gamma_i, gamma_i = gamma_max ((L - i)/L)^2,
@@ -423,7 +427,7 @@ static void current_at(const sources_t *src, long s, int t, double j[3]) {
  * field at time t0 + n into traces[r][n], n = 0..nsteps-1.  bc[a] (NULL = all
  * periodic) is the boundary of axis a: 0 periodic, 1 PEC wall, 2 PMC wall
  * (readings R6-R7); `layer` > 0 adds the absorbing layer of reading R8 inside
- * every wall.  Returns 0, or -1 for walls in 3D.
+ * every wall.  Returns 0.
  */
 int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2, const double *mu,
            const double *dlnmu, double *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
@@ -435,7 +439,6 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
     set_axes(&L, aniso_r);
     int kind[3] = {0, 0, 0};
     for (int a = 0; bc && a < 3; a++) kind[a] = a < D ? bc[a] : 0;
-    if (D == 3 && (kind[0] || kind[1] || kind[2])) return -1;
     const long len[3] = {L.nx, L.ny, L.nz};
     const long per = (long)L.Q * D * D;
     double *gpost = malloc(sizeof(double) * per * L.nsite);
@@ -489,10 +492,13 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
                     if (kind[a] && (xyz[a] < 0 || xyz[a] >= len[a])) crossed = a;
                 if (crossed >= 0) {
                     const int io = i == 0 ? 0 : (i <= D ? i + D : i - D); /* opposite direction */
-                    const double sgn = kind[crossed] == 1 ? -1.0 : 1.0;
+                    const double wall = kind[crossed] == 1 ? 1.0 : -1.0;   /* PEC: the geometric mirror */
                     const double *src = G(&L, gpost, s, i);
                     double *dst = G(&L, g, s, io);
-                    for (int k = 0; k < D * D; k++) dst[k] = sgn * src[k];
+                    for (int b = 0; b < D; b++)
+                        for (int c = 0; c < D; c++)
+                            dst[b * D + c] = wall * (b == crossed ? -1.0 : 1.0) * (c == crossed ? -1.0 : 1.0) *
+                                             src[b * D + c];
                     continue;
                 }
                 long d = wrap(x, L.c[i][0], L.nx) + L.nx * (wrap(y, L.c[i][1], L.ny) + L.ny * wrap(z, L.c[i][2], L.nz));

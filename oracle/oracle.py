@@ -96,7 +96,7 @@ def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.
            aniso=None) -> Oracle:
     """Medium upload: eps_r, mu_r -> c_eff^2, c_L^2, w0, grad ln mu (Eq. 3).
 
-    bc (x, y, z): 0 periodic, 1 PEC wall, 2 PMC wall on both ends of that axis (2D only); layer > 0 adds an
+    bc (x, y, z): 0 periodic, 1 PEC wall, 2 PMC wall on both ends of that axis; layer > 0 adds an
     absorbing layer of that many sites inside every wall, damping 1 - gamma_max ((L - i)/L)^2 at distance i.
     dispersion: dict(wp2=, wr2=, gamma=) (arrays of the grid's shape or scalars; wr2 and gamma default to 0): one
     Drude-Lorentz pole per site, d_t J + gamma J + wr2 P = wp2 E, J = d_t P; the lattice then carries D/eps_inf
@@ -105,7 +105,7 @@ def medium(D, eps_r, mu_r=None, c_ref2=None, bc=(0, 0, 0), layer=0, gamma_max=0.
     lattice speeds c_x^2 = c_ref^2/(eps_r mu_yy), c_y^2 = c_ref^2/(eps_r mu_xx) (the oracle's reading R10)."""
     lib = _load()
     bc = tuple(int(b) for b in bc) + (0,) * (3 - len(bc))
-    assert all(b in (PERIODIC, PEC, PMC) for b in bc) and (D == 2 or not any(bc))
+    assert all(b in (PERIODIC, PEC, PMC) for b in bc) and (D == 3 or bc[2] == 0)
     assert layer >= 0 and 0.0 <= gamma_max < 1.0
     eps_r = _f64(eps_r)
     shape = eps_r.shape

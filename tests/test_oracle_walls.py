@@ -220,3 +220,84 @@ def test_walls_with_a_dispersive_pole_and_anisotropy_equal_the_mirror_image(kind
     np.testing.assert_allclose(Eb[:, :nx], Ew, rtol=0, atol=1e-12 * scale)
     np.testing.assert_allclose(Bb[:, :nx], Bw, rtol=0, atol=1e-12 * scale)
     np.testing.assert_allclose(pb["P"][:, :nx], pole["P"], rtol=0, atol=1e-12 * scale)
+
+
+def _mirror3(a, axis, s=1.0):
+    return np.concatenate([a, s * np.flip(a, axis=axis)], axis=axis)
+
+
+def _mirror_g3(g, ax, kind):
+    """3D oracle state (nz, ny, nx, 7, 3, 3) doubled across the wall normal to lattice axis `ax` (0 = x, 1 = y,
+    2 = z): directions +ax and -ax swap, component (b, c) takes (b == ax ? -1 : 1)(c == ax ? -1 : 1), the
+    geometric mirror of the tensor, times +1 for PEC and -1 for PMC."""
+    arr_axis = 2 - ax
+    gm = np.flip(g, axis=arr_axis).copy()
+    p, m = 1 + ax, 4 + ax
+    gm[..., [p, m], :, :] = gm[..., [m, p], :, :]
+    sign = np.ones((3, 3))
+    sign[ax, :] *= -1
+    sign[:, ax] *= -1
+    gm *= sign * (1.0 if kind == PEC else -1.0)
+    return np.concatenate([g, gm], axis=arr_axis)
+
+
+@pytest.mark.parametrize("bc", [(PEC, 0, 0), (0, PMC, 0), (0, 0, PEC), (PMC, PEC, 0), (PEC, PEC, PMC)])
+def test_3d_walls_equal_the_mirror_image_on_a_doubled_periodic_domain(bc):
+    """3D: the tensor's geometric mirror (PEC) or its negative (PMC) per walled axis; currents mirror with an
+    extra -1 (the source enters as eps_gab S_g, a pseudotensor): j' = (PEC: -1, PMC: +1) x R j."""
+    nz, ny, nx, nsteps = 4, 5, 6, 16
+    rng = np.random.default_rng(41 + bc[0] + 3 * bc[1] + 9 * bc[2])
+    shape = (nz, ny, nx)
+    eps = 1.5 + rng.random(shape)
+    mur = 1.0 + 0.5 * rng.random(shape)
+    E = rng.standard_normal(shape + (3,))
+    B = rng.standard_normal(shape + (3,))
+    site = np.array([0, nx - 1, nx * ny * nz - 1, 37])
+    comp = np.array([0, 1, 2, 2])
+    amp = rng.standard_normal((site.size, nsteps))
+    m = O.medium(3, eps, mur, bc=bc)
+    g = O.init_state(m, E, B)
+    O.run(m, g, nsteps, sources=dict(site=site, comp=comp, amp=amp))
+    Ew, Bw = O.fields(m, g)
+
+    ebig, mbig, g0 = eps, mur, O.init_state(m, E, B)
+    for ax in range(3):
+        if bc[ax]:
+            ebig = _mirror3(ebig, 2 - ax)
+            mbig = _mirror3(mbig, 2 - ax)
+            g0 = _mirror_g3(g0, ax, bc[ax])
+    NZ, NY, NX = ebig.shape
+    Z, rem = np.divmod(site, nx * ny)
+    Y, X = np.divmod(rem, nx)
+    bsite, bcomp, bamp = [], [], []
+    for z, y, x, c, a in zip(Z, Y, X, comp, amp):
+        for fz in ((0, 1) if bc[2] else (0,)):
+            for fy in ((0, 1) if bc[1] else (0,)):
+                for fx in ((0, 1) if bc[0] else (0,)):
+                    sgn = 1.0
+                    for ax, f in ((0, fx), (1, fy), (2, fz)):
+                        if f:
+                            sgn *= (-1.0 if bc[ax] == PEC else 1.0) * (-1.0 if c == ax else 1.0)
+                    zz = 2 * nz - 1 - z if fz else z
+                    yy = 2 * ny - 1 - y if fy else y
+                    xx = 2 * nx - 1 - x if fx else x
+                    bsite.append(xx + NX * (yy + NY * zz))
+                    bcomp.append(c)
+                    bamp.append(sgn * a)
+    mb = O.medium(3, ebig, mbig)
+    O.run(mb, g0, nsteps, sources=dict(site=np.array(bsite), comp=np.array(bcomp), amp=np.array(bamp)))
+    Eb, Bb = O.fields(mb, g0)
+    scale = max(np.abs(Ew).max(), np.abs(Bw).max())
+    np.testing.assert_allclose(Eb[:nz, :ny, :nx], Ew, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(Bb[:nz, :ny, :nx], Bw, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(m.dlnmu, mb.dlnmu[:nz, :ny, :nx], rtol=0, atol=1e-15)
+
+
+def test_3d_walls_keep_the_discrete_invariant_exactly():
+    rng = np.random.default_rng(43)
+    shape = (5, 6, 7)
+    m = O.medium(3, np.full(shape, 1.7), bc=(PEC, PMC, PEC))
+    g = O.init_state(m, rng.standard_normal(shape + (3,)), rng.standard_normal(shape + (3,)))
+    inv0 = O.diagnostics(m, g)[1]
+    O.run(m, g, 60)
+    assert abs(O.diagnostics(m, g)[1] / inv0 - 1) < 1e-13
