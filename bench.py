@@ -331,6 +331,19 @@ def other_forms(lbem, torch, p, peak, stream):
     out["f32_anisotropic"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                               "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp,
                               "lb_steps": 2000, "kernel": "step2d_gen", "mu_tensor": list(pa.aniso)}
+    # 192^3 in a PEC box with a 16-site absorbing layer (walls applied by the one-site-per-thread 3D kernel),
+    # 500 steps: 172 B/site
+    qb = W.heterogeneous_3d(192, nsteps=500)
+    qb.bc, qb.layer, qb.gamma_max = (1, 1, 1), 16, 0.2
+    s = lbem.Solver(qb.shape, stream=stream.cuda_stream)
+    ms, v, _ = _time_run(lbem, torch, s, qb, 500, stream)
+    s.close()
+    n3 = int(np.prod(qb.shape))
+    per = ms / 500
+    gbs = 172 * n3 / (per * 1e-3) / 1e9
+    out["het3d_192_box"] = {"mlups": n3 * 500 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                            "frac": gbs / peak, "bytes_per_site": 172, "variant": v, "lb_steps": 500,
+                            "bc": list(qb.bc), "layer": qb.layer}
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
     ms, v, _ = _time_run(lbem, torch, s, q, 1000, stream)

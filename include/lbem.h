@@ -162,23 +162,26 @@ lbem_status lbem_set_receivers(lbem_t *h, int n, const long long *site, const in
  * nsteps >= 0. */
 lbem_status lbem_step(lbem_t *h, int nsteps);
 
-/* Walls and absorbing layers (2D, LBEM_F32 storage; the paper treats periodic
- * domains only and leaves other boundaries open).  kind[a] (a = x, y, z; z must
- * be LBEM_BC_PERIODIC) puts a wall half a site beyond the first and the last
- * site of axis a: a population that would cross it returns to the site it
- * left in the opposite direction, times -1 (LBEM_BC_PEC) or +1 (LBEM_BC_PMC)
- * (halfway bounce-back; the state then evolves as the periodic state on a
- * domain twice as long holding the mirror image).  grad ln mu at the edge sites
+/* Walls and absorbing layers (2D and 3D, LBEM_F32 storage; the paper treats
+ * periodic domains only and leaves other boundaries open).  kind[a] (a = x, y,
+ * z; z must be LBEM_BC_PERIODIC in 2D) puts a wall half a site beyond the first
+ * and the last site of axis a: a population that would cross it returns to the
+ * site it left in the opposite direction (halfway bounce-back), each tensor
+ * component g_bc times (b == a ? -1 : 1)(c == a ? -1 : 1) for LBEM_BC_PEC (the
+ * geometric mirror) and minus that for LBEM_BC_PMC -- in 2D the single
+ * component g_xy thus gets -1 (PEC) or +1 (PMC).  The state then evolves as the
+ * periodic state on a domain twice as long holding the mirror image.  grad ln mu at the edge sites
  * uses the mirror image of mu.  layer > 0 (at most half the walled axis) adds
  * an absorbing layer inside every wall: after each collision the populations of
  * a site at distance i = 0 .. layer-1 from the wall-adjacent site are scaled by
  * 1 - gamma_max ((layer - i)/layer)^2 (both axes' factors at corners), which
  * damps E and B alike and keeps the medium's wave impedance; 0 <= gamma_max < 1.
  * Every stepping mode applies (single, two and three steps per launch, graphs):
- * after each launch a small kernel recomputes that launch's steps on the sites
- * within max(layer, 1) + steps - 1 of a wall, so results stay bit-identical
- * across modes.  All-periodic kind[] removes the walls.  LBEM_ERR_ARG for other
- * values, 3D, or 16-bit storage; LBEM_ERR_STATE after lbem_forward_record (the
+ * in 2D, after each launch a small kernel recomputes that launch's steps on the
+ * sites within max(layer, 1) + steps - 1 of a wall, so results stay
+ * bit-identical across modes; in 3D the one-site-per-thread kernel applies the
+ * walls and layers itself.  All-periodic kind[] removes the walls.
+ * LBEM_ERR_ARG for other values or 16-bit storage; LBEM_ERR_STATE after lbem_forward_record (the
  * adjoint is periodic only).  Batches (lbem_batch_create) take periodic members
  * only.  Synchronises the stream. */
 lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double gamma_max);

@@ -195,11 +195,20 @@ __global__ void __launch_bounds__(BLOCK) step3d(StepArgs a) {
     }
 }
 
+// Walls (walls.cu, in 3D): a population h_{i gamma} pulled across a wall normal to axis a is the site's own
+// h_{opp(i) gamma} times wall_sign3(kind, gamma, a): the geometric mirror of the tensor component it carries
+// (+1 when gamma == a, -1 otherwise) times +1 for PEC and -1 for PMC.
+__device__ __forceinline__ float wall_sign3(int kind, int gm, int ax) {
+    return (kind == 1 ? 1.f : -1.f) * (gm == ax ? 1.f : -1.f);
+}
+
 // One site per thread: a warp covers 32 consecutive sites of a row; the +-x
 // pulls are plain (unaligned, coalesced) loads whose overlap L1/L2 absorbs.
 // Far fewer registers than the 4-sites-per-lane kernel, so more warps per SM.
-template <bool MU>
-__global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a) {
+// With WL, pulls across walls follow wall_sign3 and the absorbing layer's
+// factor fx(x) fy(y) fz(z) scales the result.
+template <bool MU, bool WL = false>
+__global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a, Walls w) {
     const Grid &G = a.g;
     const int tpr = G.pitch;  // threads per row (pitch is a multiple of 32)
     const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
@@ -220,6 +229,23 @@ __global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a) {
         h[12 + gm] = ld(12 + gm, R.r0, xp);
         h[15 + gm] = ld(15 + gm, R.yp, x);
         h[18 + gm] = ld(18 + gm, R.zp, x);
+    }
+    int y = 0, z = 0;
+    if (WL) {
+        z = row / G.ny;
+        y = row - z * G.ny;
+        const int pos[3] = {x, y, z}, len[3] = {G.nx, G.ny, G.nz};
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            if (!w.kind[ax]) continue;
+            // +ax movers (direction 1 + ax) pulled from pos - 1, -ax movers (4 + ax) from pos + 1
+            if (pos[ax] == 0)
+#pragma unroll
+                for (int gm = 0; gm < 3; gm++) h[3 * (1 + ax) + gm] = wall_sign3(w.kind[ax], gm, ax) * ld(3 * (4 + ax) + gm, R.r0, x);
+            if (pos[ax] == len[ax] - 1)
+#pragma unroll
+                for (int gm = 0; gm < 3; gm++) h[3 * (4 + ax) + gm] = wall_sign3(w.kind[ax], gm, ax) * ld(3 * (1 + ax) + gm, R.r0, x);
+        }
     }
     const long long o = (long long)row * G.pitch + x;
     const float cl = __ldg(a.med.cL2 + o);
@@ -252,6 +278,11 @@ __global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a) {
     }
     collide3d(h, cl, shx, shy, shz);
     float *out = static_cast<float *>(a.out.data);
+    if (WL && (w.fx || w.fy || w.fz)) {
+        const float f = __fmul_rn(__fmul_rn(w.fx ? w.fx[x] : 1.f, w.fy ? w.fy[y] : 1.f), w.fz ? w.fz[z] : 1.f);
+#pragma unroll
+        for (int p = 0; p < 21; p++) h[p] = __fmul_rn(h[p], f);
+    }
 #pragma unroll
     for (int p = 0; p < 21; p++) __stcs(out + p * G.plane + o, h[p]);
 }
@@ -260,12 +291,19 @@ __global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a) {
 // registers capped for 5 resident blocks per SM
 int nvariants_3d() { return 3; }
 
-cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s) {
-    if (variant >= 1) {
+cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s, const Walls *w) {
+    const bool walls = w && (w->kind[0] || w->kind[1] || w->kind[2]);
+    if (variant >= 1 || walls) {  // walls: the one-site-per-thread kernel, which applies them
         const long long threads = (long long)a.g.nrows * a.g.pitch;
         const unsigned blocks = (unsigned)((threads + BLOCK - 1) / BLOCK);
-        if (has_mu) step3d_site<true><<<blocks, BLOCK, 0, s>>>(a);
-        else step3d_site<false><<<blocks, BLOCK, 0, s>>>(a);
+        const Walls wv = walls ? *w : Walls();
+        if (walls) {
+            if (has_mu) step3d_site<true, true><<<blocks, BLOCK, 0, s>>>(a, wv);
+            else step3d_site<false, true><<<blocks, BLOCK, 0, s>>>(a, wv);
+        } else {
+            if (has_mu) step3d_site<true><<<blocks, BLOCK, 0, s>>>(a, wv);
+            else step3d_site<false><<<blocks, BLOCK, 0, s>>>(a, wv);
+        }
         return cudaGetLastError();
     }
     const long long warps = (long long)a.g.nrows * (a.g.nchunk_pad / 32);
@@ -276,8 +314,10 @@ cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStre
 }
 
 // ------------------------------------------------------------------ initial state: buf_{i gamma}(x) = h^(0)_{i gamma}(x + c_i)
+// (with walls, where x + c_i lies beyond a wall normal to axis a, buf_{i gamma}(x) is what site x pulls back:
+// wall_sign3 times h^(0)_{opp(i) gamma}(x))
 __global__ void __launch_bounds__(BLOCK) init3d(Grid G, PopBuf out, const float *cL2, const float *E, const float *B,
-                                                long long nsite) {
+                                                long long nsite, Walls w) {
     const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
     const int row = (int)(tid / G.nchunk_pad);
     const int c = (int)(tid - (long long)row * G.nchunk_pad);
@@ -290,8 +330,19 @@ __global__ void __launch_bounds__(BLOCK) init3d(Grid G, PopBuf out, const float 
         for (int j = 0; j < 4; j++) {
             const int x = 4 * c + j;
             if (x >= G.nx) break;
-            const int xs = (x + cc[i][0] + G.nx) % G.nx, ys = (y + cc[i][1] + G.ny) % G.ny,
-                      zs = (z + cc[i][2] + G.nz) % G.nz;
+            int xs = x + cc[i][0], ys = y + cc[i][1], zs = z + cc[i][2], ie = i, wax = -1;
+            const int pos[3] = {xs, ys, zs}, len[3] = {G.nx, G.ny, G.nz};
+            for (int ax = 0; ax < 3; ax++)
+                if (w.kind[ax] && (pos[ax] < 0 || pos[ax] >= len[ax])) wax = ax;
+            if (wax >= 0) {  // beyond a wall: the site's own opposite population
+                xs = x;
+                ys = y;
+                zs = z;
+                ie = i == 0 ? 0 : (i <= 3 ? i + 3 : i - 3);
+            }
+            xs = (xs + G.nx) % G.nx;
+            ys = (ys + G.ny) % G.ny;
+            zs = (zs + G.nz) % G.nz;
             const long long sd = ((long long)zs * G.ny + ys) * G.nx + xs;
             const float cl = cL2[((long long)zs * G.ny + ys) * G.pitch + xs];
             float e[3], b[3];
@@ -299,25 +350,35 @@ __global__ void __launch_bounds__(BLOCK) init3d(Grid G, PopBuf out, const float 
                 e[k] = E ? E[k * nsite + sd] : 0.f;
                 b[k] = B ? 0.5f * B[k * nsite + sd] : 0.f;  // equilibrium uses B/(D-1)
             }
-            const float cxb[3] = {cc[i][1] * b[2] - cc[i][2] * b[1], cc[i][2] * b[0] - cc[i][0] * b[2],
-                                  cc[i][0] * b[1] - cc[i][1] * b[0]};
-            const float wc = (i == 0) ? (1.f - 3.f * cl) / cl : 0.5f;
-            for (int k = 0; k < 3; k++) set(v[k], j, wc * (-e[k] + cxb[k]));
+            const float cxb[3] = {cc[ie][1] * b[2] - cc[ie][2] * b[1], cc[ie][2] * b[0] - cc[ie][0] * b[2],
+                                  cc[ie][0] * b[1] - cc[ie][1] * b[0]};
+            const float wc = (ie == 0) ? (1.f - 3.f * cl) / cl : 0.5f;
+            for (int k = 0; k < 3; k++) {
+                const float sg = wax >= 0 ? wall_sign3(w.kind[wax], k, wax) : 1.f;
+                set(v[k], j, sg * (wc * (-e[k] + cxb[k])));
+            }
         }
         for (int k = 0; k < 3; k++) Codec<LBEM_F32>::store4(out, 3 * i + k, row, c, v[k]);
     }
 }
 
+static Walls walls_of(const lbem_t *h) {
+    Walls w;
+    for (int a = 0; a < 3; a++) w.kind[a] = h->bc[a];
+    return w;
+}
+
 cudaError_t launch_init_3d(const lbem_t *h, const float *E, const float *B, cudaStream_t s) {
     const Grid &G = h->grid;
     const long long n = (long long)G.nrows * G.nchunk_pad;
-    init3d<<<(unsigned)((n + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(G, h->buf[h->cur], h->cL2, E, B, h->nsite);
+    init3d<<<(unsigned)((n + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(G, h->buf[h->cur], h->cL2, E, B, h->nsite,
+                                                                 walls_of(h));
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ field extraction
 __global__ void __launch_bounds__(BLOCK) fields3d(Grid G, PopBuf in, const float *cL2, float *E, float *B,
-                                                  long long nsite) {
+                                                  long long nsite, Walls w) {
     const int lane = threadIdx.x & 31;
     const long long wg = ((long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
     const int wpr = G.nchunk_pad >> 5;
@@ -333,6 +394,21 @@ __global__ void __launch_bounds__(BLOCK) fields3d(Grid G, PopBuf in, const float
         if (x >= G.nx) break;
         float h[21];
         for (int p = 0; p < 21; p++) h[p] = get(v[p], j);
+        {  // pulls across walls
+            const int z = row / G.ny, y = row - z * G.ny;
+            const int pos[3] = {x, y, z}, len[3] = {G.nx, G.ny, G.nz};
+            for (int ax = 0; ax < 3; ax++) {
+                if (!w.kind[ax]) continue;
+                for (int gm = 0; gm < 3; gm++) {
+                    if (pos[ax] == 0)
+                        h[3 * (1 + ax) + gm] = wall_sign3(w.kind[ax], gm, ax) *
+                                               Codec<LBEM_F32>::load1(in, 3 * (4 + ax) + gm, row, x);
+                    if (pos[ax] == len[ax] - 1)
+                        h[3 * (4 + ax) + gm] = wall_sign3(w.kind[ax], gm, ax) *
+                                               Codec<LBEM_F32>::load1(in, 3 * (1 + ax) + gm, row, x);
+                }
+            }
+        }
         const Mom3 m = moments3(h);
         const long long sd = (long long)row * G.nx + x;
         const float q = get(cl, j);
@@ -352,21 +428,32 @@ __global__ void __launch_bounds__(BLOCK) fields3d(Grid G, PopBuf in, const float
 cudaError_t launch_fields_3d(const lbem_t *h, float *E, float *B, cudaStream_t s) {
     const Grid &G = h->grid;
     const long long warps = (long long)G.nrows * (G.nchunk_pad / 32);
-    fields3d<<<(unsigned)((warps * 32 + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(G, h->buf[h->cur], h->cL2, E, B, h->nsite);
+    fields3d<<<(unsigned)((warps * 32 + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(G, h->buf[h->cur], h->cL2, E, B, h->nsite,
+                                                                          walls_of(h));
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ FP64 diagnostics
-__device__ __forceinline__ double pop3d(const PopBuf &in, const Grid &G, int p, int x, int y, int z) {
-    const int i = p / 3;
+__device__ __forceinline__ double pop3d(const PopBuf &in, const Grid &G, const Walls &w, int p, int x, int y, int z) {
+    const int i = p / 3, gm = p - 3 * i;
     const int cc[7][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {-1, 0, 0}, {0, -1, 0}, {0, 0, -1}};
-    const int xs = (x - cc[i][0] + G.nx) % G.nx, ys = (y - cc[i][1] + G.ny) % G.ny, zs = (z - cc[i][2] + G.nz) % G.nz;
+    const int u[3] = {x - cc[i][0], y - cc[i][1], z - cc[i][2]}, len[3] = {G.nx, G.ny, G.nz};
+    for (int ax = 0; ax < 3; ax++)  // across a wall: the site's own opposite population, signed
+        if (w.kind[ax] && (u[ax] < 0 || u[ax] >= len[ax])) {
+            const int io = i <= 3 ? i + 3 : i - 3;
+            return (double)wall_sign3(w.kind[ax], gm, ax) *
+                   (double)Codec<LBEM_F32>::load1(in, 3 * io + gm, z * G.ny + y, x);
+        }
+    const int xs = (u[0] + G.nx) % G.nx, ys = (u[1] + G.ny) % G.ny, zs = (u[2] + G.nz) % G.nz;
     return (double)Codec<LBEM_F32>::load1(in, p, zs * G.ny + ys, xs);
 }
 
-__device__ __forceinline__ double bcomp3d(const PopBuf &in, const Grid &G, int comp, int x, int y, int z) {
+__device__ __forceinline__ double bcomp3d(const PopBuf &in, const Grid &G, const Walls &w, int comp, int x, int y,
+                                          int z) {
     // B_x = R_yz - R_zy, B_y = R_zx - R_xz, B_z = R_xy - R_yx; R_{g k} = h[(1+k)*3+g] - h[(4+k)*3+g]
-    auto Rgk = [&](int g, int k) { return pop3d(in, G, (1 + k) * 3 + g, x, y, z) - pop3d(in, G, (4 + k) * 3 + g, x, y, z); };
+    auto Rgk = [&](int g, int k) {
+        return pop3d(in, G, w, (1 + k) * 3 + g, x, y, z) - pop3d(in, G, w, (4 + k) * 3 + g, x, y, z);
+    };
     if (comp == 0) return Rgk(1, 2) - Rgk(2, 1);
     if (comp == 1) return Rgk(2, 0) - Rgk(0, 2);
     return Rgk(0, 1) - Rgk(1, 0);
@@ -384,7 +471,7 @@ __device__ __forceinline__ double block_sum3(double v, double *sh) {
     return r;
 }
 
-__global__ void __launch_bounds__(BLOCK) diag3d(Grid G, PopBuf in, const float *cL2, double *partials) {
+__global__ void __launch_bounds__(BLOCK) diag3d(Grid G, PopBuf in, const float *cL2, double *partials, Walls w) {
     __shared__ double sh[BLOCK / 32];
     double en = 0.0, inv = 0.0, dv = 0.0;
     const long long nsite = (long long)G.nx * G.ny * G.nz;
@@ -394,13 +481,13 @@ __global__ void __launch_bounds__(BLOCK) diag3d(Grid G, PopBuf in, const float *
         const int y = (int)(rr % G.ny), z = (int)(rr / G.ny);
         double h[21], sg[3] = {0.0, 0.0, 0.0};
         for (int p = 0; p < 21; p++) {
-            h[p] = pop3d(in, G, p, x, y, z);
+            h[p] = pop3d(in, G, w, p, x, y, z);
             sg[p % 3] += h[p];
         }
         const double cl = (double)cL2[rr * G.pitch + x];
         const double ce2 = 0.5 * cl;
         double b[3];
-        for (int k = 0; k < 3; k++) b[k] = bcomp3d(in, G, k, x, y, z);
+        for (int k = 0; k < 3; k++) b[k] = bcomp3d(in, G, w, k, x, y, z);
         for (int k = 0; k < 3; k++) {
             const double e = -cl * sg[k];
             en += b[k] * b[k] + e * e / ce2;
@@ -411,9 +498,11 @@ __global__ void __launch_bounds__(BLOCK) diag3d(Grid G, PopBuf in, const float *
         if (w0 != 0.0)
             for (int p = 0; p < 3; p++) q += h[p] * h[p] / w0;
         inv += 2.0 * q;  // g_ab and g_ba both count
-        const double div = 0.5 * (bcomp3d(in, G, 0, (x + 1) % G.nx, y, z) - bcomp3d(in, G, 0, (x - 1 + G.nx) % G.nx, y, z)) +
-                           0.5 * (bcomp3d(in, G, 1, x, (y + 1) % G.ny, z) - bcomp3d(in, G, 1, x, (y - 1 + G.ny) % G.ny, z)) +
-                           0.5 * (bcomp3d(in, G, 2, x, y, (z + 1) % G.nz) - bcomp3d(in, G, 2, x, y, (z - 1 + G.nz) % G.nz));
+        // (periodic central differences, also next to walls)
+        const double div =
+            0.5 * (bcomp3d(in, G, w, 0, (x + 1) % G.nx, y, z) - bcomp3d(in, G, w, 0, (x - 1 + G.nx) % G.nx, y, z)) +
+            0.5 * (bcomp3d(in, G, w, 1, x, (y + 1) % G.ny, z) - bcomp3d(in, G, w, 1, x, (y - 1 + G.ny) % G.ny, z)) +
+            0.5 * (bcomp3d(in, G, w, 2, x, y, (z + 1) % G.nz) - bcomp3d(in, G, w, 2, x, y, (z - 1 + G.nz) % G.nz));
         dv += div * div;
     }
     const double a = block_sum3(en, sh), b = block_sum3(inv, sh), c = block_sum3(dv, sh);
@@ -425,7 +514,7 @@ __global__ void __launch_bounds__(BLOCK) diag3d(Grid G, PopBuf in, const float *
 }
 
 cudaError_t launch_diag_3d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s) {
-    diag3d<<<nblocks, BLOCK, 0, s>>>(h->grid, h->buf[h->cur], h->cL2, partials);
+    diag3d<<<nblocks, BLOCK, 0, s>>>(h->grid, h->buf[h->cur], h->cL2, partials, walls_of(h));
     return cudaGetLastError();
 }
 

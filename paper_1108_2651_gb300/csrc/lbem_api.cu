@@ -119,10 +119,10 @@ StepArgs step_args(const lbem_t *h, int cur_in) {
 
 static Walls handle_walls(const lbem_t *h) {
     Walls w;
-    w.kind[0] = h->bc[0];
-    w.kind[1] = h->bc[1];
+    for (int a = 0; a < 3; a++) w.kind[a] = h->bc[a];
     w.fx = h->bc[0] ? h->d_fx : nullptr;
     w.fy = h->bc[1] ? h->d_fy : nullptr;
+    w.fz = h->bc[2] ? h->d_fz : nullptr;
     return w;
 }
 
@@ -141,7 +141,8 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
         return launch_step_2d_gen(a, handle_walls(h), q, h->stream);
     }
     if (h->dim == 2) return launch_step_2d(a, h->storage, h->has_mu, variant, h->stream);
-    return launch_step_3d(a, h->has_mu, variant, h->stream);
+    const Walls w = handle_walls(h);
+    return launch_step_3d(a, h->has_mu, variant, h->stream, &w);  // walls and layers applied in the kernel
 }
 
 // what a captured graph depends on besides t, nsteps and the buffer: kernel variant and two-step shape
@@ -168,7 +169,7 @@ static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two
 // With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu); the
 // general kernel applies walls and layers itself.
 static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
-    if (!h->walls() || h->general()) return cudaSuccess;
+    if (!h->walls() || h->general() || h->dim != 2) return cudaSuccess;
     return launch_edge_2d(a, handle_walls(h), h->d_tiles[k], h->ntiles[k],
                           h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->stream);
 }
@@ -334,6 +335,7 @@ void lbem_destroy(lbem_t *h) {
     for (void *p : {(void *)h->pool, (void *)h->cL2, (void *)h->mu, (void *)h->dlnmu, (void *)h->d_rowptr,
                     (void *)h->d_ev, (void *)h->d_amp, (void *)h->d_traces, (void *)h->d_partials,
                     (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage, (void *)h->d_fx, (void *)h->d_fy,
+                    (void *)h->d_fz,
                     (void *)h->d_wp2, (void *)h->d_wr2, (void *)h->d_gam, (void *)h->d_J, (void *)h->d_P})
         gfree(h, p);
     for (int k = 1; k <= 3; k++) gfree(h, h->d_tiles[k]);
@@ -626,19 +628,20 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
         if (kind[a] < LBEM_BC_PERIODIC || kind[a] > LBEM_BC_PMC)
             return fail(LBEM_ERR_ARG, "lbem_set_boundaries: kind must be LBEM_BC_PERIODIC, _PEC or _PMC");
     const bool any = kind[0] || kind[1] || kind[2];
-    if (any && (h->dim != 2 || kind[2]))
-        return fail(LBEM_ERR_ARG, "lbem_set_boundaries: walls exist for 2D grids (x and y)");
+    if (any && h->dim == 2 && kind[2]) return fail(LBEM_ERR_ARG, "lbem_set_boundaries: a 2D grid has no z walls");
     if (any && h->storage != LBEM_F32) return fail(LBEM_ERR_ARG, "lbem_set_boundaries: walls need LBEM_F32 storage");
     if (layer < 0 || !(gamma_max >= 0.0 && gamma_max < 1.0))
         return fail(LBEM_ERR_ARG, "lbem_set_boundaries: layer >= 0 and 0 <= gamma_max < 1");
     if (layer > 0 && !any) return fail(LBEM_ERR_ARG, "lbem_set_boundaries: an absorbing layer needs a wall");
-    if ((kind[0] && 2 * layer > h->grid.nx) || (kind[1] && 2 * layer > h->grid.ny))
+    if ((kind[0] && 2 * layer > h->grid.nx) || (kind[1] && 2 * layer > h->grid.ny) ||
+        (kind[2] && 2 * layer > h->grid.nz))
         return fail(LBEM_ERR_ARG, "lbem_set_boundaries: layer wider than half the walled axis");
     if (h->adj) return fail(LBEM_ERR_STATE, "lbem_set_boundaries: a recorded adjoint run exists (periodic only)");
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     gfree(h, h->d_fx);
     gfree(h, h->d_fy);
-    h->d_fx = h->d_fy = nullptr;
+    gfree(h, h->d_fz);
+    h->d_fx = h->d_fy = h->d_fz = nullptr;
     for (int k = 1; k <= 3; k++) {
         gfree(h, h->d_tiles[k]);
         h->d_tiles[k] = nullptr;
@@ -649,13 +652,13 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
     h->layer = any ? layer : 0;
     h->gamma_max = any ? gamma_max : 0.0;
     drop_graph(h);
-    if (h->has_mu && h->dim == 2) LBEM_CUDA(launch_medium_grad_walls(h, h->stream));  // grad ln mu at the walls
+    if (h->has_mu) LBEM_CUDA(launch_medium_grad_walls(h, h->stream));  // grad ln mu at the walls
     if (!any) return LBEM_OK;
     // layer factors 1 - gamma_max ((L - i)/L)^2 at distance i from the wall-adjacent site, per column / row (the
     // column table padded with 1 to the row pitch, for 16-byte loads)
-    const int len[2] = {h->grid.nx, h->grid.ny}, alloc[2] = {h->grid.pitch, h->grid.ny};
-    float **dst[2] = {&h->d_fx, &h->d_fy};
-    for (int a = 0; a < 2; a++) {
+    const int len[3] = {h->grid.nx, h->grid.ny, h->grid.nz}, alloc[3] = {h->grid.pitch, h->grid.ny, h->grid.nz};
+    float **dst[3] = {&h->d_fx, &h->d_fy, &h->d_fz};
+    for (int a = 0; a < h->dim; a++) {
         if (!kind[a] || layer == 0) continue;
         std::vector<float> f(alloc[a], 1.f);
         for (int v = 0; v < len[a]; v++) {
@@ -666,7 +669,7 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
         LBEM_CUDA(gmalloc(h, (void **)dst[a], sizeof(float) * alloc[a], "layer factors"));
         LBEM_CUDA(cudaMemcpy(*dst[a], f.data(), sizeof(float) * alloc[a], cudaMemcpyHostToDevice));
     }
-    for (int k = 1; k <= 3; k++) {
+    for (int k = 1; k <= 3 && h->dim == 2; k++) {  // 2D: the edge kernel's tiles (the 3D kernel applies walls)
         const std::vector<EdgeTile> t = edge_tiles(h->grid, h->bc, h->layer, k);
         h->ntiles[k] = (int)t.size();
         h->tile_smem[k] = edge_smem_bytes(k, t, false);

@@ -300,8 +300,8 @@ struct Medium {
 // Walls and absorbing layers (walls.cu): per axis x, y 0 = periodic, 1 = PEC wall, 2 = PMC wall; layer
 // damping factors per column / row (null: no layer on that axis).
 struct Walls {
-    int kind[2] = {0, 0};
-    const float *fx = nullptr, *fy = nullptr;
+    int kind[3] = {0, 0, 0};
+    const float *fx = nullptr, *fy = nullptr, *fz = nullptr;
 };
 // What the general single-step kernel (general.cu) adds to a step: one Drude-Lorentz pole per site (parameters
 // and state as planes with the grid's pitch, J at t - 1/2, P at t; wp2 null: no pole) and a uniform in-plane permeability tensor
@@ -447,7 +447,7 @@ struct lbem {
     int bc[3] = {0, 0, 0};
     int layer = 0;
     double gamma_max = 0.0;
-    float *d_fx = nullptr, *d_fy = nullptr;
+    float *d_fx = nullptr, *d_fy = nullptr, *d_fz = nullptr;
     lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     int ntiles[4] = {0, 0, 0, 0};
     // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, planes (pitch layout)
@@ -505,7 +505,7 @@ cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);
 // 3D (kernels3d.cu)
 int nvariants_3d();
-cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s);
+cudaError_t launch_step_3d(const StepArgs &a, bool has_mu, int variant, cudaStream_t s, const Walls *w = nullptr);
 cudaError_t launch_init_3d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_3d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_3d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);

@@ -237,28 +237,36 @@ cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_
 }
 
 // grad ln mu with walls: at the first / last site of a walled axis the missing neighbour is the mirror image
-// (the site itself), as on the doubled periodic domain the walls stand for.
-__global__ void medium_grad_walls(Grid G, int kx, int ky, const float *mu_p, float *dlnmu) {
-    const long long n = (long long)G.nx * G.ny;
+// (the site itself), as on the doubled periodic domain the walls stand for (2D and 3D).
+__global__ void medium_grad_walls(Grid G, int D, int kx, int ky, int kz, const float *mu_p, float *dlnmu) {
+    const long long n = (long long)G.nx * G.nrows;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(s / G.nx), x = (int)(s - (long long)y * G.nx);
+        const long long row = s / G.nx;
+        const int x = (int)(s - row * G.nx);
+        const int z = (int)(row / G.ny), y = (int)(row - (long long)z * G.ny);
         auto nb = [](int v, int d, int len, int kind) {
             const int u = v + d;
             if (!kind) return (u + len) % len;
             return u < 0 ? 0 : (u >= len ? len - 1 : u);
         };
-        auto at = [&](int xx, int yy) { return log((double)mu_p[(long long)yy * G.pitch + xx]); };
-        const double gx = 0.5 * (at(nb(x, 1, G.nx, kx), y) - at(nb(x, -1, G.nx, kx), y));
-        const double gy = 0.5 * (at(x, nb(y, 1, G.ny, ky)) - at(x, nb(y, -1, G.ny, ky)));
-        dlnmu[(long long)y * G.pitch + x] = (float)gx;
-        dlnmu[G.plane + (long long)y * G.pitch + x] = (float)gy;
+        auto at = [&](int xx, int yy, int zz) {
+            return log((double)mu_p[((long long)zz * G.ny + yy) * G.pitch + xx]);
+        };
+        const double gx = 0.5 * (at(nb(x, 1, G.nx, kx), y, z) - at(nb(x, -1, G.nx, kx), y, z));
+        const double gy = 0.5 * (at(x, nb(y, 1, G.ny, ky), z) - at(x, nb(y, -1, G.ny, ky), z));
+        dlnmu[row * G.pitch + x] = (float)gx;
+        dlnmu[G.plane + row * G.pitch + x] = (float)gy;
+        if (D == 3) {
+            const double gz = 0.5 * (at(x, y, nb(z, 1, G.nz, kz)) - at(x, y, nb(z, -1, G.nz, kz)));
+            dlnmu[2 * G.plane + row * G.pitch + x] = (float)gz;
+        }
     }
 }
 
 cudaError_t launch_medium_grad_walls(const lbem_t *h, cudaStream_t s) {
     const long long n = h->nsite;
     const unsigned blocks = (unsigned)std::min<long long>(4096, std::max<long long>(1, (n + 255) / 256));
-    medium_grad_walls<<<blocks, 256, 0, s>>>(h->grid, h->bc[0], h->bc[1], h->mu, h->dlnmu);
+    medium_grad_walls<<<blocks, 256, 0, s>>>(h->grid, h->dim, h->bc[0], h->bc[1], h->bc[2], h->mu, h->dlnmu);
     return cudaGetLastError();
 }
 
