@@ -304,6 +304,21 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save);
  * device-side instrumentation. */
 lbem_status lbem_check_guards(lbem_t *h);
 
+/* Rows of one population plane of the current state, for spatial domain
+ * decomposition: the state holds post-collision values laid out for pull
+ * streaming (a site pulls population p from its neighbour across -c_p), so a
+ * slab that keeps one ghost row on either side stays exact if, after each
+ * single step, its ghost rows receive the populations the neighbouring slabs
+ * send across the cut (2D: plane 2 of the last real row upwards, plane 4 of the
+ * first real row downwards; 3D, slabs in z: planes 9-11 upwards and 18-20
+ * downwards, ny rows each).  Copies nrows rows (2D: row = y; 3D: row = y + ny z)
+ * starting at row0 of plane `plane` to (to_state = 0) or from (to_state = 1)
+ * buf, [nrows][nx] floats, host or device.  LBEM_F32 storage; a decomposed
+ * handle must step one step per launch (lbem_set_temporal_blocking(h, 1, -1)).
+ * LBEM_ERR_ARG for planes or rows out of range.  Host buffers synchronise the
+ * stream. */
+lbem_status lbem_rows(lbem_t *h, int plane, int row0, int nrows, float *buf, int to_state);
+
 /* ---------------------------------------------------------------- adjoint (not in the paper) */
 
 /* Forward run that records what the adjoint needs: advances nsteps steps from

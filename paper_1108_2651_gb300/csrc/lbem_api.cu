@@ -842,6 +842,22 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
     return LBEM_OK;
 }
 
+lbem_status lbem_rows(lbem_t *h, int plane, int row0, int nrows, float *buf, int to_state) {
+    if (!h || !buf) return fail(LBEM_ERR_ARG, "null argument");
+    if (h->storage != LBEM_F32) return fail(LBEM_ERR_ARG, "lbem_rows: LBEM_F32 storage only");
+    if (plane < 0 || plane >= h->npop || nrows < 0 || row0 < 0 || row0 + nrows > h->grid.nrows)
+        return fail(LBEM_ERR_ARG, "lbem_rows: plane or rows out of range");
+    if (nrows == 0) return LBEM_OK;
+    const PopBuf &p = h->buf[h->cur];
+    float *base = static_cast<float *>(p.data) + (long long)plane * p.plane + (long long)row0 * p.pitch;
+    const size_t w = sizeof(float) * (size_t)h->grid.nx, pitch = sizeof(float) * (size_t)p.pitch;
+    if (to_state) LBEM_CUDA(cudaMemcpy2DAsync(base, pitch, buf, w, w, nrows, cudaMemcpyDefault, h->stream));
+    else LBEM_CUDA(cudaMemcpy2DAsync(buf, w, base, pitch, w, nrows, cudaMemcpyDefault, h->stream));
+    if (!is_device_ptr(buf)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
+    drop_graph(h);
+    return LBEM_OK;
+}
+
 lbem_status lbem_check_guards(lbem_t *h) {
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     LBEM_CUDA(cudaStreamSynchronize(h->stream));

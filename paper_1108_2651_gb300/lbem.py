@@ -54,6 +54,7 @@ _SIGS = {
     "lbem_set_boundaries": [_VP, C.POINTER(_I), _I, _D],
     "lbem_set_dispersion": [_VP, _VP, _VP, _VP],
     "lbem_set_medium_aniso": [_VP, _VP, _D, _D],
+    "lbem_rows": [_VP, _I, _I, _I, _VP, _I],
     "lbem_get_boundaries": [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)],
     "lbem_time": [_VP, C.POINTER(_LL)],
     "lbem_fields": [_VP, _VP, _VP],
@@ -214,6 +215,12 @@ def lbem_set_boundaries(h, kind, layer=0, gamma_max=0.0):
     """kind: boundary per axis (x, y[, z]): BC_PERIODIC, BC_PEC or BC_PMC."""
     k = (_I * 3)(*(list(kind) + [0] * (3 - len(kind))))
     _check(load().lbem_set_boundaries(h, k, int(layer), float(gamma_max)))
+
+
+def lbem_rows(h, plane, row0, nrows, buf, to_state):
+    """Copy nrows rows of one population plane of the current state to (to_state False) or from (True) buf."""
+    _check(load().lbem_rows(h, int(plane), int(row0), int(nrows), _ptr(buf, writable=not to_state),
+                            1 if to_state else 0))
 
 
 def lbem_set_medium_aniso(h, eps_r, mu_xx, mu_yy):

@@ -1,0 +1,165 @@
+"""Spatial domain decomposition (slabs along the slowest axis, one ghost layer, halo exchange after each step).
+
+On the host: world-size-2 gloo ranks, each stepping its slab with the FP64 oracle and exchanging the
+populations that cross the cuts through torch.distributed, must reproduce the single-domain oracle bit for bit
+(2D and 3D, heterogeneous eps and mu, sources and receivers on either slab).  On the GPU: two slabs stepped by the
+library in one process (halo copies between them) must reproduce the single-domain library run bit for bit.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _problem(D, shape, seed, nsteps):
+    sys.path.insert(0, ROOT)
+    from paper_1108_2651_gb300 import workloads as W
+
+    eps, mu = W.random_medium(shape, seed, mu=True)
+    p = W.Problem("decomp", D, shape, eps, mu, nsteps)
+    p.E0, p.B0 = W.random_fields(shape, seed + 1, 0.3)
+    if D == 2:
+        p.E0[..., :2] = 0
+        p.B0[..., 2] = 0
+    rng = np.random.default_rng(seed + 2)
+    n = int(np.prod(shape))
+    per_layer = int(np.prod(shape[1:]))
+    # sources and receivers next to every cut and in the middle of the slabs
+    picks = np.concatenate([np.arange(per_layer), n - per_layer + np.arange(per_layer),
+                            (shape[0] // 2) * per_layer + np.arange(per_layer)])
+    p.src_site = np.unique(rng.choice(picks, 6)).astype(np.int64)
+    p.src_comp = (np.full(p.src_site.size, 2) if D == 2 else np.arange(p.src_site.size) % 3).astype(np.int32)
+    p.src_amp = rng.standard_normal((p.src_site.size, nsteps))
+    p.rec_site = np.unique(np.concatenate([rng.choice(picks, 6), rng.integers(0, n, 4)])).astype(np.int64)
+    p.rec_comp = (np.arange(p.rec_site.size) % (3 if D == 2 else 6) + (2 if D == 2 else 0)).astype(np.int32)
+    return p
+
+
+class OracleSlab:
+    """A slab stepped by the oracle (push streaming: after a step the ghost layers hold what crossed the cuts)."""
+
+    def __init__(self, q, count):
+        import oracle as O
+
+        f = lambda a: None if a is None else np.asarray(a, np.float32).astype(np.float64)
+        self.O = O
+        self.D, self.count = q.D, count
+        self.m = O.medium(q.D, f(q.eps_r), f(q.mu_r))
+        self.g = O.init_state(self.m, f(q.E0), f(q.B0))
+        src = q.sources()
+        self.src = None if src is None else dict(src, amp=f(src["amp"]))
+        self.rec = q.receivers()
+        self.up, self.down = (2, 4) if q.D == 2 else (3, 6)  # oracle directions moving up / down the slab axis
+        self.t = 0
+        self.tr = []
+
+    def step(self):
+        self.tr.append(self.O.run(self.m, self.g, 1, t0=self.t, sources=self.src, receivers=self.rec))
+        self.t += 1
+
+    def halo_out(self, up):
+        import torch
+
+        layer, d = (self.count + 1, self.up) if up else (0, self.down)
+        return torch.from_numpy(np.ascontiguousarray(self.g[layer, ..., d, :, :]))
+
+    def halo_in(self, from_below, buf):
+        layer, d = (1, self.up) if from_below else (self.count, self.down)
+        self.g[layer, ..., d, :, :] = buf.numpy()
+
+    def fields(self):
+        E, B = self.O.fields(self.m, self.g)
+        return E[1:self.count + 1], B[1:self.count + 1]
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, D, shape, nsteps, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      OMP_NUM_THREADS="2")
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch.distributed as dist
+
+    from paper_1108_2651_gb300 import decomp
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = _problem(D, shape, 7 + D, nsteps)
+    loc, start, count, recs = decomp.local_problem(p, rank, world)
+    slab = OracleSlab(loc, count)
+    decomp.step_dist(slab, rank, world, nsteps, host=True)
+    E, B = slab.fields()
+    tr = np.concatenate(slab.tr, axis=1) if slab.tr and slab.tr[0].size else np.zeros((0, nsteps))
+    dist.destroy_process_group()
+    q.put((rank, start, count, E, B, recs, tr))
+
+
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("D,shape", [(2, (11, 13)), (3, (7, 4, 5))])
+def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape):
+    import torch.multiprocessing as mp
+
+    import oracle as O
+
+    nsteps = 12
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, D, shape, nsteps, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    got = [q.get(timeout=300) for _ in range(2)]
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    p = _problem(D, shape, 7 + D, nsteps)
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    m = O.medium(D, f(p.eps_r), f(p.mu_r))
+    g = O.init_state(m, f(p.E0), f(p.B0))
+    tr = O.run(m, g, nsteps, sources=dict(p.sources(), amp=f(p.src_amp)), receivers=p.receivers())
+    E, B = O.fields(m, g)
+    for rank, start, count, Es, Bs, recs, trs in got:
+        np.testing.assert_array_equal(Es, E[start:start + count])
+        np.testing.assert_array_equal(Bs, B[start:start + count])
+        if recs.size:
+            np.testing.assert_array_equal(trs, tr[recs])
+    assert sum(c for _, _, c, *_ in got) == shape[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("D,shape,world", [(2, (40, 70), 2), (2, (37, 130), 3), (3, (16, 6, 40), 2),
+                                           (2, (9, 33), 1)])
+def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world):
+    import torch
+
+    from gpu_helpers import gpu_run
+    from paper_1108_2651_gb300 import decomp
+
+    nsteps = 15
+    p = _problem(D, shape, 21 + D, nsteps)
+    ref = gpu_run(p, steps_per_pass=1)
+    slabs, parts = [], []
+    for r in range(world):
+        loc, start, count, recs = decomp.local_problem(p, r, world)
+        slabs.append(decomp.LbemSlab(loc, count))
+        parts.append((start, count, recs, loc.rec_site.size))
+    decomp.step_local(slabs, nsteps)
+    torch.cuda.synchronize()
+    for s, (start, count, recs, nrec) in zip(slabs, parts):
+        E, B = s.fields()
+        np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0][start:start + count])
+        np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1][start:start + count])
+        if nrec:
+            np.testing.assert_array_equal(s.traces(nrec).cpu().double().numpy(), ref[2][recs])
+        lbem.lbem_check_guards(s.s.h)
+        s.close()
