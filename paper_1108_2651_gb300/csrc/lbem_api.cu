@@ -854,8 +854,7 @@ lbem_status lbem_rows(lbem_t *h, int plane, int row0, int nrows, float *buf, int
     if (to_state) LBEM_CUDA(cudaMemcpy2DAsync(base, pitch, buf, w, w, nrows, cudaMemcpyDefault, h->stream));
     else LBEM_CUDA(cudaMemcpy2DAsync(buf, w, base, pitch, w, nrows, cudaMemcpyDefault, h->stream));
     if (!is_device_ptr(buf)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
-    drop_graph(h);
-    return LBEM_OK;
+    return LBEM_OK;  // (a cached graph depends on the buffers and parameters, not on their contents)
 }
 
 lbem_status lbem_check_guards(lbem_t *h) {

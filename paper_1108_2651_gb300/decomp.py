@@ -128,8 +128,11 @@ def exchange_dist(slab, rank, world, host=False):
         slab.halo_in(False, down)
         return
     from_below, from_above = up.clone(), down.clone()
-    ops = [dist.P2POp(dist.isend, up, (rank + 1) % world), dist.P2POp(dist.isend, down, (rank - 1) % world),
-           dist.P2POp(dist.irecv, from_below, (rank - 1) % world), dist.P2POp(dist.irecv, from_above, (rank + 1) % world)]
+    UP, DOWN = 1, 2  # message tags: with two ranks both neighbours are the same rank
+    ops = [dist.P2POp(dist.isend, up, (rank + 1) % world, tag=UP),
+           dist.P2POp(dist.isend, down, (rank - 1) % world, tag=DOWN),
+           dist.P2POp(dist.irecv, from_below, (rank - 1) % world, tag=UP),
+           dist.P2POp(dist.irecv, from_above, (rank + 1) % world, tag=DOWN)]
     for req in dist.batch_isend_irecv(ops):
         req.wait()
     slab.halo_in(True, from_below)
