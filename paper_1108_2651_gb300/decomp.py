@@ -154,12 +154,13 @@ def step_dist(slab, rank, world, nsteps, host=False):
         exchange_dist(slab, rank, world, host)
 
 
-def energy(slabs_fields, eps_r_slabs, c_ref2):
-    """FP64 field energy sum (B^2 + E^2 / c_eff^2) over the real layers of slabs (2D: c_eff^2 = c_ref2 / eps_r,
-    uniform mu); to be summed over ranks (an FP64 all-reduce) when the slabs live on several."""
-    total = 0.0
-    for (E, B), eps in zip(slabs_fields, eps_r_slabs):
-        e = E.double().cpu().numpy()
-        b = B.double().cpu().numpy()
-        total += float((b ** 2).sum() + ((e ** 2).sum(axis=0) * (np.asarray(eps, np.float32) / c_ref2)).sum())
-    return total
+def energy(E, B, eps_r, mu_r, c_ref2):
+    """FP64 field energy sum_a (B_a^2 + E_a^2 / c_eff^2), c_eff^2 = c_ref2 / (eps_r mu_r), over one slab's real
+    layers (E, B: (3,) + slab shape, torch or numpy; eps_r, mu_r: slab shape, mu_r None for 1).  Summed over the
+    slabs (an FP64 all-reduce across ranks) it is the whole grid's energy."""
+    e = np.asarray(E.double().cpu().numpy() if hasattr(E, "cpu") else E, np.float64)
+    b = np.asarray(B.double().cpu().numpy() if hasattr(B, "cpu") else B, np.float64)
+    em = np.asarray(eps_r, np.float32).astype(np.float64)
+    if mu_r is not None:
+        em = em * np.asarray(mu_r, np.float32).astype(np.float64)
+    return float((b ** 2).sum() + ((e ** 2).sum(axis=0) * em / c_ref2).sum())

@@ -100,8 +100,15 @@ def _rank_main(rank, world, port, D, shape, nsteps, q):
     decomp.step_dist(slab, rank, world, nsteps, host=True)
     E, B = slab.fields()
     tr = np.concatenate(slab.tr, axis=1) if slab.tr and slab.tr[0].size else np.zeros((0, nsteps))
+    # FP64 all-reduce of the slabs' field energies (the diagnostics of a decomposed run)
+    import torch
+
+    real = slice(1, count + 1)
+    en = torch.tensor([decomp.energy(np.moveaxis(E, -1, 0), np.moveaxis(B, -1, 0), loc.eps_r[real], loc.mu_r[real],
+                                     p.c_ref2)], dtype=torch.float64)
+    dist.all_reduce(en)
     dist.destroy_process_group()
-    q.put((rank, start, count, E, B, recs, tr))
+    q.put((rank, start, count, E, B, recs, tr, float(en[0])))
 
 
 @pytest.mark.timeout(600)
@@ -128,7 +135,9 @@ def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape):
     g = O.init_state(m, f(p.E0), f(p.B0))
     tr = O.run(m, g, nsteps, sources=dict(p.sources(), amp=f(p.src_amp)), receivers=p.receivers())
     E, B = O.fields(m, g)
-    for rank, start, count, Es, Bs, recs, trs in got:
+    energy = O.diagnostics(m, g)[0]
+    for rank, start, count, Es, Bs, recs, trs, en in got:
+        assert abs(en / energy - 1) < 1e-12
         np.testing.assert_array_equal(Es, E[start:start + count])
         np.testing.assert_array_equal(Bs, B[start:start + count])
         if recs.size:
