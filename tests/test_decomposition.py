@@ -172,3 +172,23 @@ def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world):
             np.testing.assert_array_equal(s.traces(nrec).cpu().double().numpy(), ref[2][recs])
         lbem.lbem_check_guards(s.s.h)
         s.close()
+
+
+@pytest.mark.gpu
+def test_rows_argument_errors(lbem):
+    import torch
+
+    s = lbem.Solver((8, 40))
+    s.set_problem(_problem(2, (8, 40), 5, 3))
+    buf = torch.zeros(2 * 40, dtype=torch.float32, device="cuda")
+    for plane, row0, nrows in ((5, 0, 1), (-1, 0, 1), (2, 7, 2), (2, -1, 1)):
+        with pytest.raises(lbem.LbemError) as e:
+            lbem.lbem_rows(s.h, plane, row0, nrows, buf, False)
+        assert e.value.status == 1
+    lbem.lbem_rows(s.h, 2, 6, 2, buf, False)  # the last two rows of plane 2: fine
+    s.close()
+    h = lbem.Solver((8, 32), storage="bf16")
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_rows(h.h, 0, 0, 1, buf, False)
+    assert e.value.status == 1
+    h.close()

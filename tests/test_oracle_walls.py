@@ -301,3 +301,30 @@ def test_3d_walls_keep_the_discrete_invariant_exactly():
     inv0 = O.diagnostics(m, g)[1]
     O.run(m, g, 60)
     assert abs(O.diagnostics(m, g)[1] / inv0 - 1) < 1e-13
+
+
+def test_3d_layer_damps_each_population_by_the_factor_of_the_site_it_leaves():
+    """3D: one step with and without a layer; every population of the new state is the undamped one times the
+    product of the three axes' factors at the site it left (its upwind neighbour, or itself after a wall)."""
+    nz, ny, nx, L, gmax = 9, 8, 10, 3, 0.35
+    rng = np.random.default_rng(47)
+    eps = 1.5 + rng.random((nz, ny, nx))
+    E, B = rng.standard_normal((nz, ny, nx, 3)), rng.standard_normal((nz, ny, nx, 3))
+    bc = (PEC, PMC, PEC)
+    m0 = O.medium(3, eps, bc=bc)
+    m1 = O.medium(3, eps, bc=bc, layer=L, gamma_max=gmax)
+    g0 = O.init_state(m0, E, B)
+    g1 = g0.copy()
+    O.run(m0, g0, 1)
+    O.run(m1, g1, 1)
+    c = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0), (0, -1, 0), (0, 0, -1)]
+    n = (nx, ny, nz)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                for i in range(7):
+                    src = [x - c[i][0], y - c[i][1], z - c[i][2]]
+                    if any(not 0 <= src[a] < n[a] for a in range(3)):
+                        src = [x, y, z]  # reflected at a wall: it left this site
+                    f = np.prod([_layer_factor(src[a], n[a], L, gmax) for a in range(3)])
+                    np.testing.assert_allclose(g1[z, y, x, i], f * g0[z, y, x, i], rtol=1e-14, atol=1e-15)
