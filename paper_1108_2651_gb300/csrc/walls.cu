@@ -1,4 +1,5 @@
-// Walls and absorbing layers (2D, FP32 storage).
+// Walls and absorbing layers (FP32 storage): the 2D edge kernel and the wall-aware grad ln mu (2D and 3D).  In
+// 3D the one-site-per-thread stream-collide kernel applies walls and layers itself (kernels3d.cu).
 //
 // The paper treats periodic domains only and leaves other boundaries open.
 // Here a wall sits half a site beyond the first / last site of an axis: a
