@@ -111,6 +111,10 @@ def workload(name):
         return W.heterogeneous_2d_aniso(4096, seed=2, nsteps=5000)
     if name == "het3d_192":
         return W.heterogeneous_3d(192, seed=4, nsteps=1000)
+    if name == "het3d_box_192":  # the same in a PEC box with a 16-site absorbing layer
+        q = W.heterogeneous_3d(192, seed=4, nsteps=1000)
+        q.bc, q.layer, q.gamma_max = (1, 1, 1), 16, 0.2
+        return q
     raise ValueError(name)
 
 
@@ -505,7 +509,7 @@ def main():
     ap.add_argument("--impl", default="lbem", choices=["lbem", "reference"])
     ap.add_argument("--workload", default="het2d_4096",
                     choices=["het2d_4096", "het2d_1024", "het2d_walls_4096", "het2d_drude_4096",
-                             "het2d_aniso_4096", "het3d_192", "batch256", "adjoint3d_96"])
+                             "het2d_aniso_4096", "het3d_192", "het3d_box_192", "batch256", "adjoint3d_96"])
     ap.add_argument("--storage", default="f32", choices=list(BYTES_PER_SITE))
     ap.add_argument("--lb-steps", type=int, default=None, help="override the workload's step count (profiling)")
     ap.add_argument("--ref-steps", type=int, default=40)
@@ -636,8 +640,10 @@ def main():
         kname, kid = "step2d_gen (one dispersive pole per site, single steps)", "disp"
     elif aniso:
         kname, kid = "step2d_gen (anisotropic medium, single steps)", "gen"
-    elif walls:
+    elif walls and p.D == 2:
         kname += " + edge2d (walls and layers)"
+    elif walls:
+        kname = "step3d_site (walls and layers applied in the kernel)"
     traffic = NCU_TRAFFIC.get((args.workload, args.storage, kid)) if args.lb_steps is None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "steps_per_launch": spp,
@@ -678,7 +684,7 @@ def main():
         cpu = cpu_baseline(p)
     s.close()
     if rank == 0:
-        launches = args.steps * (step_launches * (2 if walls and not disp else 1) + 6 +
+        launches = args.steps * (step_launches * (2 if walls and p.D == 2 and not (disp or aniso) else 1) + 6 +
                                  (1 if args.storage == "f16" else 0))
         line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -208,7 +208,7 @@ __device__ __forceinline__ float wall_sign3(int kind, int gm, int ax) {
 // With WL, pulls across walls follow wall_sign3 and the absorbing layer's
 // factor fx(x) fy(y) fz(z) scales the result.
 template <bool MU, bool WL = false>
-__global__ void __launch_bounds__(BLOCK) step3d_site(StepArgs a, Walls w) {
+__global__ void __launch_bounds__(BLOCK, WL ? 5 : 1) step3d_site(StepArgs a, Walls w) {
     const Grid &G = a.g;
     const int tpr = G.pitch;  // threads per row (pitch is a multiple of 32)
     const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
