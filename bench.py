@@ -324,17 +324,21 @@ def other_forms(lbem, torch, p, peak, stream):
     out["f32_drude_dispersive"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                                    "frac": gbs / peak, "bytes_per_site_per_launch": 72, "steps_per_launch": spp,
                                    "lb_steps": 2000, "kernel": "step2d_gen"}
-    # the same medium made uniaxial, mu = diag(2, 1) (per-axis lattice weights), 2000 single-step launches of the
-    # general kernel: 44 B/site
+    # the same medium made uniaxial, mu = diag(2, 1) (per-axis lattice weights), 2000 steps: 44 B/site per
+    # launch, two steps per launch by default (the tile kernel with per-axis weights), then single-step launches
+    # of the general kernel
     pa = W.heterogeneous_2d_aniso(p.shape[0], seed=2, nsteps=2000)
-    s = lbem.Solver(pa.shape, stream=stream.cuda_stream)
-    ms, v, spp = _time_run(lbem, torch, s, pa, 2000, stream)
-    s.close()
-    per = ms / 2000
-    gbs = 44 * n / (per * 1e-3) / 1e9
-    out["f32_anisotropic"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
-                              "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp,
-                              "lb_steps": 2000, "kernel": "step2d_gen", "mu_tensor": list(pa.aniso)}
+    for key, spp_set in (("f32_anisotropic", 2), ("f32_anisotropic_single_step", 1)):
+        s = lbem.Solver(pa.shape, stream=stream.cuda_stream)
+        if spp_set == 1:
+            lbem.lbem_set_temporal_blocking(s.h, 1, -1)
+        ms, v, spp = _time_run(lbem, torch, s, pa, 2000, stream)
+        s.close()
+        per = ms / (2000 // spp)
+        gbs = 44 * n / (per * 1e-3) / 1e9
+        out[key] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                    "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp, "lb_steps": 2000,
+                    "kernel": "step2d_tb2<AN>" if spp == 2 else "step2d_gen", "mu_tensor": list(pa.aniso)}
     # 192^3 in a PEC box with a 16-site absorbing layer (walls applied by the one-site-per-thread 3D kernel),
     # 500 steps: 172 B/site
     qb = W.heterogeneous_3d(192, nsteps=500)
@@ -638,8 +642,10 @@ def main():
         kid = variant
     if disp:
         kname, kid = "step2d_gen (one dispersive pole per site, single steps)", "disp"
-    elif aniso:
+    elif aniso and spp == 1:
         kname, kid = "step2d_gen (anisotropic medium, single steps)", "gen"
+    elif aniso:
+        kname, kid = "step2d_tb2<AN> (anisotropic medium, tile shape 0, 2 steps per launch)", "tb2an"
     elif walls and p.D == 2:
         kname += " + edge2d (walls and layers)"
     elif walls:

@@ -232,7 +232,10 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM).  With
  * a heterogeneous mu (FP32; the two grad ln mu planes are staged beside c_L^2, 52 instead of 104 bytes per
  * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, and 1 = 14 rows, 512, 2 exist; a larger
- * shape set before the medium falls back to 0.  LBEM_ERR_ARG for values outside the current handle's set. */
+ * shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) without walls
+ * or a dispersive pole steps in pairs with shape 0 (256 threads, 5 per SM) whatever shape is set, bit-identical
+ * to its single steps; with walls or a pole, and for steps_per_pass = 3, every step is a single step.
+ * LBEM_ERR_ARG for values outside the current handle's set. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 
 /* Steps per launch in effect (2 or 3 only where that kernel is enabled and applies), the tile shape (as set

@@ -107,6 +107,8 @@ StepArgs step_args(const lbem_t *h, int cur_in) {
     a.med.cL2 = h->cL2;
     a.med.mu = h->has_mu ? h->mu : nullptr;
     a.med.dlnmu = h->has_mu ? h->dlnmu : nullptr;
+    a.med.ar = h->aniso_r;
+    a.med.amu = h->aniso_mu;
     a.evt.rowptr = h->nev ? h->d_rowptr : nullptr;
     a.evt.ev = h->d_ev;
     a.evt.amp = h->d_amp;
@@ -150,15 +152,19 @@ static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16
 
 // Whether launches of two (three) steps apply: 2D; FP32 storage with any medium, 16-bit storage with uniform mu
 // and nx % 4 == 0; three steps per launch exist for FP32 storage with uniform mu.
+// An anisotropic medium takes two steps per launch (tile shape 0) unless it has walls or a pole, which the general
+// single-step kernel handles.
 static bool multi_step_base(const lbem_t *h) {
-    return h->dim == 2 && !h->general() && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
+    if (h->disp || (h->aniso && h->walls())) return false;
+    return h->dim == 2 && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
 }
 static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
 static bool three_step_ok(const lbem_t *h) {
-    return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32 && !h->has_mu;
+    return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32 && !h->has_mu && !h->aniso;
 }
 // the two-step tile shape to launch: the one set (or autotuned) when it exists for this medium, else 0
 static int two_step_shape(const lbem_t *h) {
+    if (h->aniso) return 0;
     return h->tblock == 2 && h->tb_shape < tb2_nshapes(h->storage, h->has_mu) ? h->tb_shape : 0;
 }
 static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two_step_ok(h) ? 2 : 1; }
@@ -996,7 +1002,7 @@ lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass) *steps_per_pass = steps_per_launch(h);
     if (tile_shape) *tile_shape = h->tb_shape;
-    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : tb2_nshapes(h->storage, h->has_mu);
+    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : h->aniso ? 1 : tb2_nshapes(h->storage, h->has_mu);
     return LBEM_OK;
 }
 

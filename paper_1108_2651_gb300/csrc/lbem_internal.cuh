@@ -241,6 +241,27 @@ __device__ __forceinline__ Out5 collide2d(float g0, float g1, float g2, float g3
     return o;
 }
 
+// The site update of an anisotropic medium with per-axis speeds c_x^2 = r c^2, c_y^2 = c^2 / r (general.cu), in the
+// exact operation order of the general kernel with no pole (its P = +0 terms included, so that zeros keep their
+// signs): ri = 1/r, fs = r + 1/r.
+__device__ __forceinline__ Out5 collide2d_an(float g0, float g1, float g2, float g3, float g4, float cl, float shat,
+                                             float r, float ri, float fs) {
+    const float P = 0.f;
+    const float sig = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, g3)), g4);
+    const float Lam = __fadd_rn(__fmul_rn(cl, sig), P);
+    const float Lx = __fmul_rn(r, Lam), Ly = __fmul_rn(ri, Lam);
+    const float w0 = __fsub_rn(1.f, __fmul_rn(fs, cl));
+    const float Tm = __fmul_rn(-0.5f * cl, shat), T0 = __fmul_rn(-w0, shat);
+    const float Tx = __fmul_rn(r, Tm), Ty = __fmul_rn(ri, Tm);
+    Out5 o;
+    o.o0 = __fadd_rn(__fsub_rn(__fsub_rn(__fmul_rn(2.f * w0, sig), g0), __fmul_rn(2.f * fs, P)), T0);
+    o.o1 = __fadd_rn(__fsub_rn(Lx, g3), Tx);
+    o.o2 = __fadd_rn(__fsub_rn(Ly, g4), Ty);
+    o.o3 = __fadd_rn(__fsub_rn(Lx, g1), Tx);
+    o.o4 = __fadd_rn(__fsub_rn(Ly, g2), Ty);
+    return o;
+}
+
 // collide2d at a site without a source (S^ = +0): there T_m and T_0 are -0 (c_L^2 > 0, w0 >= 0), and adding
 // -0 leaves every value unchanged, so dropping them gives the same bits as collide2d(..., 0.f).
 __device__ __forceinline__ Out5 collide2d_free(float g0, float g1, float g2, float g3, float g4, float cl) {
@@ -295,6 +316,8 @@ struct Medium {
     const float *cL2 = nullptr;    // [plane]
     const float *mu = nullptr;     // [plane] or null
     const float *dlnmu = nullptr;  // [D][plane] or null
+    // anisotropic medium (general.cu): r = c_x / c_y = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy); 1, 1: isotropic
+    float ar = 1.f, amu = 1.f;
 };
 
 // Walls and absorbing layers (walls.cu): per axis x, y 0 = periodic, 1 = PEC wall, 2 = PMC wall; layer

@@ -206,7 +206,8 @@ struct Pull4 {
 // Four site updates (collide2d each) at global row gy, columns x0+4*lane.., time t.
 // With a heterogeneous permeability (MU) the source carries B_x d_y ln mu - B_y d_x ln mu (dlx, dly: the
 // gradient of ln mu at the four sites) at every site, as in the single-step kernels.
-template <bool EV, bool MU, class PULL>
+// With AN (an anisotropic medium, a.med.ar / a.med.amu) the update is collide2d_an, as in the general kernel.
+template <bool EV, bool MU, class PULL, bool AN = false>
 __device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, float4 cl, float4 dlx, float4 dly,
                                             int x0, int gy, long long t, bool owned_row, float4 &o0, float4 &o1,
                                             float4 &o2, float4 &o3, float4 &o4) {
@@ -218,7 +219,16 @@ __device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, fl
                     q4 = TB_COMP(g.g4, k), ck = TB_COMP(cl, k);
         Out5 o;
         const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, TB_COMP(dlx, k), TB_COMP(dly, k)) : 0.f;
-        if (EV) {
+        if (AN) {
+            const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
+            float shat = 0.f;
+            if (EV) {
+                const int gx = x0 + 4 * lane + k;
+                shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, owned_row && gx < G.nx && gy < G.ny, q0,
+                                   q1, q2, q3, q4, ck, 0.f, 0.f, r, ri, a.med.amu);
+            }
+            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs);
+        } else if (EV) {
             const int gx = x0 + 4 * lane + k;
             const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
                                            owned_row && gx < G.nx && gy < G.ny, q0, q1, q2, q3, q4, ck, shat0);
@@ -248,7 +258,7 @@ __device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, flo
 // py-2); then the ring sites x0-1 (plane 1 only) and x0+TBX (plane 3 only) of rows y0 .. y0+TBY-1.  Also
 // reads into clb the c_L^2 of the warp's step-(t+1) row (and with MU into dbx, dby its gradient of ln mu), as
 // the medium stage is reloaded before step t+1.
-template <int TBY, int NT, bool EV, bool MU = false>
+template <int TBY, int NT, bool EV, bool MU = false, bool AN = false>
 __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, const float *CL, float *P, int x0,
                                           int y0, long long t, float4 &clb, float4 &dbx, float4 &dby) {
     using Gm = TbGeom<TBY>;
@@ -268,7 +278,8 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
         const float4 cl = lds4(CL + py * TW + c);
         const float4 dlx = MU ? lds4(CL + DX + py * TW + c) : cl, dly = MU ? lds4(CL + DY + py * TW + c) : cl;
         float4 o0, o1, o2, o3, o4;
-        tb_update4m<EV, MU>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2, o3, o4);
+        tb_update4m<EV, MU, Pull4, AN>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2,
+                                       o3, o4);
         float *Pr = P + c;
         if (py >= 1 && py <= TBY) {
             sts4(Pr + 0 * PL + (py - 1) * TW, o0);
@@ -288,10 +299,19 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
                     q4 = r[4 * Gm::IN_PL];
         const float ck = CL[py * TW + cc];
         float shat = MU ? mu_source(q4 - q2, q1 - q3, CL[DX + py * TW + cc], CL[DY + py * TW + cc]) : 0.f;
-        if (EV)
-            shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3, q4,
-                               ck, shat);
-        const Out5 o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        Out5 o;
+        if (AN) {
+            const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
+            if (EV)
+                shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3,
+                                   q4, ck, 0.f, 0.f, r, ri, a.med.amu);
+            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs);
+        } else {
+            if (EV)
+                shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3,
+                                   q4, ck, shat);
+            o = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        }
         if (k & 1)
             P[3 * PL + (py - 1) * TW + cc] = o.o3;
         else
@@ -300,7 +320,7 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
 }
 
 // Step t+1 on tile row y0 + warp from the t+1 stage, written as 16-byte streaming stores.
-template <int TBY, bool EV, bool MU = false>
+template <int TBY, bool EV, bool MU = false, bool AN = false>
 __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, float4 clb, float4 dbx, float4 dby,
                                           int x0, int y0, long long t) {
     const Grid &G = a.g;
@@ -310,7 +330,7 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
     const int c = 4 + 4 * lane;
     const Pull4 g(P, TbGeom<TBY>::P_PL, oy, c);
     float4 o0, o1, o2, o3, o4;
-    tb_update4m<EV, MU>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4);
+    tb_update4m<EV, MU, Pull4, AN>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
         float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)gy * G.pitch + x0 +
                                                4 * lane);
@@ -327,7 +347,7 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
 
 // One persistent CTA per SM slot; CTA b takes tiles b, b + gridDim.x, ... (row-major over the tile grid).
 // The window of the next tile is loaded while step t+1 of the current one is computed.
-template <int TBY, int NT, int MINB, bool MU = false>
+template <int TBY, int NT, int MINB, bool MU = false, bool AN = false>
 __global__ void __launch_bounds__(NT, MINB)
     step2d_tb2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
                const __grid_constant__ CUtensorMap tmDL, int use_tma, int ntx, int nty, int dq, int dr) {
@@ -378,18 +398,18 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb;
         if (events)
-            tb_step_a<TBY, NT, true, MU>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
+            tb_step_a<TBY, NT, true, MU, AN>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
         else
-            tb_step_a<TBY, NT, false, MU>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
+            tb_step_a<TBY, NT, false, MU, AN>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
         __syncthreads();
         if (has_next)  // the t stage and the medium stage are free: start the loads of the next tile
             tb_load<TBY, MU>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar,
                              use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, NT, &tmDL);
         asm volatile("cp.async.commit_group;\n" ::);
         if (events)
-            tb_step_b<TBY, true, MU>(a, P, clb, dbx, dby, x0, y0, t);
+            tb_step_b<TBY, true, MU, AN>(a, P, clb, dbx, dby, x0, y0, t);
         else
-            tb_step_b<TBY, false, MU>(a, P, clb, dbx, dby, x0, y0, t);
+            tb_step_b<TBY, false, MU, AN>(a, P, clb, dbx, dby, x0, y0, t);
         tx = ntx_;
         ty = nty_;
         events = events_next;
@@ -733,18 +753,18 @@ static bool make_dl_map(const StepArgs &a, CUtensorMap *mDL) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TBY, int NT, int MINB, bool MU = false>
+template <int TBY, int NT, int MINB, bool MU = false, bool AN = false>
 static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     using Gm = TbGeom<TBY, MU>;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB, MU>,
+        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB, MU, AN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB, MU>, NT, Gm::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB, MU, AN>, NT, Gm::BYTES);
         if (per_sm < 1) per_sm = 1;
     }
     CUtensorMap mIn, mCL, mDL;
@@ -755,7 +775,7 @@ static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
     const int ntiles = ntx * nty;
     const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
-    step2d_tb2<TBY, NT, MINB, MU><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, use_tma, ntx, nty, blocks / ntx,
+    step2d_tb2<TBY, NT, MINB, MU, AN><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, use_tma, ntx, nty, blocks / ntx,
                                                                 blocks % ntx);
     return cudaGetLastError();
 }
@@ -1163,6 +1183,7 @@ static cudaError_t launch_16(const StepArgs &a, int shape, cudaStream_t s) {
 // Tile shapes (rows, threads, CTAs per SM).  Measured on 4096^2 (heterogeneous medium, FP32): 6 rows at five
 // CTAs per SM is the fastest; the others remain selectable for other sizes and for the bit-identity tests.
 // With a heterogeneous permeability (FP32 only): 6 rows at four CTAs per SM (51 KB), or 14 rows at two.
+// With an anisotropic medium (FP32, no mu array) only tile shape 0.
 int tb2_nshapes(int storage, bool has_mu) {
     if (has_mu) return storage == LBEM_F32 ? 2 : 0;
     return storage == LBEM_F32 ? 7 + rs2_nshapes() : 7;
@@ -1175,6 +1196,7 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
         default: break;
     }
+    if (a.med.ar != 1.f || a.med.amu != 1.f) return launch_tb<6, 256, 5, false, true>(a, s);  // anisotropic
     if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)
     switch (shape) {

@@ -2,7 +2,8 @@
 
 Tolerance as for the periodic parity tests: relative L2 of E, B and receiver traces <= 1e-5 against the FP64
 oracle.  Also: the per-axis dispersion of plane waves, the isotropic tensor against the plain scheme with a
-uniform mu, combinations with walls, layers and a dispersive pole, and the errors.
+uniform mu, combinations with walls, layers and a dispersive pole, two steps per launch against single steps
+bit for bit, and the errors.
 """
 import numpy as np
 import pytest
@@ -97,6 +98,33 @@ def test_plane_waves_on_gpu_follow_the_per_axis_dispersion(lbem):
     np.testing.assert_allclose(amp, amp[0] * np.cos(om * t) + b * np.sin(om * t), rtol=0, atol=2e-5)
 
 
+@pytest.mark.parametrize("shape,aniso", [((3, 5), (2.5, 1.2)), ((37, 130), (0.7, 1.6)), ((130, 259), (1.7, 1.7))])
+def test_two_step_launches_equal_single_steps_bit_for_bit(lbem, shape, aniso):
+    """Without walls or a pole an anisotropic medium steps in pairs (the tile kernel with per-axis weights):
+    the same bits as one step per launch (the general kernel), with and without graph replay, odd step
+    counts included."""
+    import torch
+
+    p = _problem(shape, 900 + shape[1], 37, aniso)
+    ref = gpu_run(p, steps_per_pass=1)
+    for graphs in (False, True):
+        stream = torch.cuda.Stream()  # graph capture needs a non-default stream
+        s = lbem.Solver(p.shape, stream=stream.cuda_stream)
+        s.set_problem(p)
+        assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2
+        lbem.lbem_set_graphs(s.h, graphs)
+        s.step(10)
+        s.step(27)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        lbem.lbem_check_guards(s.h)
+        s.close()
+        np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
+        np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1])
+        np.testing.assert_array_equal(tr.cpu().double().numpy()[:, :37], ref[2])
+
+
 def test_anisotropic_full_size_matches_oracle(lbem):
     """4096^2 heterogeneous medium with mu = diag(2, 1) (the benchmark's anisotropic workload), 20 steps."""
     p = W.heterogeneous_2d_aniso(4096, seed=2, nsteps=20)
@@ -119,7 +147,11 @@ def test_anisotropy_errors_and_switching_back(lbem):
         lbem.lbem_set_medium_aniso(s.h, eps, 0.3, 0.3)
     assert e.value.status == 3
     s.set_problem(p)
-    assert lbem.lbem_get_temporal_blocking(s.h)[0] == 1  # the general kernel, one step per launch
+    assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2  # no walls, no pole: two steps per launch
+    assert lbem.lbem_get_temporal_blocking(s.h)[2] == 1
+    lbem.lbem_set_boundaries(s.h, (PEC, 0, 0), 0, 0.0)
+    assert lbem.lbem_get_temporal_blocking(s.h)[0] == 1  # walls: the general kernel, one step per launch
+    lbem.lbem_set_boundaries(s.h, (0, 0, 0), 0, 0.0)
     with pytest.raises(lbem.LbemError):
         lbem.lbem_forward_record(s.h, 4, 2)
     with pytest.raises(lbem.LbemError) as e:
