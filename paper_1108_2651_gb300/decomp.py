@@ -11,7 +11,9 @@ update has the same inputs).
 
 Communication is neighbour point-to-point (torch.distributed send / receive: NCCL between GPUs, gloo on the host)
 or, for slabs held by one process, direct copies.  Each slab steps one step per launch (the halo is one layer
-deep).  Periodic isotropic media, with or without a heterogeneous mu; sources and receivers on real layers.
+deep).  Any medium the library steps: a heterogeneous mu, a uniform anisotropic tensor, a dispersive pole (its
+J and P are site-local, so nothing of it crosses a cut), walls and absorbing layers on the axes along the cuts
+(x in 2D; x, y in 3D); the slab axis itself stays periodic.  Sources and receivers on real layers.
 """
 from dataclasses import replace
 
@@ -34,12 +36,14 @@ def local_problem(p, rank, world):
     """The slab of workloads.Problem p held by `rank`, with one ghost layer on either side (the neighbouring
     layers of the whole grid, periodic).  Returns (local problem, start, count, indices of the global receivers
     it holds)."""
-    assert p.wp2 is None and p.aniso is None and not any(p.bc), "periodic isotropic media only"
+    D = len(p.shape)
+    assert not p.bc[D - 1], "the slab axis must be periodic (walls only on the axes along the cuts)"
     n = p.shape[0]
     start, count = slab_range(n, world, rank)
     assert count >= 1, "more ranks than layers"
     layers = np.arange(start - 1, start + count + 1) % n
     take = lambda a: None if a is None else np.take(a, layers, axis=0)
+    site = lambda a: None if a is None else take(np.broadcast_to(a, p.shape))  # a per-site parameter or a scalar
     shape = (count + 2,) + tuple(p.shape[1:])
     per_layer = int(np.prod(p.shape[1:]))
 
@@ -48,7 +52,8 @@ def local_problem(p, rank, world):
         keep = (layer >= start) & (layer < start + count)
         return keep, (layer - start + 1) * per_layer + sites % per_layer
 
-    q = replace(p, shape=shape, eps_r=take(p.eps_r), mu_r=take(p.mu_r), E0=take(p.E0), B0=take(p.B0))
+    q = replace(p, shape=shape, eps_r=take(p.eps_r), mu_r=take(p.mu_r), E0=take(p.E0), B0=take(p.B0),
+                wp2=site(p.wp2), wr2=site(p.wr2), gamma=site(p.gamma))
     keep, loc = localize(p.src_site)
     q.src_site, q.src_comp, q.src_amp = loc[keep].astype(np.int64), p.src_comp[keep], p.src_amp[keep]
     keep, loc = localize(p.rec_site)

@@ -2,10 +2,13 @@
 
 On the host: world-size-2 gloo ranks, each stepping its slab with the FP64 oracle and exchanging the
 populations that cross the cuts through torch.distributed, must reproduce the single-domain oracle bit for bit
-(2D and 3D, heterogeneous eps and mu, sources and receivers on either slab).  On the GPU: two slabs stepped by the
-library in one process (halo copies between them) must reproduce the single-domain library run bit for bit.
+(2D and 3D, heterogeneous eps and mu, sources and receivers on either slab; also a uniform anisotropic tensor, a
+dispersive pole, and walls with absorbing layers on the axes along the cuts).  On the GPU: two or three slabs
+stepped by the library in one process (halo copies between them) must reproduce the single-domain library run
+bit for bit, for the same media.
 """
 import os
+import queue
 import socket
 import sys
 
@@ -15,12 +18,26 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _problem(D, shape, seed, nsteps):
+def _problem(D, shape, seed, nsteps, kind="mu"):
+    """kind: "mu" a heterogeneous mu; "aniso" a uniform tensor diag(2.2, 1.3) (2D); "drude" a dispersive pole on
+    most sites (2D); "walls" a heterogeneous mu in a PEC box along the cuts with a 2-site absorbing layer."""
     sys.path.insert(0, ROOT)
     from paper_1108_2651_gb300 import workloads as W
 
-    eps, mu = W.random_medium(shape, seed, mu=True)
+    eps, mu = W.random_medium(shape, seed, lo=1.0 if kind in ("mu", "walls") else 1.2, mu=kind in ("mu", "walls"))
     p = W.Problem("decomp", D, shape, eps, mu, nsteps)
+    if kind == "aniso":
+        p.aniso = (2.2, 1.3)
+    elif kind == "drude":
+        rng = np.random.default_rng(seed + 3)
+        w0 = 1 - 1.0 / np.asarray(eps, np.float32).astype(np.float64)
+        on = rng.random(shape) < 0.7
+        p.wp2 = np.where(on, 2 * w0 * rng.random(shape), 0.0)
+        p.wr2 = np.where(on, 1.5 * w0 * rng.random(shape), 0.0)
+        p.gamma = np.where(on, 0.2 * rng.random(shape), 0.0)
+    elif kind == "walls":
+        p.bc = (1, 0, 0) if D == 2 else (1, 1, 0)
+        p.layer, p.gamma_max = 2, 0.3
     p.E0, p.B0 = W.random_fields(shape, seed + 1, 0.3)
     if D == 2:
         p.E0[..., :2] = 0
@@ -48,7 +65,10 @@ class OracleSlab:
         f = lambda a: None if a is None else np.asarray(a, np.float32).astype(np.float64)
         self.O = O
         self.D, self.count = q.D, count
-        self.m = O.medium(q.D, f(q.eps_r), f(q.mu_r))
+        disp = None if q.wp2 is None else dict(wp2=f(q.wp2), wr2=f(q.wr2), gamma=f(q.gamma))
+        self.m = O.medium(q.D, f(q.eps_r), f(q.mu_r), bc=q.bc, layer=q.layer, gamma_max=q.gamma_max,
+                          dispersion=disp, aniso=q.aniso)
+        self.pole = None if disp is None else O.pole_state(self.m)
         self.g = O.init_state(self.m, f(q.E0), f(q.B0))
         src = q.sources()
         self.src = None if src is None else dict(src, amp=f(src["amp"]))
@@ -58,7 +78,8 @@ class OracleSlab:
         self.tr = []
 
     def step(self):
-        self.tr.append(self.O.run(self.m, self.g, 1, t0=self.t, sources=self.src, receivers=self.rec))
+        self.tr.append(self.O.run(self.m, self.g, 1, t0=self.t, sources=self.src, receivers=self.rec,
+                                  pole=self.pole))
         self.t += 1
 
     def halo_out(self, up):
@@ -72,7 +93,7 @@ class OracleSlab:
         self.g[layer, ..., d, :, :] = buf.numpy()
 
     def fields(self):
-        E, B = self.O.fields(self.m, self.g)
+        E, B = self.O.fields(self.m, self.g, self.pole)
         return E[1:self.count + 1], B[1:self.count + 1]
 
 
@@ -84,7 +105,7 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, D, shape, nsteps, q):
+def _rank_main(rank, world, port, D, shape, nsteps, kind, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       OMP_NUM_THREADS="2")
     sys.path.insert(0, ROOT)
@@ -94,7 +115,7 @@ def _rank_main(rank, world, port, D, shape, nsteps, q):
     from paper_1108_2651_gb300 import decomp
 
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    p = _problem(D, shape, 7 + D, nsteps)
+    p = _problem(D, shape, 7 + D, nsteps, kind)
     loc, start, count, recs = decomp.local_problem(p, rank, world)
     slab = OracleSlab(loc, count)
     decomp.step_dist(slab, rank, world, nsteps, host=True)
@@ -104,40 +125,45 @@ def _rank_main(rank, world, port, D, shape, nsteps, q):
     import torch
 
     real = slice(1, count + 1)
-    en = torch.tensor([decomp.energy(np.moveaxis(E, -1, 0), np.moveaxis(B, -1, 0), loc.eps_r[real], loc.mu_r[real],
-                                     p.c_ref2)], dtype=torch.float64)
+    mu = None if loc.mu_r is None else loc.mu_r[real]
+    en = torch.tensor([decomp.energy(np.moveaxis(E, -1, 0), np.moveaxis(B, -1, 0), loc.eps_r[real], mu, p.c_ref2)],
+                      dtype=torch.float64)
     dist.all_reduce(en)
     dist.destroy_process_group()
     q.put((rank, start, count, E, B, recs, tr, float(en[0])))
 
 
 @pytest.mark.timeout(600)
-@pytest.mark.parametrize("D,shape", [(2, (11, 13)), (3, (7, 4, 5))])
-def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape):
+@pytest.mark.parametrize("D,shape,kind", [(2, (11, 13), "mu"), (3, (7, 4, 5), "mu"), (2, (11, 13), "aniso"),
+                                          (2, (11, 13), "drude"), (2, (11, 13), "walls"), (3, (7, 6, 5), "walls")])
+def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind):
     import torch.multiprocessing as mp
 
     import oracle as O
+    from gpu_helpers import oracle_run
 
     nsteps = 12
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, D, shape, nsteps, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, D, shape, nsteps, kind, q)) for r in range(2)]
     for pr in procs:
         pr.start()
-    got = [q.get(timeout=300) for _ in range(2)]
+    got = []
+    while len(got) < 2:  # fail as soon as a rank dies instead of waiting for its result
+        try:
+            got.append(q.get(timeout=2))
+        except queue.Empty:
+            assert all(pr.exitcode in (None, 0) for pr in procs), [pr.exitcode for pr in procs]
     for pr in procs:
         pr.join(timeout=120)
         assert pr.exitcode == 0
-    p = _problem(D, shape, 7 + D, nsteps)
-    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
-    m = O.medium(D, f(p.eps_r), f(p.mu_r))
-    g = O.init_state(m, f(p.E0), f(p.B0))
-    tr = O.run(m, g, nsteps, sources=dict(p.sources(), amp=f(p.src_amp)), receivers=p.receivers())
-    E, B = O.fields(m, g)
+    p = _problem(D, shape, 7 + D, nsteps, kind)
+    E, B, tr, m, g = oracle_run(p)
     energy = O.diagnostics(m, g)[0]
     for rank, start, count, Es, Bs, recs, trs, en in got:
-        assert abs(en / energy - 1) < 1e-12
+        if kind in ("mu", "walls"):  # the slabs' energy formula is the isotropic, non-dispersive one
+            assert abs(en / energy - 1) < 1e-12
         np.testing.assert_array_equal(Es, E[start:start + count])
         np.testing.assert_array_equal(Bs, B[start:start + count])
         if recs.size:
@@ -146,16 +172,18 @@ def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("D,shape,world", [(2, (40, 70), 2), (2, (37, 130), 3), (3, (16, 6, 40), 2),
-                                           (2, (9, 33), 1)])
-def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world):
+@pytest.mark.parametrize("D,shape,world,kind", [(2, (40, 70), 2, "mu"), (2, (37, 130), 3, "mu"),
+                                                (3, (16, 6, 40), 2, "mu"), (2, (9, 33), 1, "mu"),
+                                                (2, (40, 70), 2, "aniso"), (2, (37, 130), 3, "drude"),
+                                                (2, (40, 70), 2, "walls"), (3, (16, 12, 40), 2, "walls")])
+def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world, kind):
     import torch
 
     from gpu_helpers import gpu_run
     from paper_1108_2651_gb300 import decomp
 
     nsteps = 15
-    p = _problem(D, shape, 21 + D, nsteps)
+    p = _problem(D, shape, 21 + D, nsteps, kind)
     ref = gpu_run(p, steps_per_pass=1)
     slabs, parts = [], []
     for r in range(world):
