@@ -314,17 +314,21 @@ def other_forms(lbem, torch, p, peak, stream):
                                   "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp,
                                   "variant": v, "lb_steps": 2000, "bc": list(pw.bc), "layer": pw.layer,
                                   "gamma_max": pw.gamma_max}
-    # the same medium with a lossy Drude cylinder (one dispersive pole per site), 2000 single-step launches:
-    # 44 B/site plus the pole's J and P read and written (16) and its three parameters read (12) = 72 B/site
+    # the same medium with a lossy Drude cylinder (one dispersive pole per site), 2000 steps: 44 B/site plus the
+    # pole's J and P read and written (16) and its three parameters read (12) = 72 B/site per launch; two steps
+    # per launch by default (the tile kernel carrying the pole), then single-step launches of the general kernel
     pd = W.heterogeneous_2d_drude(p.shape[0], seed=2, nsteps=2000)
-    s = lbem.Solver(pd.shape, stream=stream.cuda_stream)
-    ms, v, spp = _time_run(lbem, torch, s, pd, 2000, stream)
-    s.close()
-    per = ms / 2000
-    gbs = 72 * n / (per * 1e-3) / 1e9
-    out["f32_drude_dispersive"] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
-                                   "frac": gbs / peak, "bytes_per_site_per_launch": 72, "steps_per_launch": spp,
-                                   "lb_steps": 2000, "kernel": "step2d_gen"}
+    for key, spp_set in (("f32_drude_dispersive", 2), ("f32_drude_single_step", 1)):
+        s = lbem.Solver(pd.shape, stream=stream.cuda_stream)
+        if spp_set == 1:
+            lbem.lbem_set_temporal_blocking(s.h, 1, -1)
+        ms, v, spp = _time_run(lbem, torch, s, pd, 2000, stream)
+        s.close()
+        per = ms / (2000 // spp)
+        gbs = 72 * n / (per * 1e-3) / 1e9
+        out[key] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
+                    "frac": gbs / peak, "bytes_per_site_per_launch": 72, "steps_per_launch": spp, "lb_steps": 2000,
+                    "kernel": "step2d_tb2<POLE>" if spp == 2 else "step2d_gen"}
     # the same medium made uniaxial, mu = diag(2, 1) (per-axis lattice weights), 2000 steps: 44 B/site per
     # launch, two steps per launch by default (the tile kernel with per-axis weights), then single-step launches
     # of the general kernel
@@ -641,8 +645,10 @@ def main():
     else:
         kname = (f"step2d<{args.storage}>" if p.D == 2 else "step3d") + f" (variant {variant})"
         kid = variant
-    if disp:
+    if disp and spp == 1:
         kname, kid = "step2d_gen (one dispersive pole per site, single steps)", "disp"
+    elif disp:
+        kname, kid = "step2d_tb2<POLE> (one dispersive pole per site, tile shape 0, 2 steps per launch)", "tb2pole"
     elif aniso and spp == 1:
         kname, kid = "step2d_gen (anisotropic medium, single steps)", "gen"
     elif aniso:

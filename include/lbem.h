@@ -203,8 +203,10 @@ lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double
  * FP64: LBEM_ERR_MEDIUM (nothing changed) unless every parameter is finite and
  * >= 0 and wp2 + wr2 <= 4 w0 (w0 the rest weight, 1 - 2 c_L^2 or 1 - c_x^2 - c_y^2: the stability
  * bound), which lbem_set_medium also checks against a new medium.  A dispersive
- * handle steps one step per launch with the general kernel (walls, layers and
- * an anisotropic medium included); lbem_set_fields starts the pole at rest (D = E); lbem_save_state
+ * handle with walls or a mu array steps one step per launch with the general kernel (walls, layers and an
+ * anisotropic medium included); without them it steps in pairs (lbem_set_temporal_blocking), bit-identical to
+ * single steps.  The handle holds a second P plane (every launch writes P to the plane paired with its output
+ * population buffer); lbem_set_fields starts the pole at rest (D = E); lbem_save_state
  * appends J and P (lbem_info's state_bytes counts them).  Batches and the
  * adjoint take non-dispersive handles only.  Synchronises the stream. */
 lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, const float *gamma);
@@ -233,8 +235,9 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * a heterogeneous mu (FP32; the two grad ln mu planes are staged beside c_L^2, 52 instead of 104 bytes per
  * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, and 1 = 14 rows, 512, 2 exist; a larger
  * shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) without walls
- * or a dispersive pole steps in pairs with shape 0 (256 threads, 5 per SM) whatever shape is set, bit-identical
- * to its single steps; with walls or a pole, and for steps_per_pass = 3, every step is a single step.
+ * steps in pairs with shape 0 (256 threads, 5 per SM) whatever shape is set, a dispersive pole without walls or
+ * a mu array with shape 0 at 4 per SM, both bit-identical to their single steps; with walls (or a pole with a
+ * mu array), and for steps_per_pass = 3, every step of these media is a single step.
  * LBEM_ERR_ARG for values outside the current handle's set. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 

@@ -98,17 +98,13 @@ __global__ void __launch_bounds__(BLOCK, 4) step2d_gen(StepArgs a, Walls w, Gene
         float4 Jn4, Pn4;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const float P = get(P4, j), gm = get(gm4, j);
-            const float E = __fsub_rn(__fmul_rn(-get(cl, j), get(sig4, j)), P);
-            const float num = __fadd_rn(
-                __fsub_rn(__fmul_rn(__fsub_rn(1.f, 0.5f * gm), get(J4, j)), __fmul_rn(get(wr4, j), P)),
-                __fmul_rn(get(wp4, j), E));
-            const float Jn = __fdiv_rn(num, __fadd_rn(1.f, 0.5f * gm));
-            set(Jn4, j, Jn);
-            set(Pn4, j, __fadd_rn(P, Jn));
+            float J = get(J4, j), P = get(P4, j);
+            pole_update(get(cl, j), get(sig4, j), get(wp4, j), get(wr4, j), get(gm4, j), J, P);
+            set(Jn4, j, J);
+            set(Pn4, j, P);
         }
         *reinterpret_cast<float4 *>(q.J + o4) = Jn4;
-        *reinterpret_cast<float4 *>(q.P + o4) = Pn4;
+        *reinterpret_cast<float4 *>(q.Pn + o4) = Pn4;
     }
     const float4 one4 = make_float4(1.f, 1.f, 1.f, 1.f);
     const float4 fx4 = w.fx ? *reinterpret_cast<const float4 *>(w.fx + x0) : one4;

@@ -845,7 +845,7 @@ cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s
     const unsigned blocks = (unsigned)((warps * 32 + BLOCK - 1) / BLOCK);
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
-    const float *Pz = h->disp ? h->d_P : nullptr;
+    const float *Pz = h->disp ? h->pole_P(h->cur) : nullptr;
     const float r = h->aniso_r;
     switch (h->storage) {
         case LBEM_F32: fields2d<LBEM_F32><<<blocks, BLOCK, 0, s>>>(G, in, h->cL2, E, B, h->nsite, w, Pz, r); break;
@@ -931,7 +931,7 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s) {
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
-    const float *Pz = h->disp ? h->d_P : nullptr;
+    const float *Pz = h->disp ? h->pole_P(h->cur) : nullptr;
     const float r = h->aniso_r;
     switch (h->storage) {
         case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;

@@ -109,6 +109,14 @@ StepArgs step_args(const lbem_t *h, int cur_in) {
     a.med.dlnmu = h->has_mu ? h->dlnmu : nullptr;
     a.med.ar = h->aniso_r;
     a.med.amu = h->aniso_mu;
+    if (h->disp) {
+        a.med.wp2 = h->d_wp2;
+        a.med.wr2 = h->d_wr2;
+        a.med.gam = h->d_gam;
+        a.med.J = h->d_J;
+        a.med.Pr = h->pole_P(cur_in);
+        a.med.Pw = h->pole_P(cur_in ^ 1);
+    }
     a.evt.rowptr = h->nev ? h->d_rowptr : nullptr;
     a.evt.ev = h->d_ev;
     a.evt.amp = h->d_amp;
@@ -136,7 +144,8 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
             q.wr2 = h->d_wr2;
             q.gam = h->d_gam;
             q.J = h->d_J;
-            q.P = h->d_P;
+            q.P = a.med.Pr;
+            q.Pn = a.med.Pw;
         }
         q.r = h->aniso_r;
         q.mubar = h->aniso_mu;
@@ -152,19 +161,19 @@ static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16
 
 // Whether launches of two (three) steps apply: 2D; FP32 storage with any medium, 16-bit storage with uniform mu
 // and nx % 4 == 0; three steps per launch exist for FP32 storage with uniform mu.
-// An anisotropic medium takes two steps per launch (tile shape 0) unless it has walls or a pole, which the general
-// single-step kernel handles.
+// An anisotropic medium or a dispersive pole takes two steps per launch (tile shape 0) unless walls or a
+// heterogeneous mu come with it, which the general single-step kernel handles.
 static bool multi_step_base(const lbem_t *h) {
-    if (h->disp || (h->aniso && h->walls())) return false;
+    if (h->general() && (h->walls() || h->has_mu)) return false;
     return h->dim == 2 && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
 }
 static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
 static bool three_step_ok(const lbem_t *h) {
-    return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32 && !h->has_mu && !h->aniso;
+    return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32 && !h->has_mu && !h->general();
 }
 // the two-step tile shape to launch: the one set (or autotuned) when it exists for this medium, else 0
 static int two_step_shape(const lbem_t *h) {
-    if (h->aniso) return 0;
+    if (h->general()) return 0;
     return h->tblock == 2 && h->tb_shape < tb2_nshapes(h->storage, h->has_mu) ? h->tb_shape : 0;
 }
 static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two_step_ok(h) ? 2 : 1; }
@@ -342,7 +351,8 @@ void lbem_destroy(lbem_t *h) {
                     (void *)h->d_ev, (void *)h->d_amp, (void *)h->d_traces, (void *)h->d_partials,
                     (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage, (void *)h->d_fx, (void *)h->d_fy,
                     (void *)h->d_fz,
-                    (void *)h->d_wp2, (void *)h->d_wr2, (void *)h->d_gam, (void *)h->d_J, (void *)h->d_P})
+                    (void *)h->d_wp2, (void *)h->d_wr2, (void *)h->d_gam, (void *)h->d_J, (void *)h->d_P,
+                    (void *)h->d_P2})
         gfree(h, p);
     for (int k = 1; k <= 3; k++) gfree(h, h->d_tiles[k]);
     delete h;
@@ -473,8 +483,8 @@ lbem_status lbem_set_fields(lbem_t *h, const float *E, const float *B) {
     h->wd_last = -1.0;
     if (h->d_traces) LBEM_CUDA(cudaMemsetAsync(h->d_traces, 0, sizeof(float) * (size_t)h->nrec * h->cap, h->stream));
     if (h->disp) {  // the pole starts at rest: D = E
-        LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * (size_t)h->grid.plane, h->stream));
-        LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * (size_t)h->grid.plane, h->stream));
+        for (float *p : {h->d_J, h->d_P, h->d_P2})
+            LBEM_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * (size_t)h->grid.plane, h->stream));
     }
     drop_graph(h);
     return LBEM_OK;
@@ -691,7 +701,7 @@ lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, c
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (!wp2) {  // back to a non-dispersive medium
         LBEM_CUDA(cudaStreamSynchronize(h->stream));
-        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P}) {
+        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P, &h->d_P2}) {
             gfree(h, *p);
             *p = nullptr;
         }
@@ -720,14 +730,13 @@ lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, c
                                          " sites with a parameter not finite and >= 0, or wp^2 + wr^2 > 4 w0");
     const size_t pl = (size_t)h->grid.plane;  // stored as planes with the grid's pitch (padding zero)
     if (!h->d_wp2) {
-        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P})
+        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P, &h->d_P2})
             LBEM_CUDA(gmalloc(h, (void **)p, sizeof(float) * pl, "dispersive pole"));
     }
     const float *src[3] = {dp, dr, dg};
     float *dst[3] = {h->d_wp2, h->d_wr2, h->d_gam};
     for (int k = 0; k < 3; k++) LBEM_CUDA(launch_to_plane(h, src[k], dst[k], h->stream));
-    LBEM_CUDA(cudaMemsetAsync(h->d_J, 0, sizeof(float) * pl, h->stream));
-    LBEM_CUDA(cudaMemsetAsync(h->d_P, 0, sizeof(float) * pl, h->stream));
+    for (float *p : {h->d_J, h->d_P, h->d_P2}) LBEM_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * pl, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     h->disp = true;
     drop_graph(h);
@@ -824,7 +833,7 @@ lbem_status lbem_save_state(lbem_t *h, void *dst) {
     if (h->disp) {  // then the pole's J and P planes
         const size_t pb = sizeof(float) * (size_t)h->grid.plane;
         LBEM_CUDA(cudaMemcpyAsync((char *)dst + db, h->d_J, pb, cudaMemcpyDefault, h->stream));
-        LBEM_CUDA(cudaMemcpyAsync((char *)dst + db + pb, h->d_P, pb, cudaMemcpyDefault, h->stream));
+        LBEM_CUDA(cudaMemcpyAsync((char *)dst + db + pb, h->pole_P(h->cur), pb, cudaMemcpyDefault, h->stream));
     }
     if (!is_device_ptr(dst)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
     return LBEM_OK;
@@ -840,7 +849,7 @@ lbem_status lbem_load_state(lbem_t *h, const void *src, long long t_at_save) {
     if (h->disp) {
         const size_t pb = sizeof(float) * (size_t)h->grid.plane;
         LBEM_CUDA(cudaMemcpyAsync(h->d_J, (const char *)src + db, pb, cudaMemcpyDefault, h->stream));
-        LBEM_CUDA(cudaMemcpyAsync(h->d_P, (const char *)src + db + pb, pb, cudaMemcpyDefault, h->stream));
+        LBEM_CUDA(cudaMemcpyAsync(h->pole_P(h->cur), (const char *)src + db + pb, pb, cudaMemcpyDefault, h->stream));
     }
     if (!is_device_ptr(src)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
     h->t = t_at_save;
@@ -1002,7 +1011,7 @@ lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass) *steps_per_pass = steps_per_launch(h);
     if (tile_shape) *tile_shape = h->tb_shape;
-    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : h->aniso ? 1 : tb2_nshapes(h->storage, h->has_mu);
+    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : h->general() ? 1 : tb2_nshapes(h->storage, h->has_mu);
     return LBEM_OK;
 }
 

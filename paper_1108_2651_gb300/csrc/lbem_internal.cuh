@@ -241,12 +241,11 @@ __device__ __forceinline__ Out5 collide2d(float g0, float g1, float g2, float g3
     return o;
 }
 
-// The site update of an anisotropic medium with per-axis speeds c_x^2 = r c^2, c_y^2 = c^2 / r (general.cu), in the
-// exact operation order of the general kernel with no pole (its P = +0 terms included, so that zeros keep their
-// signs): ri = 1/r, fs = r + 1/r.
+// The site update of the general kernel (general.cu), in its exact operation order: per-axis speeds
+// c_x^2 = r c^2, c_y^2 = c^2 / r (ri = 1/r, fs = r + 1/r; r = 1 isotropic) and the pole's P at t (+0 without a
+// pole, its terms kept so that zeros keep their signs).
 __device__ __forceinline__ Out5 collide2d_an(float g0, float g1, float g2, float g3, float g4, float cl, float shat,
-                                             float r, float ri, float fs) {
-    const float P = 0.f;
+                                             float r, float ri, float fs, float P = 0.f) {
     const float sig = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, g3)), g4);
     const float Lam = __fadd_rn(__fmul_rn(cl, sig), P);
     const float Lx = __fmul_rn(r, Lam), Ly = __fmul_rn(ri, Lam);
@@ -260,6 +259,16 @@ __device__ __forceinline__ Out5 collide2d_an(float g0, float g1, float g2, float
     o.o3 = __fadd_rn(__fsub_rn(Lx, g1), Tx);
     o.o4 = __fadd_rn(__fsub_rn(Ly, g2), Ty);
     return o;
+}
+
+// One step of the dispersive pole at a site (the displacement form of the auxiliary equation, reading R17):
+// E = -c_L^2 sigma - P, J <- ((1 - gam/2) J - wr^2 P + wp^2 E) / (1 + gam/2), P <- P + J.  Shared by the
+// single-step general kernel and the two-step tile kernel so both round identically.
+__device__ __forceinline__ void pole_update(float cl, float sig, float wp, float wr, float gm, float &J, float &P) {
+    const float E = __fsub_rn(__fmul_rn(-cl, sig), P);
+    const float num = __fadd_rn(__fsub_rn(__fmul_rn(__fsub_rn(1.f, 0.5f * gm), J), __fmul_rn(wr, P)), __fmul_rn(wp, E));
+    J = __fdiv_rn(num, __fadd_rn(1.f, 0.5f * gm));
+    P = __fadd_rn(P, J);
 }
 
 // collide2d at a site without a source (S^ = +0): there T_m and T_0 are -0 (c_L^2 > 0, w0 >= 0), and adding
@@ -318,6 +327,10 @@ struct Medium {
     const float *dlnmu = nullptr;  // [D][plane] or null
     // anisotropic medium (general.cu): r = c_x / c_y = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy); 1, 1: isotropic
     float ar = 1.f, amu = 1.f;
+    // one dispersive pole per site (null without; pitched planes): its parameters, J (updated in place) and P,
+    // read from Pr (time t) and written to Pw (the plane of the output state's parity)
+    const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr, *Pr = nullptr;
+    float *J = nullptr, *Pw = nullptr;
 };
 
 // Walls and absorbing layers (walls.cu): per axis x, y 0 = periodic, 1 = PEC wall, 2 = PMC wall; layer
@@ -331,7 +344,9 @@ struct Walls {
 // (axis speeds c_x^2 = r cbar^2, c_y^2 = cbar^2 / r with cbar^2 the stored c_L^2; mubar = sqrt(mu_xx mu_yy)).
 struct General {
     const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr;
-    float *J = nullptr, *P = nullptr;
+    float *J = nullptr;        // updated in place
+    const float *P = nullptr;  // P at t
+    float *Pn = nullptr;       // P at t + 1 (the other plane: neighbouring tiles of a multi-step launch read P at t)
     float r = 1.f, mubar = 1.f;
 };
 // Output rectangle of one edge tile: columns x0 .. x0+w-1, rows y0 .. y0+h-1.
@@ -474,12 +489,16 @@ struct lbem {
     lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     int ntiles[4] = {0, 0, 0, 0};
     // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, planes (pitch layout)
-    float *d_wp2 = nullptr, *d_wr2 = nullptr, *d_gam = nullptr, *d_J = nullptr, *d_P = nullptr;
+    // P has two planes, paired with the population buffers: P at the time of buf[c] is pole_P(c), so a launch
+    // reads P from the plane of its input's parity and writes the other one (every launch flips cur).
+    float *d_wp2 = nullptr, *d_wr2 = nullptr, *d_gam = nullptr, *d_J = nullptr, *d_P = nullptr, *d_P2 = nullptr;
+    float *pole_P(int c) const { return c ? d_P2 : d_P; }
     bool disp = false;
     // anisotropic medium (lbem_set_medium_aniso): r = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy)
     bool aniso = false;
     float aniso_r = 1.f, aniso_mu = 1.f;
-    // steps that only the general single-step kernel takes (general.cu)
+    // media the general kernel steps (general.cu); without walls or mu planes also the tile kernel, two steps
+    // per launch
     bool general() const { return disp || aniso; }
     float aniso_fsum() const { return aniso ? aniso_r + 1.f / aniso_r : 2.f; }  // (c_x^2 + c_y^2) / cbar^2
     size_t tile_smem[4] = {0, 0, 0, 0}, tile_smem_mu[4] = {0, 0, 0, 0};  // uniform / heterogeneous mu

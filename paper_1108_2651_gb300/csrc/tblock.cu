@@ -203,14 +203,28 @@ struct Pull4 {
 #define TB_COMP(v, k) (k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w)
 #define TB_SET(v, k, val) (k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w) = (val)
 
+// The dispersive pole at four sites: P at the current time, J half a step before, and its parameters.
+struct Pole4 {
+    float4 P, J, wp, wr, gm;
+};
+
+// Four values of a pitched plane at row gy, columns gx.. gx+3 (both wrapped periodically): one 16-byte load
+// where the four are inside the grid, else four loads.
+__device__ __forceinline__ float4 ld_plane4(const float *pl, const Grid &G, int gy, int gx) {
+    const float *r = pl + (long long)wrapi(gy, G.ny) * G.pitch;
+    if (gx >= 0 && gx + 3 < G.nx) return *reinterpret_cast<const float4 *>(r + gx);
+    return make_float4(r[wrapi(gx, G.nx)], r[wrapi(gx + 1, G.nx)], r[wrapi(gx + 2, G.nx)], r[wrapi(gx + 3, G.nx)]);
+}
+
 // Four site updates (collide2d each) at global row gy, columns x0+4*lane.., time t.
 // With a heterogeneous permeability (MU) the source carries B_x d_y ln mu - B_y d_x ln mu (dlx, dly: the
 // gradient of ln mu at the four sites) at every site, as in the single-step kernels.
-// With AN (an anisotropic medium, a.med.ar / a.med.amu) the update is collide2d_an, as in the general kernel.
-template <bool EV, bool MU, class PULL, bool AN = false>
+// With AN (an anisotropic medium, a.med.ar / a.med.amu) or POLE (a dispersive pole, state in *pp) the update is
+// the general kernel's collide2d_an with P at t; on owned rows POLE also advances *pp by one step (pole_update).
+template <bool EV, bool MU, class PULL, bool AN = false, bool POLE = false>
 __device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, float4 cl, float4 dlx, float4 dly,
                                             int x0, int gy, long long t, bool owned_row, float4 &o0, float4 &o1,
-                                            float4 &o2, float4 &o3, float4 &o4) {
+                                            float4 &o2, float4 &o3, float4 &o4, Pole4 *pp = nullptr) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -219,15 +233,23 @@ __device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, fl
                     q4 = TB_COMP(g.g4, k), ck = TB_COMP(cl, k);
         Out5 o;
         const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, TB_COMP(dlx, k), TB_COMP(dly, k)) : 0.f;
-        if (AN) {
+        if (AN || POLE) {
             const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
+            const float pz = POLE ? TB_COMP(pp->P, k) : 0.f;
             float shat = 0.f;
             if (EV) {
                 const int gx = x0 + 4 * lane + k;
                 shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, owned_row && gx < G.nx && gy < G.ny, q0,
-                                   q1, q2, q3, q4, ck, 0.f, 0.f, r, ri, a.med.amu);
+                                   q1, q2, q3, q4, ck, 0.f, pz, r, ri, a.med.amu);
             }
-            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs);
+            if (POLE && owned_row) {
+                const float sig = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, q3)), q4);
+                float J = TB_COMP(pp->J, k), Pn = pz;
+                pole_update(ck, sig, TB_COMP(pp->wp, k), TB_COMP(pp->wr, k), TB_COMP(pp->gm, k), J, Pn);
+                TB_SET(pp->J, k, J);
+                TB_SET(pp->P, k, Pn);
+            }
+            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz);
         } else if (EV) {
             const int gx = x0 + 4 * lane + k;
             const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
@@ -258,28 +280,49 @@ __device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, flo
 // py-2); then the ring sites x0-1 (plane 1 only) and x0+TBX (plane 3 only) of rows y0 .. y0+TBY-1.  Also
 // reads into clb the c_L^2 of the warp's step-(t+1) row (and with MU into dbx, dby its gradient of ln mu), as
 // the medium stage is reloaded before step t+1.
-template <int TBY, int NT, bool EV, bool MU = false, bool AN = false>
+// With POLE (a dispersive pole) every warp computes one row (TBY + 2 warps) and step t+1 of row py runs on the
+// same warp, so the pole's state of the warp's owned row stays in registers (Jh, Ph: J at t+1/2, P at t+1).
+template <int TBY, int NT, bool EV, bool MU = false, bool AN = false, bool POLE = false>
 __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, const float *CL, float *P, int x0,
-                                          int y0, long long t, float4 &clb, float4 &dbx, float4 &dby) {
+                                          int y0, long long t, float4 &clb, float4 &dbx, float4 &dby, float4 &Jh,
+                                          float4 &Ph) {
     using Gm = TbGeom<TBY>;
     constexpr int R = Gm::R, NW = NT / 32, PL = Gm::P_PL, DX = R * TW, DY = 2 * R * TW;
+    static_assert(!POLE || NW == R, "with a pole: one warp per row of step t");
     const Grid &G = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c = 4 + 4 * lane;
-    if (warp < TBY) {
-        clb = lds4(CL + (warp + 1) * TW + c);
+    const int bw = warp - (POLE ? 1 : 0);  // the warp's output row of step t+1
+    if (bw >= 0 && bw < TBY) {
+        clb = lds4(CL + (bw + 1) * TW + c);
         if (MU) {
-            dbx = lds4(CL + DX + (warp + 1) * TW + c);
-            dby = lds4(CL + DY + (warp + 1) * TW + c);
+            dbx = lds4(CL + DX + (bw + 1) * TW + c);
+            dby = lds4(CL + DY + (bw + 1) * TW + c);
         }
     }
     for (int py = warp; py < R; py += NW) {
         const Pull4 g(IN, Gm::IN_PL, py, c);
         const float4 cl = lds4(CL + py * TW + c);
         const float4 dlx = MU ? lds4(CL + DX + py * TW + c) : cl, dly = MU ? lds4(CL + DY + py * TW + c) : cl;
+        const bool own = py >= 1 && py <= TBY;
+        Pole4 pp;
+        if (POLE) {
+            const int gy = y0 - 1 + py, gx = x0 + 4 * lane;
+            pp.P = ld_plane4(a.med.Pr, G, gy, gx);
+            pp.J = pp.wp = pp.wr = pp.gm = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (own) {
+                pp.J = ld_plane4(a.med.J, G, gy, gx);
+                pp.wp = ld_plane4(a.med.wp2, G, gy, gx);
+                pp.wr = ld_plane4(a.med.wr2, G, gy, gx);
+                pp.gm = ld_plane4(a.med.gam, G, gy, gx);
+            }
+        }
         float4 o0, o1, o2, o3, o4;
-        tb_update4m<EV, MU, Pull4, AN>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, py >= 1 && py <= TBY, o0, o1, o2,
-                                       o3, o4);
+        tb_update4m<EV, MU, Pull4, AN, POLE>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, own, o0, o1, o2, o3, o4, &pp);
+        if (POLE && own) {
+            Jh = pp.J;
+            Ph = pp.P;
+        }
         float *Pr = P + c;
         if (py >= 1 && py <= TBY) {
             sts4(Pr + 0 * PL + (py - 1) * TW, o0);
@@ -300,12 +343,12 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
         const float ck = CL[py * TW + cc];
         float shat = MU ? mu_source(q4 - q2, q1 - q3, CL[DX + py * TW + cc], CL[DY + py * TW + cc]) : 0.f;
         Out5 o;
-        if (AN) {
+        if (AN || POLE) {
             const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
-            if (EV)
-                shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3,
-                                   q4, ck, 0.f, 0.f, r, ri, a.med.amu);
-            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs);
+            const int gx = wrapi(x0 - 4 + cc, G.nx), gy = wrapi(y0 - 1 + py, G.ny);
+            const float pz = POLE ? a.med.Pr[(long long)gy * G.pitch + gx] : 0.f;
+            if (EV) shat = site_events(a, gx, gy, t, false, q0, q1, q2, q3, q4, ck, 0.f, pz, r, ri, a.med.amu);
+            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz);
         } else {
             if (EV)
                 shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3,
@@ -320,26 +363,39 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
 }
 
 // Step t+1 on tile row y0 + warp from the t+1 stage, written as 16-byte streaming stores.
-template <int TBY, bool EV, bool MU = false, bool AN = false>
+template <int TBY, bool EV, bool MU = false, bool AN = false, bool POLE = false>
 __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, float4 clb, float4 dbx, float4 dby,
-                                          int x0, int y0, long long t) {
+                                          int x0, int y0, long long t, float4 Jh = float4(), float4 Ph = float4()) {
     const Grid &G = a.g;
-    const int lane = threadIdx.x & 31, oy = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, oy = (threadIdx.x >> 5) - (POLE ? 1 : 0);
     const int gy = y0 + oy;
-    if (oy >= TBY || gy >= G.ny) return;
+    if (oy < 0 || oy >= TBY || gy >= G.ny) return;
     const int c = 4 + 4 * lane;
     const Pull4 g(P, TbGeom<TBY>::P_PL, oy, c);
+    Pole4 pp;
+    if (POLE) {
+        const int gx = x0 + 4 * lane;
+        pp.P = Ph;
+        pp.J = Jh;
+        pp.wp = ld_plane4(a.med.wp2, G, gy, gx);
+        pp.wr = ld_plane4(a.med.wr2, G, gy, gx);
+        pp.gm = ld_plane4(a.med.gam, G, gy, gx);
+    }
     float4 o0, o1, o2, o3, o4;
-    tb_update4m<EV, MU, Pull4, AN>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4);
+    tb_update4m<EV, MU, Pull4, AN, POLE>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4, &pp);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
-        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)gy * G.pitch + x0 +
-                                               4 * lane);
+        const long long off = (long long)gy * G.pitch + x0 + 4 * lane;
+        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + off);
         const long long pl4 = G.plane / 4;
         __stcs(o, o0);
         __stcs(o + pl4, o1);
         __stcs(o + 2 * pl4, o2);
         __stcs(o + 3 * pl4, o3);
         __stcs(o + 4 * pl4, o4);
+        if (POLE) {  // J in place (only this site reads it), P to the plane of the output's parity
+            *reinterpret_cast<float4 *>(a.med.J + off) = pp.J;
+            *reinterpret_cast<float4 *>(a.med.Pw + off) = pp.P;
+        }
     }
 }
 #undef TB_SET
@@ -347,7 +403,7 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
 
 // One persistent CTA per SM slot; CTA b takes tiles b, b + gridDim.x, ... (row-major over the tile grid).
 // The window of the next tile is loaded while step t+1 of the current one is computed.
-template <int TBY, int NT, int MINB, bool MU = false, bool AN = false>
+template <int TBY, int NT, int MINB, bool MU = false, bool AN = false, bool POLE = false>
 __global__ void __launch_bounds__(NT, MINB)
     step2d_tb2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
                const __grid_constant__ CUtensorMap tmDL, int use_tma, int ntx, int nty, int dq, int dr) {
@@ -396,20 +452,20 @@ __global__ void __launch_bounds__(NT, MINB)
             mbar_wait(mbar, parity ^ 1u);
             return;
         }
-        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb;
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb, Jh = clb, Ph = clb;
         if (events)
-            tb_step_a<TBY, NT, true, MU, AN>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
+            tb_step_a<TBY, NT, true, MU, AN, POLE>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, Jh, Ph);
         else
-            tb_step_a<TBY, NT, false, MU, AN>(a, IN, CL, P, x0, y0, t, clb, dbx, dby);
+            tb_step_a<TBY, NT, false, MU, AN, POLE>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, Jh, Ph);
         __syncthreads();
         if (has_next)  // the t stage and the medium stage are free: start the loads of the next tile
             tb_load<TBY, MU>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar,
                              use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, NT, &tmDL);
         asm volatile("cp.async.commit_group;\n" ::);
         if (events)
-            tb_step_b<TBY, true, MU, AN>(a, P, clb, dbx, dby, x0, y0, t);
+            tb_step_b<TBY, true, MU, AN, POLE>(a, P, clb, dbx, dby, x0, y0, t, Jh, Ph);
         else
-            tb_step_b<TBY, false, MU, AN>(a, P, clb, dbx, dby, x0, y0, t);
+            tb_step_b<TBY, false, MU, AN, POLE>(a, P, clb, dbx, dby, x0, y0, t, Jh, Ph);
         tx = ntx_;
         ty = nty_;
         events = events_next;
@@ -753,18 +809,19 @@ static bool make_dl_map(const StepArgs &a, CUtensorMap *mDL) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TBY, int NT, int MINB, bool MU = false, bool AN = false>
+template <int TBY, int NT, int MINB, bool MU = false, bool AN = false, bool POLE = false>
 static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     using Gm = TbGeom<TBY, MU>;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB, MU, AN>,
+        cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB, MU, AN, POLE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB, MU, AN>, NT, Gm::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_tb2<TBY, NT, MINB, MU, AN, POLE>, NT,
+                                                      Gm::BYTES);
         if (per_sm < 1) per_sm = 1;
     }
     CUtensorMap mIn, mCL, mDL;
@@ -775,8 +832,8 @@ static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
     const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
     const int ntiles = ntx * nty;
     const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
-    step2d_tb2<TBY, NT, MINB, MU, AN><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, use_tma, ntx, nty, blocks / ntx,
-                                                                blocks % ntx);
+    step2d_tb2<TBY, NT, MINB, MU, AN, POLE>
+        <<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, use_tma, ntx, nty, blocks / ntx, blocks % ntx);
     return cudaGetLastError();
 }
 
@@ -1196,6 +1253,7 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
         default: break;
     }
+    if (a.med.wp2) return launch_tb<6, 256, 4, false, false, true>(a, s);  // a dispersive pole (any tensor)
     if (a.med.ar != 1.f || a.med.amu != 1.f) return launch_tb<6, 256, 5, false, true>(a, s);  // anisotropic
     if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)

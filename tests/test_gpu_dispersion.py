@@ -2,7 +2,8 @@
 
 Tolerance as for the periodic parity tests: relative L2 of E, B and receiver traces <= 1e-5 against the FP64
 oracle (FP32 arithmetic).  Also: the lattice plasma dispersion of a Drude plane wave, graphs and split step counts
-bit for bit, save / load of the pole's state, and the argument, state and stability errors.
+bit for bit, two steps per launch against single steps bit for bit, save / load of the pole's state, and the
+argument, state and stability errors.
 """
 import numpy as np
 import pytest
@@ -114,6 +115,43 @@ def test_dispersive_graphs_splits_and_state_round_trip(lbem):
     np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
     np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1])
     np.testing.assert_array_equal(tr.cpu().double().numpy()[:, :31], ref[2])
+
+
+@pytest.mark.parametrize("shape,aniso", [((1, 1), None), ((3, 5), None), ((37, 130), None), ((130, 259), None),
+                                         ((40, 70), (2.0, 1.3))])
+def test_two_step_launches_equal_single_steps_bit_for_bit(lbem, shape, aniso):
+    """Without walls or a heterogeneous mu a dispersive medium steps in pairs (the tile kernel carrying the pole's
+    J and P; P alternates between two planes with the population buffers): the same bits as one step per launch,
+    with and without graph replay, odd step counts, and a save / load across launches of both parities."""
+    import torch
+
+    p = _problem(shape, 600 + shape[1], 40)
+    if aniso is not None:  # a uniform tensor with the pole: the pole's bound uses the per-axis rest weight
+        p.aniso = aniso
+        p.wp2 = p.wp2 * 0.5
+        p.wr2 = p.wr2 * 0.5
+    ref = gpu_run(p, steps_per_pass=1)
+    for graphs in (False, True):
+        stream = torch.cuda.Stream()  # graph capture needs a non-default stream
+        s = lbem.Solver(p.shape, stream=stream.cuda_stream)
+        s.set_problem(p)
+        assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2
+        lbem.lbem_set_graphs(s.h, graphs)
+        s.step(7)  # three pairs and a single step
+        saved = torch.empty(lbem.lbem_info(s.h)[1], dtype=torch.uint8, device="cuda")
+        lbem.lbem_save_state(s.h, saved)
+        s.step(9)
+        lbem.lbem_load_state(s.h, saved, 7)  # back to t = 7 with the buffers' parity flipped
+        s.step(20)
+        s.step(13)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        lbem.lbem_check_guards(s.h)
+        s.close()
+        np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0])
+        np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1])
+        np.testing.assert_array_equal(tr.cpu().double().numpy()[:, :40], ref[2])
 
 
 def test_dispersion_full_size_matches_oracle(lbem):
