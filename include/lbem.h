@@ -125,9 +125,10 @@ lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r);
  * -cbar^2 sigma with cbar^2 = sqrt(c_x^2 c_y^2), B_x = r (g_4 - g_2), B_y =
  * (g_1 - g_3) / r, r = sqrt(mu_xx / mu_yy); a current j_z enters with
  * mu = sqrt(mu_xx mu_yy).  mu_xx = mu_yy = mu is the isotropic scheme with a
- * uniform mu.  2D, LBEM_F32 storage (LBEM_ERR_ARG otherwise); the handle then
- * steps one step per launch with the general kernel (walls, layers and a
- * dispersive pole included); lbem_set_medium makes it isotropic again.  Batches
+ * uniform mu.  2D, LBEM_F32 storage (LBEM_ERR_ARG otherwise); with walls the
+ * handle then steps one step per launch with the general kernel (layers and a
+ * dispersive pole included), without walls in pairs (lbem_set_temporal_blocking),
+ * bit-identical to single steps; lbem_set_medium makes it isotropic again.  Batches
  * and the adjoint take isotropic handles only.  Synchronises the stream. */
 lbem_status lbem_set_medium_aniso(lbem_t *h, const float *eps_r, double mu_xx, double mu_yy);
 

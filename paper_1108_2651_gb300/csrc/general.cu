@@ -34,14 +34,17 @@
 // - P, B_x = r (g_4 - g_2), B_y = (g_1 - g_3) / r.  r = 1 with no pole is the
 // plain scheme.
 //
-// step2d_gen is the single-step kernel for the media the fast kernels do not
-// cover (a pole, an anisotropic tensor).  Thread mapping as the plain
-// single-step kernel: one warp covers 128 consecutive sites of a row, 4 per
-// lane, with 16-byte loads and the +-x pulls by warp shuffle (pull2d); pulls
-// across a wall are then replaced by the wall rule of walls.cu.  Per site: the
-// B x grad ln mu source, sources and receivers, the pole, the collision, the
-// absorbing layer's factor.  The pole's arrays are planes like c_L^2; J and P
-// are read and written at the site only, so they are updated in place.
+// step2d_gen is the single-step kernel for these media (a pole, an anisotropic
+// tensor), with walls and layers too.  Without walls the two-step tile kernel
+// (tblock.cu) also steps them, with the same site update (collide2d_an,
+// pole_update).  Thread mapping as the plain single-step kernel: one warp
+// covers 128 consecutive sites of a row, 4 per lane, with 16-byte loads and
+// the +-x pulls by warp shuffle (pull2d); pulls across a wall are then replaced
+// by the wall rule of walls.cu.  Per site: the B x grad ln mu source, sources
+// and receivers, the pole, the collision, the absorbing layer's factor.  The
+// pole's arrays are planes like c_L^2; J is read and written at the site only
+// (in place), P is read from the plane of the input's parity and written to
+// the other (a two-step launch reads P at sites of neighbouring tiles).
 #include <algorithm>
 
 #include "lbem_internal.cuh"

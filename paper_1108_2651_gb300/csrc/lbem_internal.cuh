@@ -340,7 +340,8 @@ struct Walls {
     const float *fx = nullptr, *fy = nullptr, *fz = nullptr;
 };
 // What the general single-step kernel (general.cu) adds to a step: one Drude-Lorentz pole per site (parameters
-// and state as planes with the grid's pitch, J at t - 1/2, P at t; wp2 null: no pole) and a uniform in-plane permeability tensor
+// and state as planes with the grid's pitch, J at t - 1/2 (in place), P at t read from P and written to Pn; wp2
+// null: no pole) and a uniform in-plane permeability tensor
 // (axis speeds c_x^2 = r cbar^2, c_y^2 = cbar^2 / r with cbar^2 the stored c_L^2; mubar = sqrt(mu_xx mu_yy)).
 struct General {
     const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr;
