@@ -14,6 +14,8 @@ E_z obeys the 4th-order linear recurrence whose characteristic polynomial is zet
 a lossless Drude medium (wr = gamma = 0) it is a single pair, 4 sin^2(omega/2) = 4 c^2 q + wp^2, the lattice form
 of omega^2 = wp^2 + c^2 k^2 (plasma waves).  Plus: no pole (wp = 0) is the plain scheme; a uniform field in a
 lossless Drude medium oscillates at 2 sin(omega/2) = wp with D constant; the stability bound wp^2 + wr^2 <= 4 w0.
+With an anisotropic tensor (per-axis speeds) the lattice's Laplacian splits by axis, so 4 c^2 q becomes
+4 (c_x^2 sin^2(kx/2) + c_y^2 sin^2(ky/2)) in the same relation.
 """
 import numpy as np
 import pytest
@@ -24,9 +26,9 @@ import oracle as O
 N = 24
 
 
-def _amplitudes(w_eps, mode, disp, T=60):
+def _amplitudes(w_eps, mode, disp, T=60, aniso=None):
     """Fourier amplitude of E_z(t) for the plane wave E_z = cos(k.x) released from equilibrium at rest."""
-    m = O.medium(2, np.full((N, N), w_eps), dispersion=disp)
+    m = O.medium(2, np.full((N, N), w_eps), dispersion=disp, aniso=aniso)
     kx, ky = 2 * np.pi * mode[0] / N, 2 * np.pi * mode[1] / N
     y, x = np.mgrid[0:N, 0:N]
     E = np.zeros((N, N, 3))
@@ -125,3 +127,30 @@ def test_stability_bound():
         q = 2.0
         p = _charpoly(c2, q, wp2, 0.0, 0.0)
         assert (np.abs(Pn.polyroots(p)).max() > 1 + 1e-6) == grows
+
+
+@pytest.mark.parametrize("aniso,mode,disp", [((2.0, 1.0), (2, 5), dict(wp2=0.2)), ((3.0, 1.5), (0, 4), dict(wp2=0.5)),
+                                             ((1.2, 2.5), (3, 1), dict(wp2=0.3, wr2=0.2, gamma=0.1)),
+                                             ((3.0, 1.5), (5, 2), dict(wp2=0.1, wr2=0.05))])
+def test_pole_in_an_anisotropic_medium_follows_the_per_axis_discrete_permittivity(aniso, mode, disp):
+    """The pole and the anisotropic tensor together.  E = D/eps_inf - P enters the second moment per axis, so
+    with u = D/eps_inf the lattice gives A u = -L (u - P) and the pole A P = wp^2 (u - P) (lossless Drude),
+    L = 4 (c_x^2 sin^2(kx/2) + c_y^2 sin^2(ky/2)), c_x^2 = c^2/(eps mu_yy), c_y^2 = c^2/(eps mu_xx); hence
+    4 sin^2(omega/2) = L + wp^2, and with wr, gamma the same recurrence as the isotropic pole with 4 c^2 q -> L."""
+    w_eps = 1.6
+    amp, _, _ = _amplitudes(w_eps, mode, disp, aniso=aniso)
+    kx, ky = 2 * np.pi * mode[0] / N, 2 * np.pi * mode[1] / N
+    cq = 0.5 / (w_eps * aniso[1]) * np.sin(kx / 2) ** 2 + 0.5 / (w_eps * aniso[0]) * np.sin(ky / 2) ** 2
+    if set(disp) == {"wp2"}:
+        om = 2 * np.arcsin(np.sqrt(cq + disp["wp2"] / 4))
+        t = np.arange(amp.size)
+        b = (amp[1] - amp[0] * np.cos(om)) / np.sin(om)
+        np.testing.assert_allclose(amp, amp[0] * np.cos(om * t) + b * np.sin(om * t), rtol=0, atol=1e-12)
+    p = _charpoly(cq, 1.0, disp["wp2"], disp.get("wr2", 0.0), disp.get("gamma", 0.0))
+    res = np.array([np.dot(p, amp[t:t + p.size]) for t in range(amp.size - p.size + 1)])
+    assert np.abs(res).max() < 1e-13
+    # a plausible mistake, the isotropic c^2 (mean of the axes) in place of the per-axis split, fails the recurrence
+    cbar = 0.25 / w_eps * (1 / aniso[0] + 1 / aniso[1]) * (np.sin(kx / 2) ** 2 + np.sin(ky / 2) ** 2)
+    if abs(cbar - cq) > 1e-3:
+        pw = _charpoly(cbar, 1.0, disp["wp2"], disp.get("wr2", 0.0), disp.get("gamma", 0.0))
+        assert np.abs([np.dot(pw, amp[t:t + pw.size]) for t in range(amp.size - pw.size + 1)]).max() > 1e-6
