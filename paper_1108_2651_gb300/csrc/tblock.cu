@@ -310,6 +310,10 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
             const int gy = y0 - 1 + py, gx = x0 + 4 * lane;
             pp.P = ld_plane4(a.med.Pr, G, gy, gx);
             pp.J = pp.wp = pp.wr = pp.gm = make_float4(0.f, 0.f, 0.f, 0.f);
+            // J is updated in place by the tile owning the site.  Lanes past nx (rows past ny) of a ragged last
+            // tile read J at wrapped sites of another tile, which may be updating them: their pole results only
+            // ever reach the row padding or are dropped, while the collisions they feed use P at t, which no
+            // launch writes in place.
             if (own) {
                 pp.J = ld_plane4(a.med.J, G, gy, gx);
                 pp.wp = ld_plane4(a.med.wp2, G, gy, gx);
