@@ -1,6 +1,6 @@
 """Spatial domain decomposition (slabs along the slowest axis, one ghost layer, halo exchange after each step).
 
-On the host: world-size-2 gloo ranks, each stepping its slab with the FP64 oracle and exchanging the
+On the host: world-size-2 and -3 gloo ranks, each stepping its slab with the FP64 oracle and exchanging the
 populations that cross the cuts through torch.distributed, must reproduce the single-domain oracle bit for bit
 (2D and 3D, heterogeneous eps and mu, sources and receivers on either slab; also a uniform anisotropic tensor, a
 dispersive pole, and walls with absorbing layers on the axes along the cuts).  On the GPU: two or three slabs
@@ -134,9 +134,11 @@ def _rank_main(rank, world, port, D, shape, nsteps, kind, q):
 
 
 @pytest.mark.timeout(600)
-@pytest.mark.parametrize("D,shape,kind", [(2, (11, 13), "mu"), (3, (7, 4, 5), "mu"), (2, (11, 13), "aniso"),
-                                          (2, (11, 13), "drude"), (2, (11, 13), "walls"), (3, (7, 6, 5), "walls")])
-def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind):
+@pytest.mark.parametrize("D,shape,kind,world", [(2, (11, 13), "mu", 2), (3, (7, 4, 5), "mu", 2),
+                                                (2, (11, 13), "aniso", 2), (2, (11, 13), "drude", 2),
+                                                (2, (11, 13), "walls", 2), (3, (7, 6, 5), "walls", 2),
+                                                (2, (11, 13), "mu", 3), (3, (8, 6, 5), "walls", 3)])
+def test_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind, world):
     import torch.multiprocessing as mp
 
     import oracle as O
@@ -146,11 +148,11 @@ def test_two_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, D, shape, nsteps, kind, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, D, shape, nsteps, kind, q)) for r in range(world)]
     for pr in procs:
         pr.start()
     got = []
-    while len(got) < 2:  # fail as soon as a rank dies instead of waiting for its result
+    while len(got) < world:  # fail as soon as a rank dies instead of waiting for its result
         try:
             got.append(q.get(timeout=2))
         except queue.Empty:
