@@ -133,6 +133,51 @@ def _rank_main(rank, world, port, D, shape, nsteps, kind, q):
     q.put((rank, start, count, E, B, recs, tr, float(en[0])))
 
 
+@pytest.mark.parametrize("n,world", [(11, 2), (11, 3), (7, 7), (64, 5), (1, 1)])
+def test_slab_ranges_partition_the_layers(n, world):
+    sys.path.insert(0, ROOT)
+    from paper_1108_2651_gb300 import decomp
+
+    parts = [decomp.slab_range(n, world, r) for r in range(world)]
+    assert parts[0][0] == 0 and sum(c for _, c in parts) == n
+    for (s0, c0), (s1, _) in zip(parts, parts[1:]):
+        assert s0 + c0 == s1  # contiguous, in rank order
+    counts = [c for _, c in parts]
+    assert max(counts) - min(counts) <= 1 and min(counts) >= 1
+
+
+def test_local_problem_layers_receivers_and_refusals():
+    """A slab holds its real layers plus the periodic neighbours as ghosts, the sources and receivers of its real
+    layers only (renumbered), per-site pole parameters cut like eps; walls across the slab axis are refused, and so
+    are more ranks than layers."""
+    sys.path.insert(0, ROOT)
+    from paper_1108_2651_gb300 import decomp
+
+    p = _problem(2, (11, 13), 5, 4, "drude")
+    per_layer = 13
+    seen = 0
+    for rank in range(3):
+        loc, start, count, recs = decomp.local_problem(p, rank, 3)
+        layers = np.arange(start - 1, start + count + 1) % 11
+        assert loc.shape == (count + 2, 13)
+        np.testing.assert_array_equal(loc.eps_r, np.asarray(p.eps_r)[layers])
+        np.testing.assert_array_equal(loc.wp2, np.asarray(p.wp2)[layers])
+        np.testing.assert_array_equal(loc.E0, np.asarray(p.E0)[layers])
+        g = p.rec_site[recs]
+        assert np.all((g // per_layer >= start) & (g // per_layer < start + count))
+        np.testing.assert_array_equal(loc.rec_site, (g // per_layer - start + 1) * per_layer + g % per_layer)
+        np.testing.assert_array_equal(loc.rec_comp, p.rec_comp[recs])
+        assert np.all(loc.src_site // per_layer >= 1) and np.all(loc.src_site // per_layer <= count)
+        seen += recs.size
+    assert seen == p.rec_site.size  # every receiver on exactly one slab
+    q = _problem(2, (11, 13), 5, 4, "walls")
+    q.bc = (0, 1, 0)  # a wall across the slab axis (y)
+    with pytest.raises(AssertionError):
+        decomp.local_problem(q, 0, 2)
+    with pytest.raises(AssertionError):
+        decomp.local_problem(_problem(2, (3, 13), 5, 4), 3, 4)  # 3 layers, 4 ranks: the last one gets none
+
+
 @pytest.mark.timeout(600)
 @pytest.mark.parametrize("D,shape,kind,world", [(2, (11, 13), "mu", 2), (3, (7, 4, 5), "mu", 2),
                                                 (2, (11, 13), "aniso", 2), (2, (11, 13), "drude", 2),
