@@ -697,8 +697,12 @@ def main():
         cpu = cpu_baseline(p)
     s.close()
     if rank == 0:
+        # per pass: the step launches (plus the edge kernel after each with 2D walls on the tile path), the medium
+        # upload's check and write (plus the pole's re-check, and the wall-aware grad ln mu with walls and mu),
+        # init, fields, the FP64 diagnostics and its reduction
         launches = args.steps * (step_launches * (2 if walls and p.D == 2 and not (disp or aniso) else 1) + 6 +
-                                 (1 if args.storage == "f16" else 0))
+                                 (1 if args.storage == "f16" else 0) + (1 if disp else 0) +
+                                 (1 if walls and p.mu_r is not None else 0))
         line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32-math/{args.storage}-storage",
