@@ -1,4 +1,7 @@
-// Two time steps per pass (temporal blocking), 2D, FP32 storage, uniform mu.
+// Two time steps per pass (temporal blocking), 2D, FP32 storage; uniform mu, and variants for a heterogeneous mu
+// (MU: the grad ln mu planes staged beside c_L^2), an anisotropic tensor (AN) and a dispersive pole (POLE), the
+// last two with the general kernel's site update (collide2d_an, pole_update), so that they too are bit-identical
+// to single steps of general.cu.
 //
 // A persistent CTA takes tiles of 128 x TBY sites in turn.  For each it loads
 // the post-collision state at t of the tile plus a halo of 2 sites (one per
