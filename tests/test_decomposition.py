@@ -178,6 +178,27 @@ def test_local_problem_layers_receivers_and_refusals():
         decomp.local_problem(_problem(2, (3, 13), 5, 4), 3, 4)  # 3 layers, 4 ranks: the last one gets none
 
 
+def test_slabs_without_the_exchange_drift_from_the_whole_grid():
+    """The negative control: the same oracle slabs stepped without the halo exchange (each its own periodic grid)
+    do not reproduce the whole grid, so the exchange is what makes the bitwise agreement."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from gpu_helpers import oracle_run, rel
+    from paper_1108_2651_gb300 import decomp
+
+    p = _problem(2, (11, 13), 9, 12)
+    E, B, _, _, _ = oracle_run(p)
+    errs = []
+    for rank in range(2):
+        loc, start, count, _ = decomp.local_problem(p, rank, 2)
+        slab = OracleSlab(loc, count)
+        for _ in range(12):
+            slab.step()
+        Es, _ = slab.fields()
+        errs.append(rel(Es, E[start:start + count]))
+    print("rel-L2 of E without the exchange per slab:", errs)
+    assert min(errs) > 0.05
+
+
 @pytest.mark.timeout(600)
 @pytest.mark.parametrize("D,shape,kind,world", [(2, (11, 13), "mu", 2), (3, (7, 4, 5), "mu", 2),
                                                 (2, (11, 13), "aniso", 2), (2, (11, 13), "drude", 2),
