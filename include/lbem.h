@@ -321,7 +321,9 @@ lbem_status lbem_check_guards(lbem_t *h);
  * downwards, ny rows each).  Copies nrows rows (2D: row = y; 3D: row = y + ny z)
  * starting at row0 of plane `plane` to (to_state = 0) or from (to_state = 1)
  * buf, [nrows][nx] floats, host or device.  LBEM_F32 storage; a decomposed
- * handle must step one step per launch (lbem_set_temporal_blocking(h, 1, -1)).
+ * handle must step one step per launch (lbem_set_temporal_blocking(h, 1, -1)).  A
+ * dispersive pole's J and P and an anisotropic tensor need no exchange (site-local
+ * and uniform); walls may close the axes along the cuts, not the slab axis.
  * LBEM_ERR_ARG for planes or rows out of range.  Host buffers synchronise the
  * stream. */
 lbem_status lbem_rows(lbem_t *h, int plane, int row0, int nrows, float *buf, int to_state);
