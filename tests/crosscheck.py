@@ -20,6 +20,13 @@ statements of what the paper fixes, written from the mathematics.
 * maxwell_ps_2d / maxwell_ps_3d: pseudo-spectral Maxwell solvers with
   classical RK4 (the paper validates against a pseudo-spectral solver with an
   optimised Runge-Kutta scheme whose coefficients it does not give).
+* maxwell_ps_2d_h / maxwell_ps_3d_h: the same in the H form for a medium with
+  heterogeneous eps and mu, d_t B = -curl E, d_t E = (c_ref^2/eps_r) curl(B/mu_r).
+  No gradient of ln mu appears: the permeability enters only through H = B/mu,
+  differentiated spectrally, so these solvers pin the paper's Eq. 3 source
+  c^2 (B x grad ln mu) without restating it.
+* fresnel: normal-incidence reflection and transmission of E at an impedance
+  step, Z = sqrt(mu/eps).
 * spectral_divb_error: Eq. 19 with F = 1.
 """
 import numpy as np
@@ -122,6 +129,65 @@ def maxwell_ps_3d(c2, E, B, t_end, dt, L=1.0):
         k4 = rhs(y + h * k3)
         y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
     return y[:3], y[3:]
+
+
+def maxwell_ps_2d_h(ceps2, mu, E, Bx, By, t_end, dt, L=1.0):
+    """TM Maxwell in the H form on a periodic [y, x] grid of side L, for eps and mu that vary in space:
+        dBx/dt = -dE/dy, dBy/dt = dE/dx, dE/dt = ceps2 (d(By/mu)/dx - d(Bx/mu)/dy),
+    ceps2 = c_ref^2 / eps_r (so that the local wave speed squared is ceps2 / mu).  This is the form
+    eps dE/dt = curl H with H = B/mu; expanding curl(B/mu) gives the c^2 (B x grad ln mu) source of Eq. 3,
+    which is never formed here.  Spectral derivatives, classical RK4 with step <= dt."""
+    ky, kx = _kgrid(E.shape, L)
+    nst = int(np.ceil(t_end / dt - 1e-12))
+    h = t_end / nst
+
+    def rhs(y):
+        e, bx, by = y
+        de = ceps2 * (_deriv(by / mu, kx) - _deriv(bx / mu, ky))
+        return np.array([de, -_deriv(e, ky), _deriv(e, kx)])
+
+    y = np.array([E, Bx, By], dtype=np.float64)
+    for _ in range(nst):
+        k1 = rhs(y)
+        k2 = rhs(y + h / 2 * k1)
+        k3 = rhs(y + h / 2 * k2)
+        k4 = rhs(y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return y
+
+
+def maxwell_ps_3d_h(ceps2, mu, E, B, t_end, dt, L=1.0):
+    """dB/dt = -curl E, dE/dt = ceps2 curl(B/mu) on a periodic [z, y, x] grid (the H form in 3D); E, B of
+    shape (3,) + grid.  Spectral derivatives, classical RK4."""
+    kz, ky, kx = _kgrid(E.shape[1:], L)
+    K = (kx, ky, kz)
+    nst = int(np.ceil(t_end / dt - 1e-12))
+    h = t_end / nst
+
+    def curl(v):
+        d = [[_deriv(v[a], K[b]) for b in range(3)] for a in range(3)]  # d[a][b] = d_b v_a
+        return np.array([d[2][1] - d[1][2], d[0][2] - d[2][0], d[1][0] - d[0][1]])
+
+    def rhs(y):
+        e, b = y[:3], y[3:]
+        return np.concatenate([ceps2 * curl(b / mu), -curl(e)])
+
+    y = np.concatenate([E, B]).astype(np.float64)
+    for _ in range(nst):
+        k1 = rhs(y)
+        k2 = rhs(y + h / 2 * k1)
+        k3 = rhs(y + h / 2 * k2)
+        k4 = rhs(y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return y[:3], y[3:]
+
+
+def fresnel(eps1, mu1, eps2, mu2):
+    """Reflection and transmission coefficients of E for a plane wave at normal incidence on the interface
+    between two uniform media (continuity of tangential E and H = B/mu):
+        r = (Z2 - Z1)/(Z2 + Z1), t = 1 + r = 2 Z2/(Z2 + Z1), Z = sqrt(mu/eps)."""
+    z1, z2 = np.sqrt(mu1 / eps1), np.sqrt(mu2 / eps2)
+    return (z2 - z1) / (z2 + z1), 2 * z2 / (z2 + z1)
 
 
 def spectral_divb_error(Bx, By, L=1.0):
