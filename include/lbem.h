@@ -278,22 +278,28 @@ lbem_status lbem_traces(lbem_t *h, float *out, int *nrecorded);
  * fixed order.  LBEM_ERR_UNSTABLE if any of the three is not finite. */
 lbem_status lbem_diagnostics(lbem_t *h, double out[3]);
 
-/* Same three FP64 diagnostics as lbem_diagnostics, for callers that cannot
+/* The three FP64 diagnostics of lbem_diagnostics, for callers that cannot
  * allocate device memory (for example a program that hands all device memory
  * to its own pool at start-up, or a loop whose memory budget is fixed after
  * initialisation); the paper has no counterpart.  It takes no handle and
  * allocates nothing: inputs and output are the caller's device memory, and
  * the only scratch (per-block partial sums, 192 KiB) is a static device array
  * of the library, held by every GPU that loads the library until exit.
+ * Scope: the state of a periodic, isotropic, non-dispersive handle (no walls,
+ * no lbem_set_medium_aniso tensor, no lbem_set_dispersion pole); for other
+ * handles the sums are not those of lbem_diagnostics (use that call).
  *   state : FP32 distribution in the layout lbem_save_state writes for an
- *           LBEM_F32 handle of this geometry (device memory)
- *   eps_r, mu_r : the medium as given to lbem_set_medium ([nsite], device;
- *           mu_r may be NULL); c_ref2 as in lbem_desc (<= 0: default)
+ *           LBEM_F32 handle of this geometry (device memory): npop planes
+ *           (5 in 2D, 21 in 3D) of ny*nz rows of round_up(nx, 32) floats,
+ *           4 * npop * round_up(nx, 32) * ny * nz bytes
+ *   eps_r, mu_r : the medium as given to lbem_set_medium ([nsite] floats,
+ *           device; mu_r may be NULL); c_ref2 as in lbem_desc (<= 0: default)
  *   out   : 3 doubles of device memory, written asynchronously on `stream`
- * Grids above 33554432 sites are rejected (LBEM_ERR_ARG), as are host
- * pointers.  The first call on a device looks up the static array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race. */
+ * LBEM_ERR_ARG, with nothing launched, for grids above 33554432 sites, host
+ * pointers, or a buffer whose device allocation ends before the bytes above.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race. */
 lbem_status lbem_diagnostics_static(int dim, int nx, int ny, int nz, const void *state, const float *eps_r,
                                     const float *mu_r, double c_ref2, double *out, void *stream);
 

@@ -12,6 +12,12 @@
 // kSitesPerBlock sites, so grids of more than kStaticBlocks * kSitesPerBlock
 // sites are rejected (LBEM_ERR_ARG).
 //
+// Scope: the state of a periodic, isotropic, non-dispersive handle (lbem_set_medium, no walls, no pole, no
+// anisotropic tensor); for such a state the three sums are those of lbem_diagnostics.  Before anything is
+// launched, each caller buffer is checked against the extent of the device allocation that holds it
+// (cuMemGetAddressRange, fetched through the runtime's driver entry point), so an undersized or unpadded
+// state is an argument error and not an out-of-bounds read.
+//
 // Set-up: the first call on each device, with that device current, looks up
 // the array's device address with cudaGetSymbolAddress (the host-side name of
 // a __device__ array is only a stand-in and must not be passed to a kernel).
@@ -19,6 +25,7 @@
 // device.  Every call shares the one array; a call overwrites every slot it
 // later reads, so nothing needs clearing, but calls that overlap on the GPU
 // (on different streams without ordering) race on it.
+#include <cuda.h>
 #include <math.h>
 
 #include <mutex>
@@ -58,6 +65,40 @@ static bool on_device(const void *p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+using AddressRange = CUresult (*)(CUdeviceptr *, size_t *, CUdeviceptr);
+
+static AddressRange address_range_fn() {
+    static AddressRange fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<AddressRange>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Whether `bytes` bytes from p lie inside the device allocation that holds p.
+static lbem_status check_extent(const void *p, size_t bytes, const char *what) {
+    AddressRange fn = address_range_fn();
+    if (!fn) return fail(LBEM_ERR_CUDA, "lbem_diagnostics_static: cuMemGetAddressRange is unavailable");
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (CUdeviceptr)p) != CUDA_SUCCESS)
+        return fail(LBEM_ERR_ARG, std::string("lbem_diagnostics_static: the extent of ") + what +
+                                      " cannot be determined (not a device allocation)");
+    const size_t avail = (size_t)(base + size - (CUdeviceptr)p);
+    if (avail < bytes)
+        return fail(LBEM_ERR_ARG, std::string("lbem_diagnostics_static: ") + what + " needs " + std::to_string(bytes) +
+                                      " bytes but its allocation ends after " + std::to_string(avail));
+    return LBEM_OK;
 }
 
 struct StaticGeom {
@@ -181,17 +222,27 @@ extern "C" lbem_status lbem_diagnostics_static(int dim, int nx, int ny, int nz, 
     if (dim != 2 && dim != 3) return fail(LBEM_ERR_ARG, "lbem_diagnostics_static: dim must be 2 or 3");
     if (dim == 2) nz = 1;
     if (nx < 1 || ny < 1 || nz < 1) return fail(LBEM_ERR_ARG, "lbem_diagnostics_static: grid sizes must be >= 1");
+    // each factor bounded by division first, so the product below cannot overflow
+    const long long limit = (long long)kStaticBlocks * kSitesPerBlock;
+    if (nx > limit || ny > limit / nx || nz > limit / ((long long)nx * ny))
+        return fail(LBEM_ERR_ARG, "lbem_diagnostics_static: grid of " + std::to_string(nx) + " x " +
+                                      std::to_string(ny) + " x " + std::to_string(nz) +
+                                      " sites exceeds the static scratch limit of " + std::to_string(limit) +
+                                      " sites");
     const long long nsite = (long long)nx * ny * nz;
     const long long nblocks = (nsite + kSitesPerBlock - 1) / kSitesPerBlock;
-    if (nblocks > kStaticBlocks)
-        return fail(LBEM_ERR_ARG, "lbem_diagnostics_static: grid of " + std::to_string(nsite) +
-                                      " sites exceeds the static scratch limit of " +
-                                      std::to_string((long long)kStaticBlocks * kSitesPerBlock) + " sites");
     if (!state || !eps_r || !out) return fail(LBEM_ERR_ARG, "lbem_diagnostics_static: null pointer");
     if (!on_device(state) || !on_device(eps_r) || !on_device(out) || (mu_r && !on_device(mu_r)))
         return fail(LBEM_ERR_ARG, "lbem_diagnostics_static: state, eps_r, mu_r and out must be device memory");
+    const int npop = dim == 2 ? 5 : 21;
+    const size_t state_bytes = sizeof(float) * (size_t)npop * (size_t)round_up(nx, 32) * (size_t)ny * (size_t)nz;
+    lbem_status st = check_extent(state, state_bytes, "state");
+    if (st == LBEM_OK) st = check_extent(eps_r, sizeof(float) * (size_t)nsite, "eps_r");
+    if (st == LBEM_OK && mu_r) st = check_extent(mu_r, sizeof(float) * (size_t)nsite, "mu_r");
+    if (st == LBEM_OK) st = check_extent(out, 3 * sizeof(double), "out");
+    if (st != LBEM_OK) return st;
     double *scratch = nullptr;
-    lbem_status st = scratch_address(&scratch);
+    st = scratch_address(&scratch);
     if (st != LBEM_OK) return st;
     StaticGeom g;
     g.D = dim;
