@@ -95,6 +95,15 @@ lbem_status lbem_set_stream(lbem_t *h, void *stream);
  * if a shared-memory tile load of the two-step kernel (lbem_set_temporal_blocking) gave up waiting. */
 lbem_status lbem_sync(lbem_t *h);
 
+/* Limit of the bounded device-side waits on the current device (all handles on it): a CTA of the two- and
+ * three-step kernels that has waited this long for its tile's TMA window gives up, lets the copies in flight
+ * land (bounded again, 2 s, independent of this limit), records the failure and exits, and the next lbem_sync or
+ * lbem_check_guards returns LBEM_ERR_TIMEOUT; the launch's output state is then invalid (reload or re-initialise
+ * it).  Not in the paper: a failure-detection knob.  seconds in [0, 3600] (LBEM_ERR_ARG otherwise); the default
+ * is 2.  0 gives up at every wait without polling, which exercises the give-up path with ordinary, in-bounds
+ * loads.  Takes effect for launches enqueued after the call. */
+lbem_status lbem_set_wait_limit(double seconds);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *lbem_last_error(void);
 
@@ -296,7 +305,9 @@ lbem_status lbem_diagnostics(lbem_t *h, double out[3]);
  *           device; mu_r may be NULL); c_ref2 as in lbem_desc (<= 0: default)
  *   out   : 3 doubles of device memory, written asynchronously on `stream`
  * LBEM_ERR_ARG, with nothing launched, for grids above 33554432 sites, host
- * pointers, or a buffer whose device allocation ends before the bytes above.
+ * pointers, or a buffer whose device allocation ends before the bytes above
+ * (the allocation the driver knows: a buffer carved out of a larger pool
+ * allocation is checked against the end of that pool allocation).
  * The first call on a device looks up the static array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU race. */

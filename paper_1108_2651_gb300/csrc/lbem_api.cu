@@ -371,7 +371,13 @@ lbem_status lbem_sync(lbem_t *h) {
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     LBEM_CUDA(cudaGetLastError());
     if (tb2_take_timeouts())
-        return fail(LBEM_ERR_TIMEOUT, "lbem_sync: a tile load of the two-step kernel did not complete in 2 s");
+        return fail(LBEM_ERR_TIMEOUT, "lbem_sync: a tile load of the multi-step kernel did not complete within the wait limit");
+    return LBEM_OK;
+}
+
+lbem_status lbem_set_wait_limit(double seconds) {
+    if (!(seconds >= 0.0 && seconds <= 3600.0)) return fail(LBEM_ERR_ARG, "lbem_set_wait_limit: seconds must lie in [0, 3600]");
+    LBEM_CUDA(tb_set_wait_limit((unsigned long long)(seconds * 1e9)));
     return LBEM_OK;
 }
 

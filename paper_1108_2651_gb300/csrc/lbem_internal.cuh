@@ -539,6 +539,7 @@ int tb2_nshapes(int storage, bool has_mu);
 int rs2_nshapes();
 cudaError_t launch_step_2d_rs2(const StepArgs &a, int shape, cudaStream_t s);
 bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag
+cudaError_t tb_set_wait_limit(unsigned long long ns);  // limit of its bounded waits (current device)
 // three steps per launch (tblock.cu): FP32 storage, uniform mu
 int tb3_nshapes();
 cudaError_t launch_step_2d_tb3(const StepArgs &a, int shape, cudaStream_t s);

@@ -127,9 +127,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int
 }
 
 __device__ int g_tb_timeouts = 0;  // set when a bounded wait of the two-step kernel gave up
+// Limit of the bounded waits for a tile's TMA window, in ns of device time (lbem_set_wait_limit); 0 gives up at
+// once, which exercises the give-up path with ordinary, in-bounds loads.  Read once per kernel.
+__device__ unsigned long long g_wait_limit_ns = 2000000000ull;
+// After giving up, a CTA still waits this long for its copies in flight to land before it exits (shared memory
+// must not be written by a copy after its CTA is gone); independent of g_wait_limit_ns.
+constexpr unsigned long long kDrainNs = 2000000000ull;
 
-// Wait for phase `parity` of the mbarrier, giving up after about 2 s of device time.
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+// Wait for phase `parity` of the mbarrier, giving up after limit_ns of device time (at once for 0).
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity, unsigned long long limit_ns) {
+    if (limit_ns == 0) return false;
     unsigned long long t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     for (unsigned it = 0;; it++) {
@@ -143,7 +150,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
         if ((it & 63) == 63) {
             unsigned long long t1;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-            if (t1 - t0 > 2000000000ull) return false;
+            if (t1 - t0 > limit_ns) return false;
         }
     }
 }
@@ -433,6 +440,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     unsigned parity = 0;  // next phase of the mbarrier to wait for
+    const unsigned long long wait_limit = g_wait_limit_ns;
     tb_load<TBY, MU>(a, tx * TBX, ty * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
                      &tmCL, NT, &tmDL);
     asm volatile("cp.async.commit_group;\n" ::);
@@ -450,13 +458,13 @@ __global__ void __launch_bounds__(NT, MINB)
         asm volatile("cp.async.wait_group 0;\n" ::);
         bool ok = true;
         if (use_tma && tb_interior<TBY>(x0, y0, G)) {
-            ok = mbar_wait(mbar, parity);
+            ok = mbar_wait(mbar, parity, wait_limit);
             parity ^= 1u;
         }
         // every thread's copies have landed, and step t+1 of the previous tile is done with P
         if (__syncthreads_or(!ok)) {  // a TMA load never completed: flag it, let it drain (bounded), stop
             if (tid == 0) atomicExch(&g_tb_timeouts, 1);
-            mbar_wait(mbar, parity ^ 1u);
+            mbar_wait(mbar, parity ^ 1u, kDrainNs);  // drain what is in flight
             return;
         }
         float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb, Jh = clb, Ph = clb;
@@ -705,6 +713,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     unsigned parity = 0;
+    const unsigned long long wait_limit = g_wait_limit_ns;
     tb3_load<TBY>(a, tx * TBX, ty * TBY, S0, CL, mbar, use_tma && tb3_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
                   &tmCL, NT);
     asm volatile("cp.async.commit_group;\n" ::);
@@ -722,13 +731,13 @@ __global__ void __launch_bounds__(NT, MINB)
         asm volatile("cp.async.wait_group 0;\n" ::);
         bool ok = true;
         if (use_tma && tb3_interior<TBY>(x0, y0, G)) {
-            ok = mbar_wait(mbar, parity);
+            ok = mbar_wait(mbar, parity, wait_limit);
             parity ^= 1u;
         }
         // every thread's copies have landed, and step C of the previous tile is done with S2
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(&g_tb_timeouts, 1);
-            mbar_wait(mbar, parity ^ 1u);
+            mbar_wait(mbar, parity ^ 1u, kDrainNs);  // drain what is in flight
             return;
         }
         float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), clc = clb;
@@ -1089,6 +1098,7 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     __syncthreads();
     unsigned parity = 0;
+    const unsigned long long wait_limit = g_wait_limit_ns;
     tb_load16<ST, TBY>(a, tx * TBX, ty * TBY, smb, mbar, use_tma && tb_interior16<TBY>(tx * TBX, ty * TBY, G), &tmIn,
                        &tmCL, &tmEx, NT);
     asm volatile("cp.async.commit_group;\n" ::);
@@ -1106,12 +1116,12 @@ __global__ void __launch_bounds__(NT, MINB)
         asm volatile("cp.async.wait_group 0;\n" ::);
         bool ok = true;
         if (use_tma && tb_interior16<TBY>(x0, y0, G)) {
-            ok = mbar_wait(mbar, parity);
+            ok = mbar_wait(mbar, parity, wait_limit);
             parity ^= 1u;
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(&g_tb_timeouts, 1);
-            mbar_wait(mbar, parity ^ 1u);
+            mbar_wait(mbar, parity ^ 1u, kDrainNs);  // drain what is in flight
             return;
         }
         float4 clb = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1273,6 +1283,10 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case 6: return launch_tb<14, 512, 2>(a, s);
         default: return launch_tb<6, 256, 5>(a, s);  // 42 KB of shared memory
     }
+}
+
+cudaError_t tb_set_wait_limit(unsigned long long ns) {
+    return cudaMemcpyToSymbol(g_wait_limit_ns, &ns, sizeof ns);
 }
 
 bool tb2_take_timeouts() {

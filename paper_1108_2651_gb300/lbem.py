@@ -41,6 +41,7 @@ _SIGS = {
     "lbem_set_stream": [_VP, _VP],
     "lbem_sync": [_VP],
     "lbem_last_error": [],
+    "lbem_set_wait_limit": [_D],
     "lbem_info": [_VP, C.POINTER(_LL), C.POINTER(C.c_size_t)],
     "lbem_set_medium": [_VP, _VP, _VP],
     "lbem_set_fields": [_VP, _VP, _VP],
@@ -157,6 +158,10 @@ def lbem_destroy(h):
 
 def lbem_last_error():
     return load().lbem_last_error().decode()
+
+
+def lbem_set_wait_limit(seconds):
+    _check(load().lbem_set_wait_limit(float(seconds)))
 
 
 def lbem_set_stream(h, stream):

@@ -106,3 +106,12 @@ def test_null_handles_are_rejected(lib):
                      ("lbem_batch_get_variant", [None, None])):
         assert getattr(lib, f)(None, *extra) == 1, f
         assert "null" in lbem.lbem_last_error() or "bad argument" in lbem.lbem_last_error(), f
+
+
+def test_wait_limit_rejects_bad_values_before_touching_the_device(lib):
+    from paper_1108_2651_gb300 import lbem
+
+    for v in (-1.0, float("nan"), float("inf"), 1e9):
+        with pytest.raises(lbem.LbemError) as e:
+            lbem.lbem_set_wait_limit(v)
+        assert e.value.status == 1 and "seconds" in str(e.value)
