@@ -11,18 +11,25 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbem_oracle.c")
 LIB = os.path.join(HERE, "liblbem_oracle.so")
+LIB32 = os.path.join(HERE, "liblbem_oracle_f32.so")
 
 
-def build(force: bool = False) -> str:
-    """Build liblbem_oracle.so next to its source if it is missing or stale."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", SRC, "-o", tmp, "-lm"]
+def build(force: bool = False, fp32: bool = False) -> str:
+    """Build liblbem_oracle.so (FP64, the oracle) next to its source if it is missing or stale.  fp32=True builds
+    liblbem_oracle_f32.so instead: the same source with every quantity in float (and single-precision constants),
+    used only to time a like-for-like CPU figure."""
+    lib = LIB32 if fp32 else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    extra = ["-DOR_REAL=float", "-fsingle-precision-constant"] if fp32 else []
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp"] + extra + [SRC, "-o", tmp,
+                                                                                                   "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, fp32=True))

@@ -98,6 +98,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Floating-point type of every quantity.  The oracle is FP64 (the default); building with -DOR_REAL=float
+ * gives an FP32 build of the same source, used only to time a like-for-like CPU figure, never as a reference. */
+#ifndef OR_REAL
+#define OR_REAL double
+#endif
+typedef OR_REAL real;
+
 #define MAXQ 7
 #define MAXD 3
 
@@ -105,8 +112,8 @@ typedef struct {
     int D, Q, nx, ny, nz;
     long nsite;
     int c[MAXQ][3]; /* lattice velocities, unused axes 0 */
-    double fa[3];   /* per-axis lattice speeds c_a^2 = fa[a] c_L^2 (reading R10; 1 when isotropic) */
-    double bs[3];   /* B_b = bs[b] x its first moment (reading R10; 1 when isotropic) */
+    real fa[3];   /* per-axis lattice speeds c_a^2 = fa[a] c_L^2 (reading R10; 1 when isotropic) */
+    real bs[3];   /* B_b = bs[b] x its first moment (reading R10; 1 when isotropic) */
 } lattice_t;
 
 /* Lattice of Sec. "Lattice BGK formulation": 2D rest particles plus +/- unit
@@ -128,12 +135,12 @@ static void make_lattice(lattice_t *L, int D, int nx, int ny, int nz) {
 
 /* Levi-Civita symbol epsilon_{abc}, indices 0..2: +1 on even permutations of
  * (0,1,2), -1 on odd ones, 0 when an index repeats. */
-static const double LEVI[3][3][3] = {
+static const real LEVI[3][3][3] = {
     {{0, 0, 0}, {0, 0, 1}, {0, -1, 0}},
     {{0, 0, -1}, {0, 0, 0}, {1, 0, 0}},
     {{0, 1, 0}, {-1, 0, 0}, {0, 0, 0}},
 };
-static inline double levi(int a, int b, int c) { return LEVI[a][b][c]; }
+static inline real levi(int a, int b, int c) { return LEVI[a][b][c]; }
 
 /* Periodic wrap of coordinate v + d into [0, n), for |d| <= n. */
 static inline long wrap(long v, int d, long n) {
@@ -162,19 +169,19 @@ static inline long mirror_or_wrap(long v, int d, long n, int bc) {
 }
 
 /* Damping factor 1 - gamma of reading R8 at coordinate v of an axis of length n (1 outside the layer). */
-static double layer_factor(long v, long n, int layer, double gamma_max) {
+static real layer_factor(long v, long n, int layer, real gamma_max) {
     long i = v < n - 1 - v ? v : n - 1 - v; /* distance from the nearer wall-adjacent site */
     if (layer <= 0 || i >= layer) return 1.0;
-    double r = (double)(layer - i) / layer;
+    real r = (real)(layer - i) / layer;
     return 1.0 - gamma_max * r * r;
 }
 
-static inline double *G(const lattice_t *L, double *g, long s, int i) {
+static inline real *G(const lattice_t *L, real *g, long s, int i) {
     return g + ((s * L->Q + i) * L->D) * L->D;
 }
 
 /* Anisotropy ratio r = sqrt(mu_xx / mu_yy) of reading R10 (2D; r = 1: isotropic). */
-static void set_axes(lattice_t *L, double r) {
+static void set_axes(lattice_t *L, real r) {
     if (L->D != 2 || !(r > 0.0) || r == 1.0) return;
     L->fa[0] = r;
     L->fa[1] = 1.0 / r;
@@ -193,9 +200,9 @@ static int axis_of(const lattice_t *L, int i) {
  * w_i = (1 - w0)/(2D); the rest particle gets w0.  With per-axis speeds
  * (reading R10) a moving particle of axis a gets (1 - w0) fa[a] / (2 sum_b fa[b])
  * = c_a^2 / 2. */
-static double weight(const lattice_t *L, int i, double w0) {
+static real weight(const lattice_t *L, int i, real w0) {
     if (i == 0) return w0;
-    double sum = 0.0;
+    real sum = 0.0;
     for (int b = 0; b < L->D; b++) sum += L->fa[b];
     return (1.0 - w0) * L->fa[axis_of(L, i)] / (2.0 * sum);
 }
@@ -213,17 +220,17 @@ static double weight(const lattice_t *L, int i, double w0) {
  * mu_r may be NULL (mu = 1).  Returns the number of sites whose w0 falls
  * outside [0, 1) or whose inputs are not finite and positive.
  */
-long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r, const double *mu_r, const int *bc,
-               double aniso_r, double *ceff2, double *cL2, double *w0, double *mu, double *dlnmu) {
+long or_medium(int D, int nx, int ny, int nz, real c_ref2, const real *eps_r, const real *mu_r, const int *bc,
+               real aniso_r, real *ceff2, real *cL2, real *w0, real *mu, real *dlnmu) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     set_axes(&L, aniso_r);
-    double fsum = 0.0;
+    real fsum = 0.0;
     for (int a = 0; a < D; a++) fsum += L.fa[a];
     long bad = 0;
     for (long s = 0; s < L.nsite; s++) {
-        double e = eps_r[s];
-        double m = mu_r ? mu_r[s] : 1.0;
+        real e = eps_r[s];
+        real m = mu_r ? mu_r[s] : 1.0;
         if (!(e > 0.0) || !(m > 0.0) || !isfinite(e) || !isfinite(m)) {
             bad++;
             e = 1.0;
@@ -263,29 +270,29 @@ long or_medium(int D, int nx, int ny, int nz, double c_ref2, const double *eps_r
  *   B_b       = sum_{a != b} R_{a b a}                    (reading R2)
  * E and B are 3-vectors; in 2D only E_z, B_x, B_y can be non-zero.
  */
-static void site_moments(const lattice_t *L, const double *gs, double cL2, double Lam[MAXD][MAXD], double E[3],
-                         double B[3]) {
+static void site_moments(const lattice_t *L, const real *gs, real cL2, real Lam[MAXD][MAXD], real E[3],
+                         real B[3]) {
     const int D = L->D, Q = L->Q;
-    double R[MAXD][MAXD][MAXD];
+    real R[MAXD][MAXD][MAXD];
     for (int a = 0; a < D; a++)
         for (int b = 0; b < D; b++) {
-            double sum = 0.0;
+            real sum = 0.0;
             for (int i = 0; i < Q; i++) sum += gs[(i * D + a) * D + b];
             Lam[a][b] = cL2 * sum;
             for (int k = 0; k < D; k++) {
-                double r = 0.0;
+                real r = 0.0;
                 for (int i = 0; i < Q; i++) r += L->c[i][k] * gs[(i * D + a) * D + b];
                 R[a][b][k] = r;
             }
         }
     for (int g = 0; g < 3; g++) {
-        double e = 0.0;
+        real e = 0.0;
         for (int a = 0; a < D; a++)
             for (int b = 0; b < D; b++) e += levi(g, a, b) * Lam[a][b];
         E[g] = -0.5 * e;
     }
     for (int b = 0; b < 3; b++) {
-        double v = 0.0;
+        real v = 0.0;
         if (b < D)
             for (int a = 0; a < D; a++)
                 if (a != b) v += R[a][b][a];
@@ -298,13 +305,13 @@ static void site_moments(const lattice_t *L, const double *gs, double cL2, doubl
  * with Bq = B/(D-1) (reading R2).  With per-axis speeds (reading R10) the c^2
  * of the B term is that of the particle's axis, c_a^2 = fa[a] c_L^2, and Bq is
  * the first moment B/bs. */
-static void equilibrium(const lattice_t *L, double cL2, double w0, double Lam[MAXD][MAXD], const double B[3],
-                        double *geq) {
+static void equilibrium(const lattice_t *L, real cL2, real w0, real Lam[MAXD][MAXD], const real B[3],
+                        real *geq) {
     const int D = L->D, Q = L->Q;
-    double Bq[3];
+    real Bq[3];
     for (int k = 0; k < 3; k++) Bq[k] = B[k] / (D - 1) / L->bs[k];
     for (int i = 0; i < Q; i++) {
-        const double w = weight(L, i, w0), ax = i == 0 ? 1.0 : L->fa[axis_of(L, i)];
+        const real w = weight(L, i, w0), ax = i == 0 ? 1.0 : L->fa[axis_of(L, i)];
         for (int a = 0; a < D; a++)
             for (int b = 0; b < D; b++)
                 geq[(i * D + a) * D + b] =
@@ -315,16 +322,16 @@ static void equilibrium(const lattice_t *L, double cL2, double w0, double Lam[MA
 /* Initial state g = g^(0)(E, B): Lambda_ab = -eps_{g a b} E_g (Sec. "The
  * Maxwell Equations", conservative form) and B as given.  E, B are
  * [nsite][3]; either may be NULL (zero). */
-void or_init(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *E, const double *B,
-             double *g, double aniso_r) {
+void or_init(int D, int nx, int ny, int nz, const real *cL2, const real *w0, const real *E, const real *B,
+             real *g, real aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     set_axes(&L, aniso_r);
     for (long s = 0; s < L.nsite; s++) {
-        double Lam[MAXD][MAXD], Bs[3] = {0, 0, 0};
+        real Lam[MAXD][MAXD], Bs[3] = {0, 0, 0};
         for (int a = 0; a < D; a++)
             for (int b = 0; b < D; b++) {
-                double v = 0.0;
+                real v = 0.0;
                 if (E)
                     for (int k = 0; k < 3; k++) v -= levi(k, a, b) * E[3 * s + k];
                 Lam[a][b] = v;
@@ -336,14 +343,14 @@ void or_init(int D, int nx, int ny, int nz, const double *cL2, const double *w0,
 }
 
 /* E and B ([nsite][3]) of a pre-collision state. */
-void or_fields(int D, int nx, int ny, int nz, const double *cL2, const double *g, double *E, double *B,
-               double aniso_r) {
+void or_fields(int D, int nx, int ny, int nz, const real *cL2, const real *g, real *E, real *B,
+               real aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     set_axes(&L, aniso_r);
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < L.nsite; s++) {
-        double Lam[MAXD][MAXD];
+        real Lam[MAXD][MAXD];
         site_moments(&L, g + s * L.Q * D * D, cL2[s], Lam, E + 3 * s, B + 3 * s);
     }
 }
@@ -361,17 +368,17 @@ void or_fields(int D, int nx, int ny, int nz, const double *cL2, const double *g
  *   S_g    = c_eff^2 eps_{g b k} B_b d_k ln(mu) - mu c_eff^2 j_g     (Eq. 3, R3)
  * j is the current density at this site and time (3-vector).
  */
-static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2, double mus, const double dlnmu[3],
-                         const double j[3], const double *ppol, const double *gin, double *gout, double E[3],
-                         double B[3]) {
+static void collide_site(const lattice_t *L, real cL2, real w0, real ceff2, real mus, const real dlnmu[3],
+                         const real j[3], const real *ppol, const real *gin, real *gout, real E[3],
+                         real B[3]) {
     const int D = L->D, Q = L->Q;
-    const double dt = 1.0, tau = 0.5;
-    double Lam[MAXD][MAXD], S[3], geq[MAXQ * MAXD * MAXD];
+    const real dt = 1.0, tau = 0.5;
+    real Lam[MAXD][MAXD], S[3], geq[MAXQ * MAXD * MAXD];
     site_moments(L, gin, cL2, Lam, E, B);
     if (ppol) /* reading R9: the field is D/eps_inf - P */
         for (int g = 0; g < 3; g++) E[g] -= ppol[g];
     for (int g = 0; g < 3; g++) {
-        double curl = 0.0;
+        real curl = 0.0;
         for (int b = 0; b < 3; b++)
             for (int k = 0; k < 3; k++) curl += levi(g, b, k) * B[b] * dlnmu[k];
         S[g] = ceff2 * curl - mus * ceff2 * j[g];
@@ -381,19 +388,19 @@ static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2
         /* reading R9: second moment Lambda_ab + eps_gab P_g, zeroth and first moments unchanged */
         for (int a = 0; a < D; a++)
             for (int b = 0; b < D; b++) {
-                double dl = 0.0;
+                real dl = 0.0;
                 for (int g = 0; g < 3; g++) dl += levi(g, a, b) * ppol[g];
-                double fsum = 0.0; /* sum_a c_a^2 / c_L^2: D when isotropic */
+                real fsum = 0.0; /* sum_a c_a^2 / c_L^2: D when isotropic */
                 for (int k = 0; k < D; k++) fsum += L->fa[k];
                 for (int i = 0; i < Q; i++)
                     geq[(i * D + a) * D + b] += (i == 0 ? -fsum : 0.5 * L->fa[axis_of(L, i)]) * dl;
             }
     }
     for (int i = 0; i < Q; i++) {
-        double wc = weight(L, i, w0) / cL2;
+        real wc = weight(L, i, w0) / cL2;
         for (int a = 0; a < D; a++)
             for (int b = 0; b < D; b++) {
-                double T = 0.0;
+                real T = 0.0;
                 for (int g = 0; g < 3; g++) T -= wc * levi(g, a, b) * S[g];
                 int n = (i * D + a) * D + b;
                 gout[n] = (1.0 - dt / tau) * gin[n] + (dt / tau) * geq[n] + T * dt;
@@ -402,18 +409,18 @@ static void collide_site(const lattice_t *L, double cL2, double w0, double ceff2
 }
 
 /* Field sample of a receiver: comp 0..2 = E_x..E_z, 3..5 = B_x..B_z. */
-static double pick(const double E[3], const double B[3], int comp) { return comp < 3 ? E[comp] : B[comp - 3]; }
+static real pick(const real E[3], const real B[3], int comp) { return comp < 3 ? E[comp] : B[comp - 3]; }
 
 typedef struct {
     int nsrc;
     const long *site;
     const int *comp;    /* 0..2: component of j */
-    const double *amp;  /* [nsrc][nt]: j(t) */
+    const real *amp;  /* [nsrc][nt]: j(t) */
     int nt;
 } sources_t;
 
 /* j at a site and time, summed over the point sources there. */
-static void current_at(const sources_t *src, long s, int t, double j[3]) {
+static void current_at(const sources_t *src, long s, int t, real j[3]) {
     j[0] = j[1] = j[2] = 0.0;
     if (!src) return;
     for (int k = 0; k < src->nsrc; k++)
@@ -429,11 +436,11 @@ static void current_at(const sources_t *src, long s, int t, double j[3]) {
  * (readings R6-R7); `layer` > 0 adds the absorbing layer of reading R8 inside
  * every wall.  Returns 0.
  */
-int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2, const double *mu,
-           const double *dlnmu, double *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
-           const double *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, double *traces,
-           const int *bc, int layer, double gamma_max, const double *wp2, const double *wr2, const double *gam,
-           double *Jpol, double *Ppol, double aniso_r) {
+int or_run(int D, int nx, int ny, int nz, const real *cL2, const real *w0, const real *ceff2, const real *mu,
+           const real *dlnmu, real *g, int t0, int nsteps, int nsrc, const long *src_site, const int *src_comp,
+           const real *src_amp, int nt, int nrec, const long *rec_site, const int *rec_comp, real *traces,
+           const int *bc, int layer, real gamma_max, const real *wp2, const real *wr2, const real *gam,
+           real *Jpol, real *Ppol, real aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     set_axes(&L, aniso_r);
@@ -441,28 +448,28 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
     for (int a = 0; bc && a < 3; a++) kind[a] = a < D ? bc[a] : 0;
     const long len[3] = {L.nx, L.ny, L.nz};
     const long per = (long)L.Q * D * D;
-    double *gpost = malloc(sizeof(double) * per * L.nsite);
-    double *E = malloc(sizeof(double) * 3 * L.nsite);
-    double *B = malloc(sizeof(double) * 3 * L.nsite);
+    real *gpost = malloc(sizeof(real) * per * L.nsite);
+    real *E = malloc(sizeof(real) * 3 * L.nsite);
+    real *B = malloc(sizeof(real) * 3 * L.nsite);
     sources_t src = {nsrc, src_site, src_comp, src_amp, nt};
     for (int n = 0; n < nsteps; n++) {
         int t = t0 + n;
         /* collision at every site (Eq. 17) */
 #pragma omp parallel for schedule(static)
         for (long s = 0; s < L.nsite; s++) {
-            double j[3];
+            real j[3];
             current_at(&src, s, t, j);
-            double pt[3];
-            const double *ppol = NULL;
+            real pt[3];
+            const real *ppol = NULL;
             if (wp2) {
                 /* the pole's update from the pre-collision E(t) = D/eps_inf - P(t) (reading R9) */
-                double Lam[MAXD][MAXD], Et[3], Bt[3];
+                real Lam[MAXD][MAXD], Et[3], Bt[3];
                 site_moments(&L, g + s * per, cL2[s], Lam, Et, Bt);
-                const double gm = gam ? gam[s] : 0.0, om = wr2 ? wr2[s] : 0.0;
+                const real gm = gam ? gam[s] : 0.0, om = wr2 ? wr2[s] : 0.0;
                 for (int a = 0; a < 3; a++) {
                     pt[a] = Ppol[3 * s + a];
-                    const double ea = Et[a] - pt[a];
-                    const double jn = ((1.0 - 0.5 * gm) * Jpol[3 * s + a] + wp2[s] * ea - om * pt[a]) / (1.0 + 0.5 * gm);
+                    const real ea = Et[a] - pt[a];
+                    const real jn = ((1.0 - 0.5 * gm) * Jpol[3 * s + a] + wp2[s] * ea - om * pt[a]) / (1.0 + 0.5 * gm);
                     Jpol[3 * s + a] = jn;
                     Ppol[3 * s + a] = pt[a] + jn;
                 }
@@ -472,7 +479,7 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
                          E + 3 * s, B + 3 * s);
             /* absorbing layer (reading R8): scale the post-collision populations */
             const long xyz[3] = {s % L.nx, (s / L.nx) % L.ny, s / ((long)L.nx * L.ny)};
-            double f = 1.0;
+            real f = 1.0;
             for (int a = 0; a < D; a++)
                 if (kind[a]) f *= layer_factor(xyz[a], len[a], layer, gamma_max);
             if (f != 1.0)
@@ -492,9 +499,9 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
                     if (kind[a] && (xyz[a] < 0 || xyz[a] >= len[a])) crossed = a;
                 if (crossed >= 0) {
                     const int io = i == 0 ? 0 : (i <= D ? i + D : i - D); /* opposite direction */
-                    const double wall = kind[crossed] == 1 ? 1.0 : -1.0;   /* PEC: the geometric mirror */
-                    const double *src = G(&L, gpost, s, i);
-                    double *dst = G(&L, g, s, io);
+                    const real wall = kind[crossed] == 1 ? 1.0 : -1.0;   /* PEC: the geometric mirror */
+                    const real *src = G(&L, gpost, s, i);
+                    real *dst = G(&L, g, s, io);
                     for (int b = 0; b < D; b++)
                         for (int c = 0; c < D; c++)
                             dst[b * D + c] = wall * (b == crossed ? -1.0 : 1.0) * (c == crossed ? -1.0 : 1.0) *
@@ -502,7 +509,7 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
                     continue;
                 }
                 long d = wrap(x, L.c[i][0], L.nx) + L.nx * (wrap(y, L.c[i][1], L.ny) + L.ny * wrap(z, L.c[i][2], L.nz));
-                memcpy(G(&L, g, d, i), G(&L, gpost, s, i), sizeof(double) * D * D);
+                memcpy(G(&L, g, d, i), G(&L, gpost, s, i), sizeof(real) * D * D);
             }
         }
     }
@@ -522,23 +529,23 @@ int or_run(int D, int nx, int ny, int nz, const double *cL2, const double *w0, c
  * out[2] = sqrt( sum_x (div B)^2 ), div B by periodic central differences
  * Sums run over sites in order, serially.
  */
-void or_diagnostics(int D, int nx, int ny, int nz, const double *cL2, const double *w0, const double *ceff2,
-                    const double *g, double *out, double aniso_r) {
+void or_diagnostics(int D, int nx, int ny, int nz, const real *cL2, const real *w0, const real *ceff2,
+                    const real *g, real *out, real aniso_r) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     set_axes(&L, aniso_r);
-    double *E = malloc(sizeof(double) * 3 * L.nsite), *B = malloc(sizeof(double) * 3 * L.nsite);
+    real *E = malloc(sizeof(real) * 3 * L.nsite), *B = malloc(sizeof(real) * 3 * L.nsite);
     or_fields(D, nx, ny, nz, cL2, g, E, B, aniso_r);
-    double en = 0.0, inv = 0.0, dv = 0.0;
+    real en = 0.0, inv = 0.0, dv = 0.0;
     for (long s = 0; s < L.nsite; s++) {
         for (int a = 0; a < 3; a++) en += B[3 * s + a] * B[3 * s + a] + E[3 * s + a] * E[3 * s + a] / ceff2[s];
         for (int i = 0; i < L.Q; i++) {
-            double w = weight(&L, i, w0[s]);
+            real w = weight(&L, i, w0[s]);
             if (w == 0.0) continue;
-            const double *gi = g + (s * L.Q + i) * D * D;
+            const real *gi = g + (s * L.Q + i) * D * D;
             for (int n = 0; n < D * D; n++) inv += gi[n] * gi[n] / w;
         }
-        double div = 0.0;
+        real div = 0.0;
         for (int k = 0; k < D; k++) {
             int dp[3] = {0, 0, 0};
             dp[k] = 1;
@@ -569,9 +576,9 @@ void or_diagnostics(int D, int nx, int ny, int nz, const double *cL2, const doub
  *   S       : proportional to c_eff^2, multiplied by w_i/c_L^2 in T.
  * The adjoint below uses that: d g'/d c_L^2 = (g'(2c) - g'(c)) / c exactly.
  */
-static void collide_c(const lattice_t *L, double c, double mus, const double dlnmu[3], const double j[3],
-                      const double *gin, double *gout) {
-    double E[3], B[3];
+static void collide_c(const lattice_t *L, real c, real mus, const real dlnmu[3], const real j[3],
+                      const real *gin, real *gout) {
+    real E[3], B[3];
     collide_site(L, c, 1.0 - L->D * c, c / (L->D - 1), mus, dlnmu, j, NULL, gin, gout, E, B);
 }
 
@@ -588,72 +595,72 @@ static void collide_c(const lattice_t *L, double c, double mus, const double dln
  * collide_c (built column by column from unit vectors).
  * Returns the misfit; grad_eps is [nsite].
  */
-double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const double *cL2, const double *mu,
-                  const double *dlnmu, const double *g0, int t0, int nsteps, int nsrc, const long *src_site,
-                  const int *src_comp, const double *src_amp, int nt, int nrec, const long *rec_site,
-                  const int *rec_comp, const double *obs, double *grad_eps) {
+real or_adjoint(int D, int nx, int ny, int nz, const real *eps_r, const real *cL2, const real *mu,
+                  const real *dlnmu, const real *g0, int t0, int nsteps, int nsrc, const long *src_site,
+                  const int *src_comp, const real *src_amp, int nt, int nrec, const long *rec_site,
+                  const int *rec_comp, const real *obs, real *grad_eps) {
     lattice_t L;
     make_lattice(&L, D, nx, ny, nz);
     const long per = (long)L.Q * D * D;
     const long ns = L.nsite;
-    double *w0 = malloc(sizeof(double) * ns), *ceff2 = malloc(sizeof(double) * ns);
+    real *w0 = malloc(sizeof(real) * ns), *ceff2 = malloc(sizeof(real) * ns);
     for (long s = 0; s < ns; s++) {
         w0[s] = 1.0 - D * cL2[s];
         ceff2[s] = cL2[s] / (D - 1);
     }
     /* forward pass, keeping every pre-collision state */
-    double *states = malloc(sizeof(double) * per * ns * (nsteps + 1));
-    double *traces = malloc(sizeof(double) * (nrec > 0 ? nrec : 1) * (nsteps > 0 ? nsteps : 1));
-    memcpy(states, g0, sizeof(double) * per * ns);
+    real *states = malloc(sizeof(real) * per * ns * (nsteps + 1));
+    real *traces = malloc(sizeof(real) * (nrec > 0 ? nrec : 1) * (nsteps > 0 ? nsteps : 1));
+    memcpy(states, g0, sizeof(real) * per * ns);
     for (int n = 0; n < nsteps; n++) {
-        memcpy(states + (long)(n + 1) * per * ns, states + (long)n * per * ns, sizeof(double) * per * ns);
-        double *tr_n = malloc(sizeof(double) * (nrec > 0 ? nrec : 1));
+        memcpy(states + (long)(n + 1) * per * ns, states + (long)n * per * ns, sizeof(real) * per * ns);
+        real *tr_n = malloc(sizeof(real) * (nrec > 0 ? nrec : 1));
         or_run(D, nx, ny, nz, cL2, w0, ceff2, mu, dlnmu, states + (long)(n + 1) * per * ns, t0 + n, 1, nsrc, src_site,
                src_comp, src_amp, nt, nrec, rec_site, rec_comp, tr_n, NULL, 0, 0.0, NULL, NULL, NULL, NULL, NULL, 1.0);
         for (int r = 0; r < nrec; r++) traces[(long)r * nsteps + n] = tr_n[r];
         free(tr_n);
     }
-    double misfit = 0.0;
+    real misfit = 0.0;
     for (int r = 0; r < nrec; r++)
         for (int n = 0; n < nsteps; n++) {
-            double d = traces[(long)r * nsteps + n] - obs[(long)r * nsteps + n];
+            real d = traces[(long)r * nsteps + n] - obs[(long)r * nsteps + n];
             misfit += 0.5 * d * d;
         }
     /* backward pass */
-    double *lam = calloc(per * ns, sizeof(double));   /* lam^{n+1} */
-    double *lpost = malloc(sizeof(double) * per * ns); /* S^T lam^{n+1} */
-    double *gcl = calloc(ns, sizeof(double));          /* dL/dc_L^2 */
+    real *lam = calloc(per * ns, sizeof(real));   /* lam^{n+1} */
+    real *lpost = malloc(sizeof(real) * per * ns); /* S^T lam^{n+1} */
+    real *gcl = calloc(ns, sizeof(real));          /* dL/dc_L^2 */
     for (int n = nsteps - 1; n >= 0; n--) {
-        const double *gn = states + (long)n * per * ns;
+        const real *gn = states + (long)n * per * ns;
         /* S^T: streaming moved g'_i(x) to x + c_i, so its transpose pulls back */
         for (long s = 0; s < ns; s++)
             for (int i = 0; i < L.Q; i++) {
                 long d = shifted(&L, s, L.c[i][0], L.c[i][1], L.c[i][2]);
-                memcpy(G(&L, lpost, s, i), G(&L, lam, d, i), sizeof(double) * D * D);
+                memcpy(G(&L, lpost, s, i), G(&L, lam, d, i), sizeof(real) * D * D);
             }
 #pragma omp parallel for schedule(static)
         for (long s = 0; s < ns; s++) {
-            double j[3], zero[3] = {0, 0, 0};
+            real j[3], zero[3] = {0, 0, 0};
             sources_t src = {nsrc, src_site, src_comp, src_amp, nt};
             current_at(&src, s, t0 + n, j);
-            const double *gs = gn + s * per;
-            const double *ls = lpost + s * per;
-            double *out = lam + s * per;
+            const real *gs = gn + s * per;
+            const real *ls = lpost + s * per;
+            real *out = lam + s * per;
             /* lam^n(x) = M^T lpost(x): column m of M is collide_c(unit e_m) with j = 0 */
-            double unit[MAXQ * MAXD * MAXD], col[MAXQ * MAXD * MAXD];
+            real unit[MAXQ * MAXD * MAXD], col[MAXQ * MAXD * MAXD];
             for (long m = 0; m < per; m++) {
                 memset(unit, 0, sizeof(unit));
                 unit[m] = 1.0;
                 collide_c(&L, cL2[s], mu[s], dlnmu + 3 * s, zero, unit, col);
-                double v = 0.0;
+                real v = 0.0;
                 for (long q = 0; q < per; q++) v += col[q] * ls[q];
                 out[m] = v;
             }
             /* dL/dc_L^2 through the collision and source (affine in c_L^2) */
-            double ga[MAXQ * MAXD * MAXD], gb[MAXQ * MAXD * MAXD];
+            real ga[MAXQ * MAXD * MAXD], gb[MAXQ * MAXD * MAXD];
             collide_c(&L, 2.0 * cL2[s], mu[s], dlnmu + 3 * s, j, gs, ga);
             collide_c(&L, cL2[s], mu[s], dlnmu + 3 * s, j, gs, gb);
-            double v = 0.0;
+            real v = 0.0;
             for (long q = 0; q < per; q++) v += ls[q] * (ga[q] - gb[q]) / cL2[s];
             gcl[s] += v;
         }
@@ -661,15 +668,15 @@ double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const doub
         for (int r = 0; r < nrec; r++) {
             long s = rec_site[r];
             int comp = rec_comp[r];
-            double d = traces[(long)r * nsteps + n] - obs[(long)r * nsteps + n];
-            const double *gs = gn + s * per;
-            double *out = lam + s * per;
+            real d = traces[(long)r * nsteps + n] - obs[(long)r * nsteps + n];
+            const real *gs = gn + s * per;
+            real *out = lam + s * per;
             for (int i = 0; i < L.Q; i++)
                 for (int a = 0; a < D; a++)
                     for (int b = 0; b < D; b++) {
                         int m = (i * D + a) * D + b;
                         if (comp < 3) {
-                            double e = -0.5 * levi(comp, a, b);
+                            real e = -0.5 * levi(comp, a, b);
                             out[m] += d * e * cL2[s];
                             gcl[s] += d * e * gs[m];
                         } else {
@@ -691,6 +698,19 @@ double or_adjoint(int D, int nx, int ny, int nz, const double *eps_r, const doub
 }
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+/* Set the number of OpenMP threads (timing on one core); returns the number in effect. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    extern int omp_get_max_threads(void);
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int or_threads(void) {
 #ifdef _OPENMP
     extern int omp_get_max_threads(void);

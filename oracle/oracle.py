@@ -39,6 +39,8 @@ def _load():
         lib.or_adjoint.argtypes = [I, I, I, I, dp, dp, dp, dp, dp, I, I, I, lp, ip, dp, I, I, lp, ip, dp, dp]
         lib.or_threads.restype = I
         lib.or_threads.argtypes = []
+        lib.or_set_threads.restype = I
+        lib.or_set_threads.argtypes = [I]
         _lib = lib
     return _lib
 
@@ -46,6 +48,58 @@ def _load():
 def threads() -> int:
     """OpenMP threads the oracle uses."""
     return _load().or_threads()
+
+
+def set_threads(n: int) -> int:
+    """Set the oracle's OpenMP thread count (timing on fewer cores); returns the count in effect."""
+    return _load().or_set_threads(int(n))
+
+
+_lib32 = None
+
+
+def time_fp32(eps_r, nsteps, src_site, src_amp, threads_=0):
+    """Seconds for nsteps steps of the FP32 build of the same oracle source (2D isotropic periodic medium eps_r,
+    point current j_z at flat index src_site with amplitudes src_amp[t]), from a zero state: a like-for-like CPU
+    timing figure only; its results are never used as a reference."""
+    import time
+
+    global _lib32
+    if _lib32 is None:
+        lib = C.CDLL(build(fp32=True))
+        fp = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+        lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        I, F, vp = C.c_int, C.c_float, C.c_void_p
+        lib.or_medium.restype = C.c_long
+        lib.or_medium.argtypes = [I, I, I, I, F, fp, vp, ip, F, fp, fp, fp, fp, fp]
+        lib.or_run.restype = I
+        lib.or_run.argtypes = [I, I, I, I, fp, fp, fp, fp, fp, fp, I, I, I, lp, ip, fp, I, I, lp, ip, fp, ip, I, F,
+                               vp, vp, vp, vp, vp, F]
+        lib.or_set_threads.restype = I
+        lib.or_set_threads.argtypes = [I]
+        _lib32 = lib
+    lib = _lib32
+    eps = np.ascontiguousarray(eps_r, np.float32)
+    ny, nx = eps.shape
+    n = eps.size
+    out = [np.empty(n, np.float32) for _ in range(4)]
+    dl = np.empty(3 * n, np.float32)
+    bc = np.zeros(3, np.int32)
+    lib.or_medium(2, nx, ny, 1, 0.5, eps.ravel(), None, bc, 1.0, *out, dl)
+    ceff2, cL2, w0, mu = out
+    g = np.zeros(n * 5 * 4, np.float32)
+    amp = np.ascontiguousarray(src_amp, np.float32).ravel()
+    site = np.array([src_site], np.int64)
+    tr = np.zeros(1, np.float32)
+    nthr = lib.or_set_threads(int(threads_)) if threads_ else lib.or_set_threads(0)
+    t0 = time.perf_counter()
+    rc = lib.or_run(2, nx, ny, 1, cL2, w0, ceff2, mu, dl, g, 0, int(nsteps), 1, site, np.array([2], np.int32), amp,
+                    amp.size, 0, np.zeros(1, np.int64), np.zeros(1, np.int32), tr, bc, 0, 0.0, None, None, None, None,
+                    None, 1.0)
+    dt = time.perf_counter() - t0
+    assert rc == 0 and np.all(np.isfinite(g))
+    return dt, nthr
 
 
 @dataclass
