@@ -47,6 +47,11 @@ NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 433.792000e6 + 291.028224e6,
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
+def BATCH_SPL(variant):
+    """Steps per launch of a batch launch shape (lbem_batch_set_variant: 9, 10, 11 advance two steps)."""
+    return 2 if variant >= 9 else 1
+
+
 def measured_peak_gbs():
     try:
         with open(PEAKS) as f:
@@ -154,7 +159,9 @@ def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
     lbem.lbem_batch_destroy(b)
     for s in ss:
         s.close()
-    per = ms / nsteps
+    spl = BATCH_SPL(v)
+    launches = nsteps // spl + nsteps % spl
+    per = ms / launches
     gbs = 44 * sites / (per * 1e-3) / 1e9
     value = sites * nsteps / (ms * 1e-3) / 1e6
     print(json.dumps({"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": 1, "steps": args.steps,
@@ -162,9 +169,10 @@ def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
                       "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "batch256", "media": len(probs), "sites": sites, "lb_steps": nsteps},
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                                   "traffic": None, "kernel": f"step2d_batch (variant {v})",
+                                   "traffic": None, "kernel": ("step2d_batch_tb2" if spl == 2 else "step2d_batch") +
+                                   f" (variant {v})", "steps_per_launch": spl,
                                    "ms_per_launch": per, "peak_kind": peak_kind},
-                      "gpu_launches": args.steps * nsteps, "clocks": clk.summary()}), flush=True)
+                      "gpu_launches": args.steps * launches, "clocks": clk.summary()}), flush=True)
 
 
 def run_adjoint_main(args, lbem, torch, stream, peak, peak_kind):
@@ -260,7 +268,19 @@ def other_forms(lbem, torch, p, peak, stream):
     per = ms / p.nsteps
     gbs = 44 * n / (per * 1e-3) / 1e9
     out["f32_single_step"] = {"mlups": n * p.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
-                              "frac": gbs / peak, "bytes_per_site": 44, "variant": v}
+                              "frac": gbs / peak, "bytes_per_site": 44, "steps_per_launch": 1, "variant": v}
+    # config 1: the 1024^2 medium (seed 1), 5000 steps, FP32; its 2 x 21 MB distributions and 4 MB medium stay in
+    # the 129 MB L2, so the bytes per launch over the launch time are an effective rate, above the HBM copy rate
+    p1 = W.heterogeneous_2d(1024, seed=1, nsteps=5000)
+    n1 = int(np.prod(p1.shape))
+    s = lbem.Solver(p1.shape, stream=stream.cuda_stream)
+    ms, v, spp = _time_run(lbem, torch, s, p1, p1.nsteps, stream, passes=3)
+    s.close()
+    per = ms / (p1.nsteps // spp + p1.nsteps % spp)
+    gbs = 44 * n1 / (per * 1e-3) / 1e9
+    out["f32_1024"] = {"mlups": n1 * p1.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "effective_gbs": gbs,
+                       "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp, "variant": v,
+                       "l2_resident": True, "lb_steps": p1.nsteps}
     probs = W.batch_2d(256, nsteps=2000)
     ss = []
     for q in probs:
@@ -283,11 +303,13 @@ def other_forms(lbem, torch, p, peak, stream):
     lbem.lbem_batch_destroy(b)
     for s in ss:
         s.close()
-    per = ms / 2000
+    spl = BATCH_SPL(v)
+    per = ms / (2000 // spl)
     gbs = 44 * sites / (per * 1e-3) / 1e9
     out["batch256"] = {"mlups": sites * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                        "frac": gbs / peak, "sites": sites, "media": len(probs), "lb_steps": 2000, "variant": v,
-                       "graph": True}
+                       "graph": True, "steps_per_launch": spl,
+                       "kernel": "step2d_batch_tb2" if spl == 2 else "step2d_batch"}
     # heterogeneous permeability (B x grad ln mu source at every site), 2000 steps: 52 B/site per launch (the
     # grad ln mu planes add 8 to the 44), two steps per launch by default, then single-step launches
     pm = W.heterogeneous_2d_mu(p.shape[0], seed=2, nsteps=2000)
@@ -356,6 +378,7 @@ def other_forms(lbem, torch, p, peak, stream):
     gbs = 172 * n3 / (per * 1e-3) / 1e9
     out["het3d_192_box"] = {"mlups": n3 * 500 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                             "frac": gbs / peak, "bytes_per_site": 172, "variant": v, "lb_steps": 500,
+                            "steps_per_launch": 1,
                             "bc": list(qb.bc), "layer": qb.layer}
     q = W.heterogeneous_3d(192, nsteps=1000)
     s = lbem.Solver(q.shape, stream=stream.cuda_stream)
@@ -396,7 +419,7 @@ def other_forms(lbem, torch, p, peak, stream):
     per = ms / 1000
     gbs = 172 * n3 / (per * 1e-3) / 1e9
     out["het3d_192"] = {"mlups": n3 * 1000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
-                        "frac": gbs / peak, "bytes_per_site": 172, "variant": v}
+                        "frac": gbs / peak, "bytes_per_site": 172, "variant": v, "steps_per_launch": 1}
     # backward pass bytes: recompute of 900 forward steps (172 B/site) + 1000 adjoint steps (272 B/site:
     # lambda 84 read + state 84 read + c_L^2 4 + FP64 gradient 16 read/write + lambda 84 write)
     bwd_bytes = (900 * 172 + 1000 * 272) * n3
@@ -441,6 +464,190 @@ def cpu_baseline(p, budget_s=12.0):
     return {"value": n ** p.D * steps / dt / 1e6, "unit": "Mlups", "cores": O.threads(), "kind": "oracle",
             "sample": f"FP64 oracle, {n}^{p.D} crop of the workload's medium, point source, {steps} steps "
                       f"({dt:.1f} s)"}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def crop512(p):
+    """The config-2 accuracy case (reading R11): the 512^2 centre crop of the 4096^2 medium run as its own periodic
+    problem, Ricker source at its centre, 64 receivers on a circle of radius 128, 5000 steps."""
+    c0 = (p.shape[0] - 512) // 2
+    eps = np.asarray(p.eps_r[c0:c0 + 512, c0:c0 + 512], np.float64)
+    recs = W.circle_receivers((256, 256), 128, 64)
+    return W.point_source_problem(2, (512, 512), np.sqrt(eps), 5000, (256, 256), 64, recs, name="crop512")
+
+
+# rel-L2 bars of the north star: FP32 storage <= 1e-4 after 5000 steps, reduced-precision storage <= 1e-3
+TOL = {"f32": 1e-4, "f16": 1e-3, "bf16": 1e-3, "i16b": 1e-3}
+
+
+def accuracy_cases(p, spl):
+    """Per form, the problem its rel-L2 against the FP64 oracle is stated on, and how the GPU runs it:
+    {form: (problem, storage, steps per launch or None for the library default, bar)}.  spl maps a form to the
+    steps per launch its timed run used, so the accuracy run takes the same kernels.  The storage forms share
+    the 512^2 crop (reading R11); the other forms use their own recipe at 256^2 (3D: 32^3), whose oracle runs fit
+    the benchmark's CPU budget; the batch uses its four smallest members."""
+    c = crop512(p)
+    cases = {"f32": (c, "f32", spl.get("f32"), TOL["f32"])}
+    for st in ("f16", "bf16", "i16b"):
+        cases[st] = (c, st, spl.get(st), TOL[st])
+    cases["f32_single_step"] = (c, "f32", 1, TOL["f32"])
+    cases["f32_1024"] = (W.heterogeneous_2d(256, seed=1, nsteps=5000, name="het2d_1024_recipe_256"), "f32",
+                         spl.get("f32_1024"), TOL["f32"])
+    small = {"f32_mu": W.heterogeneous_2d_mu(256, seed=2, nsteps=1000),
+             "f32_walls_absorbing": W.heterogeneous_2d_walls(256, seed=2, nsteps=1000, layer=16),
+             "f32_drude": W.heterogeneous_2d_drude(256, seed=2, nsteps=1000),
+             "f32_anisotropic": W.heterogeneous_2d_aniso(256, seed=2, nsteps=1000)}
+    for key, q in (("f32_mu_heterogeneous", small["f32_mu"]), ("f32_mu_single_step", small["f32_mu"]),
+                   ("f32_walls_absorbing", small["f32_walls_absorbing"]), ("f32_drude_dispersive", small["f32_drude"]),
+                   ("f32_drude_single_step", small["f32_drude"]), ("f32_anisotropic", small["f32_anisotropic"]),
+                   ("f32_anisotropic_single_step", small["f32_anisotropic"])):
+        cases[key] = (q, "f32", spl.get(key, 1 if key.endswith("single_step") else None), TOL["f32"])
+    q3 = W.heterogeneous_3d(32, seed=4, nsteps=300, sigma=3.0, plane_dz=8, rec_grid=(4, 4))
+    cases["het3d_192"] = (q3, "f32", None, TOL["f32"])
+    qb = W.heterogeneous_3d(32, seed=4, nsteps=300, sigma=3.0, plane_dz=8, rec_grid=(4, 4))
+    qb.bc, qb.layer, qb.gamma_max = (1, 1, 1), 4, 0.2
+    qb.name = "het3d_box_32"
+    cases["het3d_192_box"] = (qb, "f32", None, TOL["f32"])
+    members = sorted(W.batch_2d(256, nsteps=2000), key=lambda q: int(np.prod(q.shape)))[:4]
+    cases["batch256"] = (members, "f32", "batch", TOL["f32"])
+    return cases
+
+
+def _f32(a):
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def gpu_result(lbem, torch, stream, q, storage, spl):
+    """E, B ((3,) + grid) and traces of problem q run on the GPU library as a form runs it (float64 numpy)."""
+    s = lbem.Solver(q.shape, storage=storage, stream=stream.cuda_stream)
+    try:
+        s.set_problem(q)
+        if spl is not None:
+            lbem.lbem_set_temporal_blocking(s.h, spl, -1)
+        s.step(q.nsteps)
+        E, B = s.fields()
+        tr = s.traces(q.rec_site.size)
+        torch.cuda.synchronize()
+        return E.cpu().double().numpy(), B.cpu().double().numpy(), tr.cpu().double().numpy()
+    finally:
+        s.close()
+
+
+def gpu_batch_result(lbem, torch, stream, members):
+    """The members stepped together by the batched kernel: [(E, B, traces)] per member."""
+    ss = []
+    for q in members:
+        s = lbem.Solver(q.shape, stream=stream.cuda_stream)
+        s.set_problem(q)
+        ss.append(s)
+    b = lbem.lbem_batch_create([s.h for s in ss], stream.cuda_stream)
+    lbem.lbem_batch_step(b, members[0].nsteps)
+    out = []
+    for s, q in zip(ss, members):
+        E, B = s.fields()
+        tr = s.traces(q.rec_site.size)
+        torch.cuda.synchronize()
+        out.append((E.cpu().double().numpy(), B.cpu().double().numpy(), tr.cpu().double().numpy()))
+    lbem.lbem_batch_destroy(b)
+    for s in ss:
+        s.close()
+    return out
+
+
+def oracle_leg(p, cases, gpu_out):
+    """The CPU-baseline leg: the FP64 oracle, as it stands, on the host cores.  It times the oracle on the config-2
+    accuracy case (the 512^2 crop x 5000 steps, all cores), on one core (a 256^2 crop, 200 steps) and as an FP32
+    build of the same source (the 512^2 crop, 500 steps), and runs the oracle on every other form's accuracy case;
+    returns (cpu_baseline, {form: rel-L2 (E, B, traces)})."""
+    import oracle as O
+
+    def run(q):
+        disp = None
+        if q.D == 2 and q.wp2 is not None:
+            full = lambda a: _f32(np.broadcast_to(0.0 if a is None else a, q.shape))
+            disp = dict(wp2=full(q.wp2), wr2=full(q.wr2), gamma=full(q.gamma))
+        m = O.medium(q.D, _f32(q.eps_r), _f32(q.mu_r), bc=q.bc, layer=q.layer, gamma_max=q.gamma_max,
+                     dispersion=disp, aniso=q.aniso)
+        g = O.init_state(m, _f32(q.E0), _f32(q.B0))
+        pole = O.pole_state(m) if disp is not None else None
+        src = q.sources()
+        if src is not None:
+            src = dict(src, amp=_f32(src["amp"]))
+        t0 = time.perf_counter()
+        tr = O.run(m, g, q.nsteps, sources=src, receivers=q.receivers(), pole=pole)
+        dt = time.perf_counter() - t0
+        E, B = O.fields(m, g, pole)
+        return np.moveaxis(E, -1, 0), np.moveaxis(B, -1, 0), tr, dt
+
+    cores = O.threads()
+    done, samples, acc = {}, {}, {}
+    for key, (q, st, spl, tol) in cases.items():
+        qs = q if isinstance(q, list) else [q]
+        res = []
+        for qq in qs:
+            if qq.name not in done:
+                done[qq.name] = run(qq)
+                samples[qq.name] = {"mlups": float(np.prod(qq.shape)) * qq.nsteps / done[qq.name][3] / 1e6,
+                                    "seconds": done[qq.name][3]}
+            res.append(done[qq.name])
+        g = gpu_out.get(key)
+        if g is None:
+            continue
+        gs = g if isinstance(q, list) else [g]
+        e = [(_rel(a[0], r[0]), _rel(a[1], r[1]), _rel(a[2], r[2])) for a, r in zip(gs, res)]
+        acc[key] = tuple(max(x[k] for x in e) for k in range(3))
+    main = done["crop512"]
+    c = crop512(p)
+    value = 512 * 512 * c.nsteps / main[3] / 1e6
+    # one core, a 256^2 crop of the same medium, 200 steps
+    q1 = crop512(p)
+    q1.eps_r = q1.eps_r[128:384, 128:384]
+    q1.shape, q1.nsteps = (256, 256), 200
+    q1.src_site = np.array([W.flat_index((256, 256), (128, 128))], np.int64)
+    q1.rec_site = np.zeros(0, np.int64)
+    q1.rec_comp = np.zeros(0, np.int32)
+    q1.name = "crop256_1core"
+    O.set_threads(1)
+    try:
+        one = run(q1)[3]
+    finally:
+        O.set_threads(cores)
+    # FP32 build of the same source, all cores, the 512^2 crop for 500 steps
+    dt32, cores32 = O.time_fp32(c.eps_r, 500, int(c.src_site[0]), c.src_amp[0], threads_=cores)
+    cpu = {"value": value, "unit": "Mlups", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"FP64 oracle, 512^2 centre crop of the {p.shape[0]}^2 medium (config 2's accuracy case), "
+                     f"Ricker at the crop centre, 64 receivers, {c.nsteps} steps ({main[3]:.1f} s)",
+           "one_core": {"value": 256 * 256 * 200 / one / 1e6, "unit": "Mlups", "cores": 1,
+                        "sample": f"FP64 oracle, 256^2 crop of the same medium, 200 steps ({one:.1f} s)"},
+           "fp32_build": {"value": 512 * 512 * 500 / dt32 / 1e6, "unit": "Mlups", "cores": cores32,
+                          "sample": f"the same oracle source built with float, 512^2 crop, 500 steps ({dt32:.1f} s)"},
+           "accuracy_samples": samples}
+    return cpu, acc
 
 
 def dist_setup(args):
@@ -502,10 +709,11 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": p.name, "grid": list(p.shape), "lb_steps": p.nsteps, "storage": "f64-oracle"},
-            "cpu_baseline": {"value": value, "unit": "Mlups", "cores": cores, "kind": "oracle",
-                             "sample": f"FP64 oracle, {n}x{n} crop of the workload's medium, {steps_per} steps "
-                                       f"per benchmark step"},
+            "config": {"workload": p.name, "grid": [n, n], "crop_of": list(p.shape), "lb_steps": steps_per,
+                       "storage": "f64-oracle"},
+            "cpu_baseline": {"value": value, "unit": "Mlups", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": f"FP64 oracle, {n}x{n} centre crop of the workload's {p.shape[0]}^2 medium, "
+                                       f"{steps_per} steps per benchmark step"},
             "e2e": {"value": value, "unit": "Mlups", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -690,11 +898,32 @@ def main():
                "d2h_bytes_per_step": int(nb(E_h) + nb(B_h) + nb(tr_h) + 24)}
 
     forms = None
-    if not args.no_forms and args.lb_steps is None:
+    if not args.no_forms and args.lb_steps is None and args.workload == "het2d_4096":
         forms = other_forms(lbem, torch, p, peak, stream)
-    cpu = None
+    cpu, acc = None, {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p)
+        if args.workload == "het2d_4096" and args.lb_steps is None:
+            # every form's accuracy against the FP64 oracle, on the GPU kernels the form's timed run used
+            spl = {k: v.get("steps_per_launch") for k, v in (forms or {}).items()}
+            spl[args.storage] = spp
+            cases = accuracy_cases(p, spl)
+            if forms is None:
+                cases = {args.storage: cases[args.storage]}
+            gpu_out = {}
+            for key, (q, st, sp, _) in cases.items():
+                if sp == "batch":
+                    gpu_out[key] = gpu_batch_result(lbem, torch, stream, q)
+                else:
+                    gpu_out[key] = gpu_result(lbem, torch, stream, q, st, sp)
+            cpu, acc = oracle_leg(p, cases, gpu_out)
+            for key, e in acc.items():
+                if forms and key in forms:
+                    forms[key]["rel_l2"] = {"E": e[0], "B": e[1], "traces": e[2], "case": cases[key][0].name
+                                            if not isinstance(cases[key][0], list) else "4 smallest batch members",
+                                            "bar": cases[key][3], "within_bar": max(e) <= cases[key][3]}
+        else:
+            cpu = cpu_baseline(p)
+            cpu["cpu_model"] = cpu_model()
     s.close()
     if rank == 0:
         # per pass: the step launches (plus the edge kernel after each with 2D walls on the tile path), the medium
@@ -712,7 +941,32 @@ def main():
                            "l2": f"inputs larger than L2 (2 x {state_mb:.0f} MB distributions), no flush",
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "diagnostics_last": list(diag), "forms": forms}
+                "clocks": clk.summary(), "diagnostics_last": list(diag)}
+        main_acc = acc.get(args.storage)
+        if main_acc is not None:
+            line["accuracy"] = {"E": main_acc[0], "B": main_acc[1], "traces": main_acc[2],
+                                "case": "512^2 centre crop x 5000 steps vs FP64 oracle (config 2, reading R11)",
+                                "bar": TOL[args.storage], "within_bar": max(main_acc) <= TOL[args.storage]}
+        line["forms"] = forms
+        # last, so that it survives a truncated tail of the output: one compact entry per form
+        summ = {"legend": "[kMlups, frac of measured HBM copy rate at the form's algorithmic bytes per launch, "
+                          "steps per launch, rel-L2 E/B/traces vs FP64 oracle on the form's accuracy case, bar]"}
+
+        def entry(mlups, frac, spl_, e, bar):
+            r = None if e is None else "/".join(f"{x:.1e}" for x in e)
+            verdict = None if e is None else (f"<={bar:g} met" if max(e) <= bar else f"<={bar:g} MISSED")
+            return [round(mlups / 1e3, 1), None if frac is None else round(frac, 3), spl_, r, verdict]
+
+        summ[f"{args.storage} (main)"] = entry(value, roofline["frac"], spp, main_acc, TOL[args.storage])
+        for k, v in (forms or {}).items():
+            if k == "adjoint_192":
+                summ[k] = [round(v["mlups_forward_plus_backward"] / 1e3, 1), round(v["backward_frac"], 3), 1,
+                           "vs FD and oracle adjoint in tests", None]
+                continue
+            e = acc.get(k)
+            bar = TOL.get(k, TOL["f32"])
+            summ[k] = entry(v["mlups"], v.get("frac"), v.get("steps_per_launch"), e, bar)
+        line["forms_summary"] = summ
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

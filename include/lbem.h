@@ -376,11 +376,17 @@ lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);
 /* ---------------------------------------------------------------- batches of independent media */
 
 /* A batch steps n independent 2D FP32 handles (members, of any sizes) with one
- * kernel launch per step over a flattened tile table; runs of steps are
- * captured once into a CUDA graph and replayed.  Members keep their own
- * medium, fields, sources, receivers and outputs (use the calls above on them);
- * all members must be at the same time t when stepped.  The batch does not own
- * the members. */
+ * kernel launch per step, or per pair of steps, over a flattened work table of
+ * all members; runs of steps are captured once into a CUDA graph and replayed.
+ * Members keep their own medium, fields, sources, receivers and outputs (use
+ * the calls above on them); all members must be at the same time t when
+ * stepped.  The batch does not own the members.  Launch shapes (variants):
+ * 0..8 advance one step per launch (rows of warps, one site per thread, a
+ * persistent pipeline, lanes linear over each member's padded plane); 9, 10, 11
+ * advance two steps per launch through shared-memory tiles of 128 x 6 sites (5
+ * or 4 blocks per SM) and 128 x 8 sites (an odd step count takes one single
+ * step first).  Every variant gives the same bits as each member stepped
+ * alone. */
 lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out);
 lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps);
 lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best);

@@ -404,6 +404,14 @@ struct lbem_batch {
     size_t map_cap = 0;
     long long *d_t0 = nullptr;
     long long total_warps = 0, total_blocks = 0;
+    // two steps per launch: per member its step arguments for both buffer parities, a tile -> member table and
+    // each member's first tile (tile rows tb_rows)
+    lbk::StepArgs *d_args = nullptr;
+    int *d_tmap = nullptr;
+    long long *d_tstart = nullptr;
+    size_t tmap_cap = 0;
+    long long ntiles = 0;
+    int tb_rows = 0;
     int variant = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0, graph_variant = -1;
@@ -415,10 +423,57 @@ using namespace lbk;
 // variant 4: persistent row mapping (R = 1 table) with contiguous unit ranges and prefetch;
 // variants 5, 6: R = 1 with registers capped for 5 / 6 resident blocks per SM;
 // variants 7, 8: linear mapping over the padded plane (uncapped / capped for 5 blocks per SM)
-static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8};
+// Variants: R = 1, 2, 4 rows per warp; 0 one site per thread; -1 persistent register pipeline; -5, -6 R = 1
+// capped for 5 / 6 blocks per SM; -7, -8 linear over each member's padded plane (uncapped / 5 blocks per SM);
+// 100 + k: two steps per launch through shared-memory tiles, tile shape k (launch_batch_tb2).
+static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8, 100, 101, 102};
 static const int kBatchVariants = (int)(sizeof(kRowsB) / sizeof(kRowsB[0]));
+static const int kLinVariant = 7;  // the single-step kernel that takes the odd step of a two-step variant
+static bool two_step(int variant) { return kRowsB[variant] >= 100; }
+
+// Tile tables of the two-step kernel (tiles of 128 x rows sites) and every member's step arguments for both
+// buffer parities (args[2 k]: state in buffer a, written to b; args[2 k + 1]: the reverse).
+static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
+    std::vector<StepArgs> args(2 * (size_t)b->n);
+    std::vector<long long> ts(b->n + 1, 0);
+    for (int k = 0; k < b->n; k++) {
+        lbem_t *h = b->members[k];
+        args[2 * k] = step_args(h, h->cur);
+        args[2 * k + 1] = step_args(h, h->cur ^ 1);
+        const long long ntx = (h->grid.nx + 127) / 128, nty = (h->grid.ny + rows - 1) / rows;
+        ts[k + 1] = ts[k] + ntx * nty;
+    }
+    const long long total = ts[b->n];
+    std::vector<int> map((size_t)total);
+    for (int k = 0; k < b->n; k++)
+        for (long long u = ts[k]; u < ts[k + 1]; u++) map[(size_t)u] = k;
+    if (b->tmap_cap < map.size()) {
+        cudaFree(b->d_tmap);
+        b->d_tmap = nullptr;
+        b->tmap_cap = 0;
+        if (cudaMalloc((void **)&b->d_tmap, sizeof(int) * map.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBEM_ERR_NOMEM, "lbem_batch: no room for the tile table");
+        }
+        b->tmap_cap = map.size();
+    }
+    LBEM_CUDA(cudaMemcpyAsync(b->d_args, args.data(), sizeof(StepArgs) * args.size(), cudaMemcpyHostToDevice,
+                              b->stream));
+    LBEM_CUDA(cudaMemcpyAsync(b->d_tstart, ts.data(), sizeof(long long) * (b->n + 1), cudaMemcpyHostToDevice,
+                              b->stream));
+    LBEM_CUDA(cudaMemcpyAsync(b->d_tmap, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, b->stream));
+    LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vectors go out of scope
+    b->ntiles = total;
+    b->tb_rows = rows;
+    return LBEM_OK;
+}
 
 static lbem_status upload_tables(lbem_batch_t *b, int variant) {
+    if (two_step(variant)) {  // the pair kernel's tiles, and the linear single-step kernel's table for an odd step
+        lbem_status st = upload_tile_tables(b, batch_tb2_rows(kRowsB[variant] - 100));
+        if (st != LBEM_OK) return st;
+        variant = kLinVariant;
+    }
     const int R = kRowsB[variant] < 0 ? 1 : kRowsB[variant];  // persistent and capped variants use the R = 1 table
     std::vector<Member> hm(b->n);
     std::vector<long long> ws(b->n + 1, 0);
@@ -496,6 +551,33 @@ static cudaError_t launch_batch(lbem_batch_t *b, int variant, int offset) {
     return cudaGetLastError();
 }
 
+// Enqueue nsteps steps of `variant` from the members' current state (t0 in device memory): one launch per step, or
+// for a two-step variant one launch per pair of steps, after a single step first when nsteps is odd.  Returns the
+// number of launches (each one flips the members' buffers) in *nlaunch.
+static cudaError_t enqueue_batch(lbem_batch_t *b, int variant, int nsteps, int *nlaunch) {
+    if (!two_step(variant)) {
+        for (int k = 0; k < nsteps; k++) {
+            cudaError_t e = launch_batch(b, variant, k);
+            if (e != cudaSuccess) return e;
+        }
+        *nlaunch = nsteps;
+        return cudaSuccess;
+    }
+    int n = 0, toff = 0;
+    if (nsteps & 1) {
+        cudaError_t e = launch_batch(b, kLinVariant, 0);
+        if (e != cudaSuccess) return e;
+        n = toff = 1;
+    }
+    for (; toff + 2 <= nsteps; toff += 2, n++) {
+        cudaError_t e = launch_batch_tb2(b->d_args, b->d_tmap, b->d_tstart, b->ntiles, b->d_t0, toff, n & 1,
+                                         kRowsB[variant] - 100, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    *nlaunch = n;
+    return cudaSuccess;
+}
+
 static void drop_batch_graph(lbem_batch_t *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -539,6 +621,8 @@ lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_
     b->stream = (cudaStream_t)stream;
     cudaError_t e = cudaMalloc((void **)&b->d_members, sizeof(Member) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_wstart, sizeof(long long) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_args, sizeof(StepArgs) * 2 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tstart, sizeof(long long) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_t0, sizeof(long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -564,18 +648,17 @@ lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps) {
         if (!(b->graph && b->graph_steps == nsteps && b->graph_variant == b->variant)) {
             drop_batch_graph(b);
             LBEM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            for (int k = 0; k < nsteps; k++) {
-                cudaError_t e = launch_batch(b, b->variant, k);
-                if (e != cudaSuccess) {
-                    cudaGraph_t g = nullptr;
-                    cudaStreamEndCapture(b->stream, &g);
-                    if (g) cudaGraphDestroy(g);
-                    return cuda_fail(e, "lbem_batch_step (capture)");
-                }
+            int nl = 0;
+            cudaError_t e = enqueue_batch(b, b->variant, nsteps, &nl);
+            if (e != cudaSuccess) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(b->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(e, "lbem_batch_step (capture)");
             }
             cudaGraph_t g = nullptr;
             LBEM_CUDA(cudaStreamEndCapture(b->stream, &g));
-            cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+            e = cudaGraphInstantiate(&b->graph, g, 0);
             cudaGraphDestroy(g);
             LBEM_CUDA(e);
             b->graph_steps = nsteps;
@@ -583,10 +666,13 @@ lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps) {
         }
         LBEM_CUDA(cudaGraphLaunch(b->graph, b->stream));
     } else {
-        for (int k = 0; k < nsteps; k++) LBEM_CUDA(launch_batch(b, b->variant, k));
+        int nl = 0;
+        LBEM_CUDA(enqueue_batch(b, b->variant, nsteps, &nl));
     }
+    // launches per call: one per step, or one per pair of steps (plus a single step first when nsteps is odd)
+    const int nlaunch = two_step(b->variant) ? nsteps / 2 + (nsteps & 1) : nsteps;
     for (lbem_t *h : b->members) {
-        h->cur ^= (nsteps & 1);
+        h->cur ^= (nlaunch & 1);
         h->t += nsteps;
     }
     // members' own streams must see the batch's work before their next call
@@ -622,7 +708,8 @@ lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best) {
         LBEM_CUDA(cudaMemcpyAsync(b->d_t0, &t0, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
         for (int rep = 0; rep < 2; rep++) {
             cudaEventRecord(e0, b->stream);
-            for (int k = 0; k < trial_steps; k++) LBEM_CUDA(launch_batch(b, v, k));
+            int nl = 0;
+            LBEM_CUDA(enqueue_batch(b, v, trial_steps, &nl));
             cudaEventRecord(e1, b->stream);
         }
         cudaEventSynchronize(e1);
@@ -669,6 +756,9 @@ void lbem_batch_destroy(lbem_batch_t *b) {
     cudaFree(b->d_wstart);
     cudaFree(b->d_map);
     cudaFree(b->d_t0);
+    cudaFree(b->d_args);
+    cudaFree(b->d_tstart);
+    cudaFree(b->d_tmap);
     delete b;
 }
 

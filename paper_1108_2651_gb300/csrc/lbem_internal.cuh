@@ -544,6 +544,11 @@ cudaError_t tb_set_wait_limit(unsigned long long ns);  // limit of its bounded w
 int tb3_nshapes();
 cudaError_t launch_step_2d_tb3(const StepArgs &a, int shape, cudaStream_t s);
 cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s);
+// two steps per launch over a batch (tblock.cu): tiles of every member from a flattened table; args[2 m + par] are
+// member m's step arguments for the launch's buffer parity; tile rows of each shape: batch_tb2_rows
+int batch_tb2_rows(int shape);
+cudaError_t launch_batch_tb2(const StepArgs *args, const int *tmember, const long long *tstart, long long ntiles,
+                             const long long *t0p, int toff, int par, int shape, cudaStream_t s);
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);

@@ -52,7 +52,7 @@ __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<flo
 // Shared-memory layout of a CTA (floats; regions start on 128-byte boundaries), then one mbarrier.  The
 // medium stage holds c_L^2 and, with a heterogeneous permeability (MU), d_x ln mu and d_y ln mu after it, each
 // R rows of TW (the two gradient planes are one TMA box, so R * TW floats must be a multiple of 128 bytes).
-template <int TBY, bool MU = false>
+template <int TBY, bool MU = false, bool POLE = false>
 struct TbGeom {
     static constexpr int R = TBY + 2;  // staged rows per plane at t (tile rows y0-1 .. y0+TBY), and of c_L^2
     static constexpr int NCL = MU ? 3 : 1;  // medium planes
@@ -60,15 +60,60 @@ struct TbGeom {
     // plane strides (each staged plane at t is a TMA destination: 128-byte aligned)
     static constexpr int IN_PL = up32(R * TW), P_PL = TBY * TW;
     static constexpr int IN_SZ = up32(5 * IN_PL), CL_SZ = up32(NCL * R * TW), P_SZ = up32(5 * P_PL);
-    static constexpr int SZ = IN_SZ + CL_SZ + P_SZ;
+    // with a dispersive pole: P at t over the window (R rows of TW), and J, wp2, wr2, gamma over the owned sites
+    // (TBY rows of TBX, plane stride JS_PL), both staged with the window
+    static constexpr int PS_SZ = POLE ? up32(R * TW) : 0, JS_PL = TBY * TBX, JS_SZ = POLE ? up32(4 * JS_PL) : 0;
+    static constexpr int SZ = IN_SZ + CL_SZ + P_SZ + PS_SZ + JS_SZ;
     static constexpr size_t BYTES = sizeof(float) * SZ + sizeof(unsigned long long);
-    static constexpr unsigned TMA_BYTES = sizeof(float) * (5 + NCL) * R * TW;
+    static constexpr unsigned TMA_BYTES = sizeof(float) * ((5 + NCL) * R * TW + (POLE ? R * TW + 4 * JS_PL : 0));
     static_assert(!MU || (R * TW) % 32 == 0, "gradient planes 128-byte aligned");
+    static_assert(!POLE || JS_PL % 32 == 0, "pole planes 128-byte aligned");
+};
+
+// Tensor maps of the pole's planes (P at t: box TW x (TBY+2) at (x0-4, y0-1); J, wp2, wr2, gamma: box TBX x TBY at
+// (x0, y0)); an unused placeholder for kernels without a pole.
+template <bool POLE>
+struct PoleMaps {
+    CUtensorMap P, J, wp, wr, gm;
+};
+template <>
+struct PoleMaps<false> {
+    int unused;
 };
 
 // Source plane k of the medium stage: c_L^2, then d_x ln mu and d_y ln mu.
 __device__ __forceinline__ const float *medium_plane(const StepArgs &a, int k) {
     return k == 0 ? a.med.cL2 : a.med.dlnmu + (k - 1) * a.g.plane;
+}
+
+// Asynchronous copies of the pole's planes for one tile (as the window: 16 bytes per copy where every group of 4
+// columns stays contiguous after the periodic wrap, else 4): P over the window's rows and columns into PS, J, wp2,
+// wr2, gamma over the tile's own rows and columns into JS.
+template <int TBY>
+__device__ __forceinline__ void tb_issue_pole(const StepArgs &a, int x0, int y0, float *PS, float *JS, int nt) {
+    constexpr int R = TbGeom<TBY>::R, JPL = TbGeom<TBY, false, true>::JS_PL, Q = TW / 4, QJ = TBX / 4;
+    const Grid &G = a.g;
+    const bool v16 = (x0 - 4 >= 0 && x0 + TBX + 4 <= G.nx) || (G.nx & 3) == 0;
+    for (int k = threadIdx.x; k < R * Q; k += nt) {
+        const int r = k / Q, q = k - r * Q;
+        const float *src = a.med.Pr + (long long)wrapi(y0 - 1 + r, G.ny) * G.pitch;
+        float *dst = PS + r * TW + 4 * q;
+        if (v16)
+            tb_cpa16(dst, src + wrapi(x0 - 4 + 4 * q, G.nx));
+        else
+            for (int j = 0; j < 4; j++) tb_cpa4(dst + j, src + wrapi(x0 - 4 + 4 * q + j, G.nx));
+    }
+    for (int k = threadIdx.x; k < 4 * TBY * QJ; k += nt) {
+        const int pr = k / QJ, q = k - pr * QJ;
+        const int pl = pr / TBY, r = pr - pl * TBY;
+        const float *base = pl == 0 ? a.med.J : pl == 1 ? a.med.wp2 : pl == 2 ? a.med.wr2 : a.med.gam;
+        const float *src = base + (long long)wrapi(y0 + r, G.ny) * G.pitch;
+        float *dst = JS + pl * JPL + r * TBX + 4 * q;
+        if (v16)
+            tb_cpa16(dst, src + wrapi(x0 + 4 * q, G.nx));
+        else
+            for (int j = 0; j < 4; j++) tb_cpa4(dst + j, src + wrapi(x0 + 4 * q + j, G.nx));
+    }
 }
 
 // Asynchronous copies of one tile's window with periodic wrap (16 bytes per copy when every group of 4
@@ -163,26 +208,36 @@ __device__ __forceinline__ bool tb_interior(int x0, int y0, const Grid &G) {
 // Start the loads of one tile's window: one thread issues six TMA copies (each population plane as a
 // (TBY+2) x (TBX+8) box at its row shift, and c_L^2) for interior tiles; every thread issues its share of the
 // asynchronous copies otherwise.
-template <int TBY, bool MU = false>
+template <int TBY, bool MU = false, bool POLE = false>
 __device__ __forceinline__ void tb_load(const StepArgs &a, int x0, int y0, float *IN, float *CL, unsigned mbar,
                                         bool tma, const CUtensorMap *tmIn, const CUtensorMap *tmCL, int nt,
-                                        const CUtensorMap *tmDL = nullptr) {
+                                        const CUtensorMap *tmDL = nullptr, float *PS = nullptr, float *JS = nullptr,
+                                        const PoleMaps<POLE> *pm = nullptr) {
     if (tma) {
         if (threadIdx.x == 0) {
             // earlier generic-proxy accesses of the window (ordered by the preceding barrier) before the
             // asynchronous-proxy writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
-                         "r"(TbGeom<TBY, MU>::TMA_BYTES)
+                         "r"(TbGeom<TBY, MU, POLE>::TMA_BYTES)
                          : "memory");
 #pragma unroll
             for (int p = 0; p < 5; p++)
                 tma_load_3d(IN + p * TbGeom<TBY>::IN_PL, tmIn, x0 - 4, y0 - 1 + in_shift(p), p, mbar);
             tma_load_2d(CL, tmCL, x0 - 4, y0 - 1, mbar);
             if (MU) tma_load_3d(CL + TbGeom<TBY>::R * TW, tmDL, x0 - 4, y0 - 1, 0, mbar);
+            if constexpr (POLE) {
+                constexpr int JPL = TbGeom<TBY, false, true>::JS_PL;
+                tma_load_2d(PS, &pm->P, x0 - 4, y0 - 1, mbar);
+                tma_load_2d(JS, &pm->J, x0, y0, mbar);
+                tma_load_2d(JS + JPL, &pm->wp, x0, y0, mbar);
+                tma_load_2d(JS + 2 * JPL, &pm->wr, x0, y0, mbar);
+                tma_load_2d(JS + 3 * JPL, &pm->gm, x0, y0, mbar);
+            }
         }
     } else {
         tb_issue<TBY, MU>(a, x0, y0, IN, CL, nt);
+        if constexpr (POLE) tb_issue_pole<TBY>(a, x0, y0, PS, JS, nt);
     }
 }
 
@@ -192,6 +247,13 @@ __device__ __forceinline__ bool tb_events(const StepArgs &a, int y0) {
     const Grid &G = a.g;
     return a.evt.rowptr && !(y0 >= 1 && y0 + TBY + 1 <= G.ny &&
                              __ldg(a.evt.rowptr + y0 - 1) == __ldg(a.evt.rowptr + y0 + TBY + 1));
+}
+
+// Whether grid row gy (wrapped) holds a source or receiver: within an event tile, only such rows take the per-site
+// event path (a warp-uniform test: one warp computes one row).
+__device__ __forceinline__ bool row_events(const StepArgs &a, int gy) {
+    const int y = wrapi(gy, a.g.ny);
+    return __ldg(a.evt.rowptr + y) != __ldg(a.evt.rowptr + y + 1);
 }
 
 // Populations pulled by four consecutive sites at shared row `row`, column c (a multiple of 4) of a shifted
@@ -294,8 +356,8 @@ __device__ __forceinline__ void tb_update4(const StepArgs &a, const PULL &g, flo
 // same warp, so the pole's state of the warp's owned row stays in registers (Jh, Ph: J at t+1/2, P at t+1).
 template <int TBY, int NT, bool EV, bool MU = false, bool AN = false, bool POLE = false>
 __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, const float *CL, float *P, int x0,
-                                          int y0, long long t, float4 &clb, float4 &dbx, float4 &dby, float4 &Jh,
-                                          float4 &Ph) {
+                                          int y0, long long t, float4 &clb, float4 &dbx, float4 &dby, Pole4 &ph,
+                                          const float *PS = nullptr, const float *JS = nullptr) {
     using Gm = TbGeom<TBY>;
     constexpr int R = Gm::R, NW = NT / 32, PL = Gm::P_PL, DX = R * TW, DY = 2 * R * TW;
     static_assert(!POLE || NW == R, "with a pole: one warp per row of step t");
@@ -316,27 +378,30 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
         const float4 dlx = MU ? lds4(CL + DX + py * TW + c) : cl, dly = MU ? lds4(CL + DY + py * TW + c) : cl;
         const bool own = py >= 1 && py <= TBY;
         Pole4 pp;
-        if (POLE) {
-            const int gy = y0 - 1 + py, gx = x0 + 4 * lane;
-            pp.P = ld_plane4(a.med.Pr, G, gy, gx);
+        if (POLE) {  // from the stages loaded with the window
+            constexpr int JPL = TbGeom<TBY, false, true>::JS_PL;
+            pp.P = lds4(PS + py * TW + c);
             pp.J = pp.wp = pp.wr = pp.gm = make_float4(0.f, 0.f, 0.f, 0.f);
             // J is updated in place by the tile owning the site.  Lanes past nx (rows past ny) of a ragged last
             // tile read J at wrapped sites of another tile, which may be updating them: their pole results only
             // ever reach the row padding or are dropped, while the collisions they feed use P at t, which no
             // launch writes in place.
             if (own) {
-                pp.J = ld_plane4(a.med.J, G, gy, gx);
-                pp.wp = ld_plane4(a.med.wp2, G, gy, gx);
-                pp.wr = ld_plane4(a.med.wr2, G, gy, gx);
-                pp.gm = ld_plane4(a.med.gam, G, gy, gx);
+                const float *js = JS + (py - 1) * TBX + 4 * lane;
+                pp.J = lds4(js);
+                pp.wp = lds4(js + JPL);
+                pp.wr = lds4(js + 2 * JPL);
+                pp.gm = lds4(js + 3 * JPL);
             }
         }
         float4 o0, o1, o2, o3, o4;
-        tb_update4m<EV, MU, Pull4, AN, POLE>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, own, o0, o1, o2, o3, o4, &pp);
-        if (POLE && own) {
-            Jh = pp.J;
-            Ph = pp.P;
-        }
+        if (EV && row_events(a, y0 - 1 + py))
+            tb_update4m<true, MU, Pull4, AN, POLE>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, own, o0, o1, o2, o3, o4,
+                                                   &pp);
+        else
+            tb_update4m<false, MU, Pull4, AN, POLE>(a, g, cl, dlx, dly, x0, y0 - 1 + py, t, own, o0, o1, o2, o3, o4,
+                                                    &pp);
+        if (POLE && own) ph = pp;  // J(t+1/2), P(t+1) and the parameters stay with this warp for step t+1
         float *Pr = P + c;
         if (py >= 1 && py <= TBY) {
             sts4(Pr + 0 * PL + (py - 1) * TW, o0);
@@ -360,7 +425,7 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
         if (AN || POLE) {
             const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
             const int gx = wrapi(x0 - 4 + cc, G.nx), gy = wrapi(y0 - 1 + py, G.ny);
-            const float pz = POLE ? a.med.Pr[(long long)gy * G.pitch + gx] : 0.f;
+            const float pz = POLE ? PS[py * TW + cc] : 0.f;
             if (EV) shat = site_events(a, gx, gy, t, false, q0, q1, q2, q3, q4, ck, 0.f, pz, r, ri, a.med.amu);
             o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz);
         } else {
@@ -379,7 +444,7 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
 // Step t+1 on tile row y0 + warp from the t+1 stage, written as 16-byte streaming stores.
 template <int TBY, bool EV, bool MU = false, bool AN = false, bool POLE = false>
 __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, float4 clb, float4 dbx, float4 dby,
-                                          int x0, int y0, long long t, float4 Jh = float4(), float4 Ph = float4()) {
+                                          int x0, int y0, long long t, const Pole4 &ph = Pole4()) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31, oy = (threadIdx.x >> 5) - (POLE ? 1 : 0);
     const int gy = y0 + oy;
@@ -387,16 +452,12 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
     const int c = 4 + 4 * lane;
     const Pull4 g(P, TbGeom<TBY>::P_PL, oy, c);
     Pole4 pp;
-    if (POLE) {
-        const int gx = x0 + 4 * lane;
-        pp.P = Ph;
-        pp.J = Jh;
-        pp.wp = ld_plane4(a.med.wp2, G, gy, gx);
-        pp.wr = ld_plane4(a.med.wr2, G, gy, gx);
-        pp.gm = ld_plane4(a.med.gam, G, gy, gx);
-    }
+    if (POLE) pp = ph;
     float4 o0, o1, o2, o3, o4;
-    tb_update4m<EV, MU, Pull4, AN, POLE>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4, &pp);
+    if (EV && row_events(a, gy))
+        tb_update4m<true, MU, Pull4, AN, POLE>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4, &pp);
+    else
+        tb_update4m<false, MU, Pull4, AN, POLE>(a, g, clb, dbx, dby, x0, gy, t + 1, true, o0, o1, o2, o3, o4, &pp);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
         const long long off = (long long)gy * G.pitch + x0 + 4 * lane;
         float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + off);
@@ -420,13 +481,16 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
 template <int TBY, int NT, int MINB, bool MU = false, bool AN = false, bool POLE = false>
 __global__ void __launch_bounds__(NT, MINB)
     step2d_tb2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
-               const __grid_constant__ CUtensorMap tmDL, int use_tma, int ntx, int nty, int dq, int dr) {
+               const __grid_constant__ CUtensorMap tmDL, const __grid_constant__ PoleMaps<POLE> pm, int use_tma,
+               int ntx, int nty, int dq, int dr) {
     static_assert(NT / 32 >= TBY, "one warp per row of step t+1");
-    using Gm = TbGeom<TBY, MU>;
+    using Gm = TbGeom<TBY, MU, POLE>;
     extern __shared__ __align__(1024) float sm[];
     float *IN = sm;              // [5][TBY+2][TW], shifted planes at t
     float *CL = sm + Gm::IN_SZ;  // [1 or 3][TBY+2][TW]: c_L^2 (and d_x ln mu, d_y ln mu)
     float *P = CL + Gm::CL_SZ;   // [5][TBY][TW], shifted planes at t+1
+    float *PS = P + Gm::P_SZ;    // with a pole: [TBY+2][TW] P at t
+    float *JS = PS + Gm::PS_SZ;  // with a pole: [4][TBY][TBX] J, wp2, wr2, gamma of the owned sites
     unsigned long long *mb = reinterpret_cast<unsigned long long *>(sm + Gm::SZ);
     const Grid &G = a.g;
     const int tid = threadIdx.x;
@@ -441,8 +505,8 @@ __global__ void __launch_bounds__(NT, MINB)
     __syncthreads();
     unsigned parity = 0;  // next phase of the mbarrier to wait for
     const unsigned long long wait_limit = g_wait_limit_ns;
-    tb_load<TBY, MU>(a, tx * TBX, ty * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(tx * TBX, ty * TBY, G), &tmIn,
-                     &tmCL, NT, &tmDL);
+    tb_load<TBY, MU, POLE>(a, tx * TBX, ty * TBY, IN, CL, mbar, use_tma && tb_interior<TBY>(tx * TBX, ty * TBY, G),
+                           &tmIn, &tmCL, NT, &tmDL, PS, JS, &pm);
     asm volatile("cp.async.commit_group;\n" ::);
     bool events = tb_events<TBY>(a, ty * TBY);
     const long long t = a.t;
@@ -467,25 +531,172 @@ __global__ void __launch_bounds__(NT, MINB)
             mbar_wait(mbar, parity ^ 1u, kDrainNs);  // drain what is in flight
             return;
         }
-        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb, Jh = clb, Ph = clb;
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb;
+        Pole4 ph;
         if (events)
-            tb_step_a<TBY, NT, true, MU, AN, POLE>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, Jh, Ph);
+            tb_step_a<TBY, NT, true, MU, AN, POLE>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, ph, PS, JS);
         else
-            tb_step_a<TBY, NT, false, MU, AN, POLE>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, Jh, Ph);
+            tb_step_a<TBY, NT, false, MU, AN, POLE>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, ph, PS, JS);
         __syncthreads();
-        if (has_next)  // the t stage and the medium stage are free: start the loads of the next tile
-            tb_load<TBY, MU>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar,
-                             use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, NT, &tmDL);
+        if (has_next)  // the t stage, the medium stage (and the pole's stages) are free: load the next tile
+            tb_load<TBY, MU, POLE>(a, ntx_ * TBX, nty_ * TBY, IN, CL, mbar,
+                                   use_tma && tb_interior<TBY>(ntx_ * TBX, nty_ * TBY, G), &tmIn, &tmCL, NT, &tmDL,
+                                   PS, JS, &pm);
         asm volatile("cp.async.commit_group;\n" ::);
         if (events)
-            tb_step_b<TBY, true, MU, AN, POLE>(a, P, clb, dbx, dby, x0, y0, t, Jh, Ph);
+            tb_step_b<TBY, true, MU, AN, POLE>(a, P, clb, dbx, dby, x0, y0, t, ph);
         else
-            tb_step_b<TBY, false, MU, AN, POLE>(a, P, clb, dbx, dby, x0, y0, t, Jh, Ph);
+            tb_step_b<TBY, false, MU, AN, POLE>(a, P, clb, dbx, dby, x0, y0, t, ph);
         tx = ntx_;
         ty = nty_;
         events = events_next;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// =====================================================================================================
+// Two steps per launch over a batch of independent media (FP32, uniform mu, periodic): one persistent launch takes
+// the tiles of every member in turn from a flattened tile table, with the same site updates as step2d_tb2, so each
+// member's result is bit-identical to its single steps.  A member's arguments are read from a device array
+// (args[2 m + par]: par = 0 reads the member's buffer a and writes b, 1 the reverse) and t from device memory, so
+// one captured graph serves every call.  The windows load by asynchronous copies (no per-member tensor maps):
+// every 4-column group inside the member is one 16-byte copy; only the groups that straddle or cross the periodic
+// wrap take element copies, and columns past x = nx + 1 are not loaded at all (no owned site's two-step pull
+// stencil reaches them; the lanes that compute there are discarded).
+
+template <int TBY>
+__device__ __forceinline__ void tb_issue_b(const StepArgs &a, int x0, int y0, float *IN, float *CL, int nt) {
+    constexpr int R = TbGeom<TBY>::R, PL = TbGeom<TBY>::IN_PL, Q = TW / 4, NP = 6;
+    const int nx = a.g.nx, ny = a.g.ny, pitch = a.g.pitch;
+    const long long plane = a.g.plane;
+    const float *in = static_cast<const float *>(a.in.data);
+    const float *cl = a.med.cL2;
+    const int lane = threadIdx.x & 31;
+    // Window column c holds x = x0 - 4 + c.  Work items of one staged row: the 4-column groups q that lie wholly
+    // inside the member (qlo .. qhi, one 16-byte copy each), then single columns: the four wrapped ones left of
+    // x = 0 (first tile of a row) and the columns from the first group past qhi up to x = nx + 1 (wrapped where
+    // x >= nx).  The items are spread over the lanes, so an edge tile costs about what an inner one does.
+    const int qlo = x0 == 0 ? 1 : 0;
+    const int qhi = min(Q - 1, (nx - x0) >> 2);
+    const int ng = max(0, qhi - qlo + 1);
+    const int nl = x0 == 0 ? 4 : 0;
+    const int cr0 = 4 * (qhi + 1), cmax = min(TW - 1, nx + 5 - x0);
+    const int nitems = ng + nl + max(0, cmax - cr0 + 1);
+    for (int pr = threadIdx.x >> 5; pr < NP * R; pr += nt >> 5) {  // one warp per (plane, row) of the window
+        const int pl = pr / R, r = pr - pl * R;
+        const float *src;
+        float *dst;
+        if (pl < 5) {
+            src = in + pl * plane + (long long)wrapi(y0 - 1 + r + in_shift(pl), ny) * pitch;
+            dst = IN + pl * PL + r * TW;
+        } else {
+            src = cl + (long long)wrapi(y0 - 1 + r, ny) * pitch;
+            dst = CL + r * TW;
+        }
+        for (int it = lane; it < nitems; it += 32) {
+            if (it < ng) {
+                const int q = qlo + it;
+                tb_cpa16(dst + 4 * q, src + x0 - 4 + 4 * q);
+            } else {
+                int c = it - ng;
+                c = c < nl ? c : cr0 + (c - nl);
+                tb_cpa4(dst + c, src + wrapi(x0 - 4 + c, nx));
+            }
+        }
+    }
+}
+
+template <int TBY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    step2d_batch_tb2(const StepArgs *__restrict__ args, const int *__restrict__ tmember,
+                     const long long *__restrict__ tstart, long long ntiles, const long long *__restrict__ t0p, int toff,
+                     int par) {
+    static_assert(NT / 32 >= TBY, "one warp per row of step t+1");
+    using Gm = TbGeom<TBY>;
+    extern __shared__ __align__(1024) float sm[];
+    float *IN = sm;
+    float *CL = sm + Gm::IN_SZ;
+    float *P = CL + Gm::CL_SZ;
+    long long k = blockIdx.x;
+    if (k >= ntiles) return;
+    const long long t = *t0p + toff;
+    // tile k -> member, origin
+    auto locate = [&](long long kk, int &m, int &x0, int &y0) {
+        m = __ldg(tmember + kk);
+        const int local = (int)(kk - __ldg(tstart + m));  // tiles of one member fit in an int
+        const int ntx = (args[2 * m + par].g.nx + TBX - 1) / TBX;
+        const int ty = local / ntx;
+        x0 = (local - ty * ntx) * TBX;
+        y0 = ty * TBY;
+    };
+    int m, x0, y0;
+    locate(k, m, x0, y0);
+    tb_issue_b<TBY>(args[2 * m + par], x0, y0, IN, CL, NT);
+    asm volatile("cp.async.commit_group;\n" ::);
+    bool events = tb_events<TBY>(args[2 * m + par], y0);
+    while (true) {
+        const long long kn = k + gridDim.x;
+        const bool has_next = kn < ntiles;
+        int mn = 0, xn = 0, yn = 0;
+        if (has_next) locate(kn, mn, xn, yn);
+        const bool events_next = has_next && tb_events<TBY>(args[2 * mn + par], yn);
+        const StepArgs &a = args[2 * m + par];
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncthreads();  // every thread's copies have landed, and step t+1 of the previous tile is done with P
+        float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb;
+        Pole4 ph;
+        if (events)
+            tb_step_a<TBY, NT, true>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, ph);
+        else
+            tb_step_a<TBY, NT, false>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, ph);
+        __syncthreads();
+        if (has_next) tb_issue_b<TBY>(args[2 * mn + par], xn, yn, IN, CL, NT);
+        asm volatile("cp.async.commit_group;\n" ::);
+        if (events)
+            tb_step_b<TBY, true>(a, P, clb, dbx, dby, x0, y0, t);
+        else
+            tb_step_b<TBY, false>(a, P, clb, dbx, dby, x0, y0, t);
+        if (!has_next) break;
+        k = kn;
+        m = mn;
+        x0 = xn;
+        y0 = yn;
+        events = events_next;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+template <int TBY, int NT, int MINB>
+static cudaError_t launch_batch_tb(const StepArgs *args, const int *tmember, const long long *tstart,
+                                   long long ntiles, const long long *t0p, int toff, int par, cudaStream_t s) {
+    using Gm = TbGeom<TBY>;
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(step2d_batch_tb2<TBY, NT, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_batch_tb2<TBY, NT, MINB>, NT, Gm::BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long slots = (long long)per_sm * nsm;
+    const unsigned blocks = (unsigned)(ntiles < slots ? ntiles : slots);
+    if (blocks == 0) return cudaSuccess;
+    step2d_batch_tb2<TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(args, tmember, tstart, ntiles, t0p, toff, par);
+    return cudaGetLastError();
+}
+
+int batch_tb2_rows(int shape) { return shape == 2 ? 8 : 6; }
+
+cudaError_t launch_batch_tb2(const StepArgs *args, const int *tmember, const long long *tstart, long long ntiles,
+                             const long long *t0p, int toff, int par, int shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_batch_tb<6, 256, 4>(args, tmember, tstart, ntiles, t0p, toff, par, s);
+        case 2: return launch_batch_tb<8, 320, 3>(args, tmember, tstart, ntiles, t0p, toff, par, s);
+        default: return launch_batch_tb<6, 256, 5>(args, tmember, tstart, ntiles, t0p, toff, par, s);
+    }
 }
 
 // =====================================================================================================
@@ -825,9 +1036,28 @@ static bool make_dl_map(const StepArgs &a, CUtensorMap *mDL) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor maps of the pole's planes for the tile kernel: P at t (pitched [ny][pitch], box TW x (TBY+2)) and J, wp2,
+// wr2, gamma (box TBX x TBY); false if unavailable.
+template <int TBY>
+static bool make_pole_maps(const StepArgs &a, PoleMaps<true> *pm) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || !a.med.Pr) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny};
+    const cuuint64_t str[1] = {(cuuint64_t)a.g.pitch * 4};
+    const cuuint32_t boxP[2] = {(cuuint32_t)TW, (cuuint32_t)(TBY + 2)}, boxJ[2] = {(cuuint32_t)TBX, (cuuint32_t)TBY};
+    const cuuint32_t one[2] = {1, 1};
+    auto enc = [&](CUtensorMap *m, const float *base, const cuuint32_t *box) {
+        return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, str, box, one,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    return enc(&pm->P, a.med.Pr, boxP) && enc(&pm->J, a.med.J, boxJ) && enc(&pm->wp, a.med.wp2, boxJ) &&
+           enc(&pm->wr, a.med.wr2, boxJ) && enc(&pm->gm, a.med.gam, boxJ);
+}
+
 template <int TBY, int NT, int MINB, bool MU = false, bool AN = false, bool POLE = false>
 static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
-    using Gm = TbGeom<TBY, MU>;
+    using Gm = TbGeom<TBY, MU, POLE>;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
         cudaError_t e = cudaFuncSetAttribute(step2d_tb2<TBY, NT, MINB, MU, AN, POLE>,
@@ -841,15 +1071,19 @@ static cudaError_t launch_tb(const StepArgs &a, cudaStream_t s) {
         if (per_sm < 1) per_sm = 1;
     }
     CUtensorMap mIn, mCL, mDL;
+    PoleMaps<POLE> pm;
     memset(&mIn, 0, sizeof mIn);
     memset(&mCL, 0, sizeof mCL);
     memset(&mDL, 0, sizeof mDL);
-    const int use_tma = (make_maps<TBY>(a, &mIn, &mCL) && (!MU || make_dl_map<TBY>(a, &mDL))) ? 1 : 0;
+    memset(&pm, 0, sizeof pm);
+    bool tma = make_maps<TBY>(a, &mIn, &mCL) && (!MU || make_dl_map<TBY>(a, &mDL));
+    if constexpr (POLE) tma = tma && make_pole_maps<TBY>(a, &pm);
+    const int use_tma = tma ? 1 : 0;
     const int ntx = (a.g.nx + TBX - 1) / TBX, nty = (a.g.ny + TBY - 1) / TBY;
     const int ntiles = ntx * nty;
     const int blocks = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
     step2d_tb2<TBY, NT, MINB, MU, AN, POLE>
-        <<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, use_tma, ntx, nty, blocks / ntx, blocks % ntx);
+        <<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mDL, pm, use_tma, ntx, nty, blocks / ntx, blocks % ntx);
     return cudaGetLastError();
 }
 
@@ -1270,7 +1504,7 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
         default: break;
     }
-    if (a.med.wp2) return launch_tb<6, 256, 4, false, false, true>(a, s);  // a dispersive pole (any tensor)
+    if (a.med.wp2) return launch_tb<6, 256, 3, false, false, true>(a, s);  // a dispersive pole (any tensor)
     if (a.med.ar != 1.f || a.med.amu != 1.f) return launch_tb<6, 256, 5, false, true>(a, s);  // anisotropic
     if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)

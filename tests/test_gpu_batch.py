@@ -129,3 +129,51 @@ def test_every_batch_variant_is_bitwise_identical(lbem):
     lbem.lbem_batch_destroy(b)
     for s in ss:
         s.close()
+
+
+def test_two_step_batch_ragged_members_odd_steps(lbem):
+    """The two-steps-per-launch batch kernels (every tile shape) on tiny and odd-width members (1x1, 3x5, widths
+    not a multiple of 4, one tile wide, a width just past one tile), sources and receivers at the corners, odd
+    step counts split over two calls (a single step first, then pairs): bit-identical to each member stepped
+    alone, and no write outside a member's arrays."""
+    import torch
+
+    shapes = [(1, 1), (3, 5), (17, 45), (9, 130), (64, 64), (70, 97), (41, 129), (33, 257)]
+    probs = []
+    for k, shp in enumerate(shapes):
+        eps, _ = W.random_medium(shp, 300 + k)
+        p = W.Problem("rb", 2, shp, eps, None, 40)
+        p.E0, p.B0 = W.random_fields(shp, 400 + k, 0.2)
+        n = int(np.prod(shp))
+        p.src_site = np.array([0, n - 1], np.int64)
+        p.src_comp = np.array([2, 2], np.int32)
+        p.src_amp = np.ones((2, 40))
+        p.rec_site = np.array([0, n // 2, n - 1], np.int64)
+        p.rec_comp = np.array([2, 3, 4], np.int32)
+        probs.append(p)
+    st = torch.cuda.Stream()
+    ref = []
+    for p in probs:
+        s = lbem.Solver(p.shape, stream=st.cuda_stream)
+        s.set_problem(p)
+        lbem.lbem_set_temporal_blocking(s.h, 1, -1)
+        s.step(37)
+        ref.append(_read(s, p))
+        s.close()
+    ss = _solvers(probs, st.cuda_stream)
+    b = lbem.lbem_batch_create([s.h for s in ss], st.cuda_stream)
+    nv = lbem.lbem_batch_get_variant(b)[1]
+    for v in range(nv - 3, nv):  # the two-step tile shapes are the last three variants
+        for s, p in zip(ss, probs):
+            s.set_problem(p)
+        lbem.lbem_batch_set_variant(b, v)
+        lbem.lbem_batch_step(b, 13)
+        lbem.lbem_batch_step(b, 24)
+        for s, p, r in zip(ss, probs, ref):
+            assert lbem.lbem_time(s.h) == 37
+            lbem.lbem_check_guards(s.h)
+            for a, q in zip(_read(s, p), r):
+                np.testing.assert_array_equal(a, q, err_msg=f"variant {v}, {p.shape}")
+    lbem.lbem_batch_destroy(b)
+    for s in ss:
+        s.close()

@@ -153,7 +153,8 @@ def test_192_cubed_full_size_elementwise_3_steps(lbem):
 def test_reduced_storage_short_run_tracks_oracle(lbem, storage, steps_per_pass):
     """Half-precision storage on the homogeneous 128^2 pulse: error within the format's rounding bound
     2 u sqrt(N/3) (u = unit roundoff; 2^-11 FP16, 2^-8 BF16, 2 * 2^-16 block int16), with single steps and
-    with two steps per launch (one rounding per two steps)."""
+    with two steps per launch (one rounding per two steps).  A regression check of each codec against the
+    rounding-walk model; the benchmark spec's 1e-3 bar is asserted on config 2's 5000-step crop below."""
     p = W.homogeneous_pulse(128, 6.0, 500)
     E, B, _ = gpu_run(p, storage, steps_per_pass=steps_per_pass)
     oE, oB, _, _, _ = oracle_run(p)
@@ -270,30 +271,57 @@ def test_homogeneous_invariant_conserved_full_size(lbem):
     assert abs(d1[1] - d0[1]) < 1e-5 * d0[1], (d0, d1)
 
 
-def test_storage_forms_5000_steps_on_512_crop_of_4096_medium(lbem):
-    """The 4096^2 (seed 2) medium's central 512^2 crop run in FP64 (oracle) and on the GPU in every storage
-    form for 5000 steps, Ricker source at the crop centre.  FP32 must meet 1e-4; each 16-bit form must stay
-    within its rounding-walk bound 2 u sqrt(N/3); block-int16 must meet the reduced-precision bar 1e-3."""
+def _crop512_problem():
     big = W.heterogeneous_2d(4096, seed=2, nsteps=5000)
     c0 = 2048 - 256
     eps = big.eps_r[c0:c0 + 512, c0:c0 + 512].copy()
     n_idx = np.sqrt(eps)
     recs = W.circle_receivers((256, 256), 128, 64)
-    p = W.point_source_problem(2, (512, 512), n_idx, 5000, (256, 256), 64, recs, name="crop512")
-    oE, oB, otr, _, _ = oracle_run(p)
-    u = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8, "i16b": 2.0 ** -15}
-    report = {}
-    for st in ("f32", "f16", "bf16", "i16b"):
-        for spp in (1, 2):
-            E, B, tr = gpu_run(p, st, steps_per_pass=spp)
-            report[(st, spp)] = (rel(E, oE), rel(B, oB), rel(tr, otr))
-    print("512^2 crop x 5000 rel-L2 (E, B, traces) by (storage, steps per launch):",
-          {f"{k[0]}/{k[1]}": tuple(f"{x:.2e}" for x in v) for k, v in report.items()})
+    return W.point_source_problem(2, (512, 512), n_idx, 5000, (256, 256), 64, recs, name="crop512")
+
+
+_CROP_REPORT = {}
+
+
+def _crop512_report():
+    """rel-L2 (E, B, traces) against the FP64 oracle of the 512^2 crop x 5000 steps, per (storage, steps per
+    launch); computed once per session."""
+    if not _CROP_REPORT:
+        p = _crop512_problem()
+        oE, oB, otr, _, _ = oracle_run(p)
+        for st in ("f32", "f16", "bf16", "i16b"):
+            for spp in (1, 2):
+                E, B, tr = gpu_run(p, st, steps_per_pass=spp)
+                _CROP_REPORT[(st, spp)] = (rel(E, oE), rel(B, oB), rel(tr, otr))
+        print("512^2 crop x 5000 rel-L2 (E, B, traces) by (storage, steps per launch):",
+              {f"{k[0]}/{k[1]}": tuple(f"{x:.2e}" for x in v) for k, v in _CROP_REPORT.items()})
+    return _CROP_REPORT
+
+
+def test_storage_forms_5000_steps_on_512_crop_of_4096_medium(lbem):
+    """The 4096^2 (seed 2) medium's central 512^2 crop run in FP64 (oracle) and on the GPU in every storage form for
+    5000 steps, Ricker source at the crop centre (config 2, reading R11).  FP32 must meet the benchmark spec's 1e-4 and
+    block-int16 its reduced-precision bar 1e-3, on E, B and the receiver traces, in single- and two-step launches.
+    FP16 and BF16 miss 1e-3 (see the strict xfail below); here they are only held to the rounding-walk model of a
+    neutral scheme, 2 u sqrt(N/3), which catches a broken codec."""
+    report = _crop512_report()
+    u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
     for spp in (1, 2):
         assert max(report[("f32", spp)]) < 1e-4, report[("f32", spp)]
+        assert max(report[("i16b", spp)]) < 1e-3, report[("i16b", spp)]
         for st in ("f16", "bf16"):
             assert max(report[(st, spp)]) < 2 * u[st] * np.sqrt(5000 / 3), (st, spp, report[(st, spp)])
-        assert max(report[("i16b", spp)][:2]) < 1e-3, report[("i16b", spp)]
+
+
+@pytest.mark.xfail(strict=True, reason="known miss: FP16 and BF16 storage round every stored value to 11 / 8 "
+                   "significant bits and the neutral scheme lets those errors random-walk (~u sqrt(N)); at 5000 steps "
+                   "they reach 7.5e-3 (FP16) and 6.0e-2 (BF16) against the 1e-3 bar")
+@pytest.mark.parametrize("st", ["f16", "bf16"])
+def test_f16_bf16_storage_meet_reduced_precision_bar(lbem, st):
+    """The benchmark spec's reduced-precision bar, 1e-3 relative L2 on E and B after 5000 steps, asserted as it stands
+    for FP16 and BF16 storage: a documented miss, reported as xfail (an unexpected pass fails the suite)."""
+    report = _crop512_report()
+    assert max(max(report[(st, 1)][:2]), max(report[(st, 2)][:2])) <= 1e-3, report
 
 
 def test_mu_heterogeneous_256_1000_steps(lbem):
