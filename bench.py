@@ -134,7 +134,7 @@ def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
         s.set_problem(q)
         ss.append(s)
     b = lbem.lbem_batch_create([s.h for s in ss], stream.cuda_stream)
-    v = lbem.lbem_batch_autotune(b, 20) if args.autotune else lbem.lbem_batch_get_variant(b)[0]
+    v = lbem.lbem_batch_autotune(b, 200) if args.autotune else lbem.lbem_batch_get_variant(b)[0]
     if args.variant is not None:
         lbem.lbem_batch_set_variant(b, args.variant)
         v = args.variant
@@ -288,7 +288,9 @@ def other_forms(lbem, torch, p, peak, stream):
         s.set_problem(q)
         ss.append(s)
     b = lbem.lbem_batch_create([s.h for s in ss], stream.cuda_stream)
-    v = lbem.lbem_batch_autotune(b, 20)
+    # trials of 200 steps: a two-step variant packs and unpacks the members once per call, which a short trial
+    # would not amortise
+    v = lbem.lbem_batch_autotune(b, 200)
     lbem.lbem_batch_step(b, 2000)
     for s in ss:
         lbem.lbem_set_fields(s.h)

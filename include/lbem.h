@@ -382,13 +382,18 @@ lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);
  * the calls above on them); all members must be at the same time t when
  * stepped.  The batch does not own the members.  Launch shapes (variants):
  * 0..8 advance one step per launch (rows of warps, one site per thread, a
- * persistent pipeline, lanes linear over each member's padded plane); 9, 10, 11
+ * persistent pipeline, lanes linear over each member's padded plane); 9 .. 13
  * advance two steps per launch through shared-memory tiles of 128 x 6 sites (5
- * or 4 blocks per SM) and 128 x 8 sites (an odd step count takes one single
- * step first).  Every variant gives the same bits as each member stepped
- * alone. */
+ * or 4 blocks per SM), 128 x 8, 128 x 10 and 128 x 12 sites, over a packed copy
+ * of the members' states with periodic halos that the batch keeps (filled at
+ * the start of a call, written back into the members' buffers at its end; an
+ * odd step count takes one single step first).  Every variant gives the same
+ * bits as each member stepped alone. */
 lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out);
 lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps);
+/* Time every variant over trial_steps steps (members' states saved and restored) and keep the fastest; *best (may
+ * be NULL) receives it.  The two-step variants pack and unpack the members once per call, so trials of a few hundred
+ * steps rank them as the long runs they are meant for. */
 lbem_status lbem_batch_autotune(lbem_batch_t *b, int trial_steps, int *best);
 /* Choose the batched kernel's launch shape directly (0 <= variant < *nvariants of lbem_batch_get_variant). */
 lbem_status lbem_batch_set_variant(lbem_batch_t *b, int variant);

@@ -407,11 +407,28 @@ struct lbem_batch {
     // two steps per launch: per member its step arguments for both buffer parities, a tile -> member table and
     // each member's first tile (tile rows tb_rows)
     lbk::StepArgs *d_args = nullptr;
-    int *d_tmap = nullptr;
-    long long *d_tstart = nullptr;
-    size_t tmap_cap = 0;
+    lbk::BatchTile *d_tiles = nullptr;
+    size_t tiles_cap = 0;
     long long ntiles = 0;
     int tb_rows = 0;
+    // the two-step kernels' packed states with halos: two population buffers and c_L^2, [rows][W] per plane, member m
+    // from packed row r0[m] (d_r0, n + 1 entries)
+    float *d_pack = nullptr;  // 11 planes: buffer 0 (5), buffer 1 (5), c_L^2 (1)
+    size_t pack_bytes = 0;
+    int *d_r0 = nullptr;
+    int pack_W = 0;
+    long long pack_rows = 0;
+    lbk::BatchPacked packed() const {
+        lbk::BatchPacked k;
+        const long long pl = pack_rows * pack_W;
+        k.buf[0] = d_pack;
+        k.buf[1] = d_pack + 5 * pl;
+        k.cl = d_pack + 10 * pl;
+        k.r0 = d_r0;
+        k.W = pack_W;
+        k.plane = pl;
+        return k;
+    }
     int variant = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0, graph_variant = -1;
@@ -426,42 +443,94 @@ using namespace lbk;
 // Variants: R = 1, 2, 4 rows per warp; 0 one site per thread; -1 persistent register pipeline; -5, -6 R = 1
 // capped for 5 / 6 blocks per SM; -7, -8 linear over each member's padded plane (uncapped / 5 blocks per SM);
 // 100 + k: two steps per launch through shared-memory tiles, tile shape k (launch_batch_tb2).
-static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8, 100, 101, 102};
+static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8, 100, 101, 102, 103, 104};
 static const int kBatchVariants = (int)(sizeof(kRowsB) / sizeof(kRowsB[0]));
 static const int kLinVariant = 7;  // the single-step kernel that takes the odd step of a two-step variant
 static bool two_step(int variant) { return kRowsB[variant] >= 100; }
+
+static void drop_batch_graph(lbem_batch_t *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = 0;
+    b->graph_variant = -1;
+}
 
 // Tile tables of the two-step kernel (tiles of 128 x rows sites) and every member's step arguments for both
 // buffer parities (args[2 k]: state in buffer a, written to b; args[2 k + 1]: the reverse).
 static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
     std::vector<StepArgs> args(2 * (size_t)b->n);
     std::vector<long long> ts(b->n + 1, 0);
+    std::vector<int> r0(b->n + 1, 0);
+    int maxw = 0;
     for (int k = 0; k < b->n; k++) {
         lbem_t *h = b->members[k];
         args[2 * k] = step_args(h, h->cur);
         args[2 * k + 1] = step_args(h, h->cur ^ 1);
         const long long ntx = (h->grid.nx + 127) / 128, nty = (h->grid.ny + rows - 1) / rows;
         ts[k + 1] = ts[k] + ntx * nty;
+        if ((long long)r0[k] + h->grid.ny + 4 > 0x7fffffffLL)
+            return fail(LBEM_ERR_ARG, "lbem_batch: members too tall for the packed layout");
+        r0[k + 1] = r0[k] + h->grid.ny + 4;  // the member's rows and two halo rows on either side
+        maxw = std::max(maxw, (int)(ntx * 128));
     }
+    // packed layout: every tile window (member columns x0 - 4 .. x0 + 131) inside a row
+    const int W = round_up(maxw + 8, 32);
+    const long long prows = r0[b->n];
+    const size_t need = sizeof(float) * 11 * (size_t)prows * W;
+    if (b->pack_bytes < need) {
+        drop_batch_graph(b);  // a captured graph may refer to the old buffers
+        cudaFree(b->d_pack);
+        b->d_pack = nullptr;
+        b->pack_bytes = 0;
+        if (cudaMalloc((void **)&b->d_pack, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBEM_ERR_NOMEM, "lbem_batch: no room for the packed states");
+        }
+        b->pack_bytes = need;
+        LBEM_CUDA(cudaMemsetAsync(b->d_pack, 0, need, b->stream));
+    }
+    b->pack_W = W;
+    b->pack_rows = prows;
+    LBEM_CUDA(cudaMemcpyAsync(b->d_r0, r0.data(), sizeof(int) * (b->n + 1), cudaMemcpyHostToDevice, b->stream));
     const long long total = ts[b->n];
-    std::vector<int> map((size_t)total);
-    for (int k = 0; k < b->n; k++)
-        for (long long u = ts[k]; u < ts[k + 1]; u++) map[(size_t)u] = k;
-    if (b->tmap_cap < map.size()) {
-        cudaFree(b->d_tmap);
-        b->d_tmap = nullptr;
-        b->tmap_cap = 0;
-        if (cudaMalloc((void **)&b->d_tmap, sizeof(int) * map.size()) != cudaSuccess) {
+    // tile descriptors: member, origin, packed row of the window's first c_L^2 row, size, and whether the window's
+    // rows (periodic) hold a source or receiver
+    std::vector<BatchTile> tl((size_t)total);
+    for (int k = 0; k < b->n; k++) {
+        lbem_t *h = b->members[k];
+        const int nx = h->grid.nx, ny = h->grid.ny, ntx = (nx + 127) / 128;
+        std::vector<char> evrow(ny, 0);
+        for (long long site : h->src_site) evrow[(site / nx) % ny] = 1;
+        for (long long site : h->rec_site) evrow[(site / nx) % ny] = 1;
+        for (long long u = ts[k]; u < ts[k + 1]; u++) {
+            const int local = (int)(u - ts[k]), ty = local / ntx, tx = local - ty * ntx;
+            BatchTile d;
+            d.m = k;
+            d.x0 = tx * 128;
+            d.y0 = ty * rows;
+            d.py = r0[k] + 2 + d.y0 - 1;
+            d.nx = nx;
+            d.ny = ny;
+            d.ev = 0;
+            for (int r = -1; r <= rows && !d.ev; r++) d.ev = evrow[(((d.y0 + r) % ny) + ny) % ny];
+            d.pad = 0;
+            tl[(size_t)(u)] = d;
+        }
+    }
+    if (b->tiles_cap < tl.size()) {
+        cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        b->tiles_cap = 0;
+        if (cudaMalloc((void **)&b->d_tiles, sizeof(BatchTile) * tl.size()) != cudaSuccess) {
             cudaGetLastError();
             return fail(LBEM_ERR_NOMEM, "lbem_batch: no room for the tile table");
         }
-        b->tmap_cap = map.size();
+        b->tiles_cap = tl.size();
     }
     LBEM_CUDA(cudaMemcpyAsync(b->d_args, args.data(), sizeof(StepArgs) * args.size(), cudaMemcpyHostToDevice,
                               b->stream));
-    LBEM_CUDA(cudaMemcpyAsync(b->d_tstart, ts.data(), sizeof(long long) * (b->n + 1), cudaMemcpyHostToDevice,
+    LBEM_CUDA(cudaMemcpyAsync(b->d_tiles, tl.data(), sizeof(BatchTile) * tl.size(), cudaMemcpyHostToDevice,
                               b->stream));
-    LBEM_CUDA(cudaMemcpyAsync(b->d_tmap, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, b->stream));
     LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vectors go out of scope
     b->ntiles = total;
     b->tb_rows = rows;
@@ -563,27 +632,28 @@ static cudaError_t enqueue_batch(lbem_batch_t *b, int variant, int nsteps, int *
         *nlaunch = nsteps;
         return cudaSuccess;
     }
-    int n = 0, toff = 0;
+    // an odd step first, on the members' own buffers (the state then sits in their other buffer: parity 1)
+    int n = 0, toff = 0, par = 0;
     if (nsteps & 1) {
         cudaError_t e = launch_batch(b, kLinVariant, 0);
         if (e != cudaSuccess) return e;
-        n = toff = 1;
+        n = toff = par = 1;
     }
-    for (; toff + 2 <= nsteps; toff += 2, n++) {
-        cudaError_t e = launch_batch_tb2(b->d_args, b->d_tmap, b->d_tstart, b->ntiles, b->d_t0, toff, n & 1,
-                                         kRowsB[variant] - 100, b->stream);
+    if (nsteps >= 2) {  // pack, pairs of steps between the packed buffers, unpack into the members' state buffers
+        const BatchPacked pk = b->packed();
+        cudaError_t e = launch_batch_pack(b->d_args, par, b->d_r0, b->n, b->pack_rows, pk, 0, false, b->stream);
+        int j = 0;
+        for (; e == cudaSuccess && toff + 2 <= nsteps; toff += 2, j++, n++)
+            e = launch_batch_tb2(b->d_args, b->d_tiles, b->ntiles, b->d_t0, toff, j & 1, pk, b->pack_rows,
+                                 kRowsB[variant] - 100, b->stream);
+        if (e == cudaSuccess)
+            e = launch_batch_pack(b->d_args, par, b->d_r0, b->n, b->pack_rows, pk, j & 1, true, b->stream);
         if (e != cudaSuccess) return e;
     }
     *nlaunch = n;
     return cudaSuccess;
 }
 
-static void drop_batch_graph(lbem_batch_t *b) {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-    b->graph_steps = 0;
-    b->graph_variant = -1;
-}
 
 static lbem_status check_members(lbem_batch_t *b) {
     const long long t = b->members[0]->t;
@@ -622,7 +692,7 @@ lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_
     cudaError_t e = cudaMalloc((void **)&b->d_members, sizeof(Member) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_wstart, sizeof(long long) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_args, sizeof(StepArgs) * 2 * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tstart, sizeof(long long) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_r0, sizeof(int) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_t0, sizeof(long long));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -669,10 +739,11 @@ lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps) {
         int nl = 0;
         LBEM_CUDA(enqueue_batch(b, b->variant, nsteps, &nl));
     }
-    // launches per call: one per step, or one per pair of steps (plus a single step first when nsteps is odd)
-    const int nlaunch = two_step(b->variant) ? nsteps / 2 + (nsteps & 1) : nsteps;
+    // each single-step launch flips the members' buffers; the two-step variants unpack the pairs' result into the
+    // buffer they packed from, so only their odd first step flips
+    const int flips = two_step(b->variant) ? (nsteps & 1) : nsteps;
     for (lbem_t *h : b->members) {
-        h->cur ^= (nlaunch & 1);
+        h->cur ^= (flips & 1);
         h->t += nsteps;
     }
     // members' own streams must see the batch's work before their next call
@@ -757,8 +828,9 @@ void lbem_batch_destroy(lbem_batch_t *b) {
     cudaFree(b->d_map);
     cudaFree(b->d_t0);
     cudaFree(b->d_args);
-    cudaFree(b->d_tstart);
-    cudaFree(b->d_tmap);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_r0);
+    cudaFree(b->d_pack);
     delete b;
 }
 

@@ -544,11 +544,28 @@ cudaError_t tb_set_wait_limit(unsigned long long ns);  // limit of its bounded w
 int tb3_nshapes();
 cudaError_t launch_step_2d_tb3(const StepArgs &a, int shape, cudaStream_t s);
 cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s);
-// two steps per launch over a batch (tblock.cu): tiles of every member from a flattened table; args[2 m + par] are
-// member m's step arguments for the launch's buffer parity; tile rows of each shape: batch_tb2_rows
+// two steps per launch over a batch (tblock.cu): tiles of every member from a flattened table over the batch's packed
+// states with halos (BatchPacked); args[2 m + par] are member m's step arguments for buffer parity par of its own
+// buffers (the kernels use args[2 m] for the grid and events); tile rows of each shape: batch_tb2_rows
+struct BatchPacked {
+    float *buf[2];    // packed population buffers: [5][rows][W]
+    float *cl;        // packed c_L^2: [rows][W]
+    const int *r0;    // per member its first packed row; r0[n] = rows
+    int W;            // packed row width (floats, a multiple of 32)
+    long long plane;  // rows * W
+};
+// One tile of the batch's two-step kernel: member m, origin (x0, y0), the packed row py of member row y0 - 1 (the
+// window's first c_L^2 row), the member's size, and whether rows y0 - 1 .. y0 + TBY (periodic) hold a source or a
+// receiver.  Built on the host, one 32-byte load per tile.
+struct __align__(16) BatchTile {
+    int m, x0, y0, py;
+    int nx, ny, ev, pad;
+};
 int batch_tb2_rows(int shape);
-cudaError_t launch_batch_tb2(const StepArgs *args, const int *tmember, const long long *tstart, long long ntiles,
-                             const long long *t0p, int toff, int par, int shape, cudaStream_t s);
+cudaError_t launch_batch_tb2(const StepArgs *args, const BatchTile *tiles, long long ntiles, const long long *t0p,
+                             int toff, int par, const BatchPacked &pk, long long rows, int shape, cudaStream_t s);
+cudaError_t launch_batch_pack(const StepArgs *args, int par, const int *r0, int n, long long rows,
+                              const BatchPacked &pk, int which, bool unpack, cudaStream_t s);
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);

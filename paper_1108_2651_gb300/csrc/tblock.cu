@@ -474,7 +474,6 @@ __device__ __forceinline__ void tb_step_b(const StepArgs &a, const float *P, flo
     }
 }
 #undef TB_SET
-#undef TB_COMP
 
 // One persistent CTA per SM slot; CTA b takes tiles b, b + gridDim.x, ... (row-major over the tile grid).
 // The window of the next tile is loaded while step t+1 of the current one is computed.
@@ -554,95 +553,183 @@ __global__ void __launch_bounds__(NT, MINB)
     asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-// =====================================================================================================
-// Two steps per launch over a batch of independent media (FP32, uniform mu, periodic): one persistent launch takes
-// the tiles of every member in turn from a flattened tile table, with the same site updates as step2d_tb2, so each
-// member's result is bit-identical to its single steps.  A member's arguments are read from a device array
-// (args[2 m + par]: par = 0 reads the member's buffer a and writes b, 1 the reverse) and t from device memory, so
-// one captured graph serves every call.  The windows load by asynchronous copies (no per-member tensor maps):
-// every 4-column group inside the member is one 16-byte copy; only the groups that straddle or cross the periodic
-// wrap take element copies, and columns past x = nx + 1 are not loaded at all (no owned site's two-step pull
-// stencil reaches them; the lanes that compute there are discarded).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int TBY>
-__device__ __forceinline__ void tb_issue_b(const StepArgs &a, int x0, int y0, float *IN, float *CL, int nt) {
-    constexpr int R = TbGeom<TBY>::R, PL = TbGeom<TBY>::IN_PL, Q = TW / 4, NP = 6;
+static EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// =====================================================================================================
+// Two steps per launch over a batch of independent media (FP32, uniform mu, periodic).  The batch keeps its members'
+// states in a packed layout of its own: member m occupies packed rows r0[m] .. r0[m] + ny + 3 of planes W floats
+// wide, packed row r0[m] + 2 + y <-> member row y in [-2, ny + 1] and packed column x + 4 <-> member column x.  The
+// two rows and columns just outside the member hold its periodic images (a halo), so every tile's window (rows
+// y0 - 2 .. y0 + TBY + 1, columns x0 - 4 .. x0 + TBX + 3) is one TMA box without wrap, as for an interior tile of a
+// single grid.  A launch reads one packed buffer and writes the other; a tile writes each output site and its images
+// in the halo (sites within two of an edge), so the next launch finds the halo current.  Sources and receivers use
+// each member's own tables and coordinates, and the site updates are those of step2d_tb2, so every member's result
+// is bit-identical to its single steps.  The state is packed at the start of a call and unpacked into each member's
+// own buffer at its end (batch_pack_kernel).
+
+// Pack (unpack == 0) or unpack a batch's states, one block per packed row (its member found by bisection of r0):
+// pack writes rows -2 .. ny+1 and columns -2 .. nx+1 of the five planes and of c_L^2 from the member's buffer (the
+// periodic images outside it); unpack writes rows 0 .. ny-1, columns 0 .. nx-1 back.  The member's buffer is that
+// of args[2 m + par]'s input.
+__global__ void batch_pack_kernel(const StepArgs *__restrict__ args, int par, const int *__restrict__ r0, int n,
+                                  BatchPacked pk, int which, int unpack) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = n;  // r0[lo] <= b < r0[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(r0 + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    const StepArgs &a = args[2 * lo + par];
     const int nx = a.g.nx, ny = a.g.ny, pitch = a.g.pitch;
     const long long plane = a.g.plane;
-    const float *in = static_cast<const float *>(a.in.data);
-    const float *cl = a.med.cL2;
-    const int lane = threadIdx.x & 31;
-    // Window column c holds x = x0 - 4 + c.  Work items of one staged row: the 4-column groups q that lie wholly
-    // inside the member (qlo .. qhi, one 16-byte copy each), then single columns: the four wrapped ones left of
-    // x = 0 (first tile of a row) and the columns from the first group past qhi up to x = nx + 1 (wrapped where
-    // x >= nx).  The items are spread over the lanes, so an edge tile costs about what an inner one does.
-    const int qlo = x0 == 0 ? 1 : 0;
-    const int qhi = min(Q - 1, (nx - x0) >> 2);
-    const int ng = max(0, qhi - qlo + 1);
-    const int nl = x0 == 0 ? 4 : 0;
-    const int cr0 = 4 * (qhi + 1), cmax = min(TW - 1, nx + 5 - x0);
-    const int nitems = ng + nl + max(0, cmax - cr0 + 1);
-    for (int pr = threadIdx.x >> 5; pr < NP * R; pr += nt >> 5) {  // one warp per (plane, row) of the window
-        const int pl = pr / R, r = pr - pl * R;
-        const float *src;
-        float *dst;
-        if (pl < 5) {
-            src = in + pl * plane + (long long)wrapi(y0 - 1 + r + in_shift(pl), ny) * pitch;
-            dst = IN + pl * PL + r * TW;
+    const int y = b - __ldg(r0 + lo) - 2;
+    float *pb = pk.buf[which] + (long long)b * pk.W + 4;
+    float *mem = static_cast<float *>(a.in.data);
+    if (unpack) {
+        if (y < 0 || y >= ny) return;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x)
+            for (int p = 0; p < 5; p++) mem[p * plane + (long long)y * pitch + x] = pb[p * pk.plane + x];
+        return;
+    }
+    const long long yr = (long long)wrapi(y, ny) * pitch;
+    float *pc = pk.cl + (long long)b * pk.W + 4;
+    for (int x = (int)threadIdx.x - 2; x <= nx + 1; x += blockDim.x) {
+        const long long src = yr + wrapi(x, nx);
+        for (int p = 0; p < 5; p++) pb[p * pk.plane + x] = mem[p * plane + src];
+        pc[x] = a.med.cL2[src];
+    }
+}
+
+// Step t+1 on tile row y0 + warp, written to the packed output with the row's and the lane's halo images.
+template <int TBY, bool EV>
+__device__ __forceinline__ void tb_step_b_packed(const StepArgs &a, const float *P, float4 clb, int x0, int y0,
+                                                 long long t, float *out, long long pplane, int W, int prow0, int nx,
+                                                 int ny) {
+    const int lane = threadIdx.x & 31, oy = threadIdx.x >> 5;
+    const int gy = y0 + oy;
+    if (oy >= TBY || gy >= ny) return;
+    const int c = 4 + 4 * lane;
+    const Pull4 g(P, TbGeom<TBY>::P_PL, oy, c);
+    float4 o[5];
+    Pole4 pp;
+    if (EV && row_events(a, gy))
+        tb_update4m<true, false, Pull4>(a, g, clb, clb, clb, x0, gy, t + 1, true, o[0], o[1], o[2], o[3], o[4], &pp);
+    else
+        tb_update4m<false, false, Pull4>(a, g, clb, clb, clb, x0, gy, t + 1, true, o[0], o[1], o[2], o[3], o[4], &pp);
+    const int xs = x0 + 4 * lane;  // the lane's first site
+    if (xs >= nx) return;
+    auto row_at = [&](int yy) { return out + (long long)(prow0 + 2 + yy) * W + 4; };
+    auto store_row = [&](int yy) {
+        float *r = row_at(yy) + xs;
+        if (xs + 3 < nx) {
+#pragma unroll
+            for (int p = 0; p < 5; p++) __stcs(reinterpret_cast<float4 *>(r + p * pplane), o[p]);
         } else {
-            src = cl + (long long)wrapi(y0 - 1 + r, ny) * pitch;
-            dst = CL + r * TW;
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                if (xs + j < nx)
+#pragma unroll
+                    for (int p = 0; p < 5; p++) r[p * pplane + j] = TB_COMP(o[p], j);
         }
-        for (int it = lane; it < nitems; it += 32) {
-            if (it < ng) {
-                const int q = qlo + it;
-                tb_cpa16(dst + 4 * q, src + x0 - 4 + 4 * q);
-            } else {
-                int c = it - ng;
-                c = c < nl ? c : cr0 + (c - nl);
-                tb_cpa4(dst + c, src + wrapi(x0 - 4 + c, nx));
-            }
+    };
+    store_row(gy);
+    for (int yy = gy + ny; yy <= ny + 1; yy += ny) store_row(yy);  // images in the upper halo rows
+    for (int yy = gy - ny; yy >= -2; yy -= ny) store_row(yy);      // and in the lower ones
+    if (xs < 2 || xs + 3 >= nx - 2) {  // sites within two of the left or right edge: their column images
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int x = xs + j;
+            if (x >= nx) break;
+            for (int xi = x + nx; xi <= nx + 1; xi += nx)
+                for (int yy = gy - ((gy + 2) / ny) * ny; yy <= ny + 1; yy += ny)
+#pragma unroll
+                    for (int p = 0; p < 5; p++) row_at(yy)[p * pplane + xi] = TB_COMP(o[p], j);
+            for (int xi = x - nx; xi >= -2; xi -= nx)
+                for (int yy = gy - ((gy + 2) / ny) * ny; yy <= ny + 1; yy += ny)
+#pragma unroll
+                    for (int p = 0; p < 5; p++) row_at(yy)[p * pplane + xi] = TB_COMP(o[p], j);
         }
     }
 }
 
 template <int TBY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-    step2d_batch_tb2(const StepArgs *__restrict__ args, const int *__restrict__ tmember,
-                     const long long *__restrict__ tstart, long long ntiles, const long long *__restrict__ t0p, int toff,
-                     int par) {
+    step2d_batch_tb2(const StepArgs *__restrict__ args, const BatchTile *__restrict__ tiles, long long ntiles,
+                     const long long *__restrict__ t0p, int toff, int par, BatchPacked pk,
+                     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmCL) {
     static_assert(NT / 32 >= TBY, "one warp per row of step t+1");
     using Gm = TbGeom<TBY>;
     extern __shared__ __align__(1024) float sm[];
     float *IN = sm;
     float *CL = sm + Gm::IN_SZ;
     float *P = CL + Gm::CL_SZ;
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(sm + Gm::SZ);
+    const int tid = threadIdx.x;
     long long k = blockIdx.x;
     if (k >= ntiles) return;
+    if (smem_u32(sm) & 127) return;  // the launch checks alignment on the host side too (TMA destinations)
+    const CUtensorMap *tmIn = par ? &tmB : &tmA;
+    float *out = pk.buf[par ^ 1];
+    const unsigned mbar = smem_u32(mb);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned long long wait_limit = g_wait_limit_ns;
+    unsigned parity = 0;
     const long long t = *t0p + toff;
-    // tile k -> member, origin
-    auto locate = [&](long long kk, int &m, int &x0, int &y0) {
-        m = __ldg(tmember + kk);
-        const int local = (int)(kk - __ldg(tstart + m));  // tiles of one member fit in an int
-        const int ntx = (args[2 * m + par].g.nx + TBX - 1) / TBX;
-        const int ty = local / ntx;
-        x0 = (local - ty * ntx) * TBX;
-        y0 = ty * TBY;
+    // the window of a tile: five shifted planes and c_L^2 as TMA boxes (member column x0 - 4 <-> packed x0,
+    // member row y0 - 1 <-> packed row py)
+    auto load = [&](int x0, int py) {
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(Gm::TMA_BYTES)
+                         : "memory");
+#pragma unroll
+            for (int p = 0; p < 5; p++) tma_load_3d(IN + p * Gm::IN_PL, tmIn, x0, py + in_shift(p), p, mbar);
+            tma_load_2d(CL, &tmCL, x0, py, mbar);
+        }
     };
-    int m, x0, y0;
-    locate(k, m, x0, y0);
-    tb_issue_b<TBY>(args[2 * m + par], x0, y0, IN, CL, NT);
-    asm volatile("cp.async.commit_group;\n" ::);
-    bool events = tb_events<TBY>(args[2 * m + par], y0);
+    BatchTile cur = tiles[k];
+    load(cur.x0, cur.py);
     while (true) {
         const long long kn = k + gridDim.x;
         const bool has_next = kn < ntiles;
-        int mn = 0, xn = 0, yn = 0;
-        if (has_next) locate(kn, mn, xn, yn);
-        const bool events_next = has_next && tb_events<TBY>(args[2 * mn + par], yn);
-        const StepArgs &a = args[2 * m + par];
-        asm volatile("cp.async.wait_group 0;\n" ::);
-        __syncthreads();  // every thread's copies have landed, and step t+1 of the previous tile is done with P
+        BatchTile nxt;
+        if (has_next) nxt = tiles[kn];  // one 32-byte descriptor, in flight while this tile is computed
+        const StepArgs &a = args[2 * cur.m];
+        const int x0 = cur.x0, y0 = cur.y0;
+        const bool events = cur.ev;
+        const bool ok = mbar_wait(mbar, parity, wait_limit);
+        parity ^= 1u;
+        // the window has landed, and step t+1 of the previous tile is done with P
+        if (__syncthreads_or(!ok)) {  // a TMA load never completed: flag it, let it drain (bounded), stop
+            if (tid == 0) atomicExch(&g_tb_timeouts, 1);
+            mbar_wait(mbar, parity ^ 1u, kDrainNs);  // drain what is in flight
+            return;
+        }
         float4 clb = make_float4(0.f, 0.f, 0.f, 0.f), dbx = clb, dby = clb;
         Pole4 ph;
         if (events)
@@ -650,25 +737,46 @@ __global__ void __launch_bounds__(NT, MINB)
         else
             tb_step_a<TBY, NT, false>(a, IN, CL, P, x0, y0, t, clb, dbx, dby, ph);
         __syncthreads();
-        if (has_next) tb_issue_b<TBY>(args[2 * mn + par], xn, yn, IN, CL, NT);
-        asm volatile("cp.async.commit_group;\n" ::);
+        if (has_next) load(nxt.x0, nxt.py);  // the t stage and c_L^2 are free
+        const int prow0 = cur.py - y0 - 1;  // the member's first packed row
         if (events)
-            tb_step_b<TBY, true>(a, P, clb, dbx, dby, x0, y0, t);
+            tb_step_b_packed<TBY, true>(a, P, clb, x0, y0, t, out, pk.plane, pk.W, prow0, cur.nx, cur.ny);
         else
-            tb_step_b<TBY, false>(a, P, clb, dbx, dby, x0, y0, t);
+            tb_step_b_packed<TBY, false>(a, P, clb, x0, y0, t, out, pk.plane, pk.W, prow0, cur.nx, cur.ny);
         if (!has_next) break;
         k = kn;
-        m = mn;
-        x0 = xn;
-        y0 = yn;
-        events = events_next;
+        cur = nxt;
     }
-    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// Tensor maps of the packed buffers ([5][rows][W] floats, box: one plane of TBY+2 rows of TW) and of the packed
+// c_L^2; false if unavailable.
+template <int TBY>
+static bool make_batch_maps(const BatchPacked &pk, long long rows, CUtensorMap *mA, CUtensorMap *mB,
+                            CUtensorMap *mCL) {
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims3[3] = {(cuuint64_t)pk.W, (cuuint64_t)rows, 5};
+    const cuuint64_t str3[2] = {(cuuint64_t)pk.W * 4, (cuuint64_t)pk.plane * 4};
+    const cuuint32_t box3[3] = {(cuuint32_t)TW, (cuuint32_t)(TBY + 2), 1};
+    const cuuint32_t one[3] = {1, 1, 1};
+    for (int k = 0; k < 2; k++)
+        if (fn(k ? mB : mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pk.buf[k], dims3, str3, box3, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    const cuuint64_t dims2[2] = {(cuuint64_t)pk.W, (cuuint64_t)rows};
+    const cuuint64_t str2[1] = {(cuuint64_t)pk.W * 4};
+    const cuuint32_t box2[2] = {(cuuint32_t)TW, (cuuint32_t)(TBY + 2)};
+    return fn(mCL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(pk.cl), dims2, str2, box2, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int TBY, int NT, int MINB>
-static cudaError_t launch_batch_tb(const StepArgs *args, const int *tmember, const long long *tstart,
-                                   long long ntiles, const long long *t0p, int toff, int par, cudaStream_t s) {
+static cudaError_t launch_batch_tb(const StepArgs *args, const BatchTile *tiles, long long ntiles,
+                                   const long long *t0p, int toff, int par, const BatchPacked &pk, long long rows,
+                                   cudaStream_t s) {
     using Gm = TbGeom<TBY>;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
@@ -681,22 +789,33 @@ static cudaError_t launch_batch_tb(const StepArgs *args, const int *tmember, con
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_batch_tb2<TBY, NT, MINB>, NT, Gm::BYTES);
         if (per_sm < 1) per_sm = 1;
     }
+    CUtensorMap mA, mB, mCL;
+    if (!make_batch_maps<TBY>(pk, rows, &mA, &mB, &mCL)) return cudaErrorNotSupported;
     const long long slots = (long long)per_sm * nsm;
     const unsigned blocks = (unsigned)(ntiles < slots ? ntiles : slots);
     if (blocks == 0) return cudaSuccess;
-    step2d_batch_tb2<TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(args, tmember, tstart, ntiles, t0p, toff, par);
+    step2d_batch_tb2<TBY, NT, MINB><<<blocks, NT, Gm::BYTES, s>>>(args, tiles, ntiles, t0p, toff, par, pk, mA, mB, mCL);
     return cudaGetLastError();
 }
 
-int batch_tb2_rows(int shape) { return shape == 2 ? 8 : 6; }
+int batch_tb2_rows(int shape) { return shape == 2 ? 8 : shape == 3 ? 10 : shape == 4 ? 12 : 6; }
 
-cudaError_t launch_batch_tb2(const StepArgs *args, const int *tmember, const long long *tstart, long long ntiles,
-                             const long long *t0p, int toff, int par, int shape, cudaStream_t s) {
+cudaError_t launch_batch_tb2(const StepArgs *args, const BatchTile *tiles, long long ntiles, const long long *t0p,
+                             int toff, int par, const BatchPacked &pk, long long rows, int shape, cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_batch_tb<6, 256, 4>(args, tmember, tstart, ntiles, t0p, toff, par, s);
-        case 2: return launch_batch_tb<8, 320, 3>(args, tmember, tstart, ntiles, t0p, toff, par, s);
-        default: return launch_batch_tb<6, 256, 5>(args, tmember, tstart, ntiles, t0p, toff, par, s);
+        case 1: return launch_batch_tb<6, 256, 4>(args, tiles, ntiles, t0p, toff, par, pk, rows, s);
+        case 2: return launch_batch_tb<8, 320, 3>(args, tiles, ntiles, t0p, toff, par, pk, rows, s);
+        case 3: return launch_batch_tb<10, 384, 3>(args, tiles, ntiles, t0p, toff, par, pk, rows, s);
+        case 4: return launch_batch_tb<12, 448, 2>(args, tiles, ntiles, t0p, toff, par, pk, rows, s);
+        default: return launch_batch_tb<6, 256, 5>(args, tiles, ntiles, t0p, toff, par, pk, rows, s);
     }
+}
+
+cudaError_t launch_batch_pack(const StepArgs *args, int par, const int *r0, int n, long long rows,
+                              const BatchPacked &pk, int which, bool unpack, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    batch_pack_kernel<<<(unsigned)rows, 256, 0, s>>>(args, par, r0, n, pk, which, unpack ? 1 : 0);
+    return cudaGetLastError();
 }
 
 // =====================================================================================================
@@ -976,27 +1095,6 @@ __global__ void __launch_bounds__(NT, MINB)
         events = events_next;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
-}
-
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiled encode_fn() {
-    static EncodeTiled fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
 }
 
 // Tensor maps of the populations ([5][ny][pitch] floats, box: one plane of TBY+2 rows) and c_L^2

@@ -1,19 +1,25 @@
 """Spatial domain decomposition: slabs along the slowest axis (y in 2D, z in 3D).
 
 The scheme is local: per step a site reads its own collided populations and one population from each neighbour
-(pull streaming, Eq. 18).  Cut the grid into slabs of whole rows (2D) or planes (3D) and give every slab one ghost
-layer on either side.  The library steps each slab as its own periodic grid, which only ever disturbs the ghost
-layers.  What a real layer reads across a cut is the population moving across it: 2D g_2 (moving +y) from the
-layer below and g_4 (-y) from the layer above; 3D the three +z and the three -z components.  So after every
-single step each slab sends those populations of its first and last real layers to its neighbours, which write
-them into their ghost layers, and the slabs together evolve exactly as the whole grid (bit for bit: every site
-update has the same inputs).
+(pull streaming, Eq. 18).  Cut the grid into slabs of whole rows (2D) or planes (3D) and give every slab `halo`
+ghost layers on either side.  The library steps each slab as its own periodic grid, which disturbs only the ghost
+layers; after every `halo` steps each slab sends its neighbours what their ghost layers need, and the slabs together
+evolve exactly as the whole grid (bit for bit: every site update has the same inputs).
+
+* halo = 1 (2D and 3D, every medium): after each single step, the populations crossing a cut: 2D g_2 (moving +y)
+  of the last real layer up and g_4 (-y) of the first real layer down; 3D the three +z and the three -z components.
+* halo = 2 (2D; not with a dispersive pole, whose P would have to cross too): two steps per exchange, so the
+  library advances each slab two steps per launch (temporal blocking).  The inner ghost layer's first-step
+  collision now feeds a real layer, so it needs its own populations and sources: up go g_0..g_3 of the last real
+  layer and g_2 of the one below it, down g_0, g_1, g_3, g_4 of the first real layer and g_4 of the one above it:
+  5 rows of nx floats per cut and direction per two steps (against 2 for two single-step exchanges), in half the
+  messages.
 
 Communication is neighbour point-to-point (torch.distributed send / receive: NCCL between GPUs, gloo on the host)
-or, for slabs held by one process, direct copies.  Each slab steps one step per launch (the halo is one layer
-deep).  Any medium the library steps: a heterogeneous mu, a uniform anisotropic tensor, a dispersive pole (its
-J and P are site-local, so nothing of it crosses a cut), walls and absorbing layers on the axes along the cuts
-(x in 2D; x, y in 3D); the slab axis itself stays periodic.  Sources and receivers on real layers.
+or, for slabs held by one process, direct copies.  Any medium the library steps: a heterogeneous mu, a uniform
+anisotropic tensor, a dispersive pole (halo 1: its J and P are site-local, so nothing of it crosses a cut), walls and
+absorbing layers on the axes along the cuts (x in 2D; x, y in 3D); the slab axis itself stays periodic.  Receivers
+on real layers; sources on real layers and, with halo = 2, on ghost layers as well.
 """
 from dataclasses import replace
 
@@ -32,76 +38,118 @@ def slab_range(n, world, rank):
     return start, base + (1 if rank < extra else 0)
 
 
-def local_problem(p, rank, world):
-    """The slab of workloads.Problem p held by `rank`, with one ghost layer on either side (the neighbouring
-    layers of the whole grid, periodic).  Returns (local problem, start, count, indices of the global receivers
-    it holds)."""
+def local_problem(p, rank, world, halo=1):
+    """The slab of workloads.Problem p held by `rank`, with `halo` ghost layers on either side (the neighbouring
+    layers of the whole grid, periodic).  Returns (local problem, start, count, indices of the global receivers it
+    holds).  Receivers are kept on the real layers only; sources on the real layers and, for halo > 1, on the ghost
+    layers too (the inner ghost layer's collisions then feed real layers)."""
     D = len(p.shape)
     assert not p.bc[D - 1], "the slab axis must be periodic (walls only on the axes along the cuts)"
+    assert halo in (1, 2) and (halo == 1 or (D == 2 and p.wp2 is None)), \
+        "a two-layer halo is for 2D media without a dispersive pole"
     n = p.shape[0]
     start, count = slab_range(n, world, rank)
-    assert count >= 1, "more ranks than layers"
-    layers = np.arange(start - 1, start + count + 1) % n
+    assert count >= halo, "each slab needs at least `halo` real layers"
+    layers = np.arange(start - halo, start + count + halo) % n
     take = lambda a: None if a is None else np.take(a, layers, axis=0)
     site = lambda a: None if a is None else take(np.broadcast_to(a, p.shape))  # a per-site parameter or a scalar
-    shape = (count + 2,) + tuple(p.shape[1:])
+    shape = (count + 2 * halo,) + tuple(p.shape[1:])
     per_layer = int(np.prod(p.shape[1:]))
+    real = np.zeros(layers.size, bool)
+    real[halo:halo + count] = True
 
-    def localize(sites):
+    def localize(sites, ghosts):
+        """(index of the global entry, local flat site) for every local layer position holding the entry's layer."""
+        if sites.size == 0:
+            return np.zeros(0, np.int64), np.zeros(0, np.int64)
         layer = sites // per_layer
-        keep = (layer >= start) & (layer < start + count)
-        return keep, (layer - start + 1) * per_layer + sites % per_layer
+        hit = (layer[:, None] == layers[None, :]) & (real | ghosts)[None, :]
+        idx, pos = np.nonzero(hit)
+        return idx, pos * per_layer + sites[idx] % per_layer
 
     q = replace(p, shape=shape, eps_r=take(p.eps_r), mu_r=take(p.mu_r), E0=take(p.E0), B0=take(p.B0),
                 wp2=site(p.wp2), wr2=site(p.wr2), gamma=site(p.gamma))
-    keep, loc = localize(p.src_site)
-    q.src_site, q.src_comp, q.src_amp = loc[keep].astype(np.int64), p.src_comp[keep], p.src_amp[keep]
-    keep, loc = localize(p.rec_site)
-    q.rec_site, q.rec_comp = loc[keep].astype(np.int64), p.rec_comp[keep]
-    return q, start, count, np.nonzero(keep)[0]
+    idx, loc = localize(p.src_site, halo > 1)
+    q.src_site, q.src_comp, q.src_amp = loc.astype(np.int64), p.src_comp[idx], p.src_amp[idx]
+    idx, loc = localize(p.rec_site, False)
+    q.rec_site, q.rec_comp = loc.astype(np.int64), p.rec_comp[idx]
+    return q, start, count, idx
+
+
+# halo = 2 (2D): (layer offset, planes) sent upwards from the last real layers and downwards from the first ones,
+# as (offset from the slab's last real layer, planes) / (offset from its first real layer, planes)
+HALO2_UP = ((0, (0, 1, 2, 3)), (-1, (2,)))
+HALO2_DOWN = ((0, (0, 1, 3, 4)), (1, (4,)))
 
 
 class LbemSlab:
-    """One slab on the current GPU, stepped by the library (one step per launch)."""
+    """One slab on the current GPU, stepped by the library: one step per launch with halo = 1, two with halo = 2."""
 
-    def __init__(self, q, count, stream=None):
+    def __init__(self, q, count, stream=None, halo=1):
         import torch
 
         self.D = len(q.shape)
         self.count = count
+        self.halo = halo
         self.rows_per_layer = 1 if self.D == 2 else q.shape[1]
         self.nx = q.shape[-1]
         self.s = lbem.Solver(q.shape, stream=stream)
         self.s.set_problem(q)
-        lbem.lbem_set_temporal_blocking(self.s.h, 1, -1)
+        lbem.lbem_set_temporal_blocking(self.s.h, halo, -1)
         self.torch = torch
 
-    def step(self):
-        self.s.step(1)
+    @property
+    def steps_per_exchange(self):
+        return self.halo
+
+    def step(self, k=None):
+        """Advance k steps (default: the steps between two exchanges)."""
+        self.s.step(self.halo if k is None else k)
 
     def _rows(self, planes, layer, buf, to_state):
         r = self.rows_per_layer
         for k, pl in enumerate(planes):
             lbem.lbem_rows(self.s.h, pl, layer * r, r, buf[k], to_state)
 
+    def _spec(self, up):
+        """[(local layer, planes)] a neighbour needs from this slab's upper (up) or lower real layers."""
+        if self.halo == 1:
+            return [(self.count if up else 1, CROSSING[self.D][0 if up else 1])]
+        last, first = self.count + 1, 2
+        return [(last + d, pl) for d, pl in HALO2_UP] if up else [(first + d, pl) for d, pl in HALO2_DOWN]
+
+    def _ghost_spec(self, from_below):
+        """[(local ghost layer, planes)] in the order the neighbour below (from_below) or above sends them."""
+        if self.halo == 1:
+            return [(0 if from_below else self.count + 1, CROSSING[self.D][0 if from_below else 1])]
+        if from_below:  # the neighbour's last real layer lands in layer 1, the one below it in layer 0
+            return [(1 + d, pl) for d, pl in HALO2_UP]
+        return [(self.count + 2 + d, pl) for d, pl in HALO2_DOWN]
+
     def halo_out(self, up):
-        """Populations this slab sends across its upper (up) or lower cut: the crossing planes of its last or
-        first real layer."""
-        planes = CROSSING[self.D][0 if up else 1]
-        buf = self.torch.empty((len(planes), self.rows_per_layer * self.nx), dtype=self.torch.float32, device="cuda")
-        self._rows(planes, self.count if up else 1, buf, False)
+        """What this slab sends across its upper (up) or lower cut, as one [rows][layer sites] tensor."""
+        spec = self._spec(up)
+        nrow = sum(len(pl) for _, pl in spec)
+        buf = self.torch.empty((nrow, self.rows_per_layer * self.nx), dtype=self.torch.float32, device="cuda")
+        k = 0
+        for layer, planes in spec:
+            self._rows(planes, layer, buf[k:k + len(planes)], False)
+            k += len(planes)
         return buf
 
     def halo_in(self, from_below, buf):
-        """Write what the slab below (from_below) or above sent into the matching ghost layer."""
-        planes = CROSSING[self.D][0 if from_below else 1]
-        self._rows(planes, 0 if from_below else self.count + 1, buf.to(device="cuda", dtype=self.torch.float32),
-                   True)
+        """Write what the slab below (from_below) or above sent into the matching ghost layers."""
+        buf = buf.to(device="cuda", dtype=self.torch.float32)
+        k = 0
+        for layer, planes in self._ghost_spec(from_below):
+            self._rows(planes, layer, buf[k:k + len(planes)], True)
+            k += len(planes)
 
     def fields(self):
         """E, B of the real layers, each (3,) + slab shape without ghosts (torch, on the GPU)."""
         E, B = self.s.fields()
-        return E[:, 1:self.count + 1], B[:, 1:self.count + 1]
+        h = self.halo
+        return E[:, h:self.count + h], B[:, h:self.count + h]
 
     def traces(self, n):
         return self.s.traces(n)
@@ -144,18 +192,26 @@ def exchange_dist(slab, rank, world, host=False):
     slab.halo_in(False, from_above)
 
 
+def _chunks(nsteps, every):
+    """Steps between exchanges: `every` at a time, then the remainder."""
+    out = [every] * (nsteps // every)
+    if nsteps % every:
+        out.append(nsteps % every)
+    return out
+
+
 def step_local(slabs, nsteps):
-    """Advance slabs held by one process by nsteps steps."""
-    for _ in range(nsteps):
+    """Advance slabs held by one process by nsteps steps, exchanging halos every slab.steps_per_exchange steps."""
+    for k in _chunks(nsteps, getattr(slabs[0], "steps_per_exchange", 1)):
         for s in slabs:
-            s.step()
+            s.step(k)
         exchange_local(slabs)
 
 
 def step_dist(slab, rank, world, nsteps, host=False):
-    """Advance this rank's slab by nsteps steps, exchanging halos after each."""
-    for _ in range(nsteps):
-        slab.step()
+    """Advance this rank's slab by nsteps steps, exchanging halos every slab.steps_per_exchange steps."""
+    for k in _chunks(nsteps, getattr(slab, "steps_per_exchange", 1)):
+        slab.step(k)
         exchange_dist(slab, rank, world, host)
 
 

@@ -1,11 +1,12 @@
-"""Spatial domain decomposition (slabs along the slowest axis, one ghost layer, halo exchange after each step).
+"""Spatial domain decomposition (slabs along the slowest axis, one or two ghost layers, halo exchange after every
+one or two steps).
 
-On the host: world-size-2 and -3 gloo ranks, each stepping its slab with the FP64 oracle and exchanging the
-populations that cross the cuts through torch.distributed, must reproduce the single-domain oracle bit for bit
-(2D and 3D, heterogeneous eps and mu, sources and receivers on either slab; also a uniform anisotropic tensor, a
-dispersive pole, and walls with absorbing layers on the axes along the cuts).  On the GPU: two or three slabs
-stepped by the library in one process (halo copies between them) must reproduce the single-domain library run
-bit for bit, for the same media.
+On the host: world-size-2 and -3 gloo ranks, each stepping its slab with the FP64 oracle and exchanging halos
+through torch.distributed, must reproduce the single-domain oracle bit for bit (2D and 3D, heterogeneous eps and mu,
+sources and receivers on either slab; also a uniform anisotropic tensor, a dispersive pole, and walls with absorbing
+layers on the axes along the cuts), with a one-layer halo after each step and, in 2D, a two-layer halo after every
+two steps.  On the GPU: slabs stepped by the library in one process (halo copies between them), and two processes
+on one GPU exchanging through gloo, must reproduce the single-domain library run bit for bit.
 """
 import os
 import queue
@@ -57,17 +58,23 @@ def _problem(D, shape, seed, nsteps, kind="mu"):
 
 
 class OracleSlab:
-    """A slab stepped by the oracle (push streaming: after a step the ghost layers hold what crossed the cuts)."""
+    """A slab stepped by the oracle (push streaming).  Halo 1: after a step the ghost layers hold what crossed the
+    cuts, which the neighbours take.  Halo 2: after two steps the real layers are exact, and the neighbours send the
+    full state of their two layers next to each cut into the ghost layers.  In this push form the outer ghost
+    layer's own collision then feeds the real layers two steps later, so its grad ln mu must be the whole grid's:
+    pass it as dlnmu (the library's pull form exchanges post-collision values and never uses that collision)."""
 
-    def __init__(self, q, count):
+    def __init__(self, q, count, halo=1, dlnmu=None):
         import oracle as O
 
         f = lambda a: None if a is None else np.asarray(a, np.float32).astype(np.float64)
         self.O = O
-        self.D, self.count = q.D, count
+        self.D, self.count, self.halo = q.D, count, halo
         disp = None if q.wp2 is None else dict(wp2=f(q.wp2), wr2=f(q.wr2), gamma=f(q.gamma))
         self.m = O.medium(q.D, f(q.eps_r), f(q.mu_r), bc=q.bc, layer=q.layer, gamma_max=q.gamma_max,
                           dispersion=disp, aniso=q.aniso)
+        if dlnmu is not None:
+            self.m.dlnmu = np.ascontiguousarray(dlnmu)
         self.pole = None if disp is None else O.pole_state(self.m)
         self.g = O.init_state(self.m, f(q.E0), f(q.B0))
         src = q.sources()
@@ -77,24 +84,44 @@ class OracleSlab:
         self.t = 0
         self.tr = []
 
-    def step(self):
-        self.tr.append(self.O.run(self.m, self.g, 1, t0=self.t, sources=self.src, receivers=self.rec,
+    @property
+    def steps_per_exchange(self):
+        return self.halo
+
+    def step(self, k=1):
+        self.tr.append(self.O.run(self.m, self.g, k, t0=self.t, sources=self.src, receivers=self.rec,
                                   pole=self.pole))
-        self.t += 1
+        self.t += k
 
     def halo_out(self, up):
         import torch
 
+        if self.halo == 2:
+            rows = slice(self.count, self.count + 2) if up else slice(2, 4)
+            return torch.from_numpy(np.ascontiguousarray(self.g[rows]))
         layer, d = (self.count + 1, self.up) if up else (0, self.down)
         return torch.from_numpy(np.ascontiguousarray(self.g[layer, ..., d, :, :]))
 
     def halo_in(self, from_below, buf):
+        if self.halo == 2:
+            self.g[slice(0, 2) if from_below else slice(self.count + 2, self.count + 4)] = buf.numpy()
+            return
         layer, d = (1, self.up) if from_below else (self.count, self.down)
         self.g[layer, ..., d, :, :] = buf.numpy()
 
     def fields(self):
         E, B = self.O.fields(self.m, self.g, self.pole)
-        return E[1:self.count + 1], B[1:self.count + 1]
+        h = self.halo
+        return E[h:self.count + h], B[h:self.count + h]
+
+
+def _global_dlnmu(p, start, count, halo):
+    """grad ln mu of the whole grid's medium on a slab's layers (ghosts included)."""
+    import oracle as O
+
+    f = lambda a: None if a is None else np.asarray(a, np.float32).astype(np.float64)
+    m = O.medium(p.D, f(p.eps_r), f(p.mu_r), bc=p.bc, aniso=p.aniso)
+    return m.dlnmu[np.arange(start - halo, start + count + halo) % p.shape[0]]
 
 
 def _free_port():
@@ -105,7 +132,7 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, D, shape, nsteps, kind, q):
+def _rank_main(rank, world, port, D, shape, nsteps, kind, q, halo=1):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       OMP_NUM_THREADS="2")
     sys.path.insert(0, ROOT)
@@ -116,15 +143,15 @@ def _rank_main(rank, world, port, D, shape, nsteps, kind, q):
 
     dist.init_process_group("gloo", rank=rank, world_size=world)
     p = _problem(D, shape, 7 + D, nsteps, kind)
-    loc, start, count, recs = decomp.local_problem(p, rank, world)
-    slab = OracleSlab(loc, count)
+    loc, start, count, recs = decomp.local_problem(p, rank, world, halo)
+    slab = OracleSlab(loc, count, halo, dlnmu=_global_dlnmu(p, start, count, halo))
     decomp.step_dist(slab, rank, world, nsteps, host=True)
     E, B = slab.fields()
     tr = np.concatenate(slab.tr, axis=1) if slab.tr and slab.tr[0].size else np.zeros((0, nsteps))
     # FP64 all-reduce of the slabs' field energies (the diagnostics of a decomposed run)
     import torch
 
-    real = slice(1, count + 1)
+    real = slice(halo, count + halo)
     mu = None if loc.mu_r is None else loc.mu_r[real]
     en = torch.tensor([decomp.energy(np.moveaxis(E, -1, 0), np.moveaxis(B, -1, 0), loc.eps_r[real], mu, p.c_ref2)],
                       dtype=torch.float64)
@@ -170,6 +197,20 @@ def test_local_problem_layers_receivers_and_refusals():
         assert np.all(loc.src_site // per_layer >= 1) and np.all(loc.src_site // per_layer <= count)
         seen += recs.size
     assert seen == p.rec_site.size  # every receiver on exactly one slab
+    # two ghost layers: sources on the ghost layers too, receivers on the real ones only
+    p2 = _problem(2, (11, 13), 5, 4, "mu")
+    for rank in range(2):
+        loc, start, count, recs = decomp.local_problem(p2, rank, 2, halo=2)
+        layers = np.arange(start - 2, start + count + 2) % 11
+        assert loc.shape == (count + 4, 13)
+        np.testing.assert_array_equal(loc.eps_r, np.asarray(p2.eps_r)[layers])
+        g = p2.rec_site[recs]
+        np.testing.assert_array_equal(loc.rec_site, (g // per_layer - start + 2) * per_layer + g % per_layer)
+        held = {(int(s) // per_layer, int(s) % per_layer) for s in loc.src_site}
+        want = {(i, int(s) % per_layer) for s in p2.src_site for i in range(count + 4) if layers[i] == s // per_layer}
+        assert held == want
+    with pytest.raises(AssertionError):
+        decomp.local_problem(p, 0, 2, halo=2)  # a dispersive pole keeps the one-layer halo
     q = _problem(2, (11, 13), 5, 4, "walls")
     q.bc = (0, 1, 0)  # a wall across the slab axis (y)
     with pytest.raises(AssertionError):
@@ -200,21 +241,24 @@ def test_slabs_without_the_exchange_drift_from_the_whole_grid():
 
 
 @pytest.mark.timeout(600)
-@pytest.mark.parametrize("D,shape,kind,world", [(2, (11, 13), "mu", 2), (3, (7, 4, 5), "mu", 2),
-                                                (2, (11, 13), "aniso", 2), (2, (11, 13), "drude", 2),
-                                                (2, (11, 13), "walls", 2), (3, (7, 6, 5), "walls", 2),
-                                                (2, (11, 13), "mu", 3), (3, (8, 6, 5), "walls", 3)])
-def test_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind, world):
+@pytest.mark.parametrize("D,shape,kind,world,halo", [(2, (11, 13), "mu", 2, 1), (3, (7, 4, 5), "mu", 2, 1),
+                                                     (2, (11, 13), "aniso", 2, 1), (2, (11, 13), "drude", 2, 1),
+                                                     (2, (11, 13), "walls", 2, 1), (3, (7, 6, 5), "walls", 2, 1),
+                                                     (2, (11, 13), "mu", 3, 1), (3, (8, 6, 5), "walls", 3, 1),
+                                                     (2, (11, 13), "mu", 2, 2), (2, (13, 13), "mu", 3, 2),
+                                                     (2, (11, 13), "aniso", 2, 2), (2, (12, 13), "walls", 2, 2)])
+def test_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind, world, halo):
     import torch.multiprocessing as mp
 
     import oracle as O
     from gpu_helpers import oracle_run
 
-    nsteps = 12
+    nsteps = 12 if halo == 1 else 13  # a two-layer halo: six two-step exchanges and a single step
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, world, port, D, shape, nsteps, kind, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, D, shape, nsteps, kind, q, halo))
+             for r in range(world)]
     for pr in procs:
         pr.start()
     got = []
@@ -240,11 +284,15 @@ def test_gloo_ranks_with_oracle_slabs_equal_the_whole_grid(D, shape, kind, world
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("D,shape,world,kind", [(2, (40, 70), 2, "mu"), (2, (37, 130), 3, "mu"),
-                                                (3, (16, 6, 40), 2, "mu"), (2, (9, 33), 1, "mu"),
-                                                (2, (40, 70), 2, "aniso"), (2, (37, 130), 3, "drude"),
-                                                (2, (40, 70), 2, "walls"), (3, (16, 12, 40), 2, "walls")])
-def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world, kind):
+@pytest.mark.parametrize("D,shape,world,kind,halo", [(2, (40, 70), 2, "mu", 1), (2, (37, 130), 3, "mu", 1),
+                                                     (3, (16, 6, 40), 2, "mu", 1), (2, (9, 33), 1, "mu", 1),
+                                                     (2, (40, 70), 2, "aniso", 1), (2, (37, 130), 3, "drude", 1),
+                                                     (2, (40, 70), 2, "walls", 1), (3, (16, 12, 40), 2, "walls", 1),
+                                                     (2, (40, 70), 2, "mu", 2), (2, (37, 130), 3, "mu", 2),
+                                                     (2, (9, 33), 1, "mu", 2), (2, (64, 300), 4, "aniso", 2),
+                                                     (2, (40, 136), 2, "walls", 2)])
+def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world, kind, halo):
+    """halo 2: each slab steps two steps per launch (the tile kernel), exchanging every two steps."""
     import torch
 
     from gpu_helpers import gpu_run
@@ -255,8 +303,8 @@ def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world, ki
     ref = gpu_run(p, steps_per_pass=1)
     slabs, parts = [], []
     for r in range(world):
-        loc, start, count, recs = decomp.local_problem(p, r, world)
-        slabs.append(decomp.LbemSlab(loc, count))
+        loc, start, count, recs = decomp.local_problem(p, r, world, halo)
+        slabs.append(decomp.LbemSlab(loc, count, halo=halo))
         parts.append((start, count, recs, loc.rec_site.size))
     decomp.step_local(slabs, nsteps)
     torch.cuda.synchronize()
@@ -268,6 +316,68 @@ def test_gpu_slabs_in_one_process_equal_the_whole_grid(lbem, D, shape, world, ki
             np.testing.assert_array_equal(s.traces(nrec).cpu().double().numpy(), ref[2][recs])
         lbem.lbem_check_guards(s.s.h)
         s.close()
+
+
+def _gpu_rank_main(rank, world, port, shape, nsteps, kind, halo, q):
+    """One process of the two-process GPU test: its slab on GPU 0, halos through gloo (host memory)."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch
+    import torch.distributed as dist
+
+    from paper_1108_2651_gb300 import decomp, lbem
+
+    torch.cuda.set_device(0)
+    lbem.load()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = _problem(2, shape, 23, nsteps, kind)
+    loc, start, count, recs = decomp.local_problem(p, rank, world, halo)
+    slab = decomp.LbemSlab(loc, count, halo=halo)
+    decomp.step_dist(slab, rank, world, nsteps, host=True)
+    E, B = slab.fields()
+    tr = slab.traces(loc.rec_site.size)
+    torch.cuda.synchronize()
+    lbem.lbem_check_guards(slab.s.h)
+    out = (rank, start, count, E.cpu().double().numpy(), B.cpu().double().numpy(), recs, tr.cpu().double().numpy())
+    slab.close()
+    dist.destroy_process_group()
+    q.put(out)
+
+
+@pytest.mark.gpu
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("halo,kind", [(2, "mu"), (2, "aniso"), (1, "drude")])
+def test_gpu_slabs_in_two_processes_exchange_through_gloo(lbem, halo, kind):
+    """Two processes, each stepping its slab with the library on the same GPU, exchange halos through gloo (staged in
+    host memory; no kernel waits on the other process): bit-identical to the single-domain run."""
+    import torch.multiprocessing as mp
+
+    from gpu_helpers import gpu_run
+
+    shape, nsteps, world = (48, 200), 15, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gpu_rank_main, args=(r, world, port, shape, nsteps, kind, halo, q))
+             for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = []
+    while len(got) < world:
+        try:
+            got.append(q.get(timeout=2))
+        except queue.Empty:
+            assert all(pr.exitcode in (None, 0) for pr in procs), [pr.exitcode for pr in procs]
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    ref = gpu_run(_problem(2, shape, 23, nsteps, kind), steps_per_pass=1)
+    for rank, start, count, E, B, recs, tr in got:
+        np.testing.assert_array_equal(np.moveaxis(E, 0, -1), ref[0][start:start + count])
+        np.testing.assert_array_equal(np.moveaxis(B, 0, -1), ref[1][start:start + count])
+        if recs.size:
+            np.testing.assert_array_equal(tr, ref[2][recs])
 
 
 @pytest.mark.gpu

@@ -163,7 +163,7 @@ def test_two_step_batch_ragged_members_odd_steps(lbem):
     ss = _solvers(probs, st.cuda_stream)
     b = lbem.lbem_batch_create([s.h for s in ss], st.cuda_stream)
     nv = lbem.lbem_batch_get_variant(b)[1]
-    for v in range(nv - 3, nv):  # the two-step tile shapes are the last three variants
+    for v in range(9, nv):  # the two-step tile shapes (variants 9 ..)
         for s, p in zip(ss, probs):
             s.set_problem(p)
         lbem.lbem_batch_set_variant(b, v)
