@@ -16,8 +16,12 @@ per site per launch (5 populations read + 5 written in FP32, plus c_L^2),
 whether a launch advances one step or two.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a
-bounded sample of the same workload.  With torchrun (N > 1) every rank runs
-its own independent replica (no data-path collective: replicas only).
+bounded sample of the same workload.  With torchrun (N > 1) the path shards:
+the 4096^2 recipe is weak-scaled into a (4096 N) x 4096 grid, rank r holding
+the slab of rows [4096 r, 4096 (r+1)) (medium seed 2 + r, its own Ricker
+source and receivers), periodic across the ranks; each slab steps two steps
+per launch and exchanges a two-row halo with its neighbours over NCCL
+(send / receive of device buffers) after every launch.
 """
 import argparse
 import json
@@ -652,6 +656,129 @@ def oracle_leg(p, cases, gpu_out):
     return cpu, acc
 
 
+def slab_problem(rank, world, n=4096, nsteps=5000, halo=2):
+    """Rank `rank`'s slab of the weak-scaled workload: a (n world) x n grid whose rows [r n, (r + 1) n) hold the n^2
+    heterogeneous recipe with seed 2 + r (Ricker source at the slab centre, 64 receivers), periodic along y across
+    the ranks.  Returns the slab with `halo` ghost rows on either side (the neighbours' rows of the medium)."""
+    from dataclasses import replace
+
+    own = W.heterogeneous_2d(n, seed=2 + rank, nsteps=nsteps)
+    below = own if world == 1 else W.heterogeneous_2d(n, seed=2 + (rank - 1) % world, nsteps=nsteps)
+    above = own if world == 1 else W.heterogeneous_2d(n, seed=2 + (rank + 1) % world, nsteps=nsteps)
+    eps = np.concatenate([below.eps_r[-halo:], own.eps_r, above.eps_r[:halo]])
+    loc = replace(own, shape=(n + 2 * halo, n), eps_r=eps, name=f"het2d_{n}_slab{rank}of{world}")
+    loc.src_site = own.src_site + halo * n
+    loc.rec_site = own.rec_site + halo * n
+    return loc
+
+
+def slab_pass(lbem, torch, slab, eps_d, E_d, B_d, tr_d, u_d, rank, world, nsteps, host=False, ev=None,
+              stream=None):
+    """One pass of the decomposed path on this rank: medium upload, initial state, nsteps steps with a halo exchange
+    after every two-step launch, fields, traces and the FP64 field energy of the real rows all-reduced over the
+    ranks.  Returns the energy."""
+    from paper_1108_2651_gb300 import decomp
+
+    h = slab.s.h
+    lbem.lbem_set_medium(h, eps_d)
+    lbem.lbem_set_fields(h)
+    if ev is not None:
+        ev[0].record(stream)
+    decomp.step_dist(slab, rank, world, nsteps, host=host)
+    if ev is not None:
+        ev[1].record(stream)
+    lbem.lbem_fields(h, E_d, B_d)
+    lbem.lbem_traces(h, tr_d)
+    lbem.lbem_energy_flux(h, u_d, None)
+    nx, hl = slab.nx, slab.halo
+    en = u_d.view(-1, nx)[hl:hl + slab.count].double().sum().reshape(1)
+    if world > 1:
+        import torch.distributed as dist
+
+        if host:
+            en = en.cpu()
+        dist.all_reduce(en)
+    return float(en.item())
+
+
+def run_slabs_main(args, lbem, torch, rank, world, local, peak, peak_kind):
+    """The N-GPU run: this rank's slab of the weak-scaled grid (slab_problem), exchanging over NCCL."""
+    import torch.distributed as dist
+
+    from paper_1108_2651_gb300 import decomp
+
+    n, halo = 4096, 2
+    nsteps = args.lb_steps or 5000
+    loc = slab_problem(rank, world, n, nsteps, halo)
+    stream = torch.cuda.current_stream()
+    slab = decomp.LbemSlab(loc, n, halo=halo)
+    h = slab.s.h
+    nsite = slab.s.nsite
+    eps_d = torch.as_tensor(np.ascontiguousarray(loc.eps_r, np.float32).ravel(), device="cuda")
+    E_d = torch.empty(3 * nsite, dtype=torch.float32, device="cuda")
+    B_d = torch.empty_like(E_d)
+    u_d = torch.empty(nsite, dtype=torch.float32, device="cuda")
+    tr_d = torch.empty(loc.rec_site.size * nsteps, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        slab_pass(lbem, torch, slab, eps_d, E_d, B_d, tr_d, u_d, rank, world, nsteps)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            en = slab_pass(lbem, torch, slab, eps_d, E_d, B_d, tr_d, u_d, rank, world, nsteps, ev=evs[k],
+                           stream=stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = dist_max(start.elapsed_time(stop), world)
+    step_ms = dist_max(float(np.mean([a.elapsed_time(b) for a, b in evs])), world)
+    launches = nsteps // 2 + nsteps % 2
+    ms_per_launch = step_ms / launches  # the stepping region: launches and halo exchanges
+    ms_per_step = total_ms / args.steps
+    real = n * n
+    value = world * real * nsteps / (ms_per_step * 1e-3) / 1e6
+    achieved = 44 * nsite / (ms_per_launch * 1e-3) / 1e9
+    # end to end: the medium from pinned host memory, fields and traces back to it, every pass
+    eps_h = torch.from_numpy(np.ascontiguousarray(loc.eps_r, np.float32).ravel()).pin_memory()
+    E_h = torch.empty(3 * nsite, dtype=torch.float32).pin_memory()
+    B_h = torch.empty(3 * nsite, dtype=torch.float32).pin_memory()
+    tr_h = torch.empty(loc.rec_site.size * nsteps, dtype=torch.float32).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    slab_pass(lbem, torch, slab, eps_h, E_h, B_h, tr_h, u_d, rank, world, nsteps)
+    torch.cuda.synchronize()
+    dt = dist_max(time.perf_counter() - t0, world)
+    nb = lambda t: t.numel() * t.element_size()
+    slab.close()
+    if rank == 0:
+        per_exchange = 2 * 5 * n * 4  # bytes each rank sends per two-step launch (5 rows up, 5 down)
+        line = {"metric": "Mlups", "value": value, "unit": "Mlups", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"het2d_4096 weak-scaled: {n * world} x {n} grid, {world} slabs of {n} rows "
+                                       f"(medium seeds 2 .. {1 + world}, one Ricker source each)",
+                           "grid": [n * world, n], "lb_steps": nsteps, "storage": "f32",
+                           "parallelism": f"slabs{world} (two-row halo, NCCL send/recv after every two-step launch, "
+                                          f"{per_exchange} B per rank per exchange)",
+                           "l2": "inputs larger than L2, no flush"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "step2d_tb2 on each slab, two steps per launch (time per launch includes the "
+                                       "halo exchange)", "steps_per_launch": 2, "ms_per_launch": ms_per_launch,
+                             "algorithmic_bytes_per_site_per_launch": 44, "peak_kind": peak_kind},
+                "cpu_baseline": None,
+                "e2e": {"value": world * real * nsteps / dt / 1e6, "unit": "Mlups", "host_memory": "pinned",
+                        "h2d_bytes_per_step": int(nb(eps_h)), "d2h_bytes_per_step": int(nb(E_h) + nb(B_h) + nb(tr_h))},
+                "gpu_launches": args.steps * (launches * 5 + 7), "clocks": clk.summary(), "energy_last": en}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -754,6 +881,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     lbem.load()
+    if world > 1:  # the path shards: slabs of a weak-scaled grid with halo exchanges over NCCL
+        peak, peak_kind = measured_peak_gbs()
+        run_slabs_main(args, lbem, torch, rank, world, local, peak, peak_kind)
+        return
     if args.workload == "batch256":
         peak, peak_kind = measured_peak_gbs()
         run_batch_main(args, lbem, torch, torch.cuda.Stream(), peak, peak_kind)
@@ -941,7 +1072,7 @@ def main():
                 "config": {"workload": p.name, "grid": list(p.shape), "lb_steps": nsteps, "storage": args.storage,
                            "sources": int(p.src_site.size), "receivers": int(p.rec_site.size),
                            "l2": f"inputs larger than L2 (2 x {state_mb:.0f} MB distributions), no flush",
-                           "parallelism": f"replicas{world}"},
+                           "parallelism": "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "diagnostics_last": list(diag)}
         main_acc = acc.get(args.storage)

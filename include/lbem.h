@@ -345,6 +345,25 @@ lbem_status lbem_check_guards(lbem_t *h);
  * stream. */
 lbem_status lbem_rows(lbem_t *h, int plane, int row0, int nrows, float *buf, int to_state);
 
+/* Halo of a slab for spatial domain decomposition along y (2D, LBEM_F32 storage): a slab of ny rows is `halo`
+ * ghost rows, its real rows, and `halo` ghost rows, stepped as its own periodic grid; after every `halo` steps each
+ * slab sends its neighbours what their ghost rows need and writes what it receives into its own.  The state holds
+ * post-collision values laid out for pull streaming (a row pulls g_2 from the row below, g_4 from the row above).
+ *   halo = 1 (exchange after every single step): up goes g_2 of the last real row, down g_4 of the first
+ *            (1 row of nx floats each way).
+ *   halo = 2 (exchange after every two steps, so each slab steps two steps per launch): the inner ghost row's first
+ *            collision feeds a real row, so up go g_0, g_1, g_2, g_3 of the last real row and g_2 of the row below
+ *            it, down g_0, g_1, g_3, g_4 of the first real row and g_4 of the row above it (5 rows of nx floats
+ *            each way, in that order).
+ * lbem_halo_out writes what goes up into `up` and what goes down into `down`; lbem_halo_in writes the rows received
+ * from the slab below into the lower ghost rows and those from above into the upper ones.  Buffers are device memory,
+ * [rows][nx] floats; either may be NULL (that direction skipped).  One small kernel per direction on the handle's
+ * stream.  LBEM_ERR_ARG for other storage or dimensions, halo outside {1, 2}, fewer than 3 * halo rows, or host
+ * buffers.  A decomposed handle with halo = 1 must step one step per launch (lbem_set_temporal_blocking(h, 1, -1)).
+ * Not in the paper (its runs were single-domain). */
+lbem_status lbem_halo_out(lbem_t *h, int halo, float *up, float *down);
+lbem_status lbem_halo_in(lbem_t *h, int halo, const float *from_below, const float *from_above);
+
 /* ---------------------------------------------------------------- adjoint (not in the paper) */
 
 /* Forward run that records what the adjoint needs: advances nsteps steps from

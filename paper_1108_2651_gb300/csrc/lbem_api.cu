@@ -271,6 +271,57 @@ static lbem_status rebuild_events(lbem_t *h) {
 
 using namespace lbk;
 
+namespace lbk {
+
+// Rows of a slab's halo (spatial domain decomposition, 2D): (row, plane) pairs, in the order the buffer holds them.
+struct HaloRows {
+    int n;
+    int row[5], plane[5];
+};
+
+// Copy the listed rows (nx floats each) of the state to buf ([k][nx]) or back.
+__global__ void halo_rows_kernel(float *state, long long plane_stride, int pitch, int nx, HaloRows spec, float *buf,
+                                 int to_state) {
+    const int k = blockIdx.y;
+    float *r = state + spec.plane[k] * plane_stride + (long long)spec.row[k] * pitch;
+    float *b = buf + (long long)k * nx;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+        if (to_state)
+            r[x] = b[x];
+        else
+            b[x] = r[x];
+    }
+}
+
+// The rows a neighbour needs (out) or that a neighbour's rows fill (in), for a slab of ny rows with `halo` ghost rows
+// on either side (real rows halo .. ny - halo - 1); pull streaming: a row pulls g_2 from the row below, g_4 from
+// the row above.  halo 1: g_2 of the last real row up, g_4 of the first down.  halo 2 (two steps per exchange): the
+// inner ghost row's first collision feeds a real row, so it needs its own g_0, g_1, g_3 and the population it pulls
+// from the outer ghost row.
+static HaloRows halo_spec(int halo, int ny, bool upper, bool out) {
+    HaloRows s{};
+    auto add = [&](int row, int plane) {
+        s.row[s.n] = row;
+        s.plane[s.n] = plane;
+        s.n++;
+    };
+    if (halo == 1) {
+        if (out) add(upper ? ny - 2 : 1, upper ? 2 : 4);
+        else add(upper ? ny - 1 : 0, upper ? 4 : 2);
+        return s;
+    }
+    // out upper: last real row (ny - 3) planes 0-3, the row below it plane 2; in lower ghosts in the same order
+    // out lower: first real row (2) planes 0, 1, 3, 4, the row above it plane 4; in upper ghosts in the same order
+    const int r1 = out ? (upper ? ny - 3 : 2) : (upper ? ny - 2 : 1);
+    const int r2 = out ? (upper ? ny - 4 : 3) : (upper ? ny - 1 : 0);
+    const bool up_going = out ? upper : !upper;  // populations moving +y (sent up, received from below)
+    for (int p : {0, 1, up_going ? 2 : 3, up_going ? 3 : 4}) add(r1, p);
+    add(r2, up_going ? 2 : 4);
+    return s;
+}
+
+}  // namespace lbk
+
 extern "C" {
 
 const char *lbem_last_error(void) { return g_err.c_str(); }
@@ -876,6 +927,37 @@ lbem_status lbem_rows(lbem_t *h, int plane, int row0, int nrows, float *buf, int
     else LBEM_CUDA(cudaMemcpy2DAsync(buf, w, base, pitch, w, nrows, cudaMemcpyDefault, h->stream));
     if (!is_device_ptr(buf)) LBEM_CUDA(cudaStreamSynchronize(h->stream));
     return LBEM_OK;  // (a cached graph depends on the buffers and parameters, not on their contents)
+}
+
+static lbem_status halo_rows(lbem_t *h, int halo, float *up, float *down, int to_state, const char *who) {
+    const std::string name(who);
+    if (!h) return fail(LBEM_ERR_ARG, "null handle");
+    if (h->dim != 2 || h->storage != LBEM_F32) return fail(LBEM_ERR_ARG, name + ": 2D LBEM_F32 handles only");
+    if (halo != 1 && halo != 2) return fail(LBEM_ERR_ARG, name + ": halo must be 1 or 2");
+    if (h->grid.ny < 3 * halo) return fail(LBEM_ERR_ARG, name + ": a slab needs at least 3 * halo rows");
+    for (float *b : {up, down})
+        if (b && !is_device_ptr(b)) return fail(LBEM_ERR_ARG, name + ": buffers must be device memory");
+    const PopBuf &p = h->buf[h->cur];
+    float *state = static_cast<float *>(p.data);
+    const int nx = h->grid.nx;
+    for (int k = 0; k < 2; k++) {
+        float *b = k ? down : up;
+        if (!b) continue;
+        const HaloRows spec = halo_spec(halo, h->grid.ny, k == 0, !to_state);
+        const dim3 grid((unsigned)std::min((nx + 255) / 256, 64), (unsigned)spec.n);
+        halo_rows_kernel<<<grid, 256, 0, h->stream>>>(state, p.plane, p.pitch, nx, spec, b, to_state);
+        LBEM_CUDA(cudaGetLastError());
+    }
+    return LBEM_OK;
+}
+
+lbem_status lbem_halo_out(lbem_t *h, int halo, float *up, float *down) {
+    return halo_rows(h, halo, up, down, 0, "lbem_halo_out");
+}
+
+lbem_status lbem_halo_in(lbem_t *h, int halo, const float *from_below, const float *from_above) {
+    // the rows from below fill the lower ghost rows, those from above the upper ones
+    return halo_rows(h, halo, const_cast<float *>(from_above), const_cast<float *>(from_below), 1, "lbem_halo_in");
 }
 
 lbem_status lbem_check_guards(lbem_t *h) {

@@ -76,12 +76,6 @@ def local_problem(p, rank, world, halo=1):
     return q, start, count, idx
 
 
-# halo = 2 (2D): (layer offset, planes) sent upwards from the last real layers and downwards from the first ones,
-# as (offset from the slab's last real layer, planes) / (offset from its first real layer, planes)
-HALO2_UP = ((0, (0, 1, 2, 3)), (-1, (2,)))
-HALO2_DOWN = ((0, (0, 1, 3, 4)), (1, (4,)))
-
-
 class LbemSlab:
     """One slab on the current GPU, stepped by the library: one step per launch with halo = 1, two with halo = 2."""
 
@@ -111,39 +105,26 @@ class LbemSlab:
         for k, pl in enumerate(planes):
             lbem.lbem_rows(self.s.h, pl, layer * r, r, buf[k], to_state)
 
-    def _spec(self, up):
-        """[(local layer, planes)] a neighbour needs from this slab's upper (up) or lower real layers."""
-        if self.halo == 1:
-            return [(self.count if up else 1, CROSSING[self.D][0 if up else 1])]
-        last, first = self.count + 1, 2
-        return [(last + d, pl) for d, pl in HALO2_UP] if up else [(first + d, pl) for d, pl in HALO2_DOWN]
-
-    def _ghost_spec(self, from_below):
-        """[(local ghost layer, planes)] in the order the neighbour below (from_below) or above sends them."""
-        if self.halo == 1:
-            return [(0 if from_below else self.count + 1, CROSSING[self.D][0 if from_below else 1])]
-        if from_below:  # the neighbour's last real layer lands in layer 1, the one below it in layer 0
-            return [(1 + d, pl) for d, pl in HALO2_UP]
-        return [(self.count + 2 + d, pl) for d, pl in HALO2_DOWN]
-
     def halo_out(self, up):
-        """What this slab sends across its upper (up) or lower cut, as one [rows][layer sites] tensor."""
-        spec = self._spec(up)
-        nrow = sum(len(pl) for _, pl in spec)
-        buf = self.torch.empty((nrow, self.rows_per_layer * self.nx), dtype=self.torch.float32, device="cuda")
-        k = 0
-        for layer, planes in spec:
-            self._rows(planes, layer, buf[k:k + len(planes)], False)
-            k += len(planes)
+        """What this slab sends across its upper (up) or lower cut, as one [rows][layer sites] tensor: in 2D the
+        library's halo rows (lbem_halo_out: 1 row with halo 1, 5 with halo 2), in 3D the crossing planes."""
+        if self.D == 2:
+            buf = self.torch.empty((1 if self.halo == 1 else 5, self.nx), dtype=self.torch.float32, device="cuda")
+            lbem.lbem_halo_out(self.s.h, self.halo, buf if up else None, None if up else buf)
+            return buf
+        planes = CROSSING[self.D][0 if up else 1]
+        buf = self.torch.empty((len(planes), self.rows_per_layer * self.nx), dtype=self.torch.float32, device="cuda")
+        self._rows(planes, self.count if up else 1, buf, False)
         return buf
 
     def halo_in(self, from_below, buf):
         """Write what the slab below (from_below) or above sent into the matching ghost layers."""
-        buf = buf.to(device="cuda", dtype=self.torch.float32)
-        k = 0
-        for layer, planes in self._ghost_spec(from_below):
-            self._rows(planes, layer, buf[k:k + len(planes)], True)
-            k += len(planes)
+        buf = buf.to(device="cuda", dtype=self.torch.float32).contiguous()
+        if self.D == 2:
+            lbem.lbem_halo_in(self.s.h, self.halo, buf if from_below else None, None if from_below else buf)
+            return
+        planes = CROSSING[self.D][0 if from_below else 1]
+        self._rows(planes, 0 if from_below else self.count + 1, buf, True)
 
     def fields(self):
         """E, B of the real layers, each (3,) + slab shape without ghosts (torch, on the GPU)."""

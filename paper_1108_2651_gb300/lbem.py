@@ -63,6 +63,8 @@ _SIGS = {
     "lbem_energy_flux": [_VP, _VP, _VP],
     "lbem_diagnostics": [_VP, C.POINTER(_D)],
     "lbem_diagnostics_static": [_I, _I, _I, _I, _VP, _VP, _VP, _D, _VP, _VP],
+    "lbem_halo_out": [_VP, _I, _VP, _VP],
+    "lbem_halo_in": [_VP, _I, _VP, _VP],
     "lbem_save_state": [_VP, _VP],
     "lbem_check_guards": [_VP],
     "lbem_load_state": [_VP, _VP, _LL],
@@ -297,6 +299,14 @@ def lbem_diagnostics_static(dim, nx, ny, nz, state, eps_r, mu_r, c_ref2, out, st
 
 def lbem_check_guards(h):
     _check(load().lbem_check_guards(h))
+
+
+def lbem_halo_out(h, halo, up, down):
+    _check(load().lbem_halo_out(h, int(halo), _ptr(up, writable=True), _ptr(down, writable=True)))
+
+
+def lbem_halo_in(h, halo, from_below, from_above):
+    _check(load().lbem_halo_in(h, int(halo), _ptr(from_below), _ptr(from_above)))
 
 
 def lbem_save_state(h, dst):

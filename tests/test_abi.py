@@ -103,7 +103,8 @@ def test_null_handles_are_rejected(lib):
                      ("lbem_forward_record", [2, 1]), ("lbem_adjoint", [None, None, None]),
                      ("lbem_autotune", [1, None]), ("lbem_get_variant", [None, None]),
                      ("lbem_batch_autotune", [1, None]), ("lbem_batch_set_variant", [0]),
-                     ("lbem_batch_get_variant", [None, None])):
+                     ("lbem_batch_get_variant", [None, None]), ("lbem_halo_out", [1, None, None]),
+                     ("lbem_halo_in", [1, None, None])):
         assert getattr(lib, f)(None, *extra) == 1, f
         assert "null" in lbem.lbem_last_error() or "bad argument" in lbem.lbem_last_error(), f
 

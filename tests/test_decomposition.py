@@ -398,3 +398,112 @@ def test_rows_argument_errors(lbem):
         lbem.lbem_rows(h.h, 0, 0, 1, buf, False)
     assert e.value.status == 1
     h.close()
+
+
+@pytest.mark.gpu
+def test_halo_argument_errors(lbem):
+    """lbem_halo_out / lbem_halo_in refuse a halo outside {1, 2}, slabs shorter than 3 * halo rows, host buffers,
+    3D and 16-bit handles, before touching the state."""
+    import torch
+
+    s = lbem.Solver((8, 40))
+    s.set_problem(_problem(2, (8, 40), 5, 3))
+    buf = torch.zeros(5 * 40, dtype=torch.float32, device="cuda")
+    for halo in (0, 3):
+        with pytest.raises(lbem.LbemError) as e:
+            lbem.lbem_halo_out(s.h, halo, buf, None)
+        assert e.value.status == 1
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_halo_in(s.h, 2, np.zeros(5 * 40, np.float32), None)
+    assert e.value.status == 1 and "device memory" in str(e.value)
+    lbem.lbem_halo_out(s.h, 2, buf, None)  # 8 rows >= 6: fine
+    s.close()
+    short = lbem.Solver((5, 40))
+    with pytest.raises(lbem.LbemError) as e:
+        lbem.lbem_halo_out(short.h, 2, buf, None)
+    assert e.value.status == 1
+    short.close()
+    for shape, st in (((6, 8, 40), "f32"), ((8, 40), "bf16")):
+        h = lbem.Solver(shape, storage=st)
+        with pytest.raises(lbem.LbemError) as e:
+            lbem.lbem_halo_out(h.h, 1, buf, None)
+        assert e.value.status == 1
+        h.close()
+
+
+def _bench_rank_main(rank, world, port, n, nsteps, q):
+    """One process of the benchmark's decomposed path on GPU 0, halos through gloo."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    from paper_1108_2651_gb300 import decomp, lbem
+
+    torch.cuda.set_device(0)
+    lbem.load()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    loc = bench.slab_problem(rank, world, n, nsteps)
+    slab = decomp.LbemSlab(loc, n, halo=2)
+    nsite = slab.s.nsite
+    eps = torch.as_tensor(np.ascontiguousarray(loc.eps_r, np.float32).ravel(), device="cuda")
+    E = torch.empty(3 * nsite, dtype=torch.float32, device="cuda")
+    B = torch.empty_like(E)
+    u = torch.empty(nsite, dtype=torch.float32, device="cuda")
+    tr = torch.empty(loc.rec_site.size * nsteps, dtype=torch.float32, device="cuda")
+    for _ in range(2):  # a second pass from the re-initialised state gives the same result
+        en = bench.slab_pass(lbem, torch, slab, eps, E, B, tr, u, rank, world, nsteps, host=True)
+    torch.cuda.synchronize()
+    real = lambda a: a.view(3, n + 4, n)[:, 2:n + 2].cpu().double().numpy()
+    out = (rank, real(E), real(B), tr.view(loc.rec_site.size, nsteps).cpu().double().numpy(), en)
+    slab.close()
+    dist.destroy_process_group()
+    q.put(out)
+
+
+@pytest.mark.gpu
+@pytest.mark.timeout(600)
+def test_bench_decomposed_path_equals_the_whole_grid(lbem):
+    """The benchmark's N-GPU path (bench.slab_problem / slab_pass: a weak-scaled grid of slabs with their own media
+    and sources, a two-row halo after every two-step launch), run as two processes on one GPU exchanging through
+    gloo, equals the single-domain run of the whole stacked grid bit for bit, and its all-reduced energy is the
+    whole grid's."""
+    import torch.multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    from gpu_helpers import gpu_run
+    from paper_1108_2651_gb300 import workloads as W
+
+    n, nsteps, world = 128, 21, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_rank_main, args=(r, world, port, n, nsteps, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = []
+    while len(got) < world:
+        try:
+            got.append(q.get(timeout=2))
+        except queue.Empty:
+            assert all(pr.exitcode in (None, 0) for pr in procs), [pr.exitcode for pr in procs]
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    own = [W.heterogeneous_2d(n, seed=2 + r, nsteps=nsteps) for r in range(world)]
+    p = W.Problem("stacked", 2, (n * world, n), np.concatenate([o.eps_r for o in own]), None, nsteps)
+    p.src_site = np.concatenate([o.src_site + r * n * n for r, o in enumerate(own)]).astype(np.int64)
+    p.src_comp = np.concatenate([o.src_comp for o in own]).astype(np.int32)
+    p.src_amp = np.concatenate([o.src_amp for o in own])
+    p.rec_site = np.concatenate([o.rec_site + r * n * n for r, o in enumerate(own)]).astype(np.int64)
+    p.rec_comp = np.concatenate([o.rec_comp for o in own]).astype(np.int32)
+    E, B, tr = gpu_run(p)
+    nrec = own[0].rec_site.size
+    energy = (B ** 2).sum() + ((E ** 2).sum(axis=-1) * np.asarray(p.eps_r, np.float32).astype(np.float64) / 0.5).sum()
+    for rank, Es, Bs, trs, en in got:
+        rows = slice(rank * n, (rank + 1) * n)
+        np.testing.assert_array_equal(np.moveaxis(Es, 0, -1), E[rows])
+        np.testing.assert_array_equal(np.moveaxis(Bs, 0, -1), B[rows])
+        np.testing.assert_array_equal(trs, tr[rank * nrec:(rank + 1) * nrec])
+        assert abs(en / energy - 1) < 1e-6, (en, energy)

@@ -1,5 +1,6 @@
-"""The benchmark's multi-rank path on CPU (gloo, world size 2): replicas only, so the only cross-rank
-operations are the barrier and the max over ranks of the timed region, and only rank 0 prints."""
+"""The benchmark's multi-rank plumbing on CPU (gloo, world size 2): the barrier and the max over ranks of the timed
+region, and the reference arm under torchrun where only rank 0 prints.  The decomposed GPU pass itself (slabs with a
+halo exchange) is tested in test_decomposition.py."""
 import json
 import os
 import socket
