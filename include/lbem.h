@@ -215,7 +215,9 @@ lbem_status lbem_get_boundaries(const lbem_t *h, int kind[3], int *layer, double
  * bound), which lbem_set_medium also checks against a new medium.  A dispersive
  * handle with walls or a mu array steps one step per launch with the general kernel (walls, layers and an
  * anisotropic medium included); without them it steps in pairs (lbem_set_temporal_blocking), bit-identical to
- * single steps.  The handle holds a second P plane (every launch writes P to the plane paired with its output
+ * single steps.  The update J <- ((1 - gamma/2) J - wr2 P + wp2 E) / (1 + gamma/2) runs with three per-site
+ * coefficients formed once here in FP64 (no division per step).  The handle holds a second P plane (every launch
+ * writes P to the plane paired with its output
  * population buffer); lbem_set_fields starts the pole at rest (D = E); lbem_save_state
  * appends J and P (lbem_info's state_bytes counts them).  Batches and the
  * adjoint take non-dispersive handles only.  Synchronises the stream. */

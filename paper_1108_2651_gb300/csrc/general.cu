@@ -95,9 +95,9 @@ __global__ void __launch_bounds__(BLOCK, 4) step2d_gen(StepArgs a, Walls w, Gene
         // the pole, from the pre-collision field E = D/eps_inf - P; the collision below uses P(t)
         P4 = *reinterpret_cast<const float4 *>(q.P + o4);
         const float4 J4 = *reinterpret_cast<const float4 *>(q.J + o4);
-        const float4 wp4 = *reinterpret_cast<const float4 *>(q.wp2 + o4);
-        const float4 wr4 = *reinterpret_cast<const float4 *>(q.wr2 + o4);
-        const float4 gm4 = *reinterpret_cast<const float4 *>(q.gam + o4);
+        const float4 wp4 = *reinterpret_cast<const float4 *>(q.pc + o4);
+        const float4 wr4 = *reinterpret_cast<const float4 *>(q.pb + o4);
+        const float4 gm4 = *reinterpret_cast<const float4 *>(q.pa + o4);
         float4 Jn4, Pn4;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -195,6 +195,24 @@ __global__ void to_plane(Grid G, const float *src, float *dst) {
 
 cudaError_t launch_to_plane(const lbem_t *h, const float *src, float *dst, cudaStream_t s) {
     to_plane<<<blocks_for((long long)h->grid.pitch * h->grid.ny), 256, 0, s>>>(h->grid, src, dst);
+    return cudaGetLastError();
+}
+
+// pole_update's per-site coefficients from the pole's parameter planes, formed in FP64 and rounded once:
+// pa = (1 - gam/2)/(1 + gam/2), pb = wr^2/(1 + gam/2), pc = wp^2/(1 + gam/2) (padding: zero parameters, pa = 1).
+__global__ void pole_coefficients(long long n, const float *wp2, const float *wr2, const float *gam, float *pc,
+                                  float *pb, float *pa) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double d = 1.0 + 0.5 * (double)gam[k];
+        pa[k] = (float)((1.0 - 0.5 * (double)gam[k]) / d);
+        pb[k] = (float)((double)wr2[k] / d);
+        pc[k] = (float)((double)wp2[k] / d);
+    }
+}
+
+cudaError_t launch_pole_coefficients(const lbem_t *h, cudaStream_t s) {
+    const long long n = h->grid.plane;
+    pole_coefficients<<<blocks_for(n), 256, 0, s>>>(n, h->d_wp2, h->d_wr2, h->d_gam, h->d_pc, h->d_pb, h->d_pa);
     return cudaGetLastError();
 }
 

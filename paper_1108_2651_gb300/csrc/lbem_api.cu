@@ -113,6 +113,9 @@ StepArgs step_args(const lbem_t *h, int cur_in) {
         a.med.wp2 = h->d_wp2;
         a.med.wr2 = h->d_wr2;
         a.med.gam = h->d_gam;
+        a.med.pc = h->d_pc;
+        a.med.pb = h->d_pb;
+        a.med.pa = h->d_pa;
         a.med.J = h->d_J;
         a.med.Pr = h->pole_P(cur_in);
         a.med.Pw = h->pole_P(cur_in ^ 1);
@@ -143,6 +146,9 @@ static cudaError_t launch_step(const lbem_t *h, const StepArgs &a, int variant) 
             q.wp2 = h->d_wp2;
             q.wr2 = h->d_wr2;
             q.gam = h->d_gam;
+            q.pc = h->d_pc;
+            q.pb = h->d_pb;
+            q.pa = h->d_pa;
             q.J = h->d_J;
             q.P = a.med.Pr;
             q.Pn = a.med.Pw;
@@ -403,7 +409,7 @@ void lbem_destroy(lbem_t *h) {
                     (void *)h->d_diag, (void *)h->d_counter, (void *)h->d_stage, (void *)h->d_fx, (void *)h->d_fy,
                     (void *)h->d_fz,
                     (void *)h->d_wp2, (void *)h->d_wr2, (void *)h->d_gam, (void *)h->d_J, (void *)h->d_P,
-                    (void *)h->d_P2})
+                    (void *)h->d_P2, (void *)h->d_pc, (void *)h->d_pb, (void *)h->d_pa})
         gfree(h, p);
     for (int k = 1; k <= 3; k++) gfree(h, h->d_tiles[k]);
     delete h;
@@ -758,7 +764,7 @@ lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, c
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (!wp2) {  // back to a non-dispersive medium
         LBEM_CUDA(cudaStreamSynchronize(h->stream));
-        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P, &h->d_P2}) {
+        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P, &h->d_P2, &h->d_pc, &h->d_pb, &h->d_pa}) {
             gfree(h, *p);
             *p = nullptr;
         }
@@ -787,12 +793,13 @@ lbem_status lbem_set_dispersion(lbem_t *h, const float *wp2, const float *wr2, c
                                          " sites with a parameter not finite and >= 0, or wp^2 + wr^2 > 4 w0");
     const size_t pl = (size_t)h->grid.plane;  // stored as planes with the grid's pitch (padding zero)
     if (!h->d_wp2) {
-        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P, &h->d_P2})
+        for (float **p : {&h->d_wp2, &h->d_wr2, &h->d_gam, &h->d_J, &h->d_P, &h->d_P2, &h->d_pc, &h->d_pb, &h->d_pa})
             LBEM_CUDA(gmalloc(h, (void **)p, sizeof(float) * pl, "dispersive pole"));
     }
     const float *src[3] = {dp, dr, dg};
     float *dst[3] = {h->d_wp2, h->d_wr2, h->d_gam};
     for (int k = 0; k < 3; k++) LBEM_CUDA(launch_to_plane(h, src[k], dst[k], h->stream));
+    LBEM_CUDA(launch_pole_coefficients(h, h->stream));
     for (float *p : {h->d_J, h->d_P, h->d_P2}) LBEM_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * pl, h->stream));
     LBEM_CUDA(cudaStreamSynchronize(h->stream));
     h->disp = true;

@@ -262,13 +262,31 @@ __device__ __forceinline__ Out5 collide2d_an(float g0, float g1, float g2, float
 }
 
 // One step of the dispersive pole at a site (the displacement form of the auxiliary equation, reading R17):
-// E = -c_L^2 sigma - P, J <- ((1 - gam/2) J - wr^2 P + wp^2 E) / (1 + gam/2), P <- P + J.  Shared by the
-// single-step general kernel and the two-step tile kernel so both round identically.
-__device__ __forceinline__ void pole_update(float cl, float sig, float wp, float wr, float gm, float &J, float &P) {
+// E = -c_L^2 sigma - P, J <- ((1 - gam/2) J - wr^2 P + wp^2 E) / (1 + gam/2), P <- P + J, with the division
+// folded into per-site coefficients computed once at upload: pa = (1 - gam/2)/(1 + gam/2), pb = wr^2/(1 + gam/2),
+// pc = wp^2/(1 + gam/2) (pole_coefficients in general.cu).  Shared by the single-step general kernel and the two-step
+// tile kernel so both round identically.
+__device__ __forceinline__ void pole_update(float cl, float sig, float pc, float pb, float pa, float &J, float &P) {
     const float E = __fsub_rn(__fmul_rn(-cl, sig), P);
-    const float num = __fadd_rn(__fsub_rn(__fmul_rn(__fsub_rn(1.f, 0.5f * gm), J), __fmul_rn(wr, P)), __fmul_rn(wp, E));
-    J = __fdiv_rn(num, __fadd_rn(1.f, 0.5f * gm));
+    J = __fadd_rn(__fsub_rn(__fmul_rn(pa, J), __fmul_rn(pb, P)), __fmul_rn(pc, E));
     P = __fadd_rn(P, J);
+}
+
+// collide2d_an of an isotropic medium with a pole (r = 1/r = 1, fs = 2): the products it drops are by 1, and 2 fs = 4
+// is a power of two, so the results are those of collide2d_an bit for bit.
+__device__ __forceinline__ Out5 collide2d_pole_iso(float g0, float g1, float g2, float g3, float g4, float cl,
+                                                   float shat, float P) {
+    const float sig = __fadd_rn(__fadd_rn(__fadd_rn(g0, g1), __fadd_rn(g2, g3)), g4);
+    const float Lam = __fadd_rn(__fmul_rn(cl, sig), P);
+    const float w0 = __fsub_rn(1.f, 2.f * cl);
+    const float Tm = __fmul_rn(-0.5f * cl, shat), T0 = __fmul_rn(-w0, shat);
+    Out5 o;
+    o.o0 = __fadd_rn(__fsub_rn(__fsub_rn(__fmul_rn(2.f * w0, sig), g0), 4.f * P), T0);
+    o.o1 = __fadd_rn(__fsub_rn(Lam, g3), Tm);
+    o.o2 = __fadd_rn(__fsub_rn(Lam, g4), Tm);
+    o.o3 = __fadd_rn(__fsub_rn(Lam, g1), Tm);
+    o.o4 = __fadd_rn(__fsub_rn(Lam, g2), Tm);
+    return o;
 }
 
 // collide2d at a site without a source (S^ = +0): there T_m and T_0 are -0 (c_L^2 > 0, w0 >= 0), and adding
@@ -327,9 +345,11 @@ struct Medium {
     const float *dlnmu = nullptr;  // [D][plane] or null
     // anisotropic medium (general.cu): r = c_x / c_y = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy); 1, 1: isotropic
     float ar = 1.f, amu = 1.f;
-    // one dispersive pole per site (null without; pitched planes): its parameters, J (updated in place) and P,
-    // read from Pr (time t) and written to Pw (the plane of the output state's parity)
+    // one dispersive pole per site (null without; pitched planes): its parameters (wp2 non-null marks a pole), the
+    // per-site coefficients of its update (pole_update: pc, pb, pa), J (updated in place) and P, read from Pr
+    // (time t) and written to Pw (the plane of the output state's parity)
     const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr, *Pr = nullptr;
+    const float *pc = nullptr, *pb = nullptr, *pa = nullptr;
     float *J = nullptr, *Pw = nullptr;
 };
 
@@ -345,6 +365,7 @@ struct Walls {
 // (axis speeds c_x^2 = r cbar^2, c_y^2 = cbar^2 / r with cbar^2 the stored c_L^2; mubar = sqrt(mu_xx mu_yy)).
 struct General {
     const float *wp2 = nullptr, *wr2 = nullptr, *gam = nullptr;
+    const float *pc = nullptr, *pb = nullptr, *pa = nullptr;  // pole_update's per-site coefficients
     float *J = nullptr;        // updated in place
     const float *P = nullptr;  // P at t
     float *Pn = nullptr;       // P at t + 1 (the other plane: neighbouring tiles of a multi-step launch read P at t)
@@ -493,6 +514,7 @@ struct lbem {
     // P has two planes, paired with the population buffers: P at the time of buf[c] is pole_P(c), so a launch
     // reads P from the plane of its input's parity and writes the other one (every launch flips cur).
     float *d_wp2 = nullptr, *d_wr2 = nullptr, *d_gam = nullptr, *d_J = nullptr, *d_P = nullptr, *d_P2 = nullptr;
+    float *d_pc = nullptr, *d_pb = nullptr, *d_pa = nullptr;  // pole_update's coefficients (pole_coefficients)
     float *pole_P(int c) const { return c ? d_P2 : d_P; }
     bool disp = false;
     // anisotropic medium (lbem_set_medium_aniso): r = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy)
@@ -602,5 +624,7 @@ cudaError_t launch_disp_check(const lbem_t *h, const float *eps, const float *mu
                               const float *wp2, const float *wr2, const float *gam, bool pitched, unsigned *bad,
                               cudaStream_t s);
 cudaError_t launch_to_plane(const lbem_t *h, const float *src, float *dst, cudaStream_t s);
+// the pole's per-site update coefficients (pole_update) from its parameter planes
+cudaError_t launch_pole_coefficients(const lbem_t *h, cudaStream_t s);
 
 }  // namespace lbk

@@ -106,7 +106,7 @@ __device__ __forceinline__ void tb_issue_pole(const StepArgs &a, int x0, int y0,
     for (int k = threadIdx.x; k < 4 * TBY * QJ; k += nt) {
         const int pr = k / QJ, q = k - pr * QJ;
         const int pl = pr / TBY, r = pr - pl * TBY;
-        const float *base = pl == 0 ? a.med.J : pl == 1 ? a.med.wp2 : pl == 2 ? a.med.wr2 : a.med.gam;
+        const float *base = pl == 0 ? a.med.J : pl == 1 ? a.med.pc : pl == 2 ? a.med.pb : a.med.pa;
         const float *src = base + (long long)wrapi(y0 + r, G.ny) * G.pitch;
         float *dst = JS + pl * JPL + r * TBX + 4 * q;
         if (v16)
@@ -306,13 +306,14 @@ __device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, fl
         Out5 o;
         const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, TB_COMP(dlx, k), TB_COMP(dly, k)) : 0.f;
         if (AN || POLE) {
-            const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
+            // AN: a tensor (with or without a pole); POLE alone: an isotropic pole (r = 1, the products by r drop)
+            const float r = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, r) : 1.f, fs = __fadd_rn(r, ri);
             const float pz = POLE ? TB_COMP(pp->P, k) : 0.f;
             float shat = 0.f;
             if (EV) {
                 const int gx = x0 + 4 * lane + k;
                 shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, owned_row && gx < G.nx && gy < G.ny, q0,
-                                   q1, q2, q3, q4, ck, 0.f, pz, r, ri, a.med.amu);
+                                   q1, q2, q3, q4, ck, 0.f, pz, r, ri, AN ? a.med.amu : 1.f);
             }
             if (POLE && owned_row) {
                 const float sig = __fadd_rn(__fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, q3)), q4);
@@ -321,7 +322,8 @@ __device__ __forceinline__ void tb_update4m(const StepArgs &a, const PULL &g, fl
                 TB_SET(pp->J, k, J);
                 TB_SET(pp->P, k, Pn);
             }
-            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz);
+            o = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz)
+                   : collide2d_pole_iso(q0, q1, q2, q3, q4, ck, shat, pz);
         } else if (EV) {
             const int gx = x0 + 4 * lane + k;
             const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
@@ -423,11 +425,13 @@ __device__ __forceinline__ void tb_step_a(const StepArgs &a, const float *IN, co
         float shat = MU ? mu_source(q4 - q2, q1 - q3, CL[DX + py * TW + cc], CL[DY + py * TW + cc]) : 0.f;
         Out5 o;
         if (AN || POLE) {
-            const float r = a.med.ar, ri = __fdiv_rn(1.f, r), fs = __fadd_rn(r, ri);
+            const float r = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, r) : 1.f, fs = __fadd_rn(r, ri);
             const int gx = wrapi(x0 - 4 + cc, G.nx), gy = wrapi(y0 - 1 + py, G.ny);
             const float pz = POLE ? PS[py * TW + cc] : 0.f;
-            if (EV) shat = site_events(a, gx, gy, t, false, q0, q1, q2, q3, q4, ck, 0.f, pz, r, ri, a.med.amu);
-            o = collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz);
+            if (EV)
+                shat = site_events(a, gx, gy, t, false, q0, q1, q2, q3, q4, ck, 0.f, pz, r, ri, AN ? a.med.amu : 1.f);
+            o = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, r, ri, fs, pz)
+                   : collide2d_pole_iso(q0, q1, q2, q3, q4, ck, shat, pz);
         } else {
             if (EV)
                 shat = site_events(a, wrapi(x0 - 4 + cc, G.nx), wrapi(y0 - 1 + py, G.ny), t, false, q0, q1, q2, q3,
@@ -1149,8 +1153,8 @@ static bool make_pole_maps(const StepArgs &a, PoleMaps<true> *pm) {
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    return enc(&pm->P, a.med.Pr, boxP) && enc(&pm->J, a.med.J, boxJ) && enc(&pm->wp, a.med.wp2, boxJ) &&
-           enc(&pm->wr, a.med.wr2, boxJ) && enc(&pm->gm, a.med.gam, boxJ);
+    return enc(&pm->P, a.med.Pr, boxP) && enc(&pm->J, a.med.J, boxJ) && enc(&pm->wp, a.med.pc, boxJ) &&
+           enc(&pm->wr, a.med.pb, boxJ) && enc(&pm->gm, a.med.pa, boxJ);
 }
 
 template <int TBY, int NT, int MINB, bool MU = false, bool AN = false, bool POLE = false>
@@ -1602,7 +1606,9 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
         case LBEM_I16B: return launch_16<LBEM_I16B>(a, shape, s);
         default: break;
     }
-    if (a.med.wp2) return launch_tb<6, 256, 3, false, false, true>(a, s);  // a dispersive pole (any tensor)
+    if (a.med.wp2)  // a dispersive pole: with a tensor (AN and POLE), or isotropic (POLE alone)
+        return (a.med.ar != 1.f || a.med.amu != 1.f) ? launch_tb<6, 256, 3, false, true, true>(a, s)
+                                                       : launch_tb<6, 256, 3, false, false, true>(a, s);
     if (a.med.ar != 1.f || a.med.amu != 1.f) return launch_tb<6, 256, 5, false, true>(a, s);  // anisotropic
     if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)
