@@ -275,16 +275,36 @@ def other_forms(lbem, torch, p, peak, stream):
                               "frac": gbs / peak, "bytes_per_site": 44, "steps_per_launch": 1, "variant": v}
     # config 1: the 1024^2 medium (seed 1), 5000 steps, FP32; its 2 x 21 MB distributions and 4 MB medium stay in
     # the 129 MB L2, so the bytes per launch over the launch time are an effective rate, above the HBM copy rate
+    # the launches are short here, so both stepping modes are timed with CUDA-graph replay and the faster is kept
     p1 = W.heterogeneous_2d(1024, seed=1, nsteps=5000)
     n1 = int(np.prod(p1.shape))
-    s = lbem.Solver(p1.shape, stream=stream.cuda_stream)
-    ms, v, spp = _time_run(lbem, torch, s, p1, p1.nsteps, stream, passes=3)
-    s.close()
+    best1 = None
+    for spl_set in (1, 2):
+        s = lbem.Solver(p1.shape, stream=stream.cuda_stream)
+        s.set_problem(p1)
+        lbem.lbem_set_temporal_blocking(s.h, spl_set, -1)
+        lbem.lbem_set_graphs(s.h, True)
+        lbem.lbem_step(s.h, p1.nsteps)
+        evs1 = []
+        for _ in range(3):
+            lbem.lbem_set_fields(s.h)
+            a1, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a1.record(stream)
+            lbem.lbem_step(s.h, p1.nsteps)
+            b1.record(stream)
+            evs1.append((a1, b1))
+        torch.cuda.synchronize()
+        ms1 = float(np.mean([a1.elapsed_time(b1) for a1, b1 in evs1]))
+        spp1, v1 = lbem.lbem_get_temporal_blocking(s.h)[0], lbem.lbem_get_variant(s.h)[0]
+        s.close()
+        if best1 is None or ms1 < best1[0]:
+            best1 = (ms1, v1, spp1)
+    ms, v, spp = best1
     per = ms / (p1.nsteps // spp + p1.nsteps % spp)
     gbs = 44 * n1 / (per * 1e-3) / 1e9
     out["f32_1024"] = {"mlups": n1 * p1.nsteps / (ms * 1e-3) / 1e6, "ms_per_launch": per, "effective_gbs": gbs,
                        "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp, "variant": v,
-                       "l2_resident": True, "lb_steps": p1.nsteps}
+                       "l2_resident": True, "graphs": True, "lb_steps": p1.nsteps}
     probs = W.batch_2d(256, nsteps=2000)
     ss = []
     for q in probs:
