@@ -47,7 +47,8 @@ NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 433.764864e6 + 300.201472e6,
                ("het2d_4096", "i16b", "tb2-0"): 264.385536e6 + 150.971648e6,
                # dram__bytes.sum.per_second x gpu__time_duration.sum (6.657849 TB/s x 174.752 us), step2d_gen
                ("het2d_drude_4096", "f32", "disp"): 6.657849e12 * 174.752e-6,
-               ("het2d_aniso_4096", "f32", "tb2an"): 431.234560e6 + 297.513216e6}
+               ("het2d_aniso_4096", "f32", "tb2an"): 431.234560e6 + 297.513216e6,
+               ("het2d_drude_4096", "f32", "tb2pole"): 801.680128e6 + 435.911168e6}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
