@@ -127,6 +127,7 @@ StepArgs step_args(const lbem_t *h, int cur_in) {
     a.evt.traces = h->d_traces;
     a.evt.cap = h->nrec ? h->cap : 0;
     a.t = h->t;
+    a.sched = reinterpret_cast<int *>(h->d_counter) + 2;
     return a;
 }
 
@@ -372,7 +373,7 @@ lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
         e = gmalloc(h, (void **)&h->d_partials, sizeof(double) * 3 * h->n_partials, "diagnostic partials");
     }
     if (e == cudaSuccess) e = gmalloc(h, (void **)&h->d_diag, sizeof(double) * 4, "diagnostics");
-    if (e == cudaSuccess) e = gmalloc(h, (void **)&h->d_counter, sizeof(unsigned) * 4, "counters");
+    if (e == cudaSuccess) e = gmalloc(h, (void **)&h->d_counter, sizeof(unsigned) * 4, "counters");  // [2..3]: StepArgs::sched
     if (e != cudaSuccess) {
         cudaGetLastError();
         lbem_destroy(h);
@@ -391,6 +392,7 @@ lbem_status lbem_create(const lbem_desc *d, lbem_t **out) {
     }
     cudaMemsetAsync(h->pool, 0, h->pool_bytes, h->stream);
     cudaMemsetAsync(h->cL2, 0, sizeof(float) * G.plane, h->stream);
+    cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned) * 4, h->stream);
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
         lbem_destroy(h);
         return cuda_fail(e, "lbem_create");

@@ -382,6 +382,9 @@ struct StepArgs {
     Medium med;
     Events evt;
     long long t;  // time of the pre-collision state being collided
+    // work queue of the strip-streaming kernel (sstream.cu), two counters of the handle: [0] the next unit to take,
+    // [1] the CTAs that finished; both zero between launches (the last CTA out resets them)
+    int *sched = nullptr;
 };
 
 // Periodic index, cheap when v is already in range (the common case).
@@ -488,7 +491,7 @@ struct lbem {
     double *d_partials = nullptr;
     int n_partials = 0;
     double *d_diag = nullptr;     // [3]
-    unsigned *d_counter = nullptr; // validation / max-abs scratch
+    unsigned *d_counter = nullptr; // [0] validation / max-abs scratch, [2..3] the strip kernel's work queue
     float *d_stage = nullptr;      // staging for host <-> device copies of grid fields
     size_t stage_bytes = 0;
     // graphs
@@ -560,6 +563,10 @@ int tb2_nshapes(int storage, bool has_mu);
 // two steps per launch by register streaming (rstream.cu): FP32 storage, uniform mu
 int rs2_nshapes();
 cudaError_t launch_step_2d_rs2(const StepArgs &a, int shape, cudaStream_t s);
+int ss2_nshapes();  // strip streaming (sstream.cu): two steps per launch, FP32, uniform mu
+cudaError_t launch_step_2d_ss2(const StepArgs &a, int shape, cudaStream_t s);
+bool ss2_take_timeouts();  // reads and clears the strip kernel's wait-timeout flag
+cudaError_t ss_set_wait_limit(unsigned long long ns);
 bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag
 cudaError_t tb_set_wait_limit(unsigned long long ns);  // limit of its bounded waits (current device)
 // three steps per launch (tblock.cu): FP32 storage, uniform mu

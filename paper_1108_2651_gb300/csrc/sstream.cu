@@ -1,0 +1,490 @@
+// Two time steps per launch by streaming a strip of rows through a ring of shared-memory stages (2D, FP32 storage,
+// uniform mu).
+//
+// A CTA owns a strip of 128 columns (x0 .. x0+127) and a run of rows ys .. ye-1 and walks down the run in chunks of
+// TBY rows.  A chunk of the state at t (the five population planes, each staged shifted by its pull offset in y so
+// that staged row w of every plane holds what the update of chunk row w pulls, and c_L^2) arrives in one of S
+// stages, ahead of the one being computed.  Phase g computes step t on the rows of chunk g (Eqs.
+// 17-18) and step t+1 on the rows one behind the previous chunk, whose pulls are then all computed: the step-t
+// results at a row are the next step's g0, g1, g3 there, g2 one row below and g4 one row above.  Step t therefore
+// stores each result plane at the row that will pull it, in a ring of 2 TBY + 2 rows (with c_L^2 beside them for
+// step t+1), and one barrier of the warps that compute, per phase, is the only synchronisation between the two
+// steps: the rows step t writes in a phase and the rows step t+1 reads in it are disjoint.
+//
+// Warps 0 .. 2 TBY - 1 consume: TBY rows of step t, and TBY rows of step t+1 with the chunk's ring sites (the
+// column left and right of the strip, which give step t+1 plane 1 at x0-1 and plane 3 at x0+128).  The last warp
+// produces: it runs up to S chunks ahead of them (full and empty mbarriers per stage) and takes units of work from a
+// queue.  Chunks inside the grid are six TMA boxes.  In the first and last strip the boxes reach past the grid's
+// columns (the copy fills zeros there) and six more boxes of 4 columns bring the periodic images into a side buffer,
+// from which those few pulls read.  Chunks whose rows wrap periodically, and ragged grids, are staged by the producer
+// warp's asynchronous copies, which arrive on the stage's mbarrier as they land.
+//
+// HBM traffic per two site updates: 24 bytes read and 20 written; the two rows outside a run and the four columns
+// either side of a strip are read again, mostly from L2.  Nothing is computed twice except those rows and the ring
+// sites.  The site updates are collide2d / collide2d_free, so the results are bit-identical to two single steps.
+#include <cuda.h>
+#include <string.h>
+
+#include "lbem_internal.cuh"
+#include "tma.cuh"
+
+namespace lbk {
+
+namespace {
+constexpr int SBX = 128;     // strip width: one warp of 4-site lanes
+constexpr int SW = SBX + 8;  // staged columns x0-4 .. x0+131 (16-byte aligned boxes); column j <-> x0-4+j
+
+// Row shift of the staged planes: plane p row w of chunk k's stage holds global row s_k + w + ss_shift(p).
+__device__ __host__ constexpr int ss_shift(int p) { return p == 2 ? -1 : p == 4 ? 1 : 0; }
+}  // namespace
+
+__device__ int g_ss_timeouts = 0;  // set when a bounded wait of the strip kernel gave up
+// Limit of the strip kernel's bounded waits for a chunk, in ns of device time (0 gives up at once).
+__device__ unsigned long long g_ss_wait_limit_ns = 2000000000ull;
+constexpr unsigned long long kSsDrainNs = 2000000000ull;  // after giving up: wait for copies in flight
+
+// Shared memory of a CTA (floats): S stages of a chunk (six planes of TBY rows of SW, each plane 128-byte aligned,
+// a TMA destination), S side buffers of the periodic images of an edge strip (six planes of TBY rows of 4), the
+// step-(t+1) ring (six planes of M rows of SW: populations 0..4, then c_L^2), the chunk descriptors, then two
+// mbarriers per stage (full: staged; empty: read by every consumer warp).
+template <int TBY, int S>
+struct SsGeom {
+    static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
+    static constexpr int M = 2 * TBY + 2;
+    static constexpr int PL_IN = up32(TBY * SW), STAGE = 6 * PL_IN;
+    static constexpr int EPL = up32(4 * TBY), ESTAGE = 6 * EPL;
+    static constexpr int PL_P = M * SW;
+    static constexpr int IN_SZ = S * STAGE, E_SZ = S * ESTAGE, P_SZ = up32(6 * PL_P);
+    static constexpr int DS = S + 2;  // chunk descriptors (int4) after the ring, then the mbarriers
+    static constexpr int SZ = IN_SZ + E_SZ + P_SZ + 4 * DS;
+    static constexpr size_t BYTES = sizeof(float) * SZ + 2 * S * sizeof(unsigned long long);
+    static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * TBY * SW, E_BYTES = sizeof(float) * 6 * TBY * 4;
+};
+
+// Which columns of the strip wrap: 0 none (x0-4 .. x0+131 inside the grid), 1 the first strip (x0 = 0, the images
+// of columns nx-4 .. nx-1 left of it), 2 the last strip of a grid of whole strips (the images of columns 0 .. 3
+// right of it), 3 anything else (a single strip, or a last strip reaching past nx), staged by element copies.
+__device__ __forceinline__ int ss_xmode(const Grid &G, int x0) {
+    if (x0 - 4 >= 0 && x0 + SBX + 4 <= G.nx) return 0;
+    if ((G.nx & 3) == 0 && x0 == 0 && SBX + 4 <= G.nx) return 1;
+    if ((G.nx & 3) == 0 && x0 >= SBX && x0 + SBX == G.nx) return 2;
+    return 3;
+}
+
+// How chunk rows s .. s+TBY-1 are staged: 0 six TMA boxes, 1 six boxes and the six boxes of the images (xmode 1
+// or 2), 2 every thread's asynchronous copies (rows that wrap, xmode 3, or no tensor maps).
+template <int TBY>
+__device__ __forceinline__ int ss_chunk_mode(const Grid &G, int xm, int s, bool tma) {
+    if (!tma || xm == 3 || s < 1 || s + TBY + 1 > G.ny) return 2;
+    return xm == 0 ? 0 : 1;
+}
+
+// Stage the chunk of step-t rows s .. s+TBY-1 into `st` (and `es`), by the producer warp, arriving on the stage's
+// full mbarrier (count 1).  Modes 0 and 1: lane 0 arrives with the transaction bytes and issues the boxes.  Mode 2:
+// every lane issues its share of asynchronous copies (16 bytes where every group of 4 columns stays contiguous after
+// the periodic wrap, else 4), each lane's copies tracked by the mbarrier (its pending count rises until they land),
+// then lane 0 arrives.
+template <int TBY, int S>
+__device__ __forceinline__ void ss_issue(const StepArgs &a, int x0, int xm, int s, int mode, float *st, float *es,
+                                         unsigned mbar, const CUtensorMap *tmIn, const CUtensorMap *tmCL,
+                                         const CUtensorMap *tmIn4, const CUtensorMap *tmCL4) {
+    using Gm = SsGeom<TBY, S>;
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31;
+    if (mode != 2) {
+        if (lane == 0) {
+            // the consumers' reads of this stage (ordered by the empty mbarrier) before the async-proxy writes
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            const unsigned bytes = Gm::TMA_BYTES + (mode == 1 ? Gm::E_BYTES : 0u);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+                         : "memory");
+#pragma unroll
+            for (int p = 0; p < 5; p++) tma_load_3d(st + p * Gm::PL_IN, tmIn, x0 - 4, s + ss_shift(p), p, mbar);
+            tma_load_2d(st + 5 * Gm::PL_IN, tmCL, x0 - 4, s, mbar);
+            if (mode == 1) {
+                const int xe = xm == 1 ? G.nx - 4 : 0;
+#pragma unroll
+                for (int p = 0; p < 5; p++) tma_load_3d(es + p * Gm::EPL, tmIn4, xe, s + ss_shift(p), p, mbar);
+                tma_load_2d(es + 5 * Gm::EPL, tmCL4, xe, s, mbar);
+            }
+        }
+        return;
+    }
+    const float *in = static_cast<const float *>(a.in.data);
+    if (xm == 0 || (G.nx & 3) == 0) {
+        constexpr int Q = SW / 4;
+        for (int k = lane; k < 6 * TBY * Q; k += 32) {
+            const int pr = k / Q, q = k - pr * Q;  // pr = plane * TBY + row
+            const int p = pr / TBY, w = pr - p * TBY;
+            const float *row = p < 5 ? in + p * G.plane + (long long)wrapi(s + w + ss_shift(p), G.ny) * G.pitch
+                                     : a.med.cL2 + (long long)wrapi(s + w, G.ny) * G.pitch;
+            tb_cpa16(st + p * Gm::PL_IN + w * SW + 4 * q, row + wrapi(x0 - 4 + 4 * q, G.nx));
+        }
+    } else {
+        for (int k = lane; k < 6 * TBY * SW; k += 32) {
+            const int pr = k / SW, c = k - pr * SW;
+            const int p = pr / TBY, w = pr - p * TBY;
+            const float *row = p < 5 ? in + p * G.plane + (long long)wrapi(s + w + ss_shift(p), G.ny) * G.pitch
+                                     : a.med.cL2 + (long long)wrapi(s + w, G.ny) * G.pitch;
+            tb_cpa4(st + p * Gm::PL_IN + w * SW + c, row + wrapi(x0 - 4 + c, G.nx));
+        }
+    }
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];\n" ::"r"(mbar) : "memory");
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+// Four site updates at global row gy, columns x0+4*lane.. (collide2d with the sites' sources and receivers where
+// EV, else collide2d_free), from the pulled populations q[0..4] and c_L^2.
+template <bool EV>
+__device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[5], float4 cl, int x0, int gy,
+                                           long long t, bool owned, float4 (&o)[5]) {
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k), q4 = get(q[4], k),
+                    ck = get(cl, k);
+        Out5 r;
+        if (EV) {
+            const int gx = x0 + 4 * lane + k;
+            const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
+                                           owned && gx < G.nx && gy < G.ny, q0, q1, q2, q3, q4, ck);
+            r = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        } else {
+            r = collide2d_free(q0, q1, q2, q3, q4, ck);
+        }
+        set(o[0], k, r.o0);
+        set(o[1], k, r.o1);
+        set(o[2], k, r.o2);
+        set(o[3], k, r.o3);
+        set(o[4], k, r.o4);
+    }
+}
+
+// The populations pulled by a lane's four sites at row `row` of a stage S with plane stride PL: g0, g2, g4 from
+// columns c.., g1 from c-1.., g3 from c+1.. (Eq. 17), and c_L^2 from plane 5.
+__device__ __forceinline__ void ss_pull(const float *S, int PL, int row, int c, float4 (&q)[5], float4 &cl) {
+    const float *r = S + row * SW + c;
+    q[0] = lds4(r);
+    const float4 l1 = lds4(r + PL - 4), m1 = lds4(r + PL);
+    q[1] = make_float4(l1.w, m1.x, m1.y, m1.z);
+    q[2] = lds4(r + 2 * PL);
+    const float4 m3 = lds4(r + 3 * PL), h3 = lds4(r + 3 * PL + 4);
+    q[3] = make_float4(m3.y, m3.z, m3.w, h3.x);
+    q[4] = lds4(r + 4 * PL);
+    cl = lds4(r + 5 * PL);
+}
+
+__device__ __forceinline__ bool ss_row_events(const StepArgs &a, int gy) {
+    const int y = wrapi(gy, a.g.ny);
+    return __ldg(a.evt.rowptr + y) != __ldg(a.evt.rowptr + y + 1);
+}
+
+// Step t on row w of the chunk in stage `st` (global row r = s + w), the lane's four sites; results go to the ring at
+// the rows that pull them (ring row u = r - ys + 2 for planes 0, 1, 3 and c_L^2, u + 1 for plane 2, u - 1 for plane
+// 4).  With the images in `es` (emode 1: left of the strip, 2: right of it) lane 0's g1 or lane 31's g3 come from
+// there.
+template <int TBY, int S, bool EV>
+__device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, const float *es, int emode, float *P,
+                                          int x0, int ys, int ye, int r, int w, int u, long long t) {
+    using Gm = SsGeom<TBY, S>;
+    constexpr int M = Gm::M, PP = Gm::PL_P;
+    const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
+    float4 q[5], cl, o[5];
+    ss_pull(st, Gm::PL_IN, w, c, q, cl);
+    if (emode == 1 && lane == 0) q[1].x = es[Gm::EPL + w * 4 + 3];        // column x0-1 = nx-1
+    if (emode == 2 && lane == 31) q[3].w = es[3 * Gm::EPL + w * 4 + 0];   // column x0+128 = 0
+    ss_update4<EV>(a, q, cl, x0, r, t, r >= ys && r < ye, o);
+    const int s0 = u % M, s2 = s0 == M - 1 ? 0 : s0 + 1, s4 = s0 == 0 ? M - 1 : s0 - 1;
+    float *p0 = P + s0 * SW + c;
+    sts4(p0, o[0]);
+    sts4(p0 + PP, o[1]);
+    sts4(p0 + 3 * PP, o[3]);
+    sts4(p0 + 5 * PP, cl);
+    sts4(P + 2 * PP + s2 * SW + c, o[2]);
+    sts4(P + 4 * PP + s4 * SW + c, o[4]);
+}
+
+// The ring sites of chunk row w in stage `st` (lane 0: column x0-1, plane 1 only; lane 1: column x0+128, plane 3
+// only), at ring row p TBY + w + 1 (p: the CTA's phase); with the images in `es` the columns outside the grid come
+// from there.
+template <int TBY, int S>
+__device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, const float *es, int emode, float *P,
+                                        int x0, int s, int w, int p, bool events, long long t) {
+    using Gm = SsGeom<TBY, S>;
+    const int lane = threadIdx.x & 31;
+    if (lane >= 2) return;
+    const int right = lane, cc = right ? SBX + 4 : 3, r = s + w;
+    auto v = [&](int pl, int col) -> float {
+        if (emode == 1 && col < 4) return es[pl * Gm::EPL + w * 4 + col];
+        if (emode == 2 && col >= SBX + 4) return es[pl * Gm::EPL + w * 4 + col - (SBX + 4)];
+        return st[pl * Gm::PL_IN + w * SW + col];
+    };
+    const float q0 = v(0, cc), q1 = v(1, cc - 1), q2 = v(2, cc), q3 = v(3, cc + 1), q4 = v(4, cc), ck = v(5, cc);
+    float shat = 0.f;
+    if (events && ss_row_events(a, r))
+        shat = site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck);
+    const Out5 ro = collide2d(q0, q1, q2, q3, q4, ck, shat);
+    const int s0 = (p * TBY + w + 1) % Gm::M;
+    if (right)
+        P[3 * Gm::PL_P + s0 * SW + cc] = ro.o3;
+    else
+        P[Gm::PL_P + s0 * SW + cc] = ro.o1;
+}
+
+// Step t+1 on global row rb (ring row ub), written as 16-byte streaming stores.
+template <int TBY, int S, bool EV>
+__device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int x0, int rb, int ub, long long t) {
+    using Gm = SsGeom<TBY, S>;
+    const Grid &G = a.g;
+    const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
+    float4 q[5], cl, o[5];
+    ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl);
+    ss_update4<EV>(a, q, cl, x0, rb, t + 1, true, o);
+    if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
+        float4 *op = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)rb * G.pitch + x0 +
+                                                4 * lane);
+        const long long pl4 = G.plane / 4;
+        __stcs(op, o[0]);
+        __stcs(op + pl4, o[1]);
+        __stcs(op + 2 * pl4, o[2]);
+        __stcs(op + 3 * pl4, o[3]);
+        __stcs(op + 4 * pl4, o[4]);
+    }
+}
+
+// A chunk's descriptor (in shared memory, DS = S + 2 of them in a ring): the unit's strip x0 and rows ys .. ye-1, and
+// w = the chunk's index k in the unit | staging mode << 16 | column mode << 20 | 1 << 24 (0: the stream has ended)
+// | 1 << 25 when rows s-1 .. s+TBY of the chunk may hold a source or receiver.
+__device__ __forceinline__ bool ss_valid(int4 d) { return (d.w >> 24) & 1; }
+__device__ __forceinline__ bool ss_events(int4 d) { return (d.w >> 25) & 1; }
+
+// Block barrier 1 of the n consumer threads, returning whether any of them passed true.
+__device__ __forceinline__ bool ss_consumers_or(bool v, int n) {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"((int)v), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+// Persistent CTAs over a queue of units (strip, run of H rows): unit i is strip i % nstrip, rows (i / nstrip) H ..
+// + H - 1, taken in order from the handle's counter, so that CTAs slowed down by sources, receivers or the memory
+// they read take fewer units.  The chunks of a CTA's successive units form one stream.
+//
+// The producer warp (the last) runs ahead of the others: for stream chunk c it waits until stage c % S is free (its
+// empty mbarrier: every consumer warp has read chunk c - S), writes the chunk's descriptor and stages it (full
+// mbarrier), taking units from the queue one unit ahead; after the last chunk it writes an end descriptor.
+//
+// The 2 TBY consumer warps run phase p on stream chunk p: warps 0 .. TBY-1 step t on its rows, warps TBY .. 2 TBY - 1
+// its ring sites (two lanes) and step t+1 one behind chunk p - 1, whatever units the two chunks belong to; ring rows
+// are numbered by the phase (rows of step t+1 that would pull across a unit boundary lie outside their unit and are
+// skipped).  Each consumer warp releases the stage once it has read it, and a barrier of the consumers closes the
+// phase.
+template <int TBY, int S, int MINB>
+__global__ void __launch_bounds__((2 * TBY + 1) * 32, MINB)
+    step2d_ss2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
+               const __grid_constant__ CUtensorMap tmIn4, const __grid_constant__ CUtensorMap tmCL4, int use_tma,
+               int nstrip, int H, int nunits) {
+    using Gm = SsGeom<TBY, S>;
+    constexpr int NWC = 2 * TBY, DS = Gm::DS;
+    extern __shared__ __align__(1024) float sm[];
+    float *E = sm + Gm::IN_SZ;
+    float *P = E + Gm::E_SZ;
+    int4 *desc = reinterpret_cast<int4 *>(P + Gm::P_SZ);
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(desc + DS);  // full[S], then empty[S]
+    const Grid &G = a.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool tma = use_tma && !(smem_u32(sm) & 127);  // TMA destinations here are 128-byte aligned
+    const unsigned full0 = smem_u32(mb), empty0 = full0 + 8 * S;
+    if (tid < S) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * tid) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(empty0 + 8 * tid), "r"(NWC) : "memory");
+    }
+    if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncthreads();
+    const unsigned long long wait_limit = g_ss_wait_limit_ns;
+    if (warp == NWC) {
+        // ---- producer
+        int cK = 0, ck = 0, cx0 = 0, cys = 0, cye = 0, cxm = 0, nu = 0;
+        if (lane == 0) nu = atomicAdd(a.sched, 1);
+        int c = 0;
+        bool ok = true;
+        for (;; c++) {
+            if (c >= S && !mbar_wait(empty0 + 8 * (c % S), (unsigned)(c / S - 1) & 1u, wait_limit)) {
+                ok = false;
+                break;
+            }
+            int4 d = make_int4(0, 0, 0, 0);
+            if (lane == 0) {
+                if (ck == cK && nu < nunits) {  // the next unit
+                    cx0 = (nu % nstrip) * SBX;
+                    cys = (nu / nstrip) * H;
+                    cye = min(cys + H, G.ny);
+                    cK = (cye - cys + 2 + TBY - 1) / TBY;  // step-t chunks: rows ys-1 .. ys-2+K*TBY (through ye)
+                    cxm = ss_xmode(G, cx0);
+                    ck = 0;
+                    nu = atomicAdd(a.sched, 1);
+                }
+                if (ck < cK) {
+                    const int s = cys - 1 + ck * TBY, mode = ss_chunk_mode<TBY>(G, cxm, s, tma);
+                    d = make_int4(cx0, cys, cye, ck | mode << 16 | cxm << 20 | 1 << 24);
+                    if (a.evt.rowptr && !(s - 1 >= 0 && s + TBY + 1 <= G.ny &&
+                                          __ldg(a.evt.rowptr + s - 1) == __ldg(a.evt.rowptr + s + TBY + 1)))
+                        d.w |= 1 << 25;
+                    ck++;
+                }
+                desc[c % DS] = d;
+            }
+            d.x = __shfl_sync(0xffffffffu, d.x, 0);
+            d.y = __shfl_sync(0xffffffffu, d.y, 0);
+            d.w = __shfl_sync(0xffffffffu, d.w, 0);
+            if (!ss_valid(d)) {  // end of the stream: the consumers find the end descriptor
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8 * (c % S)) : "memory");
+                break;
+            }
+            ss_issue<TBY, S>(a, d.x, (d.w >> 20) & 15, d.y - 1 + (d.w & 0xffff) * TBY, (d.w >> 16) & 15,
+                             sm + (c % S) * Gm::STAGE, E + (c % S) * Gm::ESTAGE, full0 + 8 * (c % S), &tmIn, &tmCL,
+                             &tmIn4, &tmCL4);
+        }
+        if (!ok) {  // the consumers stopped: flag it, let this warp's copies in flight land (bounded)
+            if (lane == 0) atomicExch(&g_ss_timeouts, 1);
+            for (int k = c > S ? c - S : 0; k < c; k++)
+                mbar_wait(full0 + 8 * (k % S), (unsigned)(k / S) & 1u, kSsDrainNs);
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        if (lane == 0) __threadfence();  // the queue accesses before the CTA counts itself out
+    } else {
+        // ---- consumers
+        const long long t = a.t;
+        for (int p = 0;; p++) {
+            const bool ok = mbar_wait(full0 + 8 * (p % S), (unsigned)(p / S) & 1u, wait_limit);
+            const int4 da = desc[p % DS], db = desc[(p + DS - 1) % DS];
+            const bool va = ok && ss_valid(da), vb = p >= 1 && ss_valid(db);
+            const float *st = sm + (p % S) * Gm::STAGE, *es = E + (p % S) * Gm::ESTAGE;
+            const int emode = ((da.w >> 16) & 15) == 1 ? (da.w >> 20) & 15 : 0, s = da.y - 1 + (da.w & 0xffff) * TBY;
+            if (warp < TBY) {
+                if (va) {
+                    const int r = s + warp;
+                    if (ss_events(da) && ss_row_events(a, r))
+                        ss_step_a<TBY, S, true>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t);
+                    else
+                        ss_step_a<TBY, S, false>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t);
+                }
+            } else {
+                const int w = warp - TBY;
+                if (va) ss_ring<TBY, S>(a, st, es, emode, P, da.x, s, w, p, ss_events(da), t);
+                if (vb) {
+                    const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
+                    if (rb >= db.y && rb < db.z) {
+                        if (ss_events(db) && ss_row_events(a, rb))
+                            ss_step_b<TBY, S, true>(a, P, db.x, rb, (p - 1) * TBY + w, t);
+                        else
+                            ss_step_b<TBY, S, false>(a, P, db.x, rb, (p - 1) * TBY + w, t);
+                    }
+                }
+            }
+            if (va) {  // this warp has read the stage: release it to the producer
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(empty0 + 8 * (p % S)) : "memory");
+            }
+            // the phase's ring writes before the next phase's reads
+            if (ss_consumers_or(!ok, NWC * 32)) {  // a chunk never arrived: flag it and stop (the producer drains)
+                if (tid == 0) atomicExch(&g_ss_timeouts, 1);
+                break;
+            }
+            if (!ss_valid(da)) break;  // the end descriptor: step t+1 of the last chunk was this phase's
+        }
+    }
+    // count this CTA out; the last one resets the queue for the next launch
+    __syncthreads();
+    if (tid == 0 && atomicAdd(a.sched + 1, 1) == (int)gridDim.x - 1) {
+        a.sched[0] = 0;
+        a.sched[1] = 0;
+    }
+}
+
+// Tensor maps of the populations ([5][ny][pitch] floats, box: one plane of TBY rows of `w` columns) and c_L^2;
+// false if unavailable (every chunk is then staged by asynchronous copies).
+static bool ss_make_maps(const StepArgs &a, int tby, int w, CUtensorMap *mIn, CUtensorMap *mCL) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || a.g.nx < SW || a.g.ny < tby + 2) return false;
+    const cuuint64_t dims3[3] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny, 5};
+    const cuuint64_t str3[2] = {(cuuint64_t)a.g.pitch * 4, (cuuint64_t)a.g.plane * 4};
+    const cuuint32_t box3[3] = {(cuuint32_t)w, (cuuint32_t)tby, 1};
+    const cuuint32_t one[3] = {1, 1, 1};
+    if (fn(mIn, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.in.data), dims3, str3, box3, one,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t dims2[2] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny};
+    const cuuint64_t str2[1] = {(cuuint64_t)a.g.pitch * 4};
+    const cuuint32_t box2[2] = {(cuuint32_t)w, (cuuint32_t)tby};
+    return fn(mCL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(a.med.cL2), dims2, str2, box2, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Persistent CTAs (as many as are resident, at most one per unit) over units of m TBY - 2 rows (m chunks each).
+template <int TBY, int S, int MINB, int MCH>
+static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
+    using Gm = SsGeom<TBY, S>;
+    constexpr int NT = (2 * TBY + 1) * 32;
+    if (!a.sched) return cudaErrorInvalidValue;
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(step2d_ss2<TBY, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Gm::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_ss2<TBY, S, MINB>, NT, Gm::BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    CUtensorMap mIn, mCL, mIn4, mCL4;
+    memset(&mIn, 0, sizeof mIn);
+    memset(&mCL, 0, sizeof mCL);
+    memset(&mIn4, 0, sizeof mIn4);
+    memset(&mCL4, 0, sizeof mCL4);
+    const int use_tma = ss_make_maps(a, TBY, SW, &mIn, &mCL) && ss_make_maps(a, TBY, 4, &mIn4, &mCL4) ? 1 : 0;
+    const int nstrip = (a.g.nx + SBX - 1) / SBX, H = MCH * TBY - 2;
+    const long long nunits = (long long)nstrip * ((a.g.ny + H - 1) / H);
+    if (nunits > (1 << 30)) return cudaErrorInvalidValue;
+    const int blocks = (int)(nunits < (long long)per_sm * nsm ? nunits : (long long)per_sm * nsm);
+    step2d_ss2<TBY, S, MINB><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mIn4, mCL4, use_tma, nstrip, H, (int)nunits);
+    return cudaGetLastError();
+}
+
+// Shapes (rows per chunk, stages, CTAs per SM, chunks per unit); shared memory 88, 74, 109, 69, 74 and 142 KB.
+int ss2_nshapes() { return 6; }
+
+cudaError_t launch_step_2d_ss2(const StepArgs &a, int shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_ss<4, 3, 3, 10>(a, s);
+        case 2: return launch_ss<6, 3, 2, 8>(a, s);
+        case 3: return launch_ss<3, 4, 3, 12>(a, s);
+        case 4: return launch_ss<4, 3, 3, 20>(a, s);
+        case 5: return launch_ss<8, 3, 1, 6>(a, s);
+        default: return launch_ss<4, 4, 2, 10>(a, s);
+    }
+}
+
+cudaError_t ss_set_wait_limit(unsigned long long ns) {
+    return cudaMemcpyToSymbol(g_ss_wait_limit_ns, &ns, sizeof ns);
+}
+
+bool ss2_take_timeouts() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_ss_timeouts, sizeof v) != cudaSuccess) return false;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_ss_timeouts, &z, sizeof z);
+    }
+    return v != 0;
+}
+
+}  // namespace lbk

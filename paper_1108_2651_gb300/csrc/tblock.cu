@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include "lbem_internal.cuh"
+#include "tma.cuh"
 
 namespace lbk {
 
@@ -38,16 +39,6 @@ constexpr int TW = TBX + 8;  // staged columns x0-4 .. x0+TBX+3 (16-byte aligned
 // plane p row j of the t+1 stage holds global row y0 + j + in_shift(p).
 __device__ __host__ constexpr int in_shift(int p) { return p == 2 ? -1 : p == 4 ? 1 : 0; }
 
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void tb_cpa4(float *dst, const float *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src));
-}
-__device__ __forceinline__ void tb_cpa16(float *dst, const float *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
-}
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
 // Shared-memory layout of a CTA (floats; regions start on 128-byte boundaries), then one mbarrier.  The
 // medium stage holds c_L^2 and, with a heterogeneous permeability (MU), d_x ln mu and d_y ln mu after it, each
@@ -157,20 +148,6 @@ __device__ __forceinline__ void tb_issue(const StepArgs &a, int x0, int y0, floa
 
 // ---- tensor-memory-accelerator (TMA) window loads for tiles whose window needs no periodic wrap
 
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *m, int x, int y, int z, unsigned mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(smem_u32(dst)),
-        "l"(m), "r"(x), "r"(y), "r"(z), "r"(mbar)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int x, int y, unsigned mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-        ::"r"(smem_u32(dst)), "l"(m), "r"(x), "r"(y), "r"(mbar)
-        : "memory");
-}
-
 __device__ int g_tb_timeouts = 0;  // set when a bounded wait of the two-step kernel gave up
 // Limit of the bounded waits for a tile's TMA window, in ns of device time (lbem_set_wait_limit); 0 gives up at
 // once, which exercises the give-up path with ordinary, in-bounds loads.  Read once per kernel.
@@ -178,27 +155,6 @@ __device__ unsigned long long g_wait_limit_ns = 2000000000ull;
 // After giving up, a CTA still waits this long for its copies in flight to land before it exits (shared memory
 // must not be written by a copy after its CTA is gone); independent of g_wait_limit_ns.
 constexpr unsigned long long kDrainNs = 2000000000ull;
-
-// Wait for phase `parity` of the mbarrier, giving up after limit_ns of device time (at once for 0).
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity, unsigned long long limit_ns) {
-    if (limit_ns == 0) return false;
-    unsigned long long t0;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (unsigned it = 0;; it++) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 63) == 63) {
-            unsigned long long t1;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-            if (t1 - t0 > limit_ns) return false;
-        }
-    }
-}
 
 template <int TBY>
 __device__ __forceinline__ bool tb_interior(int x0, int y0, const Grid &G) {
@@ -555,27 +511,6 @@ __global__ void __launch_bounds__(NT, MINB)
         events = events_next;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
-}
-
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiled encode_fn() {
-    static EncodeTiled fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
 }
 
 // =====================================================================================================
@@ -1596,7 +1531,7 @@ static cudaError_t launch_16(const StepArgs &a, int shape, cudaStream_t s) {
 // With an anisotropic medium (FP32, no mu array) only tile shape 0.
 int tb2_nshapes(int storage, bool has_mu) {
     if (has_mu) return storage == LBEM_F32 ? 2 : 0;
-    return storage == LBEM_F32 ? 7 + rs2_nshapes() : 7;
+    return storage == LBEM_F32 ? 7 + rs2_nshapes() + ss2_nshapes() : 7;
 }
 
 cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaStream_t s) {
@@ -1611,6 +1546,7 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
                                                        : launch_tb<6, 256, 3, false, false, true>(a, s);
     if (a.med.ar != 1.f || a.med.amu != 1.f) return launch_tb<6, 256, 5, false, true>(a, s);  // anisotropic
     if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
+    if (shape >= 7 + rs2_nshapes()) return launch_step_2d_ss2(a, shape - 7 - rs2_nshapes(), s);  // sstream.cu
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)
     switch (shape) {
         case 1: return launch_tb<8, 320, 3>(a, s);
@@ -1624,17 +1560,19 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
 }
 
 cudaError_t tb_set_wait_limit(unsigned long long ns) {
-    return cudaMemcpyToSymbol(g_wait_limit_ns, &ns, sizeof ns);
+    const cudaError_t e = cudaMemcpyToSymbol(g_wait_limit_ns, &ns, sizeof ns);
+    return e != cudaSuccess ? e : ss_set_wait_limit(ns);
 }
 
 bool tb2_take_timeouts() {
+    const bool ss = ss2_take_timeouts();
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, g_tb_timeouts, sizeof v) != cudaSuccess) return false;
     if (v) {
         const int z = 0;
         cudaMemcpyToSymbol(g_tb_timeouts, &z, sizeof z);
     }
-    return v != 0;
+    return v != 0 || ss;
 }
 
 }  // namespace lbk

@@ -416,9 +416,10 @@ def test_two_step_blocking_is_bitwise_identical(lbem, shape):
     import torch
 
     probe = lbem.Solver((4, 4))
-    nsh = lbem.lbem_get_temporal_blocking(probe.h)[2]  # FP32: tile shapes, then the register-streaming kernel
+    # FP32: tile shapes 0-6, the register-streaming kernel 7-8, the strip-streaming kernel 9-14
+    nsh = lbem.lbem_get_temporal_blocking(probe.h)[2]
     probe.close()
-    assert nsh == 9
+    assert nsh == 15
     for tile_shape, graphs in [(k, g) for k in range(nsh) for g in (False, True)]:
         stream = torch.cuda.Stream() if graphs else None
         s = lbem.Solver(p.shape, stream=stream.cuda_stream if stream else None)
@@ -566,7 +567,7 @@ def test_two_step_blocking_heterogeneous_mu_is_bitwise_identical(lbem, shape):
 
 def test_two_step_blocking_rejects_bad_arguments(lbem):
     s = lbem.Solver((16, 16))
-    for steps, shape in ((0, 0), (4, 0), (2, 9), (3, 3), (2, -2)):
+    for steps, shape in ((0, 0), (4, 0), (2, 15), (3, 3), (2, -2)):
         with pytest.raises(lbem.LbemError) as e:
             lbem.lbem_set_temporal_blocking(s.h, steps, shape)
         assert e.value.status == 1
@@ -580,7 +581,7 @@ def test_two_step_blocking_full_size_matches_oracle(lbem):
     import torch
 
     res = []
-    for tile_shape in range(9):
+    for tile_shape in range(15):
         s = lbem.Solver(p.shape)
         s.set_problem(p)
         lbem.lbem_set_temporal_blocking(s.h, 2, tile_shape)

@@ -1,6 +1,7 @@
 """The bounded device-side wait gives up cleanly (failure detection without a GPU fault).
 
-The multi-step kernels wait on an mbarrier for each tile's TMA window.  With the
+The multi-step kernels wait on an mbarrier for each tile's TMA window (the strip
+kernel for each chunk of rows).  With the
 wait limit set to 0 every such wait gives up at once on ordinary, in-bounds
 loads: each CTA lets its copies in flight land (a separate bounded wait), flags
 the failure and exits, and the next lbem_sync reports LBEM_ERR_TIMEOUT.  After
@@ -16,8 +17,8 @@ from paper_1108_2651_gb300 import lbem, workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("storage,spp", [("f32", 2), ("f32", 3), ("i16b", 2)])
-def test_zero_wait_limit_reports_timeout_then_handle_recovers(lbem, storage, spp):
+@pytest.mark.parametrize("storage,spp,tile_shape", [("f32", 2, -1), ("f32", 3, -1), ("i16b", 2, -1), ("f32", 2, 9)])
+def test_zero_wait_limit_reports_timeout_then_handle_recovers(lbem, storage, spp, tile_shape):
     import torch
 
     shape = (64, 512)  # wide enough for interior tiles, whose windows are TMA loads
@@ -33,7 +34,7 @@ def test_zero_wait_limit_reports_timeout_then_handle_recovers(lbem, storage, spp
     s = lbem.Solver(shape, storage=storage)
     try:
         s.set_problem(p)
-        lbem.lbem_set_temporal_blocking(s.h, spp, -1)
+        lbem.lbem_set_temporal_blocking(s.h, spp, tile_shape)
         assert lbem.lbem_get_temporal_blocking(s.h)[0] == spp
         snap = torch.empty(lbem.lbem_info(s.h)[1], dtype=torch.uint8, device="cuda")
         lbem.lbem_save_state(s.h, snap)
