@@ -43,6 +43,7 @@ BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
 # (workload, storage, variant); the capture and its command are summarised in profiles/.  Only reported for
 # the kernel that was captured.
 NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 433.764864e6 + 300.201472e6,
+               ("het2d_4096", "f32", "tb2-10"): 433.149440e6 + 284.277760e6,
                ("het2d_4096", "f16", "tb2-0"): 238.282240e6 + 128.542464e6,
                ("het2d_4096", "i16b", "tb2-0"): 264.385536e6 + 150.971648e6,
                # dram__bytes.sum.per_second x gpu__time_duration.sum (6.657849 TB/s x 174.752 us), step2d_gen
@@ -1001,7 +1002,11 @@ def main():
     peak, peak_kind = measured_peak_gbs()
     bps = (72 if disp else BYTES_PER_SITE[args.storage]) if p.D == 2 else 172
     achieved = bps * nsite / (ms_per_launch * 1e-3) / 1e9
-    if spp >= 2:
+    if spp == 2 and args.storage == "f32" and tile_shape >= 9:
+        kname, kid = f"step2d_ss2 (strip streaming, tile shape {tile_shape}, 2 steps per launch)", f"tb2-{tile_shape}"
+    elif spp == 2 and args.storage == "f32" and tile_shape >= 7:
+        kname, kid = f"step2d_rs2 (register streaming, tile shape {tile_shape}, 2 steps per launch)", f"tb2-{tile_shape}"
+    elif spp >= 2:
         kern = {2: "step2d_tb2", 3: "step2d_tb3"}[spp] + ("" if args.storage == "f32" else f"h<{args.storage}>")
         kname, kid = f"{kern} (tile shape {tile_shape}, {spp} steps per launch)", f"tb{spp}-{tile_shape}"
     else:

@@ -92,7 +92,7 @@ void lbem_destroy(lbem_t *h);
 lbem_status lbem_set_stream(lbem_t *h, void *stream);
 
 /* Wait for all work enqueued on the handle's stream; reports deferred device errors, and LBEM_ERR_TIMEOUT
- * if a shared-memory tile load of the two-step kernel (lbem_set_temporal_blocking) gave up waiting. */
+ * if a shared-memory tile or chunk load of a two-step kernel (lbem_set_temporal_blocking) gave up waiting. */
 lbem_status lbem_sync(lbem_t *h);
 
 /* Limit of the bounded device-side waits on the current device (all handles on it): a CTA of the two- and
@@ -243,7 +243,12 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * selects the tile (128 sites wide) height, threads per CTA and CTAs per SM: 0 = 6 rows, 256 threads, 5
  * per SM (the default, also -1); 1 = 8 rows, 320, 3; 2 = 8 rows, 352, 3; 3 = 10 rows, 384, 3; 4 = 5 rows,
  * 224, 5; 5 = 4 rows, 192, 6; 6 = 14 rows, 512, 2; FP32 only: 7, 8 = no tiles: each warp streams a
- * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM).  With
+ * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM); 9 - 14 =
+ * strip streaming: persistent CTAs take units of rows of a 128-column strip from a queue and stream them in
+ * chunks through shared-memory stages (a producer warp loads chunks ahead by TMA), computing step t+1 one row
+ * behind step t (chunk rows, stages, CTAs per SM, chunks per unit: 9 = 4, 4, 2, 16; 10 = 4, 3, 3, 16;
+ * 11 = 6, 3, 2, 12; 12 = 3, 4, 3, 24; 13 = 4, 3, 3, 32; 14 = 3, 4, 3, 12).  With -1 (or never set), an FP32
+ * grid of uniform mu with at least 12 000 000 sites takes shape 10, any other shape 0.  With
  * a heterogeneous mu (FP32; the two grad ln mu planes are staged beside c_L^2, 52 instead of 104 bytes per
  * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, and 1 = 14 rows, 512, 2 exist; a larger
  * shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) without walls
@@ -253,8 +258,9 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * LBEM_ERR_ARG for values outside the current handle's set. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 
-/* Steps per launch in effect (2 or 3 only where that kernel is enabled and applies), the tile shape (as set
- * or autotuned) and the number of tile shapes of the selected steps per pass; any pointer may be NULL. */
+/* Steps per launch in effect (2 or 3 only where that kernel is enabled and applies), the tile shape (the one
+ * launched when two steps per launch are in effect, else as set or autotuned) and the number of tile shapes of
+ * the selected steps per pass; any pointer may be NULL. */
 lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int *tile_shape, int *nshapes);
 
 /* Use (on != 0) or not CUDA-graph replay of runs of steps in lbem_step. */

@@ -503,6 +503,7 @@ struct lbem {
     int variant = 0;
     int tblock = 2;  // steps per pass (lbem_set_temporal_blocking)
     int tb_shape = 0;  // tile shape of the two-step kernel
+    bool tb_shape_set = false;  // set by lbem_set_temporal_blocking (a shape >= 0) or lbem_autotune; else by grid size
     // watchdog (lbem_set_watchdog)
     int wd_every = 0;
     double wd_growth = 0.0, wd_last = -1.0;
