@@ -414,8 +414,11 @@ lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);
  * or 4 blocks per SM), 128 x 8, 128 x 10 and 128 x 12 sites, over a packed copy
  * of the members' states with periodic halos that the batch keeps (filled at
  * the start of a call, written back into the members' buffers at its end; an
- * odd step count takes one single step first).  Every variant gives the same
- * bits as each member stepped alone. */
+ * odd step count takes one single step first); 14, 15 advance two steps per
+ * launch over the same packed copy by strip streaming (persistent CTAs take
+ * units of 46 or 34 rows of a member's 128-column strip from a queue and stream
+ * them in chunks of 4 or 3 rows through shared-memory stages).  Every variant
+ * gives the same bits as each member stepped alone. */
 lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out);
 lbem_status lbem_batch_step(lbem_batch_t *b, int nsteps);
 /* Time every variant over trial_steps steps (members' states saved and restored) and keep the fastest; *best (may

@@ -411,6 +411,11 @@ struct lbem_batch {
     size_t tiles_cap = 0;
     long long ntiles = 0;
     int tb_rows = 0;
+    // the strip kernel's units (sstream.cu) and its work queue (two counters, zero between launches)
+    lbk::BatchUnit *d_units = nullptr;
+    size_t units_cap = 0;
+    int nunits = 0;
+    int *d_sched = nullptr;
     // the two-step kernels' packed states with halos: two population buffers and c_L^2, [rows][W] per plane, member m
     // from packed row r0[m] (d_r0, n + 1 entries)
     float *d_pack = nullptr;  // 11 planes: buffer 0 (5), buffer 1 (5), c_L^2 (1)
@@ -442,11 +447,13 @@ using namespace lbk;
 // variants 7, 8: linear mapping over the padded plane (uncapped / capped for 5 blocks per SM)
 // Variants: R = 1, 2, 4 rows per warp; 0 one site per thread; -1 persistent register pipeline; -5, -6 R = 1
 // capped for 5 / 6 blocks per SM; -7, -8 linear over each member's padded plane (uncapped / 5 blocks per SM);
-// 100 + k: two steps per launch through shared-memory tiles, tile shape k (launch_batch_tb2).
-static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8, 100, 101, 102, 103, 104};
+// 100 + k: two steps per launch through shared-memory tiles, tile shape k (launch_batch_tb2); 200 + k: two steps per
+// launch by strip streaming, shape k (launch_batch_ss2).
+static const int kRowsB[] = {1, 2, 4, 0, -1, -5, -6, -7, -8, 100, 101, 102, 103, 104, 200, 201};
 static const int kBatchVariants = (int)(sizeof(kRowsB) / sizeof(kRowsB[0]));
 static const int kLinVariant = 7;  // the single-step kernel that takes the odd step of a two-step variant
 static bool two_step(int variant) { return kRowsB[variant] >= 100; }
+static bool strip_variant(int variant) { return kRowsB[variant] >= 200; }
 
 static void drop_batch_graph(lbem_batch_t *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -455,25 +462,23 @@ static void drop_batch_graph(lbem_batch_t *b) {
     b->graph_variant = -1;
 }
 
-// Tile tables of the two-step kernel (tiles of 128 x rows sites) and every member's step arguments for both
-// buffer parities (args[2 k]: state in buffer a, written to b; args[2 k + 1]: the reverse).
-static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
+// Every member's step arguments for both buffer parities (args[2 k]: state in buffer a, written to b; args[2 k + 1]:
+// the reverse) and the packed layout of the two-step kernels: member k from packed row r0[k], its rows and two halo
+// rows on either side, rows W floats wide so that every window (member columns x0 - 4 .. x0 + 131 of a 128-column
+// tile or strip) lies inside a row.  Uploads the arguments and r0, (re)allocates the packed buffers; r0 to the caller.
+static lbem_status upload_packed_layout(lbem_batch_t *b, std::vector<int> &r0) {
     std::vector<StepArgs> args(2 * (size_t)b->n);
-    std::vector<long long> ts(b->n + 1, 0);
-    std::vector<int> r0(b->n + 1, 0);
+    r0.assign(b->n + 1, 0);
     int maxw = 0;
     for (int k = 0; k < b->n; k++) {
         lbem_t *h = b->members[k];
         args[2 * k] = step_args(h, h->cur);
         args[2 * k + 1] = step_args(h, h->cur ^ 1);
-        const long long ntx = (h->grid.nx + 127) / 128, nty = (h->grid.ny + rows - 1) / rows;
-        ts[k + 1] = ts[k] + ntx * nty;
         if ((long long)r0[k] + h->grid.ny + 4 > 0x7fffffffLL)
             return fail(LBEM_ERR_ARG, "lbem_batch: members too tall for the packed layout");
-        r0[k + 1] = r0[k] + h->grid.ny + 4;  // the member's rows and two halo rows on either side
-        maxw = std::max(maxw, (int)(ntx * 128));
+        r0[k + 1] = r0[k] + h->grid.ny + 4;
+        maxw = std::max(maxw, (h->grid.nx + 127) / 128 * 128);
     }
-    // packed layout: every tile window (member columns x0 - 4 .. x0 + 131) inside a row
     const int W = round_up(maxw + 8, 32);
     const long long prows = r0[b->n];
     const size_t need = sizeof(float) * 11 * (size_t)prows * W;
@@ -492,6 +497,31 @@ static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
     b->pack_W = W;
     b->pack_rows = prows;
     LBEM_CUDA(cudaMemcpyAsync(b->d_r0, r0.data(), sizeof(int) * (b->n + 1), cudaMemcpyHostToDevice, b->stream));
+    LBEM_CUDA(cudaMemcpyAsync(b->d_args, args.data(), sizeof(StepArgs) * args.size(), cudaMemcpyHostToDevice,
+                              b->stream));
+    LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vectors go out of scope
+    return LBEM_OK;
+}
+
+// Rows of member h that hold a source or receiver.
+static std::vector<char> event_rows(const lbem_t *h) {
+    const int nx = h->grid.nx, ny = h->grid.ny;
+    std::vector<char> evrow(ny, 0);
+    for (long long site : h->src_site) evrow[(site / nx) % ny] = 1;
+    for (long long site : h->rec_site) evrow[(site / nx) % ny] = 1;
+    return evrow;
+}
+
+// Tile tables of the two-step tile kernel (tiles of 128 x rows sites) over the packed layout.
+static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
+    std::vector<int> r0;
+    lbem_status st = upload_packed_layout(b, r0);
+    if (st != LBEM_OK) return st;
+    std::vector<long long> ts(b->n + 1, 0);
+    for (int k = 0; k < b->n; k++) {
+        const lbem_t *h = b->members[k];
+        ts[k + 1] = ts[k] + (long long)((h->grid.nx + 127) / 128) * ((h->grid.ny + rows - 1) / rows);
+    }
     const long long total = ts[b->n];
     // tile descriptors: member, origin, packed row of the window's first c_L^2 row, size, and whether the window's
     // rows (periodic) hold a source or receiver
@@ -499,9 +529,7 @@ static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
     for (int k = 0; k < b->n; k++) {
         lbem_t *h = b->members[k];
         const int nx = h->grid.nx, ny = h->grid.ny, ntx = (nx + 127) / 128;
-        std::vector<char> evrow(ny, 0);
-        for (long long site : h->src_site) evrow[(site / nx) % ny] = 1;
-        for (long long site : h->rec_site) evrow[(site / nx) % ny] = 1;
+        const std::vector<char> evrow = event_rows(h);
         for (long long u = ts[k]; u < ts[k + 1]; u++) {
             const int local = (int)(u - ts[k]), ty = local / ntx, tx = local - ty * ntx;
             BatchTile d;
@@ -527,8 +555,6 @@ static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
         }
         b->tiles_cap = tl.size();
     }
-    LBEM_CUDA(cudaMemcpyAsync(b->d_args, args.data(), sizeof(StepArgs) * args.size(), cudaMemcpyHostToDevice,
-                              b->stream));
     LBEM_CUDA(cudaMemcpyAsync(b->d_tiles, tl.data(), sizeof(BatchTile) * tl.size(), cudaMemcpyHostToDevice,
                               b->stream));
     LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vectors go out of scope
@@ -537,9 +563,58 @@ static lbem_status upload_tile_tables(lbem_batch_t *b, int rows) {
     return LBEM_OK;
 }
 
+// Unit table of the strip kernel over the packed layout: per member and 128-column strip, runs of
+// chunks * rows - 2 rows (the strip kernel's step t covers rows ys-1 .. ye in whole chunks), with the member's event
+// tables; tall units first so that the ragged ones come last in the queue.
+static lbem_status upload_unit_tables(lbem_batch_t *b, int shape) {
+    std::vector<int> r0;
+    lbem_status st = upload_packed_layout(b, r0);
+    if (st != LBEM_OK) return st;
+    const int tby = batch_ss2_rows(shape), H = batch_ss2_chunks(shape) * tby - 2;
+    std::vector<BatchUnit> ul;
+    for (int k = 0; k < b->n; k++) {
+        const lbem_t *h = b->members[k];
+        const int nx = h->grid.nx, ny = h->grid.ny;
+        for (int ys = 0; ys < ny; ys += H)
+            for (int x0 = 0; x0 < nx; x0 += 128) {
+                BatchUnit u;
+                u.m = k;
+                u.x0 = x0;
+                u.ys = ys;
+                u.ye = std::min(ys + H, ny);
+                u.prow0 = r0[k];
+                u.nx = nx;
+                u.ny = ny;
+                u.pad = 0;
+                u.rowptr = h->nev ? h->d_rowptr : nullptr;
+                u.ev = h->d_ev;
+                ul.push_back(u);
+            }
+    }
+    std::stable_sort(ul.begin(), ul.end(),
+                     [](const BatchUnit &a, const BatchUnit &c) { return a.ye - a.ys > c.ye - c.ys; });
+    if (ul.size() > (size_t)(1 << 30)) return fail(LBEM_ERR_ARG, "lbem_batch: too many units");
+    if (b->units_cap < ul.size()) {
+        cudaFree(b->d_units);
+        b->d_units = nullptr;
+        b->units_cap = 0;
+        if (cudaMalloc((void **)&b->d_units, sizeof(BatchUnit) * ul.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBEM_ERR_NOMEM, "lbem_batch: no room for the unit table");
+        }
+        b->units_cap = ul.size();
+    }
+    LBEM_CUDA(cudaMemcpyAsync(b->d_units, ul.data(), sizeof(BatchUnit) * ul.size(), cudaMemcpyHostToDevice,
+                              b->stream));
+    LBEM_CUDA(cudaStreamSynchronize(b->stream));  // host vector goes out of scope
+    b->nunits = (int)ul.size();
+    return LBEM_OK;
+}
+
 static lbem_status upload_tables(lbem_batch_t *b, int variant) {
     if (two_step(variant)) {  // the pair kernel's tiles, and the linear single-step kernel's table for an odd step
-        lbem_status st = upload_tile_tables(b, batch_tb2_rows(kRowsB[variant] - 100));
+        lbem_status st = strip_variant(variant) ? upload_unit_tables(b, kRowsB[variant] - 200)
+                                                : upload_tile_tables(b, batch_tb2_rows(kRowsB[variant] - 100));
         if (st != LBEM_OK) return st;
         variant = kLinVariant;
     }
@@ -644,8 +719,11 @@ static cudaError_t enqueue_batch(lbem_batch_t *b, int variant, int nsteps, int *
         cudaError_t e = launch_batch_pack(b->d_args, par, b->d_r0, b->n, b->pack_rows, pk, 0, false, b->stream);
         int j = 0;
         for (; e == cudaSuccess && toff + 2 <= nsteps; toff += 2, j++, n++)
-            e = launch_batch_tb2(b->d_args, b->d_tiles, b->ntiles, b->d_t0, toff, j & 1, pk, b->pack_rows,
-                                 kRowsB[variant] - 100, b->stream);
+            e = strip_variant(variant)
+                    ? launch_batch_ss2(b->d_args, b->d_units, b->nunits, b->d_sched, b->d_t0, toff, j & 1, pk,
+                                       b->pack_rows, kRowsB[variant] - 200, b->stream)
+                    : launch_batch_tb2(b->d_args, b->d_tiles, b->ntiles, b->d_t0, toff, j & 1, pk, b->pack_rows,
+                                       kRowsB[variant] - 100, b->stream);
         if (e == cudaSuccess)
             e = launch_batch_pack(b->d_args, par, b->d_r0, b->n, b->pack_rows, pk, j & 1, true, b->stream);
         if (e != cudaSuccess) return e;
@@ -694,6 +772,8 @@ lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_args, sizeof(StepArgs) * 2 * (size_t)n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_r0, sizeof(int) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_t0, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_sched, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMemset(b->d_sched, 0, sizeof(int) * 2);
     if (e != cudaSuccess) {
         cudaGetLastError();
         lbem_batch_destroy(b);
@@ -829,6 +909,8 @@ void lbem_batch_destroy(lbem_batch_t *b) {
     cudaFree(b->d_t0);
     cudaFree(b->d_args);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_units);
+    cudaFree(b->d_sched);
     cudaFree(b->d_r0);
     cudaFree(b->d_pack);
     delete b;

@@ -596,6 +596,20 @@ cudaError_t launch_batch_tb2(const StepArgs *args, const BatchTile *tiles, long 
                              int toff, int par, const BatchPacked &pk, long long rows, int shape, cudaStream_t s);
 cudaError_t launch_batch_pack(const StepArgs *args, int par, const int *r0, int n, long long rows,
                               const BatchPacked &pk, int which, bool unpack, cudaStream_t s);
+// One unit of the batch's strip-streaming kernel (sstream.cu): member m, its 128-column strip from column x0 and rows
+// ys .. ye-1, its packed row prow0 (member row -2) and size, and the member's event tables (row pointer and records;
+// null without events).  Built on the host, tall units first.
+struct __align__(16) BatchUnit {
+    int m, x0, ys, ye;
+    int prow0, nx, ny, pad;
+    const int *rowptr;
+    const Event *ev;
+};
+int batch_ss2_nshapes();
+int batch_ss2_rows(int shape);    // chunk rows (TBY) of a shape
+int batch_ss2_chunks(int shape);  // chunks of a full unit
+cudaError_t launch_batch_ss2(const StepArgs *args, const BatchUnit *units, int nunits, int *sched, const long long *t0p,
+                             int toff, int par, const BatchPacked &pk, long long rows, int shape, cudaStream_t s);
 cudaError_t launch_init_2d(const lbem_t *h, const float *E, const float *B, cudaStream_t s);
 cudaError_t launch_fields_2d(const lbem_t *h, float *E, float *B, cudaStream_t s);
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s);

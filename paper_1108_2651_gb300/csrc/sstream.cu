@@ -47,6 +47,23 @@ constexpr unsigned long long kSsDrainNs = 2000000000ull;  // after giving up: wa
 // a TMA destination), S side buffers of the periodic images of an edge strip (six planes of TBY rows of 4), the
 // step-(t+1) ring (six planes of M rows of SW: populations 0..4, then c_L^2), the chunk descriptors, then two
 // mbarriers per stage (full: staged; empty: read by every consumer warp).
+// The sources and receivers of a chunk's rows s-1 .. s+TBY-1 (window rows 0 .. TBY), staged in shared memory so that
+// the site updates match against a short list instead of walking the event tables: the records of the tables' row
+// range, copied asynchronously by the producer (tracked by the stage's mbarrier), and per window row the first
+// record of that row (b[i]; b[TBY + 1] = n).  At most SS_EMAX records; a chunk with more, or whose window wraps
+// periodically, is not staged.
+constexpr int SS_EMAX = 12, SS_RMAX = 10;
+struct SsEvList {
+    int n, b[SS_RMAX + 1];
+    Event rec[SS_EMAX];
+};
+// A chunk's descriptor slot: two int4 (d0: the unit's x0, ys, ye and k | flags; d1: the batch member's m, packed row,
+// size) and the chunk's event list.
+struct SsDesc {
+    int4 d0, d1;
+    SsEvList ev;
+};
+
 template <int TBY, int S>
 struct SsGeom {
     static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
@@ -55,8 +72,8 @@ struct SsGeom {
     static constexpr int EPL = up32(4 * TBY), ESTAGE = 6 * EPL;
     static constexpr int PL_P = M * SW;
     static constexpr int IN_SZ = S * STAGE, E_SZ = S * ESTAGE, P_SZ = up32(6 * PL_P);
-    static constexpr int DS = S + 2;  // chunk descriptors (int4) after the ring, then the mbarriers
-    static constexpr int SZ = IN_SZ + E_SZ + P_SZ + 4 * DS;
+    static constexpr int DS = S + 2;  // chunk descriptor slots (SsDesc) after the ring, then the mbarriers
+    static constexpr int SZ = IN_SZ + E_SZ + P_SZ + DS * (int)(sizeof(SsDesc) / 4);
     static constexpr size_t BYTES = sizeof(float) * SZ + 2 * S * sizeof(unsigned long long);
     static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * TBY * SW, E_BYTES = sizeof(float) * 6 * TBY * 4;
 };
@@ -136,11 +153,75 @@ __device__ __forceinline__ void ss_issue(const StepArgs &a, int x0, int xm, int 
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
 }
 
+// site_events (source current at column x of window row i and time t, receiver writes where owned) from a staged
+// list: the same arithmetic in the same order.  Uniform mu only.
+__device__ __forceinline__ float ss_list_events(const StepArgs &a, const SsEvList *L, int i, int x, long long t,
+                                                bool owned, float g0, float g1, float g2, float g3, float g4,
+                                                float cl) {
+    float shat = 0.f;
+    for (int j = L->b[i]; j < L->b[i + 1]; j++) {
+        const Event ev = L->rec[j];
+        if (ev.x != x) continue;
+        if (ev.kind == 0) {
+            if (ev.comp == 2 && t < a.evt.nt)
+                shat = __fsub_rn(shat, __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t));
+        } else if (owned && t < a.evt.cap) {
+            const float s = ((g0 + g1) + (g2 + g3)) + g4;
+            a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+        }
+    }
+    return shat;
+}
+
+// Whether window row i of a staged list holds an event.
+__device__ __forceinline__ bool ss_list_has_row(const SsEvList *L, int i) { return L->b[i + 1] > L->b[i]; }
+
+// The row pointers of rows ys-2+q (q = lane + 32 j, j < 3) of a unit, -1 outside 0 .. ny.
+__device__ __forceinline__ void ss_load_rowptr(const int *rowptr, int ny, int ys, int (&rp)[3]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int r = ys - 2 + lane + 32 * j;
+        rp[j] = rowptr && r >= 0 && r <= ny ? __ldg(rowptr + r) : -1;
+    }
+}
+
+// For chunk k of a unit whose row pointers are rp (rows ys-2 ..): whether its rows s-1 .. s+TBY may hold an event
+// (bit 25 of the descriptor), and whether they are staged into L (bit 26): the window's row boundaries written, the
+// records copied asynchronously, each lane's copies tracked by the stage's mbarrier.  Every lane of the producer warp
+// calls it; it ends with __syncwarp, before the producer's arrival on the stage.
+template <int TBY>
+__device__ __forceinline__ int ss_stage_chunk(const int (&rp)[3], const Event *ev, bool has_events, int ny, int s,
+                                              int k, SsEvList *L, unsigned mbar) {
+    const int lane = threadIdx.x & 31;
+    if (!has_events) return 0;
+    const int q = k * TBY + (lane <= TBY + 1 ? lane : 0);  // window row boundary `lane` <-> row s-1+lane
+    const int v0 = __shfl_sync(0xffffffffu, rp[0], q & 31), v1 = __shfl_sync(0xffffffffu, rp[1], q & 31),
+              v2 = __shfl_sync(0xffffffffu, rp[2], q & 31);
+    const int v = (q >> 5) == 0 ? v0 : (q >> 5) == 1 ? v1 : v2;
+    const int b0 = __shfl_sync(0xffffffffu, v, 0), bend = __shfl_sync(0xffffffffu, v, TBY + 1);
+    const bool inside = s - 1 >= 0 && s + TBY <= ny && k * TBY + TBY + 1 < 96;
+    if (!inside) return 1 << 25;  // not staged: the site updates walk the tables
+    const int n = bend - b0;
+    if (n == 0) return 0;
+    if (n > SS_EMAX) return 1 << 25;
+    if (lane <= TBY + 1) L->b[lane] = v - b0;
+    if (lane == 0) L->n = n;
+    if (lane < n) {
+        tb_cpa16(reinterpret_cast<float *>(&L->rec[lane]), reinterpret_cast<const float *>(ev + b0 + lane));
+        asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];\n" ::"r"(mbar) : "memory");
+    }
+    __syncwarp();
+    return 3 << 25;
+}
+
 // Four site updates at global row gy, columns x0+4*lane.. (collide2d with the sites' sources and receivers where
-// EV, else collide2d_free), from the pulled populations q[0..4] and c_L^2.
+// EV, else collide2d_free), from the pulled populations q[0..4] and c_L^2; with a staged list `el` the events come
+// from it (window row li).
 template <bool EV>
 __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[5], float4 cl, int x0, int gy,
-                                           long long t, bool owned, float4 (&o)[5]) {
+                                           long long t, bool owned, float4 (&o)[5], const SsEvList *el = nullptr,
+                                           int li = 0) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -150,8 +231,9 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
         Out5 r;
         if (EV) {
             const int gx = x0 + 4 * lane + k;
-            const float shat = site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t,
-                                           owned && gx < G.nx && gy < G.ny, q0, q1, q2, q3, q4, ck);
+            const bool own = owned && gx < G.nx && gy < G.ny;
+            const float shat = el ? ss_list_events(a, el, li, wrapi(gx, G.nx), t, own, q0, q1, q2, q3, q4, ck)
+                                  : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck);
             r = collide2d(q0, q1, q2, q3, q4, ck, shat);
         } else {
             r = collide2d_free(q0, q1, q2, q3, q4, ck);
@@ -189,7 +271,8 @@ __device__ __forceinline__ bool ss_row_events(const StepArgs &a, int gy) {
 // there.
 template <int TBY, int S, bool EV>
 __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, const float *es, int emode, float *P,
-                                          int x0, int ys, int ye, int r, int w, int u, long long t) {
+                                          int x0, int ys, int ye, int r, int w, int u, long long t,
+                                          const SsEvList *el) {
     using Gm = SsGeom<TBY, S>;
     constexpr int M = Gm::M, PP = Gm::PL_P;
     const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
@@ -197,7 +280,7 @@ __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, co
     ss_pull(st, Gm::PL_IN, w, c, q, cl);
     if (emode == 1 && lane == 0) q[1].x = es[Gm::EPL + w * 4 + 3];        // column x0-1 = nx-1
     if (emode == 2 && lane == 31) q[3].w = es[3 * Gm::EPL + w * 4 + 0];   // column x0+128 = 0
-    ss_update4<EV>(a, q, cl, x0, r, t, r >= ys && r < ye, o);
+    ss_update4<EV>(a, q, cl, x0, r, t, r >= ys && r < ye, o, el, w + 1);
     const int s0 = u % M, s2 = s0 == M - 1 ? 0 : s0 + 1, s4 = s0 == 0 ? M - 1 : s0 - 1;
     float *p0 = P + s0 * SW + c;
     sts4(p0, o[0]);
@@ -213,7 +296,7 @@ __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, co
 // `es` the columns outside the grid come from there.
 template <int TBY, int S>
 __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, const float *es, int emode, float *P,
-                                        int x0, int s, int p, bool events, long long t) {
+                                        int x0, int s, int p, bool events, long long t, const SsEvList *el) {
     using Gm = SsGeom<TBY, S>;
     const int lane = threadIdx.x & 31;
     if (lane >= 2 * TBY) return;
@@ -225,7 +308,9 @@ __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, cons
     };
     const float q0 = v(0, cc), q1 = v(1, cc - 1), q2 = v(2, cc), q3 = v(3, cc + 1), q4 = v(4, cc), ck = v(5, cc);
     float shat = 0.f;
-    if (events && ss_row_events(a, r))
+    if (el)
+        shat = ss_list_events(a, el, w + 1, wrapi(x0 - 4 + cc, a.g.nx), t, false, q0, q1, q2, q3, q4, ck);
+    else if (events && ss_row_events(a, r))
         shat = site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck);
     const Out5 ro = collide2d(q0, q1, q2, q3, q4, ck, shat);
     const int s0 = (p * TBY + w + 1) % Gm::M;
@@ -237,13 +322,14 @@ __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, cons
 
 // Step t+1 on global row rb (ring row ub), written as 16-byte streaming stores.
 template <int TBY, int S, bool EV>
-__device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int x0, int rb, int ub, long long t) {
+__device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int x0, int rb, int ub, long long t,
+                                          const SsEvList *el, int w) {
     using Gm = SsGeom<TBY, S>;
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
     float4 q[5], cl, o[5];
     ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl);
-    ss_update4<EV>(a, q, cl, x0, rb, t + 1, true, o);
+    ss_update4<EV>(a, q, cl, x0, rb, t + 1, true, o, el, w);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
         float4 *op = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)rb * G.pitch + x0 +
                                                 4 * lane);
@@ -315,7 +401,7 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
     extern __shared__ __align__(1024) float sm[];
     float *E = sm + Gm::IN_SZ;
     float *P = E + Gm::E_SZ;
-    int4 *desc = reinterpret_cast<int4 *>(P + Gm::P_SZ);
+    SsDesc *desc = reinterpret_cast<SsDesc *>(P + Gm::P_SZ);
     unsigned long long *mb = reinterpret_cast<unsigned long long *>(desc + DS);  // full[S], then empty[S]
     const Grid &G = a.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -335,25 +421,15 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
             asm volatile("prefetch.tensormap [%0];\n" ::"l"(m) : "memory");
         }
         int cK = 0, ck = 0, cx0 = 0, cys = 0, cye = 0, cxm = 0;
-        unsigned cmask = 0;      // chunks of the current unit whose rows s-1 .. s+TBY may hold events
-        int nu = 0, nlo = 0, nhi = 0;  // the next unit, and this lane's row pointers around its chunk `lane`
+        int nu = 0, rpc[3], rpn[3];  // the next unit; row pointers of the current and the next unit (rows ys-2 ..)
         auto fetch_next = [&]() {
             int u = 0;
             if (lane == 0) u = atomicAdd(a.sched, 1);
             nu = __shfl_sync(0xffffffffu, u, 0);
-            nlo = nhi = 0;
-            if (nu < U.nunits && a.evt.rowptr) {
+            if (nu < U.nunits && a.evt.rowptr) {  // loaded now, used when the unit starts
                 int x0, ys, ye;
                 ss_unit(U, G.ny, nu, x0, ys, ye);
-                const int s = ys - 1 + lane * TBY;
-                if (lane < (ye - ys + 2 + TBY - 1) / TBY) {
-                    if (s - 1 >= 0 && s + TBY + 1 <= G.ny) {
-                        nlo = __ldg(a.evt.rowptr + s - 1);
-                        nhi = __ldg(a.evt.rowptr + s + TBY + 1);
-                    } else {
-                        nhi = 1;  // rows that wrap: taken as holding events
-                    }
-                }
+                ss_load_rowptr(a.evt.rowptr, G.ny, ys, rpn);
             }
         };
         fetch_next();
@@ -369,16 +445,19 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                 cK = (cye - cys + 2 + TBY - 1) / TBY;  // step-t chunks: rows ys-1 .. ys-2+K*TBY (through ye)
                 cxm = ss_xmode(G, cx0);
                 ck = 0;
-                cmask = __ballot_sync(0xffffffffu, nlo != nhi);
+#pragma unroll
+                for (int j = 0; j < 3; j++) rpc[j] = rpn[j];
                 fetch_next();
             }
             int4 d = make_int4(0, 0, 0, 0);
             if (ck < cK) {
                 const int s = cys - 1 + ck * TBY, mode = ss_chunk_mode<TBY>(G, cxm, s, tma);
-                d = make_int4(cx0, cys, cye, ck | mode << 16 | cxm << 20 | 1 << 24 | (int)((cmask >> ck) & 1u) << 25);
+                d = make_int4(cx0, cys, cye, ck | mode << 16 | cxm << 20 | 1 << 24);
+                d.w |= ss_stage_chunk<TBY>(rpc, a.evt.ev, a.evt.rowptr != nullptr, G.ny, s, ck, &desc[c % DS].ev,
+                                           full0 + 8 * (c % S));
                 ck++;
             }
-            if (lane == 0) desc[c % DS] = d;
+            if (lane == 0) desc[c % DS].d0 = d;
             if (!ss_valid(d)) {  // end of the stream: the consumers find the end descriptor
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8 * (c % S)) : "memory");
@@ -399,31 +478,35 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
         const long long t = a.t;
         for (int p = 0;; p++) {
             const bool ok = mbar_wait(full0 + 8 * (p % S), (unsigned)(p / S) & 1u, wait_limit);
-            const int4 da = desc[p % DS], db = desc[(p + DS - 1) % DS];
+            const int4 da = desc[p % DS].d0, db = desc[(p + DS - 1) % DS].d0;
             const bool va = ok && ss_valid(da), vb = p >= 1 && ss_valid(db);
+            const SsEvList *ela = (da.w >> 26) & 1 ? &desc[p % DS].ev : nullptr;
+            const SsEvList *elb = (db.w >> 26) & 1 ? &desc[(p + DS - 1) % DS].ev : nullptr;
             const float *st = sm + (p % S) * Gm::STAGE, *es = E + (p % S) * Gm::ESTAGE;
             const int emode = ((da.w >> 16) & 15) == 1 ? (da.w >> 20) & 15 : 0, s = da.y - 1 + (da.w & 0xffff) * TBY;
             if (warp < TBY) {
                 if (va) {
                     const int r = s + warp;
-                    if (ss_events(da) && ss_row_events(a, r))
-                        ss_step_a<TBY, S, true>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t);
+                    if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(a, r)))
+                        ss_step_a<TBY, S, true>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                                                ela);
                     else
-                        ss_step_a<TBY, S, false>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t);
+                        ss_step_a<TBY, S, false>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                                                 nullptr);
                 }
             } else if (warp < 2 * TBY) {
                 const int w = warp - TBY;
                 if (vb) {
                     const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
                     if (rb >= db.y && rb < db.z) {
-                        if (ss_events(db) && ss_row_events(a, rb))
-                            ss_step_b<TBY, S, true>(a, P, db.x, rb, (p - 1) * TBY + w, t);
+                        if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(a, rb)))
+                            ss_step_b<TBY, S, true>(a, P, db.x, rb, (p - 1) * TBY + w, t, elb, w);
                         else
-                            ss_step_b<TBY, S, false>(a, P, db.x, rb, (p - 1) * TBY + w, t);
+                            ss_step_b<TBY, S, false>(a, P, db.x, rb, (p - 1) * TBY + w, t, nullptr, w);
                     }
                 }
             } else if (va) {
-                ss_ring<TBY, S>(a, st, es, emode, P, da.x, s, p, ss_events(da), t);
+                ss_ring<TBY, S>(a, st, es, emode, P, da.x, s, p, ss_events(da), t, ela);
             }
             if (va && (warp < TBY || warp == 2 * TBY)) {  // this warp has read the stage: release it to the producer
                 __syncwarp();
@@ -521,6 +604,308 @@ cudaError_t launch_step_2d_ss2(const StepArgs &a, int shape, cudaStream_t s) {
         case 5: return launch_ss<3, 4, 3, 12>(a, s);
         default: return launch_ss<4, 4, 2, 16>(a, s);
     }
+}
+
+// =====================================================================================================
+// The batch over its packed states (the layout of step2d_batch_tb2: member m from packed row r0[m], packed row
+// r0[m] + 2 + y <-> member row y in [-2, ny + 1], packed column x + 4 <-> member column x, two rows and columns of
+// periodic images around each member).  The strip kernel's phases run over units of one member each; every chunk is
+// six TMA boxes of the packed input (the images make a window never wrap), and step t+1 writes each output site and,
+// within two of an edge, its images, so the next launch finds the halo current.  The site updates are those of
+// step2d_ss2, so every member's result is bit-identical to its single steps.
+
+// Step t+1 on member row rb (ring row ub), written to the packed output with the row's and the lane's images.
+template <int TBY, int S, bool EV>
+__device__ __forceinline__ void ss_step_b_packed(const StepArgs &a, const float *P, int x0, int rb, int ub, long long t,
+                                                 float *out, long long pplane, int W, int prow0, int nx, int ny,
+                                                 const SsEvList *el, int w) {
+    using Gm = SsGeom<TBY, S>;
+    const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
+    float4 q[5], cl, o[5];
+    ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl);
+    ss_update4<EV>(a, q, cl, x0, rb, t + 1, true, o, el, w);
+    const int xs = x0 + 4 * lane;  // the lane's first site
+    if (xs >= nx) return;
+    auto row_at = [&](int yy) { return out + (long long)(prow0 + 2 + yy) * W + 4; };
+    auto store_row = [&](int yy) {
+        float *r = row_at(yy) + xs;
+        if (xs + 3 < nx) {
+#pragma unroll
+            for (int p = 0; p < 5; p++) __stcs(reinterpret_cast<float4 *>(r + p * pplane), o[p]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                if (xs + j < nx)
+#pragma unroll
+                    for (int p = 0; p < 5; p++) r[p * pplane + j] = get(o[p], j);
+        }
+    };
+    store_row(rb);
+    for (int yy = rb + ny; yy <= ny + 1; yy += ny) store_row(yy);  // images in the upper halo rows
+    for (int yy = rb - ny; yy >= -2; yy -= ny) store_row(yy);      // and in the lower ones
+    if (xs < 2 || xs + 3 >= nx - 2) {  // sites within two of the left or right edge: their column images
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int x = xs + j;
+            const float v0 = get(o[0], j), v1 = get(o[1], j), v2 = get(o[2], j), v3 = get(o[3], j), v4 = get(o[4], j);
+            auto put = [&](int yy, int xi) {
+                float *r = row_at(yy) + xi;
+                r[0] = v0;
+                r[pplane] = v1;
+                r[2 * pplane] = v2;
+                r[3 * pplane] = v3;
+                r[4 * pplane] = v4;
+            };
+            if (x < nx) {
+                for (int xi = x + nx; xi <= nx + 1; xi += nx)
+                    for (int yy = rb - ((rb + 2) / ny) * ny; yy <= ny + 1; yy += ny) put(yy, xi);
+                for (int xi = x - nx; xi >= -2; xi -= nx)
+                    for (int yy = rb - ((rb + 2) / ny) * ny; yy <= ny + 1; yy += ny) put(yy, xi);
+            }
+        }
+    }
+}
+
+// Persistent CTAs over the queue of units (taken in order from the counters `sched`), a producer warp running ahead
+// of the step-t, step-t+1 and ring warps, as step2d_ss2.  A chunk's descriptor is two int4: the unit's x0, ys, ye and
+// k | 1 << 24 | event flag << 25, then its member m, packed row prow0 and size; the producer reads the next unit's
+// table entry (one word per lane) when it starts a unit.
+template <int TBY, int S, int MINB>
+__global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
+    step2d_batch_ss2(const StepArgs *__restrict__ args, const BatchUnit *__restrict__ units, int nunits, int *sched,
+                     const long long *__restrict__ t0p, int toff, int par, BatchPacked pk,
+                     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmCL) {
+    using Gm = SsGeom<TBY, S>;
+    constexpr int NC = 2 * TBY + 1, DS = Gm::DS;
+    extern __shared__ __align__(1024) float sm[];
+    float *P = sm + Gm::IN_SZ + Gm::E_SZ;
+    SsDesc *desc = reinterpret_cast<SsDesc *>(P + Gm::P_SZ);
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(desc + DS);  // full[S], then empty[S]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned full0 = smem_u32(mb), empty0 = full0 + 8 * S;
+    if (tid < S) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * tid) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(empty0 + 8 * tid), "r"(TBY + 1) : "memory");
+    }
+    if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncthreads();
+    const unsigned long long wait_limit = g_ss_wait_limit_ns;
+    const bool aligned = !(smem_u32(sm) & 127);  // TMA destinations here are 128-byte aligned (checked on the host too)
+    if (warp == NC) {
+        // ---- producer
+        const CUtensorMap *tmIn = par ? &tmB : &tmA;
+        if (lane < 2) asm volatile("prefetch.tensormap [%0];\n" ::"l"(lane == 0 ? tmIn : &tmCL) : "memory");
+        int cK = 0, ck = 0, nu = 0, nd = 0;
+        int cm = 0, cx0 = 0, cys = 0, cye = 0, cpr = 0, cnx = 0, cny = 0;
+        const int *crp = nullptr;
+        const Event *cev = nullptr;
+        int rpc[3], rpn[3];  // row pointers of the current and the next unit's rows ys-2 ..
+        bool rpn_ready = false;
+        auto field = [&](int f) { return __shfl_sync(0xffffffffu, nd, f); };
+        auto ptr = [&](int f) {  // a pointer field of the next unit's table entry (two words)
+            return (const void *)(((unsigned long long)(unsigned)field(f + 1) << 32) | (unsigned)field(f));
+        };
+        auto fetch_next = [&]() {  // the next unit and its table entry (one word per lane), in flight from here
+            int u = 0;
+            if (lane == 0) u = atomicAdd(sched, 1);
+            nu = __shfl_sync(0xffffffffu, u, 0);
+            nd = nu < nunits && lane < 12 ? __ldg(reinterpret_cast<const int *>(units + nu) + lane) : 0;
+            rpn_ready = false;
+        };
+        auto load_next_rowptr = [&]() {  // once the entry has landed: the next unit's row pointers
+            ss_load_rowptr(static_cast<const int *>(ptr(8)), field(6), field(2), rpn);
+            rpn_ready = true;
+        };
+        fetch_next();
+        int c = 0;
+        bool ok = aligned;
+        for (; ok; c++) {
+            if (c >= S && !mbar_wait(empty0 + 8 * (c % S), (unsigned)(c / S - 1) & 1u, wait_limit)) {
+                ok = false;
+                break;
+            }
+            if (ck == cK && nu < nunits) {  // start the next unit
+                if (!rpn_ready) load_next_rowptr();
+                cm = field(0);
+                cx0 = field(1);
+                cys = field(2);
+                cye = field(3);
+                cpr = field(4);
+                cnx = field(5);
+                cny = field(6);
+                crp = static_cast<const int *>(ptr(8));
+                cev = static_cast<const Event *>(ptr(10));
+#pragma unroll
+                for (int j = 0; j < 3; j++) rpc[j] = rpn[j];
+                cK = (cye - cys + 2 + TBY - 1) / TBY;
+                ck = 0;
+                fetch_next();
+            } else if (!rpn_ready && nu < nunits) {
+                load_next_rowptr();
+            }
+            int4 d0 = make_int4(0, 0, 0, 0), d1 = make_int4(0, 0, 0, 0);
+            if (ck < cK) {
+                const int s = cys - 1 + ck * TBY;
+                d0 = make_int4(cx0, cys, cye, ck | 1 << 24);
+                d0.w |= ss_stage_chunk<TBY>(rpc, cev, crp != nullptr, cny, s, ck, &desc[c % DS].ev,
+                                            full0 + 8 * (c % S));
+                d1 = make_int4(cm, cpr, cnx, cny);
+                ck++;
+            }
+            if (lane == 0) {
+                desc[c % DS].d0 = d0;
+                desc[c % DS].d1 = d1;
+            }
+            if (!ss_valid(d0)) {  // end of the stream
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8 * (c % S)) : "memory");
+                break;
+            }
+            // six boxes, one per lane: member column x0 - 4 <-> packed column x0, member row y <-> prow0 + 2 + y
+            const unsigned mbar = full0 + 8 * (c % S);
+            float *st = sm + (c % S) * Gm::STAGE;
+            const int s = cys - 1 + (ck - 1) * TBY, py = cpr + 2 + s;
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(Gm::TMA_BYTES)
+                             : "memory");
+            __syncwarp();
+            if (lane < 6) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                if (lane < 5)
+                    tma_load_3d(st + lane * Gm::PL_IN, tmIn, cx0, py + ss_shift(lane), lane, mbar);
+                else
+                    tma_load_2d(st + 5 * Gm::PL_IN, &tmCL, cx0, py, mbar);
+            }
+        }
+        if (!ok) {  // the consumers stopped (or shared memory is misaligned): flag it, let the copies land (bounded)
+            if (lane == 0) atomicExch(&g_ss_timeouts, 1);
+            for (int k = c > S ? c - S : 0; k < c; k++)
+                mbar_wait(full0 + 8 * (k % S), (unsigned)(k / S) & 1u, kSsDrainNs);
+            if (!aligned && lane == 0)  // the consumers wait for an end descriptor in stage 0
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0) : "memory");
+        }
+        __threadfence();  // the queue accesses before the CTA counts itself out
+    } else {
+        // ---- step t, step t+1 and the ring sites
+        const long long t = *t0p + toff;
+        float *out = par ? pk.buf[0] : pk.buf[1];  // (a select: an index into the parameter would copy it to the stack)
+        for (int p = 0;; p++) {
+            const bool ok = mbar_wait(full0 + 8 * (p % S), (unsigned)(p / S) & 1u, wait_limit);
+            const int4 da = desc[p % DS].d0, dam = desc[p % DS].d1;
+            const int4 db = desc[(p + DS - 1) % DS].d0, dbm = desc[(p + DS - 1) % DS].d1;
+            const bool va = ok && ss_valid(da), vb = p >= 1 && ss_valid(db);
+            const SsEvList *ela = (da.w >> 26) & 1 ? &desc[p % DS].ev : nullptr;
+            const SsEvList *elb = (db.w >> 26) & 1 ? &desc[(p + DS - 1) % DS].ev : nullptr;
+            const float *st = sm + (p % S) * Gm::STAGE;
+            const int s = da.y - 1 + (da.w & 0xffff) * TBY;
+            if (warp < TBY) {
+                if (va) {
+                    const StepArgs &am = args[2 * dam.x];
+                    const int r = s + warp;
+                    if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(am, r)))
+                        ss_step_a<TBY, S, true>(am, st, st, 0, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                                                ela);
+                    else
+                        ss_step_a<TBY, S, false>(am, st, st, 0, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                                                 nullptr);
+                }
+            } else if (warp < 2 * TBY) {
+                const int w = warp - TBY;
+                if (vb) {
+                    const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
+                    if (rb >= db.y && rb < db.z) {
+                        const StepArgs &bm = args[2 * dbm.x];
+                        if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(bm, rb)))
+                            ss_step_b_packed<TBY, S, true>(bm, P, db.x, rb, (p - 1) * TBY + w, t, out, pk.plane, pk.W,
+                                                           dbm.y, dbm.z, dbm.w, elb, w);
+                        else
+                            ss_step_b_packed<TBY, S, false>(bm, P, db.x, rb, (p - 1) * TBY + w, t, out, pk.plane, pk.W,
+                                                            dbm.y, dbm.z, dbm.w, nullptr, w);
+                    }
+                }
+            } else if (va) {
+                ss_ring<TBY, S>(args[2 * dam.x], st, st, 0, P, da.x, s, p, ss_events(da), t, ela);
+            }
+            if (va && (warp < TBY || warp == 2 * TBY)) {  // this warp has read the stage: release it to the producer
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(empty0 + 8 * (p % S)) : "memory");
+            }
+            if (ss_consumers_or(!ok, NC * 32)) {  // a chunk never arrived: flag it and stop (the producer drains)
+                if (tid == 0) atomicExch(&g_ss_timeouts, 1);
+                break;
+            }
+            if (!ss_valid(da)) break;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
+        sched[0] = 0;
+        sched[1] = 0;
+    }
+}
+
+// Tensor maps of the packed buffers ([5][rows][W] floats, box: one plane of TBY rows of SW) and of the packed c_L^2.
+static bool ss_batch_maps(const BatchPacked &pk, long long rows, int tby, CUtensorMap *mA, CUtensorMap *mB,
+                          CUtensorMap *mCL) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || pk.W < SW) return false;
+    const cuuint64_t dims3[3] = {(cuuint64_t)pk.W, (cuuint64_t)rows, 5};
+    const cuuint64_t str3[2] = {(cuuint64_t)pk.W * 4, (cuuint64_t)pk.plane * 4};
+    const cuuint32_t box3[3] = {(cuuint32_t)SW, (cuuint32_t)tby, 1};
+    const cuuint32_t one[3] = {1, 1, 1};
+    for (int b = 0; b < 2; b++)
+        if (fn(b ? mB : mA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pk.buf[b], dims3, str3, box3, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    const cuuint64_t dims2[2] = {(cuuint64_t)pk.W, (cuuint64_t)rows};
+    const cuuint64_t str2[1] = {(cuuint64_t)pk.W * 4};
+    const cuuint32_t box2[2] = {(cuuint32_t)SW, (cuuint32_t)tby};
+    return fn(mCL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, pk.cl, dims2, str2, box2, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TBY, int S, int MINB>
+static cudaError_t launch_bss(const StepArgs *args, const BatchUnit *units, int nunits, int *sched,
+                              const long long *t0p, int toff, int par, const BatchPacked &pk, long long rows,
+                              cudaStream_t s) {
+    using Gm = SsGeom<TBY, S>;
+    constexpr int NT = (2 * TBY + 2) * 32;
+    static int per_sm = 0, nsm = 0;
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(step2d_batch_ss2<TBY, S, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_batch_ss2<TBY, S, MINB>, NT, Gm::BYTES);
+        if (per_sm < 1) per_sm = 1;
+    }
+    CUtensorMap mA, mB, mCL;
+    memset(&mA, 0, sizeof mA);
+    memset(&mB, 0, sizeof mB);
+    memset(&mCL, 0, sizeof mCL);
+    if (!ss_batch_maps(pk, rows, TBY, &mA, &mB, &mCL)) return cudaErrorNotSupported;
+    const long long slots = (long long)per_sm * nsm;
+    const int blocks = (int)(nunits < slots ? nunits : slots);
+    if (blocks < 1) return cudaSuccess;
+    step2d_batch_ss2<TBY, S, MINB>
+        <<<blocks, NT, Gm::BYTES, s>>>(args, units, nunits, sched, t0p, toff, par, pk, mA, mB, mCL);
+    return cudaGetLastError();
+}
+
+// Shapes of the batch's strip kernel (chunk rows, stages, CTAs per SM, chunks per unit).
+int batch_ss2_nshapes() { return 2; }
+int batch_ss2_rows(int shape) { return shape == 1 ? 3 : 4; }
+int batch_ss2_chunks(int shape) { return shape == 1 ? 12 : 16; }
+
+cudaError_t launch_batch_ss2(const StepArgs *args, const BatchUnit *units, int nunits, int *sched, const long long *t0p,
+                             int toff, int par, const BatchPacked &pk, long long rows, int shape, cudaStream_t s) {
+    if (shape == 1) return launch_bss<3, 4, 3>(args, units, nunits, sched, t0p, toff, par, pk, rows, s);
+    return launch_bss<4, 3, 3>(args, units, nunits, sched, t0p, toff, par, pk, rows, s);
 }
 
 cudaError_t ss_set_wait_limit(unsigned long long ns) {

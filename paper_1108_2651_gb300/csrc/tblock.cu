@@ -542,7 +542,7 @@ __global__ void batch_pack_kernel(const StepArgs *__restrict__ args, int par, co
     const int nx = a.g.nx, ny = a.g.ny, pitch = a.g.pitch;
     const long long plane = a.g.plane;
     const int y = b - __ldg(r0 + lo) - 2;
-    float *pb = pk.buf[which] + (long long)b * pk.W + 4;
+    float *pb = (which ? pk.buf[1] : pk.buf[0]) + (long long)b * pk.W + 4;
     float *mem = static_cast<float *>(a.in.data);
     if (unpack) {
         if (y < 0 || y >= ny) return;
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(NT, MINB)
     if (k >= ntiles) return;
     if (smem_u32(sm) & 127) return;  // the launch checks alignment on the host side too (TMA destinations)
     const CUtensorMap *tmIn = par ? &tmB : &tmA;
-    float *out = pk.buf[par ^ 1];
+    float *out = par ? pk.buf[0] : pk.buf[1];  // (a select: an index into the parameter would copy it to the stack)
     const unsigned mbar = smem_u32(mb);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
