@@ -64,16 +64,19 @@ struct SsDesc {
     SsEvList ev;
 };
 
-template <int TBY, int S>
+template <int TBY, int S, bool BATCH = false>
 struct SsGeom {
     static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
     static constexpr int M = 2 * TBY + 2;
     static constexpr int PL_IN = up32(TBY * SW), STAGE = 6 * PL_IN;
     static constexpr int EPL = up32(4 * TBY), ESTAGE = 6 * EPL;
     static constexpr int PL_P = M * SW;
-    static constexpr int IN_SZ = S * STAGE, E_SZ = S * ESTAGE, P_SZ = up32(6 * PL_P);
+    static constexpr int IN_SZ = S * STAGE, E_SZ = BATCH ? 0 : S * ESTAGE, P_SZ = up32(6 * PL_P);  // (no images:
+    // the batch's packed members carry theirs)
     static constexpr int DS = S + 2;  // chunk descriptor slots (SsDesc) after the ring, then the mbarriers
-    static constexpr int SZ = IN_SZ + E_SZ + P_SZ + DS * (int)(sizeof(SsDesc) / 4);
+    // (the batch kernel keeps a copy of each chunk's member arguments beside the descriptors)
+    static constexpr int SZ = IN_SZ + E_SZ + P_SZ + DS * (int)(sizeof(SsDesc) / 4) +
+                              (BATCH ? DS * (int)(sizeof(StepArgs) / 4) : 0);
     static constexpr size_t BYTES = sizeof(float) * SZ + 2 * S * sizeof(unsigned long long);
     static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * TBY * SW, E_BYTES = sizeof(float) * 6 * TBY * 4;
 };
@@ -676,12 +679,17 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                      const long long *__restrict__ t0p, int toff, int par, BatchPacked pk,
                      const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmCL) {
-    using Gm = SsGeom<TBY, S>;
+    using Gm = SsGeom<TBY, S, true>;
     constexpr int NC = 2 * TBY + 1, DS = Gm::DS;
+    constexpr int NA = (int)(sizeof(StepArgs) / 16);  // 16-byte pieces of a member's arguments
+    static_assert(sizeof(StepArgs) % 16 == 0 && NA <= 32, "arguments copied by one warp in 16-byte pieces");
     extern __shared__ __align__(1024) float sm[];
     float *P = sm + Gm::IN_SZ + Gm::E_SZ;
     SsDesc *desc = reinterpret_cast<SsDesc *>(P + Gm::P_SZ);
-    unsigned long long *mb = reinterpret_cast<unsigned long long *>(desc + DS);  // full[S], then empty[S]
+    // per descriptor slot its member's arguments: the site updates' event path reads them from shared memory (global
+    // loads of them missed L1, which shared memory fills, and stalled each event row)
+    StepArgs *sargs = reinterpret_cast<StepArgs *>(desc + DS);
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(sargs + DS);  // full[S], then empty[S]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned full0 = smem_u32(mb), empty0 = full0 + 8 * S;
     if (tid < S) {
@@ -748,6 +756,13 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
             if (ck < cK) {
                 const int s = cys - 1 + ck * TBY;
                 d0 = make_int4(cx0, cys, cye, ck | 1 << 24);
+                if (lane < NA) {  // the member's arguments beside the descriptor (tracked by the stage's mbarrier)
+                    tb_cpa16(reinterpret_cast<float *>(sargs + c % DS) + 4 * lane,
+                             reinterpret_cast<const float *>(args + 2 * cm) + 4 * lane);
+                    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];\n" ::"r"(full0 + 8 * (c % S))
+                                 : "memory");
+                }
+                __syncwarp();  // the copies' arrivals before lane 0's
                 d0.w |= ss_stage_chunk<TBY>(rpc, cev, crp != nullptr, cny, s, ck, &desc[c % DS].ev,
                                             full0 + 8 * (c % S));
                 d1 = make_int4(cm, cpr, cnx, cny);
@@ -792,7 +807,7 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
         float *out = par ? pk.buf[0] : pk.buf[1];  // (a select: an index into the parameter would copy it to the stack)
         for (int p = 0;; p++) {
             const bool ok = mbar_wait(full0 + 8 * (p % S), (unsigned)(p / S) & 1u, wait_limit);
-            const int4 da = desc[p % DS].d0, dam = desc[p % DS].d1;
+            const int4 da = desc[p % DS].d0;
             const int4 db = desc[(p + DS - 1) % DS].d0, dbm = desc[(p + DS - 1) % DS].d1;
             const bool va = ok && ss_valid(da), vb = p >= 1 && ss_valid(db);
             const SsEvList *ela = (da.w >> 26) & 1 ? &desc[p % DS].ev : nullptr;
@@ -801,7 +816,7 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
             const int s = da.y - 1 + (da.w & 0xffff) * TBY;
             if (warp < TBY) {
                 if (va) {
-                    const StepArgs &am = args[2 * dam.x];
+                    const StepArgs &am = sargs[p % DS];
                     const int r = s + warp;
                     if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(am, r)))
                         ss_step_a<TBY, S, true>(am, st, st, 0, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
@@ -815,7 +830,7 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                 if (vb) {
                     const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
                     if (rb >= db.y && rb < db.z) {
-                        const StepArgs &bm = args[2 * dbm.x];
+                        const StepArgs &bm = sargs[(p + DS - 1) % DS];
                         if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(bm, rb)))
                             ss_step_b_packed<TBY, S, true>(bm, P, db.x, rb, (p - 1) * TBY + w, t, out, pk.plane, pk.W,
                                                            dbm.y, dbm.z, dbm.w, elb, w);
@@ -825,7 +840,7 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                     }
                 }
             } else if (va) {
-                ss_ring<TBY, S>(args[2 * dam.x], st, st, 0, P, da.x, s, p, ss_events(da), t, ela);
+                ss_ring<TBY, S>(sargs[p % DS], st, st, 0, P, da.x, s, p, ss_events(da), t, ela);
             }
             if (va && (warp < TBY || warp == 2 * TBY)) {  // this warp has read the stage: release it to the producer
                 __syncwarp();
@@ -871,7 +886,7 @@ template <int TBY, int S, int MINB>
 static cudaError_t launch_bss(const StepArgs *args, const BatchUnit *units, int nunits, int *sched,
                               const long long *t0p, int toff, int par, const BatchPacked &pk, long long rows,
                               cudaStream_t s) {
-    using Gm = SsGeom<TBY, S>;
+    using Gm = SsGeom<TBY, S, true>;
     constexpr int NT = (2 * TBY + 2) * 32;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
