@@ -565,6 +565,19 @@ def test_two_step_blocking_heterogeneous_mu_is_bitwise_identical(lbem, shape):
         np.testing.assert_array_equal(tr.cpu().double().numpy(), ref[2])
 
 
+def test_default_two_step_shape_follows_grid_size(lbem):
+    """An FP32 grid of uniform mu with at least 12M sites launches the strip-streaming kernel (shape 10) unless a
+    shape is set; smaller grids, and any grid once a shape is set, launch that shape (0 by default)."""
+    for shape, want in (((3000, 4096), 10), ((2048, 2048), 0)):
+        s = lbem.Solver(shape)
+        assert lbem.lbem_get_temporal_blocking(s.h)[:2] == (2, want)
+        lbem.lbem_set_temporal_blocking(s.h, 2, 0)
+        assert lbem.lbem_get_temporal_blocking(s.h)[:2] == (2, 0)
+        lbem.lbem_set_temporal_blocking(s.h, 2, -1)
+        assert lbem.lbem_get_temporal_blocking(s.h)[:2] == (2, want)
+        s.close()
+
+
 def test_two_step_blocking_rejects_bad_arguments(lbem):
     s = lbem.Solver((16, 16))
     for steps, shape in ((0, 0), (4, 0), (2, 15), (3, 3), (2, -2)):

@@ -60,8 +60,8 @@ def test_walls_are_bitwise_identical_across_stepping_modes(lbem, shape, bc, laye
     p = _problem(shape, 600 + shape[0], 41, bc, layer, 0.25 if layer else 0.0, mu)
     ref = gpu_run(p, steps_per_pass=1)
     modes = [(1, 0, True), (2, 0, False), (2, 1, True), (3, 0, False), (3, 2, True)]
-    if not mu:
-        modes += [(2, k, False) for k in range(2, 9)]
+    if not mu:  # the other tile shapes, the register-streaming kernel and the strip-streaming kernel
+        modes += [(2, k, False) for k in range(2, 15)]
     for spp, tile, graphs in modes:
         stream = torch.cuda.Stream() if graphs else None
         s = lbem.Solver(p.shape, stream=stream.cuda_stream if stream else None)
