@@ -380,20 +380,22 @@ def other_forms(lbem, torch, p, peak, stream):
                     "frac": gbs / peak, "bytes_per_site_per_launch": 72, "steps_per_launch": spp, "lb_steps": 2000,
                     "kernel": "step2d_tb2<POLE>" if spp == 2 else "step2d_gen"}
     # the same medium made uniaxial, mu = diag(2, 1) (per-axis lattice weights), 2000 steps: 44 B/site per
-    # launch, two steps per launch by default (the tile kernel with per-axis weights), then single-step launches
-    # of the general kernel
+    # launch, two steps per launch by default (the strip or the tile kernel with per-axis weights, as autotuned),
+    # then single-step launches of the general kernel
     pa = W.heterogeneous_2d_aniso(p.shape[0], seed=2, nsteps=2000)
     for key, spp_set in (("f32_anisotropic", 2), ("f32_anisotropic_single_step", 1)):
         s = lbem.Solver(pa.shape, stream=stream.cuda_stream)
         if spp_set == 1:
             lbem.lbem_set_temporal_blocking(s.h, 1, -1)
         ms, v, spp = _time_run(lbem, torch, s, pa, 2000, stream)
+        shape_an = lbem.lbem_get_temporal_blocking(s.h)[1]
         s.close()
         per = ms / (2000 // spp)
         gbs = 44 * n / (per * 1e-3) / 1e9
+        kern = ("step2d_ss2<AN>" if shape_an == 1 else "step2d_tb2<AN>") if spp == 2 else "step2d_gen"
         out[key] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                     "frac": gbs / peak, "bytes_per_site_per_launch": 44, "steps_per_launch": spp, "lb_steps": 2000,
-                    "kernel": "step2d_tb2<AN>" if spp == 2 else "step2d_gen", "mu_tensor": list(pa.aniso)}
+                    "kernel": kern, "mu_tensor": list(pa.aniso)}
     # 192^3 in a PEC box with a 16-site absorbing layer (walls applied by the one-site-per-thread 3D kernel),
     # 500 steps: 172 B/site
     qb = W.heterogeneous_3d(192, nsteps=500)
@@ -1018,6 +1020,8 @@ def main():
         kname, kid = "step2d_tb2<POLE> (one dispersive pole per site, tile shape 0, 2 steps per launch)", "tb2pole"
     elif aniso and spp == 1:
         kname, kid = "step2d_gen (anisotropic medium, single steps)", "gen"
+    elif aniso and tile_shape == 1:
+        kname, kid = "step2d_ss2<AN> (anisotropic medium, strip streaming, 2 steps per launch)", "ss2an"
     elif aniso:
         kname, kid = "step2d_tb2<AN> (anisotropic medium, tile shape 0, 2 steps per launch)", "tb2an"
     elif walls and p.D == 2:

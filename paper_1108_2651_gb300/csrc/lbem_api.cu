@@ -179,14 +179,20 @@ static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_b
 static bool three_step_ok(const lbem_t *h) {
     return h->tblock == 3 && multi_step_base(h) && h->storage == LBEM_F32 && !h->has_mu && !h->general();
 }
-// The two-step shape to launch: the one set (or autotuned) when it exists for this medium, else 0, except that
-// an FP32 grid of uniform mu and at least 12M sites defaults to the strip-streaming kernel (shape 1 of sstream.cu:
-// 259.6k Mlups at 4096^2 against 247.3k for tile shape 0; at 2048^2 and below the tile kernel is faster).
+// Two-step shapes of the handle's medium: a dispersive pole 1 (the tile kernel), an anisotropic tensor 2 (the tile
+// kernel, the strip kernel), otherwise those of tblock.cu.
+static int two_step_nshapes(const lbem_t *h) {
+    return h->disp ? 1 : h->aniso ? 2 : tb2_nshapes(h->storage, h->has_mu);
+}
+// The two-step shape to launch: the one set (or autotuned) when it exists for this medium, else 0, except that a
+// large FP32 grid (at least 12M sites) of uniform mu, or with an anisotropic tensor and no pole, defaults to the
+// strip-streaming kernel (sstream.cu; at 4096^2 274.6k Mlups against 247.3k for tile shape 0; at 2048^2 and below
+// the tile kernel is faster).
 static int two_step_shape(const lbem_t *h) {
-    if (h->general()) return 0;
-    if (!h->tb_shape_set && h->tblock == 2 && h->dim == 2 && h->storage == LBEM_F32 && !h->has_mu &&
-        h->nsite >= 12000000)
-        return 7 + rs2_nshapes() + 1;
+    if (h->disp) return 0;
+    const bool big = h->tblock == 2 && h->dim == 2 && h->storage == LBEM_F32 && !h->has_mu && h->nsite >= 12000000;
+    if (h->aniso) return h->tb_shape_set ? (h->tb_shape == 1 ? 1 : 0) : (big ? 1 : 0);
+    if (!h->tb_shape_set && big) return 7 + rs2_nshapes() + 1;
     return h->tblock == 2 && h->tb_shape < tb2_nshapes(h->storage, h->has_mu) ? h->tb_shape : 0;
 }
 static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two_step_ok(h) ? 2 : 1; }
@@ -1067,7 +1073,7 @@ lbem_status lbem_autotune(lbem_t *h, int trial_steps, int *best) {
     for (int k = 2; k <= max_k && st == LBEM_OK; k++) {
         if (!multi_step_base(h) || (k == 3 && (h->storage != LBEM_F32 || h->has_mu))) continue;
         const int nl = trial_steps / k > 0 ? trial_steps / k : 1;
-        const int nsh = k == 3 ? tb3_nshapes() : tb2_nshapes(h->storage, h->has_mu);
+        const int nsh = k == 3 ? tb3_nshapes() : two_step_nshapes(h);
         for (int shape = 0; shape < nsh && st == LBEM_OK; shape++) {
             int cur = cur0;
             for (int rep = 0; rep < 2 && st == LBEM_OK; rep++) {
@@ -1116,7 +1122,7 @@ lbem_status lbem_get_temporal_blocking(const lbem_t *h, int *steps_per_pass, int
     if (!h) return fail(LBEM_ERR_ARG, "null handle");
     if (steps_per_pass) *steps_per_pass = steps_per_launch(h);
     if (tile_shape) *tile_shape = steps_per_launch(h) == 2 ? two_step_shape(h) : h->tb_shape;
-    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : h->general() ? 1 : tb2_nshapes(h->storage, h->has_mu);
+    if (nshapes) *nshapes = h->tblock == 3 ? tb3_nshapes() : two_step_nshapes(h);
     return LBEM_OK;
 }
 

@@ -158,19 +158,24 @@ __device__ __forceinline__ void ss_issue(const StepArgs &a, int x0, int xm, int 
 
 // site_events (source current at column x of window row i and time t, receiver writes where owned) from a staged
 // list: the same arithmetic in the same order.  Uniform mu only.
+// With an anisotropic medium (site_events' sbx, sby, jmu: B_x, B_y scaled by r and 1/r, j_z by mubar; 1 leaves every
+// value unchanged).
 __device__ __forceinline__ float ss_list_events(const StepArgs &a, const SsEvList *L, int i, int x, long long t,
                                                 bool owned, float g0, float g1, float g2, float g3, float g4,
-                                                float cl) {
+                                                float cl, float sbx = 1.f, float sby = 1.f, float jmu = 1.f) {
     float shat = 0.f;
     for (int j = L->b[i]; j < L->b[i + 1]; j++) {
         const Event ev = L->rec[j];
         if (ev.x != x) continue;
         if (ev.kind == 0) {
             if (ev.comp == 2 && t < a.evt.nt)
-                shat = __fsub_rn(shat, __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t));
+                shat = __fsub_rn(shat, __fmul_rn(__ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t), jmu));
         } else if (owned && t < a.evt.cap) {
             const float s = ((g0 + g1) + (g2 + g3)) + g4;
-            a.evt.traces[(long long)ev.index * a.evt.cap + t] = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+            float v = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
+            if (ev.comp == 3) v = __fmul_rn(v, sbx);
+            if (ev.comp == 4) v = __fmul_rn(v, sby);
+            a.evt.traces[(long long)ev.index * a.evt.cap + t] = v;
         }
     }
     return shat;
@@ -221,12 +226,16 @@ __device__ __forceinline__ int ss_stage_chunk(const int (&rp)[3], const Event *e
 // Four site updates at global row gy, columns x0+4*lane.. (collide2d with the sites' sources and receivers where
 // EV, else collide2d_free), from the pulled populations q[0..4] and c_L^2; with a staged list `el` the events come
 // from it (window row li).
-template <bool EV>
+//
+// With AN (a uniform in-plane permeability tensor, a.med.ar / a.med.amu) the site update is the general kernel's
+// collide2d_an with its per-axis speeds (r, 1/r) and no pole, and the events scale as in site_events.
+template <bool EV, bool AN = false>
 __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[5], float4 cl, int x0, int gy,
                                            long long t, bool owned, float4 (&o)[5], const SsEvList *el = nullptr,
                                            int li = 0) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
+    const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k), q4 = get(q[4], k),
@@ -235,11 +244,16 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
         if (EV) {
             const int gx = x0 + 4 * lane + k;
             const bool own = owned && gx < G.nx && gy < G.ny;
-            const float shat = el ? ss_list_events(a, el, li, wrapi(gx, G.nx), t, own, q0, q1, q2, q3, q4, ck)
-                                  : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck);
-            r = collide2d(q0, q1, q2, q3, q4, ck, shat);
+            const float jmu = AN ? a.med.amu : 1.f;
+            const float shat = el ? ss_list_events(a, el, li, wrapi(gx, G.nx), t, own, q0, q1, q2, q3, q4, ck, ar, ri,
+                                                   jmu)
+                                  : AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4,
+                                                     ck, 0.f, 0.f, ar, ri, jmu)
+                                       : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4,
+                                                     ck);
+            r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f) : collide2d(q0, q1, q2, q3, q4, ck, shat);
         } else {
-            r = collide2d_free(q0, q1, q2, q3, q4, ck);
+            r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, 0.f, ar, ri, fs, 0.f) : collide2d_free(q0, q1, q2, q3, q4, ck);
         }
         set(o[0], k, r.o0);
         set(o[1], k, r.o1);
@@ -272,7 +286,7 @@ __device__ __forceinline__ bool ss_row_events(const StepArgs &a, int gy) {
 // the rows that pull them (ring row u = r - ys + 2 for planes 0, 1, 3 and c_L^2, u + 1 for plane 2, u - 1 for plane
 // 4).  With the images in `es` (emode 1: left of the strip, 2: right of it) lane 0's g1 or lane 31's g3 come from
 // there.
-template <int TBY, int S, bool EV>
+template <int TBY, int S, bool EV, bool AN = false>
 __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, const float *es, int emode, float *P,
                                           int x0, int ys, int ye, int r, int w, int u, long long t,
                                           const SsEvList *el) {
@@ -283,7 +297,7 @@ __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, co
     ss_pull(st, Gm::PL_IN, w, c, q, cl);
     if (emode == 1 && lane == 0) q[1].x = es[Gm::EPL + w * 4 + 3];        // column x0-1 = nx-1
     if (emode == 2 && lane == 31) q[3].w = es[3 * Gm::EPL + w * 4 + 0];   // column x0+128 = 0
-    ss_update4<EV>(a, q, cl, x0, r, t, r >= ys && r < ye, o, el, w + 1);
+    ss_update4<EV, AN>(a, q, cl, x0, r, t, r >= ys && r < ye, o, el, w + 1);
     const int s0 = u % M, s2 = s0 == M - 1 ? 0 : s0 + 1, s4 = s0 == 0 ? M - 1 : s0 - 1;
     float *p0 = P + s0 * SW + c;
     sts4(p0, o[0]);
@@ -297,7 +311,7 @@ __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, co
 // The ring sites of the chunk in stage `st`, by the ring warp: lane 2w takes column x0-1 of chunk row w (plane 1
 // only), lane 2w+1 column x0+128 (plane 3 only), at ring row p TBY + w + 1 (p: the CTA's phase); with the images in
 // `es` the columns outside the grid come from there.
-template <int TBY, int S>
+template <int TBY, int S, bool AN = false>
 __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, const float *es, int emode, float *P,
                                         int x0, int s, int p, bool events, long long t, const SsEvList *el) {
     using Gm = SsGeom<TBY, S>;
@@ -310,12 +324,17 @@ __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, cons
         return st[pl * Gm::PL_IN + w * SW + col];
     };
     const float q0 = v(0, cc), q1 = v(1, cc - 1), q2 = v(2, cc), q3 = v(3, cc + 1), q4 = v(4, cc), ck = v(5, cc);
+    const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
+    const float jmu = AN ? a.med.amu : 1.f;
     float shat = 0.f;
     if (el)
-        shat = ss_list_events(a, el, w + 1, wrapi(x0 - 4 + cc, a.g.nx), t, false, q0, q1, q2, q3, q4, ck);
+        shat = ss_list_events(a, el, w + 1, wrapi(x0 - 4 + cc, a.g.nx), t, false, q0, q1, q2, q3, q4, ck, ar, ri, jmu);
     else if (events && ss_row_events(a, r))
-        shat = site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck);
-    const Out5 ro = collide2d(q0, q1, q2, q3, q4, ck, shat);
+        shat = AN ? site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck, 0.f,
+                                0.f, ar, ri, jmu)
+                  : site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck);
+    const Out5 ro = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f)
+                       : collide2d(q0, q1, q2, q3, q4, ck, shat);
     const int s0 = (p * TBY + w + 1) % Gm::M;
     if (right)
         P[3 * Gm::PL_P + s0 * SW + cc] = ro.o3;
@@ -324,7 +343,7 @@ __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, cons
 }
 
 // Step t+1 on global row rb (ring row ub), written as 16-byte streaming stores.
-template <int TBY, int S, bool EV>
+template <int TBY, int S, bool EV, bool AN = false>
 __device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int x0, int rb, int ub, long long t,
                                           const SsEvList *el, int w) {
     using Gm = SsGeom<TBY, S>;
@@ -332,7 +351,7 @@ __device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int
     const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
     float4 q[5], cl, o[5];
     ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl);
-    ss_update4<EV>(a, q, cl, x0, rb, t + 1, true, o, el, w);
+    ss_update4<EV, AN>(a, q, cl, x0, rb, t + 1, true, o, el, w);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
         float4 *op = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)rb * G.pitch + x0 +
                                                 4 * lane);
@@ -394,7 +413,7 @@ __device__ __forceinline__ void ss_unit(const SsUnits &U, int ny, int u, int &x0
 // numbered by the phase (rows of step t+1 that would pull across a unit boundary lie outside their unit and are
 // skipped).  The step-t and ring warps release the stage once they have read it; a barrier of these 2 TBY + 1 warps
 // closes the phase.
-template <int TBY, int S, int MINB>
+template <int TBY, int S, int MINB, bool AN = false>
 __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
     step2d_ss2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
                const __grid_constant__ CUtensorMap tmIn4, const __grid_constant__ CUtensorMap tmCL4, int use_tma,
@@ -491,10 +510,10 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                 if (va) {
                     const int r = s + warp;
                     if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(a, r)))
-                        ss_step_a<TBY, S, true>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                        ss_step_a<TBY, S, true, AN>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
                                                 ela);
                     else
-                        ss_step_a<TBY, S, false>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                        ss_step_a<TBY, S, false, AN>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
                                                  nullptr);
                 }
             } else if (warp < 2 * TBY) {
@@ -503,13 +522,13 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                     const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
                     if (rb >= db.y && rb < db.z) {
                         if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(a, rb)))
-                            ss_step_b<TBY, S, true>(a, P, db.x, rb, (p - 1) * TBY + w, t, elb, w);
+                            ss_step_b<TBY, S, true, AN>(a, P, db.x, rb, (p - 1) * TBY + w, t, elb, w);
                         else
-                            ss_step_b<TBY, S, false>(a, P, db.x, rb, (p - 1) * TBY + w, t, nullptr, w);
+                            ss_step_b<TBY, S, false, AN>(a, P, db.x, rb, (p - 1) * TBY + w, t, nullptr, w);
                     }
                 }
             } else if (va) {
-                ss_ring<TBY, S>(a, st, es, emode, P, da.x, s, p, ss_events(da), t, ela);
+                ss_ring<TBY, S, AN>(a, st, es, emode, P, da.x, s, p, ss_events(da), t, ela);
             }
             if (va && (warp < TBY || warp == 2 * TBY)) {  // this warp has read the stage: release it to the producer
                 __syncwarp();
@@ -554,7 +573,7 @@ static bool ss_make_maps(const StepArgs &a, int tby, int w, CUtensorMap *mIn, CU
 
 // Persistent CTAs (as many as are resident, at most one per unit) over units of MCH TBY - 2 rows (MCH chunks each),
 // and units of 2 TBY - 2 rows (two chunks) for the last rows: about two short units per CTA.
-template <int TBY, int S, int MINB, int MCH>
+template <int TBY, int S, int MINB, int MCH, bool AN = false>
 static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
     using Gm = SsGeom<TBY, S>;
     constexpr int NT = (2 * TBY + 2) * 32;
@@ -562,13 +581,13 @@ static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
     if (!a.sched) return cudaErrorInvalidValue;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(step2d_ss2<TBY, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Gm::BYTES);
+        cudaError_t e = cudaFuncSetAttribute(step2d_ss2<TBY, S, MINB, AN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_ss2<TBY, S, MINB>, NT, Gm::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_ss2<TBY, S, MINB, AN>, NT, Gm::BYTES);
         if (per_sm < 1) per_sm = 1;
     }
     CUtensorMap mIn, mCL, mIn4, mCL4;
@@ -590,7 +609,7 @@ static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
     if (nunits > (1 << 30)) return cudaErrorInvalidValue;
     U.nunits = (int)nunits;
     const int blocks = (int)(nunits < slots ? nunits : slots);
-    step2d_ss2<TBY, S, MINB><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mIn4, mCL4, use_tma, U);
+    step2d_ss2<TBY, S, MINB, AN><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mIn4, mCL4, use_tma, U);
     return cudaGetLastError();
 }
 
@@ -922,6 +941,10 @@ cudaError_t launch_batch_ss2(const StepArgs *args, const BatchUnit *units, int n
     if (shape == 1) return launch_bss<3, 4, 3>(args, units, nunits, sched, t0p, toff, par, pk, rows, s);
     return launch_bss<4, 3, 3>(args, units, nunits, sched, t0p, toff, par, pk, rows, s);
 }
+
+// An anisotropic medium (uniform tensor, no pole): the strip kernel with the general kernel's site update, chunk
+// rows, stages, CTAs per SM and chunks per unit of shape 1.
+cudaError_t launch_step_2d_ss2_an(const StepArgs &a, cudaStream_t s) { return launch_ss<4, 3, 3, 16, true>(a, s); }
 
 cudaError_t ss_set_wait_limit(unsigned long long ns) {
     return cudaMemcpyToSymbol(g_ss_wait_limit_ns, &ns, sizeof ns);

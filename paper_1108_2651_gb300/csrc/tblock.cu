@@ -1544,7 +1544,8 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
     if (a.med.wp2)  // a dispersive pole: with a tensor (AN and POLE), or isotropic (POLE alone)
         return (a.med.ar != 1.f || a.med.amu != 1.f) ? launch_tb<6, 256, 3, false, true, true>(a, s)
                                                        : launch_tb<6, 256, 3, false, false, true>(a, s);
-    if (a.med.ar != 1.f || a.med.amu != 1.f) return launch_tb<6, 256, 5, false, true>(a, s);  // anisotropic
+    if (a.med.ar != 1.f || a.med.amu != 1.f)  // anisotropic: the tile kernel (shape 0) or the strip kernel (1)
+        return shape == 1 ? launch_step_2d_ss2_an(a, s) : launch_tb<6, 256, 5, false, true>(a, s);
     if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7 + rs2_nshapes()) return launch_step_2d_ss2(a, shape - 7 - rs2_nshapes(), s);  // sstream.cu
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)

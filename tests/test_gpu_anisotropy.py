@@ -100,18 +100,19 @@ def test_plane_waves_on_gpu_follow_the_per_axis_dispersion(lbem):
 
 @pytest.mark.parametrize("shape,aniso", [((3, 5), (2.5, 1.2)), ((37, 130), (0.7, 1.6)), ((130, 259), (1.7, 1.7))])
 def test_two_step_launches_equal_single_steps_bit_for_bit(lbem, shape, aniso):
-    """Without walls or a pole an anisotropic medium steps in pairs (the tile kernel with per-axis weights):
-    the same bits as one step per launch (the general kernel), with and without graph replay, odd step
-    counts included."""
+    """Without walls or a pole an anisotropic medium steps in pairs (the tile kernel, shape 0, or the strip
+    kernel, shape 1, with per-axis weights): the same bits as one step per launch (the general kernel), with
+    and without graph replay, odd step counts included."""
     import torch
 
     p = _problem(shape, 900 + shape[1], 37, aniso)
     ref = gpu_run(p, steps_per_pass=1)
-    for graphs in (False, True):
+    for tile_shape, graphs in ((0, False), (0, True), (1, False), (1, True)):
         stream = torch.cuda.Stream()  # graph capture needs a non-default stream
         s = lbem.Solver(p.shape, stream=stream.cuda_stream)
         s.set_problem(p)
-        assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2
+        lbem.lbem_set_temporal_blocking(s.h, 2, tile_shape)
+        assert lbem.lbem_get_temporal_blocking(s.h)[:2] == (2, tile_shape)
         lbem.lbem_set_graphs(s.h, graphs)
         s.step(10)
         s.step(27)
@@ -148,7 +149,7 @@ def test_anisotropy_errors_and_switching_back(lbem):
     assert e.value.status == 3
     s.set_problem(p)
     assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2  # no walls, no pole: two steps per launch
-    assert lbem.lbem_get_temporal_blocking(s.h)[2] == 1
+    assert lbem.lbem_get_temporal_blocking(s.h)[2] == 2  # the tile kernel and the strip kernel
     lbem.lbem_set_boundaries(s.h, (PEC, 0, 0), 0, 0.0)
     assert lbem.lbem_get_temporal_blocking(s.h)[0] == 1  # walls: the general kernel, one step per launch
     lbem.lbem_set_boundaries(s.h, (0, 0, 0), 0, 0.0)
