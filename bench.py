@@ -346,12 +346,15 @@ def other_forms(lbem, torch, p, peak, stream):
         if spp_set == 1:
             lbem.lbem_set_temporal_blocking(s.h, 1, -1)
         ms, v, spp = _time_run(lbem, torch, s, pm, 2000, stream)
+        shape_mu = lbem.lbem_get_temporal_blocking(s.h)[1]
         s.close()
         per = ms / (2000 // spp)
         gbs = 52 * n / (per * 1e-3) / 1e9
+        kern = ("step2d_ss2<MU>" if shape_mu == 2 else f"step2d_tb2<MU> (tile shape {shape_mu})") if spp == 2 \
+            else f"step2d<f32, MU> (variant {v})"
         out[key] = {"mlups": n * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                     "frac": gbs / peak, "bytes_per_site_per_launch": 52, "steps_per_launch": spp, "variant": v,
-                    "lb_steps": 2000}
+                    "lb_steps": 2000, "kernel": kern}
     # the same medium in a PEC box with a 32-site absorbing layer, 2000 steps: the stream-collide launches plus
     # the edge kernel after each (44 algorithmic B/site per launch; the edge recompute counts as overhead)
     pw = W.heterogeneous_2d_walls(p.shape[0], seed=2, nsteps=2000)

@@ -185,14 +185,14 @@ static int two_step_nshapes(const lbem_t *h) {
     return h->disp ? 1 : h->aniso ? 2 : tb2_nshapes(h->storage, h->has_mu);
 }
 // The two-step shape to launch: the one set (or autotuned) when it exists for this medium, else 0, except that a
-// large FP32 grid (at least 12M sites) of uniform mu, or with an anisotropic tensor and no pole, defaults to the
-// strip-streaming kernel (sstream.cu; at 4096^2 274.6k Mlups against 247.3k for tile shape 0; at 2048^2 and below
-// the tile kernel is faster).
+// large FP32 grid (at least 12M sites) without a pole defaults to the strip-streaming kernel (sstream.cu; uniform mu
+// at 4096^2: 274.6k Mlups against 247.3k for tile shape 0; at 2048^2 and below the tile kernel is faster): shape 10
+// for uniform mu, 2 with a heterogeneous mu, 1 with an anisotropic tensor.
 static int two_step_shape(const lbem_t *h) {
     if (h->disp) return 0;
-    const bool big = h->tblock == 2 && h->dim == 2 && h->storage == LBEM_F32 && !h->has_mu && h->nsite >= 12000000;
+    const bool big = h->tblock == 2 && h->dim == 2 && h->storage == LBEM_F32 && h->nsite >= 12000000;
     if (h->aniso) return h->tb_shape_set ? (h->tb_shape == 1 ? 1 : 0) : (big ? 1 : 0);
-    if (!h->tb_shape_set && big) return 7 + rs2_nshapes() + 1;
+    if (!h->tb_shape_set && big) return h->has_mu ? 2 : 7 + rs2_nshapes() + 1;
     return h->tblock == 2 && h->tb_shape < tb2_nshapes(h->storage, h->has_mu) ? h->tb_shape : 0;
 }
 static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two_step_ok(h) ? 2 : 1; }

@@ -567,6 +567,7 @@ cudaError_t launch_step_2d_rs2(const StepArgs &a, int shape, cudaStream_t s);
 int ss2_nshapes();  // strip streaming (sstream.cu): two steps per launch, FP32, uniform mu
 cudaError_t launch_step_2d_ss2(const StepArgs &a, int shape, cudaStream_t s);
 cudaError_t launch_step_2d_ss2_an(const StepArgs &a, cudaStream_t s);  // anisotropic medium, no pole
+cudaError_t launch_step_2d_ss2_mu(const StepArgs &a, cudaStream_t s);  // heterogeneous permeability
 bool ss2_take_timeouts();  // reads and clears the strip kernel's wait-timeout flag
 cudaError_t ss_set_wait_limit(unsigned long long ns);
 bool tb2_take_timeouts();  // reads and clears the two-step kernel's wait-timeout flag

@@ -64,21 +64,22 @@ struct SsDesc {
     SsEvList ev;
 };
 
-template <int TBY, int S, bool BATCH = false>
+template <int TBY, int S, bool BATCH = false, bool MU = false>
 struct SsGeom {
     static constexpr int up32(int n) { return (n + 31) / 32 * 32; }
+    static constexpr int NPL = MU ? 8 : 6;  // staged planes: populations 0..4, c_L^2 (and d_x ln mu, d_y ln mu)
     static constexpr int M = 2 * TBY + 2;
-    static constexpr int PL_IN = up32(TBY * SW), STAGE = 6 * PL_IN;
-    static constexpr int EPL = up32(4 * TBY), ESTAGE = 6 * EPL;
+    static constexpr int PL_IN = up32(TBY * SW), STAGE = NPL * PL_IN;
+    static constexpr int EPL = up32(4 * TBY), ESTAGE = NPL * EPL;
     static constexpr int PL_P = M * SW;
-    static constexpr int IN_SZ = S * STAGE, E_SZ = BATCH ? 0 : S * ESTAGE, P_SZ = up32(6 * PL_P);  // (no images:
+    static constexpr int IN_SZ = S * STAGE, E_SZ = BATCH ? 0 : S * ESTAGE, P_SZ = up32(NPL * PL_P);  // (no images:
     // the batch's packed members carry theirs)
     static constexpr int DS = S + 2;  // chunk descriptor slots (SsDesc) after the ring, then the mbarriers
     // (the batch kernel keeps a copy of each chunk's member arguments beside the descriptors)
     static constexpr int SZ = IN_SZ + E_SZ + P_SZ + DS * (int)(sizeof(SsDesc) / 4) +
                               (BATCH ? DS * (int)(sizeof(StepArgs) / 4) : 0);
     static constexpr size_t BYTES = sizeof(float) * SZ + 2 * S * sizeof(unsigned long long);
-    static constexpr unsigned TMA_BYTES = sizeof(float) * 6 * TBY * SW, E_BYTES = sizeof(float) * 6 * TBY * 4;
+    static constexpr unsigned TMA_BYTES = sizeof(float) * NPL * TBY * SW, E_BYTES = sizeof(float) * NPL * TBY * 4;
 };
 
 // Which columns of the strip wrap: 0 none (x0-4 .. x0+131 inside the grid), 1 the first strip (x0 = 0, the images
@@ -100,15 +101,18 @@ __device__ __forceinline__ int ss_chunk_mode(const Grid &G, int xm, int s, bool 
 }
 
 // Stage the chunk of step-t rows s .. s+TBY-1 into `st` (and `es`), by the producer warp, arriving on the stage's
-// full mbarrier (count 1).  Modes 0 and 1: lane 0 arrives with the transaction bytes, then lanes issue one box each.
-// Mode 2: every lane issues its share of asynchronous copies (16 bytes where every group of 4 columns stays contiguous
-// after the periodic wrap, else 4), each lane's copies tracked by the mbarrier (its pending count rises until they
-// land), then lane 0 arrives.
-template <int TBY, int S>
+// full mbarrier (count 1): the five population planes at their row shifts, c_L^2 and, with MU, d_x ln mu and d_y ln mu.
+// Modes 0 and 1: lane 0 arrives with the transaction bytes, then lanes issue one box each (lane p plane p, lane
+// NPL + p its images).  Mode 2: every lane issues its share of asynchronous copies (16 bytes where every group of 4
+// columns stays contiguous after the periodic wrap, else 4), each lane's copies tracked by the mbarrier (its pending
+// count rises until they land), then lane 0 arrives.
+template <int TBY, int S, bool MU = false>
 __device__ __forceinline__ void ss_issue(const StepArgs &a, int x0, int xm, int s, int mode, float *st, float *es,
                                          unsigned mbar, const CUtensorMap *tmIn, const CUtensorMap *tmCL,
-                                         const CUtensorMap *tmIn4, const CUtensorMap *tmCL4) {
-    using Gm = SsGeom<TBY, S>;
+                                         const CUtensorMap *tmIn4, const CUtensorMap *tmCL4,
+                                         const CUtensorMap *tmDL = nullptr, const CUtensorMap *tmDL4 = nullptr) {
+    using Gm = SsGeom<TBY, S, false, MU>;
+    constexpr int NPL = Gm::NPL;
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
     if (mode != 2) {
@@ -118,37 +122,40 @@ __device__ __forceinline__ void ss_issue(const StepArgs &a, int x0, int xm, int 
                          : "memory");
         }
         __syncwarp();
-        // one box per lane: lanes 0-5 the planes (c_L^2 last), lanes 6-11 their images
-        const int p = lane < 6 ? lane : lane - 6;
-        if (lane < (mode == 1 ? 12 : 6)) {
+        const bool image = lane >= NPL;
+        const int p = image ? lane - NPL : lane;
+        if (lane < (mode == 1 ? 2 * NPL : NPL)) {
             // the consumers' reads of this stage (ordered by the empty mbarrier) before the async-proxy writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            const int x = lane < 6 ? x0 - 4 : (xm == 1 ? G.nx - 4 : 0);
-            float *dst = lane < 6 ? st + p * Gm::PL_IN : es + p * Gm::EPL;
+            const int x = image ? (xm == 1 ? G.nx - 4 : 0) : x0 - 4;
+            float *dst = image ? es + p * Gm::EPL : st + p * Gm::PL_IN;
             if (p < 5)
-                tma_load_3d(dst, lane < 6 ? tmIn : tmIn4, x, s + ss_shift(p), p, mbar);
+                tma_load_3d(dst, image ? tmIn4 : tmIn, x, s + ss_shift(p), p, mbar);
+            else if (p == 5)
+                tma_load_2d(dst, image ? tmCL4 : tmCL, x, s, mbar);
             else
-                tma_load_2d(dst, lane < 6 ? tmCL : tmCL4, x, s, mbar);
+                tma_load_3d(dst, image ? tmDL4 : tmDL, x, s, p - 6, mbar);
         }
         return;
     }
     const float *in = static_cast<const float *>(a.in.data);
+    auto row_of = [&](int p, int w) -> const float * {  // plane p's source row for staged row w
+        if (p < 5) return in + p * G.plane + (long long)wrapi(s + w + ss_shift(p), G.ny) * G.pitch;
+        const float *base = p == 5 ? a.med.cL2 : a.med.dlnmu + (p - 6) * G.plane;
+        return base + (long long)wrapi(s + w, G.ny) * G.pitch;
+    };
     if (xm == 0 || (G.nx & 3) == 0) {
         constexpr int Q = SW / 4;
-        for (int k = lane; k < 6 * TBY * Q; k += 32) {
+        for (int k = lane; k < NPL * TBY * Q; k += 32) {
             const int pr = k / Q, q = k - pr * Q;  // pr = plane * TBY + row
             const int p = pr / TBY, w = pr - p * TBY;
-            const float *row = p < 5 ? in + p * G.plane + (long long)wrapi(s + w + ss_shift(p), G.ny) * G.pitch
-                                     : a.med.cL2 + (long long)wrapi(s + w, G.ny) * G.pitch;
-            tb_cpa16(st + p * Gm::PL_IN + w * SW + 4 * q, row + wrapi(x0 - 4 + 4 * q, G.nx));
+            tb_cpa16(st + p * Gm::PL_IN + w * SW + 4 * q, row_of(p, w) + wrapi(x0 - 4 + 4 * q, G.nx));
         }
     } else {
-        for (int k = lane; k < 6 * TBY * SW; k += 32) {
+        for (int k = lane; k < NPL * TBY * SW; k += 32) {
             const int pr = k / SW, c = k - pr * SW;
             const int p = pr / TBY, w = pr - p * TBY;
-            const float *row = p < 5 ? in + p * G.plane + (long long)wrapi(s + w + ss_shift(p), G.ny) * G.pitch
-                                     : a.med.cL2 + (long long)wrapi(s + w, G.ny) * G.pitch;
-            tb_cpa4(st + p * Gm::PL_IN + w * SW + c, row + wrapi(x0 - 4 + c, G.nx));
+            tb_cpa4(st + p * Gm::PL_IN + w * SW + c, row_of(p, w) + wrapi(x0 - 4 + c, G.nx));
         }
     }
     asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];\n" ::"r"(mbar) : "memory");
@@ -160,16 +167,22 @@ __device__ __forceinline__ void ss_issue(const StepArgs &a, int x0, int xm, int 
 // list: the same arithmetic in the same order.  Uniform mu only.
 // With an anisotropic medium (site_events' sbx, sby, jmu: B_x, B_y scaled by r and 1/r, j_z by mubar; 1 leaves every
 // value unchanged).
+// With a heterogeneous permeability the sum starts from the B x grad ln mu term shat0 and a source's current is scaled
+// by mu at the site (wrapped row y).
 __device__ __forceinline__ float ss_list_events(const StepArgs &a, const SsEvList *L, int i, int x, long long t,
                                                 bool owned, float g0, float g1, float g2, float g3, float g4,
-                                                float cl, float sbx = 1.f, float sby = 1.f, float jmu = 1.f) {
-    float shat = 0.f;
+                                                float cl, float sbx = 1.f, float sby = 1.f, float jmu = 1.f,
+                                                float shat0 = 0.f, int y = 0) {
+    float shat = shat0;
     for (int j = L->b[i]; j < L->b[i + 1]; j++) {
         const Event ev = L->rec[j];
         if (ev.x != x) continue;
         if (ev.kind == 0) {
-            if (ev.comp == 2 && t < a.evt.nt)
-                shat = __fsub_rn(shat, __fmul_rn(__ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t), jmu));
+            if (ev.comp == 2 && t < a.evt.nt) {
+                float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
+                if (a.med.mu) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)y * a.g.pitch + x));
+                shat = __fsub_rn(shat, __fmul_rn(jz, jmu));
+            }
         } else if (owned && t < a.evt.cap) {
             const float s = ((g0 + g1) + (g2 + g3)) + g4;
             float v = field2d(ev.comp, cl, s, g4 - g2, g1 - g3);
@@ -229,10 +242,13 @@ __device__ __forceinline__ int ss_stage_chunk(const int (&rp)[3], const Event *e
 //
 // With AN (a uniform in-plane permeability tensor, a.med.ar / a.med.amu) the site update is the general kernel's
 // collide2d_an with its per-axis speeds (r, 1/r) and no pole, and the events scale as in site_events.
-template <bool EV, bool AN = false>
+//
+// With MU (a heterogeneous permeability: d_x ln mu, d_y ln mu of the four sites in dlx, dly) each site's S^ carries
+// B_x d_y ln mu - B_y d_x ln mu (mu_source), as in the single-step kernels.
+template <bool EV, bool AN = false, bool MU = false>
 __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[5], float4 cl, int x0, int gy,
                                            long long t, bool owned, float4 (&o)[5], const SsEvList *el = nullptr,
-                                           int li = 0) {
+                                           int li = 0, float4 dlx = float4(), float4 dly = float4()) {
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
     const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
@@ -240,20 +256,23 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
     for (int k = 0; k < 4; k++) {
         const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k), q4 = get(q[4], k),
                     ck = get(cl, k);
+        const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, get(dlx, k), get(dly, k)) : 0.f;
         Out5 r;
         if (EV) {
             const int gx = x0 + 4 * lane + k;
             const bool own = owned && gx < G.nx && gy < G.ny;
             const float jmu = AN ? a.med.amu : 1.f;
             const float shat = el ? ss_list_events(a, el, li, wrapi(gx, G.nx), t, own, q0, q1, q2, q3, q4, ck, ar, ri,
-                                                   jmu)
+                                                   jmu, shat0, wrapi(gy, G.ny))
                                   : AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4,
                                                      ck, 0.f, 0.f, ar, ri, jmu)
                                        : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4,
-                                                     ck);
+                                                     ck, shat0);
             r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f) : collide2d(q0, q1, q2, q3, q4, ck, shat);
         } else {
-            r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, 0.f, ar, ri, fs, 0.f) : collide2d_free(q0, q1, q2, q3, q4, ck);
+            r = AN   ? collide2d_an(q0, q1, q2, q3, q4, ck, 0.f, ar, ri, fs, 0.f)
+                : MU ? collide2d(q0, q1, q2, q3, q4, ck, shat0)
+                     : collide2d_free(q0, q1, q2, q3, q4, ck);
         }
         set(o[0], k, r.o0);
         set(o[1], k, r.o1);
@@ -265,8 +284,13 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
 
 // The populations pulled by a lane's four sites at row `row` of a stage S with plane stride PL: g0, g2, g4 from
 // columns c.., g1 from c-1.., g3 from c+1.. (Eq. 17), and c_L^2 from plane 5.
-__device__ __forceinline__ void ss_pull(const float *S, int PL, int row, int c, float4 (&q)[5], float4 &cl) {
+__device__ __forceinline__ void ss_pull(const float *S, int PL, int row, int c, float4 (&q)[5], float4 &cl,
+                                        float4 *dlx = nullptr, float4 *dly = nullptr) {
     const float *r = S + row * SW + c;
+    if (dlx) {  // planes 6 and 7: d_x ln mu, d_y ln mu
+        *dlx = lds4(r + 6 * PL);
+        *dly = lds4(r + 7 * PL);
+    }
     q[0] = lds4(r);
     const float4 l1 = lds4(r + PL - 4), m1 = lds4(r + PL);
     q[1] = make_float4(l1.w, m1.x, m1.y, m1.z);
@@ -286,24 +310,28 @@ __device__ __forceinline__ bool ss_row_events(const StepArgs &a, int gy) {
 // the rows that pull them (ring row u = r - ys + 2 for planes 0, 1, 3 and c_L^2, u + 1 for plane 2, u - 1 for plane
 // 4).  With the images in `es` (emode 1: left of the strip, 2: right of it) lane 0's g1 or lane 31's g3 come from
 // there.
-template <int TBY, int S, bool EV, bool AN = false>
+template <int TBY, int S, bool EV, bool AN = false, bool MU = false>
 __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, const float *es, int emode, float *P,
                                           int x0, int ys, int ye, int r, int w, int u, long long t,
                                           const SsEvList *el) {
     using Gm = SsGeom<TBY, S>;
     constexpr int M = Gm::M, PP = Gm::PL_P;
     const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
-    float4 q[5], cl, o[5];
-    ss_pull(st, Gm::PL_IN, w, c, q, cl);
+    float4 q[5], cl, o[5], dlx = make_float4(0.f, 0.f, 0.f, 0.f), dly = dlx;
+    ss_pull(st, Gm::PL_IN, w, c, q, cl, MU ? &dlx : nullptr, MU ? &dly : nullptr);
     if (emode == 1 && lane == 0) q[1].x = es[Gm::EPL + w * 4 + 3];        // column x0-1 = nx-1
     if (emode == 2 && lane == 31) q[3].w = es[3 * Gm::EPL + w * 4 + 0];   // column x0+128 = 0
-    ss_update4<EV, AN>(a, q, cl, x0, r, t, r >= ys && r < ye, o, el, w + 1);
+    ss_update4<EV, AN, MU>(a, q, cl, x0, r, t, r >= ys && r < ye, o, el, w + 1, dlx, dly);
     const int s0 = u % M, s2 = s0 == M - 1 ? 0 : s0 + 1, s4 = s0 == 0 ? M - 1 : s0 - 1;
     float *p0 = P + s0 * SW + c;
     sts4(p0, o[0]);
     sts4(p0 + PP, o[1]);
     sts4(p0 + 3 * PP, o[3]);
     sts4(p0 + 5 * PP, cl);
+    if (MU) {  // the medium of the row, for step t+1
+        sts4(p0 + 6 * PP, dlx);
+        sts4(p0 + 7 * PP, dly);
+    }
     sts4(P + 2 * PP + s2 * SW + c, o[2]);
     sts4(P + 4 * PP + s4 * SW + c, o[4]);
 }
@@ -311,7 +339,7 @@ __device__ __forceinline__ void ss_step_a(const StepArgs &a, const float *st, co
 // The ring sites of the chunk in stage `st`, by the ring warp: lane 2w takes column x0-1 of chunk row w (plane 1
 // only), lane 2w+1 column x0+128 (plane 3 only), at ring row p TBY + w + 1 (p: the CTA's phase); with the images in
 // `es` the columns outside the grid come from there.
-template <int TBY, int S, bool AN = false>
+template <int TBY, int S, bool AN = false, bool MU = false>
 __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, const float *es, int emode, float *P,
                                         int x0, int s, int p, bool events, long long t, const SsEvList *el) {
     using Gm = SsGeom<TBY, S>;
@@ -326,13 +354,16 @@ __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, cons
     const float q0 = v(0, cc), q1 = v(1, cc - 1), q2 = v(2, cc), q3 = v(3, cc + 1), q4 = v(4, cc), ck = v(5, cc);
     const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
     const float jmu = AN ? a.med.amu : 1.f;
-    float shat = 0.f;
+    const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, v(6, cc), v(7, cc)) : 0.f;
+    float shat = shat0;
     if (el)
-        shat = ss_list_events(a, el, w + 1, wrapi(x0 - 4 + cc, a.g.nx), t, false, q0, q1, q2, q3, q4, ck, ar, ri, jmu);
+        shat = ss_list_events(a, el, w + 1, wrapi(x0 - 4 + cc, a.g.nx), t, false, q0, q1, q2, q3, q4, ck, ar, ri, jmu,
+                              shat0, wrapi(r, a.g.ny));
     else if (events && ss_row_events(a, r))
         shat = AN ? site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck, 0.f,
                                 0.f, ar, ri, jmu)
-                  : site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck);
+                  : site_events(a, wrapi(x0 - 4 + cc, a.g.nx), wrapi(r, a.g.ny), t, false, q0, q1, q2, q3, q4, ck,
+                                shat0);
     const Out5 ro = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f)
                        : collide2d(q0, q1, q2, q3, q4, ck, shat);
     const int s0 = (p * TBY + w + 1) % Gm::M;
@@ -343,15 +374,15 @@ __device__ __forceinline__ void ss_ring(const StepArgs &a, const float *st, cons
 }
 
 // Step t+1 on global row rb (ring row ub), written as 16-byte streaming stores.
-template <int TBY, int S, bool EV, bool AN = false>
+template <int TBY, int S, bool EV, bool AN = false, bool MU = false>
 __device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int x0, int rb, int ub, long long t,
                                           const SsEvList *el, int w) {
     using Gm = SsGeom<TBY, S>;
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31, c = 4 + 4 * lane;
-    float4 q[5], cl, o[5];
-    ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl);
-    ss_update4<EV, AN>(a, q, cl, x0, rb, t + 1, true, o, el, w);
+    float4 q[5], cl, o[5], dlx = make_float4(0.f, 0.f, 0.f, 0.f), dly = dlx;
+    ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl, MU ? &dlx : nullptr, MU ? &dly : nullptr);
+    ss_update4<EV, AN, MU>(a, q, cl, x0, rb, t + 1, true, o, el, w, dlx, dly);
     if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
         float4 *op = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)rb * G.pitch + x0 +
                                                 4 * lane);
@@ -413,12 +444,13 @@ __device__ __forceinline__ void ss_unit(const SsUnits &U, int ny, int u, int &x0
 // numbered by the phase (rows of step t+1 that would pull across a unit boundary lie outside their unit and are
 // skipped).  The step-t and ring warps release the stage once they have read it; a barrier of these 2 TBY + 1 warps
 // closes the phase.
-template <int TBY, int S, int MINB, bool AN = false>
+template <int TBY, int S, int MINB, bool AN = false, bool MU = false>
 __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
     step2d_ss2(StepArgs a, const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmCL,
-               const __grid_constant__ CUtensorMap tmIn4, const __grid_constant__ CUtensorMap tmCL4, int use_tma,
+               const __grid_constant__ CUtensorMap tmIn4, const __grid_constant__ CUtensorMap tmCL4,
+               const __grid_constant__ CUtensorMap tmDL, const __grid_constant__ CUtensorMap tmDL4, int use_tma,
                SsUnits U) {
-    using Gm = SsGeom<TBY, S>;
+    using Gm = SsGeom<TBY, S, false, MU>;
     constexpr int NC = 2 * TBY + 1, DS = Gm::DS;  // consumer warps (the ring warp is warp 2 TBY)
     extern __shared__ __align__(1024) float sm[];
     float *E = sm + Gm::IN_SZ;
@@ -438,8 +470,13 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
     const unsigned long long wait_limit = g_ss_wait_limit_ns;
     if (warp == NC) {
         // ---- producer (every lane keeps the same unit state)
-        if (lane < 4) {  // the tensor maps, into the copy engine's descriptor cache
-            const CUtensorMap *m = lane == 0 ? &tmIn : lane == 1 ? &tmCL : lane == 2 ? &tmIn4 : &tmCL4;
+        if (lane < (MU ? 6 : 4)) {  // the tensor maps, into the copy engine's descriptor cache
+            const CUtensorMap *m = lane == 0   ? &tmIn
+                                   : lane == 1 ? &tmCL
+                                   : lane == 2 ? &tmIn4
+                                   : lane == 3 ? &tmCL4
+                                   : lane == 4 ? &tmDL
+                                               : &tmDL4;
             asm volatile("prefetch.tensormap [%0];\n" ::"l"(m) : "memory");
         }
         int cK = 0, ck = 0, cx0 = 0, cys = 0, cye = 0, cxm = 0;
@@ -485,8 +522,9 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8 * (c % S)) : "memory");
                 break;
             }
-            ss_issue<TBY, S>(a, d.x, cxm, d.y - 1 + (d.w & 0xffff) * TBY, (d.w >> 16) & 15, sm + (c % S) * Gm::STAGE,
-                             E + (c % S) * Gm::ESTAGE, full0 + 8 * (c % S), &tmIn, &tmCL, &tmIn4, &tmCL4);
+            ss_issue<TBY, S, MU>(a, d.x, cxm, d.y - 1 + (d.w & 0xffff) * TBY, (d.w >> 16) & 15,
+                                 sm + (c % S) * Gm::STAGE, E + (c % S) * Gm::ESTAGE, full0 + 8 * (c % S), &tmIn, &tmCL,
+                                 &tmIn4, &tmCL4, &tmDL, &tmDL4);
         }
         if (!ok) {  // the consumers stopped: flag it, let this warp's copies in flight land (bounded)
             if (lane == 0) atomicExch(&g_ss_timeouts, 1);
@@ -510,10 +548,10 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                 if (va) {
                     const int r = s + warp;
                     if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(a, r)))
-                        ss_step_a<TBY, S, true, AN>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                        ss_step_a<TBY, S, true, AN, MU>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
                                                 ela);
                     else
-                        ss_step_a<TBY, S, false, AN>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
+                        ss_step_a<TBY, S, false, AN, MU>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
                                                  nullptr);
                 }
             } else if (warp < 2 * TBY) {
@@ -522,13 +560,13 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                     const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
                     if (rb >= db.y && rb < db.z) {
                         if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(a, rb)))
-                            ss_step_b<TBY, S, true, AN>(a, P, db.x, rb, (p - 1) * TBY + w, t, elb, w);
+                            ss_step_b<TBY, S, true, AN, MU>(a, P, db.x, rb, (p - 1) * TBY + w, t, elb, w);
                         else
-                            ss_step_b<TBY, S, false, AN>(a, P, db.x, rb, (p - 1) * TBY + w, t, nullptr, w);
+                            ss_step_b<TBY, S, false, AN, MU>(a, P, db.x, rb, (p - 1) * TBY + w, t, nullptr, w);
                     }
                 }
             } else if (va) {
-                ss_ring<TBY, S, AN>(a, st, es, emode, P, da.x, s, p, ss_events(da), t, ela);
+                ss_ring<TBY, S, AN, MU>(a, st, es, emode, P, da.x, s, p, ss_events(da), t, ela);
             }
             if (va && (warp < TBY || warp == 2 * TBY)) {  // this warp has read the stage: release it to the producer
                 __syncwarp();
@@ -571,31 +609,49 @@ static bool ss_make_maps(const StepArgs &a, int tby, int w, CUtensorMap *mIn, CU
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of the gradient of ln mu ([2][ny][pitch] floats: d_x, d_y; box: one plane of TBY rows of `w` columns).
+static bool ss_make_dl_map(const StepArgs &a, int tby, int w, CUtensorMap *m) {
+    EncodeTiled fn = encode_fn();
+    if (!fn || !a.med.dlnmu || a.g.nx < SW || a.g.ny < tby + 2) return false;
+    const cuuint64_t dims3[3] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny, 2};
+    const cuuint64_t str3[2] = {(cuuint64_t)a.g.pitch * 4, (cuuint64_t)a.g.plane * 4};
+    const cuuint32_t box3[3] = {(cuuint32_t)w, (cuuint32_t)tby, 1};
+    const cuuint32_t one[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(a.med.dlnmu), dims3, str3, box3, one,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Persistent CTAs (as many as are resident, at most one per unit) over units of MCH TBY - 2 rows (MCH chunks each),
 // and units of 2 TBY - 2 rows (two chunks) for the last rows: about two short units per CTA.
-template <int TBY, int S, int MINB, int MCH, bool AN = false>
+template <int TBY, int S, int MINB, int MCH, bool AN = false, bool MU = false>
 static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
-    using Gm = SsGeom<TBY, S>;
+    using Gm = SsGeom<TBY, S, false, MU>;
     constexpr int NT = (2 * TBY + 2) * 32;
     static_assert(MCH <= 32, "a unit's event flags are one 32-bit mask");
     if (!a.sched) return cudaErrorInvalidValue;
     static int per_sm = 0, nsm = 0;
     if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(step2d_ss2<TBY, S, MINB, AN>,
+        cudaError_t e = cudaFuncSetAttribute(step2d_ss2<TBY, S, MINB, AN, MU>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::BYTES);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_ss2<TBY, S, MINB, AN>, NT, Gm::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step2d_ss2<TBY, S, MINB, AN, MU>, NT, Gm::BYTES);
         if (per_sm < 1) per_sm = 1;
     }
-    CUtensorMap mIn, mCL, mIn4, mCL4;
+    CUtensorMap mIn, mCL, mIn4, mCL4, mDL, mDL4;
     memset(&mIn, 0, sizeof mIn);
     memset(&mCL, 0, sizeof mCL);
     memset(&mIn4, 0, sizeof mIn4);
     memset(&mCL4, 0, sizeof mCL4);
-    const int use_tma = ss_make_maps(a, TBY, SW, &mIn, &mCL) && ss_make_maps(a, TBY, 4, &mIn4, &mCL4) ? 1 : 0;
+    memset(&mDL, 0, sizeof mDL);
+    memset(&mDL4, 0, sizeof mDL4);
+    const int use_tma = ss_make_maps(a, TBY, SW, &mIn, &mCL) && ss_make_maps(a, TBY, 4, &mIn4, &mCL4) &&
+                                (!MU || (ss_make_dl_map(a, TBY, SW, &mDL) && ss_make_dl_map(a, TBY, 4, &mDL4)))
+                            ? 1
+                            : 0;
     SsUnits U;
     U.nstrip = (a.g.nx + SBX - 1) / SBX;
     U.H = MCH * TBY - 2;
@@ -609,7 +665,7 @@ static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
     if (nunits > (1 << 30)) return cudaErrorInvalidValue;
     U.nunits = (int)nunits;
     const int blocks = (int)(nunits < slots ? nunits : slots);
-    step2d_ss2<TBY, S, MINB, AN><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mIn4, mCL4, use_tma, U);
+    step2d_ss2<TBY, S, MINB, AN, MU><<<blocks, NT, Gm::BYTES, s>>>(a, mIn, mCL, mIn4, mCL4, mDL, mDL4, use_tma, U);
     return cudaGetLastError();
 }
 
@@ -945,6 +1001,12 @@ cudaError_t launch_batch_ss2(const StepArgs *args, const BatchUnit *units, int n
 // An anisotropic medium (uniform tensor, no pole): the strip kernel with the general kernel's site update, chunk
 // rows, stages, CTAs per SM and chunks per unit of shape 1.
 cudaError_t launch_step_2d_ss2_an(const StepArgs &a, cudaStream_t s) { return launch_ss<4, 3, 3, 16, true>(a, s); }
+
+// A heterogeneous permeability: the strip kernel with the d_x ln mu, d_y ln mu planes staged beside c_L^2 (and kept
+// with it for step t+1), 4-row chunks, 3 stages, 2 CTAs per SM (96 KB), 16 chunks per unit.
+cudaError_t launch_step_2d_ss2_mu(const StepArgs &a, cudaStream_t s) {
+    return launch_ss<4, 3, 2, 16, false, true>(a, s);
+}
 
 cudaError_t ss_set_wait_limit(unsigned long long ns) {
     return cudaMemcpyToSymbol(g_ss_wait_limit_ns, &ns, sizeof ns);

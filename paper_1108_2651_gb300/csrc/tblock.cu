@@ -1527,10 +1527,11 @@ static cudaError_t launch_16(const StepArgs &a, int shape, cudaStream_t s) {
 
 // Tile shapes (rows, threads, CTAs per SM).  Measured on 4096^2 (heterogeneous medium, FP32): 6 rows at five
 // CTAs per SM is the fastest; the others remain selectable for other sizes and for the bit-identity tests.
-// With a heterogeneous permeability (FP32 only): 6 rows at four CTAs per SM (51 KB), or 14 rows at two.
+// With a heterogeneous permeability (FP32 only): 6 rows at four CTAs per SM (51 KB), 14 rows at two, or the strip
+// kernel (sstream.cu).
 // With an anisotropic medium (FP32, no mu array) only tile shape 0.
 int tb2_nshapes(int storage, bool has_mu) {
-    if (has_mu) return storage == LBEM_F32 ? 2 : 0;
+    if (has_mu) return storage == LBEM_F32 ? 3 : 0;
     return storage == LBEM_F32 ? 7 + rs2_nshapes() + ss2_nshapes() : 7;
 }
 
@@ -1546,7 +1547,10 @@ cudaError_t launch_step_2d_tb2(const StepArgs &a, int storage, int shape, cudaSt
                                                        : launch_tb<6, 256, 3, false, false, true>(a, s);
     if (a.med.ar != 1.f || a.med.amu != 1.f)  // anisotropic: the tile kernel (shape 0) or the strip kernel (1)
         return shape == 1 ? launch_step_2d_ss2_an(a, s) : launch_tb<6, 256, 5, false, true>(a, s);
-    if (a.med.dlnmu) return shape == 1 ? launch_tb<14, 512, 2, true>(a, s) : launch_tb<6, 256, 4, true>(a, s);
+    if (a.med.dlnmu)  // heterogeneous mu: two tile shapes, then the strip kernel
+        return shape == 2   ? launch_step_2d_ss2_mu(a, s)
+               : shape == 1 ? launch_tb<14, 512, 2, true>(a, s)
+                            : launch_tb<6, 256, 4, true>(a, s);
     if (shape >= 7 + rs2_nshapes()) return launch_step_2d_ss2(a, shape - 7 - rs2_nshapes(), s);  // sstream.cu
     if (shape >= 7) return launch_step_2d_rs2(a, shape - 7, s);  // register streaming (rstream.cu)
     switch (shape) {

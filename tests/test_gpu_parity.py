@@ -529,27 +529,27 @@ def test_autotuned_stepping_is_bitwise_identical(lbem, spp):
                                    (9, 1), (200, 7), (301, 777), (40, 4), (50, 264)])
 def test_two_step_blocking_heterogeneous_mu_is_bitwise_identical(lbem, shape):
     """Two steps per launch with a heterogeneous permeability (the grad ln mu planes staged beside c_L^2): the
-    same bits as single steps for both tile shapes, with sources and receivers anywhere, odd step counts and
-    graphs; a third tile shape does not exist for such a medium, and three steps per launch fall back to two
-    (uniform mu only), as does a shape set before the medium."""
+    same bits as single steps for both tile shapes and the strip kernel, with sources and receivers anywhere, odd
+    step counts and graphs; a fourth shape does not exist for such a medium, and three steps per launch fall back
+    to two (uniform mu only), as does a shape set before the medium."""
     p = _problem_small(2, shape, 98, 41, mu=True, nsrc=7, nrec=15)
     ref = gpu_run(p, steps_per_pass=1)
     import torch
 
-    for spp_set, tile_shape, graphs in [(2, k, g) for k in range(2) for g in (False, True)] + [(3, 0, False),
+    for spp_set, tile_shape, graphs in [(2, k, g) for k in range(3) for g in (False, True)] + [(3, 0, False),
                                                                                               (2, 8, False)]:
         stream = torch.cuda.Stream() if graphs else None
         s = lbem.Solver(p.shape, stream=stream.cuda_stream if stream else None)
-        if tile_shape < 2:
+        if tile_shape < 3:
             s.set_problem(p)
             lbem.lbem_set_temporal_blocking(s.h, spp_set, tile_shape)
         else:
             lbem.lbem_set_temporal_blocking(s.h, spp_set, tile_shape)
             s.set_problem(p)
         spp, _, nsh = lbem.lbem_get_temporal_blocking(s.h)
-        assert spp == 2 and nsh == (3 if spp_set == 3 else 2)
+        assert spp == 2 and nsh == 3
         with pytest.raises(lbem.LbemError):
-            lbem.lbem_set_temporal_blocking(s.h, 2, 2)
+            lbem.lbem_set_temporal_blocking(s.h, 2, 3)
         if graphs:
             lbem.lbem_set_graphs(s.h, True)
         s.step(20)
