@@ -175,8 +175,8 @@ def run_batch_main(args, lbem, torch, stream, peak, peak_kind):
                       "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "batch256", "media": len(probs), "sites": sites, "lb_steps": nsteps},
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                                   "traffic": None, "kernel": ("step2d_batch_tb2" if spl == 2 else "step2d_batch") +
-                                   f" (variant {v})", "steps_per_launch": spl,
+                                   "traffic": None, "kernel": ("step2d_batch_ss2" if v >= 14 else "step2d_batch_tb2" if spl == 2
+                                                                 else "step2d_batch") + f" (variant {v})", "steps_per_launch": spl,
                                    "ms_per_launch": per, "peak_kind": peak_kind},
                       "gpu_launches": args.steps * launches, "clocks": clk.summary()}), flush=True)
 
@@ -337,7 +337,7 @@ def other_forms(lbem, torch, p, peak, stream):
     out["batch256"] = {"mlups": sites * 2000 / (ms * 1e-3) / 1e6, "ms_per_launch": per, "achieved_gbs": gbs,
                        "frac": gbs / peak, "sites": sites, "media": len(probs), "lb_steps": 2000, "variant": v,
                        "graph": True, "steps_per_launch": spl,
-                       "kernel": "step2d_batch_tb2" if spl == 2 else "step2d_batch"}
+                       "kernel": "step2d_batch_ss2" if v >= 14 else "step2d_batch_tb2" if spl == 2 else "step2d_batch"}
     # heterogeneous permeability (B x grad ln mu source at every site), 2000 steps: 52 B/site per launch (the
     # grad ln mu planes add 8 to the 44), two steps per launch by default, then single-step launches
     pm = W.heterogeneous_2d_mu(p.shape[0], seed=2, nsteps=2000)

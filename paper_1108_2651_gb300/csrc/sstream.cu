@@ -194,6 +194,48 @@ __device__ __forceinline__ float ss_list_events(const StepArgs &a, const SsEvLis
     return shat;
 }
 
+// The staged events of window row i for a lane's four sites (columns gx0 .. gx0+3, wrapped into 0 .. nx-1), in one
+// pass over the row's records: S^ of each site (shat0 minus mu j_z of the site's sources, in record order, as
+// ss_list_events forms it) and the receiver writes of the pre-collision fields of the owned sites (`owned`: the
+// row is the caller's; a site is owned when also gx < nx, so an owned column appears at most once).
+__device__ __forceinline__ float4 ss_list_events4(const StepArgs &a, const SsEvList *L, int i, int gx0, int nx,
+                                                  long long t, bool owned, const float4 (&q)[5], float4 cl,
+                                                  float sbx, float sby, float jmu, float4 sh, int y) {
+    const int w0 = wrapi(gx0, nx);
+    for (int j = L->b[i]; j < L->b[i + 1]; j++) {
+        const Event ev = L->rec[j];
+        int dx = ev.x - w0;  // site k sits at column ev.x when k = dx + a multiple of nx (several only if nx < 4)
+        if (dx < 0) dx += nx;
+        const bool m0 = dx == 0, m1 = dx == 1 || (dx == 0 && nx == 1),
+                   m2 = dx == 2 || (dx < 2 && (2 - dx) % nx == 0), m3 = dx == 3 || (dx < 3 && (3 - dx) % nx == 0);
+        if (!(m0 || m1 || m2 || m3)) continue;
+        if (ev.kind == 0) {
+            if (ev.comp == 2 && t < a.evt.nt) {
+                float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
+                if (a.med.mu) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)y * a.g.pitch + ev.x));
+                const float d = __fmul_rn(jz, jmu);
+                if (m0) sh.x = __fsub_rn(sh.x, d);
+                if (m1) sh.y = __fsub_rn(sh.y, d);
+                if (m2) sh.z = __fsub_rn(sh.z, d);
+                if (m3) sh.w = __fsub_rn(sh.w, d);
+            }
+        } else if (owned && t < a.evt.cap) {
+            const bool r0 = m0 && gx0 < nx, r1 = m1 && gx0 + 1 < nx, r2 = m2 && gx0 + 2 < nx, r3 = m3 && gx0 + 3 < nx;
+            if (r0 || r1 || r2 || r3) {
+                const int k = r0 ? 0 : r1 ? 1 : r2 ? 2 : 3;
+                const float g0 = get(q[0], k), g1 = get(q[1], k), g2 = get(q[2], k), g3 = get(q[3], k),
+                            g4 = get(q[4], k);
+                const float s = ((g0 + g1) + (g2 + g3)) + g4;
+                float v = field2d(ev.comp, get(cl, k), s, g4 - g2, g1 - g3);
+                if (ev.comp == 3) v = __fmul_rn(v, sbx);
+                if (ev.comp == 4) v = __fmul_rn(v, sby);
+                a.evt.traces[(long long)ev.index * a.evt.cap + t] = v;
+            }
+        }
+    }
+    return sh;
+}
+
 // Whether window row i of a staged list holds an event.
 __device__ __forceinline__ bool ss_list_has_row(const SsEvList *L, int i) { return L->b[i + 1] > L->b[i]; }
 
@@ -252,22 +294,44 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
     const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
+    if (EV && el) {  // the staged list: one pass over the row's records for the four sites, then the collisions
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MU) {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                set(sh, k, mu_source(get(q[4], k) - get(q[2], k), get(q[1], k) - get(q[3], k), get(dlx, k),
+                                     get(dly, k)));
+        }
+        sh = ss_list_events4(a, el, li, x0 + 4 * lane, G.nx, t, owned && gy < G.ny, q, cl, ar, ri,
+                             AN ? a.med.amu : 1.f, sh, wrapi(gy, G.ny));
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k),
+                        q4 = get(q[4], k), ck = get(cl, k);
+            const Out5 r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, get(sh, k), ar, ri, fs, 0.f)
+                              : collide2d(q0, q1, q2, q3, q4, ck, get(sh, k));
+            set(o[0], k, r.o0);
+            set(o[1], k, r.o1);
+            set(o[2], k, r.o2);
+            set(o[3], k, r.o3);
+            set(o[4], k, r.o4);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k), q4 = get(q[4], k),
                     ck = get(cl, k);
         const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, get(dlx, k), get(dly, k)) : 0.f;
         Out5 r;
-        if (EV) {
+        if (EV) {  // events walked in the global tables
             const int gx = x0 + 4 * lane + k;
             const bool own = owned && gx < G.nx && gy < G.ny;
             const float jmu = AN ? a.med.amu : 1.f;
-            const float shat = el ? ss_list_events(a, el, li, wrapi(gx, G.nx), t, own, q0, q1, q2, q3, q4, ck, ar, ri,
-                                                   jmu, shat0, wrapi(gy, G.ny))
-                                  : AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4,
-                                                     ck, 0.f, 0.f, ar, ri, jmu)
-                                       : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4,
-                                                     ck, shat0);
+            const float shat = AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck,
+                                                0.f, 0.f, ar, ri, jmu)
+                                  : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck,
+                                                shat0);
             r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f) : collide2d(q0, q1, q2, q3, q4, ck, shat);
         } else {
             r = AN   ? collide2d_an(q0, q1, q2, q3, q4, ck, 0.f, ar, ri, fs, 0.f)
