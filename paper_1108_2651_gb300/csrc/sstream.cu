@@ -200,7 +200,7 @@ __device__ __forceinline__ float ss_list_events(const StepArgs &a, const SsEvLis
 // row is the caller's; a site is owned when also gx < nx, so an owned column appears at most once).
 __device__ __forceinline__ float4 ss_list_events4(const StepArgs &a, const SsEvList *L, int i, int gx0, int nx,
                                                   long long t, bool owned, const float4 (&q)[5], float4 cl,
-                                                  float sbx, float sby, float jmu, float4 sh, int y) {
+                                                  float sbx, float sby, float jmu, float4 sh, int y, bool &src) {
     const int w0 = wrapi(gx0, nx);
     for (int j = L->b[i]; j < L->b[i + 1]; j++) {
         const Event ev = L->rec[j];
@@ -214,6 +214,7 @@ __device__ __forceinline__ float4 ss_list_events4(const StepArgs &a, const SsEvL
                 float jz = __ldg(a.evt.amp + (long long)ev.index * a.evt.nt + t);
                 if (a.med.mu) jz = __fmul_rn(jz, __ldg(a.med.mu + (long long)y * a.g.pitch + ev.x));
                 const float d = __fmul_rn(jz, jmu);
+                src = true;
                 if (m0) sh.x = __fsub_rn(sh.x, d);
                 if (m1) sh.y = __fsub_rn(sh.y, d);
                 if (m2) sh.z = __fsub_rn(sh.z, d);
@@ -278,12 +279,15 @@ __device__ __forceinline__ int ss_stage_chunk(const int (&rp)[3], const Event *e
     return 3 << 25;
 }
 
-// Four site updates at global row gy, columns x0+4*lane.. (collide2d with the sites' sources and receivers where
-// EV, else collide2d_free), from the pulled populations q[0..4] and c_L^2; with a staged list `el` the events come
-// from it (window row li).
+// Four site updates at global row gy, columns x0+4*lane.., from the pulled populations q[0..4] and c_L^2.  Without
+// EV the sources and receivers, if any, come from a staged list `el` (window row li): the row takes the plain path,
+// collide2d_free, and a lane with a source adds the collision's S^ terms afterwards (collide2d is collide2d_free
+// followed by those additions, so the bits are collide2d's).  With EV they come from a staged list `el`, or with
+// none (a chunk not staged) are looked up per site in the global tables, and every site takes collide2d.
 //
 // With AN (a uniform in-plane permeability tensor, a.med.ar / a.med.amu) the site update is the general kernel's
-// collide2d_an with its per-axis speeds (r, 1/r) and no pole, and the events scale as in site_events.
+// collide2d_an with its per-axis speeds (r, 1/r) and no pole, and the events scale as in site_events; its event
+// rows take the EV path (folded into the plain path they slowed its plain rows).
 //
 // With MU (a heterogeneous permeability: d_x ln mu, d_y ln mu of the four sites in dlx, dly) each site's S^ carries
 // B_x d_y ln mu - B_y d_x ln mu (mu_source), as in the single-step kernels.
@@ -294,7 +298,9 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
     const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
-    if (EV && el) {  // the staged list: one pass over the row's records for the four sites, then the collisions
+    if (!EV) {
+        // S^ of the four sites: the permeability term (MU), minus mu j_z of the sources of a staged list `el`, whose
+        // receivers are written here from the pre-collision populations
         float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
         if (MU) {
 #pragma unroll
@@ -302,14 +308,47 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
                 set(sh, k, mu_source(get(q[4], k) - get(q[2], k), get(q[1], k) - get(q[3], k), get(dlx, k),
                                      get(dly, k)));
         }
-        sh = ss_list_events4(a, el, li, x0 + 4 * lane, G.nx, t, owned && gy < G.ny, q, cl, ar, ri,
-                             AN ? a.med.amu : 1.f, sh, wrapi(gy, G.ny));
+        bool src = false;
+        if (!AN && el)
+            sh = ss_list_events4(a, el, li, x0 + 4 * lane, G.nx, t, owned && gy < G.ny, q, cl, ar, ri,
+                                 AN ? a.med.amu : 1.f, sh, wrapi(gy, G.ny), src);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k),
                         q4 = get(q[4], k), ck = get(cl, k);
-            const Out5 r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, get(sh, k), ar, ri, fs, 0.f)
-                              : collide2d(q0, q1, q2, q3, q4, ck, get(sh, k));
+            const Out5 r = AN   ? collide2d_an(q0, q1, q2, q3, q4, ck, 0.f, ar, ri, fs, 0.f)
+                           : MU ? collide2d(q0, q1, q2, q3, q4, ck, get(sh, k))
+                                : collide2d_free(q0, q1, q2, q3, q4, ck);
+            set(o[0], k, r.o0);
+            set(o[1], k, r.o1);
+            set(o[2], k, r.o2);
+            set(o[3], k, r.o3);
+            set(o[4], k, r.o4);
+        }
+        if (!MU && src) {  // the source terms added as the collision with S^ adds them (+0 S^ adds -0: no change)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float ck = get(cl, k), h = get(sh, k);
+                const float w0 = __fsub_rn(1.f, 2.f * ck);
+                const float Tm = __fmul_rn(-0.5f * ck, h), T0 = __fmul_rn(-w0, h);
+                set(o[0], k, __fadd_rn(get(o[0], k), T0));
+                set(o[1], k, __fadd_rn(get(o[1], k), Tm));
+                set(o[2], k, __fadd_rn(get(o[2], k), Tm));
+                set(o[3], k, __fadd_rn(get(o[3], k), Tm));
+                set(o[4], k, __fadd_rn(get(o[4], k), Tm));
+            }
+        }
+        return;
+    }
+    if (AN && el) {  // EV with a staged list (the anisotropic medium's event rows): one pass, then collide2d_an with S^
+        float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool src = false;
+        sh = ss_list_events4(a, el, li, x0 + 4 * lane, G.nx, t, owned && gy < G.ny, q, cl, ar, ri,
+                             AN ? a.med.amu : 1.f, sh, wrapi(gy, G.ny), src);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const Out5 r = collide2d_an(get(q[0], k), get(q[1], k), get(q[2], k), get(q[3], k), get(q[4], k),
+                                        get(cl, k), get(sh, k), ar, ri, fs, 0.f);
             set(o[0], k, r.o0);
             set(o[1], k, r.o1);
             set(o[2], k, r.o2);
@@ -318,26 +357,20 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
         }
         return;
     }
+    // EV: a chunk whose events were not staged, each site's events looked up in the global tables
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const float q0 = get(q[0], k), q1 = get(q[1], k), q2 = get(q[2], k), q3 = get(q[3], k), q4 = get(q[4], k),
                     ck = get(cl, k);
         const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, get(dlx, k), get(dly, k)) : 0.f;
-        Out5 r;
-        if (EV) {  // events walked in the global tables
-            const int gx = x0 + 4 * lane + k;
-            const bool own = owned && gx < G.nx && gy < G.ny;
-            const float jmu = AN ? a.med.amu : 1.f;
-            const float shat = AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck,
-                                                0.f, 0.f, ar, ri, jmu)
-                                  : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck,
-                                                shat0);
-            r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f) : collide2d(q0, q1, q2, q3, q4, ck, shat);
-        } else {
-            r = AN   ? collide2d_an(q0, q1, q2, q3, q4, ck, 0.f, ar, ri, fs, 0.f)
-                : MU ? collide2d(q0, q1, q2, q3, q4, ck, shat0)
-                     : collide2d_free(q0, q1, q2, q3, q4, ck);
-        }
+        const int gx = x0 + 4 * lane + k;
+        const bool own = owned && gx < G.nx && gy < G.ny;
+        const float jmu = AN ? a.med.amu : 1.f;
+        const float shat = AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck, 0.f,
+                                            0.f, ar, ri, jmu)
+                              : site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck, shat0);
+        const Out5 r = AN ? collide2d_an(q0, q1, q2, q3, q4, ck, shat, ar, ri, fs, 0.f)
+                          : collide2d(q0, q1, q2, q3, q4, ck, shat);
         set(o[0], k, r.o0);
         set(o[1], k, r.o1);
         set(o[2], k, r.o2);
@@ -611,22 +644,25 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
             if (warp < TBY) {
                 if (va) {
                     const int r = s + warp;
-                    if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(a, r)))
-                        ss_step_a<TBY, S, true, AN, MU>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
-                                                ela);
+                    const bool ev = ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(a, r));
+                    if (ev && (!ela || AN))  // (a chunk whose events were not staged walks the global tables)
+                        ss_step_a<TBY, S, true, AN, MU>(a, st, es, emode, P, da.x, da.y, da.z, r, warp,
+                                                        p * TBY + warp + 1, t, ela);
                     else
-                        ss_step_a<TBY, S, false, AN, MU>(a, st, es, emode, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
-                                                 nullptr);
+                        ss_step_a<TBY, S, false, AN, MU>(a, st, es, emode, P, da.x, da.y, da.z, r, warp,
+                                                         p * TBY + warp + 1, t, ev ? ela : nullptr);
                 }
             } else if (warp < 2 * TBY) {
                 const int w = warp - TBY;
                 if (vb) {
                     const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
                     if (rb >= db.y && rb < db.z) {
-                        if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(a, rb)))
+                        const bool ev = ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(a, rb));
+                        if (ev && (!elb || AN))
                             ss_step_b<TBY, S, true, AN, MU>(a, P, db.x, rb, (p - 1) * TBY + w, t, elb, w);
                         else
-                            ss_step_b<TBY, S, false, AN, MU>(a, P, db.x, rb, (p - 1) * TBY + w, t, nullptr, w);
+                            ss_step_b<TBY, S, false, AN, MU>(a, P, db.x, rb, (p - 1) * TBY + w, t, ev ? elb : nullptr,
+                                                             w);
                     }
                 }
             } else if (va) {
@@ -957,12 +993,13 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                 if (va) {
                     const StepArgs &am = sargs[p % DS];
                     const int r = s + warp;
-                    if (ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(am, r)))
+                    const bool ev = ss_events(da) && (ela ? ss_list_has_row(ela, warp + 1) : ss_row_events(am, r));
+                    if (ev && !ela)
                         ss_step_a<TBY, S, true>(am, st, st, 0, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
-                                                ela);
+                                                nullptr);
                     else
                         ss_step_a<TBY, S, false>(am, st, st, 0, P, da.x, da.y, da.z, r, warp, p * TBY + warp + 1, t,
-                                                 nullptr);
+                                                 ev ? ela : nullptr);
                 }
             } else if (warp < 2 * TBY) {
                 const int w = warp - TBY;
@@ -970,12 +1007,13 @@ __global__ void __launch_bounds__((2 * TBY + 2) * 32, MINB)
                     const int rb = db.y - 2 + (db.w & 0xffff) * TBY + w;
                     if (rb >= db.y && rb < db.z) {
                         const StepArgs &bm = sargs[(p + DS - 1) % DS];
-                        if (ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(bm, rb)))
+                        const bool ev = ss_events(db) && (elb ? ss_list_has_row(elb, w) : ss_row_events(bm, rb));
+                        if (ev && !elb)
                             ss_step_b_packed<TBY, S, true>(bm, P, db.x, rb, (p - 1) * TBY + w, t, out, pk.plane, pk.W,
-                                                           dbm.y, dbm.z, dbm.w, elb, w);
+                                                           dbm.y, dbm.z, dbm.w, nullptr, w);
                         else
                             ss_step_b_packed<TBY, S, false>(bm, P, db.x, rb, (p - 1) * TBY + w, t, out, pk.plane, pk.W,
-                                                            dbm.y, dbm.z, dbm.w, nullptr, w);
+                                                            dbm.y, dbm.z, dbm.w, ev ? elb : nullptr, w);
                     }
                 }
             } else if (va) {
