@@ -1089,10 +1089,12 @@ static cudaError_t launch_bss(const StepArgs *args, const BatchUnit *units, int 
     return cudaGetLastError();
 }
 
-// Shapes of the batch's strip kernel (chunk rows, stages, CTAs per SM, chunks per unit).
+// Shapes of the batch's strip kernel (chunk rows, stages, CTAs per SM, chunks per unit).  Shape 0's units are 30 rows
+// (8 chunks): with 256 media of 64-512 rows, taller units lengthened the tail (on 256 media: 16 chunks 184.5k Mlups,
+// 8 chunks 192.3k, 32 chunks 140k).
 int batch_ss2_nshapes() { return 2; }
 int batch_ss2_rows(int shape) { return shape == 1 ? 3 : 4; }
-int batch_ss2_chunks(int shape) { return shape == 1 ? 12 : 16; }
+int batch_ss2_chunks(int shape) { return shape == 1 ? 12 : 8; }
 
 cudaError_t launch_batch_ss2(const StepArgs *args, const BatchUnit *units, int nunits, int *sched, const long long *t0p,
                              int toff, int par, const BatchPacked &pk, long long rows, int shape, cudaStream_t s) {
