@@ -416,7 +416,7 @@ lbem_status lbem_get_variant(const lbem_t *h, int *variant, int *nvariants);
  * the start of a call, written back into the members' buffers at its end; an
  * odd step count takes one single step first); 14, 15 advance two steps per
  * launch over the same packed copy by strip streaming (persistent CTAs take
- * units of 46 or 34 rows of a member's 128-column strip from a queue and stream
+ * units of 30 or 34 rows of a member's 128-column strip from a queue and stream
  * them in chunks of 4 or 3 rows through shared-memory stages).  Every variant
  * gives the same bits as each member stepped alone. */
 lbem_status lbem_batch_create(int n, lbem_t *const *members, void *stream, lbem_batch_t **out);
