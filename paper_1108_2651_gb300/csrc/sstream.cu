@@ -770,12 +770,13 @@ static cudaError_t launch_ss(const StepArgs &a, cudaStream_t s) {
 }
 
 // Shapes (rows per chunk, stages, CTAs per SM, chunks per tall unit); shared memory 86, 73, 106, 68, 73 and 68 KB.
-// Measured on 4096^2 (heterogeneous medium): 257-261k Mlups for shapes 0, 1 and 5, against 247k for the tile kernel.
+// Measured on 4096^2 (heterogeneous medium): 257-261k Mlups for shapes 0, 1 and 5, against 247k for the tile kernel,
+// before later changes; shape 1 (the default) with 12 chunks per unit 271.8k, with 16 268.8k, 24 266.9k, 8 271.6k.
 int ss2_nshapes() { return 6; }
 
 cudaError_t launch_step_2d_ss2(const StepArgs &a, int shape, cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_ss<4, 3, 3, 16>(a, s);
+        case 1: return launch_ss<4, 3, 3, 12>(a, s);
         case 2: return launch_ss<6, 3, 2, 12>(a, s);
         case 3: return launch_ss<3, 4, 3, 24>(a, s);
         case 4: return launch_ss<4, 3, 3, 32>(a, s);
@@ -1104,10 +1105,10 @@ cudaError_t launch_batch_ss2(const StepArgs *args, const BatchUnit *units, int n
 
 // An anisotropic medium (uniform tensor, no pole): the strip kernel with the general kernel's site update, chunk
 // rows, stages, CTAs per SM and chunks per unit of shape 1.
-cudaError_t launch_step_2d_ss2_an(const StepArgs &a, cudaStream_t s) { return launch_ss<4, 3, 3, 16, true>(a, s); }
+cudaError_t launch_step_2d_ss2_an(const StepArgs &a, cudaStream_t s) { return launch_ss<4, 3, 3, 12, true>(a, s); }
 
 // A heterogeneous permeability: the strip kernel with the d_x ln mu, d_y ln mu planes staged beside c_L^2 (and kept
-// with it for step t+1), 4-row chunks, 3 stages, 2 CTAs per SM (96 KB), 16 chunks per unit.
+// with it for step t+1), 4-row chunks, 3 stages, 2 CTAs per SM (96 KB), 16 chunks per unit (12: 1.4 % slower).
 cudaError_t launch_step_2d_ss2_mu(const StepArgs &a, cudaStream_t s) {
     return launch_ss<4, 3, 2, 16, false, true>(a, s);
 }
