@@ -43,7 +43,7 @@ BYTES_PER_SITE = {"f32": 44, "f16": 24, "bf16": 24, "i16b": 26.5}
 # (workload, storage, variant); the capture and its command are summarised in profiles/.  Only reported for
 # the kernel that was captured.
 NCU_TRAFFIC = {("het2d_4096", "f32", "tb2-0"): 433.764864e6 + 300.201472e6,
-               ("het2d_4096", "f32", "tb2-10"): 415.521280e6 + 284.354560e6,
+               ("het2d_4096", "f32", "tb2-10"): 412.030720e6 + 284.538624e6,
                ("het2d_4096", "f16", "tb2-0"): 238.282240e6 + 128.542464e6,
                ("het2d_4096", "i16b", "tb2-0"): 264.385536e6 + 150.971648e6,
                # dram__bytes.sum.per_second x gpu__time_duration.sum (6.657849 TB/s x 174.752 us), step2d_gen
