@@ -928,11 +928,71 @@ __global__ void __launch_bounds__(BLOCK) diag2d(Grid G, PopBuf in, const float *
     }
 }
 
+// The same three sums for a periodic grid (no walls), rows strided over the blocks and columns over the threads:
+// the energy and sum g^2/w terms of a site formed in FP32 (its pulled FP32 populations, one division each) and
+// added in FP64; the divergence from the eight FP32 populations its four neighbours' B need, differenced in FP64
+// (each B component is exact there).  GB300's FP64 rate made the all-FP64 site terms of diag2d the cost of a call.
+template <int ST>
+__global__ void __launch_bounds__(BLOCK) diag2d_periodic(Grid G, PopBuf in, const float *cL2, double *partials,
+                                                         const float *Pz, float r) {
+    __shared__ double sh[BLOCK / 32];
+    double en = 0.0, inv = 0.0, dv = 0.0;
+    const float ri = 1.f / r;
+    const double fs64 = (double)r + 1.0 / (double)r;  // for w0 of an anisotropic medium (it can be small there)
+    for (int y = blockIdx.x; y < G.ny; y += gridDim.x) {
+        const int ym = y == 0 ? G.ny - 1 : y - 1, yp = y + 1 == G.ny ? 0 : y + 1;
+        for (int x = threadIdx.x; x < G.nx; x += BLOCK) {
+            const int xm = x == 0 ? G.nx - 1 : x - 1, xp = x + 1 == G.nx ? 0 : x + 1;
+            const float g0 = Codec<ST>::load1(in, 0, y, x), g1 = Codec<ST>::load1(in, 1, y, xm),
+                        g2 = Codec<ST>::load1(in, 2, ym, x), g3 = Codec<ST>::load1(in, 3, y, xp),
+                        g4 = Codec<ST>::load1(in, 4, yp, x);
+            const long long o = (long long)y * G.pitch + x;
+            const float cl = cL2[o];
+            const float Ez = -cl * (((g0 + g1) + (g2 + g3)) + g4) - (Pz ? Pz[o] : 0.f);
+            const float bx = r * (g4 - g2), by = (g1 - g3) * ri;
+            en += (double)(bx * bx + by * by + Ez * Ez / cl);
+            const float wx = 0.5f * r * cl, wy = 0.5f * cl * ri;
+            const float q = (g1 * g1 + g3 * g3) / wx + (g2 * g2 + g4 * g4) / wy;
+            double q0 = 0.0;  // g0^2 / w0; isotropic w0 = 1 - 2 c_L^2 is exact in FP32 wherever it is below 1/2
+            if (r == 1.f) {
+                const float w0 = 1.f - 2.f * cl;
+                if (w0 != 0.f) q0 = (double)(g0 * g0 / w0);
+            } else {
+                const double w0 = 1.0 - fs64 * (double)cl;
+                if (w0 != 0.0) q0 = (double)g0 * (double)g0 / w0;
+            }
+            inv += 2.0 * ((double)q + q0);  // g_xy and g_yx = -g_xy both count
+            // B at the four neighbours: B_x = g4 - g2 at (x +- 1, y), B_y = g1 - g3 at (x, y +- 1)
+            const double bxp = (double)Codec<ST>::load1(in, 4, yp, xp) - (double)Codec<ST>::load1(in, 2, ym, xp);
+            const double bxm = (double)Codec<ST>::load1(in, 4, yp, xm) - (double)Codec<ST>::load1(in, 2, ym, xm);
+            const double byp = (double)Codec<ST>::load1(in, 1, yp, xm) - (double)Codec<ST>::load1(in, 3, yp, xp);
+            const double bym = (double)Codec<ST>::load1(in, 1, ym, xm) - (double)Codec<ST>::load1(in, 3, ym, xp);
+            const double div = 0.5 * (bxp - bxm) + 0.5 * (byp - bym);
+            dv += div * div;
+        }
+    }
+    const double a = block_sum(en, sh), b = block_sum(inv, sh), c = block_sum(dv, sh);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = a;
+        partials[3 * blockIdx.x + 1] = b;
+        partials[3 * blockIdx.x + 2] = c;
+    }
+}
+
 cudaError_t launch_diag_2d(const lbem_t *h, double *partials, int nblocks, cudaStream_t s) {
     const PopBuf &in = h->buf[h->cur];
     const Walls w = handle_walls(h);
     const float *Pz = h->disp ? h->pole_P(h->cur) : nullptr;
     const float r = h->aniso_r;
+    if (!w.kind[0] && !w.kind[1]) {
+        switch (h->storage) {
+            case LBEM_F32: diag2d_periodic<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, Pz, r); break;
+            case LBEM_F16: diag2d_periodic<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, Pz, r); break;
+            case LBEM_BF16: diag2d_periodic<LBEM_BF16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, Pz, r); break;
+            default: diag2d_periodic<LBEM_I16B><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, Pz, r); break;
+        }
+        return cudaGetLastError();
+    }
     switch (h->storage) {
         case LBEM_F32: diag2d<LBEM_F32><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;
         case LBEM_F16: diag2d<LBEM_F16><<<nblocks, BLOCK, 0, s>>>(h->grid, in, h->cL2, partials, w, Pz, r); break;
