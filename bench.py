@@ -1045,10 +1045,7 @@ def main():
         E_h = torch.empty(3 * nsite, dtype=torch.float32).pin_memory()
         B_h = torch.empty(3 * nsite, dtype=torch.float32).pin_memory()
         tr_h = torch.empty(p.rec_site.size * nsteps, dtype=torch.float32).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        reps = max(1, min(args.steps, 2))
-        for _ in range(reps):
+        def e2e_pass():
             upload_medium(eps_h)
             lbem.lbem_set_sources(h, p.src_site, p.src_comp, p.src_amp)
             lbem.lbem_set_fields(h)
@@ -1056,6 +1053,13 @@ def main():
             lbem.lbem_fields(h, E_h, B_h)
             lbem.lbem_traces(h, tr_h)
             lbem.lbem_diagnostics(h)
+
+        e2e_pass()  # warm-up: the library's host staging buffer is allocated on the first host-buffer call
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 2))
+        for _ in range(reps):
+            e2e_pass()
         dt = (time.perf_counter() - t0) / reps
         dt = dist_max(dt, world)
         nb = lambda t: t.numel() * t.element_size()
