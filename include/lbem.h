@@ -134,10 +134,11 @@ lbem_status lbem_set_medium(lbem_t *h, const float *eps_r, const float *mu_r);
  * -cbar^2 sigma with cbar^2 = sqrt(c_x^2 c_y^2), B_x = r (g_4 - g_2), B_y =
  * (g_1 - g_3) / r, r = sqrt(mu_xx / mu_yy); a current j_z enters with
  * mu = sqrt(mu_xx mu_yy).  mu_xx = mu_yy = mu is the isotropic scheme with a
- * uniform mu.  2D, LBEM_F32 storage (LBEM_ERR_ARG otherwise); with walls the
- * handle then steps one step per launch with the general kernel (layers and a
- * dispersive pole included), without walls in pairs (lbem_set_temporal_blocking),
- * bit-identical to single steps; lbem_set_medium makes it isotropic again.  Batches
+ * uniform mu.  2D, LBEM_F32 storage (LBEM_ERR_ARG otherwise); the handle then
+ * steps in pairs (lbem_set_temporal_blocking; with walls and layers each pair is
+ * followed by a pass recomputing the bands next to the walls), with a dispersive
+ * pole and walls one step per launch with the general kernel, bit-identical to
+ * single steps either way; lbem_set_medium makes it isotropic again.  Batches
  * and the adjoint take isotropic handles only.  Synchronises the stream. */
 lbem_status lbem_set_medium_aniso(lbem_t *h, const float *eps_r, double mu_xx, double mu_yy);
 
@@ -251,10 +252,11 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * grid of uniform mu with at least 12 000 000 sites takes shape 10, any other shape 0.  With
  * a heterogeneous mu (FP32; the two grad ln mu planes are staged beside c_L^2, 52 instead of 104 bytes per
  * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, and 1 = 14 rows, 512, 2 exist; a larger
- * shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) without walls
- * steps in pairs with shape 0 (256 threads, 5 per SM) whatever shape is set, a dispersive pole without walls or
- * a mu array with shape 0 at 4 per SM, both bit-identical to their single steps; with walls (or a pole with a
- * mu array), and for steps_per_pass = 3, every step of these media is a single step.
+ * shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) steps in pairs
+ * with shape 0 (the tile kernel, 256 threads, 5 per SM) or 1 (the strip kernel, the default from 12 000 000
+ * sites), walls and layers included; a dispersive pole without walls or a mu array with shape 0 at 4 per SM;
+ * both bit-identical to their single steps.  With a pole and walls (or a pole with a mu array), and for
+ * steps_per_pass = 3, every step of these media is a single step.
  * LBEM_ERR_ARG for values outside the current handle's set. */
 lbem_status lbem_set_temporal_blocking(lbem_t *h, int steps_per_pass, int tile_shape);
 

@@ -169,10 +169,11 @@ static int graph_key(const lbem_t *h) { return (h->variant * 4 + h->tblock) * 16
 
 // Whether launches of two (three) steps apply: 2D; FP32 storage with any medium, 16-bit storage with uniform mu
 // and nx % 4 == 0; three steps per launch exist for FP32 storage with uniform mu.
-// An anisotropic medium or a dispersive pole takes two steps per launch (tile shape 0) unless walls or a
-// heterogeneous mu come with it, which the general single-step kernel handles.
+// An anisotropic medium or a dispersive pole takes two steps per launch unless a heterogeneous mu comes with it,
+// or walls with the pole, which the general single-step kernel handles (with walls an anisotropic medium's launches
+// of two steps are followed by the anisotropic edge pass).
 static bool multi_step_base(const lbem_t *h) {
-    if (h->general() && (h->walls() || h->has_mu)) return false;
+    if (h->general() && (h->has_mu || (h->walls() && h->disp))) return false;
     return h->dim == 2 && (h->storage == LBEM_F32 || (!h->has_mu && h->grid.nx % 4 == 0));
 }
 static bool two_step_ok(const lbem_t *h) { return h->tblock >= 2 && multi_step_base(h); }
@@ -201,11 +202,11 @@ static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two
 // (two-step) kernel when enabled, a remaining pair with the two-step kernel's default tile, single steps
 // otherwise; returns the buffer holding the final state in *cur_out.
 // With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu); the
-// general kernel applies walls and layers itself.
+// general kernel's single steps apply walls and layers themselves (a pole with walls steps only that way).
 static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
-    if (!h->walls() || h->general() || h->dim != 2) return cudaSuccess;
+    if (!h->walls() || h->dim != 2 || h->disp || (h->aniso && k == 1)) return cudaSuccess;
     return launch_edge_2d(a, handle_walls(h), h->d_tiles[k], h->ntiles[k],
-                          h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->stream);
+                          h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->aniso, h->stream);
 }
 
 static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {

@@ -524,7 +524,7 @@ struct lbem {
     // anisotropic medium (lbem_set_medium_aniso): r = sqrt(mu_xx / mu_yy), mubar = sqrt(mu_xx mu_yy)
     bool aniso = false;
     float aniso_r = 1.f, aniso_mu = 1.f;
-    // media the general kernel steps (general.cu); without walls or mu planes also the tile kernel, two steps
+    // media the general kernel steps (general.cu); without mu planes (and a pole without walls) also two steps
     // per launch
     bool general() const { return disp || aniso; }
     float aniso_fsum() const { return aniso ? aniso_r + 1.f / aniso_r : 2.f; }  // (c_x^2 + c_y^2) / cbar^2
@@ -639,7 +639,7 @@ void adjoint_free(lbem_t *h);
 std::vector<EdgeTile> edge_tiles(const Grid &G, const int kind[2], int layer, int k);
 size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu);
 cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
-                           cudaStream_t s);
+                           bool aniso, cudaStream_t s);
 cudaError_t launch_medium_grad_walls(const lbem_t *h, cudaStream_t s);
 // general.cu: single steps with a dispersive pole and / or an anisotropic medium (walls and layers applied in the
 // kernel)

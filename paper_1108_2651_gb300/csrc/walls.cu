@@ -37,7 +37,9 @@ constexpr int EDGE_PER_THREAD = EDGE_MAX_WINDOW / EDGE_THREADS;
 // holds sources or receivers.
 __host__ __device__ constexpr int edge_floats_per_site(bool mu) { return 12 + (mu ? 2 : 0); }
 
-template <bool MU>
+// AN: an anisotropic medium (a uniform in-plane tensor, a.med.ar, a.med.amu, no pole): collide2d_an and the events
+// scaled as site_events scales them, as the general single-step kernel and step2d_ss2<AN> / step2d_tb2<AN> do.
+template <bool MU, bool AN = false>
 __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, const EdgeTile *tiles, int k) {
     extern __shared__ __align__(16) float sm[];
     const Grid &G = a.g;
@@ -107,6 +109,7 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, c
     }
     __syncthreads();
 
+    const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
     for (int step = 0; step < k; step++) {
         const long long t = a.t + step;
 #pragma unroll
@@ -133,9 +136,11 @@ __global__ void __launch_bounds__(EDGE_THREADS, 3) edge2d(StepArgs a, Walls w, c
             if (MU) shat = mu_source(g4 - g2, g1 - g3, dxm[s], dym[s]);
             if (rowev[j]) {
                 const bool owned = i >= k && i < k + T.w && j >= k && j < k + T.h;
-                shat = site_events(a, gx, gy, t, owned, g0, g1, g2, g3, g4, c, shat);
+                shat = AN ? site_events(a, gx, gy, t, owned, g0, g1, g2, g3, g4, c, 0.f, 0.f, ar, ri, a.med.amu)
+                          : site_events(a, gx, gy, t, owned, g0, g1, g2, g3, g4, c, shat);
             }
-            Out5 r = collide2d(g0, g1, g2, g3, g4, c, shat);
+            const Out5 r = AN ? collide2d_an(g0, g1, g2, g3, g4, c, shat, ar, ri, fs, 0.f)
+                              : collide2d(g0, g1, g2, g3, g4, c, shat);
             const float f = fac[s];
             nxt[s] = __fmul_rn(r.o0, f);
             nxt[NW + s] = __fmul_rn(r.o1, f);
@@ -221,18 +226,25 @@ size_t edge_smem_bytes(int k, const std::vector<EdgeTile> &tiles, bool mu) {
 }
 
 cudaError_t launch_edge_2d(const StepArgs &a, const Walls &w, const EdgeTile *d_tiles, int ntiles, size_t smem, int k,
-                           cudaStream_t s) {
+                           bool aniso, cudaStream_t s) {
     if (ntiles == 0) return cudaSuccess;
-    static bool attr[2] = {false, false};
+    static bool attr[3] = {false, false, false};
     const bool mu = a.med.dlnmu != nullptr;
-    if (!attr[mu]) {
+    if (aniso && mu) return cudaErrorInvalidValue;  // an anisotropic medium has a uniform permeability
+    const int v = aniso ? 2 : mu ? 1 : 0;
+    if (!attr[v]) {
         const int max_bytes = (int)((sizeof(float) * edge_floats_per_site(true) + 3 * sizeof(int)) * EDGE_MAX_WINDOW);
-        cudaError_t e = mu ? cudaFuncSetAttribute(edge2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes)
-                           : cudaFuncSetAttribute(edge2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaError_t e = v == 2   ? cudaFuncSetAttribute(edge2d<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        max_bytes)
+                        : v == 1 ? cudaFuncSetAttribute(edge2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        max_bytes)
+                                 : cudaFuncSetAttribute(edge2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        max_bytes);
         if (e != cudaSuccess) return e;
-        attr[mu] = true;
+        attr[v] = true;
     }
-    if (mu) edge2d<true><<<ntiles, EDGE_THREADS, smem, s>>>(a, w, d_tiles, k);
+    if (v == 2) edge2d<false, true><<<ntiles, EDGE_THREADS, smem, s>>>(a, w, d_tiles, k);
+    else if (v == 1) edge2d<true><<<ntiles, EDGE_THREADS, smem, s>>>(a, w, d_tiles, k);
     else edge2d<false><<<ntiles, EDGE_THREADS, smem, s>>>(a, w, d_tiles, k);
     return cudaGetLastError();
 }

@@ -126,6 +126,45 @@ def test_two_step_launches_equal_single_steps_bit_for_bit(lbem, shape, aniso):
         np.testing.assert_array_equal(tr.cpu().double().numpy()[:, :37], ref[2])
 
 
+@pytest.mark.parametrize("shape,aniso,bc,layer", [((17, 45), (0.7, 1.6), (PEC, 0), 0),
+                                                ((40, 131), (2.0, 1.0), (PMC, PEC), 6),
+                                                ((64, 300), (3.0, 1.5), (PEC, PEC), 12),
+                                                ((9, 7), (1.3, 2.2), (PEC, PMC), 3)])
+def test_walls_two_step_launches_equal_single_steps_bit_for_bit(lbem, shape, aniso, bc, layer):
+    """With walls and absorbing layers an anisotropic medium also steps in pairs: the tile or the strip kernel
+    (periodic), then the edge pass recomputing the two steps on the bands next to the walls with the per-axis
+    collision. The same bits as single steps of the general kernel, which applies the walls and layers itself,
+    with graphs and odd step counts; with a pole as well the medium steps singly."""
+    import torch
+
+    p = _problem(shape, 950 + shape[1], 37, aniso, bc, layer)
+    ref = gpu_run(p, steps_per_pass=1)
+    for tile_shape, graphs in ((0, False), (0, True), (1, False), (1, True)):
+        stream = torch.cuda.Stream()
+        s = lbem.Solver(p.shape, stream=stream.cuda_stream)
+        s.set_problem(p)
+        lbem.lbem_set_temporal_blocking(s.h, 2, tile_shape)
+        assert lbem.lbem_get_temporal_blocking(s.h)[:2] == (2, tile_shape)
+        lbem.lbem_set_graphs(s.h, graphs)
+        s.step(10)
+        s.step(27)
+        E, B = s.fields()
+        tr = s.traces(p.rec_site.size)
+        torch.cuda.synchronize()
+        lbem.lbem_sync(s.h)
+        lbem.lbem_check_guards(s.h)
+        s.close()
+        msg = f"tile shape {tile_shape}, graphs {graphs}"
+        np.testing.assert_array_equal(np.moveaxis(E.cpu().double().numpy(), 0, -1), ref[0], err_msg=msg)
+        np.testing.assert_array_equal(np.moveaxis(B.cpu().double().numpy(), 0, -1), ref[1], err_msg=msg)
+        np.testing.assert_array_equal(tr.cpu().double().numpy()[:, :37], ref[2], err_msg=msg)
+    q = _problem(shape, 950 + shape[1], 5, aniso, bc, layer, pole=True)
+    s = lbem.Solver(q.shape)
+    s.set_problem(q)
+    assert lbem.lbem_get_temporal_blocking(s.h)[0] == 1
+    s.close()
+
+
 def test_anisotropic_full_size_matches_oracle(lbem):
     """4096^2 heterogeneous medium with mu = diag(2, 1) (the benchmark's anisotropic workload), 20 steps."""
     p = W.heterogeneous_2d_aniso(4096, seed=2, nsteps=20)
@@ -151,7 +190,7 @@ def test_anisotropy_errors_and_switching_back(lbem):
     assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2  # no walls, no pole: two steps per launch
     assert lbem.lbem_get_temporal_blocking(s.h)[2] == 2  # the tile kernel and the strip kernel
     lbem.lbem_set_boundaries(s.h, (PEC, 0, 0), 0, 0.0)
-    assert lbem.lbem_get_temporal_blocking(s.h)[0] == 1  # walls: the general kernel, one step per launch
+    assert lbem.lbem_get_temporal_blocking(s.h)[0] == 2  # walls: still pairs, then the anisotropic edge pass
     lbem.lbem_set_boundaries(s.h, (0, 0, 0), 0, 0.0)
     with pytest.raises(lbem.LbemError):
         lbem.lbem_forward_record(s.h, 4, 2)
