@@ -1,5 +1,6 @@
-// Two time steps per launch by streaming a strip of rows through a ring of shared-memory stages (2D, FP32 storage,
-// uniform mu).
+// Two time steps per launch by streaming a strip of rows through a ring of shared-memory stages (2D, FP32 storage):
+// uniform mu; variants for a heterogeneous mu (the two grad ln mu planes staged as planes 6-7) and for an
+// anisotropic tensor (the per-axis collision); and the batch of independent media over their packed copy.
 //
 // A CTA owns a strip of 128 columns (x0 .. x0+127) and a run of rows ys .. ye-1 and walks down the run in chunks of
 // TBY rows.  A chunk of the state at t (the five population planes, each staged shifted by its pull offset in y so
@@ -18,6 +19,11 @@
 // columns (the copy fills zeros there) and six more boxes of 4 columns bring the periodic images into a side buffer,
 // from which those few pulls read.  Chunks whose rows wrap periodically, and ragged grids, are staged by the producer
 // warp's asynchronous copies, which arrive on the stage's mbarrier as they land.
+//
+// A chunk's sources and receivers are staged beside its descriptor by the producer (row boundaries read a unit
+// ahead, records copied asynchronously on the stage's mbarrier); a row holding some matches them against its lanes'
+// sites in one pass, writes the receivers from the pulled populations and adds the sources' terms after the plain
+// collision, which is the collision with S^ operation for operation.
 //
 // HBM traffic per two site updates: 24 bytes read and 20 written; the two rows outside a run and the four columns
 // either side of a strip are read again, mostly from L2.  Nothing is computed twice except those rows and the ring
