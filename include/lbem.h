@@ -247,12 +247,12 @@ lbem_status lbem_set_watchdog(lbem_t *h, int every, double max_growth);
  * 128-column strip down a segment of rows through registers (5 or 4 blocks of 128 threads per SM); 9 - 14 =
  * strip streaming: persistent CTAs take units of rows of a 128-column strip from a queue and stream them in
  * chunks through shared-memory stages (a producer warp loads chunks ahead by TMA), computing step t+1 one row
- * behind step t (chunk rows, stages, CTAs per SM, chunks per unit: 9 = 4, 4, 2, 16; 10 = 4, 3, 3, 16;
+ * behind step t (chunk rows, stages, CTAs per SM, chunks per unit: 9 = 4, 4, 2, 16; 10 = 4, 3, 3, 12;
  * 11 = 6, 3, 2, 12; 12 = 3, 4, 3, 24; 13 = 4, 3, 3, 32; 14 = 3, 4, 3, 12).  With -1 (or never set), an FP32
  * grid of uniform mu with at least 12 000 000 sites takes shape 10, any other shape 0.  With
  * a heterogeneous mu (FP32; the two grad ln mu planes are staged beside c_L^2, 52 instead of 104 bytes per
- * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, and 1 = 14 rows, 512, 2 exist; a larger
- * shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) steps in pairs
+ * site and step pair) only 0 = 6 rows, 256 threads, 4 per SM, 1 = 14 rows, 512, 2, and 2 = strip streaming
+ * (4, 3, 2, 16; the default from 12 000 000 sites) exist; a larger shape set before the medium falls back to 0.  An anisotropic medium (lbem_set_medium_aniso) steps in pairs
  * with shape 0 (the tile kernel, 256 threads, 5 per SM) or 1 (the strip kernel, the default from 12 000 000
  * sites), walls and layers included; a dispersive pole without walls or a mu array with shape 0 at 4 per SM;
  * both bit-identical to their single steps.  With a pole and walls (or a pole with a mu array), and for
