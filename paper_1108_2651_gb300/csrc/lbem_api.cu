@@ -203,10 +203,32 @@ static int steps_per_launch(const lbem_t *h) { return three_step_ok(h) ? 3 : two
 // otherwise; returns the buffer holding the final state in *cur_out.
 // With walls: the k steps of a launch recomputed on the bands the walls and layers change (walls.cu); the
 // general kernel's single steps apply walls and layers themselves (a pole with walls steps only that way).
-static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) {
+static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k, cudaStream_t s) {
     if (!h->walls() || h->dim != 2 || h->disp || (h->aniso && k == 1)) return cudaSuccess;
     return launch_edge_2d(a, handle_walls(h), h->d_tiles[k], h->ntiles[k],
-                          h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->aniso, h->stream);
+                          h->has_mu ? h->tile_smem_mu[k] : h->tile_smem[k], k, h->aniso, s);
+}
+static cudaError_t edge_fixup(const lbem_t *h, const StepArgs &a, int k) { return edge_fixup(h, a, k, h->stream); }
+
+// Whether a two-step shape is a strip-streaming launch (sstream.cu) for this medium.
+static bool strip_shape(const lbem_t *h, int shape) {
+    if (h->storage != LBEM_F32 || h->disp) return false;
+    const int first = 7 + rs2_nshapes();  // the strip shapes follow the tile and register-streaming ones
+    return h->aniso ? shape == 1 : h->has_mu ? shape == 2 : shape >= first && shape < first + ss2_nshapes();
+}
+
+// With walls, a strip-streaming launch of k steps writes only outside the bands the edge pass rewrites (the edge
+// tiles' bands: the sites within max(L, 1) + k - 1 of a wall, the whole axis when the two bands meet), so that the
+// two launches write disjoint sites and the edge pass can run beside it.
+static void write_window(const lbem_t *h, int k, StepArgs &a) {
+    const int bw = std::max(h->layer, 1) + k - 1, n[2] = {h->grid.nx, h->grid.ny};
+    int *lo[2] = {&a.wx0, &a.wy0}, *hi[2] = {&a.wx1, &a.wy1};
+    for (int d = 0; d < 2; d++) {
+        if (!h->bc[d]) continue;
+        const bool all = 2 * bw >= n[d];
+        *lo[d] = all ? 0 : bw;
+        *hi[d] = all ? 0 : n[d] - bw;
+    }
 }
 
 static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nsteps, int *cur_out) {
@@ -222,11 +244,26 @@ static cudaError_t enqueue_steps(const lbem_t *h, int cur, long long t0, int nst
         }
     }
     if (two_step_ok(h)) {
+        const int shape = two_step_shape(h);
+        // walls beside a strip-streaming launch: fork the edge pass onto its stream, launch it first (its tiles
+        // take their SMs before the persistent strip grid fills them), and join it before the next launch
+        const bool beside = h->walls() && h->dim == 2 && h->edge_stream && strip_shape(h, shape);
         for (; n + 2 <= nsteps; n += 2) {
             StepArgs a = step_args(h, cur);
             a.t = t0 + n;
-            cudaError_t e = launch_step_2d_tb2(a, h->storage, two_step_shape(h), h->stream);
-            if (e == cudaSuccess) e = edge_fixup(h, a, 2);
+            cudaError_t e;
+            if (beside) {
+                write_window(h, 2, a);
+                e = cudaEventRecord(h->ev_fork, h->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->edge_stream, h->ev_fork, 0);
+                if (e == cudaSuccess) e = edge_fixup(h, a, 2, h->edge_stream);
+                if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->edge_stream);
+                if (e == cudaSuccess) e = launch_step_2d_tb2(a, h->storage, shape, h->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+            } else {
+                e = launch_step_2d_tb2(a, h->storage, shape, h->stream);
+                if (e == cudaSuccess) e = edge_fixup(h, a, 2);
+            }
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -427,6 +464,12 @@ void lbem_destroy(lbem_t *h) {
                     (void *)h->d_P2, (void *)h->d_pc, (void *)h->d_pb, (void *)h->d_pa})
         gfree(h, p);
     for (int k = 1; k <= 3; k++) gfree(h, h->d_tiles[k]);
+    if (h->edge_stream) {
+        cudaStreamSynchronize(h->edge_stream);
+        cudaStreamDestroy(h->edge_stream);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
@@ -763,6 +806,11 @@ lbem_status lbem_set_boundaries(lbem_t *h, const int kind[3], int layer, double 
         }
         LBEM_CUDA(gmalloc(h, (void **)dst[a], sizeof(float) * alloc[a], "layer factors"));
         LBEM_CUDA(cudaMemcpy(*dst[a], f.data(), sizeof(float) * alloc[a], cudaMemcpyHostToDevice));
+    }
+    if (h->dim == 2 && !h->edge_stream) {  // the edge pass's stream and events (kept for the handle's life)
+        LBEM_CUDA(cudaStreamCreateWithFlags(&h->edge_stream, cudaStreamNonBlocking));
+        LBEM_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        LBEM_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     }
     for (int k = 1; k <= 3 && h->dim == 2; k++) {  // 2D: the edge kernel's tiles (the 3D kernel applies walls)
         const std::vector<EdgeTile> t = edge_tiles(h->grid, h->bc, h->layer, k);

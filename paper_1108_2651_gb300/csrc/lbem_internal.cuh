@@ -385,6 +385,9 @@ struct StepArgs {
     // work queue of the strip-streaming kernel (sstream.cu), two counters of the handle: [0] the next unit to take,
     // [1] the CTAs that finished; both zero between launches (the last CTA out resets them)
     int *sched = nullptr;
+    // the strip-streaming kernel writes sites and receiver samples only with wx0 <= x < wx1 and wy0 <= y < wy1: with
+    // walls its launches leave the bands next to them to the edge pass running beside it (everything otherwise)
+    int wx0 = 0, wx1 = 1 << 30, wy0 = 0, wy1 = 1 << 30;
 };
 
 // Periodic index, cheap when v is already in range (the common case).
@@ -514,6 +517,10 @@ struct lbem {
     float *d_fx = nullptr, *d_fy = nullptr, *d_fz = nullptr;
     lbk::EdgeTile *d_tiles[4] = {nullptr, nullptr, nullptr, nullptr};
     int ntiles[4] = {0, 0, 0, 0};
+    // 2D walls: the stream the edge pass runs on beside a strip-streaming launch, and the events that fork it from
+    // and join it to the handle's stream
+    cudaStream_t edge_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // frequency-dispersive permittivity (lbem_set_dispersion): pole parameters and state, planes (pitch layout)
     // P has two planes, paired with the population buffers: P at the time of buf[c] is pole_P(c), so a launch
     // reads P from the plane of its input's parity and writes the other one (every launch flips cur).

@@ -227,7 +227,9 @@ __device__ __forceinline__ float4 ss_list_events4(const StepArgs &a, const SsEvL
                 if (m3) sh.w = __fsub_rn(sh.w, d);
             }
         } else if (owned && t < a.evt.cap) {
-            const bool r0 = m0 && gx0 < nx, r1 = m1 && gx0 + 1 < nx, r2 = m2 && gx0 + 2 < nx, r3 = m3 && gx0 + 3 < nx;
+            const int lo = a.wx0, hi = min(a.wx1, nx);  // owned columns (the write window's, inside the grid)
+            const bool r0 = m0 && gx0 >= lo && gx0 < hi, r1 = m1 && gx0 + 1 >= lo && gx0 + 1 < hi,
+                       r2 = m2 && gx0 + 2 >= lo && gx0 + 2 < hi, r3 = m3 && gx0 + 3 >= lo && gx0 + 3 < hi;
             if (r0 || r1 || r2 || r3) {
                 const int k = r0 ? 0 : r1 ? 1 : r2 ? 2 : 3;
                 const float g0 = get(q[0], k), g1 = get(q[1], k), g2 = get(q[2], k), g3 = get(q[3], k),
@@ -304,6 +306,7 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
     const Grid &G = a.g;
     const int lane = threadIdx.x & 31;
     const float ar = AN ? a.med.ar : 1.f, ri = AN ? __fdiv_rn(1.f, ar) : 1.f, fs = __fadd_rn(ar, ri);
+    owned = owned && gy >= a.wy0 && gy < a.wy1;  // receivers only inside the write window
     if (!EV) {
         // S^ of the four sites: the permeability term (MU), minus mu j_z of the sources of a staged list `el`, whose
         // receivers are written here from the pre-collision populations
@@ -370,7 +373,7 @@ __device__ __forceinline__ void ss_update4(const StepArgs &a, const float4 (&q)[
                     ck = get(cl, k);
         const float shat0 = MU ? mu_source(q4 - q2, q1 - q3, get(dlx, k), get(dly, k)) : 0.f;
         const int gx = x0 + 4 * lane + k;
-        const bool own = owned && gx < G.nx && gy < G.ny;
+        const bool own = owned && gx < G.nx && gy < G.ny && gx >= a.wx0 && gx < a.wx1;
         const float jmu = AN ? a.med.amu : 1.f;
         const float shat = AN ? site_events(a, wrapi(gx, G.nx), wrapi(gy, G.ny), t, own, q0, q1, q2, q3, q4, ck, 0.f,
                                             0.f, ar, ri, jmu)
@@ -486,15 +489,33 @@ __device__ __forceinline__ void ss_step_b(const StepArgs &a, const float *P, int
     float4 q[5], cl, o[5], dlx = make_float4(0.f, 0.f, 0.f, 0.f), dly = dlx;
     ss_pull(P, Gm::PL_P, ub % Gm::M, c, q, cl, MU ? &dlx : nullptr, MU ? &dly : nullptr);
     ss_update4<EV, AN, MU>(a, q, cl, x0, rb, t + 1, true, o, el, w, dlx, dly);
-    if (x0 + 4 * lane < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
-        float4 *op = reinterpret_cast<float4 *>(static_cast<float *>(a.out.data) + (long long)rb * G.pitch + x0 +
-                                                4 * lane);
-        const long long pl4 = G.plane / 4;
-        __stcs(op, o[0]);
-        __stcs(op + pl4, o[1]);
-        __stcs(op + 2 * pl4, o[2]);
-        __stcs(op + 3 * pl4, o[3]);
-        __stcs(op + 4 * pl4, o[4]);
+    const int xs = x0 + 4 * lane;
+    if (xs < G.pitch) {  // pitch is a multiple of 4: a lane's 4 columns are all in or all out
+        float *op = static_cast<float *>(a.out.data) + (long long)rb * G.pitch + xs;
+        // the write window (walls: the bands next to them are the edge pass's); columns past nx are padding
+        unsigned m = 15u;
+        if (a.wx0 > 0 || a.wy0 > 0 || a.wx1 < G.pitch || a.wy1 < G.ny) {  // (a window: walls)
+            const bool rowin = rb >= a.wy0 && rb < a.wy1;
+            m = 0u;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                m |= (xs + j >= G.nx || (rowin && xs + j >= a.wx0 && xs + j < a.wx1)) ? 1u << j : 0u;
+        }
+        if (m == 15u) {
+            float4 *op4 = reinterpret_cast<float4 *>(op);
+            const long long pl4 = G.plane / 4;
+            __stcs(op4, o[0]);
+            __stcs(op4 + pl4, o[1]);
+            __stcs(op4 + 2 * pl4, o[2]);
+            __stcs(op4 + 3 * pl4, o[3]);
+            __stcs(op4 + 4 * pl4, o[4]);
+        } else if (m) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if ((m >> j) & 1u)
+#pragma unroll
+                    for (int p = 0; p < 5; p++) op[p * G.plane + j] = get(o[p], j);
+        }
     }
 }
 
